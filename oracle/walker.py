@@ -1,0 +1,79 @@
+"""The Step 6' random walk over integer alias tables, driven by Philox4x32-10
+(oracle; test infrastructure only).
+
+One walker = one Monte Carlo sample of Sec. II.E with fixed start lead p (Eq. elast_lin_xpq):
+Step 4 draws the injection eigenvector of Gamma_p, then Step 6' repeats (site or lead) until a
+lead is drawn.  Random numbers: draw s of walker ``wid`` in task ``task`` uses Philox block
+b = s // 2 with counter (b, wid_lo, wid_hi, task) and key (seed_lo, seed_hi); even s takes output
+words (x0, x1), odd s takes (x2, x3).  Draw 0 is the injection draw (always consumed); draws
+1, 2, ... are transitions and each one counts as a step.  A draw with words (x, y) over a K-entry
+row picks c = (x*K)>>32 and keeps c if y < thr[c], else takes alias[c].
+
+Outcomes per walker: lead 0 (L) or 1 (R); -1 when the start lead has no open channel at this
+energy (Tr Gamma_p A = 0, nothing to inject); -2 when ``max_steps`` transitions were drawn without
+absorption (the walk is cut, the sample is counted as truncated).
+"""
+import numpy as np
+
+from .philox import philox4x32_10
+
+MASK32 = np.uint64(0xFFFFFFFF)
+
+
+def walk(entries, mode_entries, n, W, c_open, task, start_lead, seed, wids, max_steps):
+    """Run walkers ``wids`` (uint64 array) to absorption.  Returns (lead int32, steps uint32).
+
+    entries [n + 2W, n + 2] uint64 alias rows, mode_entries [2, W] uint64 injection alias rows,
+    c_open [2] bool (lead p has an open channel).  Pinned by: the empirical absorption
+    probabilities and mean steps of many walkers against the exact chain expectation.
+    """
+    wids = np.asarray(wids, dtype=np.uint64)
+    m = wids.size
+    K = n + 2
+    lead = np.full(m, -2, dtype=np.int32)
+    steps = np.zeros(m, dtype=np.uint32)
+    if m == 0:
+        return lead, steps
+    if not c_open[start_lead]:
+        lead[:] = -1
+        return lead, steps
+    wlo = wids & MASK32
+    whi = wids >> np.uint64(32)
+    k0 = int(seed) & 0xFFFFFFFF
+    k1 = (int(seed) >> 32) & 0xFFFFFFFF
+    active = np.arange(m)
+    row = np.zeros(m, dtype=np.int64)
+    words = None
+    s = 0
+    while active.size:
+        if s >= 1 and s > max_steps:
+            break
+        if s % 2 == 0:
+            b = np.full(active.size, s // 2, dtype=np.uint64)
+            words = philox4x32_10(b, wlo[active], whi[active], np.full(active.size, task), k0, k1)
+            x, y = words[0], words[1]
+        else:
+            x, y = words[2], words[3]
+        x = x.astype(np.uint64)
+        y = y.astype(np.uint64)
+        if s == 0:
+            c = ((x * np.uint64(W)) >> np.uint64(32)).astype(np.int64)
+            e = mode_entries[start_lead][c]
+            keep = y < (e & MASK32)
+            mode = np.where(keep, c, (e >> np.uint64(32)).astype(np.int64))
+            row[active] = n + start_lead * W + mode
+        else:
+            c = ((x * np.uint64(K)) >> np.uint64(32)).astype(np.int64)
+            e = entries[row[active], c]
+            keep = y < (e & MASK32)
+            j = np.where(keep, c, (e >> np.uint64(32)).astype(np.int64))
+            steps[active] = s
+            done = j >= n
+            lead[active[done]] = (j[done] - n).astype(np.int32)
+            row[active] = np.where(done, 0, j)
+            sel = ~done
+            active = active[sel]
+            if words is not None:
+                words = tuple(wd[sel] for wd in words)
+        s += 1
+    return lead, steps
