@@ -1,0 +1,362 @@
+"""Benchmark of the Monte Carlo NEGF walk path on GB300.
+
+One step = one pass of the whole hot path over the benchmark workload: transition tables for
+every (wire, energy) task (lead self-energies, RGF sweeps, block columns -> Step 6' weights,
+alias tables), the walks (walkers_per_task per task, start lead L) with their tally, and the
+current with its standard error.  Workload (default): 2D wire W = 10 x L = 50, t = 1, onsite
+U[-1, 1], eta = 0.05, 64 midpoint energies on [-3.5, 3.5], 1e6 walkers per energy, FP32 tables,
+FP64 tally/current; inputs resident on the device.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl gb300|reference] [--workload NAME]
+
+Prints one JSON line on rank 0.  --impl reference times the CPU FP64 oracle (test
+infrastructure) on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")      # the CPU baseline is the oracle as it stands: 1 thread
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1805_10164_gb300 import inputs  # noqa: E402
+
+METRIC = "walker steps/s and s per lead current at 1% std error on 1 GB300; frac of roofline"
+UNIT = "walker steps/s"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def workload(name):
+    if name == "wire_10x50":
+        return inputs.wire_10x50()
+    if name == "chain_l20":
+        return inputs.chain_l20()
+    if name == "wire_16x100":
+        return inputs.wire_16x100(precision="fp32")
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampler running during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.proc = None
+        self.index = index
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("NEGF_BENCH_GLOO") is None else "gloo")
+    return rank, world, local
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ algorithmic bytes per kernel
+
+def algorithmic_bytes(kernel, wl, precision, counts):
+    """Bytes a kernel must move per launch by its definition (tables in, tables out)."""
+    tasks = [(w.W, w.L) for w in wl.wires for _ in w.energy]
+    entries = sum((W * L + 2 * W) * (W * L + 2) for W, L in tasks)
+    wsz = 8 if precision == "fp64" else 4
+    if kernel == "walk_kernel":
+        walkers = int(counts[:, 0].sum())
+        steps = int(counts[:, 4].sum())
+        return 8 * (steps + walkers)            # one 8-byte alias entry per draw
+    if kernel == "alias_kernel":
+        return entries * (wsz + 8)              # read a weight, write an entry
+    if kernel == "block_column_kernel":
+        return entries * wsz                    # write every weight once
+    return None
+
+
+# ------------------------------------------------------------------ GPU arm
+
+def run_gpu(args):
+    import torch
+    from paper_1805_10164_gb300 import build, negf
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    build.build()
+    wl = workload(args.workload)
+    prec = args.precision or wl.precision
+    N = args.walkers or wl.walkers_per_task
+    dev_wires = [inputs.Wire(W=w.W, L=w.L, t=w.t, onsite=torch.from_numpy(w.onsite).cuda(),
+                             eta=torch.from_numpy(w.eta).cuda(),
+                             energy=torch.from_numpy(w.energy).cuda(),
+                             energy_weight=torch.from_numpy(w.energy_weight).cuda())
+                 for w in wl.wires]
+    stream = torch.cuda.current_stream()
+    ctx = negf.negf_create(local, stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    n_tasks = sum(len(w.energy) for w in wl.wires)
+    state = {"steps": 0, "walkers": 0, "I": None, "se": None, "counts": None}
+
+    def one_step(step_idx, wires, memspace):
+        tables = negf.negf_build_tables(ctx, wires, precision=prec, memspace=memspace)
+        tally = negf.negf_walk(ctx, tables, 0, args.seed, N,
+                               walker_id_offset=(rank * 1000 + step_idx) * N, max_steps=args.max_steps)
+        res = negf.negf_current(ctx, tables, tally, wl.mu_p, wl.mu_q, wl.kT)
+        counts = negf.negf_tally_counts(ctx, tally, n_tasks)
+        negf.negf_tally_free(tally)
+        negf.negf_tables_free(tables)
+        return res, counts
+
+    for i in range(args.warmup):
+        one_step(10_000 + i, dev_wires, "device")
+    torch.cuda.synchronize()
+    # ---- timed region (device-resident inputs)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = Clocks(local) if rank == 0 else None
+    negf.negf_profile_enable(ctx, True)
+    total_ms, tot_steps, tot_walkers = 0.0, 0, 0
+    last = None
+    for i in range(args.steps):
+        flush.fill_(float(i))                      # evict the previous step's tables from L2
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, counts = one_step(i, dev_wires, "device")
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        tot_steps += int(counts[:, 4].sum())
+        tot_walkers += int(counts[:, 0].sum())
+        last = (res, counts)
+    torch.cuda.synchronize()
+    prof = negf.negf_profile_read(ctx)
+    negf.negf_profile_enable(ctx, False)
+    clk = clocks.stop() if clocks else None
+    barrier(world)
+    t_max = max_over_ranks(total_ms, world)
+    all_steps = sum_over_ranks(float(tot_steps), world)
+    # ---- end-to-end through the public API with host buffers (copies inside the region)
+    e2e_ms, e2e_steps = 0.0, 0
+    h2d = sum(w.onsite.nbytes + w.eta.nbytes + w.energy.nbytes + w.energy_weight.nbytes
+              for w in wl.wires)
+    d2h = 8 * (2 * len(wl.wires) + 2 * n_tasks + 1) + 4 + 8 * n_tasks * negf.TALLY_FIELDS
+    for i in range(max(1, min(args.steps, 3))):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, counts = one_step(20_000 + i, wl.wires, "host")
+        torch.cuda.synchronize()
+        e2e_ms += 1e3 * (time.perf_counter() - t0)
+        e2e_steps += int(counts[:, 4].sum())
+    e2e_ms = max_over_ranks(e2e_ms, world)
+    e2e_steps = sum_over_ranks(float(e2e_steps), world)
+    negf.negf_destroy(ctx)
+    if rank != 0:
+        return
+    res, counts = last
+    ms_per_step = t_max / args.steps
+    value = all_steps / (t_max / 1e3)
+    # roofline of the dominant kernel
+    dom = max(prof.items(), key=lambda kv: kv[1][1])
+    kname, (klaunch, kms) = dom
+    peak, src = peaks()
+    abytes = algorithmic_bytes(kname, wl, prec, counts)
+    roof = None
+    if abytes is not None and klaunch > 0:
+        per_launch_s = kms / 1e3 / klaunch * (1 if kname != "walk_kernel" else 1)
+        launches_per_step = klaunch / args.steps
+        per_launch_bytes = abytes / max(1, launches_per_step)
+        ach = per_launch_bytes / per_launch_s / 1e9
+        roof = {"kernel": kname, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": src,
+                "traffic": None, "algorithmic_bytes_per_launch": int(per_launch_bytes),
+                "avg_launch_ms": round(kms / klaunch, 4)}
+    # seconds per current at 1 % relative standard error: fixed table cost + walks scaled by
+    # the binomial variance (N_needed = N (rel_se / 0.01)^2)
+    walk_ms = prof.get("walk_kernel", (0, 0.0))[1] / args.steps
+    rel = float(res["se"][0] / abs(res["I"][0])) if res["I"][0] != 0 else float("nan")
+    s_per_current = ((ms_per_step - walk_ms) + walk_ms * (rel / 0.01) ** 2) / 1e3
+    launches = int(sum(v[0] for v in prof.values()))
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 tables, u32 walks, f64 tally",
+        "data": "synthetic (seeded square-lattice wire standing in for the paper's CdTe nanowires)",
+        "config": {"workload": wl.name, "wires": len(wl.wires), "tasks": n_tasks,
+                   "walkers_per_task": N, "precision": prec, "start_lead": "L",
+                   "mu_p": wl.mu_p, "mu_q": wl.mu_q, "kT": wl.kT,
+                   "l2": "flushed between timed steps (258 MiB write, outside the timed events)",
+                   "parallelism": f"tasks replicated per rank, walker ids disjoint ({world} GPU)"},
+        "walker_steps_per_step": all_steps / args.steps / world,
+        "walkers_per_step": tot_walkers / args.steps,
+        "current": float(res["I"][0]), "current_rel_se": rel,
+        "s_per_current_1pct": s_per_current,
+        "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
+        "roofline": roof,
+        "e2e": {"value": e2e_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(wl, args, budget_s=args.cpu_budget)
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------ CPU oracle (baseline)
+
+def cpu_sample(wl, n_energy, walkers, seed, t_budget=None):
+    """Oracle on a sample of the workload: tables for n_energy energies spread over the grid
+    and `walkers` walks each.  Returns (walker steps, seconds, sample description)."""
+    from oracle import pipeline, walker
+    w = wl.wires[0]
+    idx = np.linspace(0, len(w.energy) - 1, n_energy).round().astype(int)
+    steps = 0
+    t0 = time.perf_counter()
+    for k in idx:
+        ref = pipeline.task_reference(w.onsite, w.eta, w.t, w.energy[k], w.lead_model,
+                                      w.gamma_lead, with_direct=False)
+        lead, st = walker.walk(ref["entries"], ref["mode_entries"], ref["n"], w.W, ref["c_open"],
+                               int(k), 0, seed, np.arange(walkers, dtype=np.uint64), 1 << 20)
+        steps += int(st.sum())
+    dt = time.perf_counter() - t0
+    return steps, dt, f"{n_energy} of {len(w.energy)} energies x {walkers} walkers"
+
+
+def cpu_baseline(wl, args, budget_s=20.0):
+    walkers = wl.walkers_per_task
+    steps, dt, desc = cpu_sample(wl, min(16, len(wl.wires[0].energy)), walkers, args.seed)
+    return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": desc + f" ({dt:.1f} s, numpy/LAPACK single thread)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = workload(args.workload)
+    walkers = wl.walkers_per_task
+    for i in range(args.warmup):
+        cpu_sample(wl, 1, 1000, args.seed + i)
+    tot_steps, tot_s = 0, 0.0
+    desc = ""
+    for i in range(args.steps):
+        st, dt, desc = cpu_sample(wl, min(2, len(wl.wires[0].energy)), walkers,
+                                  args.seed + 100 + i)
+        tot_steps += st
+        tot_s += dt
+    value = tot_steps / tot_s
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": wl.name, "walkers_per_task": wl.walkers_per_task,
+                      "sampled": desc},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": desc + " per step"},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="wire_10x50")
+    ap.add_argument("--precision", default=None)
+    ap.add_argument("--walkers", type=int, default=None)
+    ap.add_argument("--seed", type=int, default=20240607)
+    ap.add_argument("--max-steps", type=int, default=1 << 20)
+    ap.add_argument("--cpu-budget", type=float, default=20.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,209 @@
+/*
+ * negf.h -- C ABI of the GB300 Monte Carlo NEGF walk library (libnegf.so).
+ *
+ * Method: Musland, Bergli, Flage-Larsen, "A Monte Carlo method for solving the NEGF equations
+ * for electron transport" (arXiv:1805.10164).  The library computes, for wires with Buttiker
+ * dephasing probes in the elastic linear-response limit (Sec. II.E-F, III.A):
+ *   1. per (wire, energy) task, the retarded Green's function by recursive Green's function
+ *      sweeps (Sec. III.B) and from it the Step 6' transition weights (Eq. draw_i_simult and
+ *      the lead probability of Step 6') plus the Step 4 injection distribution
+ *      (Eq. lead_out_probability), stored as integer alias tables;
+ *   2. batches of random walks, one Monte Carlo sample each (Sec. II.D-F), absorbed at a lead;
+ *   3. the estimator X_pq = Tr[Gamma_p A] delta_rq (Eq. elast_lin_xpq) tallied into the
+ *      transmission T_qp(E) and the lead current of Eq. (iqof_t_el_db) with its binomial
+ *      standard error (Sec. IV.B.2).
+ * Units: e = h = 1, energies in units of the hopping scale chosen by the caller.
+ *
+ * Conventions shared by every call
+ *  - A context binds one CUDA device and one CUDA stream; all device work of a call is enqueued
+ *    on that stream.  Calls that return host data (negf_current, negf_tally_counts,
+ *    negf_get_task_info, negf_export_tables) synchronise the stream.  Other calls are asynchronous:
+ *    caller-owned device buffers must stay valid until the stream reaches the work.
+ *  - Handles (negf_tables, negf_tally) are owned by the library and released with their free
+ *    function; freeing NULL is a no-op.  Freeing is stream-ordered.
+ *  - Nothing throws across the ABI.  Every call returns a negf_status; on failure the message
+ *    is available from negf_last_error(ctx) until the next failing call on that context.
+ *  - Numerical failures detected on the device (non-finite Green's function, a table row whose
+ *    weights do not sum to a positive value) are recorded in the tables handle and reported as
+ *    NEGF_E_NUMERIC by the next synchronising call that uses the handle.
+ *  - A context must not be used by two host threads at once.
+ */
+#ifndef NEGF_H
+#define NEGF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NEGF_ABI_VERSION 1
+#define NEGF_MAX_W 64            /* widest supported slice (sites across the wire) */
+#define NEGF_MAX_STEPS (1u << 24) /* largest accepted per-walk step cap */
+#define NEGF_TALLY_FIELDS 5      /* u64 counters per task, see negf_tally_counts */
+
+typedef struct negf_ctx_s* negf_ctx;
+typedef struct negf_tables_s* negf_tables;
+typedef struct negf_tally_s* negf_tally;
+
+typedef enum {
+  NEGF_OK = 0,
+  NEGF_E_INVALID = 1,  /* bad argument or input outside the supported domain */
+  NEGF_E_NOMEM = 2,    /* device or host allocation failed */
+  NEGF_E_CUDA = 3,     /* a CUDA runtime call failed */
+  NEGF_E_NUMERIC = 4,  /* non-finite or non-positive quantity found on the device */
+  NEGF_E_STEPCAP = 5,  /* some walks reached max_steps; outputs are still written */
+  NEGF_E_TIMEOUT = 6   /* a bounded device wait gave up */
+} negf_status;
+
+/* Arithmetic of the table build.  NEGF_FP64: everything in FP64.  NEGF_FP32: the W x W
+ * inversions of the RGF sweeps and the diagonal blocks in FP64, the block-column propagation
+ * and the transition weights in FP32, row sums and alias thresholds in FP64.
+ * NEGF_SPLIT_TF32 is accepted and currently computed as NEGF_FP32. */
+typedef enum { NEGF_FP64 = 0, NEGF_FP32 = 1, NEGF_SPLIT_TF32 = 2 } negf_precision;
+
+/* Where the arrays of a negf_wire live. */
+typedef enum { NEGF_MEM_HOST = 0, NEGF_MEM_DEVICE = 1 } negf_memspace;
+
+/* Lead model.  NEGF_LEAD_STRIP: exact clean semi-infinite square-lattice strip of the wire's
+ * width (onsite 0, hopping -t), diagonal in the transverse sine modes with self-energy
+ * t^2 g_s(E - eps_m) per mode.  NEGF_LEAD_WIDE_BAND: the paper's Sigma_p = -(i/2) Gamma_l P_p
+ * on the boundary slice (Sec. III.A, lead self energy paragraph). */
+typedef enum { NEGF_LEAD_STRIP = 0, NEGF_LEAD_WIDE_BAND = 1 } negf_lead_model;
+
+/* One wire (Sec. III.A model; Buttiker self-energy sigma_i = -i gamma_i / 2, Eq. for sigma_i).
+ * Sites are slice-major: site (k, a) of slice k in [0, L) and row a in [0, W) has index k*W+a.
+ * Lead L couples to slice 0, lead R to slice L-1.  H has onsite[k*W+a] on the diagonal and -t
+ * between nearest neighbours along and across the slices. */
+typedef struct {
+  int32_t W, L;                  /* 1 <= W <= NEGF_MAX_W, L >= 1 */
+  double t;                      /* hopping magnitude, > 0 */
+  const double* onsite;          /* [L*W] onsite energies, finite */
+  const double* eta;             /* [L*W] Buttiker gamma_i >= 0, finite */
+  int32_t n_energy;              /* >= 0 */
+  const double* energy;          /* [n_energy]; for NEGF_LEAD_STRIP no energy may lie within
+                                    1e-12*t of a lead sub-band edge |E - eps_m| = 2t */
+  const double* energy_weight;   /* [n_energy] quadrature weights, or NULL for all 1 */
+  int32_t lead_model;            /* negf_lead_model */
+  double gamma_lead;             /* Gamma_l for NEGF_LEAD_WIDE_BAND, > 0 */
+} negf_wire;
+
+typedef struct {
+  int32_t precision;    /* negf_precision */
+  int32_t memspace;     /* negf_memspace of every array in the wires */
+  int32_t keep_weights; /* nonzero: keep the FP transition weights for negf_export_tables */
+  int32_t reserved;     /* must be 0 */
+} negf_build_opts;
+
+/* Per-task facts, read back from the device (synchronises). */
+typedef struct {
+  int32_t wire, energy_index;
+  int32_t W, L, n;       /* n = W*L sites */
+  int32_t K;             /* row length = n + 2 (sites, then lead L, lead R) */
+  int32_t rows;          /* n site rows, then W injection rows of lead L, W of lead R */
+  int32_t reserved;
+  double energy, energy_weight;
+  double c[2];           /* Tr[Gamma_p A] for p = L (0) and R (1), Eq. elast_lin_xpq */
+} negf_task_info;
+
+/* --- context -------------------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` enqueuing on `stream` (a cudaStream_t, NULL for the
+ * legacy default stream).  The stream must outlive the context. */
+negf_status negf_create(negf_ctx* out, int device, void* stream);
+void negf_destroy(negf_ctx ctx);
+const char* negf_last_error(negf_ctx ctx);
+int negf_abi_version(void);
+
+/* --- tables (Sec. III.B and Step 6') -------------------------------------------------- */
+
+/* Build the transition tables of every (wire, energy) task.  Tasks are numbered wire-major:
+ * all energies of wire 0, then wire 1, ...  Inputs are read during the call (host arrays) or by
+ * the enqueued work (device arrays).  Per task the handle holds (rows x K) alias entries
+ * (u64: low 32 bits threshold, high 32 bits alias; Sec. III.B inverse-CDF draw replaced by
+ * Walker's alias method), 2 x W injection-mode alias entries and c[2].
+ * Errors: NEGF_E_INVALID for bad sizes/values (host memspace checks every value; device
+ * memspace checks sizes here and values on the device, reported later as NEGF_E_INVALID by the
+ * next synchronising call), NEGF_E_NOMEM, NEGF_E_CUDA. */
+negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
+                              const negf_build_opts* opts, negf_tables* out);
+int32_t negf_tables_num_tasks(negf_tables tables);
+int32_t negf_tables_num_wires(negf_tables tables);
+/* Device bytes held by the handle (tables, scratch kept, descriptors). */
+uint64_t negf_tables_device_bytes(negf_tables tables);
+negf_status negf_get_task_info(negf_ctx ctx, negf_tables tables, int32_t task,
+                               negf_task_info* out);
+void negf_tables_free(negf_tables tables);
+
+/* Copy one task's data to host memory.  `what`:
+ *   NEGF_EXPORT_ALIAS       u64 [rows*K]  alias entries, row-major
+ *   NEGF_EXPORT_MODE_ALIAS  u64 [2*W]     injection-mode alias entries, lead L then R
+ *   NEGF_EXPORT_WEIGHTS     f64 [rows*K]  transition weights (needs keep_weights)
+ *   NEGF_EXPORT_MODE_WEIGHTS f64 [2*W]    lambda_m <phi_m|A|phi_m> (Eq. lead_out_probability)
+ *   NEGF_EXPORT_ROWSUM      f64 [rows]    FP64 sum of each row's weights (= <i|A|i>)
+ * If host_buf is NULL, *bytes receives the size needed.  Otherwise *bytes must be at least
+ * that size (NEGF_E_INVALID if not) and receives the bytes written.  Synchronises. */
+enum { NEGF_EXPORT_ALIAS = 0, NEGF_EXPORT_MODE_ALIAS = 1, NEGF_EXPORT_WEIGHTS = 2,
+       NEGF_EXPORT_MODE_WEIGHTS = 3, NEGF_EXPORT_ROWSUM = 4 };
+negf_status negf_export_tables(negf_ctx ctx, negf_tables tables, int32_t task, int32_t what,
+                               void* host_buf, size_t* bytes);
+
+/* --- walks (Sec. II.D Steps 1-4, Sec. II.F Step 6') ------------------------------------ */
+
+/* Run walkers_per_task walks in every task, all starting at lead start_lead (0 = L, 1 = R;
+ * the paper keeps the initial lead fixed, Sec. II.E).  Walker w of task k has id
+ * walker_id_offset + w; its draw s uses Philox4x32-10 block s/2 with counter
+ * (s/2, id_lo, id_hi, k) and key (seed_lo, seed_hi), words (x0,x1) for even s and (x2,x3) for
+ * odd s.  Draw 0 picks the injection mode, draws 1.. are Step 6' transitions (steps).  A walk
+ * stops when a lead is drawn or after max_steps steps (then it counts as truncated).
+ * Results from disjoint id ranges add up exactly (negf_tally_accumulate), so runs can be split
+ * or resumed.  1 <= max_steps <= NEGF_MAX_STEPS.  A new tally handle is returned in *out. */
+negf_status negf_walk(negf_ctx ctx, negf_tables tables, int32_t start_lead, uint64_t seed,
+                      uint64_t walkers_per_task, uint64_t walker_id_offset, uint32_t max_steps,
+                      negf_tally* out);
+
+/* Same walks for one task, recording each walker's outcome: d_lead[w] = 0 (L), 1 (R),
+ * -1 (no open channel in the start lead: nothing injected), -2 (truncated); d_steps[w] = steps.
+ * d_lead / d_steps are caller-owned device arrays of n_walkers entries. */
+negf_status negf_walk_trace(negf_ctx ctx, negf_tables tables, int32_t task, int32_t start_lead,
+                            uint64_t seed, uint64_t walker_id_offset, uint64_t n_walkers,
+                            uint32_t max_steps, int32_t* d_lead, uint32_t* d_steps);
+
+/* Per-task counters [n_tasks][NEGF_TALLY_FIELDS] u64: walkers done, absorbed at L, absorbed at
+ * R, truncated, sum of steps.  Synchronises. */
+negf_status negf_tally_counts(negf_ctx ctx, negf_tally tally, uint64_t* host_counts);
+/* Add host counters (same layout) into a tally, e.g. from another rank or an earlier run. */
+negf_status negf_tally_accumulate(negf_ctx ctx, negf_tally tally, const uint64_t* host_counts);
+int32_t negf_tally_start_lead(negf_tally tally);
+void negf_tally_free(negf_tally tally);
+
+/* --- current (Eq. iqof_t_el_db, Eq. elast_lin_xpq, Sec. IV.B.2) --------------------------- */
+
+/* From a tally of walks started at lead p = start_lead, with absorbing lead q = 1 - p:
+ *   T_qp(task) = c_p n_q / N,  SE = c_p sqrt(P (1-P) / N)  (P = n_q / N, N = walkers done),
+ *   I(wire) = sum_E w_E (f(E; mu_p, kT) - f(E; mu_q, kT)) T_qp(E),
+ *   SE(I)^2 = sum_E (w_E (f_p - f_q))^2 SE(T_qp(E))^2,
+ * computed on the device in FP64.  Host outputs: I[n_wires], se[n_wires]; T[n_tasks] and
+ * T_se[n_tasks] may be NULL.  Returns NEGF_E_STEPCAP (after writing the outputs) if any walk
+ * was truncated.  Synchronises. */
+negf_status negf_current(negf_ctx ctx, negf_tables tables, negf_tally tally, double mu_p,
+                         double mu_q, double kT, double* I, double* se, double* T,
+                         double* T_se);
+
+/* --- profiling (CUDA events around every kernel launch) ----------------------------------- */
+
+/* Turn per-kernel device-time accounting on (on != 0) or off; either way the counters reset.
+ * While on, each kernel launch of the context is bracketed by two CUDA events on the context
+ * stream. */
+negf_status negf_profile_enable(negf_ctx ctx, int32_t on);
+/* Read the counters (synchronises on the recorded events): for i < min(cap, *n_out) entries,
+ * names[32*i ..] receives the kernel name (NUL-terminated), launches[i] the number of kernel
+ * launches and total_ms[i] their summed device time.  *n_out = number of entries. */
+negf_status negf_profile_read(negf_ctx ctx, int32_t cap, char* names, uint64_t* launches,
+                              double* total_ms, int32_t* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NEGF_H */

@@ -66,8 +66,11 @@ def absorption(tab):
     """Exact absorption probabilities and mean steps of the Step 6' chain.
 
     Returns P_site [n, 2], steps_site [n], P_inj [2, 2] (start lead p -> absorbing lead q,
-    averaged over the injection distribution), steps_inj [2] and T_eff [q, p] = c_p P(q|p).
-    Pinned by: equality with the Buttiker probe solve and the Neumann series; P(L)+P(R) = 1.
+    averaged over the injection distribution), steps_inj [2], steps2_inj [2] (second moment of
+    the number of steps) and T_eff [q, p] = c_p P(q|p).  The second moment uses the standard
+    absorbing-chain identity E[S_i^2] = ((2N - I) t)_i with N = (I - Q)^{-1}, t = N 1.
+    Pinned by: equality with the Buttiker probe solve and the Neumann series; P(L)+P(R) = 1;
+    the step moments against brute-force iteration of the chain and the walker's samples.
     """
     w, n, W = tab["w"], tab["n"], tab["W"]
     tot = w.sum(axis=1)
@@ -79,8 +82,10 @@ def absorption(tab):
     IQ = np.eye(n) - Q
     P_site = np.linalg.solve(IQ, R)
     steps_site = np.linalg.solve(IQ, np.ones(n))
+    m2_site = 2.0 * np.linalg.solve(IQ, steps_site) - steps_site    # (2N - I) t
     P_inj = np.zeros((2, 2))
     steps_inj = np.zeros(2)
+    steps2_inj = np.zeros(2)
     T_eff = np.zeros((2, 2))
     for p in range(2):
         mw = tab["mode_w"][p]
@@ -91,6 +96,8 @@ def absorption(tab):
         Pi = P[rows]
         P_inj[p] = u @ (Pi[:, n:] + Pi[:, :n] @ P_site)
         steps_inj[p] = u @ (1.0 + Pi[:, :n] @ steps_site)
+        # S = 1 + T_j after a first draw to site j (T = 0 when the first draw is a lead)
+        steps2_inj[p] = u @ (1.0 + Pi[:, :n] @ (2.0 * steps_site + m2_site))
         T_eff[:, p] = tab["c"][p] * P_inj[p]
-    return dict(P_site=P_site, steps_site=steps_site, P_inj=P_inj, steps_inj=steps_inj,
-                T_eff=T_eff)
+    return dict(P_site=P_site, steps_site=steps_site, m2_site=m2_site, P_inj=P_inj,
+                steps_inj=steps_inj, steps2_inj=steps2_inj, T_eff=T_eff)

@@ -1,0 +1,102 @@
+// Current assembly from walk tallies (Eq. iqof_t_el_db with the Monte Carlo estimator of
+// Eq. elast_lin_xpq and the binomial standard error of Sec. IV.B.2), and the device-side input
+// check used when the wire arrays live on the device.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "negf_internal.cuh"
+
+namespace negf {
+namespace {
+
+__device__ __forceinline__ double fermi(double E, double mu, double kT) {
+  return 0.5 * (1.0 - tanh(0.5 * (E - mu) / kT));   // 1 / (1 + exp((E - mu) / kT))
+}
+
+// out layout: I[n_wires] | se[n_wires] | T[n_tasks] | T_se[n_tasks] | truncated (as double)
+// One thread per wire; its energies are summed in task order (deterministic).
+__global__ void current_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, int n_wires,
+                               const int32_t* __restrict__ wire_task0,
+                               const double* __restrict__ cvals,
+                               const unsigned long long* __restrict__ tally, int p, double mu_p,
+                               double mu_q, double kT, double* __restrict__ out) {
+  const int q = 1 - p;
+  double* I = out;
+  double* se = out + n_wires;
+  double* T = se + n_wires;
+  double* Tse = T + n_tasks;
+  double* trunc = Tse + n_tasks;
+  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < n_wires; w += gridDim.x * blockDim.x) {
+    double acc = 0.0, var = 0.0, tr = 0.0;
+    for (int k = wire_task0[w]; k < wire_task0[w + 1]; ++k) {
+      const TaskDesc d = tasks[k];
+      const unsigned long long* c = tally + (size_t)k * NEGF_TALLY_FIELDS;
+      const double N = (double)c[0];
+      const double nq = (double)c[1 + q];
+      const double cp = cvals[2 * k + p];
+      double Tk = 0.0, sk = 0.0;
+      if (N > 0.0) {
+        const double P = nq / N;
+        Tk = cp * P;
+        sk = cp * sqrt(P * (1.0 - P) / N);
+      }
+      T[k] = Tk;
+      Tse[k] = sk;
+      const double wd = d.w_E * (fermi(d.E, mu_p, kT) - fermi(d.E, mu_q, kT));
+      acc += wd * Tk;
+      var += wd * wd * sk * sk;
+      tr += (double)c[3];
+    }
+    I[w] = acc;
+    se[w] = sqrt(var);
+    atomicAdd(trunc, tr);
+  }
+}
+
+__global__ void validate_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
+                                const double* __restrict__ wire, int32_t* err) {
+  const TaskDesc d = tasks[blockIdx.x];
+  // only the first task of each wire checks that wire's arrays
+  if (d.e_idx != 0) return;
+  const double* onsite = wire + d.onsite_off;
+  const double* eta = onsite + d.n;
+  bool bad = false;
+  for (int i = threadIdx.x; i < d.n; i += blockDim.x)
+    bad |= !isfinite(onsite[i]) || !isfinite(eta[i]) || !(eta[i] >= 0.0);
+  if (bad) atomicOr(err, ERR_INPUT);
+  if (threadIdx.x == 0 && !(isfinite(d.E) && isfinite(d.w_E))) atomicOr(err, ERR_INPUT);
+}
+
+__global__ void validate_energy_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
+                                       int32_t* err) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n_tasks && !(isfinite(tasks[k].E) && isfinite(tasks[k].w_E))) atomicOr(err, ERR_INPUT);
+}
+
+}  // namespace
+
+cudaError_t launch_current(const TaskDesc* d_tasks, int n_tasks, int n_wires,
+                           const int32_t* d_wire_task0, const double* d_c,
+                           const uint64_t* d_tally, int start_lead, double mu_p, double mu_q,
+                           double kT, double* d_out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(d_out + 2 * (size_t)n_wires + 2 * (size_t)n_tasks, 0,
+                                  sizeof(double), s);
+  if (e != cudaSuccess) return e;
+  if (n_wires == 0) return cudaSuccess;
+  const int threads = 128;
+  const int blocks = (n_wires + threads - 1) / threads;
+  current_kernel<<<blocks, threads, 0, s>>>(
+      d_tasks, n_tasks, n_wires, d_wire_task0, d_c,
+      reinterpret_cast<const unsigned long long*>(d_tally), start_lead, mu_p, mu_q, kT, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(const TaskDesc* d_tasks, int n_tasks, const double* d_wire,
+                            int32_t* d_err, cudaStream_t s) {
+  if (n_tasks == 0) return cudaSuccess;
+  validate_kernel<<<n_tasks, 128, 0, s>>>(d_tasks, n_tasks, d_wire, d_err);
+  validate_energy_kernel<<<(n_tasks + 127) / 128, 128, 0, s>>>(d_tasks, n_tasks, d_err);
+  return cudaGetLastError();
+}
+
+}  // namespace negf

@@ -1,0 +1,239 @@
+// Persistent random-walk kernel (Sec. II.D Steps 1-4 with the start lead fixed as in Sec. II.E,
+// and Step 6' of Sec. II.F) and its tally.
+//
+// Each lane owns one walker at a time and keeps its state in registers: task, current table
+// row, draw index s and steps taken.  Draw s takes Philox4x32-10 block s/2 with counter
+// (s/2, id_lo, id_hi, task) and key (seed_lo, seed_hi), words (x0, x1) for even s, (x2, x3) for
+// odd s (the odd half is cached from the even draw).  Draw 0 picks the injection eigenvector of
+// Gamma_p from the mode alias row (Eq. lead_out_probability); every later draw is one Step 6'
+// transition from the current row: slot c = (x*K)>>32, keep c if y < thr[c] else alias[c].
+// Columns n and n+1 are the leads: drawing one ends the walk, and the sample's estimator is
+// X_pq = Tr[Gamma_p A] delta_rq (Eq. elast_lin_xpq), tallied as counts per absorbing lead.
+// When a walk ends the lane takes the next walker from its warp's chunk of walker indices (a
+// warp claims 256 at a time from a global counter), so lanes stay busy although walk lengths
+// differ.  Each lane counts its own outcomes for its current task in registers; when lanes move
+// to another task their counts are summed per task across the warp (match + reduce) and added
+// to the block's shared tally, which is added to global memory once per block.
+#include <cuda_runtime.h>
+
+#include "negf_internal.cuh"
+#include "philox.cuh"
+
+namespace negf {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kFields = NEGF_TALLY_FIELDS;   // done, absorbed L, absorbed R, truncated, steps
+constexpr int kMaxWindow = 1024;             // tasks per launch (40 KB shared tally)
+constexpr unsigned kChunk = 256;             // walkers a warp claims from the global counter
+constexpr unsigned kFlushAt = 1u << 26;      // flush a lane's counters before they can overflow
+
+// 64-bit shared counter kept as two 32-bit words (native 32-bit shared atomics).
+__device__ __forceinline__ void smem_add64(unsigned* lohi, unsigned v) {
+  const unsigned old = atomicAdd(lohi, v);
+  if (old + v < old) atomicAdd(lohi + 1, 1u);
+}
+
+// Sum the lanes' counters per task over the lanes in `mask` that call this, then one lane per
+// task adds them to the block's shared tally.
+__device__ __forceinline__ void flush_group(unsigned mask, int task_local, const unsigned (&a)[kFields],
+                                            unsigned* s_tally) {
+  const unsigned grp = __match_any_sync(mask, task_local);
+  unsigned sum[kFields];
+#pragma unroll
+  for (int f = 0; f < kFields; ++f) sum[f] = __reduce_add_sync(grp, a[f]);
+  if ((threadIdx.x & 31) == __ffs(grp) - 1) {
+    unsigned* t = s_tally + task_local * kFields * 2;
+#pragma unroll
+    for (int f = 0; f < kFields; ++f)
+      if (sum[f]) smem_add64(t + 2 * f, sum[f]);
+  }
+}
+
+template <bool kTrace>
+__global__ void __launch_bounds__(kThreads) walk_kernel(
+    const TaskDesc* __restrict__ tasks, int task0, int n_tasks, const uint64_t* __restrict__ tab,
+    const uint64_t* __restrict__ mode_tab, const double* __restrict__ cvals, int start_lead,
+    PhiloxKey key, uint64_t walkers_per_task, uint64_t id_offset, uint32_t max_steps,
+    unsigned long long* __restrict__ counter, unsigned long long* __restrict__ tally /*window*/,
+    int32_t* __restrict__ trace_lead, uint32_t* __restrict__ trace_steps) {
+  extern __shared__ unsigned s_tally[];   // [n_tasks][kFields][lo, hi]
+  for (int i = threadIdx.x; i < n_tasks * kFields * 2; i += blockDim.x) s_tally[i] = 0u;
+  __syncthreads();
+
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt_mask = (1u << lane) - 1u;
+  const unsigned long long total = (unsigned long long)n_tasks * walkers_per_task;
+
+  // walker state (registers)
+  bool has = false;
+  uint64_t g = 0;
+  int tl = 0;                      // task index within the window
+  uint32_t task_id = 0, K = 0, n = 0, W = 0, row = 0, s = 0, steps = 0, cx2 = 0, cx3 = 0;
+  uint32_t wid_lo = 0, wid_hi = 0;
+  const uint64_t* trow = nullptr;
+  const uint64_t* mrow = nullptr;
+  // this lane's counters for task acc_tl
+  int acc_tl = -1;
+  unsigned a[kFields] = {0u, 0u, 0u, 0u, 0u};
+  // warp's current chunk of walker indices [c_next, c_end) (warp-uniform)
+  unsigned long long c_next = 0, c_end = 0;
+  bool no_more = false;
+
+  while (true) {
+    // ---- refill idle lanes from the warp's chunk (claiming chunks as needed)
+    unsigned need = __ballot_sync(FULL, !has);
+    while (need && !no_more) {
+      if (c_next == c_end) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(counter, (unsigned long long)kChunk);
+        base = __shfl_sync(FULL, base, 0);
+        if (base >= total) { no_more = true; break; }
+        c_next = base;
+        c_end = base + kChunk < total ? base + kChunk : total;
+      }
+      const unsigned avail = (unsigned)(c_end - c_next);
+      const unsigned rank = __popc(need & lt_mask);
+      const bool mine = ((need >> lane) & 1u) && rank < avail;
+      int new_tl = -1;
+      if (mine) {
+        g = c_next + rank;
+        new_tl = (int)(g / walkers_per_task);
+      }
+      const unsigned took = __popc(need) < avail ? __popc(need) : avail;
+      c_next += took;
+      // counters of a lane that moves to another task go to the shared tally first
+      const bool fl = mine && new_tl != acc_tl && acc_tl >= 0;
+      const unsigned fm = __ballot_sync(FULL, fl);
+      if (fl) flush_group(fm, acc_tl, a, s_tally);
+      if (mine) {
+        if (new_tl != acc_tl) {
+          acc_tl = new_tl;
+#pragma unroll
+          for (int f = 0; f < kFields; ++f) a[f] = 0u;
+        }
+        tl = new_tl;
+        const uint64_t w = id_offset + (g - (uint64_t)tl * walkers_per_task);
+        const TaskDesc& d = tasks[task0 + tl];
+        task_id = (uint32_t)(task0 + tl);
+        K = (uint32_t)d.K;
+        n = (uint32_t)d.n;
+        W = (uint32_t)d.W;
+        trow = tab + d.tab_off;
+        mrow = mode_tab + d.mode_off + start_lead * d.W;
+        wid_lo = (uint32_t)w;
+        wid_hi = (uint32_t)(w >> 32);
+        s = 0;
+        steps = 0;
+        if (cvals[2 * (task0 + tl) + start_lead] > 0.0) {
+          has = true;
+        } else {
+          // no open channel in the start lead: nothing to inject (T = 0 exactly)
+          a[0] += 1u;
+          if (kTrace) { trace_lead[g] = -1; trace_steps[g] = 0; }
+        }
+      }
+      need = __ballot_sync(FULL, !has);
+    }
+    if (!__any_sync(FULL, has)) break;   // no walker in flight and no work left
+    if (has) {
+      uint32_t x, y;
+      if ((s & 1u) == 0u) {
+        const uint4 r = philox4x32_10(make_uint4(s >> 1, wid_lo, wid_hi, task_id), key);
+        x = r.x; y = r.y; cx2 = r.z; cx3 = r.w;
+      } else {
+        x = cx2; y = cx3;
+      }
+      if (s == 0u) {
+        const uint32_t c = __umulhi(x, W);
+        const uint64_t e = __ldg(mrow + c);
+        const uint32_t mode = y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+        row = n + (uint32_t)start_lead * W + mode;
+      } else {
+        const uint32_t c = __umulhi(x, K);
+        const uint64_t e = __ldg(trow + (uint64_t)row * K + c);
+        const uint32_t j = y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+        ++steps;
+        int outcome = -3;
+        if (j >= n) outcome = (int)(j - n);              // absorbed at lead 0 (L) or 1 (R)
+        else if (steps >= max_steps) outcome = -2;       // cut: counted as truncated
+        else row = j;
+        if (outcome != -3) {
+          a[0] += 1u;
+          a[outcome >= 0 ? 1 + outcome : 3] += 1u;
+          a[4] += steps;
+          if (kTrace) { trace_lead[g] = outcome; trace_steps[g] = steps; }
+          has = false;
+          if (a[4] >= kFlushAt || a[0] >= kFlushAt) {
+            unsigned* t = s_tally + acc_tl * kFields * 2;
+#pragma unroll
+            for (int f = 0; f < kFields; ++f) {
+              if (a[f]) smem_add64(t + 2 * f, a[f]);
+              a[f] = 0u;
+            }
+          }
+        }
+      }
+      ++s;
+    }
+  }
+  // ---- final flush of every lane's counters, then the block's tally to global memory
+  const bool fl = acc_tl >= 0;
+  const unsigned fm = __ballot_sync(FULL, fl);
+  if (fl) flush_group(fm, acc_tl, a, s_tally);
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_tasks * kFields; i += blockDim.x) {
+    const unsigned long long v =
+        (unsigned long long)s_tally[2 * i] | ((unsigned long long)s_tally[2 * i + 1] << 32);
+    if (v) atomicAdd(&tally[i], v);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, const uint64_t* d_tab,
+                        const uint64_t* d_mode_tab, const double* d_c, int start_lead,
+                        uint64_t seed, uint64_t walkers_per_task, uint64_t id_offset,
+                        uint32_t max_steps, unsigned long long* d_counter, uint64_t* d_tally,
+                        int32_t* d_trace_lead, uint32_t* d_trace_steps, int sm_count,
+                        cudaStream_t s) {
+  if (n_tasks <= 0 || walkers_per_task == 0) return cudaSuccess;
+  const PhiloxKey key{(uint32_t)seed, (uint32_t)(seed >> 32)};
+  unsigned long long* tally = reinterpret_cast<unsigned long long*>(d_tally);
+  for (int w0 = 0; w0 < n_tasks; w0 += kMaxWindow) {
+    const int nt = (n_tasks - w0) < kMaxWindow ? (n_tasks - w0) : kMaxWindow;
+    cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const unsigned long long total = (unsigned long long)nt * walkers_per_task;
+    const size_t smem = sizeof(unsigned) * 2 * (size_t)nt * kFields;
+    int per_sm = 0;
+    if (d_trace_lead) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<true>, kThreads,
+                                                        smem);
+    } else {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<false>, kThreads,
+                                                        smem);
+    }
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    unsigned long long blocks = (unsigned long long)sm_count * per_sm;
+    const unsigned long long need = (total + kThreads - 1) / kThreads;
+    if (blocks > need) blocks = need;
+    if (d_trace_lead) {
+      walk_kernel<true><<<(unsigned)blocks, kThreads, smem, s>>>(
+          d_tasks, task0 + w0, nt, d_tab, d_mode_tab, d_c, start_lead, key, walkers_per_task,
+          id_offset, max_steps, d_counter, tally + (size_t)w0 * kFields, d_trace_lead,
+          d_trace_steps);
+    } else {
+      walk_kernel<false><<<(unsigned)blocks, kThreads, smem, s>>>(
+          d_tasks, task0 + w0, nt, d_tab, d_mode_tab, d_c, start_lead, key, walkers_per_task,
+          id_offset, max_steps, d_counter, tally + (size_t)w0 * kFields, nullptr, nullptr);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace negf

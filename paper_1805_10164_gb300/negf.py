@@ -1,0 +1,256 @@
+"""Thin ctypes binding of libnegf (include/negf.h).  Argument marshalling only: every step of
+the walk path runs in the library's CUDA kernels.  Functions carry the C entry points' names.
+
+Device memory and streams come from PyTorch: a context binds ``torch.cuda.current_stream()``
+unless a stream is given, and device-resident wire arrays may be torch CUDA tensors.
+The library must have been built (``paper_1805_10164_gb300.build.build()``); loading fails
+loudly otherwise - there is no fallback.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+NEGF_OK, NEGF_E_INVALID, NEGF_E_NOMEM, NEGF_E_CUDA, NEGF_E_NUMERIC, NEGF_E_STEPCAP, NEGF_E_TIMEOUT = range(7)
+PRECISION = {"fp64": 0, "fp32": 1, "split_tf32": 2}
+EXPORT = {"alias": 0, "mode_alias": 1, "weights": 2, "mode_weights": 3, "rowsum": 4}
+TALLY_FIELDS = 5
+MAX_STEPS = 1 << 24
+_STATUS = {0: "NEGF_OK", 1: "NEGF_E_INVALID", 2: "NEGF_E_NOMEM", 3: "NEGF_E_CUDA",
+           4: "NEGF_E_NUMERIC", 5: "NEGF_E_STEPCAP", 6: "NEGF_E_TIMEOUT"}
+
+
+class NegfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class negf_wire(C.Structure):
+    _fields_ = [("W", C.c_int32), ("L", C.c_int32), ("t", C.c_double),
+                ("onsite", C.c_void_p), ("eta", C.c_void_p), ("n_energy", C.c_int32),
+                ("energy", C.c_void_p), ("energy_weight", C.c_void_p),
+                ("lead_model", C.c_int32), ("gamma_lead", C.c_double)]
+
+
+class negf_build_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("memspace", C.c_int32), ("keep_weights", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
+class negf_task_info(C.Structure):
+    _fields_ = [("wire", C.c_int32), ("energy_index", C.c_int32), ("W", C.c_int32),
+                ("L", C.c_int32), ("n", C.c_int32), ("K", C.c_int32), ("rows", C.c_int32),
+                ("reserved", C.c_int32), ("energy", C.c_double), ("energy_weight", C.c_double),
+                ("c", C.c_double * 2)]
+
+
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load():
+    """Load libnegf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libnegf.so is not built ({path}); call "
+                           "paper_1805_10164_gb300.build.build() first")
+    lib = C.CDLL(path)
+    P, I32, U32, U64, D = C.c_void_p, C.c_int32, C.c_uint32, C.c_uint64, C.c_double
+    sig = {
+        "negf_abi_version": (C.c_int, []),
+        "negf_create": (I32, [C.POINTER(P), C.c_int, P]),
+        "negf_destroy": (None, [P]),
+        "negf_last_error": (C.c_char_p, [P]),
+        "negf_build_tables": (I32, [P, C.POINTER(negf_wire), I32, C.POINTER(negf_build_opts),
+                                    C.POINTER(P)]),
+        "negf_tables_num_tasks": (I32, [P]),
+        "negf_tables_num_wires": (I32, [P]),
+        "negf_tables_device_bytes": (U64, [P]),
+        "negf_get_task_info": (I32, [P, P, I32, C.POINTER(negf_task_info)]),
+        "negf_tables_free": (None, [P]),
+        "negf_export_tables": (I32, [P, P, I32, I32, P, C.POINTER(C.c_size_t)]),
+        "negf_walk": (I32, [P, P, I32, U64, U64, U64, U32, C.POINTER(P)]),
+        "negf_walk_trace": (I32, [P, P, I32, I32, U64, U64, U64, U32, P, P]),
+        "negf_tally_counts": (I32, [P, P, P]),
+        "negf_tally_accumulate": (I32, [P, P, P]),
+        "negf_tally_start_lead": (I32, [P]),
+        "negf_tally_free": (None, [P]),
+        "negf_current": (I32, [P, P, P, D, D, D, P, P, P, P]),
+        "negf_profile_enable": (I32, [P, I32]),
+        "negf_profile_read": (I32, [P, I32, P, P, P, C.POINTER(I32)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(ctx, st, allow=()):
+    if st != NEGF_OK and st not in allow:
+        msg = load().negf_last_error(ctx)
+        raise NegfError(st, msg.decode() if msg else "")
+    return st
+
+
+def _ptr(x):
+    """Address of a numpy array (host) or torch tensor (device/host)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def negf_create(device=0, stream=None):
+    import torch
+    lib = load()
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    out = C.c_void_p()
+    st = lib.negf_create(C.byref(out), int(device), C.c_void_p(handle))
+    if st != NEGF_OK:
+        raise NegfError(st, "negf_create failed")
+    return out
+
+
+def negf_destroy(ctx):
+    load().negf_destroy(ctx)
+
+
+def negf_build_tables(ctx, wires, precision="fp64", memspace="host", keep_weights=False):
+    """wires: objects with W, L, t, onsite, eta, energy, energy_weight, lead_model, gamma_lead
+    (numpy float64 arrays for memspace 'host', torch CUDA float64 tensors for 'device')."""
+    lib = load()
+    keep = []
+    arr = (negf_wire * max(1, len(wires)))()
+    for i, w in enumerate(wires):
+        if memspace == "host":
+            on = np.ascontiguousarray(w.onsite, dtype=np.float64).reshape(-1)
+            et = np.ascontiguousarray(w.eta, dtype=np.float64).reshape(-1)
+            E = np.ascontiguousarray(w.energy, dtype=np.float64).reshape(-1)
+            wE = None if w.energy_weight is None else np.ascontiguousarray(
+                w.energy_weight, dtype=np.float64).reshape(-1)
+        else:
+            on, et, E, wE = (t.contiguous() if t is not None else None
+                             for t in (w.onsite, w.eta, w.energy, w.energy_weight))
+        keep.extend([on, et, E, wE])
+        arr[i] = negf_wire(int(w.W), int(w.L), float(w.t), _ptr(on), _ptr(et), int(len(E)),
+                           _ptr(E), _ptr(wE), int(getattr(w, "lead_model", 0)),
+                           float(getattr(w, "gamma_lead", 0.0)))
+    opts = negf_build_opts(PRECISION[precision], 0 if memspace == "host" else 1,
+                           1 if keep_weights else 0, 0)
+    out = C.c_void_p()
+    _check(ctx, lib.negf_build_tables(ctx, arr, len(wires), C.byref(opts), C.byref(out)))
+    del keep
+    return out
+
+
+def negf_tables_num_tasks(tables):
+    return load().negf_tables_num_tasks(tables)
+
+
+def negf_tables_device_bytes(tables):
+    return load().negf_tables_device_bytes(tables)
+
+
+def negf_get_task_info(ctx, tables, task):
+    info = negf_task_info()
+    _check(ctx, load().negf_get_task_info(ctx, tables, int(task), C.byref(info)))
+    return dict(wire=info.wire, energy_index=info.energy_index, W=info.W, L=info.L, n=info.n,
+                K=info.K, rows=info.rows, energy=info.energy, energy_weight=info.energy_weight,
+                c=np.array([info.c[0], info.c[1]]))
+
+
+def negf_tables_free(tables):
+    load().negf_tables_free(tables)
+
+
+def negf_export_tables(ctx, tables, task, what):
+    lib = load()
+    kind = EXPORT[what]
+    nbytes = C.c_size_t(0)
+    _check(ctx, lib.negf_export_tables(ctx, tables, int(task), kind, None, C.byref(nbytes)))
+    dtype = np.uint64 if what in ("alias", "mode_alias") else np.float64
+    buf = np.empty(nbytes.value // 8, dtype=dtype)
+    _check(ctx, lib.negf_export_tables(ctx, tables, int(task), kind, buf.ctypes.data,
+                                       C.byref(nbytes)))
+    return buf
+
+
+def negf_walk(ctx, tables, start_lead, seed, walkers_per_task, walker_id_offset=0,
+              max_steps=1 << 20):
+    out = C.c_void_p()
+    _check(ctx, load().negf_walk(ctx, tables, int(start_lead), int(seed), int(walkers_per_task),
+                                 int(walker_id_offset), int(max_steps), C.byref(out)))
+    return out
+
+
+def negf_walk_trace(ctx, tables, task, start_lead, seed, walker_id_offset, d_lead, d_steps,
+                    max_steps=1 << 20):
+    """d_lead: torch int32 CUDA tensor, d_steps: torch int32/uint32 CUDA tensor (n_walkers)."""
+    n = int(d_lead.numel())
+    _check(ctx, load().negf_walk_trace(ctx, tables, int(task), int(start_lead), int(seed),
+                                       int(walker_id_offset), n, int(max_steps), _ptr(d_lead),
+                                       _ptr(d_steps)))
+
+
+def negf_tally_counts(ctx, tally, n_tasks):
+    buf = np.zeros((n_tasks, TALLY_FIELDS), dtype=np.uint64)
+    _check(ctx, load().negf_tally_counts(ctx, tally, buf.ctypes.data))
+    return buf
+
+
+def negf_tally_accumulate(ctx, tally, counts):
+    counts = np.ascontiguousarray(counts, dtype=np.uint64)
+    _check(ctx, load().negf_tally_accumulate(ctx, tally, counts.ctypes.data))
+
+
+def negf_tally_free(tally):
+    load().negf_tally_free(tally)
+
+
+def negf_current(ctx, tables, tally, mu_p, mu_q, kT):
+    """Returns dict(I, se, T, T_se, stepcap) with I/se per wire and T/T_se per task."""
+    lib = load()
+    nw = lib.negf_tables_num_wires(tables)
+    nt = lib.negf_tables_num_tasks(tables)
+    I = np.zeros(max(nw, 1))
+    se = np.zeros(max(nw, 1))
+    T = np.zeros(max(nt, 1))
+    Tse = np.zeros(max(nt, 1))
+    st = _check(ctx, lib.negf_current(ctx, tables, tally, float(mu_p), float(mu_q), float(kT),
+                                      I.ctypes.data, se.ctypes.data, T.ctypes.data,
+                                      Tse.ctypes.data), allow=(NEGF_E_STEPCAP,))
+    return dict(I=I[:nw], se=se[:nw], T=T[:nt], T_se=Tse[:nt], stepcap=st == NEGF_E_STEPCAP)
+
+
+def negf_profile_enable(ctx, on=True):
+    _check(ctx, load().negf_profile_enable(ctx, 1 if on else 0))
+
+
+def negf_profile_read(ctx, cap=32):
+    """{kernel name: (launch groups, total device ms)} accumulated since profiling was enabled."""
+    names = C.create_string_buffer(32 * cap)
+    launches = np.zeros(cap, dtype=np.uint64)
+    ms = np.zeros(cap)
+    n = C.c_int32(0)
+    _check(ctx, load().negf_profile_read(ctx, cap, names, launches.ctypes.data, ms.ctypes.data,
+                                         C.byref(n)))
+    out = {}
+    raw = names.raw
+    for i in range(min(n.value, cap)):
+        name = raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[name] = (int(launches[i]), float(ms[i]))
+    return out

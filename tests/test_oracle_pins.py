@@ -258,7 +258,36 @@ def test_walker_statistics_match_exact_chain():
     Phat = np.mean(lead == 1)
     assert abs(Phat - P) < 4.5 * np.sqrt(P * (1 - P) / N)
     m = r["exact"]["steps_inj"][0]
-    assert abs(steps.mean() - m) < 4.5 * steps.std() / np.sqrt(N)
+    var = r["exact"]["steps2_inj"][0] - m * m
+    assert abs(steps.mean() - m) < 4.5 * np.sqrt(var / N)
+    assert abs(steps.var() / var - 1.0) < 0.1
+
+
+def test_step_moments_brute_force():
+    """Second moment of the number of steps: the fundamental-matrix identity against direct
+    iteration of the chain's step distribution P(S = k) on a small wire."""
+    on, et = _wire(12, 2, 4, 0.6)
+    r = pipeline.task_reference(on, et, 1.0, 0.2, with_alias=False)
+    tab, ex = r["tab"], r["exact"]
+    n, W = r["n"], r["W"]
+    P = tab["w"] / tab["w"].sum(1, keepdims=True)
+    u = tab["mode_w"][0] / tab["mode_w"][0].sum()
+    dist = u @ P[n:n + W]                     # state after draw 1 (sites then leads)
+    alive = dist[:n].copy()
+    m1 = m2 = 0.0
+    k = 1
+    absorbed = dist[n:].sum()
+    m1 += k * absorbed
+    m2 += k * k * absorbed
+    while alive.sum() > 1e-16 and k < 100000:
+        k += 1
+        nxt = alive @ P[:n]
+        absorbed = nxt[n:].sum()
+        m1 += k * absorbed
+        m2 += k * k * absorbed
+        alive = nxt[:n]
+    assert abs(m1 - ex["steps_inj"][0]) < 1e-10 * m1
+    assert abs(m2 - ex["steps2_inj"][0]) < 1e-10 * m2
 
 
 def test_walker_reproducible_and_truncation():
