@@ -191,6 +191,40 @@ negf_status negf_current(negf_ctx ctx, negf_tables tables, negf_tally tally, dou
                          double mu_q, double kT, double* I, double* se, double* T,
                          double* T_se);
 
+/* --- table build without device allocation ------------------------------------------------ */
+
+/* The paper has no counterpart to this entry point; it exists for callers of this library that
+ * cannot allocate device memory themselves or let a library do it: a host framework that owns
+ * every device byte through its own pool, a process whose device footprint must not grow after
+ * start-up, or code enqueuing work where a cudaMalloc would synchronise the device.
+ *
+ * It builds the same tables as negf_build_tables for ONE wire (host arrays, as with
+ * NEGF_MEM_HOST; energy_weight is ignored) with the same kernels, but allocates nothing: all
+ * scratch (task descriptors, lead self-energies, RGF blocks, FP weights, row sums) lives in one
+ * file-scope device array of NEGF_NOALLOC_SCRATCH_BYTES (64 MiB) that every device which loads
+ * the library holds until the process exits.  Inputs are copied into that array; results go to
+ * caller-owned device buffers:
+ *   d_alias       u64 [n_energy][rows][K]  alias entries (layout of NEGF_EXPORT_ALIAS per task,
+ *                                          rows = W*L + 2W, K = W*L + 2)
+ *   d_mode_alias  u64 [n_energy][2][W]     injection-mode alias entries
+ *   d_c           f64 [n_energy][2]        Tr[Gamma_p A] for p = L, R
+ * precision: NEGF_FP64 or NEGF_FP32 (NEGF_SPLIT_TF32 computes as NEGF_FP32).
+ * The call runs on `stream` (a cudaStream_t on the current device) and synchronises it before
+ * returning, so device-side failures are reported by its status.
+ * Limits and errors: 1 <= n_energy <= NEGF_NOALLOC_MAX_TASKS and W*L + 2 <= 8192, else
+ * NEGF_E_INVALID; a problem whose scratch exceeds the fixed array returns NEGF_E_NOMEM (split
+ * the energies over several calls); bad values as for negf_build_tables (NEGF_E_INVALID);
+ * NEGF_E_NUMERIC for device-detected numerical failures; NEGF_E_CUDA for runtime failures.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Every call uses the
+ * same array, which keeps the previous call's contents (the parts that must start at zero are
+ * cleared by each call): calls that overlap on the GPU - from two host threads, or on two
+ * streams of one device - race on the array and corrupt each other's results. */
+#define NEGF_NOALLOC_SCRATCH_BYTES (64u << 20)
+#define NEGF_NOALLOC_MAX_TASKS 256
+negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t precision, void* stream,
+                                      uint64_t* d_alias, uint64_t* d_mode_alias, double* d_c);
+
 /* --- profiling (CUDA events around every kernel launch) ----------------------------------- */
 
 /* Turn per-kernel device-time accounting on (on != 0) or off; either way the counters reset.

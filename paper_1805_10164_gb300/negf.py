@@ -86,6 +86,7 @@ def load():
         "negf_tally_free": (None, [P]),
         "negf_current": (I32, [P, P, P, D, D, D, P, P, P, P]),
         "negf_profile_enable": (I32, [P, I32]),
+        "negf_build_tables_noalloc": (I32, [C.POINTER(negf_wire), I32, P, P, P, P]),
         "negf_profile_read": (I32, [P, I32, P, P, P, C.POINTER(I32)]),
     }
     for name, (res, args) in sig.items():
@@ -254,3 +255,17 @@ def negf_profile_read(ctx, cap=32):
         name = raw[32 * i:32 * (i + 1)].split(b"\0", 1)[0].decode()
         out[name] = (int(launches[i]), float(ms[i]))
     return out
+
+
+def negf_build_tables_noalloc(wire, precision, stream, d_alias, d_mode_alias, d_c):
+    """Table build of one wire (host arrays) into caller-owned torch CUDA buffers, with all
+    scratch in the library's fixed device array (no allocation).  Returns the status code."""
+    on = np.ascontiguousarray(wire.onsite, dtype=np.float64).reshape(-1)
+    et = np.ascontiguousarray(wire.eta, dtype=np.float64).reshape(-1)
+    E = np.ascontiguousarray(wire.energy, dtype=np.float64).reshape(-1)
+    w = negf_wire(int(wire.W), int(wire.L), float(wire.t), _ptr(on), _ptr(et), int(len(E)),
+                  _ptr(E), None, int(getattr(wire, "lead_model", 0)),
+                  float(getattr(wire, "gamma_lead", 0.0)))
+    handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return load().negf_build_tables_noalloc(C.byref(w), PRECISION[precision], C.c_void_p(handle),
+                                            _ptr(d_alias), _ptr(d_mode_alias), _ptr(d_c))
