@@ -148,7 +148,7 @@ def algorithmic_bytes(kernel, wl, precision, counts):
         return 8 * (steps + walkers)            # one 8-byte alias entry per draw
     if kernel == "alias_kernel":
         return entries * (wsz + 8)              # read a weight, write an entry
-    if kernel == "block_column_kernel":
+    if kernel == "diag_chain_kernels":
         return entries * wsz                    # write every weight once
     return None
 

@@ -40,6 +40,7 @@ extern "C" {
 
 #define NEGF_ABI_VERSION 1
 #define NEGF_MAX_W 64            /* widest supported slice (sites across the wire) */
+#define NEGF_MAX_SITES 6400      /* largest supported W*L per wire */
 #define NEGF_MAX_STEPS (1u << 24) /* largest accepted per-walk step cap */
 #define NEGF_TALLY_FIELDS 5      /* u64 counters per task, see negf_tally_counts */
 
@@ -77,7 +78,7 @@ typedef enum { NEGF_LEAD_STRIP = 0, NEGF_LEAD_WIDE_BAND = 1 } negf_lead_model;
  * Lead L couples to slice 0, lead R to slice L-1.  H has onsite[k*W+a] on the diagonal and -t
  * between nearest neighbours along and across the slices. */
 typedef struct {
-  int32_t W, L;                  /* 1 <= W <= NEGF_MAX_W, L >= 1 */
+  int32_t W, L;                  /* 1 <= W <= NEGF_MAX_W, L >= 1, W*L <= NEGF_MAX_SITES */
   double t;                      /* hopping magnitude, > 0 */
   const double* onsite;          /* [L*W] onsite energies, finite */
   const double* eta;             /* [L*W] Buttiker gamma_i >= 0, finite */
@@ -110,7 +111,9 @@ typedef struct {
 /* --- context -------------------------------------------------------------------------- */
 
 /* Create a context on CUDA device `device` enqueuing on `stream` (a cudaStream_t, NULL for the
- * legacy default stream).  The stream must outlive the context. */
+ * legacy default stream).  The stream must outlive the context.  Device buffers of the library
+ * come from the device's default stream-ordered memory pool; creating a context sets that
+ * pool's release threshold to "keep everything" so repeated builds reuse their memory. */
 negf_status negf_create(negf_ctx* out, int device, void* stream);
 void negf_destroy(negf_ctx ctx);
 const char* negf_last_error(negf_ctx ctx);
@@ -211,7 +214,7 @@ negf_status negf_current(negf_ctx ctx, negf_tables tables, negf_tally tally, dou
  * precision: NEGF_FP64 or NEGF_FP32 (NEGF_SPLIT_TF32 computes as NEGF_FP32).
  * The call runs on `stream` (a cudaStream_t on the current device) and synchronises it before
  * returning, so device-side failures are reported by its status.
- * Limits and errors: 1 <= n_energy <= NEGF_NOALLOC_MAX_TASKS and W*L + 2 <= 8192, else
+ * Limits and errors: 1 <= n_energy <= NEGF_NOALLOC_MAX_TASKS and W*L <= NEGF_MAX_SITES, else
  * NEGF_E_INVALID; a problem whose scratch exceeds the fixed array returns NEGF_E_NOMEM (split
  * the energies over several calls); bad values as for negf_build_tables (NEGF_E_INVALID);
  * NEGF_E_NUMERIC for device-detected numerical failures; NEGF_E_CUDA for runtime failures.

@@ -14,42 +14,59 @@ __device__ __forceinline__ double fermi(double E, double mu, double kT) {
 }
 
 // out layout: I[n_wires] | se[n_wires] | T[n_tasks] | T_se[n_tasks] | truncated (as double)
-// One thread per wire; its energies are summed in task order (deterministic).
-__global__ void current_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, int n_wires,
-                               const int32_t* __restrict__ wire_task0,
-                               const double* __restrict__ cvals,
-                               const unsigned long long* __restrict__ tally, int p, double mu_p,
-                               double mu_q, double kT, double* __restrict__ out) {
+// One block per wire; its energies are summed in a fixed order (thread-strided partial sums,
+// then a shared-memory tree), so the result does not depend on timing.
+constexpr int kCurThreads = 128;
+
+__global__ void __launch_bounds__(kCurThreads) current_kernel(
+    const TaskDesc* __restrict__ tasks, int n_tasks, int n_wires,
+    const int32_t* __restrict__ wire_task0, const double* __restrict__ cvals,
+    const unsigned long long* __restrict__ tally, int p, double mu_p, double mu_q, double kT,
+    double* __restrict__ out) {
+  __shared__ double s_acc[kCurThreads], s_var[kCurThreads], s_tr[kCurThreads];
   const int q = 1 - p;
   double* I = out;
   double* se = out + n_wires;
   double* T = se + n_wires;
   double* Tse = T + n_tasks;
   double* trunc = Tse + n_tasks;
-  for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < n_wires; w += gridDim.x * blockDim.x) {
-    double acc = 0.0, var = 0.0, tr = 0.0;
-    for (int k = wire_task0[w]; k < wire_task0[w + 1]; ++k) {
-      const TaskDesc d = tasks[k];
-      const unsigned long long* c = tally + (size_t)k * NEGF_TALLY_FIELDS;
-      const double N = (double)c[0];
-      const double nq = (double)c[1 + q];
-      const double cp = cvals[2 * k + p];
-      double Tk = 0.0, sk = 0.0;
-      if (N > 0.0) {
-        const double P = nq / N;
-        Tk = cp * P;
-        sk = cp * sqrt(P * (1.0 - P) / N);
-      }
-      T[k] = Tk;
-      Tse[k] = sk;
-      const double wd = d.w_E * (fermi(d.E, mu_p, kT) - fermi(d.E, mu_q, kT));
-      acc += wd * Tk;
-      var += wd * wd * sk * sk;
-      tr += (double)c[3];
+  const int w = blockIdx.x;
+  double acc = 0.0, var = 0.0, tr = 0.0;
+  for (int k = wire_task0[w] + threadIdx.x; k < wire_task0[w + 1]; k += blockDim.x) {
+    const TaskDesc& d = tasks[k];
+    const unsigned long long* c = tally + (size_t)k * NEGF_TALLY_FIELDS;
+    const double N = (double)c[0];
+    const double nq = (double)c[1 + q];
+    const double cp = cvals[2 * k + p];
+    double Tk = 0.0, sk = 0.0;
+    if (N > 0.0) {
+      const double P = nq / N;
+      Tk = cp * P;
+      sk = cp * sqrt(P * (1.0 - P) / N);
     }
-    I[w] = acc;
-    se[w] = sqrt(var);
-    atomicAdd(trunc, tr);
+    T[k] = Tk;
+    Tse[k] = sk;
+    const double wd = d.w_E * (fermi(d.E, mu_p, kT) - fermi(d.E, mu_q, kT));
+    acc += wd * Tk;
+    var += wd * wd * sk * sk;
+    tr += (double)c[3];
+  }
+  s_acc[threadIdx.x] = acc;
+  s_var[threadIdx.x] = var;
+  s_tr[threadIdx.x] = tr;
+  __syncthreads();
+  for (int h = kCurThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) {
+      s_acc[threadIdx.x] += s_acc[threadIdx.x + h];
+      s_var[threadIdx.x] += s_var[threadIdx.x + h];
+      s_tr[threadIdx.x] += s_tr[threadIdx.x + h];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    I[w] = s_acc[0];
+    se[w] = sqrt(s_var[0]);
+    if (s_tr[0] > 0.0) atomicAdd(trunc, s_tr[0]);
   }
 }
 
@@ -83,9 +100,7 @@ cudaError_t launch_current(const TaskDesc* d_tasks, int n_tasks, int n_wires,
                                   sizeof(double), s);
   if (e != cudaSuccess) return e;
   if (n_wires == 0) return cudaSuccess;
-  const int threads = 128;
-  const int blocks = (n_wires + threads - 1) / threads;
-  current_kernel<<<blocks, threads, 0, s>>>(
+  current_kernel<<<n_wires, kCurThreads, 0, s>>>(
       d_tasks, n_tasks, n_wires, d_wire_task0, d_c,
       reinterpret_cast<const unsigned long long*>(d_tally), start_lead, mu_p, mu_q, kT, d_out);
   return cudaGetLastError();

@@ -5,14 +5,22 @@
 // row needs is produced once per (wire, energy) task:
 //   * lead_modes_kernel   - eigen self-energies Sigma_m and Gamma_m of the lead strips
 //                           (Sec. II.A lead self-energies; Sec. III.A model)
-//   * rgf_sweep_kernel    - left- and right-connected blocks g^L_k, g^R_k (one CTA per sweep)
-//   * block_column_kernel - per slice m: G_mm by one more inversion, then the block column
-//                           G_{k,m} = -t g^L_k G_{k+1,m} (k < m), -t g^R_k G_{k-1,m} (k > m),
-//                           emitted directly as Step 6' weights (Eq. draw_i_simult and the lead
-//                           probability of Step 6'); two extra CTAs per task propagate G Phi for
-//                           the injection rows of Step 4/5 and the mode weights of
-//                           Eq. lead_out_probability.
-// W x W block inversions are Gauss-Jordan with partial pivoting in FP64 in shared memory.
+//   * rgf_sweep_kernel    - left- and right-connected blocks g^L_k, g^R_k (one warp per task
+//                           and direction; the sweep is a chain of W x W inversions)
+//   * diag_kernel         - per slice m: G_mm by one more inversion (one warp each); for the
+//                           boundary slices also G Phi, the A of every row (for the sum-rule
+//                           check), the mode weights of Eq. lead_out_probability and
+//                           c_p = Tr[Gamma_p A] (Eq. elast_lin_xpq)
+//   * chain_kernel        - per slice m and direction, the block column
+//                           G_{k,m} = -t g^L_k G_{k+1,m} (k < m), -t g^R_k G_{k-1,m} (k > m)
+//                           (one warp each), emitted directly as Step 6' weights
+//                           (Eq. draw_i_simult and the lead probability of Step 6'); the two
+//                           injection columns propagate G Phi for the rows of Steps 4-5.
+// W x W block inversions are Gauss-Jordan with partial pivoting in shared memory, one warp per
+// matrix (no block-wide barriers on the latency-bound chains), lanes owning columns.  All of
+// it runs in the precision of the tables: complex128 for NEGF_FP64, complex64 for NEGF_FP32;
+// the lead self-energies, whose square roots are singular at the sub-band edges, are FP64 in
+// both and rounded once.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -21,100 +29,118 @@
 namespace negf {
 namespace {
 
-constexpr int kThreads = 256;
+template <typename C> struct Real;
+template <> struct Real<cd> { using T = double; };
+template <> struct Real<cf> { using T = float; };
 
-__device__ __forceinline__ bool finite_cd(cd v) { return isfinite(v.x) && isfinite(v.y); }
+__device__ __forceinline__ cd to_c(cd v, cd) { return v; }
+__device__ __forceinline__ cf to_c(cd v, cf) { return cf{(float)v.x, (float)v.y}; }
+__device__ __forceinline__ cd mkc(double a, double b, cd) { return cd{a, b}; }
+__device__ __forceinline__ cf mkc(double a, double b, cf) { return cf{(float)a, (float)b}; }
+__device__ __forceinline__ bool finite_c(cd v) { return isfinite(v.x) && isfinite(v.y); }
+__device__ __forceinline__ bool finite_c(cf v) { return isfinite(v.x) && isfinite(v.y); }
 
 // Sine mode phi_m(a) of a W-site cross-section, m, a in [0, W).
 __device__ __forceinline__ double phi_mode(int a, int m, int W) {
   return sqrt(2.0 / (W + 1)) * sinpi((double)((m + 1) * (a + 1)) / (double)(W + 1));
 }
 
-// Gauss-Jordan inversion of the W x W left half of aug [W][2W] (right half holds I on entry,
-// the inverse on exit).  Partial pivoting by |a_ik|^2 (lowest index on ties).  All threads of
-// the block must call it.  Returns false (uniformly) on an exactly zero pivot column.
-__device__ bool gj_invert(cd* aug, int W, cd* fcol, int* s_piv) {
-  const int W2 = 2 * W;
-  const int tid = threadIdx.x, bd = blockDim.x, lane = tid & 31;
+// Gauss-Jordan inversion of the W x W left half of aug [W][2W] by one warp (right half holds
+// I on entry, the inverse on exit).  Partial pivoting by |a_ik|^2, lowest index on ties.
+// Lanes own columns of the pivot-row update, so each lane's W row updates are independent.
+// Returns false (uniformly across the warp) on an exactly zero or non-finite pivot column.
+template <typename C>
+__device__ bool warp_gj(C* aug, int W, C* fcol) {
+  using R = typename Real<C>::T;
+  const int W2 = 2 * W, lane = threadIdx.x & 31;
+  const unsigned FULL = 0xffffffffu;
   for (int k = 0; k < W; ++k) {
-    if (tid < 32) {
-      double best = -1.0;
-      int bi = k;
-      for (int i = k + lane; i < W; i += 32) {
-        double v = norm2(aug[i * W2 + k]);
-        if (v > best) { best = v; bi = i; }
-      }
-      for (int off = 16; off > 0; off >>= 1) {
-        double ov = __shfl_xor_sync(0xffffffffu, best, off);
-        int oi = __shfl_xor_sync(0xffffffffu, bi, off);
-        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-      }
-      if (lane == 0) *s_piv = (best > 0.0 && isfinite(best)) ? bi : -1;
+    R best = -1;
+    int bi = k;
+    for (int i = k + lane; i < W; i += 32) {
+      const R v = norm2(aug[i * W2 + k]);
+      if (v > best) { best = v; bi = i; }
     }
-    __syncthreads();
-    const int p = *s_piv;
-    if (p < 0) return false;
-    if (p != k) {
-      for (int j = k + tid; j < W2; j += bd) {
-        cd tmp = aug[k * W2 + j];
-        aug[k * W2 + j] = aug[p * W2 + j];
-        aug[p * W2 + j] = tmp;
+    for (int off = 16; off > 0; off >>= 1) {
+      const R ov = __shfl_xor_sync(FULL, best, off);
+      const int oi = __shfl_xor_sync(FULL, bi, off);
+      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (!(best > 0) || !isfinite(best)) return false;
+    if (bi != k) {
+      for (int j = k + lane; j < W2; j += 32) {
+        const C tmp = aug[k * W2 + j];
+        aug[k * W2 + j] = aug[bi * W2 + j];
+        aug[bi * W2 + j] = tmp;
       }
     }
-    __syncthreads();
-    const cd inv = cdiv(mk(1.0, 0.0), aug[k * W2 + k]);
-    for (int i = tid; i < W; i += bd) fcol[i] = aug[i * W2 + k];
-    __syncthreads();
-    for (int j = k + tid; j < W2; j += bd) aug[k * W2 + j] = aug[k * W2 + j] * inv;
-    __syncthreads();
-    const int span = W2 - k;
-    for (int idx = tid; idx < W * span; idx += bd) {
-      const int i = idx / span, j = k + idx % span;
-      if (i != k) aug[i * W2 + j] = aug[i * W2 + j] - fcol[i] * aug[k * W2 + j];
+    __syncwarp();
+    const C inv = cdiv(mkc(1.0, 0.0, C{}), aug[k * W2 + k]);
+    for (int i = lane; i < W; i += 32) fcol[i] = aug[i * W2 + k];
+    __syncwarp();
+    for (int j = k + lane; j < W2; j += 32) {
+      const C pk = aug[k * W2 + j] * inv;
+      aug[k * W2 + j] = pk;
+#pragma unroll 4
+      for (int i = 0; i < W; ++i)
+        if (i != k) aug[i * W2 + j] = aug[i * W2 + j] - fcol[i] * pk;
     }
-    __syncthreads();
+    __syncwarp();
   }
   return true;
 }
 
-// Boundary self-energy block Phi diag(sig) Phi^T of one lead into out [W][W] (smem).
-__device__ void lead_block(const double* phi, const cd* sig, int W, cd* out) {
-  for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+// Boundary self-energy block Phi diag(sig) Phi^T of one lead into out [W][W] (one warp).
+template <typename C>
+__device__ void lead_block(const double* phi, const cd* sig, int W, C* out) {
+  for (int idx = threadIdx.x & 31; idx < W * W; idx += 32) {
     const int a = idx / W, b = idx % W;
     cd acc = mk(0.0, 0.0);
     for (int m = 0; m < W; ++m) acc = acc + (phi[a * W + m] * phi[b * W + m]) * sig[m];
-    out[idx] = acc;
+    out[idx] = to_c(acc, C{});
   }
 }
 
-// aug <- [E - H_kk - Sigma_s(k) - extra | I] where extra = sum of the given W x W blocks
-// scaled by the given factors (lead blocks with factor 1, connected blocks with t^2).
-__device__ void build_slice(cd* aug, int W, double E, double t, const double* onsite,
-                            const double* eta, int k, const cd* x1, double f1, const cd* x2,
+// aug <- [E - H_kk - Sigma_s(k) - f1 x1 - f2 x2 | I] (one warp); x1/x2 are the lead block
+// (factor 1) or a connected block g (factor t^2), or null.
+template <typename C>
+__device__ void build_slice(C* aug, int W, double E, double t, const double* onsite,
+                            const double* eta, int k, const C* x1, double f1, const C* x2,
                             double f2) {
+  using R = typename Real<C>::T;
   const int W2 = 2 * W;
-  for (int idx = threadIdx.x; idx < W * W2; idx += blockDim.x) {
+  for (int idx = threadIdx.x & 31; idx < W * W2; idx += 32) {
     const int a = idx / W2, j = idx % W2;
-    cd v;
+    C v;
     if (j < W) {
       const int b = j;
-      v = mk(0.0, 0.0);
-      if (a == b) v = mk(E - onsite[k * W + a], 0.5 * eta[k * W + a]);
-      if (a - b == 1 || b - a == 1) v.x += t;
-      if (x1) v = v - f1 * x1[a * W + b];
-      if (x2) v = v - f2 * x2[a * W + b];
+      v = mkc(a == b ? E - onsite[k * W + a] : 0.0, a == b ? 0.5 * eta[k * W + a] : 0.0, C{});
+      if (a - b == 1 || b - a == 1) v.x += (R)t;
+      if (x1) v = v - (R)f1 * x1[a * W + b];
+      if (x2) v = v - (R)f2 * x2[a * W + b];
     } else {
-      v = mk((j - W) == a ? 1.0 : 0.0, 0.0);
+      v = mkc((j - W) == a ? 1.0 : 0.0, 0.0, C{});
     }
     aug[idx] = v;
   }
 }
 
-__global__ void lead_modes_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, cd* sig,
-                                  double* gam, int32_t* err) {
+__global__ void lead_modes_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
+                                  const double* __restrict__ wire, double* phi, float* phi32,
+                                  float* eta32, cd* sig, double* gam, int32_t* err) {
   const int task = blockIdx.x;
   if (task >= n_tasks) return;
   const TaskDesc d = tasks[task];
+  if (d.e_idx == 0) {
+    // once per wire: transverse modes and the FP32 copy of eta
+    for (int idx = threadIdx.x; idx < d.W * d.W; idx += blockDim.x) {
+      const double v = phi_mode(idx / d.W, idx % d.W, d.W);
+      phi[d.phi_off + idx] = v;
+      phi32[d.phi_off + idx] = (float)v;
+    }
+    const double* eta = wire + d.onsite_off + d.n;
+    for (int i = threadIdx.x; i < d.n; i += blockDim.x) eta32[d.onsite_off / 2 + i] = (float)eta[i];
+  }
   for (int m = threadIdx.x; m < d.W; m += blockDim.x) {
     cd s;
     double g;
@@ -141,315 +167,343 @@ __global__ void lead_modes_kernel(const TaskDesc* __restrict__ tasks, int n_task
   }
 }
 
-// One CTA per (task, direction): direction 0 = left sweep g^L_0..g^L_{L-2} (Sigma_L at slice
+// per-warp shared memory of the inversion kernels (FP64, W = 64: 225 KB)
+template <typename C>
+__host__ __device__ inline size_t inv_warp_bytes(int W) {
+  // aug W x 2W | lblk W x W | fcol W  (complex)  | phi W x W double
+  return sizeof(C) * (size_t)(3 * W * W + W) + sizeof(double) * (size_t)(W * W);
+}
+
+// One warp per (task, direction): direction 0 = left sweep g^L_0..g^L_{L-2} (Sigma_L at slice
 // 0); direction 1 = right sweep g^R_{L-1}..g^R_1 (Sigma_R at slice L-1).
-__global__ void __launch_bounds__(kThreads) rgf_sweep_kernel(
-    const TaskDesc* __restrict__ tasks, const double* __restrict__ wire, const cd* __restrict__ sig,
-    cd* gL, cd* gR, int32_t* err) {
-  const TaskDesc d = tasks[blockIdx.x];
-  const int dir = blockIdx.y;
-  const int W = d.W, L = d.L, W2 = 2 * W;
+template <typename C>
+__global__ void rgf_sweep_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, int max_W,
+                                 const double* __restrict__ wire, const double* __restrict__ phig,
+                                 const cd* __restrict__ sig, C* gL, C* gR, int32_t* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cd* aug = reinterpret_cast<cd*>(smem_raw);           // W x 2W
-  cd* prev = aug + W * W2;                              // W x W
-  cd* lblk = prev + W * W;                              // W x W
-  cd* fcol = lblk + W * W;                              // W
-  double* phi = reinterpret_cast<double*>(fcol + W);    // W x W
-  int* s_piv = reinterpret_cast<int*>(phi + W * W);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int job = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (job >= 2 * n_tasks) return;
+  const TaskDesc d = tasks[job >> 1];
+  const int dir = job & 1;
+  const int W = d.W, L = d.L, W2 = 2 * W;
+  unsigned char* base = smem_raw + (size_t)warp * inv_warp_bytes<C>(max_W);
+  C* aug = reinterpret_cast<C*>(base);
+  C* lblk = aug + W * W2;          // lead block, then the previous connected block
+  C* fcol = lblk + W * W;
+  double* phi = reinterpret_cast<double*>(fcol + W);
   const double* onsite = wire + d.onsite_off;
   const double* eta = onsite + d.n;
-  const int steps = L - 1;
-  if (steps <= 0) return;
-  for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x)
-    phi[idx] = phi_mode(idx / W, idx % W, W);
-  __syncthreads();
+  if (L < 2) return;
+  for (int idx = lane; idx < W * W; idx += 32) phi[idx] = phig[d.phi_off + idx];
+  __syncwarp();
   lead_block(phi, sig + d.lead_off, W, lblk);
-  __syncthreads();
-  cd* out = dir == 0 ? gL : gR;
-  for (int s = 0; s < steps; ++s) {
+  __syncwarp();
+  C* out = dir == 0 ? gL : gR;
+  for (int s = 0; s < L - 1; ++s) {
     const int k = dir == 0 ? s : L - 1 - s;
-    if (s == 0) build_slice(aug, W, d.E, d.t, onsite, eta, k, lblk, 1.0, nullptr, 0.0);
-    else build_slice(aug, W, d.E, d.t, onsite, eta, k, prev, d.t * d.t, nullptr, 0.0);
-    __syncthreads();
-    if (!gj_invert(aug, W, fcol, s_piv)) {
-      if (threadIdx.x == 0) atomicOr(err, ERR_SINGULAR);
+    build_slice(aug, W, d.E, d.t, onsite, eta, k, lblk, s == 0 ? 1.0 : d.t * d.t,
+                (const C*)nullptr, 0.0);
+    __syncwarp();
+    if (!warp_gj(aug, W, fcol)) {
+      if (lane == 0) atomicOr(err, ERR_SINGULAR);
       return;
     }
-    cd* dst = out + d.g_off + (uint64_t)k * W * W;
+    C* dst = out + d.g_off + (uint64_t)k * W * W;
     bool bad = false;
-    for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
-      const cd v = aug[(idx / W) * W2 + W + idx % W];
-      prev[idx] = v;
+    for (int idx = lane; idx < W * W; idx += 32) {
+      const C v = aug[(idx / W) * W2 + W + idx % W];
+      lblk[idx] = v;
       dst[idx] = v;
-      bad |= !finite_cd(v);
+      bad |= !finite_c(v);
     }
-    if (bad) atomicOr(err, ERR_NONFINITE);
-    __syncthreads();
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
+    __syncwarp();
   }
 }
 
-template <typename R> struct CT;
-template <> struct CT<double> { using T = cd; };
-template <> struct CT<float> { using T = cf; };
-__device__ __forceinline__ cd to_c(cd v, double) { return v; }
-__device__ __forceinline__ cf to_c(cd v, float) { return cf{(float)v.x, (float)v.y}; }
-
-// Shared-memory layout of block_column_kernel for slice width W and propagation type C:
-//   region0 : max(W x 2W cd (inversion), 4 W x W C (propagation X0, X1, Gb, Xs))
-//   phi, rs, red : W x W double each;  lblk : W x W cd;  fcol : W cd;  arow, lgam : W double
-template <typename C>
-__host__ __device__ inline size_t column_region0(int W) {
-  const size_t a = sizeof(cd) * (size_t)(2 * W * W);
-  const size_t b = sizeof(C) * (size_t)(4 * W * W);
-  return ((a > b ? a : b) + 15) & ~size_t(15);
-}
-template <typename C>
-__host__ __device__ inline size_t column_smem_bytes(int W) {
-  return column_region0<C>(W) + sizeof(double) * (size_t)(3 * W * W) +
-         sizeof(cd) * (size_t)(W * W + W) + sizeof(double) * (size_t)(2 * W) + 16;
+// last task whose first job index (`first(t)`) is <= job
+template <typename F>
+__device__ __forceinline__ int find_task(int n_tasks, uint32_t job, F first) {
+  int lo = 0, hi = n_tasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first(mid) <= job) lo = mid; else hi = mid - 1;
+  }
+  return lo;
 }
 
-// Per block column: see the file header.  blockIdx.y = m in [0, L) for site column m,
-// L for the injection rows of lead L, L+1 for those of lead R.
-template <typename R>
-__global__ void __launch_bounds__(kThreads) block_column_kernel(
-    const TaskDesc* __restrict__ tasks, const double* __restrict__ wire, const cd* __restrict__ sig,
-    const double* __restrict__ gam, const cd* __restrict__ gL, const cd* __restrict__ gR,
-    R* __restrict__ weights, double* __restrict__ rowsum, double* __restrict__ mode_w,
-    double* __restrict__ cvals, int32_t* err) {
-  using C = typename CT<R>::T;
-  const TaskDesc d = tasks[blockIdx.x];
-  const int W = d.W, L = d.L, n = d.n, K = d.K, W2 = 2 * W;
-  const int y = blockIdx.y;
-  if (y >= L + 2) return;
-  const int tid = threadIdx.x, bd = blockDim.x;
-  const bool inj = y >= L;
-  const int p = y - L;                        // injection lead (valid if inj)
-  const int m0 = inj ? (p == 0 ? 0 : L - 1) : y;
-
+// One warp per (task, y): y in [0, L) site column m = y, y = L / L+1 injection columns of lead
+// L / R.  Computes G_mm, the start block S = G_mm or G_mm Phi, A of its W rows, and for
+// injection columns the mode weights and c_p.  A is stored where the row sums will go; the
+// alias build checks each row's sum against it and then overwrites it.
+template <typename C>
+__global__ void diag_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
+                            int max_W, const double* __restrict__ wire,
+                            const double* __restrict__ phig, const cd* __restrict__ sig,
+                            const double* __restrict__ gam, const C* __restrict__ gL,
+                            const C* __restrict__ gR, C* __restrict__ start,
+                            double* __restrict__ rowsum, double* __restrict__ mode_w,
+                            double* __restrict__ cvals, int32_t* err) {
+  using R = typename Real<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cd* aug = reinterpret_cast<cd*>(smem_raw);                       // W x 2W (inversion)
-  C* X0 = reinterpret_cast<C*>(smem_raw);                          // propagation, after it
-  C* X1 = X0 + W * W;
-  C* Gb = X1 + W * W;
-  C* Xs = Gb + W * W;
-  double* phi = reinterpret_cast<double*>(smem_raw + column_region0<C>(W));
-  double* rs = phi + W * W;                                        // partial row sums [b][a]
-  double* red = rs + W * W;                                        // reduction scratch
-  cd* lblk = reinterpret_cast<cd*>(red + W * W);                   // lead / start block
-  cd* fcol = lblk + W * W;
-  double* arow = reinterpret_cast<double*>(fcol + W);              // A_ii per row
-  double* lgam = arow + W;                                         // lead Gamma_m
-  __shared__ int s_piv;
-
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t job = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (job >= n_jobs) return;
+  const int task = find_task(n_tasks, job, [&](int t) { return tasks[t].col_base; });
+  const TaskDesc d = tasks[task];
+  const int W = d.W, L = d.L, n = d.n, W2 = 2 * W;
+  const int y = (int)(job - d.col_base);
+  const bool inj = y >= L;
+  const int p = y - L;
+  const int m0 = inj ? (p == 0 ? 0 : L - 1) : y;
+  unsigned char* base = smem_raw + (size_t)warp * inv_warp_bytes<C>(max_W);
+  C* aug = reinterpret_cast<C*>(base);
+  C* lblk = aug + W * W2;             // lead block, then the start block
+  C* fcol = lblk + W * W;
+  double* phi = reinterpret_cast<double*>(fcol + W);
   const double* onsite = wire + d.onsite_off;
   const double* eta = onsite + n;
   const double t = d.t;
-  for (int idx = tid; idx < W * W; idx += bd) {
-    phi[idx] = phi_mode(idx / W, idx % W, W);
-    rs[idx] = 0.0;
+  for (int idx = lane; idx < W * W; idx += 32) phi[idx] = phig[d.phi_off + idx];
+  __syncwarp();
+  if (m0 == 0 || m0 == L - 1) lead_block(phi, sig + d.lead_off, W, lblk);
+  __syncwarp();
+  const C* left = m0 == 0 ? lblk : gL + d.g_off + (uint64_t)(m0 - 1) * W * W;
+  const C* right = m0 == L - 1 ? lblk : gR + d.g_off + (uint64_t)(m0 + 1) * W * W;
+  build_slice(aug, W, d.E, t, onsite, eta, m0, left, m0 == 0 ? 1.0 : t * t, right,
+              m0 == L - 1 ? 1.0 : t * t);
+  __syncwarp();
+  if (!warp_gj(aug, W, fcol)) {
+    if (lane == 0) atomicOr(err, ERR_SINGULAR);
+    return;
   }
-  for (int m = tid; m < W; m += bd) lgam[m] = gam[d.lead_off + m];
-  __syncthreads();
-
-  // ---- diagonal block G_{m0 m0} in FP64: invert E - H - Sigma_s - left - right
-  {
-    const cd* left;
-    const cd* right;
-    double fl, fr;
-    const bool lead_here = (m0 == 0) || (m0 == L - 1);
-    if (lead_here) lead_block(phi, sig + d.lead_off, W, lblk);
-    __syncthreads();
-    if (m0 == 0) { left = lblk; fl = 1.0; }
-    else { left = gL + d.g_off + (uint64_t)(m0 - 1) * W * W; fl = t * t; }
-    if (m0 == L - 1) { right = lblk; fr = 1.0; }
-    else { right = gR + d.g_off + (uint64_t)(m0 + 1) * W * W; fr = t * t; }
-    build_slice(aug, W, d.E, t, onsite, eta, m0, left, fl, right, fr);
-    __syncthreads();
-    if (!gj_invert(aug, W, fcol, &s_piv)) {
-      if (tid == 0) atomicOr(err, ERR_SINGULAR);
-      return;
-    }
-  }
-  // start block S = G_mm (site column) or G_mm Phi (injection) in FP64, kept in lblk
-  for (int idx = tid; idx < W * W; idx += bd) {
+  C* dst = start + d.start_off + (uint64_t)y * W * W;
+  C* sblk = lblk;                     // the lead block is no longer needed
+  bool bad = false;
+  for (int idx = lane; idx < W * W; idx += 32) {
     const int a = idx / W, b = idx % W;
-    cd v;
+    C v;
     if (!inj) {
       v = aug[a * W2 + W + b];
     } else {
-      v = mk(0.0, 0.0);
-      for (int c = 0; c < W; ++c) v = v + phi[c * W + b] * aug[a * W2 + W + c];
+      v = mkc(0.0, 0.0, C{});
+      for (int c = 0; c < W; ++c) v = v + (R)phi[c * W + b] * aug[a * W2 + W + c];
     }
-    lblk[idx] = v;
+    sblk[idx] = v;
+    dst[idx] = v;
+    bad |= !finite_c(v);
   }
-  __syncthreads();
-  // A of each row: site b: -2 Im G_bb;  mode mu: -2 Im (Phi^T G Phi)_{mu mu}
-  if (tid < W) {
-    const int b = tid;
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
+  __syncwarp();
+  // A per row: site b: -2 Im G_bb;  mode mu: -2 Im (Phi^T G Phi)_{mu mu}
+  double* mw_s = reinterpret_cast<double*>(aug);      // aug is dead
+  for (int b = lane; b < W; b += 32) {
     double A;
     if (!inj) {
-      A = -2.0 * lblk[b * W + b].y;
+      A = -2.0 * (double)sblk[b * W + b].y;
+      rowsum[d.row_base + m0 * W + b] = A;
     } else {
       double im = 0.0;
-      for (int a = 0; a < W; ++a) im += phi[a * W + b] * lblk[a * W + b].y;
+      for (int a = 0; a < W; ++a) im += phi[a * W + b] * (double)sblk[a * W + b].y;
       A = -2.0 * im;
-      const double mw = lgam[b] * A;
+      rowsum[d.row_base + n + p * W + b] = A;
+      const double mw = gam[d.lead_off + b] * A;
       mode_w[d.mode_off + p * W + b] = mw;
-      red[b] = mw;
+      mw_s[b] = mw;
     }
-    arow[b] = A;
   }
-  __syncthreads();
-  if (inj && tid == 0) {
+  __syncwarp();
+  if (inj && lane == 0) {
     double c = 0.0;
-    for (int b = 0; b < W; ++b) c += red[b];
-    cvals[blockIdx.x * 2 + p] = c;
+    for (int b = 0; b < W; ++b) c += mw_s[b];      // fixed order
+    cvals[task * 2 + p] = c;
     rowsum[d.row_base + d.rows + p] = c;
   }
-  // the inversion buffer is dead: convert the start block into the propagation precision
-  for (int idx = tid; idx < W * W; idx += bd) {
-    const C v = to_c(lblk[idx], R(0));
-    X0[idx] = v;
-    Xs[idx] = v;
-  }
-  __syncthreads();
+}
 
+template <typename C>
+__host__ __device__ inline size_t chain_warp_bytes(int W) {
+  // X0, X1, Gb : W x W complex | phi : W x W real | lgam : W real
+  return sizeof(C) * (size_t)(3 * W * W) + sizeof(typename Real<C>::T) * (size_t)(W * W + W);
+}
+
+// One warp per (task, y, direction): the block column of start slice m0 propagated towards
+// slice 0 (direction 0, which also emits the start block) or towards slice L-1 (direction 1),
+// each block emitted as Step 6' weights of the column's W rows.
+template <typename C>
+__global__ void chain_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
+                             int max_W, const typename Real<C>::T* __restrict__ eta_all,
+                             const typename Real<C>::T* __restrict__ phig,
+                             const double* __restrict__ gam, const C* __restrict__ gL,
+                             const C* __restrict__ gR, const C* __restrict__ start,
+                             typename Real<C>::T* __restrict__ weights) {
+  using R = typename Real<C>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t job = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (job >= n_jobs) return;
+  const int task = find_task(n_tasks, job, [&](int t) { return 2 * tasks[t].col_base; });
+  const TaskDesc d = tasks[task];
+  const int W = d.W, L = d.L, n = d.n, K = d.K;
+  const uint32_t local = job - 2 * d.col_base;
+  const int y = (int)(local >> 1), dir = (int)(local & 1);
+  const bool inj = y >= L;
+  const int p = y - L;
+  const int m0 = inj ? (p == 0 ? 0 : L - 1) : y;
+  if (dir == 1 && m0 == L - 1) return;           // nothing towards slice L-1
+  unsigned char* base = smem_raw + (size_t)warp * chain_warp_bytes<C>(max_W);
+  C* X0 = reinterpret_cast<C*>(base);
+  C* X1 = X0 + W * W;
+  C* Gb = X1 + W * W;
+  R* phi = reinterpret_cast<R*>(Gb + W * W);
+  R* lgam = phi + W * W;
+  // eta in the table precision: the FP64 wire array (+ n past onsite) or its FP32 copy
+  const R* eta = eta_all + (sizeof(R) == 8 ? d.onsite_off + n : d.onsite_off / 2);
+  const R mt = (R)(-d.t);
+  for (int idx = lane; idx < W * W; idx += 32) {
+    phi[idx] = phig[d.phi_off + idx];
+    X0[idx] = start[d.start_off + (uint64_t)y * W * W + idx];
+  }
+  for (int m = lane; m < W; m += 32) lgam[m] = (R)gam[d.lead_off + m];
+  __syncwarp();
   const int row0 = inj ? n + p * W : m0 * W;
   R* wrow = weights + d.wt_off;
-  // Emit the weights of block k held in X (X[a][b] = G_{(k,a),(m0,b)}, or (G Phi)_{(k,a),mu}):
-  // site columns gamma_(k,a) |X[a][b]|^2, and at the boundary slices the lead columns
-  // sum_nu Gamma_nu |(Phi^T X)_{nu b}|^2 = <psi_b|Gamma_lead|psi_b>.  Partial row sums in rs.
+  // weights of block k held in X (X[a][b] = G_{(k,a),(m0,b)} or (G Phi)_{(k,a),mu})
   auto emit = [&](const C* X, int k) {
-    for (int idx = tid; idx < W * W; idx += bd) {
+    for (int idx = lane; idx < W * W; idx += 32) {
       const int b = idx / W, a = idx % W;
-      const R w = (R)eta[k * W + a] * norm2(X[a * W + b]);
-      wrow[(uint64_t)(row0 + b) * K + k * W + a] = w;
-      rs[idx] += (double)w;
+      wrow[(uint64_t)(row0 + b) * K + k * W + a] = eta[k * W + a] * norm2(X[a * W + b]);
     }
     if (k == 0 || k == L - 1) {
-      for (int idx = tid; idx < W * W; idx += bd) {
-        const int nu = idx / W, b = idx % W;
-        C acc = C{0, 0};
-        for (int a = 0; a < W; ++a) acc = acc + (R)phi[a * W + nu] * X[a * W + b];
-        red[idx] = lgam[nu] * (double)norm2(acc);
-      }
-      __syncthreads();
-      if (tid < W) {
-        const int b = tid;
-        double s = 0.0;
-        for (int nu = 0; nu < W; ++nu) s += red[nu * W + b];
-        const R wl = (R)s;
-        if (k == 0) wrow[(uint64_t)(row0 + b) * K + n + 0] = wl;
-        if (k == L - 1) wrow[(uint64_t)(row0 + b) * K + n + 1] = wl;
-        rs[b * W] += (double)wl * (double)((k == 0) + (k == L - 1));
+      // lead weight of row b: sum_nu Gamma_nu |(Phi^T X)_{nu b}|^2 = <psi_b|Gamma_lead|psi_b>
+      for (int b = lane; b < W; b += 32) {
+        R sum = 0;
+        for (int nu = 0; nu < W; ++nu) {
+          C acc = C{0, 0};
+          for (int a = 0; a < W; ++a) acc = acc + phi[a * W + nu] * X[a * W + b];
+          sum += lgam[nu] * norm2(acc);
+        }
+        if (k == 0) wrow[(uint64_t)(row0 + b) * K + n + 0] = sum;
+        if (k == L - 1) wrow[(uint64_t)(row0 + b) * K + n + 1] = sum;
       }
     }
-    __syncthreads();
   };
-  emit(X0, m0);
   C* cur = X0;
   C* nxt = X1;
-  // towards slice 0: X_k = -t g^L_k X_{k+1}
-  for (int k = m0 - 1; k >= 0; --k) {
-    const cd* gk = gL + d.g_off + (uint64_t)k * W * W;
-    for (int idx = tid; idx < W * W; idx += bd) Gb[idx] = to_c(gk[idx], R(0));
-    __syncthreads();
-    for (int idx = tid; idx < W * W; idx += bd) {
+  if (dir == 0) emit(cur, m0);
+  const int k_end = dir == 0 ? -1 : L;
+  const int step = dir == 0 ? -1 : 1;
+  const C* gsrc = dir == 0 ? gL : gR;
+  for (int k = m0 + step; k != k_end; k += step) {
+    const C* gk = gsrc + d.g_off + (uint64_t)k * W * W;
+    for (int idx = lane; idx < W * W; idx += 32) Gb[idx] = gk[idx];
+    __syncwarp();
+    for (int idx = lane; idx < W * W; idx += 32) {
       const int a = idx / W, b = idx % W;
       C acc = C{0, 0};
       for (int c = 0; c < W; ++c) acc = acc + Gb[a * W + c] * cur[c * W + b];
-      nxt[idx] = (R)(-t) * acc;
+      nxt[idx] = mt * acc;
     }
-    __syncthreads();
+    __syncwarp();
     C* tmp = cur; cur = nxt; nxt = tmp;
     emit(cur, k);
+    __syncwarp();
   }
-  // towards slice L-1 from the saved start: X_k = -t g^R_k X_{k-1}
-  for (int idx = tid; idx < W * W; idx += bd) X0[idx] = Xs[idx];
-  cur = X0;
-  nxt = X1;
-  __syncthreads();
-  for (int k = m0 + 1; k < L; ++k) {
-    const cd* gk = gR + d.g_off + (uint64_t)k * W * W;
-    for (int idx = tid; idx < W * W; idx += bd) Gb[idx] = to_c(gk[idx], R(0));
-    __syncthreads();
-    for (int idx = tid; idx < W * W; idx += bd) {
-      const int a = idx / W, b = idx % W;
-      C acc = C{0, 0};
-      for (int c = 0; c < W; ++c) acc = acc + Gb[a * W + c] * cur[c * W + b];
-      nxt[idx] = (R)(-t) * acc;
-    }
-    __syncthreads();
-    C* tmp = cur; cur = nxt; nxt = tmp;
-    emit(cur, k);
+}
+
+int warps_for(size_t per_warp, int max_warps) {
+  int w = max_warps;
+  while (w > 1 && per_warp * w > 96 * 1024) --w;
+  return w;
+}
+
+template <typename C>
+cudaError_t sweep_impl(const TaskDesc* d_tasks, int n_tasks, int max_W, const double* d_wire,
+                       const double* d_phi, const cd* d_sig, C* d_gL, C* d_gR, int32_t* d_err,
+                       cudaStream_t s) {
+  // one warp per CTA: each sweep is a serial chain, best spread one per SM
+  const size_t smem = inv_warp_bytes<C>(max_W);
+  cudaError_t e = cudaFuncSetAttribute(rgf_sweep_kernel<C>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  rgf_sweep_kernel<C><<<2 * n_tasks, 32, smem, s>>>(d_tasks, n_tasks, max_W, d_wire, d_phi,
+                                                    d_sig, d_gL, d_gR, d_err);
+  return cudaGetLastError();
+}
+
+template <typename C>
+cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, int max_W,
+                         const double* d_wire, const typename Real<C>::T* d_eta,
+                         const double* d_phi, const typename Real<C>::T* d_phiR, const cd* d_sig,
+                         const double* d_gam, const C* d_gL, const C* d_gR, C* d_start,
+                         typename Real<C>::T* d_w, double* d_rowsum, double* d_mode_w,
+                         double* d_c, int32_t* d_err, cudaStream_t s) {
+  {
+    const size_t per = inv_warp_bytes<C>(max_W);
+    const int warps = warps_for(per, 4);
+    const size_t smem = per * warps;
+    cudaError_t e = cudaFuncSetAttribute(diag_kernel<C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    diag_kernel<C><<<(n_cols + warps - 1) / warps, 32 * warps, smem, s>>>(
+        d_tasks, n_tasks, n_cols, max_W, d_wire, d_phi, d_sig, d_gam, d_gL, d_gR, d_start,
+        d_rowsum, d_mode_w, d_c, d_err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
-  // FP64 row sums and the sum-rule check (rows must add up to <i|A|i>, Sec. II.D)
-  if (tid < W) {
-    const int b = tid;
-    double s = 0.0;
-    for (int a = 0; a < W; ++a) s += rs[b * W + a];
-    rowsum[d.row_base + row0 + b] = s;
-    const double A = arow[b];
-    const double tol = sizeof(R) == 8 ? 1e-6 : 1e-2;
-    if (!isfinite(s) || s < 0.0) atomicOr(err, ERR_NONFINITE);
-    else if (A > 1e-300 && fabs(s - A) > tol * A) atomicOr(err, ERR_ROWSUM);
-  }
+  const uint32_t jobs = 2 * n_cols;
+  const size_t per = chain_warp_bytes<C>(max_W);
+  const int warps = warps_for(per, 8);
+  const size_t smem = per * warps;
+  cudaError_t e = cudaFuncSetAttribute(chain_kernel<C>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  chain_kernel<C><<<(jobs + warps - 1) / warps, 32 * warps, smem, s>>>(
+      d_tasks, n_tasks, jobs, max_W, d_eta, d_phiR, d_gam, d_gL, d_gR, d_start, d_w);
+  return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_lead_modes(const TaskDesc* d_tasks, int n_tasks, int max_W, cd* d_sig,
-                              double* d_gam, int32_t* d_err, cudaStream_t s) {
+cudaError_t launch_lead_modes(const TaskDesc* d_tasks, int n_tasks, int max_W,
+                              const double* d_wire, double* d_phi, float* d_phi32,
+                              float* d_eta32, cd* d_sig, double* d_gam, int32_t* d_err,
+                              cudaStream_t s) {
   if (n_tasks == 0) return cudaSuccess;
-  lead_modes_kernel<<<n_tasks, 64, 0, s>>>(d_tasks, n_tasks, d_sig, d_gam, d_err);
+  lead_modes_kernel<<<n_tasks, 128, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_phi32, d_eta32,
+                                            d_sig, d_gam, d_err);
   return cudaGetLastError();
 }
 
-static size_t sweep_smem(int W) {
-  return sizeof(cd) * (size_t)(W * 2 * W + W * W + W * W + W) + sizeof(double) * W * W + 16;
+cudaError_t launch_rgf_sweep(const TaskDesc* d_tasks, int n_tasks, int max_W, int precision,
+                             const double* d_wire, const double* d_phi, const cd* d_sig,
+                             void* d_gL, void* d_gR, int32_t* d_err, cudaStream_t s) {
+  if (n_tasks == 0) return cudaSuccess;
+  if (precision == NEGF_FP64)
+    return sweep_impl<cd>(d_tasks, n_tasks, max_W, d_wire, d_phi, d_sig,
+                          static_cast<cd*>(d_gL), static_cast<cd*>(d_gR), d_err, s);
+  return sweep_impl<cf>(d_tasks, n_tasks, max_W, d_wire, d_phi, d_sig, static_cast<cf*>(d_gL),
+                        static_cast<cf*>(d_gR), d_err, s);
 }
 
-cudaError_t launch_rgf_sweep(const TaskDesc* d_tasks, int n_tasks, int max_W,
-                             const double* d_wire, const cd* d_sig, cd* d_gL, cd* d_gR,
-                             int32_t* d_err, cudaStream_t s) {
-  if (n_tasks == 0) return cudaSuccess;
-  const size_t smem = sweep_smem(max_W);
-  cudaError_t e = cudaFuncSetAttribute(rgf_sweep_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  rgf_sweep_kernel<<<dim3(n_tasks, 2), kThreads, smem, s>>>(d_tasks, d_wire, d_sig, d_gL, d_gR,
-                                                            d_err);
-  return cudaGetLastError();
-}
-
-
-cudaError_t launch_block_columns(const TaskDesc* d_tasks, int n_tasks, int max_W, int max_L,
-                                 int precision, const double* d_wire, const cd* d_sig,
-                                 const double* d_gam, const cd* d_gL, const cd* d_gR,
-                                 void* d_weights, double* d_rowsum, double* d_mode_w,
-                                 double* d_c, int32_t* d_err, cudaStream_t s) {
-  if (n_tasks == 0) return cudaSuccess;
-  dim3 grid(n_tasks, max_L + 2);
-  cudaError_t e;
-  if (precision == NEGF_FP64) {
-    const size_t smem = column_smem_bytes<cd>(max_W);
-    e = cudaFuncSetAttribute(block_column_kernel<double>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    block_column_kernel<double><<<grid, kThreads, smem, s>>>(
-        d_tasks, d_wire, d_sig, d_gam, d_gL, d_gR, static_cast<double*>(d_weights), d_rowsum,
-        d_mode_w, d_c, d_err);
-  } else {
-    const size_t smem = column_smem_bytes<cf>(max_W);
-    e = cudaFuncSetAttribute(block_column_kernel<float>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    block_column_kernel<float><<<grid, kThreads, smem, s>>>(
-        d_tasks, d_wire, d_sig, d_gam, d_gL, d_gR, static_cast<float*>(d_weights), d_rowsum,
-        d_mode_w, d_c, d_err);
-  }
-  return cudaGetLastError();
+cudaError_t launch_block_columns(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols,
+                                 int max_W, int precision, const double* d_wire,
+                                 const float* d_eta32, const double* d_phi, const float* d_phi32,
+                                 const cd* d_sig, const double* d_gam, const void* d_gL,
+                                 const void* d_gR, void* d_start, void* d_weights,
+                                 double* d_rowsum, double* d_mode_w, double* d_c, int32_t* d_err,
+                                 cudaStream_t s) {
+  if (n_tasks == 0 || n_cols == 0) return cudaSuccess;
+  if (precision == NEGF_FP64)
+    return columns_impl<cd>(d_tasks, n_tasks, n_cols, max_W, d_wire, d_wire, d_phi, d_phi,
+                            d_sig, d_gam, static_cast<const cd*>(d_gL),
+                            static_cast<const cd*>(d_gR), static_cast<cd*>(d_start),
+                            static_cast<double*>(d_weights), d_rowsum, d_mode_w, d_c, d_err, s);
+  return columns_impl<cf>(d_tasks, n_tasks, n_cols, max_W, d_wire, d_eta32, d_phi, d_phi32,
+                          d_sig, d_gam, static_cast<const cf*>(d_gL),
+                          static_cast<const cf*>(d_gR), static_cast<cf*>(d_start),
+                          static_cast<float*>(d_weights), d_rowsum, d_mode_w, d_c, d_err, s);
 }
 
 }  // namespace negf

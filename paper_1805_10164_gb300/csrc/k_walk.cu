@@ -9,11 +9,12 @@
 // transition from the current row: slot c = (x*K)>>32, keep c if y < thr[c] else alias[c].
 // Columns n and n+1 are the leads: drawing one ends the walk, and the sample's estimator is
 // X_pq = Tr[Gamma_p A] delta_rq (Eq. elast_lin_xpq), tallied as counts per absorbing lead.
-// When a walk ends the lane takes the next walker from its warp's chunk of walker indices (a
-// warp claims 256 at a time from a global counter), so lanes stay busy although walk lengths
-// differ.  Each lane counts its own outcomes for its current task in registers; when lanes move
-// to another task their counts are summed per task across the warp (match + reduce) and added
-// to the block's shared tally, which is added to global memory once per block.
+// When a walk ends the lane starts the next walker of its own run of consecutive walker indices
+// (16 per lane) with no warp coordination; once enough lanes of a warp have run dry, one lane
+// claims a new range for all of them from a global counter.  The injection draw is made when a
+// walker starts, so the loop body is one Step 6' transition.  Each lane counts its outcomes for
+// its current task in registers and adds them to the block's shared tally when it moves to
+// another task; the block adds its tally to global memory once.
 #include <cuda_runtime.h>
 
 #include "negf_internal.cuh"
@@ -25,7 +26,8 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kFields = NEGF_TALLY_FIELDS;   // done, absorbed L, absorbed R, truncated, steps
 constexpr int kMaxWindow = 1024;             // tasks per launch (40 KB shared tally)
-constexpr unsigned kChunk = 256;             // walkers a warp claims from the global counter
+constexpr unsigned kRun = 16;                // consecutive walkers handed to a lane at a time
+constexpr int kClaimMin = 8;                 // dry lanes that trigger a claim
 constexpr unsigned kFlushAt = 1u << 26;      // flush a lane's counters before they can overflow
 
 // 64-bit shared counter kept as two 32-bit words (native 32-bit shared atomics).
@@ -34,24 +36,17 @@ __device__ __forceinline__ void smem_add64(unsigned* lohi, unsigned v) {
   if (old + v < old) atomicAdd(lohi + 1, 1u);
 }
 
-// Sum the lanes' counters per task over the lanes in `mask` that call this, then one lane per
-// task adds them to the block's shared tally.
-__device__ __forceinline__ void flush_group(unsigned mask, int task_local, const unsigned (&a)[kFields],
-                                            unsigned* s_tally) {
-  const unsigned grp = __match_any_sync(mask, task_local);
-  unsigned sum[kFields];
+__device__ __forceinline__ void flush_lane(unsigned* s_tally, int task_local, unsigned (&a)[kFields]) {
+  unsigned* t = s_tally + task_local * kFields * 2;
 #pragma unroll
-  for (int f = 0; f < kFields; ++f) sum[f] = __reduce_add_sync(grp, a[f]);
-  if ((threadIdx.x & 31) == __ffs(grp) - 1) {
-    unsigned* t = s_tally + task_local * kFields * 2;
-#pragma unroll
-    for (int f = 0; f < kFields; ++f)
-      if (sum[f]) smem_add64(t + 2 * f, sum[f]);
+  for (int f = 0; f < kFields; ++f) {
+    if (a[f]) smem_add64(t + 2 * f, a[f]);
+    a[f] = 0u;
   }
 }
 
 template <bool kTrace>
-__global__ void __launch_bounds__(kThreads) walk_kernel(
+__global__ void __launch_bounds__(kThreads, 5) walk_kernel(
     const TaskDesc* __restrict__ tasks, int task0, int n_tasks, const uint64_t* __restrict__ tab,
     const uint64_t* __restrict__ mode_tab, const double* __restrict__ cvals, int start_lead,
     PhiloxKey key, uint64_t walkers_per_task, uint64_t id_offset, uint32_t max_steps,
@@ -68,53 +63,28 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(
 
   // walker state (registers)
   bool has = false;
-  uint64_t g = 0;
-  int tl = 0;                      // task index within the window
-  uint32_t task_id = 0, K = 0, n = 0, W = 0, row = 0, s = 0, steps = 0, cx2 = 0, cx3 = 0;
-  uint32_t wid_lo = 0, wid_hi = 0;
+  unsigned long long g = 0;
+  uint32_t row = 0, s = 0, steps = 0, cx2 = 0, cx3 = 0, wid_lo = 0, wid_hi = 0;
+  // this lane's run of walker indices [r_next, r_end)
+  unsigned long long r_next = 0, r_end = 0;
+  // cached task: index window [t_first, t_first + walkers_per_task)
+  int tl = -1;
+  unsigned long long t_first = 0;
+  uint32_t task_id = 0, K = 0, n = 0, W = 0;
+  bool t_open = false;
   const uint64_t* trow = nullptr;
   const uint64_t* mrow = nullptr;
-  // this lane's counters for task acc_tl
-  int acc_tl = -1;
-  unsigned a[kFields] = {0u, 0u, 0u, 0u, 0u};
-  // warp's current chunk of walker indices [c_next, c_end) (warp-uniform)
-  unsigned long long c_next = 0, c_end = 0;
+  unsigned a[kFields] = {0u, 0u, 0u, 0u, 0u};    // counts of task tl not yet in shared memory
   bool no_more = false;
 
   while (true) {
-    // ---- refill idle lanes from the warp's chunk (claiming chunks as needed)
-    unsigned need = __ballot_sync(FULL, !has);
-    while (need && !no_more) {
-      if (c_next == c_end) {
-        unsigned long long base = 0;
-        if (lane == 0) base = atomicAdd(counter, (unsigned long long)kChunk);
-        base = __shfl_sync(FULL, base, 0);
-        if (base >= total) { no_more = true; break; }
-        c_next = base;
-        c_end = base + kChunk < total ? base + kChunk : total;
-      }
-      const unsigned avail = (unsigned)(c_end - c_next);
-      const unsigned rank = __popc(need & lt_mask);
-      const bool mine = ((need >> lane) & 1u) && rank < avail;
-      int new_tl = -1;
-      if (mine) {
-        g = c_next + rank;
-        new_tl = (int)(g / walkers_per_task);
-      }
-      const unsigned took = __popc(need) < avail ? __popc(need) : avail;
-      c_next += took;
-      // counters of a lane that moves to another task go to the shared tally first
-      const bool fl = mine && new_tl != acc_tl && acc_tl >= 0;
-      const unsigned fm = __ballot_sync(FULL, fl);
-      if (fl) flush_group(fm, acc_tl, a, s_tally);
-      if (mine) {
-        if (new_tl != acc_tl) {
-          acc_tl = new_tl;
-#pragma unroll
-          for (int f = 0; f < kFields; ++f) a[f] = 0u;
-        }
-        tl = new_tl;
-        const uint64_t w = id_offset + (g - (uint64_t)tl * walkers_per_task);
+    // ---- start walkers from the lane's own run (closed tasks are consumed on the spot)
+    while (!has && r_next < r_end) {
+      g = r_next++;
+      if (tl < 0 || g - t_first >= walkers_per_task) {
+        if (tl >= 0) flush_lane(s_tally, tl, a);
+        tl = (int)(g / walkers_per_task);
+        t_first = (unsigned long long)tl * walkers_per_task;
         const TaskDesc& d = tasks[task0 + tl];
         task_id = (uint32_t)(task0 + tl);
         K = (uint32_t)d.K;
@@ -122,66 +92,75 @@ __global__ void __launch_bounds__(kThreads) walk_kernel(
         W = (uint32_t)d.W;
         trow = tab + d.tab_off;
         mrow = mode_tab + d.mode_off + start_lead * d.W;
-        wid_lo = (uint32_t)w;
-        wid_hi = (uint32_t)(w >> 32);
-        s = 0;
-        steps = 0;
-        if (cvals[2 * (task0 + tl) + start_lead] > 0.0) {
-          has = true;
-        } else {
-          // no open channel in the start lead: nothing to inject (T = 0 exactly)
-          a[0] += 1u;
-          if (kTrace) { trace_lead[g] = -1; trace_steps[g] = 0; }
-        }
+        t_open = cvals[2 * (task0 + tl) + start_lead] > 0.0;
       }
-      need = __ballot_sync(FULL, !has);
+      if (!t_open) {
+        // no open channel in the start lead: nothing to inject (T = 0 exactly)
+        a[0] += 1u;
+        if (kTrace) { trace_lead[g] = -1; trace_steps[g] = 0; }
+        continue;
+      }
+      const uint64_t w = id_offset + (g - t_first);
+      wid_lo = (uint32_t)w;
+      wid_hi = (uint32_t)(w >> 32);
+      // draw 0: injection eigenvector of Gamma_p (Eq. lead_out_probability); keep (x2, x3)
+      const uint4 r = philox4x32_10(make_uint4(0u, wid_lo, wid_hi, task_id), key);
+      const uint32_t c = __umulhi(r.x, W);
+      const uint64_t e = __ldg(mrow + c);
+      const uint32_t mode = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+      row = n + (uint32_t)start_lead * W + mode;
+      cx2 = r.z;
+      cx3 = r.w;
+      s = 1;
+      steps = 0;
+      has = true;
     }
-    if (!__any_sync(FULL, has)) break;   // no walker in flight and no work left
-    if (has) {
-      uint32_t x, y;
-      if ((s & 1u) == 0u) {
-        const uint4 r = philox4x32_10(make_uint4(s >> 1, wid_lo, wid_hi, task_id), key);
-        x = r.x; y = r.y; cx2 = r.z; cx3 = r.w;
-      } else {
-        x = cx2; y = cx3;
+    // ---- claim new runs once enough lanes are dry (or none has work left)
+    const unsigned dry = __ballot_sync(FULL, !has);
+    if (dry && !no_more && (__popc(dry) >= kClaimMin || dry == FULL)) {
+      unsigned long long base = 0;
+      if (lane == 0) base = atomicAdd(counter, (unsigned long long)__popc(dry) * kRun);
+      base = __shfl_sync(FULL, base, 0);
+      if (base >= total) {
+        no_more = true;
+      } else if (!has) {
+        const unsigned long long lo = base + (unsigned long long)__popc(dry & lt_mask) * kRun;
+        r_next = lo < total ? lo : total;
+        r_end = lo + kRun < total ? lo + kRun : total;
       }
-      if (s == 0u) {
-        const uint32_t c = __umulhi(x, W);
-        const uint64_t e = __ldg(mrow + c);
-        const uint32_t mode = y < (uint32_t)e ? c : (uint32_t)(e >> 32);
-        row = n + (uint32_t)start_lead * W + mode;
-      } else {
-        const uint32_t c = __umulhi(x, K);
-        const uint64_t e = __ldg(trow + (uint64_t)row * K + c);
-        const uint32_t j = y < (uint32_t)e ? c : (uint32_t)(e >> 32);
-        ++steps;
-        int outcome = -3;
-        if (j >= n) outcome = (int)(j - n);              // absorbed at lead 0 (L) or 1 (R)
-        else if (steps >= max_steps) outcome = -2;       // cut: counted as truncated
-        else row = j;
-        if (outcome != -3) {
-          a[0] += 1u;
-          a[outcome >= 0 ? 1 + outcome : 3] += 1u;
-          a[4] += steps;
-          if (kTrace) { trace_lead[g] = outcome; trace_steps[g] = steps; }
-          has = false;
-          if (a[4] >= kFlushAt || a[0] >= kFlushAt) {
-            unsigned* t = s_tally + acc_tl * kFields * 2;
-#pragma unroll
-            for (int f = 0; f < kFields; ++f) {
-              if (a[f]) smem_add64(t + 2 * f, a[f]);
-              a[f] = 0u;
-            }
-          }
-        }
-      }
-      ++s;
+      continue;      // start the new walkers first
+    }
+    if (dry == FULL) break;           // nothing in flight and nothing left to claim
+    if (!has) continue;
+
+    // ---- one Step 6' transition from the current row
+    uint32_t x, y;
+    if ((s & 1u) == 0u) {
+      const uint4 r = philox4x32_10(make_uint4(s >> 1, wid_lo, wid_hi, task_id), key);
+      x = r.x; y = r.y; cx2 = r.z; cx3 = r.w;
+    } else {
+      x = cx2; y = cx3;
+    }
+    ++s;
+    const uint32_t c = __umulhi(x, K);
+    const uint64_t e = __ldg(trow + (uint64_t)row * K + c);
+    const uint32_t j = y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+    ++steps;
+    if (j >= n || steps >= max_steps) {
+      // absorbed at lead j - n (0 = L, 1 = R), or cut at the step cap (truncated)
+      a[0] += 1u;
+      if (j == n) a[1] += 1u;
+      else if (j == n + 1) a[2] += 1u;
+      else a[3] += 1u;
+      a[4] += steps;
+      if (kTrace) { trace_lead[g] = j >= n ? (int)(j - n) : -2; trace_steps[g] = steps; }
+      has = false;
+      if (a[4] >= kFlushAt || a[0] >= kFlushAt) flush_lane(s_tally, tl, a);
+    } else {
+      row = j;
     }
   }
-  // ---- final flush of every lane's counters, then the block's tally to global memory
-  const bool fl = acc_tl >= 0;
-  const unsigned fm = __ballot_sync(FULL, fl);
-  if (fl) flush_group(fm, acc_tl, a, s_tally);
+  if (tl >= 0) flush_lane(s_tally, tl, a);
   __syncthreads();
   for (int i = threadIdx.x; i < n_tasks * kFields; i += blockDim.x) {
     const unsigned long long v =

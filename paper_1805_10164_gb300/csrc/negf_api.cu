@@ -188,7 +188,6 @@ std::string err_bits(int32_t e) {
   if (e & negf::ERR_ROWSUM) s += " table row does not sum to <i|A|i>;";
   if (e & negf::ERR_INPUT) s += " input value outside the domain (non-finite, eta < 0 or energy on a lead band edge);";
   if (e & negf::ERR_SINGULAR) s += " singular slice block;";
-  if (e & negf::ERR_ALIAS) s += " alias construction found no heavy item;";
   return s;
 }
 
@@ -226,6 +225,14 @@ negf_status negf_create(negf_ctx* out, int device, void* stream) {
   ctx->device = device;
   ctx->stream = static_cast<cudaStream_t>(stream);
   DeviceGuard g(device);
+  // Tables and scratch come from the device's default stream-ordered pool.  Keep freed blocks
+  // in the pool across synchronisations instead of unmapping them at every sync (the default
+  // release threshold of 0 makes each build re-map hundreds of MB).
+  cudaMemPool_t pool = nullptr;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess && pool) {
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   if (cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device) !=
           cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&ctx->d_counter), sizeof(unsigned long long)) !=
@@ -301,8 +308,8 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   t->n_wires = n_wires;
   t->precision = prec;
   // ---- validate and lay out the batch
-  uint64_t tab_off = 0, g_off = 0, wire_off = 0;
-  uint32_t mode_off = 0, lead_off = 0, row_base = 0;
+  uint64_t tab_off = 0, g_off = 0, wire_off = 0, start_off = 0;
+  uint32_t mode_off = 0, lead_off = 0, row_base = 0, col_base = 0, phi_off = 0;
   t->h_wire_task0.push_back(0);
   for (int w = 0; w < n_wires; ++w) {
     const negf_wire& wr = wires[w];
@@ -322,10 +329,10 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
     }
     const int64_t n = (int64_t)wr.W * wr.L;
     const int64_t K = n + 2, rows = n + 2 * wr.W;
-    if (K > 8192) {
+    if (n > NEGF_MAX_SITES) {
       release_tables(t);
-      return fail(ctx, NEGF_E_INVALID, "wire %d: W*L = %lld exceeds the supported 8190 sites",
-                  w, (long long)n);
+      return fail(ctx, NEGF_E_INVALID, "wire %d: W*L = %lld exceeds the supported %d sites",
+                  w, (long long)n, NEGF_MAX_SITES);
     }
     if (!wr.onsite || !wr.eta || (wr.n_energy > 0 && !wr.energy)) {
       release_tables(t);
@@ -383,26 +390,37 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
       d.lead_off = lead_off;
       d.onsite_off = (uint32_t)wire_off;
       d.row_base = row_base;
+      d.col_base = col_base;
+      d.phi_off = phi_off;
+      d.start_off = start_off;
       t->h_tasks.push_back(d);
       tab_off += (uint64_t)rows * K;
       g_off += (uint64_t)wr.L * wr.W * wr.W;
       mode_off += 2 * wr.W;
       lead_off += wr.W;
       row_base += (uint32_t)(rows + 2);
+      col_base += (uint32_t)(wr.L + 2);
+      start_off += (uint64_t)(wr.L + 2) * wr.W * wr.W;
       t->max_W = std::max(t->max_W, wr.W);
       t->max_L = std::max(t->max_L, wr.L);
       t->max_K = std::max(t->max_K, (int)K);
     }
     wire_off += 2 * (uint64_t)n;
+    phi_off += (uint32_t)(wr.W * wr.W);
     t->h_wire_task0.push_back((int32_t)t->h_tasks.size());
   }
   t->n_tasks = (int)t->h_tasks.size();
   t->total_jobs = row_base;
   const int nt = t->n_tasks;
   // ---- device buffers
-  cd* d_gL = nullptr;
-  cd* d_gR = nullptr;
+  // RGF and start blocks in the table precision: complex128 (FP64) or complex64 (FP32)
+  double* d_gL = nullptr;
+  double* d_gR = nullptr;
+  double* d_start = nullptr;
+  double* d_phi = nullptr;       // per wire: transverse modes (FP64), then the FP32 copy
+  float* d_eta32 = nullptr;      // per wire: eta in FP32
   void* d_weights = nullptr;
+  const uint64_t cw = negf::block_bytes(prec) / sizeof(double);   // doubles per complex
   const size_t wsz = prec == NEGF_FP64 ? sizeof(double) : sizeof(float);
 #define ALLOC(ptr, count)                                                  \
   do {                                                                     \
@@ -411,6 +429,9 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
       release_tables(t);                                                   \
       dfree(d_gL, s);                                                      \
       dfree(d_gR, s);                                                      \
+      dfree(d_start, s);                                                   \
+      dfree(d_phi, s);                                                     \
+      dfree(d_eta32, s);                                                   \
       if (d_weights) cudaFreeAsync(d_weights, s);                          \
       return fail(ctx, e_ == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA, \
                   "allocation of %s (%zu elements): %s", #ptr, (size_t)(count), \
@@ -428,14 +449,20 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   ALLOC(t->d_c, 2 * (size_t)nt);
   ALLOC(t->d_rowsum, row_base);
   ALLOC(t->d_err, 1);
-  ALLOC(d_gL, g_off);
-  ALLOC(d_gR, g_off);
+  ALLOC(d_gL, g_off * cw);
+  ALLOC(d_gR, g_off * cw);
+  ALLOC(d_start, start_off * cw);
+  ALLOC(d_phi, (uint64_t)phi_off + (phi_off + 1) / 2);
+  ALLOC(d_eta32, wire_off / 2);
   {
     cudaError_t e_ = cudaMallocAsync(&d_weights, std::max<uint64_t>(tab_off, 1) * wsz, s);
     if (e_ != cudaSuccess) {
       release_tables(t);
       dfree(d_gL, s);
       dfree(d_gR, s);
+      dfree(d_start, s);
+      dfree(d_phi, s);
+      dfree(d_eta32, s);
       return fail(ctx, e_ == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,
                   "allocation of the weight scratch: %s", cudaGetErrorString(e_));
     }
@@ -446,6 +473,9 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
     release_tables(t);
     dfree(d_gL, s);
     dfree(d_gR, s);
+    dfree(d_start, s);
+    dfree(d_phi, s);
+    dfree(d_eta32, s);
     if (d_weights) cudaFreeAsync(d_weights, s);
     return st;
   };
@@ -492,18 +522,21 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
     }
     {
       ProfScope ps(ctx, "lead_modes_kernel");
-      STEP(negf::launch_lead_modes(t->d_tasks, nt, t->max_W, t->d_sig, t->d_gam, t->d_err, s));
+      STEP(negf::launch_lead_modes(t->d_tasks, nt, t->max_W, t->d_wire, d_phi,
+                                   reinterpret_cast<float*>(d_phi + phi_off), d_eta32, t->d_sig,
+                                   t->d_gam, t->d_err, s));
     }
     {
       ProfScope ps(ctx, "rgf_sweep_kernel");
-      STEP(negf::launch_rgf_sweep(t->d_tasks, nt, t->max_W, t->d_wire, t->d_sig, d_gL, d_gR,
-                                  t->d_err, s));
+      STEP(negf::launch_rgf_sweep(t->d_tasks, nt, t->max_W, prec, t->d_wire, d_phi, t->d_sig,
+                                  d_gL, d_gR, t->d_err, s));
     }
     {
-      ProfScope ps(ctx, "block_column_kernel");
-      STEP(negf::launch_block_columns(t->d_tasks, nt, t->max_W, t->max_L, prec, t->d_wire,
-                                      t->d_sig, t->d_gam, d_gL, d_gR, d_weights, t->d_rowsum,
-                                      t->d_mode_w, t->d_c, t->d_err, s));
+      ProfScope ps(ctx, "diag_chain_kernels", 2);
+      STEP(negf::launch_block_columns(t->d_tasks, nt, col_base, t->max_W, prec, t->d_wire,
+                                      d_eta32, d_phi, reinterpret_cast<float*>(d_phi + phi_off),
+                                      t->d_sig, t->d_gam, d_gL, d_gR, d_start, d_weights,
+                                      t->d_rowsum, t->d_mode_w, t->d_c, t->d_err, s));
     }
     {
       ProfScope ps(ctx, "alias_kernel");
@@ -515,7 +548,12 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
 #undef STEP
   dfree(d_gL, s);
   dfree(d_gR, s);
-  t->bytes -= 2 * g_off * sizeof(cd);
+  dfree(d_start, s);
+  dfree(d_phi, s);
+  dfree(d_eta32, s);
+  t->bytes -= (2 * std::max<uint64_t>(g_off * cw, 1) + std::max<uint64_t>(start_off * cw, 1) +
+               std::max<uint64_t>((uint64_t)phi_off + (phi_off + 1) / 2, 1)) * sizeof(double) +
+              std::max<uint64_t>(wire_off / 2, 1) * sizeof(float);
   if (o.keep_weights) {
     t->d_weights = d_weights;
     t->bytes += std::max<uint64_t>(tab_off, 1) * wsz;

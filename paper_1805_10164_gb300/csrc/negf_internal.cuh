@@ -13,8 +13,7 @@ enum : int32_t {
   ERR_NONFINITE = 1,      // a Green's function block or weight is not finite
   ERR_ROWSUM = 2,         // a table row sums to <= 0 where the site is coupled
   ERR_INPUT = 4,          // device-resident input failed validation
-  ERR_SINGULAR = 8,       // zero pivot in a block inversion
-  ERR_ALIAS = 16          // alias construction inconsistent (no heavy item)
+  ERR_SINGULAR = 8        // zero pivot in a block inversion
 };
 
 // One (wire, energy) task.  Offsets are in elements of the array they index.
@@ -24,11 +23,14 @@ struct TaskDesc {
   double E, t, w_E, gamma_lead;
   uint64_t tab_off;      // alias entries [rows][K]
   uint64_t wt_off;       // weights [rows][K] (float or double)
-  uint64_t g_off;        // RGF blocks [L][W][W] complex (FP64) for gL and gR
+  uint64_t g_off;        // RGF blocks [L][W][W] complex for gL and gR
   uint32_t mode_off;     // mode alias / weights [2][W]
   uint32_t lead_off;     // lead eigen self-energies [W] complex and Gamma [W] double
   uint32_t onsite_off;   // into the wire data array: onsite [L*W], eta follows at +n
   uint32_t row_base;     // first global row-job index of this task (alias build)
+  uint32_t col_base;     // first block-column job of this task (L + 2 per task)
+  uint32_t phi_off;      // transverse modes phi[a][m] of this wire's width (W x W)
+  uint64_t start_off;    // start blocks [L + 2][W][W] complex
 };
 
 struct cd { double x, y; };
@@ -46,6 +48,7 @@ __host__ __device__ inline cf operator*(cf a, cf b) {
   return cf{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }
 __host__ __device__ inline cf operator*(float s, cf a) { return cf{s * a.x, s * a.y}; }
+__host__ __device__ inline cf operator-(cf a, cf b) { return cf{a.x - b.x, a.y - b.y}; }
 __host__ __device__ inline double norm2(cd a) { return a.x * a.x + a.y * a.y; }
 __host__ __device__ inline float norm2(cf a) { return a.x * a.x + a.y * a.y; }
 // complex division a / b by multiplication with conj(b) / |b|^2
@@ -53,23 +56,40 @@ __host__ __device__ inline cd cdiv(cd a, cd b) {
   double d = b.x * b.x + b.y * b.y;
   return cd{(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
 }
+__host__ __device__ inline cf cdiv(cf a, cf b) {
+  float d = b.x * b.x + b.y * b.y;
+  return cf{(a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d};
+}
 
 // Launchers (each returns the cudaError_t of its launch).
-cudaError_t launch_lead_modes(const TaskDesc* d_tasks, int n_tasks, int max_W, cd* d_sig,
-                              double* d_gam, int32_t* d_err, cudaStream_t s);
-cudaError_t launch_rgf_sweep(const TaskDesc* d_tasks, int n_tasks, int max_W,
-                             const double* d_wire, const cd* d_sig, cd* d_gL, cd* d_gR,
-                             int32_t* d_err, cudaStream_t s);
-cudaError_t launch_block_columns(const TaskDesc* d_tasks, int n_tasks, int max_W, int max_L,
-                                 int precision, const double* d_wire, const cd* d_sig,
-                                 const double* d_gam, const cd* d_gL, const cd* d_gR,
-                                 void* d_weights, double* d_rowsum, double* d_mode_w,
-                                 double* d_c, int32_t* d_err, cudaStream_t s);
+// Per wire: transverse modes phi (FP64 and FP32 copies, [W][W] at phi_off) and an FP32 copy of
+// eta ([n] at onsite_off / 2); per task: lead eigen self-energies.
+cudaError_t launch_lead_modes(const TaskDesc* d_tasks, int n_tasks, int max_W,
+                              const double* d_wire, double* d_phi, float* d_phi32,
+                              float* d_eta32, cd* d_sig, double* d_gam, int32_t* d_err,
+                              cudaStream_t s);
+// RGF blocks, start blocks: complex128 [..] for NEGF_FP64, complex64 for NEGF_FP32 (the lead
+// self-energies stay FP64 in both).  block_bytes() gives the element size.
+inline size_t block_bytes(int precision) { return precision == NEGF_FP64 ? 16 : 8; }
+cudaError_t launch_rgf_sweep(const TaskDesc* d_tasks, int n_tasks, int max_W, int precision,
+                             const double* d_wire, const double* d_phi, const cd* d_sig,
+                             void* d_gL, void* d_gR, int32_t* d_err, cudaStream_t s);
+// Diagonal blocks (start blocks, A per row, mode weights, c_p) then the block-column chains
+// emitting the weights.  n_cols = sum over tasks of L + 2.  On return rowsum holds A of every
+// table row and c_p in the two mode-row slots; the alias build replaces them by the row sums.
+cudaError_t launch_block_columns(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols,
+                                 int max_W, int precision, const double* d_wire,
+                                 const float* d_eta32, const double* d_phi, const float* d_phi32,
+                                 const cd* d_sig, const double* d_gam, const void* d_gL,
+                                 const void* d_gR, void* d_start, void* d_weights,
+                                 double* d_rowsum, double* d_mode_w, double* d_c, int32_t* d_err,
+                                 cudaStream_t s);
+// Alias tables of every row (and mode row); replaces the A values in rowsum by the FP64 row
+// sums after checking them.
 cudaError_t launch_alias_build(const TaskDesc* d_tasks, int n_tasks, uint32_t total_jobs,
                                int max_K, int precision, const void* d_weights,
-                               const double* d_rowsum, const double* d_mode_w,
-                               uint64_t* d_tab, uint64_t* d_mode_tab, int32_t* d_err,
-                               cudaStream_t s);
+                               double* d_rowsum, const double* d_mode_w, uint64_t* d_tab,
+                               uint64_t* d_mode_tab, int32_t* d_err, cudaStream_t s);
 // d_tally holds the counters of tasks task0 .. task0 + n_tasks - 1 (index 0 = task0).
 cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, const uint64_t* d_tab,
                         const uint64_t* d_mode_tab, const double* d_c, int start_lead,

@@ -56,7 +56,7 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
   if (wr.lead_model == NEGF_LEAD_WIDE_BAND && !(wr.gamma_lead > 0.0 && isfinite(wr.gamma_lead)))
     return NEGF_E_INVALID;
   const int64_t n = (int64_t)wr.W * wr.L, K = n + 2, rows = n + 2 * wr.W;
-  if (K > 8192) return NEGF_E_INVALID;
+  if (n > NEGF_MAX_SITES) return NEGF_E_INVALID;
   for (int64_t i = 0; i < n; ++i)
     if (!isfinite(wr.onsite[i]) || !isfinite(wr.eta[i]) || !(wr.eta[i] >= 0.0)) return NEGF_E_INVALID;
   const int nt = wr.n_energy;
@@ -73,8 +73,13 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
   const size_t o_wire = off;   off += align256(sizeof(double) * 2 * n);
   const size_t o_sig = off;    off += align256(sizeof(cd) * nt * wr.W);
   const size_t o_gam = off;    off += align256(sizeof(double) * nt * wr.W);
-  const size_t o_gL = off;     off += align256(sizeof(cd) * nt * (size_t)wr.L * wr.W * wr.W);
-  const size_t o_gR = off;     off += align256(sizeof(cd) * nt * (size_t)wr.L * wr.W * wr.W);
+  const size_t cb = negf::block_bytes(prec);      // bytes per complex block element
+  const size_t o_gL = off;     off += align256(cb * nt * (size_t)wr.L * wr.W * wr.W);
+  const size_t o_gR = off;     off += align256(cb * nt * (size_t)wr.L * wr.W * wr.W);
+  const size_t o_st = off;     off += align256(cb * nt * (size_t)(wr.L + 2) * wr.W * wr.W);
+  const size_t o_phi = off;    off += align256(sizeof(double) * wr.W * wr.W);
+  const size_t o_phi32 = off;  off += align256(sizeof(float) * wr.W * wr.W);
+  const size_t o_eta32 = off;  off += align256(sizeof(float) * n);
   const size_t o_w = off;      off += align256(wsz * nt * per_task_tab);
   const size_t o_rs = off;     off += align256(sizeof(double) * nt * (rows + 2));
   const size_t o_mw = off;     off += align256(sizeof(double) * nt * 2 * wr.W);
@@ -115,34 +120,44 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
     d.lead_off = (uint32_t)(wr.W * k);
     d.onsite_off = 0;
     d.row_base = (uint32_t)(k * (rows + 2));
+    d.col_base = (uint32_t)(k * (wr.L + 2));
+    d.phi_off = 0;
+    d.start_off = (uint64_t)k * (wr.L + 2) * wr.W * wr.W;
   }
   TaskDesc* d_tasks = reinterpret_cast<TaskDesc*>(base + o_tasks);
   double* d_wire = reinterpret_cast<double*>(base + o_wire);
   cd* d_sig = reinterpret_cast<cd*>(base + o_sig);
   double* d_gam = reinterpret_cast<double*>(base + o_gam);
-  cd* d_gL = reinterpret_cast<cd*>(base + o_gL);
-  cd* d_gR = reinterpret_cast<cd*>(base + o_gR);
+  void* d_gL = base + o_gL;
+  void* d_gR = base + o_gR;
+  void* d_st = base + o_st;
+  double* d_phi = reinterpret_cast<double*>(base + o_phi);
+  float* d_phi32 = reinterpret_cast<float*>(base + o_phi32);
+  float* d_eta32 = reinterpret_cast<float*>(base + o_eta32);
   void* d_w = base + o_w;
   double* d_rs = reinterpret_cast<double*>(base + o_rs);
   double* d_mw = reinterpret_cast<double*>(base + o_mw);
   int32_t* d_err = reinterpret_cast<int32_t*>(base + o_err);
 
-  // the array keeps the previous call's contents: the error word and the accumulated row sums
-  // must start at zero
+  // the array keeps the previous call's contents: the error word must start at zero (every
+  // other scratch value is written before it is read)
   cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int32_t), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_rs, 0, sizeof(double) * nt * (rows + 2), s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_tasks, h_tasks, sizeof(TaskDesc) * nt, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_wire, wr.onsite, sizeof(double) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_wire + n, wr.eta, sizeof(double) * n, cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = negf::launch_lead_modes(d_tasks, nt, wr.W, d_sig, d_gam, d_err, s);
   if (e == cudaSuccess)
-    e = negf::launch_rgf_sweep(d_tasks, nt, wr.W, d_wire, d_sig, d_gL, d_gR, d_err, s);
+    e = negf::launch_lead_modes(d_tasks, nt, wr.W, d_wire, d_phi, d_phi32, d_eta32, d_sig, d_gam,
+                                d_err, s);
   if (e == cudaSuccess)
-    e = negf::launch_block_columns(d_tasks, nt, wr.W, wr.L, prec, d_wire, d_sig, d_gam, d_gL,
-                                   d_gR, d_w, d_rs, d_mw, d_c, d_err, s);
+    e = negf::launch_rgf_sweep(d_tasks, nt, wr.W, prec, d_wire, d_phi, d_sig, d_gL, d_gR, d_err,
+                               s);
+  if (e == cudaSuccess)
+    e = negf::launch_block_columns(d_tasks, nt, (uint32_t)(nt * (wr.L + 2)), wr.W, prec, d_wire,
+                                   d_eta32, d_phi, d_phi32, d_sig, d_gam, d_gL, d_gR, d_st, d_w,
+                                   d_rs, d_mw, d_c, d_err, s);
   if (e == cudaSuccess)
     e = negf::launch_alias_build(d_tasks, nt, (uint32_t)(nt * (rows + 2)), (int)K, prec, d_w,
                                  d_rs, d_mw, d_alias, d_mode_alias, d_err, s);

@@ -65,7 +65,7 @@ def test_noalloc_rejects_oversized_problems():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     stream = torch.cuda.current_stream()
-    big = inputs.small_wire(63, W=40, L=210, n_energy=1)          # W*L + 2 > 8192 sites limit
+    big = inputs.small_wire(63, W=40, L=170, n_energy=1)          # W*L > 6400 sites limit
     buf = torch.zeros(8, dtype=torch.int64, device="cuda")
     c = torch.zeros(2, dtype=torch.float64, device="cuda")
     assert negf.negf_build_tables_noalloc(big, "fp32", stream, buf, buf, c) == negf.NEGF_E_INVALID
