@@ -222,6 +222,140 @@ __global__ void rgf_sweep_kernel(const TaskDesc* __restrict__ tasks, int n_tasks
   }
 }
 
+// ---- register-resident variants for complex64 blocks with W <= MAXW <= 16 -----------------
+// Lane j < W holds column j of the slice matrix and lane W + j column j of the identity (then
+// of the inverse), MAXW rows each in registers; Gauss-Jordan with partial pivoting runs with
+// shuffles only (no shared memory on the sequential sweep).
+
+// Gauss-Jordan on the register-held augmented matrix (rows i < W are live).  Returns false
+// uniformly on a zero or non-finite pivot.
+template <int MAXW>
+__device__ bool gj_reg(cf (&a)[MAXW], int W) {
+  const unsigned FULL = 0xffffffffu;
+  for (int k = 0; k < W; ++k) {
+    float best = -1.f;
+    int p = k;
+#pragma unroll
+    for (int i = 0; i < MAXW; ++i) {
+      if (i >= k && i < W) {
+        const float v = norm2(a[i]);
+        if (v > best) { best = v; p = i; }
+      }
+    }
+    p = __shfl_sync(FULL, p, k);
+    best = __shfl_sync(FULL, best, k);
+    if (!(best > 0.f) || !isfinite(best)) return false;
+    if (p != k) {
+      cf vk = a[0], vp = a[0];
+#pragma unroll
+      for (int i = 0; i < MAXW; ++i) {
+        if (i == k) vk = a[i];
+        if (i == p) vp = a[i];
+      }
+#pragma unroll
+      for (int i = 0; i < MAXW; ++i) {
+        if (i == k) a[i] = vp;
+        if (i == p) a[i] = vk;
+      }
+    }
+    cf f[MAXW];
+#pragma unroll
+    for (int i = 0; i < MAXW; ++i) {
+      f[i].x = __shfl_sync(FULL, a[i].x, k);
+      f[i].y = __shfl_sync(FULL, a[i].y, k);
+    }
+    cf piv = f[0], pk = a[0];
+#pragma unroll
+    for (int i = 0; i < MAXW; ++i) {
+      if (i == k) { piv = f[i]; pk = a[i]; }
+    }
+    pk = pk * cdiv(cf{1.f, 0.f}, piv);
+#pragma unroll
+    for (int i = 0; i < MAXW; ++i) {
+      if (i == k) a[i] = pk;
+      else if (i < W) a[i] = a[i] - f[i] * pk;
+    }
+  }
+  return true;
+}
+
+// Column j (lane j < W) of E - H_kk - Sigma_s(k) - x, where x is given as this lane's column;
+// lanes W <= j < 2W get identity columns, other lanes zeros.
+template <int MAXW>
+__device__ void build_col(cf (&a)[MAXW], int W, double E, double t, double onsite_j,
+                          double eta_j, const cf (&x)[MAXW]) {
+  const int j = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < MAXW; ++i) {
+    cf v{0.f, 0.f};
+    if (j < W && i < W) {
+      if (i == j) v = cf{(float)(E - onsite_j), (float)(0.5 * eta_j)};
+      if (i - j == 1 || j - i == 1) v.x += (float)t;
+      v = v - x[i];
+    } else if (j >= W && j < 2 * W) {
+      v = cf{i == j - W ? 1.f : 0.f, 0.f};
+    }
+    a[i] = v;
+  }
+}
+
+// column j of the lead block Phi diag(sig) Phi^T (lanes j < W)
+template <int MAXW>
+__device__ void lead_col(const double* phi, const cd* sig, int W, cf (&x)[MAXW]) {
+  const int j = threadIdx.x & 31;
+#pragma unroll
+  for (int i = 0; i < MAXW; ++i) {
+    cd acc = mk(0.0, 0.0);
+    if (i < W && j < W)
+      for (int m = 0; m < W; ++m) acc = acc + (phi[i * W + m] * phi[j * W + m]) * sig[m];
+    x[i] = cf{(float)acc.x, (float)acc.y};
+  }
+}
+
+template <int MAXW>
+__global__ void rgf_sweep_reg_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
+                                     const double* __restrict__ wire,
+                                     const double* __restrict__ phig, const cd* __restrict__ sig,
+                                     cf* gL, cf* gR, int32_t* err) {
+  const int job = blockIdx.x;
+  if (job >= 2 * n_tasks) return;
+  const TaskDesc d = tasks[job >> 1];
+  const int dir = job & 1;
+  const int W = d.W, L = d.L;
+  const int lane = threadIdx.x & 31;
+  if (L < 2) return;
+  const double* onsite = wire + d.onsite_off;
+  const double* eta = onsite + d.n;
+  const double tt = d.t * d.t;
+  cf x[MAXW], a[MAXW];
+  lead_col<MAXW>(phig + d.phi_off, sig + d.lead_off, W, x);
+  cf* out = dir == 0 ? gL : gR;
+  const int jc = lane < W ? lane : 0;
+  for (int s = 0; s < L - 1; ++s) {
+    const int k = dir == 0 ? s : L - 1 - s;
+    build_col<MAXW>(a, W, d.E, d.t, onsite[k * W + jc], eta[k * W + jc], x);
+    if (!gj_reg<MAXW>(a, W)) {
+      if (lane == 0) atomicOr(err, ERR_SINGULAR);
+      return;
+    }
+    // lanes W..2W-1 hold the columns of g_k; store them and hand column j to lane j as t^2 g_k
+    cf* dst = out + d.g_off + (uint64_t)k * W * W;
+    bool bad = false;
+    const int src = W + (lane < W ? lane : 0);
+#pragma unroll
+    for (int i = 0; i < MAXW; ++i) {
+      if (lane >= W && lane < 2 * W && i < W) {
+        dst[i * W + (lane - W)] = a[i];
+        bad |= !finite_c(a[i]);
+      }
+      const float gx = __shfl_sync(0xffffffffu, a[i].x, src);
+      const float gy = __shfl_sync(0xffffffffu, a[i].y, src);
+      x[i] = cf{(float)(tt * gx), (float)(tt * gy)};
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
+  }
+}
+
 // last task whose first job index (`first(t)`) is <= job
 template <typename F>
 __device__ __forceinline__ int find_task(int n_tasks, uint32_t job, F first) {
@@ -317,6 +451,113 @@ __global__ void diag_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, uin
   if (inj && lane == 0) {
     double c = 0.0;
     for (int b = 0; b < W; ++b) c += mw_s[b];      // fixed order
+    cvals[task * 2 + p] = c;
+    rowsum[d.row_base + d.rows + p] = c;
+  }
+}
+
+// Register-resident diagonal-block kernel (complex64, W <= MAXW <= 16); same outputs as
+// diag_kernel.  Shared memory per warp: G (W x W complex64) and phi (W x W double).
+template <int MAXW>
+__global__ void diag_reg_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
+                                const double* __restrict__ wire, const double* __restrict__ phig,
+                                const cd* __restrict__ sig, const double* __restrict__ gam,
+                                const cf* __restrict__ gL, const cf* __restrict__ gR,
+                                cf* __restrict__ start, double* __restrict__ rowsum,
+                                double* __restrict__ mode_w, double* __restrict__ cvals,
+                                int32_t* err) {
+  __shared__ cf s_G[8][MAXW * MAXW];
+  __shared__ double s_phi[8][MAXW * MAXW];
+  __shared__ double s_mw[8][MAXW];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t job = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (job >= n_jobs) return;
+  const int task = find_task(n_tasks, job, [&](int t) { return tasks[t].col_base; });
+  const TaskDesc d = tasks[task];
+  const int W = d.W, L = d.L, n = d.n;
+  const int y = (int)(job - d.col_base);
+  const bool inj = y >= L;
+  const int p = y - L;
+  const int m0 = inj ? (p == 0 ? 0 : L - 1) : y;
+  const double* onsite = wire + d.onsite_off;
+  const double* eta = onsite + n;
+  const double tt = d.t * d.t;
+  cf* sG = s_G[warp];
+  double* phi = s_phi[warp];
+  for (int idx = lane; idx < W * W; idx += 32) phi[idx] = phig[d.phi_off + idx];
+  // this lane's column of left + right (lead block or t^2 g)
+  cf x[MAXW], a[MAXW];
+  const bool lead_l = m0 == 0, lead_r = m0 == L - 1;
+  if (lead_l || lead_r) {
+    lead_col<MAXW>(phig + d.phi_off, sig + d.lead_off, W, x);
+    if (lead_l && lead_r) {
+#pragma unroll
+      for (int i = 0; i < MAXW; ++i) x[i] = 2.f * x[i];
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < MAXW; ++i) x[i] = cf{0.f, 0.f};
+  }
+  const int jc = lane < W ? lane : 0;
+  const cf* gl = lead_l ? nullptr : gL + d.g_off + (uint64_t)(m0 - 1) * W * W;
+  const cf* gr = lead_r ? nullptr : gR + d.g_off + (uint64_t)(m0 + 1) * W * W;
+#pragma unroll
+  for (int i = 0; i < MAXW; ++i) {
+    if (i < W && lane < W) {
+      if (gl) x[i] = x[i] + (float)tt * gl[i * W + jc];
+      if (gr) x[i] = x[i] + (float)tt * gr[i * W + jc];
+    }
+  }
+  build_col<MAXW>(a, W, d.E, d.t, onsite[m0 * W + jc], eta[m0 * W + jc], x);
+  if (!gj_reg<MAXW>(a, W)) {
+    if (lane == 0) atomicOr(err, ERR_SINGULAR);
+    return;
+  }
+  bool bad = false;
+#pragma unroll
+  for (int i = 0; i < MAXW; ++i) {
+    if (lane >= W && lane < 2 * W && i < W) {
+      sG[i * W + (lane - W)] = a[i];
+      bad |= !finite_c(a[i]);
+    }
+  }
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
+  __syncwarp();
+  // start block: G_mm, or G_mm Phi for the injection columns
+  cf* dst = start + d.start_off + (uint64_t)y * W * W;
+  for (int idx = lane; idx < W * W; idx += 32) {
+    cf v;
+    if (!inj) {
+      v = sG[idx];
+    } else {
+      const int r = idx / W, b = idx % W;
+      v = cf{0.f, 0.f};
+      for (int c = 0; c < W; ++c) v = v + (float)phi[c * W + b] * sG[r * W + c];
+    }
+    dst[idx] = v;
+  }
+  // A per row: site b: -2 Im G_bb;  mode mu: -2 sum_{a,c} phi_mu(a) phi_mu(c) Im G_ac
+  for (int b = lane; b < W; b += 32) {
+    if (!inj) {
+      rowsum[d.row_base + m0 * W + b] = -2.0 * (double)sG[b * W + b].y;
+    } else {
+      double im = 0.0;
+      for (int r = 0; r < W; ++r) {
+        double row_im = 0.0;
+        for (int c = 0; c < W; ++c) row_im += phi[c * W + b] * (double)sG[r * W + c].y;
+        im += phi[r * W + b] * row_im;
+      }
+      const double A = -2.0 * im;
+      rowsum[d.row_base + n + p * W + b] = A;
+      const double mw = gam[d.lead_off + b] * A;
+      mode_w[d.mode_off + p * W + b] = mw;
+      s_mw[warp][b] = mw;
+    }
+  }
+  __syncwarp();
+  if (inj && lane == 0) {
+    double c = 0.0;
+    for (int b = 0; b < W; ++b) c += s_mw[warp][b];      // fixed order
     cvals[task * 2 + p] = c;
     rowsum[d.row_base + d.rows + p] = c;
   }
@@ -421,6 +662,16 @@ int warps_for(size_t per_warp, int max_warps) {
 template <typename C>
 cudaError_t sweep_impl(const TaskDesc* d_tasks, int n_tasks, int max_W, const double* d_wire,
                        const double* d_phi, const cd* d_sig, C* d_gL, C* d_gR, int32_t* d_err,
+                       cudaStream_t s);
+
+template <>
+cudaError_t sweep_impl<cf>(const TaskDesc* d_tasks, int n_tasks, int max_W,
+                           const double* d_wire, const double* d_phi, const cd* d_sig, cf* d_gL,
+                           cf* d_gR, int32_t* d_err, cudaStream_t s);
+
+template <typename C>
+cudaError_t sweep_smem(const TaskDesc* d_tasks, int n_tasks, int max_W, const double* d_wire,
+                       const double* d_phi, const cd* d_sig, C* d_gL, C* d_gR, int32_t* d_err,
                        cudaStream_t s) {
   // one warp per CTA: each sweep is a serial chain, best spread one per SM
   const size_t smem = inv_warp_bytes<C>(max_W);
@@ -432,6 +683,30 @@ cudaError_t sweep_impl(const TaskDesc* d_tasks, int n_tasks, int max_W, const do
   return cudaGetLastError();
 }
 
+template <>
+cudaError_t sweep_impl<cd>(const TaskDesc* d_tasks, int n_tasks, int max_W,
+                           const double* d_wire, const double* d_phi, const cd* d_sig, cd* d_gL,
+                           cd* d_gR, int32_t* d_err, cudaStream_t s) {
+  return sweep_smem<cd>(d_tasks, n_tasks, max_W, d_wire, d_phi, d_sig, d_gL, d_gR, d_err, s);
+}
+
+template <>
+cudaError_t sweep_impl<cf>(const TaskDesc* d_tasks, int n_tasks, int max_W,
+                           const double* d_wire, const double* d_phi, const cd* d_sig, cf* d_gL,
+                           cf* d_gR, int32_t* d_err, cudaStream_t s) {
+  if (max_W <= 8) {
+    rgf_sweep_reg_kernel<8><<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig,
+                                                       d_gL, d_gR, d_err);
+    return cudaGetLastError();
+  }
+  if (max_W <= 16) {
+    rgf_sweep_reg_kernel<16><<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig,
+                                                        d_gL, d_gR, d_err);
+    return cudaGetLastError();
+  }
+  return sweep_smem<cf>(d_tasks, n_tasks, max_W, d_wire, d_phi, d_sig, d_gL, d_gR, d_err, s);
+}
+
 template <typename C>
 cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, int max_W,
                          const double* d_wire, const typename Real<C>::T* d_eta,
@@ -439,7 +714,24 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
                          const double* d_gam, const C* d_gL, const C* d_gR, C* d_start,
                          typename Real<C>::T* d_w, double* d_rowsum, double* d_mode_w,
                          double* d_c, int32_t* d_err, cudaStream_t s) {
-  {
+  if (sizeof(C) == sizeof(cf) && max_W <= 16) {
+    // register-resident diagonal blocks, 4 warps per block
+    const int warps = 4;
+    const unsigned blocks = (n_cols + warps - 1) / warps;
+    const cf* gl = reinterpret_cast<const cf*>(d_gL);
+    const cf* gr = reinterpret_cast<const cf*>(d_gR);
+    cf* st = reinterpret_cast<cf*>(d_start);
+    if (max_W <= 8)
+      diag_reg_kernel<8><<<blocks, 32 * warps, 0, s>>>(d_tasks, n_tasks, n_cols, d_wire, d_phi,
+                                                       d_sig, d_gam, gl, gr, st, d_rowsum,
+                                                       d_mode_w, d_c, d_err);
+    else
+      diag_reg_kernel<16><<<blocks, 32 * warps, 0, s>>>(d_tasks, n_tasks, n_cols, d_wire, d_phi,
+                                                        d_sig, d_gam, gl, gr, st, d_rowsum,
+                                                        d_mode_w, d_c, d_err);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  } else {
     const size_t per = inv_warp_bytes<C>(max_W);
     const int warps = warps_for(per, 4);
     const size_t smem = per * warps;

@@ -11,8 +11,9 @@
 // X_pq = Tr[Gamma_p A] delta_rq (Eq. elast_lin_xpq), tallied as counts per absorbing lead.
 // When a walk ends the lane starts the next walker of its own run of consecutive walker indices
 // (16 per lane) with no warp coordination; once enough lanes of a warp have run dry, one lane
-// claims a new range for all of them from a global counter.  The injection draw is made when a
-// walker starts, so the loop body is one Step 6' transition.  Each lane counts its outcomes for
+// claims a new range for all of them from a global counter.  Every loop iteration consumes one
+// whole Philox block (two draws: the injection and the first transition for a new walker, two
+// transitions afterwards), so the generator runs warp-uniformly.  Each lane counts its outcomes for
 // its current task in registers and adds them to the block's shared tally when it moves to
 // another task; the block adds its tally to global memory once.
 #include <cuda_runtime.h>
@@ -61,16 +62,16 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
   const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned long long total = (unsigned long long)n_tasks * walkers_per_task;
 
-  // walker state (registers)
+  // walker state (registers): b = next Philox block (draws 2b, 2b + 1)
   bool has = false;
   unsigned long long g = 0;
-  uint32_t row = 0, s = 0, steps = 0, cx2 = 0, cx3 = 0, wid_lo = 0, wid_hi = 0;
+  uint32_t row = 0, b = 0, steps = 0, wid_lo = 0, wid_hi = 0;
   // this lane's run of walker indices [r_next, r_end)
   unsigned long long r_next = 0, r_end = 0;
   // cached task: index window [t_first, t_first + walkers_per_task)
   int tl = -1;
   unsigned long long t_first = 0;
-  uint32_t task_id = 0, K = 0, n = 0, W = 0;
+  uint32_t task_id = 0, K = 0, n = 0, W = 0, inj_row0 = 0;
   bool t_open = false;
   const uint64_t* trow = nullptr;
   const uint64_t* mrow = nullptr;
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
         K = (uint32_t)d.K;
         n = (uint32_t)d.n;
         W = (uint32_t)d.W;
+        inj_row0 = (uint32_t)(d.n + start_lead * d.W);
         trow = tab + d.tab_off;
         mrow = mode_tab + d.mode_off + start_lead * d.W;
         t_open = cvals[2 * (task0 + tl) + start_lead] > 0.0;
@@ -103,15 +105,7 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
       const uint64_t w = id_offset + (g - t_first);
       wid_lo = (uint32_t)w;
       wid_hi = (uint32_t)(w >> 32);
-      // draw 0: injection eigenvector of Gamma_p (Eq. lead_out_probability); keep (x2, x3)
-      const uint4 r = philox4x32_10(make_uint4(0u, wid_lo, wid_hi, task_id), key);
-      const uint32_t c = __umulhi(r.x, W);
-      const uint64_t e = __ldg(mrow + c);
-      const uint32_t mode = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
-      row = n + (uint32_t)start_lead * W + mode;
-      cx2 = r.z;
-      cx3 = r.w;
-      s = 1;
+      b = 0;
       steps = 0;
       has = true;
     }
@@ -133,31 +127,42 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
     if (dry == FULL) break;           // nothing in flight and nothing left to claim
     if (!has) continue;
 
-    // ---- one Step 6' transition from the current row
-    uint32_t x, y;
-    if ((s & 1u) == 0u) {
-      const uint4 r = philox4x32_10(make_uint4(s >> 1, wid_lo, wid_hi, task_id), key);
-      x = r.x; y = r.y; cx2 = r.z; cx3 = r.w;
+    // ---- one Philox block = two draws.  Block 0: the injection draw (Step 4) then the first
+    // transition; later blocks: two Step 6' transitions.
+    const uint4 r = philox4x32_10(make_uint4(b, wid_lo, wid_hi, task_id), key);
+    int outcome = -3;                  // -3: continue, 0/1: absorbed at L/R, -2: truncated
+    if (b == 0) {
+      const uint32_t c = __umulhi(r.x, W);
+      const uint64_t e = __ldg(mrow + c);
+      row = inj_row0 + (r.y < (uint32_t)e ? c : (uint32_t)(e >> 32));
     } else {
-      x = cx2; y = cx3;
+      const uint32_t c = __umulhi(r.x, K);
+      const uint64_t e = __ldg(trow + (uint64_t)row * K + c);
+      const uint32_t j = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+      ++steps;
+      if (j >= n) outcome = (int)(j - n);
+      else if (steps >= max_steps) outcome = -2;
+      else row = j;
     }
-    ++s;
-    const uint32_t c = __umulhi(x, K);
-    const uint64_t e = __ldg(trow + (uint64_t)row * K + c);
-    const uint32_t j = y < (uint32_t)e ? c : (uint32_t)(e >> 32);
-    ++steps;
-    if (j >= n || steps >= max_steps) {
-      // absorbed at lead j - n (0 = L, 1 = R), or cut at the step cap (truncated)
+    if (outcome == -3) {
+      const uint32_t c = __umulhi(r.z, K);
+      const uint64_t e = __ldg(trow + (uint64_t)row * K + c);
+      const uint32_t j = r.w < (uint32_t)e ? c : (uint32_t)(e >> 32);
+      ++steps;
+      if (j >= n) outcome = (int)(j - n);
+      else if (steps >= max_steps) outcome = -2;
+      else row = j;
+    }
+    ++b;
+    if (outcome != -3) {
       a[0] += 1u;
-      if (j == n) a[1] += 1u;
-      else if (j == n + 1) a[2] += 1u;
+      if (outcome == 0) a[1] += 1u;
+      else if (outcome == 1) a[2] += 1u;
       else a[3] += 1u;
       a[4] += steps;
-      if (kTrace) { trace_lead[g] = j >= n ? (int)(j - n) : -2; trace_steps[g] = steps; }
+      if (kTrace) { trace_lead[g] = outcome; trace_steps[g] = steps; }
       has = false;
       if (a[4] >= kFlushAt || a[0] >= kFlushAt) flush_lane(s_tally, tl, a);
-    } else {
-      row = j;
     }
   }
   if (tl >= 0) flush_lane(s_tally, tl, a);
