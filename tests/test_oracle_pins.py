@@ -374,3 +374,40 @@ def test_pins_catch_a_wrong_lead_sign(monkeypatch):
     r = pipeline.task_reference(on, et, 1.0, 0.5, with_alias=False)
     tab = r["tab"]
     assert not np.allclose(tab["w"].sum(1), tab["A_row"], rtol=1e-6)
+
+
+# ---------------------------------------------------------------- gradients
+
+@pytest.mark.parametrize("seed,W,L,E,lm", [(21, 3, 5, 0.4, 0), (22, 1, 8, -0.7, 0), (23, 2, 4, 1.1, 1)])
+def test_gradient_matches_finite_differences_of_direct_solve(seed, W, L, E, lm):
+    """The FP64 tangent of T_qp (through the walk's absorbing chain) against central
+    differences (h = 1e-5) of the direct probe solve, an independent route to T."""
+    from oracle import adjoint
+    rng = np.random.default_rng(seed)
+    on = rng.uniform(-1, 1, (L, W))
+    et = 0.1 + rng.uniform(0, 0.05, (L, W))
+    T, gV, gE = adjoint.transmission_gradient(on, et, 1.0, E, 0, 1, lm, 0.6)
+
+    def Td(o, e):
+        return buttiker.effective_transmission(wire.green_retarded(E, o, e, 1.0, lm, 0.6))[1, 0]
+
+    assert abs(T - Td(on, et)) < 1e-11 * T
+    h = 1e-5
+    for a in range(L):
+        for b in range(W):
+            d = np.zeros((L, W))
+            d[a, b] = h
+            fdV = (Td(on + d, et) - Td(on - d, et)) / (2 * h)
+            fdE = (Td(on, et + d) - Td(on, et - d)) / (2 * h)
+            assert abs(fdV - gV[a, b]) <= 1e-6 * max(abs(fdV), 1e-3 * abs(T))
+            assert abs(fdE - gE[a, b]) <= 1e-6 * max(abs(fdE), 1e-3 * abs(T))
+
+
+def test_gradient_reciprocity():
+    from oracle import adjoint
+    on, et = _wire(24, 3, 4, 0.15)
+    T1, gV1, gE1 = adjoint.transmission_gradient(on, et, 1.0, -0.3, 0, 1)
+    T2, gV2, gE2 = adjoint.transmission_gradient(on, et, 1.0, -0.3, 1, 0)
+    assert abs(T1 - T2) < 1e-12 * T1
+    assert np.allclose(gV1, gV2, atol=1e-12 * np.abs(gV1).max())
+    assert np.allclose(gE1, gE2, atol=1e-12 * np.abs(gE1).max())
