@@ -177,9 +177,18 @@ def run_gpu(args):
     state = {"steps": 0, "walkers": 0, "I": None, "se": None, "counts": None}
 
     def one_step(step_idx, wires, memspace):
-        tables = negf.negf_build_tables(ctx, wires, precision=prec, memspace=memspace)
-        tally = negf.negf_walk(ctx, tables, 0, args.seed, N,
-                               walker_id_offset=(rank * 1000 + step_idx) * N, max_steps=args.max_steps)
+        wid0 = (rank * 1000 + step_idx) * N
+        if args.mode == "pipeline":
+            # build wave w+1 while wave w walks; tables are freed wave by wave
+            tables, tally = negf.negf_run(ctx, wires, 0, args.seed, N, precision=prec,
+                                          memspace=memspace, walker_id_offset=wid0,
+                                          max_steps=args.max_steps,
+                                          tasks_per_wave=args.tasks_per_wave,
+                                          walk_blocks_per_sm=args.walk_blocks_per_sm)
+        else:
+            tables = negf.negf_build_tables(ctx, wires, precision=prec, memspace=memspace)
+            tally = negf.negf_walk(ctx, tables, 0, args.seed, N, walker_id_offset=wid0,
+                                   max_steps=args.max_steps)
         res = negf.negf_current(ctx, tables, tally, wl.mu_p, wl.mu_q, wl.kT)
         counts = negf.negf_tally_counts(ctx, tally, n_tasks)
         negf.negf_tally_free(tally)
@@ -230,6 +239,15 @@ def run_gpu(args):
         e2e_steps += int(counts[:, 4].sum())
     e2e_ms = max_over_ranks(e2e_ms, world)
     e2e_steps = sum_over_ranks(float(e2e_steps), world)
+    # ceiling for the walk's 8-byte alias-entry gathers (measured, this GPU, this run)
+    per_task_bytes = 8 * max((w.W * w.L + 2 * w.W) * (w.W * w.L + 2) for w in wl.wires)
+    probe_tab = 2 * per_task_bytes
+    probe_gps = negf.negf_probe_gather(ctx, probe_tab, ilp=8, chain=64)
+    probe_gps1 = negf.negf_probe_gather(ctx, probe_tab, ilp=1, chain=64)
+    probe_gbs = 8 * probe_gps / 1e9
+    probe_src = (f"measured: negf_probe_gather, random 8-byte gathers over {probe_tab >> 20} MiB "
+                 f"(two tasks' alias tables), 8 independent chains per thread "
+                 f"({probe_gps:.3g}/s; 1 chain: {probe_gps1:.3g}/s)")
     negf.negf_destroy(ctx)
     if rank != 0:
         return
@@ -241,16 +259,22 @@ def run_gpu(args):
     kname, (klaunch, kms) = dom
     peak, src = peaks()
     abytes = algorithmic_bytes(kname, wl, prec, counts)
-    roof = None
+    roof = roof_hbm = None
     if abytes is not None and klaunch > 0:
-        per_launch_s = kms / 1e3 / klaunch * (1 if kname != "walk_kernel" else 1)
         launches_per_step = klaunch / args.steps
         per_launch_bytes = abytes / max(1, launches_per_step)
+        per_launch_s = kms / 1e3 / klaunch
         ach = per_launch_bytes / per_launch_s / 1e9
-        roof = {"kernel": kname, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": src,
-                "traffic": None, "algorithmic_bytes_per_launch": int(per_launch_bytes),
-                "avg_launch_ms": round(kms / klaunch, 4)}
+        roof_hbm = {"kernel": kname, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": src + " HBM copy",
+                    "traffic": None, "algorithmic_bytes_per_launch": int(per_launch_bytes),
+                    "avg_launch_ms": round(kms / klaunch, 5)}
+        roof = dict(roof_hbm)
+        if kname == "walk_kernel" and probe_gbs:
+            # the alias tables of the tasks in flight sit in L2: the ceiling is the measured
+            # random 8-byte gather rate over a table of that size
+            roof.update(bound="l2", peak=round(probe_gbs, 1), frac=round(ach / probe_gbs, 4),
+                        peak_source=probe_src)
     # seconds per current at 1 % relative standard error: fixed table cost + walks scaled by
     # the binomial variance (N_needed = N (rel_se / 0.01)^2)
     walk_ms = prof.get("walk_kernel", (0, 0.0))[1] / args.steps
@@ -266,6 +290,7 @@ def run_gpu(args):
                    "walkers_per_task": N, "precision": prec, "start_lead": "L",
                    "mu_p": wl.mu_p, "mu_q": wl.mu_q, "kT": wl.kT,
                    "l2": "flushed between timed steps (258 MiB write, outside the timed events)",
+                   "mode": args.mode, "tasks_per_wave": args.tasks_per_wave,
                    "parallelism": f"tasks replicated per rank, walker ids disjoint ({world} GPU)"},
         "walker_steps_per_step": all_steps / args.steps / world,
         "walkers_per_step": tot_walkers / args.steps,
@@ -273,6 +298,7 @@ def run_gpu(args):
         "s_per_current_1pct": s_per_current,
         "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
         "roofline": roof,
+        "roofline_hbm": roof_hbm,
         "e2e": {"value": e2e_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": launches,
@@ -351,6 +377,9 @@ def main():
     ap.add_argument("--max-steps", type=int, default=1 << 20)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="separate", choices=["pipeline", "separate"])
+    ap.add_argument("--tasks-per-wave", type=int, default=8)
+    ap.add_argument("--walk-blocks-per-sm", type=int, default=4)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -94,7 +94,8 @@ typedef struct {
   int32_t precision;    /* negf_precision */
   int32_t memspace;     /* negf_memspace of every array in the wires */
   int32_t keep_weights; /* nonzero: keep the FP transition weights for negf_export_tables */
-  int32_t reserved;     /* must be 0 */
+  int32_t keep_green;   /* nonzero: also keep G (dense n x n per task), G Phi, the weights and
+                           the transverse modes, as negf_current_backward needs them */
 } negf_build_opts;
 
 /* Per-task facts, read back from the device (synchronises). */
@@ -106,6 +107,8 @@ typedef struct {
   int32_t reserved;
   double energy, energy_weight;
   double c[2];           /* Tr[Gamma_p A] for p = L (0) and R (1), Eq. elast_lin_xpq */
+  uint64_t table_offset; /* first entry of this task's rows x K block (tables, score tallies) */
+  uint64_t mode_offset;  /* first entry of this task's 2 x W block (mode tables / tallies) */
 } negf_task_info;
 
 /* --- context -------------------------------------------------------------------------- */
@@ -181,6 +184,69 @@ negf_status negf_tally_accumulate(negf_ctx ctx, negf_tally tally, const uint64_t
 int32_t negf_tally_start_lead(negf_tally tally);
 void negf_tally_free(negf_tally tally);
 
+/* --- batched build + walk pipeline ------------------------------------------------------ */
+
+typedef struct {
+  int32_t start_lead;          /* 0 = L, 1 = R (as in negf_walk) */
+  int32_t tasks_per_wave;      /* tasks built per wave; 0 = about an eighth of the tasks */
+  uint64_t seed;
+  uint64_t walkers_per_task;
+  uint64_t walker_id_offset;
+  uint32_t max_steps;          /* 1 <= max_steps <= NEGF_MAX_STEPS */
+  int32_t waves_in_flight;     /* waves whose tables may coexist; 0 = 2 */
+  uint64_t memory_budget;      /* bytes of tables + scratch in flight; 0 = half the free memory */
+  int32_t walk_blocks_per_sm;  /* cap of the walk grid per SM; 0 = as many as fit */
+  int32_t reserved;            /* must be 0 */
+} negf_run_opts;
+
+/* The whole hot path for a batch of wires of any sizes (paper silent; Sec. IV runs many
+ * independent samples side by side): tasks are split into waves of consecutive tasks whose
+ * tables fit the memory budget; wave w+1 is built on the context stream while wave w walks on
+ * a second stream of the context, and each wave's tables are freed as soon as its walks are
+ * done.  Walks are identical to negf_build_tables + negf_walk with the same seed and walker
+ * ids (the Philox task number is the task's index in the batch), so tallies agree bit for bit.
+ * Returns a task handle (descriptors and c_p; its alias tables are released, so
+ * NEGF_EXPORT_ALIAS / NEGF_EXPORT_ROWSUM are refused) and the tally, both usable with
+ * negf_current.  Asynchronous like negf_build_tables (host inputs are read during the call). */
+negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
+                     const negf_build_opts* build, const negf_run_opts* run,
+                     negf_tables* out_tasks, negf_tally* out_tally);
+int32_t negf_tables_num_waves(negf_tables tables);
+
+/* --- gradient (paper silent) ---------------------------------------------------------------- */
+
+/* negf_walk that also records score tallies: every walk absorbed at lead r is replayed and
+ * each transition a -> b adds 1 to counts[r][table_offset + a K + b] of its task, its injection
+ * mode m to mode_counts[r][mode_offset + p W + m] (offsets from negf_get_task_info).  Replaying
+ * doubles the walk work.  The tables must still hold their alias rows (negf_build_tables). */
+negf_status negf_walk_score(negf_ctx ctx, negf_tables tables, int32_t start_lead, uint64_t seed,
+                            uint64_t walkers_per_task, uint64_t walker_id_offset,
+                            uint32_t max_steps, negf_tally* out);
+/* Score tallies of a tally from negf_walk_score: host_counts [2][negf_tally_score_size] and
+ * host_mode_counts [2][negf_tally_mode_size] (lead-major).  Synchronises. */
+negf_status negf_tally_score_counts(negf_ctx ctx, negf_tally tally, uint64_t* host_counts,
+                                    uint64_t* host_mode_counts);
+/* Add host score counts (same layout) into the tally: merges runs over disjoint walker ids. */
+negf_status negf_tally_score_accumulate(negf_ctx ctx, negf_tally tally,
+                                        const uint64_t* host_counts,
+                                        const uint64_t* host_mode_counts);
+uint64_t negf_tally_score_size(negf_tally tally);
+uint32_t negf_tally_mode_size(negf_tally tally);
+
+/* Gradient of the Monte Carlo current of every wire (as negf_current with the same mu, kT)
+ * w.r.t. the onsite energies and the Buttiker dephasing of every site:
+ *   d_onsite[s] = sum_w dI[w] dI_w/dV_s,   d_eta[s] = sum_w dI[w] dI_w/deta_s,
+ * sites s numbered wire after wire (wire w's L*W sites follow those of wires < w).  The
+ * transmission's derivative is the score-function estimator dT = dc_p P + c_p
+ * E[(1_q - P) d log p(path)] from the score tallies, pushed through the tables' dependence on
+ * G and of G on the parameters (dG = G e_k e_k^T G, resp. -(i/2) G e_k e_k^T G).  Requires
+ * tables built with keep_green and a tally from negf_walk_score.  dI [n_wires], d_onsite and
+ * d_eta are host arrays.  Returns NEGF_E_STEPCAP (after writing the outputs) if walks were
+ * truncated.  Synchronises. */
+negf_status negf_current_backward(negf_ctx ctx, negf_tables tables, negf_tally tally,
+                                  double mu_p, double mu_q, double kT, const double* dI,
+                                  double* d_onsite, double* d_eta);
+
 /* --- current (Eq. iqof_t_el_db, Eq. elast_lin_xpq, Sec. IV.B.2) --------------------------- */
 
 /* From a tally of walks started at lead p = start_lead, with absorbing lead q = 1 - p:
@@ -239,6 +305,14 @@ negf_status negf_profile_enable(negf_ctx ctx, int32_t on);
  * launches and total_ms[i] their summed device time.  *n_out = number of entries. */
 negf_status negf_profile_read(negf_ctx ctx, int32_t cap, char* names, uint64_t* launches,
                               double* total_ms, int32_t* n_out);
+
+/* Measurement aid (no counterpart in the paper): random 8-byte gathers over a device table of
+ * table_bytes, each thread following `ilp` independent chains (1 or 8) of `chain` dependent
+ * loads, on a grid shaped like the walk's.  Returns the achieved gathers per second, the
+ * ceiling the walk's alias-entry loads are compared with.  Allocates and frees its table on
+ * the context stream and synchronises it. */
+negf_status negf_probe_gather(negf_ctx ctx, uint64_t table_bytes, int32_t ilp, int32_t chain,
+                              double* gathers_per_s);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,396 @@
+// Gradient of the Monte Carlo transmission w.r.t. onsite energies and dephasing.
+//
+// The paper does not differentiate its estimator.  Per task the walk estimates
+// T = c_p P(q|p) with c_p = sum_m u_m (Eq. elast_lin_xpq, Eq. lead_out_probability), and a walk
+// is a path m -> a_1 -> ... -> lead drawn with probability (u_m / c_p) prod P_ab, P_ab = w_ab /
+// rowsum_a.  The score-function identity d E[1_q] = E[(1_q - b) d log p(path)] (any constant b;
+// b = P_hat makes the injection term's c_p part vanish) gives, from the score tallies
+// C^r_ab = number of a -> b transitions on walks absorbed at r,
+//   s_ab = (C^q_ab - P_hat (C^L_ab + C^R_ab)) / N,     s_m likewise for the injection modes,
+//   dT  = sum_m (P_hat + c_p s_m / u_m) du_m + c_p sum_ab (s_ab / w_ab - S_a / rowsum_a) dw_ab,
+// S_a = sum_b s_ab.  The weights depend on G = (E - H - Sigma)^{-1}; with Gbar the Wirtinger
+// seed of every G element (dT = 2 Re sum Gbar_ij dG_ij) and dG = G e_k e_k^T G for V_k,
+// dG = -(i/2) G e_k e_k^T G for eta_k:
+//   dT/dV_k = 2 Re (G Gbar G)_kk,   dT/deta_k = Im (G Gbar G)_kk + (explicit gamma_k terms).
+// Kernels: seeds (one warp per table row), Gbar assembly (site, lead, injection and mode
+// terms in separate passes so no two threads add to one element), Y = Gbar G (tiled complex
+// GEMM), the diagonal of G Y, and the per-wire sums weighted by w_E (f_p - f_q).
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "negf_internal.cuh"
+
+namespace negf {
+namespace {
+
+template <typename C> struct RealOf;
+template <> struct RealOf<cd> { using T = double; };
+template <> struct RealOf<cf> { using T = float; };
+__device__ __forceinline__ cd conjc(cd a) { return cd{a.x, -a.y}; }
+__device__ __forceinline__ cf conjc(cf a) { return cf{a.x, -a.y}; }
+__device__ __forceinline__ cd addc(cd a, cd b) { return cd{a.x + b.x, a.y + b.y}; }
+__device__ __forceinline__ cf addc(cf a, cf b) { return cf{a.x + b.x, a.y + b.y}; }
+
+// ---- seeds: wbar_ab = c_p (s_ab / w_ab - S_a / rowsum_a) for every row; one warp per row.
+// Injection-mode seeds ubar_m = P_hat + c_p s_m / u_m (rows = rows + 2 jobs per task: the last
+// two are the mode rows).
+template <typename R>
+__global__ void seeds_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
+                             const R* __restrict__ weights, const double* __restrict__ rowsum,
+                             const double* __restrict__ mode_w, const double* __restrict__ cvals,
+                             const unsigned long long* __restrict__ counts,
+                             const unsigned long long* __restrict__ score, uint64_t stride,
+                             const unsigned long long* __restrict__ mode_score,
+                             uint32_t mode_stride, int p, double* __restrict__ wbar,
+                             double* __restrict__ ubar) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t job = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (job >= n_jobs) return;
+  int lo = 0, hi = n_tasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tasks[mid].row_base <= job) lo = mid; else hi = mid - 1;
+  }
+  const int task = lo;
+  const TaskDesc& d = tasks[task];
+  const int q = 1 - p;
+  const unsigned long long* tc = counts + (size_t)task * NEGF_TALLY_FIELDS;
+  const double N = (double)tc[0];
+  const double Ph = N > 0.0 ? (double)tc[1 + q] / N : 0.0;
+  const double c = cvals[2 * task + p];
+  const int row = (int)(job - d.row_base);
+  if (row < d.rows) {
+    const int K = d.K;
+    const uint64_t off = d.tab_off + (uint64_t)row * K;
+    const unsigned long long* C0 = score + off;
+    const unsigned long long* C1 = score + stride + off;
+    const unsigned long long* Cq = q == 0 ? C0 : C1;
+    double S = 0.0;
+    for (int b = lane; b < K; b += 32)
+      S += N > 0.0 ? ((double)Cq[b] - Ph * ((double)C0[b] + (double)C1[b])) / N : 0.0;
+    for (int o = 16; o > 0; o >>= 1) S += __shfl_down_sync(0xffffffffu, S, o);
+    S = __shfl_sync(0xffffffffu, S, 0);
+    const double rs = rowsum[d.row_base + row];
+    for (int b = lane; b < K; b += 32) {
+      const double wv = (double)weights[off + b];
+      const double s = N > 0.0 ? ((double)Cq[b] - Ph * ((double)C0[b] + (double)C1[b])) / N : 0.0;
+      double v = 0.0;
+      if (wv > 0.0) v = s / wv;
+      if (rs > 0.0) v -= S / rs;
+      wbar[off + b] = c * v;
+    }
+  } else if (row == d.rows && lane < d.W) {
+    // injection modes of the start lead p
+    const int m = lane;
+    const uint32_t mo = d.mode_off + p * d.W + m;
+    const double u = mode_w[mo];
+    const double C0 = (double)mode_score[mo], C1 = (double)mode_score[mode_stride + mo];
+    const double Cq = q == 0 ? C0 : C1;
+    const double s = N > 0.0 ? (Cq - Ph * (C0 + C1)) / N : 0.0;
+    ubar[d.mode_off + p * d.W + m] = Ph + (u > 0.0 ? c * s / u : 0.0);
+  }
+}
+
+// ---- Gbar assembly for one task (dense n x n, row-major, element (i, j)).
+// Pass A: site rows a, site columns b: Gbar[b][a] = wbar_ab gamma_b conj(G[b][a]).
+template <typename C>
+__global__ void gbar_sites_kernel(TaskDesc d, const C* __restrict__ G,
+                                  const double* __restrict__ wbar, const double* __restrict__ eta,
+                                  C* __restrict__ Gbar) {
+  using R = typename RealOf<C>::T;
+  const int n = d.n, K = d.K;
+  const uint64_t total = (uint64_t)n * n;
+  for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(idx / n), a = (int)(idx % n);      // element (b, a)
+    const R s = (R)(wbar[d.tab_off + (uint64_t)a * K + b] * eta[b]);
+    const C g = conjc(G[idx]);
+    Gbar[idx] = C{s * g.x, s * g.y};
+  }
+}
+
+// Pass B: lead columns of the site rows: for row a and lead r, y_nu = sum_x phi_nu(x)
+// G[(r,x)][a]; Gbar[(r,x)][a] += wbar_{a,n+r} sum_nu Gamma_nu phi_nu(x) conj(y_nu).
+// One thread per (a, x); the two leads are done one after the other (L = 1 puts both on
+// slice 0, so they must not run concurrently).
+template <typename C>
+__global__ void gbar_leads_kernel(TaskDesc d, const C* __restrict__ G,
+                                  const double* __restrict__ wbar, const double* __restrict__ phi,
+                                  const double* __restrict__ gam, C* __restrict__ Gbar, int r) {
+  using R = typename RealOf<C>::T;
+  const int n = d.n, W = d.W, K = d.K;
+  const int k0 = (r == 0 ? 0 : d.L - 1) * W;
+  const int total = n * W;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int a = idx / W, x = idx % W;
+    const double wb = wbar[d.tab_off + (uint64_t)a * K + n + r];
+    if (wb == 0.0) continue;
+    double tx = 0.0, ty = 0.0;
+    for (int nu = 0; nu < W; ++nu) {
+      double yx = 0.0, yy = 0.0;
+      for (int xx = 0; xx < W; ++xx) {
+        const C g = G[(uint64_t)(k0 + xx) * n + a];
+        yx += phi[xx * W + nu] * (double)g.x;
+        yy += phi[xx * W + nu] * (double)g.y;
+      }
+      const double f = gam[nu] * phi[x * W + nu];
+      tx += f * yx;
+      ty -= f * yy;                                          // conj(y)
+    }
+    C* o = Gbar + (uint64_t)(k0 + x) * n + a;
+    o->x += (R)(wb * tx);
+    o->y += (R)(wb * ty);
+  }
+}
+
+// Pass C: injection rows (p, m): psi = G Phi_p[:, m] (gphi), psibar_b = wbar gamma_b conj(psi_b)
+// for sites, plus the lead-column terms on the boundary slices; then
+// Gbar[b][(p,y)] += sum_m psibar^(m)_b phi_m(y).  One thread per (b, y).
+template <typename C>
+__global__ void gbar_inj_kernel(TaskDesc d, const C* __restrict__ gphi,
+                                const double* __restrict__ wbar, const double* __restrict__ eta,
+                                const double* __restrict__ phi, const double* __restrict__ gam,
+                                int p, C* __restrict__ Gbar) {
+  using R = typename RealOf<C>::T;
+  const int n = d.n, W = d.W, K = d.K, L = d.L;
+  const int total = n * W;
+  const int kp = (p == 0 ? 0 : L - 1) * W;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int b = idx / W, y = idx % W;
+    const int sb = b / W, xb = b % W;                         // slice and row of site b
+    double ax = 0.0, ay = 0.0;
+    for (int m = 0; m < W; ++m) {
+      const uint64_t roff = d.tab_off + (uint64_t)(n + p * W + m) * K;
+      const C ps = gphi[(uint64_t)b * 2 * W + p * W + m];
+      double bx = wbar[roff + b] * eta[b] * (double)ps.x;     // psibar_b = wbar gamma conj(psi)
+      double by = -wbar[roff + b] * eta[b] * (double)ps.y;
+      for (int r = 0; r < 2; ++r) {
+        const int sr = r == 0 ? 0 : L - 1;
+        if (sb != sr) continue;
+        const double wl = wbar[roff + n + r];
+        if (wl == 0.0) continue;
+        double tx = 0.0, ty = 0.0;
+        for (int nu = 0; nu < W; ++nu) {
+          double zx = 0.0, zy = 0.0;
+          for (int xx = 0; xx < W; ++xx) {
+            const C g = gphi[(uint64_t)(sr * W + xx) * 2 * W + p * W + m];
+            zx += phi[xx * W + nu] * (double)g.x;
+            zy += phi[xx * W + nu] * (double)g.y;
+          }
+          const double f = gam[nu] * phi[xb * W + nu];
+          tx += f * zx;
+          ty -= f * zy;
+        }
+        bx += wl * tx;
+        by += wl * ty;
+      }
+      ax += bx * phi[y * W + m];
+      ay += by * phi[y * W + m];
+    }
+    C* o = Gbar + (uint64_t)b * n + kp + y;
+    o->x += (R)ax;
+    o->y += (R)ay;
+  }
+}
+
+// Pass D: mode weights u_m = lambda_m <phi_m|A|phi_m> = -2 lambda_m Im(phi_m^T G phi_m):
+// Gbar[(p,x)][(p,y)] += i ubar_m lambda_m phi_m(x) phi_m(y).
+template <typename C>
+__global__ void gbar_modes_kernel(TaskDesc d, const double* __restrict__ ubar,
+                                  const double* __restrict__ phi, const double* __restrict__ gam,
+                                  int p, C* __restrict__ Gbar) {
+  using R = typename RealOf<C>::T;
+  const int n = d.n, W = d.W;
+  const int kp = (p == 0 ? 0 : d.L - 1) * W;
+  for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+    const int x = idx / W, y = idx % W;
+    double v = 0.0;
+    for (int m = 0; m < W; ++m)
+      v += ubar[d.mode_off + p * W + m] * gam[m] * phi[x * W + m] * phi[y * W + m];
+    C* o = Gbar + (uint64_t)(kp + x) * n + kp + y;
+    o->y += (R)v;
+  }
+}
+
+// ---- Y = A B for dense complex n x n (row-major), tiled in shared memory.
+template <typename C>
+__global__ void __launch_bounds__(256) cgemm_kernel(const C* __restrict__ A,
+                                                    const C* __restrict__ B, C* __restrict__ Y,
+                                                    int n) {
+  constexpr int T = 32;
+  __shared__ C sA[T][T + 1];
+  __shared__ C sB[T][T + 1];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;     // 32 x 8 threads, 4 rows each
+  const int row0 = blockIdx.y * T, col = blockIdx.x * T + tx;
+  C acc[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) acc[r] = C{0, 0};
+  for (int k0 = 0; k0 < n; k0 += T) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = ty + 8 * r;
+      const int ar = row0 + i, ac = k0 + tx;
+      sA[i][tx] = (ar < n && ac < n) ? A[(uint64_t)ar * n + ac] : C{0, 0};
+      const int br = k0 + i;
+      sB[i][tx] = (br < n && col < n) ? B[(uint64_t)br * n + col] : C{0, 0};
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < T; ++k) {
+      const C b = sB[k][tx];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        const C a = sA[ty + 8 * r][k];
+        acc[r].x += a.x * b.x - a.y * b.y;
+        acc[r].y += a.x * b.y + a.y * b.x;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = row0 + ty + 8 * r;
+    if (i < n && col < n) Y[(uint64_t)i * n + col] = acc[r];
+  }
+}
+
+// ---- dT/dV_k = 2 Re (G Y)_kk, dT/deta_k = Im (G Y)_kk + explicit gamma_k terms:
+// sum over rows of wbar_{row,k} |.|^2 where |.|^2 = |G[k][a]|^2 (site rows a) or |psi_m,k|^2.
+// One warp per k.
+template <typename C>
+__global__ void grad_diag_kernel(TaskDesc d, const C* __restrict__ G, const C* __restrict__ Y,
+                                 const C* __restrict__ gphi, const double* __restrict__ wbar,
+                                 double* __restrict__ dV, double* __restrict__ dEta) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * (blockDim.x >> 5) + warp;
+  const int n = d.n, K = d.K, W = d.W;
+  if (k >= n) return;
+  double zx = 0.0, zy = 0.0, ex = 0.0;
+  for (int i = lane; i < n; i += 32) {
+    const C g = G[(uint64_t)k * n + i];
+    const C y = Y[(uint64_t)i * n + k];
+    zx += (double)g.x * y.x - (double)g.y * y.y;
+    zy += (double)g.x * y.y + (double)g.y * y.x;
+    ex += wbar[d.tab_off + (uint64_t)i * K + k] * ((double)g.x * g.x + (double)g.y * g.y);
+  }
+  for (int j = lane; j < 2 * W; j += 32) {
+    const C ps = gphi[(uint64_t)k * 2 * W + j];
+    ex += wbar[d.tab_off + (uint64_t)(n + j) * K + k] * ((double)ps.x * ps.x + (double)ps.y * ps.y);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    zx += __shfl_down_sync(0xffffffffu, zx, o);
+    zy += __shfl_down_sync(0xffffffffu, zy, o);
+    ex += __shfl_down_sync(0xffffffffu, ex, o);
+  }
+  if (lane == 0) {
+    dV[k] = 2.0 * zx;
+    dEta[k] = zy + ex;
+  }
+}
+
+// ---- dI/dtheta per wire: sum over the wire's tasks (fixed order) of
+// seed_w * w_E (f_p - f_q) dT/dtheta.  One thread per (wire, site).
+__device__ __forceinline__ double fermi_b(double E, double mu, double kT) {
+  return 0.5 * (1.0 - tanh(0.5 * (E - mu) / kT));
+}
+
+__global__ void grad_sum_kernel(const TaskDesc* __restrict__ tasks, int n_wires,
+                                const int32_t* __restrict__ wire_task0,
+                                const uint64_t* __restrict__ task_site_off,
+                                const uint64_t* __restrict__ wire_site_off,
+                                const double* __restrict__ dT_V, const double* __restrict__ dT_E,
+                                const double* __restrict__ seed, double mu_p, double mu_q,
+                                double kT, double* __restrict__ out_V, double* __restrict__ out_E) {
+  const int w = blockIdx.x;
+  if (w >= n_wires) return;
+  const int t0 = wire_task0[w], t1 = wire_task0[w + 1];
+  if (t0 == t1) return;
+  const int n = tasks[t0].n;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    double aV = 0.0, aE = 0.0;
+    for (int t = t0; t < t1; ++t) {
+      const TaskDesc& d = tasks[t];
+      const double wd = seed[w] * d.w_E * (fermi_b(d.E, mu_p, kT) - fermi_b(d.E, mu_q, kT));
+      aV += wd * dT_V[task_site_off[t] + k];
+      aE += wd * dT_E[task_site_off[t] + k];
+    }
+    out_V[wire_site_off[w] + k] = aV;
+    out_E[wire_site_off[w] + k] = aE;
+  }
+}
+
+template <typename C>
+cudaError_t backward_task(const TaskDesc& d, const C* G, const C* gphi, const double* wbar,
+                          const double* ubar, const double* eta, const double* phi,
+                          const double* gam, int p, C* Gbar, C* Y, double* dV, double* dE,
+                          int sm_count, cudaStream_t s) {
+  const int n = d.n, W = d.W;
+  const uint64_t nn = (uint64_t)n * n;
+  unsigned blocks = (unsigned)((nn + 255) / 256);
+  if (blocks > (unsigned)sm_count * 32) blocks = (unsigned)sm_count * 32;
+  gbar_sites_kernel<C><<<blocks, 256, 0, s>>>(d, G, wbar, eta, Gbar);
+  const unsigned bl = (unsigned)((n * W + 255) / 256);
+  gbar_leads_kernel<C><<<bl, 256, 0, s>>>(d, G, wbar, phi, gam, Gbar, 0);
+  gbar_leads_kernel<C><<<bl, 256, 0, s>>>(d, G, wbar, phi, gam, Gbar, 1);
+  gbar_inj_kernel<C><<<bl, 256, 0, s>>>(d, gphi, wbar, eta, phi, gam, p, Gbar);
+  gbar_modes_kernel<C><<<1, 256, 0, s>>>(d, ubar, phi, gam, p, Gbar);
+  dim3 grid((n + 31) / 32, (n + 31) / 32);
+  cgemm_kernel<C><<<grid, 256, 0, s>>>(Gbar, G, Y, n);
+  grad_diag_kernel<C><<<(n + 7) / 8, 256, 0, s>>>(d, G, Y, gphi, wbar, dV, dE);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_backward_seeds(const TaskDesc* d_tasks, int n_tasks, uint32_t n_jobs,
+                                  int precision, const void* d_weights, const double* d_rowsum,
+                                  const double* d_mode_w, const double* d_c,
+                                  const uint64_t* d_counts, const uint64_t* d_score,
+                                  uint64_t stride, const uint64_t* d_mode_score,
+                                  uint32_t mode_stride, int start_lead, double* d_wbar,
+                                  double* d_ubar, cudaStream_t s) {
+  if (n_jobs == 0) return cudaSuccess;
+  const unsigned blocks = (n_jobs + 7) / 8;
+  const auto* cnt = reinterpret_cast<const unsigned long long*>(d_counts);
+  const auto* sc = reinterpret_cast<const unsigned long long*>(d_score);
+  const auto* ms = reinterpret_cast<const unsigned long long*>(d_mode_score);
+  if (precision == NEGF_FP64)
+    seeds_kernel<double><<<blocks, 256, 0, s>>>(d_tasks, n_tasks, n_jobs,
+                                                static_cast<const double*>(d_weights), d_rowsum,
+                                                d_mode_w, d_c, cnt, sc, stride, ms, mode_stride,
+                                                start_lead, d_wbar, d_ubar);
+  else
+    seeds_kernel<float><<<blocks, 256, 0, s>>>(d_tasks, n_tasks, n_jobs,
+                                               static_cast<const float*>(d_weights), d_rowsum,
+                                               d_mode_w, d_c, cnt, sc, stride, ms, mode_stride,
+                                               start_lead, d_wbar, d_ubar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_backward_task(const TaskDesc& d, int precision, const void* G,
+                                 const void* gphi, const double* wbar, const double* ubar,
+                                 const double* eta, const double* phi, const double* gam,
+                                 int start_lead, void* Gbar, void* Y, double* dV, double* dE,
+                                 int sm_count, cudaStream_t s) {
+  if (precision == NEGF_FP64)
+    return backward_task<cd>(d, static_cast<const cd*>(G), static_cast<const cd*>(gphi), wbar,
+                             ubar, eta, phi, gam, start_lead, static_cast<cd*>(Gbar),
+                             static_cast<cd*>(Y), dV, dE, sm_count, s);
+  return backward_task<cf>(d, static_cast<const cf*>(G), static_cast<const cf*>(gphi), wbar,
+                           ubar, eta, phi, gam, start_lead, static_cast<cf*>(Gbar),
+                           static_cast<cf*>(Y), dV, dE, sm_count, s);
+}
+
+cudaError_t launch_grad_sum(const TaskDesc* d_tasks, int n_wires, const int32_t* d_wire_task0,
+                            const uint64_t* d_task_site_off, const uint64_t* d_wire_site_off,
+                            const double* dT_V, const double* dT_E, const double* d_seed,
+                            double mu_p, double mu_q, double kT, double* out_V, double* out_E,
+                            cudaStream_t s) {
+  if (n_wires == 0) return cudaSuccess;
+  grad_sum_kernel<<<n_wires, 256, 0, s>>>(d_tasks, n_wires, d_wire_task0, d_task_site_off,
+                                          d_wire_site_off, dT_V, dT_E, d_seed, mu_p, mu_q, kT,
+                                          out_V, out_E);
+  return cudaGetLastError();
+}
+
+}  // namespace negf

@@ -578,7 +578,8 @@ __global__ void chain_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
                              const typename Real<C>::T* __restrict__ phig,
                              const double* __restrict__ gam, const C* __restrict__ gL,
                              const C* __restrict__ gR, const C* __restrict__ start,
-                             typename Real<C>::T* __restrict__ weights) {
+                             typename Real<C>::T* __restrict__ weights, C* __restrict__ green,
+                             C* __restrict__ gphi) {
   using R = typename Real<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -615,6 +616,11 @@ __global__ void chain_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
     for (int idx = lane; idx < W * W; idx += 32) {
       const int b = idx / W, a = idx % W;
       wrow[(uint64_t)(row0 + b) * K + k * W + a] = eta[k * W + a] * norm2(X[a * W + b]);
+      if (green) {
+        // keep G (site columns) or G Phi (injection columns) for the gradient
+        if (!inj) green[d.green_off + (uint64_t)(k * W + a) * n + m0 * W + b] = X[a * W + b];
+        else gphi[d.gphi_off + (uint64_t)(k * W + a) * 2 * W + p * W + b] = X[a * W + b];
+      }
     }
     if (k == 0 || k == L - 1) {
       // lead weight of row b: sum_nu Gamma_nu |(Phi^T X)_{nu b}|^2 = <psi_b|Gamma_lead|psi_b>
@@ -713,7 +719,7 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
                          const double* d_phi, const typename Real<C>::T* d_phiR, const cd* d_sig,
                          const double* d_gam, const C* d_gL, const C* d_gR, C* d_start,
                          typename Real<C>::T* d_w, double* d_rowsum, double* d_mode_w,
-                         double* d_c, int32_t* d_err, cudaStream_t s) {
+                         double* d_c, int32_t* d_err, C* d_green, C* d_gphi, cudaStream_t s) {
   if (sizeof(C) == sizeof(cf) && max_W <= 16) {
     // register-resident diagonal blocks, 4 warps per block
     const int warps = 4;
@@ -752,7 +758,8 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   chain_kernel<C><<<(jobs + warps - 1) / warps, 32 * warps, smem, s>>>(
-      d_tasks, n_tasks, jobs, max_W, d_eta, d_phiR, d_gam, d_gL, d_gR, d_start, d_w);
+      d_tasks, n_tasks, jobs, max_W, d_eta, d_phiR, d_gam, d_gL, d_gR, d_start, d_w, d_green,
+      d_gphi);
   return cudaGetLastError();
 }
 
@@ -785,17 +792,19 @@ cudaError_t launch_block_columns(const TaskDesc* d_tasks, int n_tasks, uint32_t 
                                  const cd* d_sig, const double* d_gam, const void* d_gL,
                                  const void* d_gR, void* d_start, void* d_weights,
                                  double* d_rowsum, double* d_mode_w, double* d_c, int32_t* d_err,
-                                 cudaStream_t s) {
+                                 void* d_green, void* d_gphi, cudaStream_t s) {
   if (n_tasks == 0 || n_cols == 0) return cudaSuccess;
   if (precision == NEGF_FP64)
     return columns_impl<cd>(d_tasks, n_tasks, n_cols, max_W, d_wire, d_wire, d_phi, d_phi,
                             d_sig, d_gam, static_cast<const cd*>(d_gL),
                             static_cast<const cd*>(d_gR), static_cast<cd*>(d_start),
-                            static_cast<double*>(d_weights), d_rowsum, d_mode_w, d_c, d_err, s);
+                            static_cast<double*>(d_weights), d_rowsum, d_mode_w, d_c, d_err,
+                            static_cast<cd*>(d_green), static_cast<cd*>(d_gphi), s);
   return columns_impl<cf>(d_tasks, n_tasks, n_cols, max_W, d_wire, d_eta32, d_phi, d_phi32,
                           d_sig, d_gam, static_cast<const cf*>(d_gL),
                           static_cast<const cf*>(d_gR), static_cast<cf*>(d_start),
-                          static_cast<float*>(d_weights), d_rowsum, d_mode_w, d_c, d_err, s);
+                          static_cast<float*>(d_weights), d_rowsum, d_mode_w, d_c, d_err,
+                          static_cast<cf*>(d_green), static_cast<cf*>(d_gphi), s);
 }
 
 }  // namespace negf

@@ -46,13 +46,25 @@ __device__ __forceinline__ void flush_lane(unsigned* s_tally, int task_local, un
   }
 }
 
-template <bool kTrace>
+// Score tallies (kScore): when a walk is absorbed at lead r it is replayed from its first draw
+// (same counters, same tables) and every transition a -> b adds 1 to score[r][a][b] of its task
+// (and the injection mode to mode_score[r][m]); these are the counts the score-function
+// gradient needs.
+struct ScoreOut {
+  unsigned long long* cnt;        // [2][stride] at each task's tab_off (rows x K)
+  unsigned long long* mode_cnt;   // [2][mode_stride] at each task's mode_off (2 x W)
+  unsigned long long stride;
+  unsigned mode_stride;
+};
+
+template <bool kTrace, bool kScore>
 __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
-    const TaskDesc* __restrict__ tasks, int task0, int n_tasks, const uint64_t* __restrict__ tab,
-    const uint64_t* __restrict__ mode_tab, const double* __restrict__ cvals, int start_lead,
-    PhiloxKey key, uint64_t walkers_per_task, uint64_t id_offset, uint32_t max_steps,
+    const TaskDesc* __restrict__ tasks, int task0, int n_tasks, uint32_t id_base,
+    const uint64_t* __restrict__ tab, const uint64_t* __restrict__ mode_tab,
+    const double* __restrict__ cvals, int start_lead, PhiloxKey key, uint64_t walkers_per_task,
+    uint64_t id_offset, uint32_t max_steps,
     unsigned long long* __restrict__ counter, unsigned long long* __restrict__ tally /*window*/,
-    int32_t* __restrict__ trace_lead, uint32_t* __restrict__ trace_steps) {
+    int32_t* __restrict__ trace_lead, uint32_t* __restrict__ trace_steps, ScoreOut score) {
   extern __shared__ unsigned s_tally[];   // [n_tasks][kFields][lo, hi]
   for (int i = threadIdx.x; i < n_tasks * kFields * 2; i += blockDim.x) s_tally[i] = 0u;
   __syncthreads();
@@ -72,6 +84,8 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
   int tl = -1;
   unsigned long long t_first = 0;
   uint32_t task_id = 0, K = 0, n = 0, W = 0, inj_row0 = 0;
+  uint64_t t_tab_off = 0;
+  uint32_t t_mode_off = 0;
   bool t_open = false;
   const uint64_t* trow = nullptr;
   const uint64_t* mrow = nullptr;
@@ -87,11 +101,13 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
         tl = (int)(g / walkers_per_task);
         t_first = (unsigned long long)tl * walkers_per_task;
         const TaskDesc& d = tasks[task0 + tl];
-        task_id = (uint32_t)(task0 + tl);
+        task_id = id_base + (uint32_t)(task0 + tl);
         K = (uint32_t)d.K;
         n = (uint32_t)d.n;
         W = (uint32_t)d.W;
         inj_row0 = (uint32_t)(d.n + start_lead * d.W);
+        t_tab_off = d.tab_off;
+        t_mode_off = d.mode_off + start_lead * d.W;
         trow = tab + d.tab_off;
         mrow = mode_tab + d.mode_off + start_lead * d.W;
         t_open = cvals[2 * (task0 + tl) + start_lead] > 0.0;
@@ -154,6 +170,38 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
       else row = j;
     }
     ++b;
+    if (kScore && outcome >= 0) {
+      // replay the finished walk and count its transitions under its absorbing lead
+      unsigned long long* cnt = score.cnt + (size_t)outcome * score.stride + t_tab_off;
+      unsigned long long* mcnt = score.mode_cnt + (size_t)outcome * score.mode_stride + t_mode_off;
+      uint32_t rrow = 0;
+      bool live = true;
+      for (uint32_t bb = 0; live; ++bb) {
+        const uint4 q = philox4x32_10(make_uint4(bb, wid_lo, wid_hi, task_id), key);
+        if (bb == 0) {
+          const uint32_t c = __umulhi(q.x, W);
+          const uint64_t e = __ldg(mrow + c);
+          const uint32_t mode = q.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+          atomicAdd(mcnt + mode, 1ull);
+          rrow = inj_row0 + mode;
+        } else {
+          const uint32_t c = __umulhi(q.x, K);
+          const uint64_t e = __ldg(trow + (uint64_t)rrow * K + c);
+          const uint32_t j = q.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+          atomicAdd(cnt + (uint64_t)rrow * K + j, 1ull);
+          if (j >= n) live = false;
+          rrow = j;
+        }
+        if (live) {
+          const uint32_t c = __umulhi(q.z, K);
+          const uint64_t e = __ldg(trow + (uint64_t)rrow * K + c);
+          const uint32_t j = q.w < (uint32_t)e ? c : (uint32_t)(e >> 32);
+          atomicAdd(cnt + (uint64_t)rrow * K + j, 1ull);
+          if (j >= n) live = false;
+          rrow = j;
+        }
+      }
+    }
     if (outcome != -3) {
       a[0] += 1u;
       if (outcome == 0) a[1] += 1u;
@@ -174,13 +222,58 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
   }
 }
 
+// ---- gather probe: the memory-system ceiling the walk is measured against ------------------
+// Each thread follows `ilp` independent chains of dependent random 8-byte loads over a table
+// of n entries (the next index is derived from the loaded value, like a walk step that reads
+// one alias entry).  With ilp = 1 this is the walk's access pattern at its occupancy; larger
+// ilp gives the throughput ceiling of random 8-byte gathers from that table.
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x) {
+  // splitmix64 finaliser (Steele, Lea, Flood, "Fast splittable pseudorandom number
+  // generators", OOPSLA 2014)
+  x ^= x >> 30;
+  x *= 0xbf58476d1ce4e5b9ull;
+  x ^= x >> 27;
+  x *= 0x94d049bb133111ebull;
+  x ^= x >> 31;
+  return x;
+}
+
+__global__ void probe_fill_kernel(uint64_t* tab, uint64_t n) {
+  for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n;
+       i += (uint64_t)gridDim.x * blockDim.x)
+    tab[i] = mix64(i + 0x9e3779b97f4a7c15ull);
+}
+
+template <int ILP>
+__global__ void __launch_bounds__(kThreads, 5) probe_gather_kernel(const uint64_t* __restrict__ tab,
+                                                                    uint32_t n, int chain,
+                                                                    unsigned long long* sink) {
+  uint32_t idx[ILP];
+  const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+#pragma unroll
+  for (int c = 0; c < ILP; ++c) idx[c] = (uint32_t)(mix64(tid * ILP + c) % n);
+  uint64_t acc = 0;
+  for (int it = 0; it < chain; ++it) {
+#pragma unroll
+    for (int c = 0; c < ILP; ++c) {
+      const uint64_t e = __ldg(tab + idx[c]);
+      acc += e;
+      idx[c] = __umulhi((uint32_t)e ^ (uint32_t)it, n);
+    }
+  }
+  if (acc == 0x123456789ull) atomicAdd(sink, 1ull);   // keeps the loads alive
+}
+
 }  // namespace
 
-cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, const uint64_t* d_tab,
-                        const uint64_t* d_mode_tab, const double* d_c, int start_lead,
-                        uint64_t seed, uint64_t walkers_per_task, uint64_t id_offset,
-                        uint32_t max_steps, unsigned long long* d_counter, uint64_t* d_tally,
-                        int32_t* d_trace_lead, uint32_t* d_trace_steps, int sm_count,
+cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_t id_base,
+                        const uint64_t* d_tab, const uint64_t* d_mode_tab, const double* d_c,
+                        int start_lead, uint64_t seed, uint64_t walkers_per_task,
+                        uint64_t id_offset, uint32_t max_steps, unsigned long long* d_counter,
+                        uint64_t* d_tally, int32_t* d_trace_lead, uint32_t* d_trace_steps,
+                        uint64_t* d_score, uint64_t score_stride, uint64_t* d_mode_score,
+                        uint32_t mode_stride, int sm_count, int max_blocks_per_sm,
                         cudaStream_t s) {
   if (n_tasks <= 0 || walkers_per_task == 0) return cudaSuccess;
   const PhiloxKey key{(uint32_t)seed, (uint32_t)(seed >> 32)};
@@ -191,33 +284,63 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, const u
     if (e != cudaSuccess) return e;
     const unsigned long long total = (unsigned long long)nt * walkers_per_task;
     const size_t smem = sizeof(unsigned) * 2 * (size_t)nt * kFields;
+    const ScoreOut so{reinterpret_cast<unsigned long long*>(d_score),
+                      reinterpret_cast<unsigned long long*>(d_mode_score),
+                      (unsigned long long)score_stride, mode_stride};
+    auto kern = d_trace_lead ? (d_score ? walk_kernel<true, true> : walk_kernel<true, false>)
+                             : (d_score ? walk_kernel<false, true> : walk_kernel<false, false>);
     int per_sm = 0;
-    if (d_trace_lead) {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<true>, kThreads,
-                                                        smem);
-    } else {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, walk_kernel<false>, kThreads,
-                                                        smem);
-    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return e;
+    if (max_blocks_per_sm > 0 && per_sm > max_blocks_per_sm) per_sm = max_blocks_per_sm;
     if (per_sm < 1) per_sm = 1;
     unsigned long long blocks = (unsigned long long)sm_count * per_sm;
     const unsigned long long need = (total + kThreads - 1) / kThreads;
     if (blocks > need) blocks = need;
-    if (d_trace_lead) {
-      walk_kernel<true><<<(unsigned)blocks, kThreads, smem, s>>>(
-          d_tasks, task0 + w0, nt, d_tab, d_mode_tab, d_c, start_lead, key, walkers_per_task,
-          id_offset, max_steps, d_counter, tally + (size_t)w0 * kFields, d_trace_lead,
-          d_trace_steps);
-    } else {
-      walk_kernel<false><<<(unsigned)blocks, kThreads, smem, s>>>(
-          d_tasks, task0 + w0, nt, d_tab, d_mode_tab, d_c, start_lead, key, walkers_per_task,
-          id_offset, max_steps, d_counter, tally + (size_t)w0 * kFields, nullptr, nullptr);
-    }
+    kern<<<(unsigned)blocks, kThreads, smem, s>>>(
+        d_tasks, task0 + w0, nt, id_base, d_tab, d_mode_tab, d_c, start_lead, key,
+        walkers_per_task, id_offset, max_steps, d_counter, tally + (size_t)w0 * kFields,
+        d_trace_lead, d_trace_steps, so);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+}  // namespace negf
+
+namespace negf {
+
+cudaError_t probe_gather(uint64_t table_bytes, int ilp, int chain, int sm_count,
+                         uint64_t* gathers, float* ms, cudaStream_t s) {
+  const uint64_t n = table_bytes / 8;
+  if (n < 2 || n > 0xffffffffull || chain < 1) return cudaErrorInvalidValue;
+  uint64_t* tab = nullptr;
+  unsigned long long* sink = nullptr;
+  cudaError_t e = cudaMallocAsync(&tab, n * 8, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&sink, 8, s);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) {
+    probe_fill_kernel<<<sm_count * 8, 256, 0, s>>>(tab, n);
+    const unsigned blocks = (unsigned)sm_count * 5;
+    // warm the table into the cache hierarchy once, then time
+    if (ilp >= 4) probe_gather_kernel<8><<<blocks, kThreads, 0, s>>>(tab, (uint32_t)n, 4, sink);
+    else probe_gather_kernel<1><<<blocks, kThreads, 0, s>>>(tab, (uint32_t)n, 4, sink);
+    cudaEventRecord(a, s);
+    if (ilp >= 4) probe_gather_kernel<8><<<blocks, kThreads, 0, s>>>(tab, (uint32_t)n, chain, sink);
+    else probe_gather_kernel<1><<<blocks, kThreads, 0, s>>>(tab, (uint32_t)n, chain, sink);
+    cudaEventRecord(b, s);
+    e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(ms, a, b);
+    *gathers = (uint64_t)blocks * kThreads * (ilp >= 4 ? 8 : 1) * (uint64_t)chain;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (tab) cudaFreeAsync(tab, s);
+  if (sink) cudaFreeAsync(sink, s);
+  return e;
 }
 
 }  // namespace negf

@@ -33,6 +33,7 @@ struct negf_ctx_s {
   bool prof = false;
   std::vector<ProfEntry> prof_entries;
   std::vector<cudaEvent_t> event_pool;
+  cudaStream_t walk_stream = nullptr;        // second stream of negf_run (created on first use)
 };
 
 struct negf_tables_s {
@@ -54,6 +55,13 @@ struct negf_tables_s {
   void* d_weights = nullptr;     // kept only with keep_weights
   int32_t* d_err = nullptr;
   uint64_t bytes = 0;
+  bool tables_released = false;  // negf_run: alias tables freed wave by wave
+  int n_waves = 1;
+  void* d_green = nullptr;       // keep_green: dense G per task, then G Phi per task
+  void* d_gphi = nullptr;
+  double* d_phi = nullptr;       // keep_green: transverse modes (the gradient needs them)
+  uint64_t green_total = 0, gphi_total = 0, score_stride = 0;
+  uint32_t mode_stride = 0;
 };
 
 struct negf_tally_s {
@@ -61,6 +69,10 @@ struct negf_tally_s {
   int n_tasks = 0;
   int start_lead = 0;
   uint64_t* d_counts = nullptr;
+  uint64_t* d_score = nullptr;        // score tallies [2][score_stride] (negf_walk_score)
+  uint64_t* d_mode_score = nullptr;   // [2][mode_stride]
+  uint64_t score_stride = 0;
+  uint32_t mode_stride = 0;
 };
 
 namespace {
@@ -127,6 +139,9 @@ void release_tables(negf_tables t) {
   dfree(t->d_rowsum, s);
   dfree(t->d_weights, s);
   dfree(t->d_err, s);
+  dfree(t->d_green, s);
+  dfree(t->d_gphi, s);
+  dfree(t->d_phi, s);
   delete t;
 }
 
@@ -146,8 +161,10 @@ struct ProfScope {
   negf_ctx ctx;
   int idx = -1;
   uint64_t kernels = 1;
+  cudaStream_t stream = nullptr;
   cudaEvent_t a = nullptr, b = nullptr;
-  ProfScope(negf_ctx c, const char* name, uint64_t n_kernels = 1) : ctx(c), kernels(n_kernels) {
+  ProfScope(negf_ctx c, const char* name, uint64_t n_kernels = 1, cudaStream_t s = nullptr)
+      : ctx(c), kernels(n_kernels), stream(s ? s : (c ? c->stream : nullptr)) {
     if (!ctx || !ctx->prof) return;
     for (size_t i = 0; i < ctx->prof_entries.size(); ++i)
       if (ctx->prof_entries[i].name == name) idx = (int)i;
@@ -158,11 +175,11 @@ struct ProfScope {
     }
     a = take_event(ctx);
     b = take_event(ctx);
-    if (a && b) cudaEventRecord(a, ctx->stream);
+    if (a && b) cudaEventRecord(a, stream);
   }
   ~ProfScope() {
     if (idx < 0 || !a || !b) return;
-    cudaEventRecord(b, ctx->stream);
+    cudaEventRecord(b, stream);
     ctx->prof_entries[idx].pending.emplace_back(a, b);
     ctx->prof_entries[idx].launches += kernels;
   }
@@ -250,6 +267,10 @@ void negf_destroy(negf_ctx ctx) {
   cudaStreamSynchronize(ctx->stream);
   prof_resolve(ctx);
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
+  if (ctx->walk_stream) {
+    cudaStreamSynchronize(ctx->walk_stream);
+    cudaStreamDestroy(ctx->walk_stream);
+  }
   cudaFree(ctx->d_counter);
   delete ctx;
 }
@@ -283,69 +304,47 @@ negf_status negf_profile_read(negf_ctx ctx, int32_t cap, char* names, uint64_t* 
 
 const char* negf_last_error(negf_ctx ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
-negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
-                              const negf_build_opts* opts, negf_tables* out) {
-  if (!ctx) return NEGF_E_INVALID;
-  if (!out) return fail(ctx, NEGF_E_INVALID, "negf_build_tables: out is NULL");
-  *out = nullptr;
-  if (n_wires < 0 || (n_wires > 0 && !wires))
-    return fail(ctx, NEGF_E_INVALID, "negf_build_tables: bad wire list");
-  negf_build_opts o{NEGF_FP64, NEGF_MEM_HOST, 0, 0};
-  if (opts) o = *opts;
-  if (o.precision < NEGF_FP64 || o.precision > NEGF_SPLIT_TF32)
-    return fail(ctx, NEGF_E_INVALID, "negf_build_tables: unknown precision %d", o.precision);
-  if (o.memspace != NEGF_MEM_HOST && o.memspace != NEGF_MEM_DEVICE)
-    return fail(ctx, NEGF_E_INVALID, "negf_build_tables: unknown memspace %d", o.memspace);
-  if (o.reserved != 0) return fail(ctx, NEGF_E_INVALID, "negf_build_tables: reserved != 0");
-  const bool dev_in = o.memspace == NEGF_MEM_DEVICE;
-  const int prec = o.precision == NEGF_FP64 ? NEGF_FP64 : NEGF_FP32;
-  DeviceGuard guard(ctx->device);
-  cudaStream_t s = ctx->stream;
+}  // extern "C"
 
-  negf_tables t = new (std::nothrow) negf_tables_s;
-  if (!t) return fail(ctx, NEGF_E_NOMEM, "negf_build_tables: host allocation");
-  t->ctx = ctx;
-  t->n_wires = n_wires;
-  t->precision = prec;
-  // ---- validate and lay out the batch
-  uint64_t tab_off = 0, g_off = 0, wire_off = 0, start_off = 0;
+namespace {
+
+// Validated layout of a batch of wires: one descriptor per (wire, energy) task with offsets as
+// if the whole batch were built at once.
+struct Plan {
+  std::vector<TaskDesc> tasks;
+  std::vector<int32_t> wire_task0;
+  uint64_t tab_total = 0, green_total = 0, gphi_total = 0, g_total = 0;
+  uint64_t wire_total = 0;                 // doubles: onsite then eta per wire
+  uint32_t lead_total = 0, mode_total = 0, phi_total = 0;
+  int max_W = 1, max_L = 1, max_K = 3;
+};
+
+negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool dev_in, Plan& P) {
+  uint64_t tab_off = 0, g_off = 0, wire_off = 0, start_off = 0, green_off = 0, gphi_off = 0;
   uint32_t mode_off = 0, lead_off = 0, row_base = 0, col_base = 0, phi_off = 0;
-  t->h_wire_task0.push_back(0);
+  P.wire_task0.assign(1, 0);
   for (int w = 0; w < n_wires; ++w) {
     const negf_wire& wr = wires[w];
     if (wr.W < 1 || wr.W > NEGF_MAX_W || wr.L < 1 || !(wr.t > 0.0) || !isfinite(wr.t) ||
-        wr.n_energy < 0) {
-      release_tables(t);
+        wr.n_energy < 0)
       return fail(ctx, NEGF_E_INVALID, "wire %d: need 1 <= W <= %d, L >= 1, t > 0, n_energy >= 0",
                   w, NEGF_MAX_W);
-    }
-    if (wr.lead_model != NEGF_LEAD_STRIP && wr.lead_model != NEGF_LEAD_WIDE_BAND) {
-      release_tables(t);
+    if (wr.lead_model != NEGF_LEAD_STRIP && wr.lead_model != NEGF_LEAD_WIDE_BAND)
       return fail(ctx, NEGF_E_INVALID, "wire %d: unknown lead model %d", w, wr.lead_model);
-    }
-    if (wr.lead_model == NEGF_LEAD_WIDE_BAND && !(wr.gamma_lead > 0.0 && isfinite(wr.gamma_lead))) {
-      release_tables(t);
+    if (wr.lead_model == NEGF_LEAD_WIDE_BAND && !(wr.gamma_lead > 0.0 && isfinite(wr.gamma_lead)))
       return fail(ctx, NEGF_E_INVALID, "wire %d: wide-band lead needs gamma_lead > 0", w);
-    }
     const int64_t n = (int64_t)wr.W * wr.L;
     const int64_t K = n + 2, rows = n + 2 * wr.W;
-    if (n > NEGF_MAX_SITES) {
-      release_tables(t);
-      return fail(ctx, NEGF_E_INVALID, "wire %d: W*L = %lld exceeds the supported %d sites",
-                  w, (long long)n, NEGF_MAX_SITES);
-    }
-    if (!wr.onsite || !wr.eta || (wr.n_energy > 0 && !wr.energy)) {
-      release_tables(t);
+    if (n > NEGF_MAX_SITES)
+      return fail(ctx, NEGF_E_INVALID, "wire %d: W*L = %lld exceeds the supported %d sites", w,
+                  (long long)n, NEGF_MAX_SITES);
+    if (!wr.onsite || !wr.eta || (wr.n_energy > 0 && !wr.energy))
       return fail(ctx, NEGF_E_INVALID, "wire %d: NULL array", w);
-    }
     if (!dev_in) {
-      for (int64_t i = 0; i < n; ++i) {
-        if (!isfinite(wr.onsite[i]) || !isfinite(wr.eta[i]) || !(wr.eta[i] >= 0.0)) {
-          release_tables(t);
+      for (int64_t i = 0; i < n; ++i)
+        if (!isfinite(wr.onsite[i]) || !isfinite(wr.eta[i]) || !(wr.eta[i] >= 0.0))
           return fail(ctx, NEGF_E_INVALID, "wire %d: site %lld: onsite/eta not finite or eta < 0",
                       w, (long long)i);
-        }
-      }
     }
     // energies and weights are always brought to the host (they become task scalars)
     std::vector<double> E(wr.n_energy), wE(wr.n_energy, 1.0);
@@ -362,14 +361,10 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
       }
     }
     for (int k = 0; k < wr.n_energy; ++k) {
-      if (!isfinite(E[k]) || !isfinite(wE[k])) {
-        release_tables(t);
+      if (!isfinite(E[k]) || !isfinite(wE[k]))
         return fail(ctx, NEGF_E_INVALID, "wire %d: energy %d not finite", w, k);
-      }
-      if (wr.lead_model == NEGF_LEAD_STRIP && band_edge(E[k], wr.W, wr.t)) {
-        release_tables(t);
+      if (wr.lead_model == NEGF_LEAD_STRIP && band_edge(E[k], wr.W, wr.t))
         return fail(ctx, NEGF_E_INVALID, "wire %d: energy %.17g lies on a lead band edge", w, E[k]);
-      }
       TaskDesc d{};
       d.wire = w;
       d.e_idx = k;
@@ -393,7 +388,11 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
       d.col_base = col_base;
       d.phi_off = phi_off;
       d.start_off = start_off;
-      t->h_tasks.push_back(d);
+      d.green_off = green_off;
+      d.gphi_off = gphi_off;
+      P.tasks.push_back(d);
+      green_off += (uint64_t)n * n;
+      gphi_off += (uint64_t)n * 2 * wr.W;
       tab_off += (uint64_t)rows * K;
       g_off += (uint64_t)wr.L * wr.W * wr.W;
       mode_off += 2 * wr.W;
@@ -401,166 +400,528 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
       row_base += (uint32_t)(rows + 2);
       col_base += (uint32_t)(wr.L + 2);
       start_off += (uint64_t)(wr.L + 2) * wr.W * wr.W;
-      t->max_W = std::max(t->max_W, wr.W);
-      t->max_L = std::max(t->max_L, wr.L);
-      t->max_K = std::max(t->max_K, (int)K);
+      P.max_W = std::max(P.max_W, wr.W);
+      P.max_L = std::max(P.max_L, wr.L);
+      P.max_K = std::max(P.max_K, (int)K);
     }
     wire_off += 2 * (uint64_t)n;
     phi_off += (uint32_t)(wr.W * wr.W);
-    t->h_wire_task0.push_back((int32_t)t->h_tasks.size());
+    P.wire_task0.push_back((int32_t)P.tasks.size());
   }
-  t->n_tasks = (int)t->h_tasks.size();
-  t->total_jobs = row_base;
-  const int nt = t->n_tasks;
-  // ---- device buffers
-  // RGF and start blocks in the table precision: complex128 (FP64) or complex64 (FP32)
-  double* d_gL = nullptr;
-  double* d_gR = nullptr;
-  double* d_start = nullptr;
-  double* d_phi = nullptr;       // per wire: transverse modes (FP64), then the FP32 copy
-  float* d_eta32 = nullptr;      // per wire: eta in FP32
-  void* d_weights = nullptr;
-  const uint64_t cw = negf::block_bytes(prec) / sizeof(double);   // doubles per complex
-  const size_t wsz = prec == NEGF_FP64 ? sizeof(double) : sizeof(float);
-#define ALLOC(ptr, count)                                                  \
-  do {                                                                     \
-    cudaError_t e_ = dalloc(&(ptr), (count), s, &t->bytes);                \
-    if (e_ != cudaSuccess) {                                               \
-      release_tables(t);                                                   \
-      dfree(d_gL, s);                                                      \
-      dfree(d_gR, s);                                                      \
-      dfree(d_start, s);                                                   \
-      dfree(d_phi, s);                                                     \
-      dfree(d_eta32, s);                                                   \
-      if (d_weights) cudaFreeAsync(d_weights, s);                          \
-      return fail(ctx, e_ == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA, \
-                  "allocation of %s (%zu elements): %s", #ptr, (size_t)(count), \
-                  cudaGetErrorString(e_));                                 \
-    }                                                                      \
+  P.wire_total = wire_off;
+  P.tab_total = tab_off;
+  P.g_total = g_off;
+  P.green_total = green_off;
+  P.gphi_total = gphi_off;
+  P.lead_total = lead_off;
+  P.mode_total = mode_off;
+  P.phi_total = phi_off;
+  return NEGF_OK;
+}
+
+// A contiguous range of tasks built on its own: descriptors rebased to the range's buffers
+// (tables, weights, RGF and start blocks, row sums); lead, mode, wire and phi offsets stay global.
+struct Wave {
+  int t0 = 0, t1 = 0;
+  uint64_t tab = 0, g = 0, start = 0, green = 0, gphi = 0;
+  uint32_t rows = 0, cols = 0;
+  std::vector<TaskDesc> desc;
+};
+
+Wave make_wave(const Plan& P, int t0, int t1) {
+  Wave w;
+  w.t0 = t0;
+  w.t1 = t1;
+  for (int k = t0; k < t1; ++k) {
+    TaskDesc d = P.tasks[k];
+    const uint64_t sz = (uint64_t)d.rows * d.K;
+    d.tab_off = w.tab;
+    d.wt_off = w.tab;
+    d.start_off = w.start;
+    d.row_base = w.rows;
+    d.col_base = w.cols;          // g_off stays global: the sweeps run once for the batch
+    d.green_off = w.green;
+    d.gphi_off = w.gphi;
+    w.green += (uint64_t)d.n * d.n;
+    w.gphi += (uint64_t)d.n * 2 * d.W;
+    w.tab += sz;
+    w.g += (uint64_t)d.L * d.W * d.W;
+    w.start += (uint64_t)(d.L + 2) * d.W * d.W;
+    w.rows += (uint32_t)(d.rows + 2);
+    w.cols += (uint32_t)(d.L + 2);
+    w.desc.push_back(d);
+  }
+  return w;
+}
+
+// device bytes a wave needs while it is built (tables + every scratch buffer)
+uint64_t wave_bytes(const Wave& w, int prec) {
+  const uint64_t cb = negf::block_bytes(prec);
+  const uint64_t wsz = prec == NEGF_FP64 ? 8 : 4;
+  return w.tab * (8 + wsz) + w.start * cb + 8ull * w.rows;
+}
+
+// Buffers shared by every wave of a batch.
+struct Persist {
+  TaskDesc* d_tasks = nullptr;       // global descriptors (current assembly)
+  int32_t* d_wire_task0 = nullptr;
+  double* d_wire = nullptr;
+  cd* d_sig = nullptr;
+  double* d_gam = nullptr;
+  double* d_phi = nullptr;           // FP64 modes, then their FP32 copy
+  float* d_eta32 = nullptr;
+  uint64_t* d_mode_tab = nullptr;
+  double* d_mode_w = nullptr;
+  double* d_c = nullptr;
+  int32_t* d_err = nullptr;
+};
+
+void free_persist_scratch(Persist& q, cudaStream_t s) {
+  dfree(q.d_phi, s);
+  dfree(q.d_eta32, s);
+}
+
+// Allocate and fill the shared buffers, then run validation (device inputs) and the lead
+// kernel for every task.  Records the allocated bytes in *bytes.
+negf_status setup_batch(negf_ctx ctx, cudaStream_t s, const negf_wire* wires, int n_wires,
+                        bool dev_in, const Plan& P, Persist& q, uint64_t* bytes) {
+  const int nt = (int)P.tasks.size();
+#define PALLOC(ptr, count)                                                                   \
+  do {                                                                                       \
+    cudaError_t e_ = dalloc(&(ptr), (count), s, bytes);                                      \
+    if (e_ != cudaSuccess)                                                                   \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,         \
+                  "allocation of %s (%zu elements): %s", #ptr, (size_t)(count),              \
+                  cudaGetErrorString(e_));                                                   \
   } while (0)
-  ALLOC(t->d_tasks, nt);
-  ALLOC(t->d_wire_task0, n_wires + 1);
-  ALLOC(t->d_wire, wire_off);
-  ALLOC(t->d_sig, lead_off);
-  ALLOC(t->d_gam, lead_off);
-  ALLOC(t->d_tab, tab_off);
-  ALLOC(t->d_mode_tab, mode_off);
-  ALLOC(t->d_mode_w, mode_off);
-  ALLOC(t->d_c, 2 * (size_t)nt);
-  ALLOC(t->d_rowsum, row_base);
-  ALLOC(t->d_err, 1);
-  ALLOC(d_gL, g_off * cw);
-  ALLOC(d_gR, g_off * cw);
-  ALLOC(d_start, start_off * cw);
-  ALLOC(d_phi, (uint64_t)phi_off + (phi_off + 1) / 2);
-  ALLOC(d_eta32, wire_off / 2);
-  {
-    cudaError_t e_ = cudaMallocAsync(&d_weights, std::max<uint64_t>(tab_off, 1) * wsz, s);
-    if (e_ != cudaSuccess) {
-      release_tables(t);
-      dfree(d_gL, s);
-      dfree(d_gR, s);
-      dfree(d_start, s);
-      dfree(d_phi, s);
-      dfree(d_eta32, s);
-      return fail(ctx, e_ == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,
-                  "allocation of the weight scratch: %s", cudaGetErrorString(e_));
+  PALLOC(q.d_tasks, nt);
+  PALLOC(q.d_wire_task0, n_wires + 1);
+  PALLOC(q.d_wire, P.wire_total);
+  PALLOC(q.d_sig, P.lead_total);
+  PALLOC(q.d_gam, P.lead_total);
+  PALLOC(q.d_phi, (uint64_t)P.phi_total + (P.phi_total + 1) / 2);
+  PALLOC(q.d_eta32, P.wire_total / 2);
+  PALLOC(q.d_mode_tab, P.mode_total);
+  PALLOC(q.d_mode_w, P.mode_total);
+  PALLOC(q.d_c, 2 * (size_t)nt);
+  PALLOC(q.d_err, 1);
+#undef PALLOC
+  CUDA_TRY(ctx, cudaMemsetAsync(q.d_err, 0, sizeof(int32_t), s));
+  if (nt > 0)
+    CUDA_TRY(ctx, cudaMemcpyAsync(q.d_tasks, P.tasks.data(), sizeof(TaskDesc) * nt,
+                                  cudaMemcpyHostToDevice, s));
+  CUDA_TRY(ctx, cudaMemcpyAsync(q.d_wire_task0, P.wire_task0.data(),
+                                sizeof(int32_t) * (n_wires + 1), cudaMemcpyHostToDevice, s));
+  std::vector<double> stage;
+  uint64_t off = 0;
+  for (int w = 0; w < n_wires; ++w) {
+    const int64_t n = (int64_t)wires[w].W * wires[w].L;
+    if (dev_in) {
+      CUDA_TRY(ctx, cudaMemcpyAsync(q.d_wire + off, wires[w].onsite, sizeof(double) * n,
+                                    cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(ctx, cudaMemcpyAsync(q.d_wire + off + n, wires[w].eta, sizeof(double) * n,
+                                    cudaMemcpyDeviceToDevice, s));
+    } else {
+      stage.insert(stage.end(), wires[w].onsite, wires[w].onsite + n);
+      stage.insert(stage.end(), wires[w].eta, wires[w].eta + n);
     }
+    off += 2 * n;
   }
-#undef ALLOC
-  // ---- inputs
-  auto bail = [&](negf_status st) {
-    release_tables(t);
-    dfree(d_gL, s);
-    dfree(d_gR, s);
-    dfree(d_start, s);
-    dfree(d_phi, s);
-    dfree(d_eta32, s);
-    if (d_weights) cudaFreeAsync(d_weights, s);
-    return st;
-  };
-#define STEP(call)                                                                        \
-  do {                                                                                    \
-    cudaError_t e_ = (call);                                                              \
-    if (e_ != cudaSuccess)                                                                \
-      return bail(fail(ctx, NEGF_E_CUDA, "%s: %s", #call, cudaGetErrorString(e_)));      \
-  } while (0)
-  STEP(cudaMemsetAsync(t->d_err, 0, sizeof(int32_t), s));
-  if (nt > 0) {
-    STEP(cudaMemcpyAsync(t->d_tasks, t->h_tasks.data(), sizeof(TaskDesc) * nt,
-                         cudaMemcpyHostToDevice, s));
+  if (!dev_in && off > 0) {
+    CUDA_TRY(ctx, cudaMemcpyAsync(q.d_wire, stage.data(), sizeof(double) * off,
+                                  cudaMemcpyHostToDevice, s));
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));   // the staging vector dies here
   }
-  STEP(cudaMemcpyAsync(t->d_wire_task0, t->h_wire_task0.data(), sizeof(int32_t) * (n_wires + 1),
-                       cudaMemcpyHostToDevice, s));
-  {
-    std::vector<double> stage;
-    if (!dev_in) stage.reserve(wire_off);
-    uint64_t off = 0;
-    for (int w = 0; w < n_wires; ++w) {
-      const int64_t n = (int64_t)wires[w].W * wires[w].L;
-      if (dev_in) {
-        STEP(cudaMemcpyAsync(t->d_wire + off, wires[w].onsite, sizeof(double) * n,
-                             cudaMemcpyDeviceToDevice, s));
-        STEP(cudaMemcpyAsync(t->d_wire + off + n, wires[w].eta, sizeof(double) * n,
-                             cudaMemcpyDeviceToDevice, s));
-      } else {
-        stage.insert(stage.end(), wires[w].onsite, wires[w].onsite + n);
-        stage.insert(stage.end(), wires[w].eta, wires[w].eta + n);
-      }
-      off += 2 * n;
-    }
-    if (!dev_in && off > 0)
-      STEP(cudaMemcpyAsync(t->d_wire, stage.data(), sizeof(double) * off, cudaMemcpyHostToDevice,
-                           s));
-    if (!dev_in) STEP(cudaStreamSynchronize(s));   // the staging vector dies here
-  }
-  // ---- kernels: validation, lead modes, sweeps, block columns + weights, alias tables
   if (nt > 0) {
     if (dev_in) {
-      ProfScope ps(ctx, "validate_kernel", 2);
-      STEP(negf::launch_validate(t->d_tasks, nt, t->d_wire, t->d_err, s));
+      ProfScope ps(ctx, "validate_kernel", 2, s);
+      CUDA_TRY(ctx, negf::launch_validate(q.d_tasks, nt, q.d_wire, q.d_err, s));
     }
-    {
-      ProfScope ps(ctx, "lead_modes_kernel");
-      STEP(negf::launch_lead_modes(t->d_tasks, nt, t->max_W, t->d_wire, d_phi,
-                                   reinterpret_cast<float*>(d_phi + phi_off), d_eta32, t->d_sig,
-                                   t->d_gam, t->d_err, s));
-    }
-    {
-      ProfScope ps(ctx, "rgf_sweep_kernel");
-      STEP(negf::launch_rgf_sweep(t->d_tasks, nt, t->max_W, prec, t->d_wire, d_phi, t->d_sig,
-                                  d_gL, d_gR, t->d_err, s));
-    }
-    {
-      ProfScope ps(ctx, "diag_chain_kernels", 2);
-      STEP(negf::launch_block_columns(t->d_tasks, nt, col_base, t->max_W, prec, t->d_wire,
-                                      d_eta32, d_phi, reinterpret_cast<float*>(d_phi + phi_off),
-                                      t->d_sig, t->d_gam, d_gL, d_gR, d_start, d_weights,
-                                      t->d_rowsum, t->d_mode_w, t->d_c, t->d_err, s));
-    }
-    {
-      ProfScope ps(ctx, "alias_kernel");
-      STEP(negf::launch_alias_build(t->d_tasks, nt, t->total_jobs, t->max_K, prec, d_weights,
-                                    t->d_rowsum, t->d_mode_w, t->d_tab, t->d_mode_tab,
-                                    t->d_err, s));
-    }
+    ProfScope ps(ctx, "lead_modes_kernel", 1, s);
+    CUDA_TRY(ctx, negf::launch_lead_modes(q.d_tasks, nt, P.max_W, q.d_wire, q.d_phi,
+                                          reinterpret_cast<float*>(q.d_phi + P.phi_total),
+                                          q.d_eta32, q.d_sig, q.d_gam, q.d_err, s));
   }
-#undef STEP
-  dfree(d_gL, s);
-  dfree(d_gR, s);
-  dfree(d_start, s);
-  dfree(d_phi, s);
-  dfree(d_eta32, s);
-  t->bytes -= (2 * std::max<uint64_t>(g_off * cw, 1) + std::max<uint64_t>(start_off * cw, 1) +
-               std::max<uint64_t>((uint64_t)phi_off + (phi_off + 1) / 2, 1)) * sizeof(double) +
-              std::max<uint64_t>(wire_off / 2, 1) * sizeof(float);
-  if (o.keep_weights) {
-    t->d_weights = d_weights;
-    t->bytes += std::max<uint64_t>(tab_off, 1) * wsz;
-  } else {
-    cudaFreeAsync(d_weights, s);
+  return NEGF_OK;
+}
+
+// RGF sweeps of every task of the batch (one launch: the sweep is a sequential chain per task,
+// so its latency is paid once) into gL / gR at the tasks' global offsets.
+negf_status sweep_all(negf_ctx ctx, cudaStream_t s, const Plan& P, const Persist& q, int prec,
+                      void* d_gL, void* d_gR) {
+  const int nt = (int)P.tasks.size();
+  if (nt == 0) return NEGF_OK;
+  ProfScope ps(ctx, "rgf_sweep_kernel", 1, s);
+  CUDA_TRY(ctx, negf::launch_rgf_sweep(q.d_tasks, nt, P.max_W, prec, q.d_wire, q.d_phi, q.d_sig,
+                                       d_gL, d_gR, q.d_err, s));
+  return NEGF_OK;
+}
+
+// Enqueue the rest of the build of one wave on stream s (the sweeps are done): diagonal blocks
+// + chains (weights), alias tables into d_tab.  Scratch is allocated and freed on s; the
+// weights go to *weights_out when it is non-null (kept), else they are freed too.  Row sums go
+// to d_rowsum.
+negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& w,
+                       TaskDesc* d_wdesc, const Persist& q, int prec, const void* d_gL,
+                       const void* d_gR, uint64_t* d_tab, double* d_rowsum, void** weights_out,
+                       void* d_green = nullptr, void* d_gphi = nullptr) {
+  const int nt = w.t1 - w.t0;
+  if (nt == 0) return NEGF_OK;
+  const uint64_t cw = negf::block_bytes(prec) / sizeof(double);
+  const size_t wsz = prec == NEGF_FP64 ? sizeof(double) : sizeof(float);
+  double* d_start = nullptr;
+  void* d_weights = nullptr;
+  cudaError_t e = dalloc(&d_start, w.start * cw, s, nullptr);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_weights, std::max<uint64_t>(w.tab, 1) * wsz, s);
+  auto cleanup = [&]() {
+    dfree(d_start, s);
+    if (d_weights) cudaFreeAsync(d_weights, s);
+    d_weights = nullptr;
+  };
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(ctx, e == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,
+                "build scratch allocation: %s", cudaGetErrorString(e));
+  }
+  {
+    ProfScope ps(ctx, "diag_chain_kernels", 2, s);
+    e = negf::launch_block_columns(d_wdesc, nt, w.cols, P.max_W, prec, q.d_wire, q.d_eta32,
+                                   q.d_phi, reinterpret_cast<float*>(q.d_phi + P.phi_total),
+                                   q.d_sig, q.d_gam, d_gL, d_gR, d_start, d_weights, d_rowsum,
+                                   q.d_mode_w, q.d_c + 2 * (size_t)w.t0, q.d_err, d_green,
+                                   d_gphi, s);
+  }
+  if (e == cudaSuccess) {
+    ProfScope ps(ctx, "alias_kernel", 1, s);
+    e = negf::launch_alias_build(d_wdesc, nt, w.rows, P.max_K, prec, d_weights, d_rowsum,
+                                 q.d_mode_w, d_tab, q.d_mode_tab, q.d_err, s);
+  }
+  if (e != cudaSuccess) {
+    cleanup();
+    return fail(ctx, NEGF_E_CUDA, "table build: %s", cudaGetErrorString(e));
+  }
+  if (weights_out) {
+    *weights_out = d_weights;
+    d_weights = nullptr;
+  }
+  cleanup();
+  return NEGF_OK;
+}
+
+void adopt_persist(negf_tables t, const Persist& q) {
+  t->d_tasks = q.d_tasks;
+  t->d_wire_task0 = q.d_wire_task0;
+  t->d_wire = q.d_wire;
+  t->d_sig = q.d_sig;
+  t->d_gam = q.d_gam;
+  t->d_mode_tab = q.d_mode_tab;
+  t->d_mode_w = q.d_mode_w;
+  t->d_c = q.d_c;
+  t->d_err = q.d_err;
+}
+
+negf_status check_opts(negf_ctx ctx, const negf_build_opts* opts, negf_build_opts& o) {
+  o = negf_build_opts{NEGF_FP64, NEGF_MEM_HOST, 0, 0};
+  if (opts) o = *opts;
+  if (o.precision < NEGF_FP64 || o.precision > NEGF_SPLIT_TF32)
+    return fail(ctx, NEGF_E_INVALID, "unknown precision %d", o.precision);
+  if (o.memspace != NEGF_MEM_HOST && o.memspace != NEGF_MEM_DEVICE)
+    return fail(ctx, NEGF_E_INVALID, "unknown memspace %d", o.memspace);
+  if (o.keep_green < 0) return fail(ctx, NEGF_E_INVALID, "build opts: keep_green < 0");
+  return NEGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
+                              const negf_build_opts* opts, negf_tables* out) {
+  if (!ctx) return NEGF_E_INVALID;
+  if (!out) return fail(ctx, NEGF_E_INVALID, "negf_build_tables: out is NULL");
+  *out = nullptr;
+  if (n_wires < 0 || (n_wires > 0 && !wires))
+    return fail(ctx, NEGF_E_INVALID, "negf_build_tables: bad wire list");
+  negf_build_opts o;
+  negf_status st = check_opts(ctx, opts, o);
+  if (st != NEGF_OK) return st;
+  const bool dev_in = o.memspace == NEGF_MEM_DEVICE;
+  const int prec = o.precision == NEGF_FP64 ? NEGF_FP64 : NEGF_FP32;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = ctx->stream;
+  Plan P;
+  st = make_plan(ctx, wires, n_wires, dev_in, P);
+  if (st != NEGF_OK) return st;
+  negf_tables t = new (std::nothrow) negf_tables_s;
+  if (!t) return fail(ctx, NEGF_E_NOMEM, "negf_build_tables: host allocation");
+  t->ctx = ctx;
+  t->n_wires = n_wires;
+  t->precision = prec;
+  t->h_tasks = P.tasks;
+  t->h_wire_task0 = P.wire_task0;
+  t->n_tasks = (int)P.tasks.size();
+  t->max_W = P.max_W;
+  t->max_L = P.max_L;
+  t->max_K = P.max_K;
+  Persist q;
+  st = setup_batch(ctx, s, wires, n_wires, dev_in, P, q, &t->bytes);
+  adopt_persist(t, q);
+  if (st != NEGF_OK) {
+    free_persist_scratch(q, s);
+    release_tables(t);
+    return st;
+  }
+  // one wave holding every task: its rebased descriptors equal the global ones
+  const Wave w = make_wave(P, 0, t->n_tasks);
+  t->total_jobs = w.rows;
+  cudaError_t e = dalloc(&t->d_tab, w.tab, s, &t->bytes);
+  if (e == cudaSuccess) e = dalloc(&t->d_rowsum, w.rows, s, &t->bytes);
+  if (e != cudaSuccess) {
+    free_persist_scratch(q, s);
+    release_tables(t);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,
+                "table allocation: %s", cudaGetErrorString(e));
+  }
+  void* kept = nullptr;
+  t->score_stride = w.tab;
+  t->mode_stride = P.mode_total;
+  if (o.keep_green) {
+    const uint64_t cb = negf::block_bytes(prec);
+    e = cudaMallocAsync(&t->d_green, std::max<uint64_t>(w.green, 1) * cb, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&t->d_gphi, std::max<uint64_t>(w.gphi, 1) * cb, s);
+    if (e != cudaSuccess) {
+      free_persist_scratch(q, s);
+      release_tables(t);
+      return fail(ctx, e == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,
+                  "allocation of the kept Green's functions: %s", cudaGetErrorString(e));
+    }
+    t->green_total = w.green;
+    t->gphi_total = w.gphi;
+    t->bytes += (w.green + w.gphi) * cb;
+  }
+  void* d_gL = nullptr;
+  void* d_gR = nullptr;
+  {
+    const uint64_t gb = std::max<uint64_t>(P.g_total, 1) * negf::block_bytes(prec);
+    e = cudaMallocAsync(&d_gL, gb, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_gR, gb, s);
+  }
+  if (e != cudaSuccess) st = fail(ctx, NEGF_E_NOMEM, "RGF scratch: %s", cudaGetErrorString(e));
+  if (st == NEGF_OK) st = sweep_all(ctx, s, P, q, prec, d_gL, d_gR);
+  if (st == NEGF_OK)
+    st = build_wave(ctx, s, P, w, t->d_tasks, q, prec, d_gL, d_gR, t->d_tab, t->d_rowsum,
+                    (o.keep_weights || o.keep_green) ? &kept : nullptr, t->d_green, t->d_gphi);
+  if (d_gL) cudaFreeAsync(d_gL, s);
+  if (d_gR) cudaFreeAsync(d_gR, s);
+  if (o.keep_green) {
+    t->d_phi = q.d_phi;          // the gradient needs the transverse modes
+    q.d_phi = nullptr;
+  }
+  free_persist_scratch(q, s);
+  if (st != NEGF_OK) {
+    release_tables(t);
+    return st;
+  }
+  if (kept) {
+    t->d_weights = kept;
+    t->bytes += std::max<uint64_t>(w.tab, 1) * (prec == NEGF_FP64 ? 8 : 4);
   }
   *out = t;
+  return NEGF_OK;
+}
+
+negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
+                     const negf_build_opts* bopts, const negf_run_opts* ropts,
+                     negf_tables* out_tasks, negf_tally* out_tally) {
+  if (!ctx) return NEGF_E_INVALID;
+  if (!out_tasks || !out_tally || !ropts)
+    return fail(ctx, NEGF_E_INVALID, "negf_run: NULL output or options");
+  *out_tasks = nullptr;
+  *out_tally = nullptr;
+  if (n_wires < 0 || (n_wires > 0 && !wires))
+    return fail(ctx, NEGF_E_INVALID, "negf_run: bad wire list");
+  negf_build_opts o;
+  negf_status st = check_opts(ctx, bopts, o);
+  if (st != NEGF_OK) return st;
+  if (o.keep_weights) return fail(ctx, NEGF_E_INVALID, "negf_run releases tables; keep_weights must be 0");
+  const negf_run_opts& r = *ropts;
+  if (r.start_lead != 0 && r.start_lead != 1)
+    return fail(ctx, NEGF_E_INVALID, "negf_run: start_lead must be 0 or 1");
+  if (r.max_steps < 1 || r.max_steps > NEGF_MAX_STEPS)
+    return fail(ctx, NEGF_E_INVALID, "negf_run: max_steps must be in [1, %u]", NEGF_MAX_STEPS);
+  if (r.walkers_per_task > (1ull << 40) || r.tasks_per_wave < 0 || r.waves_in_flight < 0 ||
+      r.walk_blocks_per_sm < 0 || r.reserved != 0)
+    return fail(ctx, NEGF_E_INVALID, "negf_run: bad walker count, wave size, depth or reserved");
+  const bool dev_in = o.memspace == NEGF_MEM_DEVICE;
+  const int prec = o.precision == NEGF_FP64 ? NEGF_FP64 : NEGF_FP32;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = ctx->stream;
+  if (!ctx->walk_stream &&
+      cudaStreamCreateWithFlags(&ctx->walk_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(ctx, NEGF_E_CUDA, "negf_run: stream creation failed");
+  cudaStream_t sw = ctx->walk_stream;
+  Plan P;
+  st = make_plan(ctx, wires, n_wires, dev_in, P);
+  if (st != NEGF_OK) return st;
+  const int nt = (int)P.tasks.size();
+  negf_tables t = new (std::nothrow) negf_tables_s;
+  negf_tally tl = new (std::nothrow) negf_tally_s;
+  if (!t || !tl) {
+    delete t;
+    delete tl;
+    return fail(ctx, NEGF_E_NOMEM, "negf_run: host allocation");
+  }
+  t->ctx = ctx;
+  t->n_wires = n_wires;
+  t->precision = prec;
+  t->h_tasks = P.tasks;
+  t->h_wire_task0 = P.wire_task0;
+  t->n_tasks = nt;
+  t->max_W = P.max_W;
+  t->max_L = P.max_L;
+  t->max_K = P.max_K;
+  t->tables_released = true;
+  tl->ctx = ctx;
+  tl->n_tasks = nt;
+  tl->start_lead = r.start_lead;
+  Persist q;
+  st = setup_batch(ctx, s, wires, n_wires, dev_in, P, q, &t->bytes);
+  adopt_persist(t, q);
+  cudaError_t e = cudaSuccess;
+  if (st == NEGF_OK) {
+    e = dalloc(&tl->d_counts, (size_t)std::max(1, nt) * NEGF_TALLY_FIELDS, s, nullptr);
+    if (e == cudaSuccess)
+      e = cudaMemsetAsync(tl->d_counts, 0,
+                          sizeof(uint64_t) * (size_t)std::max(1, nt) * NEGF_TALLY_FIELDS, s);
+    if (e != cudaSuccess) st = fail(ctx, NEGF_E_CUDA, "negf_run: tally: %s", cudaGetErrorString(e));
+  }
+  // ---- waves: consecutive tasks whose tables and scratch fit the budget (depth waves in flight)
+  const int depth = r.waves_in_flight > 0 ? r.waves_in_flight : 2;
+  uint64_t budget = r.memory_budget;
+  if (budget == 0) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    budget = free_b / 2;
+  }
+  const int per_wave = r.tasks_per_wave > 0 ? r.tasks_per_wave : std::max(1, (nt + 7) / 8);
+  std::vector<uint64_t> task_bytes(nt);
+  for (int k = 0; k < nt; ++k) task_bytes[k] = wave_bytes(make_wave(P, k, k + 1), prec);
+  std::vector<Wave> waves;
+  for (int k = 0; k < nt && st == NEGF_OK;) {
+    int k1 = k + 1;
+    uint64_t bytes_w = task_bytes[k];
+    while (k1 < nt && k1 - k < per_wave && (bytes_w + task_bytes[k1]) * depth <= budget)
+      bytes_w += task_bytes[k1++];
+    waves.push_back(make_wave(P, k, k1));
+    k = k1;
+  }
+  TaskDesc* d_wdesc = nullptr;
+  if (st == NEGF_OK && nt > 0) {
+    std::vector<TaskDesc> all;
+    for (const Wave& w : waves) all.insert(all.end(), w.desc.begin(), w.desc.end());
+    e = dalloc(&d_wdesc, all.size(), s, nullptr);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_wdesc, all.data(), sizeof(TaskDesc) * all.size(),
+                          cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // `all` dies here
+    if (e != cudaSuccess) st = fail(ctx, NEGF_E_CUDA, "negf_run: descriptors: %s", cudaGetErrorString(e));
+  }
+  // ---- RGF sweeps of every task, once
+  void* d_gL = nullptr;
+  void* d_gR = nullptr;
+  if (st == NEGF_OK && nt > 0) {
+    const uint64_t gb = std::max<uint64_t>(P.g_total, 1) * negf::block_bytes(prec);
+    e = cudaMallocAsync(&d_gL, gb, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_gR, gb, s);
+    if (e != cudaSuccess) st = fail(ctx, NEGF_E_NOMEM, "negf_run: RGF scratch: %s", cudaGetErrorString(e));
+    if (st == NEGF_OK) st = sweep_all(ctx, s, P, q, prec, d_gL, d_gR);
+  }
+  // ---- pipeline: build wave w on the context stream while wave w-1 walks on the second one
+  std::vector<cudaEvent_t> built(waves.size(), nullptr), walked(waves.size(), nullptr);
+  for (size_t w = 0; w < waves.size() && st == NEGF_OK; ++w) {
+    const Wave& wv = waves[w];
+    if (cudaEventCreateWithFlags(&built[w], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&walked[w], cudaEventDisableTiming) != cudaSuccess) {
+      st = fail(ctx, NEGF_E_CUDA, "negf_run: event creation failed");
+      break;
+    }
+    if (w >= (size_t)depth) cudaStreamWaitEvent(s, walked[w - depth], 0);
+    uint64_t* d_tab = nullptr;
+    double* d_rs = nullptr;
+    e = dalloc(&d_tab, wv.tab, s, nullptr);
+    if (e == cudaSuccess) e = dalloc(&d_rs, wv.rows, s, nullptr);
+    if (e != cudaSuccess) {
+      dfree(d_tab, s);
+      dfree(d_rs, s);
+      st = fail(ctx, e == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,
+                "negf_run: wave %zu tables: %s", w, cudaGetErrorString(e));
+      break;
+    }
+    size_t off = 0;
+    for (size_t v = 0; v < w; ++v) off += waves[v].desc.size();
+    st = build_wave(ctx, s, P, wv, d_wdesc + off, q, prec, d_gL, d_gR, d_tab, d_rs, nullptr);
+    dfree(d_rs, s);
+    if (st != NEGF_OK) {
+      dfree(d_tab, s);
+      break;
+    }
+    cudaEventRecord(built[w], s);
+    cudaStreamWaitEvent(sw, built[w], 0);
+    {
+      ProfScope ps(ctx, "walk_kernel", (uint64_t)(wv.t1 - wv.t0 + 1023) / 1024, sw);
+      e = negf::launch_walk(d_wdesc + off, 0, wv.t1 - wv.t0, (uint32_t)wv.t0, d_tab,
+                            q.d_mode_tab, q.d_c + 2 * (size_t)wv.t0, r.start_lead, r.seed,
+                            r.walkers_per_task, r.walker_id_offset, r.max_steps, ctx->d_counter,
+                            tl->d_counts + (size_t)wv.t0 * NEGF_TALLY_FIELDS, nullptr, nullptr,
+                            nullptr, 0, nullptr, 0, ctx->sm_count, r.walk_blocks_per_sm, sw);
+    }
+    cudaFreeAsync(d_tab, sw);
+    cudaEventRecord(walked[w], sw);
+    if (e != cudaSuccess) st = fail(ctx, NEGF_E_CUDA, "negf_run: walk: %s", cudaGetErrorString(e));
+  }
+  // ---- join: the context stream waits for the last walk
+  if (!waves.empty() && walked.back()) cudaStreamWaitEvent(s, walked.back(), 0);
+  else {
+    cudaEvent_t j = nullptr;
+    if (cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess) {
+      cudaEventRecord(j, sw);
+      cudaStreamWaitEvent(s, j, 0);
+      cudaEventDestroy(j);
+    }
+  }
+  for (size_t w = 0; w < waves.size(); ++w) {
+    if (built[w]) cudaEventDestroy(built[w]);
+    if (walked[w]) cudaEventDestroy(walked[w]);
+  }
+  dfree(d_wdesc, s);
+  if (d_gL) cudaFreeAsync(d_gL, s);
+  if (d_gR) cudaFreeAsync(d_gR, s);
+  free_persist_scratch(q, s);
+  if (st != NEGF_OK) {
+    if (tl->d_counts) cudaFreeAsync(tl->d_counts, s);
+    delete tl;
+    release_tables(t);
+    return st;
+  }
+  t->n_waves = (int)waves.size();
+  *out_tasks = t;
+  *out_tally = tl;
+  return NEGF_OK;
+}
+
+int32_t negf_tables_num_waves(negf_tables t) { return t ? t->n_waves : 0; }
+
+negf_status negf_probe_gather(negf_ctx ctx, uint64_t table_bytes, int32_t ilp, int32_t chain,
+                              double* gathers_per_s) {
+  if (!ctx || !gathers_per_s) return NEGF_E_INVALID;
+  DeviceGuard g(ctx->device);
+  uint64_t n = 0;
+  float ms = 0.f;
+  cudaError_t e = negf::probe_gather(table_bytes, ilp, chain, ctx->sm_count, &n, &ms, ctx->stream);
+  if (e == cudaErrorInvalidValue)
+    return fail(ctx, NEGF_E_INVALID, "negf_probe_gather: table must hold 2 .. 2^32 entries");
+  if (e != cudaSuccess) return fail(ctx, NEGF_E_CUDA, "negf_probe_gather: %s", cudaGetErrorString(e));
+  *gathers_per_s = ms > 0.f ? (double)n / (ms * 1e-3) : 0.0;
   return NEGF_OK;
 }
 
@@ -591,6 +952,8 @@ negf_status negf_get_task_info(negf_ctx ctx, negf_tables t, int32_t task, negf_t
   out->K = d.K;
   out->rows = d.rows;
   out->reserved = 0;
+  out->table_offset = d.tab_off;
+  out->mode_offset = d.mode_off;
   out->energy = d.E;
   out->energy_weight = d.w_E;
   out->c[0] = c[0];
@@ -615,6 +978,8 @@ negf_status negf_export_tables(negf_ctx ctx, negf_tables t, int32_t task, int32_
     case NEGF_EXPORT_ROWSUM: need = sizeof(double) * (size_t)d.rows; break;
     default: return fail(ctx, NEGF_E_INVALID, "unknown export kind %d", what);
   }
+  if (t->tables_released && (what == NEGF_EXPORT_ALIAS || what == NEGF_EXPORT_ROWSUM))
+    return fail(ctx, NEGF_E_INVALID, "the alias tables of this handle were released (negf_run)");
   if (!host_buf) { *bytes = need; return NEGF_OK; }
   if (*bytes < need) return fail(ctx, NEGF_E_INVALID, "export buffer too small (%zu < %zu)", *bytes, need);
   DeviceGuard g(ctx->device);
@@ -685,9 +1050,10 @@ negf_status negf_walk(negf_ctx ctx, negf_tables t, int32_t start_lead, uint64_t 
                       ctx->stream);
   if (e == cudaSuccess) {
     ProfScope ps(ctx, "walk_kernel", (t->n_tasks + 1023) / 1024);
-    e = negf::launch_walk(t->d_tasks, 0, t->n_tasks, t->d_tab, t->d_mode_tab, t->d_c, start_lead,
-                          seed, walkers_per_task, walker_id_offset, max_steps, ctx->d_counter,
-                          tl->d_counts, nullptr, nullptr, ctx->sm_count, ctx->stream);
+    e = negf::launch_walk(t->d_tasks, 0, t->n_tasks, 0, t->d_tab, t->d_mode_tab, t->d_c,
+                          start_lead, seed, walkers_per_task, walker_id_offset, max_steps,
+                          ctx->d_counter, tl->d_counts, nullptr, nullptr, nullptr, 0, nullptr,
+                          0, ctx->sm_count, 0, ctx->stream);
   }
   if (e != cudaSuccess) {
     cudaFreeAsync(tl->d_counts, ctx->stream);
@@ -711,9 +1077,10 @@ negf_status negf_walk_trace(negf_ctx ctx, negf_tables t, int32_t task, int32_t s
   CUDA_TRY(ctx, dalloc(&tmp, NEGF_TALLY_FIELDS, ctx->stream, nullptr));
   cudaError_t e = cudaMemsetAsync(tmp, 0, sizeof(uint64_t) * NEGF_TALLY_FIELDS, ctx->stream);
   if (e == cudaSuccess)
-    e = negf::launch_walk(t->d_tasks, task, 1, t->d_tab, t->d_mode_tab, t->d_c, start_lead, seed,
-                          n_walkers, walker_id_offset, max_steps, ctx->d_counter, tmp, d_lead,
-                          d_steps, ctx->sm_count, ctx->stream);
+    e = negf::launch_walk(t->d_tasks, task, 1, 0, t->d_tab, t->d_mode_tab, t->d_c, start_lead,
+                          seed, n_walkers, walker_id_offset, max_steps, ctx->d_counter, tmp,
+                          d_lead, d_steps, nullptr, 0, nullptr, 0, ctx->sm_count, 0,
+                          ctx->stream);
   cudaFreeAsync(tmp, ctx->stream);
   if (e != cudaSuccess) return fail(ctx, NEGF_E_CUDA, "negf_walk_trace: %s", cudaGetErrorString(e));
   return NEGF_OK;
@@ -748,12 +1115,215 @@ negf_status negf_tally_accumulate(negf_ctx ctx, negf_tally tl, const uint64_t* h
   return NEGF_OK;
 }
 
+negf_status negf_walk_score(negf_ctx ctx, negf_tables t, int32_t start_lead, uint64_t seed,
+                            uint64_t walkers_per_task, uint64_t walker_id_offset,
+                            uint32_t max_steps, negf_tally* out) {
+  negf_status st = walk_common(ctx, t, start_lead, max_steps, "negf_walk_score");
+  if (st != NEGF_OK) return st;
+  if (!out) return fail(ctx, NEGF_E_INVALID, "negf_walk_score: out is NULL");
+  *out = nullptr;
+  if (t->tables_released || !t->d_tab)
+    return fail(ctx, NEGF_E_INVALID, "negf_walk_score: the tables of this handle were released");
+  if (walkers_per_task > (1ull << 40))
+    return fail(ctx, NEGF_E_INVALID, "negf_walk_score: walkers_per_task above 2^40");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = ctx->stream;
+  negf_tally tl = new (std::nothrow) negf_tally_s;
+  if (!tl) return fail(ctx, NEGF_E_NOMEM, "negf_walk_score: host allocation");
+  tl->ctx = ctx;
+  tl->n_tasks = t->n_tasks;
+  tl->start_lead = start_lead;
+  tl->score_stride = t->score_stride;
+  tl->mode_stride = t->mode_stride;
+  const size_t nc = (size_t)std::max(1, t->n_tasks) * NEGF_TALLY_FIELDS;
+  cudaError_t e = dalloc(&tl->d_counts, nc, s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&tl->d_score, 2 * std::max<uint64_t>(tl->score_stride, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&tl->d_mode_score, 2 * (size_t)std::max<uint32_t>(tl->mode_stride, 1), s, nullptr);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tl->d_counts, 0, sizeof(uint64_t) * nc, s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(tl->d_score, 0, sizeof(uint64_t) * 2 * std::max<uint64_t>(tl->score_stride, 1), s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(tl->d_mode_score, 0,
+                        sizeof(uint64_t) * 2 * std::max<uint32_t>(tl->mode_stride, 1), s);
+  if (e == cudaSuccess) {
+    ProfScope ps(ctx, "walk_score_kernel", (t->n_tasks + 1023) / 1024);
+    e = negf::launch_walk(t->d_tasks, 0, t->n_tasks, 0, t->d_tab, t->d_mode_tab, t->d_c,
+                          start_lead, seed, walkers_per_task, walker_id_offset, max_steps,
+                          ctx->d_counter, tl->d_counts, nullptr, nullptr, tl->d_score,
+                          tl->score_stride, tl->d_mode_score, tl->mode_stride, ctx->sm_count, 0,
+                          s);
+  }
+  if (e != cudaSuccess) {
+    negf_tally_free(tl);
+    return fail(ctx, NEGF_E_CUDA, "negf_walk_score: %s", cudaGetErrorString(e));
+  }
+  *out = tl;
+  return NEGF_OK;
+}
+
+negf_status negf_tally_score_counts(negf_ctx ctx, negf_tally tl, uint64_t* host_counts,
+                                    uint64_t* host_mode_counts) {
+  if (!ctx || !tl || tl->ctx != ctx || !tl->d_score || !host_counts || !host_mode_counts)
+    return fail(ctx, NEGF_E_INVALID, "negf_tally_score_counts: bad argument or no score tallies");
+  DeviceGuard g(ctx->device);
+  CUDA_TRY(ctx, cudaMemcpyAsync(host_counts, tl->d_score, sizeof(uint64_t) * 2 * tl->score_stride,
+                                cudaMemcpyDeviceToHost, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(host_mode_counts, tl->d_mode_score,
+                                sizeof(uint64_t) * 2 * tl->mode_stride, cudaMemcpyDeviceToHost,
+                                ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return NEGF_OK;
+}
+
+negf_status negf_tally_score_accumulate(negf_ctx ctx, negf_tally tl, const uint64_t* host_counts,
+                                        const uint64_t* host_mode_counts) {
+  if (!ctx || !tl || tl->ctx != ctx || !tl->d_score || !host_counts || !host_mode_counts)
+    return fail(ctx, NEGF_E_INVALID, "negf_tally_score_accumulate: bad argument or no score tallies");
+  std::vector<uint64_t> c(2 * tl->score_stride), m(2 * (size_t)tl->mode_stride);
+  negf_status st = negf_tally_score_counts(ctx, tl, c.data(), m.data());
+  if (st != NEGF_OK) return st;
+  for (size_t i = 0; i < c.size(); ++i) c[i] += host_counts[i];
+  for (size_t i = 0; i < m.size(); ++i) m[i] += host_mode_counts[i];
+  DeviceGuard g(ctx->device);
+  CUDA_TRY(ctx, cudaMemcpyAsync(tl->d_score, c.data(), sizeof(uint64_t) * c.size(),
+                                cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaMemcpyAsync(tl->d_mode_score, m.data(), sizeof(uint64_t) * m.size(),
+                                cudaMemcpyHostToDevice, ctx->stream));
+  CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return NEGF_OK;
+}
+
+uint64_t negf_tally_score_size(negf_tally tl) { return tl ? tl->score_stride : 0; }
+uint32_t negf_tally_mode_size(negf_tally tl) { return tl ? tl->mode_stride : 0; }
+
+negf_status negf_current_backward(negf_ctx ctx, negf_tables t, negf_tally tl, double mu_p,
+                                  double mu_q, double kT, const double* dI, double* d_onsite,
+                                  double* d_eta) {
+  if (!ctx || !t || !tl || t->ctx != ctx || tl->ctx != ctx || tl->n_tasks != t->n_tasks)
+    return fail(ctx, NEGF_E_INVALID, "negf_current_backward: bad or mismatched handles");
+  if (!t->d_green || !t->d_weights || !t->d_phi)
+    return fail(ctx, NEGF_E_INVALID, "negf_current_backward: build the tables with keep_green");
+  if (!tl->d_score) return fail(ctx, NEGF_E_INVALID, "negf_current_backward: tally has no score counts (use negf_walk_score)");
+  if (!(kT > 0.0) || !isfinite(mu_p) || !isfinite(mu_q) || !isfinite(kT))
+    return fail(ctx, NEGF_E_INVALID, "negf_current_backward: need finite mu and kT > 0");
+  if (t->n_wires > 0 && (!dI || !d_onsite || !d_eta))
+    return fail(ctx, NEGF_E_INVALID, "negf_current_backward: NULL seed or output");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = ctx->stream;
+  const int nt = t->n_tasks, nw = t->n_wires, prec = t->precision;
+  const size_t cb = negf::block_bytes(prec);
+  // per-task and per-wire site offsets; the largest task sizes the scratch
+  std::vector<uint64_t> tso(nt), wso(nw);
+  uint64_t n_sites_tasks = 0, n_sites_wires = 0;
+  int max_n = 1;
+  for (int k = 0; k < nt; ++k) {
+    tso[k] = n_sites_tasks;
+    n_sites_tasks += t->h_tasks[k].n;
+    max_n = std::max(max_n, t->h_tasks[k].n);
+  }
+  for (int w = 0; w < nw; ++w) {
+    wso[w] = n_sites_wires;
+    const int k0 = t->h_wire_task0[w];
+    if (k0 < t->h_wire_task0[w + 1]) n_sites_wires += t->h_tasks[k0].n;
+  }
+  // wires without energies still own sites in the output: size them from the caller's view
+  double* d_wbar = nullptr;
+  double* d_ubar = nullptr;
+  double* d_dT = nullptr;
+  double* d_seed = nullptr;
+  double* d_out = nullptr;
+  uint64_t* d_tso = nullptr;
+  uint64_t* d_wso = nullptr;
+  void* d_Gbar = nullptr;
+  void* d_Y = nullptr;
+  cudaError_t e = dalloc(&d_wbar, std::max<uint64_t>(t->score_stride, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_ubar, std::max<uint32_t>(t->mode_stride, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_dT, 2 * std::max<uint64_t>(n_sites_tasks, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_seed, std::max(nw, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_out, 2 * std::max<uint64_t>(n_sites_wires, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_tso, std::max(nt, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_wso, std::max(nw, 1), s, nullptr);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_Gbar, (size_t)max_n * max_n * cb, s);
+  if (e == cudaSuccess) e = cudaMallocAsync(&d_Y, (size_t)max_n * max_n * cb, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_ubar, 0, sizeof(double) * std::max<uint32_t>(t->mode_stride, 1), s);
+  if (e == cudaSuccess && nt > 0)
+    e = cudaMemcpyAsync(d_tso, tso.data(), sizeof(uint64_t) * nt, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && nw > 0) {
+    e = cudaMemcpyAsync(d_wso, wso.data(), sizeof(uint64_t) * nw, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_seed, dI, sizeof(double) * nw, cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess) {
+    ProfScope ps(ctx, "backward_seeds_kernel", 1);
+    e = negf::launch_backward_seeds(t->d_tasks, nt, t->total_jobs, prec, t->d_weights, t->d_rowsum,
+                                    t->d_mode_w, t->d_c, tl->d_counts, tl->d_score,
+                                    tl->score_stride, tl->d_mode_score, tl->mode_stride,
+                                    tl->start_lead, d_wbar, d_ubar, s);
+  }
+  for (int k = 0; k < nt && e == cudaSuccess; ++k) {
+    const TaskDesc& d = t->h_tasks[k];
+    ProfScope ps(ctx, "backward_task_kernels", 8);
+    e = negf::launch_backward_task(
+        d, prec, static_cast<const char*>(t->d_green) + d.green_off * cb,
+        static_cast<const char*>(t->d_gphi) + d.gphi_off * cb, d_wbar, d_ubar,
+        t->d_wire + d.onsite_off + d.n, t->d_phi + d.phi_off, t->d_gam + d.lead_off,
+        tl->start_lead, d_Gbar, d_Y, d_dT + tso[k], d_dT + n_sites_tasks + tso[k],
+        ctx->sm_count, s);
+  }
+  if (e == cudaSuccess) {
+    ProfScope ps(ctx, "grad_sum_kernel", 1);
+    e = negf::launch_grad_sum(t->d_tasks, nw, t->d_wire_task0, d_tso, d_wso, d_dT,
+                              d_dT + n_sites_tasks, d_seed, mu_p, mu_q, kT, d_out,
+                              d_out + n_sites_wires, s);
+  }
+  std::vector<double> h(2 * n_sites_wires);
+  if (e == cudaSuccess && n_sites_wires > 0)
+    e = cudaMemcpyAsync(h.data(), d_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
+  dfree(d_wbar, s);
+  dfree(d_ubar, s);
+  dfree(d_dT, s);
+  dfree(d_seed, s);
+  dfree(d_out, s);
+  dfree(d_tso, s);
+  dfree(d_wso, s);
+  if (d_Gbar) cudaFreeAsync(d_Gbar, s);
+  if (d_Y) cudaFreeAsync(d_Y, s);
+  if (e != cudaSuccess) return fail(ctx, NEGF_E_CUDA, "negf_current_backward: %s", cudaGetErrorString(e));
+  negf_status st = check_device(ctx, t);
+  if (st != NEGF_OK) return st;
+  // scatter per wire into the caller's layout (sites of wire w at sum of n of earlier wires;
+  // wires without energies get zeros)
+  uint64_t off = 0;
+  for (int w = 0; w < nw; ++w) {
+    const int k0 = t->h_wire_task0[w];
+    const bool has = k0 < t->h_wire_task0[w + 1];
+    int n = 0;
+    if (has) n = t->h_tasks[k0].n;
+    for (int i = 0; i < n; ++i) {
+      d_onsite[off + i] = h[wso[w] + i];
+      d_eta[off + i] = h[n_sites_wires + wso[w] + i];
+    }
+    off += n;
+  }
+  std::vector<uint64_t> cnt((size_t)nt * NEGF_TALLY_FIELDS);
+  if (nt > 0) {
+    st = negf_tally_counts(ctx, tl, cnt.data());
+    if (st != NEGF_OK) return st;
+    for (int k = 0; k < nt; ++k)
+      if (cnt[(size_t)k * NEGF_TALLY_FIELDS + 3] > 0)
+        return fail(ctx, NEGF_E_STEPCAP, "negf_current_backward: truncated walks bias the gradient");
+  }
+  return NEGF_OK;
+}
+
 int32_t negf_tally_start_lead(negf_tally tl) { return tl ? tl->start_lead : -1; }
 
 void negf_tally_free(negf_tally tl) {
   if (!tl) return;
   DeviceGuard g(tl->ctx->device);
   if (tl->d_counts) cudaFreeAsync(tl->d_counts, tl->ctx->stream);
+  if (tl->d_score) cudaFreeAsync(tl->d_score, tl->ctx->stream);
+  if (tl->d_mode_score) cudaFreeAsync(tl->d_mode_score, tl->ctx->stream);
   delete tl;
 }
 

@@ -31,6 +31,8 @@ struct TaskDesc {
   uint32_t col_base;     // first block-column job of this task (L + 2 per task)
   uint32_t phi_off;      // transverse modes phi[a][m] of this wire's width (W x W)
   uint64_t start_off;    // start blocks [L + 2][W][W] complex
+  uint64_t green_off;    // dense G [n][n] (kept for the gradient)
+  uint64_t gphi_off;     // G Phi of both leads [n][2W] (kept for the gradient)
 };
 
 struct cd { double x, y; };
@@ -83,24 +85,51 @@ cudaError_t launch_block_columns(const TaskDesc* d_tasks, int n_tasks, uint32_t 
                                  const cd* d_sig, const double* d_gam, const void* d_gL,
                                  const void* d_gR, void* d_start, void* d_weights,
                                  double* d_rowsum, double* d_mode_w, double* d_c, int32_t* d_err,
-                                 cudaStream_t s);
+                                 void* d_green, void* d_gphi, cudaStream_t s);
 // Alias tables of every row (and mode row); replaces the A values in rowsum by the FP64 row
 // sums after checking them.
 cudaError_t launch_alias_build(const TaskDesc* d_tasks, int n_tasks, uint32_t total_jobs,
                                int max_K, int precision, const void* d_weights,
                                double* d_rowsum, const double* d_mode_w, uint64_t* d_tab,
                                uint64_t* d_mode_tab, int32_t* d_err, cudaStream_t s);
-// d_tally holds the counters of tasks task0 .. task0 + n_tasks - 1 (index 0 = task0).
-cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, const uint64_t* d_tab,
-                        const uint64_t* d_mode_tab, const double* d_c, int start_lead,
-                        uint64_t seed, uint64_t walkers_per_task, uint64_t id_offset,
-                        uint32_t max_steps, unsigned long long* d_counter, uint64_t* d_tally,
-                        int32_t* d_trace_lead, uint32_t* d_trace_steps, int sm_count,
+// Walks of tasks d_tasks[task0 .. task0 + n_tasks); d_c is indexed like d_tasks, d_tally holds
+// the counters of those tasks (index 0 = task0).  The Philox task number of d_tasks[k] is
+// id_base + k.  max_blocks_per_sm > 0 caps the persistent grid (leaving room for concurrent
+// kernels).  With d_score non-null every absorbed walk also adds its transitions to
+// d_score[lead][tab_off + a K + b] and its injection mode to d_mode_score[lead][mode_off + m].
+cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_t id_base,
+                        const uint64_t* d_tab, const uint64_t* d_mode_tab, const double* d_c,
+                        int start_lead, uint64_t seed, uint64_t walkers_per_task,
+                        uint64_t id_offset, uint32_t max_steps, unsigned long long* d_counter,
+                        uint64_t* d_tally, int32_t* d_trace_lead, uint32_t* d_trace_steps,
+                        uint64_t* d_score, uint64_t score_stride, uint64_t* d_mode_score,
+                        uint32_t mode_stride, int sm_count, int max_blocks_per_sm,
                         cudaStream_t s);
+// Timed random 8-byte gathers over a table of table_bytes (see k_walk.cu); synchronises s.
+cudaError_t probe_gather(uint64_t table_bytes, int ilp, int chain, int sm_count,
+                         uint64_t* gathers, float* ms, cudaStream_t s);
 cudaError_t launch_current(const TaskDesc* d_tasks, int n_tasks, int n_wires,
                            const int32_t* d_wire_task0, const double* d_c,
                            const uint64_t* d_tally, int start_lead, double mu_p, double mu_q,
                            double kT, double* d_out, cudaStream_t s);
+// Backward (score-function gradient, see k_backward.cu).
+cudaError_t launch_backward_seeds(const TaskDesc* d_tasks, int n_tasks, uint32_t n_jobs,
+                                  int precision, const void* d_weights, const double* d_rowsum,
+                                  const double* d_mode_w, const double* d_c,
+                                  const uint64_t* d_counts, const uint64_t* d_score,
+                                  uint64_t stride, const uint64_t* d_mode_score,
+                                  uint32_t mode_stride, int start_lead, double* d_wbar,
+                                  double* d_ubar, cudaStream_t s);
+cudaError_t launch_backward_task(const TaskDesc& d, int precision, const void* G,
+                                 const void* gphi, const double* wbar, const double* ubar,
+                                 const double* eta, const double* phi, const double* gam,
+                                 int start_lead, void* Gbar, void* Y, double* dV, double* dE,
+                                 int sm_count, cudaStream_t s);
+cudaError_t launch_grad_sum(const TaskDesc* d_tasks, int n_wires, const int32_t* d_wire_task0,
+                            const uint64_t* d_task_site_off, const uint64_t* d_wire_site_off,
+                            const double* dT_V, const double* dT_E, const double* d_seed,
+                            double mu_p, double mu_q, double kT, double* out_V, double* out_E,
+                            cudaStream_t s);
 cudaError_t launch_validate(const TaskDesc* d_tasks, int n_tasks, const double* d_wire,
                             int32_t* d_err, cudaStream_t s);
 

@@ -157,7 +157,7 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
   if (e == cudaSuccess)
     e = negf::launch_block_columns(d_tasks, nt, (uint32_t)(nt * (wr.L + 2)), wr.W, prec, d_wire,
                                    d_eta32, d_phi, d_phi32, d_sig, d_gam, d_gL, d_gR, d_st, d_w,
-                                   d_rs, d_mw, d_c, d_err, s);
+                                   d_rs, d_mw, d_c, d_err, nullptr, nullptr, s);
   if (e == cudaSuccess)
     e = negf::launch_alias_build(d_tasks, nt, (uint32_t)(nt * (rows + 2)), (int)K, prec, d_w,
                                  d_rs, d_mw, d_alias, d_mode_alias, d_err, s);

@@ -37,14 +37,22 @@ class negf_wire(C.Structure):
 
 class negf_build_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("memspace", C.c_int32), ("keep_weights", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("keep_green", C.c_int32)]
 
 
 class negf_task_info(C.Structure):
     _fields_ = [("wire", C.c_int32), ("energy_index", C.c_int32), ("W", C.c_int32),
                 ("L", C.c_int32), ("n", C.c_int32), ("K", C.c_int32), ("rows", C.c_int32),
                 ("reserved", C.c_int32), ("energy", C.c_double), ("energy_weight", C.c_double),
-                ("c", C.c_double * 2)]
+                ("c", C.c_double * 2), ("table_offset", C.c_uint64), ("mode_offset", C.c_uint64)]
+
+
+class negf_run_opts(C.Structure):
+    _fields_ = [("start_lead", C.c_int32), ("tasks_per_wave", C.c_int32), ("seed", C.c_uint64),
+                ("walkers_per_task", C.c_uint64), ("walker_id_offset", C.c_uint64),
+                ("max_steps", C.c_uint32), ("waves_in_flight", C.c_int32),
+                ("memory_budget", C.c_uint64), ("walk_blocks_per_sm", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 _lib = None
@@ -87,6 +95,16 @@ def load():
         "negf_current": (I32, [P, P, P, D, D, D, P, P, P, P]),
         "negf_profile_enable": (I32, [P, I32]),
         "negf_build_tables_noalloc": (I32, [C.POINTER(negf_wire), I32, P, P, P, P]),
+        "negf_run": (I32, [P, C.POINTER(negf_wire), I32, C.POINTER(negf_build_opts),
+                           C.POINTER(negf_run_opts), C.POINTER(P), C.POINTER(P)]),
+        "negf_tables_num_waves": (I32, [P]),
+        "negf_probe_gather": (I32, [P, U64, I32, I32, C.POINTER(D)]),
+        "negf_walk_score": (I32, [P, P, I32, U64, U64, U64, U32, C.POINTER(P)]),
+        "negf_tally_score_counts": (I32, [P, P, P, P]),
+        "negf_tally_score_accumulate": (I32, [P, P, P, P]),
+        "negf_tally_score_size": (U64, [P]),
+        "negf_tally_mode_size": (U32, [P]),
+        "negf_current_backward": (I32, [P, P, P, D, D, D, P, P, P]),
         "negf_profile_read": (I32, [P, I32, P, P, P, C.POINTER(I32)]),
     }
     for name, (res, args) in sig.items():
@@ -130,11 +148,7 @@ def negf_destroy(ctx):
     load().negf_destroy(ctx)
 
 
-def negf_build_tables(ctx, wires, precision="fp64", memspace="host", keep_weights=False):
-    """wires: objects with W, L, t, onsite, eta, energy, energy_weight, lead_model, gamma_lead
-    (numpy float64 arrays for memspace 'host', torch CUDA float64 tensors for 'device')."""
-    lib = load()
-    keep = []
+def _wire_array(wires, memspace, keep):
     arr = (negf_wire * max(1, len(wires)))()
     for i, w in enumerate(wires):
         if memspace == "host":
@@ -150,8 +164,40 @@ def negf_build_tables(ctx, wires, precision="fp64", memspace="host", keep_weight
         arr[i] = negf_wire(int(w.W), int(w.L), float(w.t), _ptr(on), _ptr(et), int(len(E)),
                            _ptr(E), _ptr(wE), int(getattr(w, "lead_model", 0)),
                            float(getattr(w, "gamma_lead", 0.0)))
+    return arr
+
+
+def negf_run(ctx, wires, start_lead, seed, walkers_per_task, precision="fp32", memspace="host",
+             walker_id_offset=0, max_steps=1 << 20, tasks_per_wave=0, waves_in_flight=0,
+             memory_budget=0, walk_blocks_per_sm=0):
+    """Build + walk pipelined in waves.  Returns (tasks handle, tally handle)."""
+    lib = load()
+    keep = []
+    arr = _wire_array(wires, memspace, keep)
+    bopts = negf_build_opts(PRECISION[precision], 0 if memspace == "host" else 1, 0, 0)
+    ropts = negf_run_opts(int(start_lead), int(tasks_per_wave), int(seed), int(walkers_per_task),
+                          int(walker_id_offset), int(max_steps), int(waves_in_flight),
+                          int(memory_budget), int(walk_blocks_per_sm), 0)
+    t_out, tl_out = C.c_void_p(), C.c_void_p()
+    _check(ctx, lib.negf_run(ctx, arr, len(wires), C.byref(bopts), C.byref(ropts),
+                             C.byref(t_out), C.byref(tl_out)))
+    del keep
+    return t_out, tl_out
+
+
+def negf_tables_num_waves(tables):
+    return load().negf_tables_num_waves(tables)
+
+
+def negf_build_tables(ctx, wires, precision="fp64", memspace="host", keep_weights=False,
+                      keep_green=False):
+    """wires: objects with W, L, t, onsite, eta, energy, energy_weight, lead_model, gamma_lead
+    (numpy float64 arrays for memspace 'host', torch CUDA float64 tensors for 'device')."""
+    lib = load()
+    keep = []
+    arr = _wire_array(wires, memspace, keep)
     opts = negf_build_opts(PRECISION[precision], 0 if memspace == "host" else 1,
-                           1 if keep_weights else 0, 0)
+                           1 if keep_weights else 0, 1 if keep_green else 0)
     out = C.c_void_p()
     _check(ctx, lib.negf_build_tables(ctx, arr, len(wires), C.byref(opts), C.byref(out)))
     del keep
@@ -171,7 +217,8 @@ def negf_get_task_info(ctx, tables, task):
     _check(ctx, load().negf_get_task_info(ctx, tables, int(task), C.byref(info)))
     return dict(wire=info.wire, energy_index=info.energy_index, W=info.W, L=info.L, n=info.n,
                 K=info.K, rows=info.rows, energy=info.energy, energy_weight=info.energy_weight,
-                c=np.array([info.c[0], info.c[1]]))
+                c=np.array([info.c[0], info.c[1]]), table_offset=info.table_offset,
+                mode_offset=info.mode_offset)
 
 
 def negf_tables_free(tables):
@@ -269,3 +316,46 @@ def negf_build_tables_noalloc(wire, precision, stream, d_alias, d_mode_alias, d_
     handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return load().negf_build_tables_noalloc(C.byref(w), PRECISION[precision], C.c_void_p(handle),
                                             _ptr(d_alias), _ptr(d_mode_alias), _ptr(d_c))
+
+
+def negf_probe_gather(ctx, table_bytes, ilp=8, chain=64):
+    """Achieved random 8-byte gathers per second over a device table of table_bytes."""
+    out = C.c_double(0.0)
+    _check(ctx, load().negf_probe_gather(ctx, int(table_bytes), int(ilp), int(chain),
+                                         C.byref(out)))
+    return out.value
+
+
+def negf_walk_score(ctx, tables, start_lead, seed, walkers_per_task, walker_id_offset=0,
+                    max_steps=1 << 20):
+    out = C.c_void_p()
+    _check(ctx, load().negf_walk_score(ctx, tables, int(start_lead), int(seed),
+                                       int(walkers_per_task), int(walker_id_offset),
+                                       int(max_steps), C.byref(out)))
+    return out
+
+
+def negf_tally_score_counts(ctx, tally):
+    lib = load()
+    ns, nm = lib.negf_tally_score_size(tally), lib.negf_tally_mode_size(tally)
+    c = np.zeros((2, ns), dtype=np.uint64)
+    m = np.zeros((2, nm), dtype=np.uint64)
+    _check(ctx, lib.negf_tally_score_counts(ctx, tally, c.ctypes.data, m.ctypes.data))
+    return c, m
+
+
+def negf_tally_score_accumulate(ctx, tally, counts, mode_counts):
+    c = np.ascontiguousarray(counts, dtype=np.uint64)
+    m = np.ascontiguousarray(mode_counts, dtype=np.uint64)
+    _check(ctx, load().negf_tally_score_accumulate(ctx, tally, c.ctypes.data, m.ctypes.data))
+
+
+def negf_current_backward(ctx, tables, tally, mu_p, mu_q, kT, dI, n_sites):
+    """Returns (d_onsite, d_eta, stepcap) for all sites (wire after wire)."""
+    dI = np.ascontiguousarray(dI, dtype=np.float64)
+    dV = np.zeros(max(n_sites, 1))
+    dE = np.zeros(max(n_sites, 1))
+    st = _check(ctx, load().negf_current_backward(ctx, tables, tally, float(mu_p), float(mu_q),
+                                                  float(kT), dI.ctypes.data, dV.ctypes.data,
+                                                  dE.ctypes.data), allow=(NEGF_E_STEPCAP,))
+    return dV[:n_sites], dE[:n_sites], st == NEGF_E_STEPCAP

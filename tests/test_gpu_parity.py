@@ -273,3 +273,38 @@ def test_tally_accumulate_resumes_exactly(ctx):
             negf.negf_tally_free(t)
     finally:
         negf.negf_tables_free(tables)
+
+
+def test_run_pipeline_matches_build_and_walk(ctx):
+    """negf_run (waves built on one stream while the previous wave walks on another, tables
+    freed per wave) gives bit-identical tallies to negf_build_tables + negf_walk, for uneven
+    wires and several wave sizes, and its task handle serves negf_current."""
+    wires = [inputs.small_wire(71, W=3, L=7, n_energy=3, eta=0.1),
+             inputs.small_wire(72, W=6, L=4, n_energy=2, eta=0.2),
+             inputs.small_wire(73, W=1, L=15, n_energy=4, eta=0.05, e_lo=-1.9, e_hi=1.9),
+             inputs.small_wire(74, W=9, L=3, n_energy=1, eta=0.3)]
+    n_tasks = sum(len(w.energy) for w in wires)
+    N = 30000
+    ref_t = negf.negf_build_tables(ctx, wires, precision="fp32")
+    ref_tl = negf.negf_walk(ctx, ref_t, 1, 4242, N, walker_id_offset=17)
+    ref = negf.negf_tally_counts(ctx, ref_tl, n_tasks)
+    ref_cur = negf.negf_current(ctx, ref_t, ref_tl, 3.5, -3.5, 0.025)
+    try:
+        for per_wave, budget in ((0, 0), (1, 0), (3, 0), (0, 1)):
+            t, tl = negf.negf_run(ctx, wires, 1, 4242, N, precision="fp32", walker_id_offset=17,
+                                  tasks_per_wave=per_wave, memory_budget=budget)
+            try:
+                got = negf.negf_tally_counts(ctx, tl, n_tasks)
+                assert np.array_equal(got, ref), (per_wave, budget)
+                cur = negf.negf_current(ctx, t, tl, 3.5, -3.5, 0.025)
+                assert np.array_equal(cur["T"], ref_cur["T"]) and np.array_equal(cur["I"], ref_cur["I"])
+                if budget == 1:
+                    assert negf.negf_tables_num_waves(t) == n_tasks     # one task per wave
+                with pytest.raises(negf.NegfError, match="released"):
+                    negf.negf_export_tables(ctx, t, 0, "alias")
+            finally:
+                negf.negf_tally_free(tl)
+                negf.negf_tables_free(t)
+    finally:
+        negf.negf_tally_free(ref_tl)
+        negf.negf_tables_free(ref_t)
