@@ -28,13 +28,20 @@ def terminal_transmissions(g):
     T_Pq = np.empty((probes.size, 2))
     T_qP = np.empty((2, probes.size))
     T_qp = np.empty((2, 2))
+    L, W = g["L"], g["W"]
+    sls = [slice(0, W), slice((L - 1) * W, L * W)]     # where Gamma_L, Gamma_R are nonzero
     for q in range(2):
-        GqG = G @ Gl[q] @ Gd                      # G Gamma_q G^dag
-        T_Pq[:, q] = gamma[probes] * np.real(np.diag(GqG))[probes]
-        GdqG = Gd @ Gl[q] @ G                     # G^dag Gamma_q G ; (.)_ii = T_qi / gamma_i
-        T_qP[q, :] = gamma[probes] * np.real(np.diag(GdqG))[probes]
+        sq = sls[q]
+        Gb = Gl[q][sq, sq]
+        # (G Gamma_q G^dag)_ii and (G^dag Gamma_q G)_ii, summed over the boundary slice of q
+        T_Pq[:, q] = gamma[probes] * np.real(
+            np.einsum("ia,ab,ib->i", G[:, sq], Gb, G[:, sq].conj()))[probes]
+        T_qP[q, :] = gamma[probes] * np.real(
+            np.einsum("ai,ab,bi->i", G[sq, :].conj(), Gb, G[sq, :]))[probes]
         for p in range(2):
-            T_qp[q, p] = np.real(np.trace(Gl[q] @ G @ Gl[p] @ Gd))
+            sp = sls[p]
+            # Tr[Gamma_q G Gamma_p G^dag] on the two boundary slices
+            T_qp[q, p] = np.real(np.trace(Gb @ G[sq, sp] @ Gl[p][sp, sp] @ G[sq, sp].conj().T))
     return probes, T_PP, T_Pq, T_qP, T_qp
 
 

@@ -42,7 +42,10 @@ def transition_weights(g, lead_model_modes):
     absG2 = np.abs(G) ** 2
     w[:n, :n] = absG2.T * gamma[None, :]            # w[i, j] = gamma_j |G_ji|^2
     for r in range(2):
-        w[:n, n + r] = np.real(np.diag(Gd @ Gam[r] @ G))
+        # (G^dag Gamma_r G)_ii, summed over the boundary slice where Gamma_r is nonzero
+        sl = slice((0 if r == 0 else L - 1) * W, (1 if r == 0 else L) * W)
+        Gs = G[sl, :]
+        w[:n, n + r] = np.real(np.einsum("ai,ab,bi->i", Gs.conj(), Gam[r][sl, sl], Gs))
     A_row[:n] = np.real(np.diag(A))
     # injection rows and mode distributions
     mode_w = np.zeros((2, W))

@@ -1,0 +1,97 @@
+"""Full-size configurations beyond the benchmark workload, on the GPU.
+
+* Batched uneven wires (256 wires, W in 4..32, L in 20..200, 32 energies each) through the
+  batched pipeline (negf_run) with a reduced walker count: properties that hold at any size
+  (every walker accounted for, 0 <= T <= c_p, P(L) + P(R) = 1) for all 8192 tasks, and sampled
+  small tasks against the direct probe solve (within 4.5 standard errors).
+* Differentiation case (W = 16, L = 100, 16 energies): the score-function gradient of the
+  current against the oracle's exact derivative on sampled sites (batch means, 4.5 SE).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import adjoint, buttiker, current as ocur, wire as owire  # noqa: E402
+from paper_1805_10164_gb300 import inputs, negf  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_10164_gb300 import build
+    build.build()
+    c = negf.negf_create(0)
+    yield c
+    negf.negf_destroy(c)
+
+
+def test_batched_uneven_full_size(ctx):
+    wl = inputs.batched_uneven()
+    wires = wl.wires
+    N = 20_000
+    n_tasks = sum(len(w.energy) for w in wires)
+    t, tl = negf.negf_run(ctx, wires, 0, 31337, N, precision="fp32")
+    try:
+        counts = negf.negf_tally_counts(ctx, tl, n_tasks)
+        res = negf.negf_current(ctx, t, tl, wl.mu_p, wl.mu_q, wl.kT)
+        assert not res["stepcap"]
+        assert np.all(counts[:, 0] == N)
+        c = np.array([negf.negf_get_task_info(ctx, t, k)["c"][0] for k in range(n_tasks)])
+        open_ = c > 0
+        assert np.all(counts[open_, 1] + counts[open_, 2] == N)
+        assert np.all((res["T"] >= 0) & (res["T"] <= c + 1e-12))
+        assert np.all(np.isfinite(res["I"]))
+        # sampled small tasks against the direct probe solve
+        k = 0
+        checked = 0
+        for wi, w in enumerate(wires):
+            if w.W * w.L <= 400 and checked < 4:
+                for e_idx in (3, 17):
+                    g = owire.green_retarded(w.energy[e_idx], w.onsite, w.eta, w.t)
+                    T_ref = buttiker.effective_transmission(g)[1, 0]
+                    task = k + e_idx
+                    assert abs(res["T"][task] - T_ref) <= 4.5 * res["T_se"][task] + 1e-9, (wi, e_idx)
+                checked += 1
+            k += len(w.energy)
+        assert checked >= 2
+    finally:
+        negf.negf_tally_free(tl)
+        negf.negf_tables_free(t)
+
+
+def test_differentiation_case_full_size(ctx):
+    wl = inputs.wire_16x100(precision="fp32")
+    w = wl.wires[0]
+    n = w.W * w.L
+    sites = [0, 7, 805, 1599]
+    # oracle: exact dI/dV, dI/deta on the sampled sites (sum over the 16 energies)
+    df = ocur.fermi(w.energy, wl.mu_p, wl.kT) - ocur.fermi(w.energy, wl.mu_q, wl.kT)
+    gV = np.zeros(n)
+    gE = np.zeros(n)
+    for k, E in enumerate(w.energy):
+        if df[k] * w.energy_weight[k] == 0:
+            continue
+        _, dV, dE = adjoint.transmission_gradient(w.onsite, w.eta, w.t, E, 0, 1, sites=sites)
+        gV += w.energy_weight[k] * df[k] * dV.reshape(-1)
+        gE += w.energy_weight[k] * df[k] * dE.reshape(-1)
+    tables = negf.negf_build_tables(ctx, [w], precision="fp32", keep_green=True)
+    try:
+        est = []
+        for b in range(8):
+            tally = negf.negf_walk_score(ctx, tables, 0, 99, 100_000, walker_id_offset=b * 100_000)
+            dV, dE, cap = negf.negf_current_backward(ctx, tables, tally, wl.mu_p, wl.mu_q, wl.kT,
+                                                     [1.0], n)
+            negf.negf_tally_free(tally)
+            assert not cap
+            est.append(np.concatenate([dV[sites], dE[sites]]))
+        est = np.array(est)
+        ref = np.concatenate([gV[sites], gE[sites]])
+        mean = est.mean(0)
+        se = est.std(0, ddof=1) / np.sqrt(len(est))
+        z = np.abs(mean - ref) / np.maximum(se, 1e-15)
+        assert np.all(z <= 4.5), (mean, ref, se)
+    finally:
+        negf.negf_tables_free(tables)
