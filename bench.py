@@ -27,7 +27,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1805_10164_gb300 import inputs  # noqa: E402
+from paper_1805_10164_gb300 import dist as ndist, inputs  # noqa: E402
 
 METRIC = "walker steps/s and s per lead current at 1% std error on 1 GB300; frac of roofline"
 UNIT = "walker steps/s"
@@ -63,12 +63,16 @@ class Clocks:
     def __init__(self, index):
         self.proc = None
         self.index = index
+        self.t0 = time.perf_counter()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+
+    def elapsed(self):
+        return time.perf_counter() - self.t0
 
     def stop(self):
         if self.proc is None:
@@ -176,8 +180,8 @@ def run_gpu(args):
     n_tasks = sum(len(w.energy) for w in wl.wires)
     state = {"steps": 0, "walkers": 0, "I": None, "se": None, "counts": None}
 
-    def one_step(step_idx, wires, memspace):
-        wid0 = (rank * 1000 + step_idx) * N
+    def one_step(step_idx, wires, memspace, prec=prec):
+        wid0 = ndist.weak_walker_offset(rank, step_idx, N)
         if args.mode == "pipeline":
             # build wave w+1 while wave w walks; tables are freed wave by wave
             tables, tally = negf.negf_run(ctx, wires, 0, args.seed, N, precision=prec,
@@ -220,7 +224,19 @@ def run_gpu(args):
     torch.cuda.synchronize()
     prof = negf.negf_profile_read(ctx)
     negf.negf_profile_enable(ctx, False)
+    if clocks is not None:
+        # nvidia-smi samples every 200 ms: when the timed steps were shorter than a second,
+        # keep running the same step (untimed) so that the clock record holds a few samples
+        t_soak = time.perf_counter()
+        i = 0
+        while clocks.elapsed() < 1.2 and time.perf_counter() - t_soak < 5.0:
+            flush.fill_(float(i))
+            one_step(30_000 + i, dev_wires, "device")
+            torch.cuda.synchronize()
+            i += 1
     clk = clocks.stop() if clocks else None
+    if clk is not None:
+        clk["window"] = "timed steps, then repeats of the same step until 1.2 s had passed"
     barrier(world)
     t_max = max_over_ranks(total_ms, world)
     all_steps = sum_over_ranks(float(tot_steps), world)
@@ -248,6 +264,10 @@ def run_gpu(args):
     probe_src = (f"measured: negf_probe_gather, random 8-byte gathers over {probe_tab >> 20} MiB "
                  f"(two tasks' alias tables), 8 independent chains per thread "
                  f"({probe_gps:.3g}/s; 1 chain: {probe_gps1:.3g}/s)")
+    # seconds per current at 1 % SE with FP64 tables (the plain FP64 form), for comparison
+    fp64_cmp = None
+    if args.compare_fp64 and prec != "fp64":
+        fp64_cmp = time_precision("fp64", one_step, dev_wires, negf, ctx, stream, flush, args)
     negf.negf_destroy(ctx)
     if rank != 0:
         return
@@ -304,9 +324,43 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if fp64_cmp is not None:
+        fp64_cmp["s_per_current_1pct_" + prec] = s_per_current
+        fp64_cmp["speedup_" + prec + "_over_fp64"] = fp64_cmp["s_per_current_1pct"] / s_per_current
+        out["fp64_tables"] = fp64_cmp
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(wl, args, budget_s=args.cpu_budget)
     print(json.dumps(out), flush=True)
+
+
+def time_precision(prec, one_step, dev_wires, negf, ctx, stream, flush, args, steps=3):
+    """ms per step, walk ms and s per current at 1 % SE of the same workload with tables of
+    precision ``prec`` (device-resident inputs, L2 flushed between steps)."""
+    import torch
+    for i in range(2):
+        one_step(40_000 + i, dev_wires, "device", prec)
+    torch.cuda.synchronize()
+    negf.negf_profile_enable(ctx, True)
+    tot = 0.0
+    res = None
+    for i in range(steps):
+        flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, _ = one_step(41_000 + i, dev_wires, "device", prec)
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    prof = negf.negf_profile_read(ctx)
+    negf.negf_profile_enable(ctx, False)
+    ms = tot / steps
+    walk_ms = prof.get("walk_kernel", (0, 0.0))[1] / steps
+    rel = float(res["se"][0] / abs(res["I"][0])) if res["I"][0] != 0 else float("nan")
+    return {"precision": prec, "ms_per_step": ms, "walk_ms": walk_ms, "current": float(res["I"][0]),
+            "current_rel_se": rel,
+            "s_per_current_1pct": ((ms - walk_ms) + walk_ms * (rel / 0.01) ** 2) / 1e3,
+            "kernel_ms_per_step": {k: round(v[1] / steps, 4) for k, v in prof.items()}}
 
 
 # ------------------------------------------------------------------ CPU oracle (baseline)
@@ -380,6 +434,7 @@ def main():
     ap.add_argument("--mode", default="separate", choices=["pipeline", "separate"])
     ap.add_argument("--tasks-per-wave", type=int, default=8)
     ap.add_argument("--walk-blocks-per-sm", type=int, default=4)
+    ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -58,10 +58,12 @@ typedef enum {
   NEGF_E_TIMEOUT = 6   /* a bounded device wait gave up */
 } negf_status;
 
-/* Arithmetic of the table build.  NEGF_FP64: everything in FP64.  NEGF_FP32: the W x W
- * inversions of the RGF sweeps and the diagonal blocks in FP64, the block-column propagation
- * and the transition weights in FP32, row sums and alias thresholds in FP64.
- * NEGF_SPLIT_TF32 is accepted and currently computed as NEGF_FP32. */
+/* Arithmetic of the table build.  NEGF_FP64: everything in FP64 (complex128 blocks).
+ * NEGF_FP32: lead self-energies in FP64; the W x W inversions of the RGF sweeps and of the
+ * diagonal blocks, the block-column propagation and the transition weights in complex64 /
+ * FP32; the sum-rule values <i|A|i>, row sums, mode weights and c_p in FP64; alias thresholds
+ * in exact integer arithmetic.  NEGF_SPLIT_TF32 is accepted and currently computed as
+ * NEGF_FP32. */
 typedef enum { NEGF_FP64 = 0, NEGF_FP32 = 1, NEGF_SPLIT_TF32 = 2 } negf_precision;
 
 /* Where the arrays of a negf_wire live. */

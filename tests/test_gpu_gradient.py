@@ -132,3 +132,34 @@ def test_gradient_from_walks_is_unbiased(ctx):
             assert abs(proj.mean() - g_exact @ d) <= 4.5 * se + 1e-12, (proj.mean(), g_exact @ d, se)
     finally:
         negf.negf_tables_free(tables)
+
+
+def test_autograd_function_matches_abi(ctx):
+    """NegfCurrent (torch.autograd.Function) makes exactly the C-ABI calls: same current, same
+    gradient as negf_build_tables + negf_walk_score + negf_current(_backward)."""
+    from paper_1805_10164_gb300 import autograd as nag
+    w = inputs.small_wire(83, W=3, L=5, n_energy=2, eta=0.2, e_lo=-1.0, e_hi=1.0)
+    spec = nag.CurrentSpec(W=w.W, L=w.L, t=w.t, energy=w.energy, energy_weight=w.energy_weight,
+                           mu_p=MU_P, mu_q=MU_Q, kT=KT, walkers_per_task=100_000, seed=9,
+                           precision="fp64")
+    V = torch.tensor(w.onsite, device="cuda", requires_grad=True)
+    eta = torch.tensor(w.eta, device="cuda", requires_grad=True)
+    I, se = nag.current(V, eta, ctx, spec)
+    (3.0 * I).backward()
+    tables = negf.negf_build_tables(ctx, [w], precision="fp64", keep_green=True)
+    tally = negf.negf_walk_score(ctx, tables, 0, 9, 100_000)
+    try:
+        res = negf.negf_current(ctx, tables, tally, MU_P, MU_Q, KT)
+        dV, dE, cap = negf.negf_current_backward(ctx, tables, tally, MU_P, MU_Q, KT, [3.0],
+                                                 w.W * w.L)
+    finally:
+        negf.negf_tally_free(tally)
+        negf.negf_tables_free(tables)
+    assert not cap
+    assert I.item() == res["I"][0] and se.item() == res["se"][0]
+    np.testing.assert_allclose(V.grad.cpu().numpy().reshape(-1), dV, rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(eta.grad.cpu().numpy().reshape(-1), dE, rtol=1e-12, atol=1e-15)
+    # without a gradient the plain walk runs: same walks, same current
+    with torch.no_grad():
+        I2, _ = nag.current(V, eta, ctx, spec)
+    assert I2.item() == I.item()

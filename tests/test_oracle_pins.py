@@ -376,6 +376,47 @@ def test_pins_catch_a_wrong_lead_sign(monkeypatch):
     assert not np.allclose(tab["w"].sum(1), tab["A_row"], rtol=1e-6)
 
 
+def _vary_eta(seed, W, L):
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1, 1, (L, W)), rng.uniform(0.05, 0.4, (L, W))
+
+
+def test_pins_catch_transposed_site_weights(monkeypatch):
+    """Plant gamma_i |G_ij|^2 in place of gamma_j |G_ji|^2 (source and destination swapped):
+    the walk's exact expectation must leave the direct probe solve."""
+    orig = markov.transition_weights
+
+    def broken(g, modes):
+        tab = orig(g, modes)
+        n = tab["n"]
+        tab["w"][:n, :n] = np.abs(g["G"]) ** 2 * g["gamma"][:, None]
+        return tab
+
+    on, et = _vary_eta(12, 2, 5)
+    good = pipeline.task_reference(on, et, 1.0, 0.4, with_alias=False)
+    assert abs(good["exact"]["T_eff"][1, 0] - good["T_direct"][1, 0]) <= 1e-10
+    monkeypatch.setattr(markov, "transition_weights", broken)
+    r = pipeline.task_reference(on, et, 1.0, 0.4, with_alias=False)
+    assert abs(r["exact"]["T_eff"][1, 0] - r["T_direct"][1, 0]) > 1e-4 * r["T_direct"][1, 0]
+
+
+def test_pins_catch_a_dropped_self_transition(monkeypatch):
+    """Plant j != i in the Step 6' sum (drop the self-transition): the row-sum pin fails."""
+    orig = markov.transition_weights
+
+    def broken(g, modes):
+        tab = orig(g, modes)
+        n = tab["n"]
+        tab["w"][np.arange(n), np.arange(n)] = 0.0
+        return tab
+
+    monkeypatch.setattr(markov, "transition_weights", broken)
+    on, et = _vary_eta(13, 2, 4)
+    r = pipeline.task_reference(on, et, 1.0, -0.6, with_alias=False)
+    tab = r["tab"]
+    assert not np.allclose(tab["w"].sum(1), tab["A_row"], rtol=1e-6)
+
+
 # ---------------------------------------------------------------- gradients
 
 @pytest.mark.parametrize("seed,W,L,E,lm", [(21, 3, 5, 0.4, 0), (22, 1, 8, -0.7, 0), (23, 2, 4, 1.1, 1)])
