@@ -178,10 +178,23 @@ def run_gpu(args):
     ctx = negf.negf_create(local, stream)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     n_tasks = sum(len(w.energy) for w in wl.wires)
-    state = {"steps": 0, "walkers": 0, "I": None, "se": None, "counts": None}
+    plan = None
+    plan_prec = prec
+    tuning = None
+    if args.mode == "graph":
+        # the whole step captured once (device-resident inputs re-read by every launch);
+        # launch shapes picked by the library's autotuner on this workload
+        plan = negf.negf_plan_create(ctx, dev_wires, 0, N, wl.mu_p, wl.mu_q, wl.kT,
+                                     precision=prec, memspace="device", max_steps=args.max_steps,
+                                     autotune=True)
+        tuning = negf.negf_plan_get_tuning(plan)
 
     def one_step(step_idx, wires, memspace, prec=prec):
         wid0 = ndist.weak_walker_offset(rank, step_idx, N)
+        if plan is not None and memspace == "device" and prec == plan_prec:
+            negf.negf_plan_launch(ctx, plan, args.seed, wid0)
+            r = negf.negf_plan_result(ctx, plan)
+            return r, r["counts"]
         if args.mode == "pipeline":
             # build wave w+1 while wave w walks; tables are freed wave by wave
             tables, tally = negf.negf_run(ctx, wires, 0, args.seed, N, precision=prec,
@@ -268,6 +281,8 @@ def run_gpu(args):
     fp64_cmp = None
     if args.compare_fp64 and prec != "fp64":
         fp64_cmp = time_precision("fp64", one_step, dev_wires, negf, ctx, stream, flush, args)
+    if plan is not None:
+        negf.negf_plan_destroy(plan)
     negf.negf_destroy(ctx)
     if rank != 0:
         return
@@ -311,6 +326,7 @@ def run_gpu(args):
                    "mu_p": wl.mu_p, "mu_q": wl.mu_q, "kT": wl.kT,
                    "l2": "flushed between timed steps (258 MiB write, outside the timed events)",
                    "mode": args.mode, "tasks_per_wave": args.tasks_per_wave,
+                   "launch_shapes": tuning,
                    "parallelism": f"tasks replicated per rank, walker ids disjoint ({world} GPU)"},
         "walker_steps_per_step": all_steps / args.steps / world,
         "walkers_per_step": tot_walkers / args.steps,
@@ -431,7 +447,7 @@ def main():
     ap.add_argument("--max-steps", type=int, default=1 << 20)
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="separate", choices=["pipeline", "separate"])
+    ap.add_argument("--mode", default="graph", choices=["graph", "pipeline", "separate"])
     ap.add_argument("--tasks-per-wave", type=int, default=8)
     ap.add_argument("--walk-blocks-per-sm", type=int, default=4)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")

@@ -215,6 +215,57 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
                      negf_tables* out_tasks, negf_tally* out_tally);
 int32_t negf_tables_num_waves(negf_tables tables);
 
+/* --- captured plans (CUDA graph) and launch-shape autotuning -------------------------------- */
+
+typedef struct negf_plan_s* negf_plan;
+
+/* Launch shapes of a plan.  Picked by timing candidates on the plan's first wave when
+ * negf_plan_create is asked to autotune, else the built-in defaults (0 = default). */
+typedef struct {
+  int32_t walk_blocks_per_sm;   /* CTAs per SM of the persistent walk grid */
+  int32_t chain_warps;          /* warps per CTA of the block-column chain kernel */
+  int32_t alias_warps;          /* warps per CTA of the alias kernel */
+  int32_t tuned;                /* 1 when picked by the autotuner */
+  float walk_ms, chain_ms, alias_ms;   /* device time of the chosen shapes while tuning */
+} negf_plan_tuning;
+
+/* A plan is the whole path of negf_run followed by negf_current — lead modes, RGF sweeps,
+ * block columns, Step 6' weights, alias tables, walks, tally, current and standard error —
+ * for a fixed batch of wires (paper silent: Sec. IV repeats the same calculation for many
+ * samples), captured once into a CUDA graph over buffers allocated here, and relaunched by
+ * negf_plan_launch with a new seed and walker-id range.  build->memspace: for
+ * NEGF_MEM_DEVICE every launch re-reads the wires' onsite and eta arrays, which must stay
+ * allocated at the same addresses until negf_plan_destroy; host arrays, energies and energy
+ * weights are read once here.  run: start_lead, tasks_per_wave (0 = all tasks in one wave),
+ * walkers_per_task, max_steps, waves_in_flight, memory_budget as in negf_run; run->seed and
+ * run->walker_id_offset are ignored (given per launch); walk_blocks_per_sm > 0 overrides the
+ * tuned value.  mu_p, mu_q, kT: as negf_current.  autotune nonzero: time candidate launch
+ * shapes on the first wave first (one build and a few walks of that wave).  keep_weights and
+ * keep_green must be 0.  Device memory: every wave slot's tables and scratch stay allocated
+ * (negf_plan_device_bytes).  Synchronises the context stream. */
+negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
+                             const negf_build_opts* build, const negf_run_opts* run,
+                             double mu_p, double mu_q, double kT, int32_t autotune,
+                             negf_plan* out);
+/* Enqueue one launch of the plan on the context stream: walkers
+ * [walker_id_offset, walker_id_offset + walkers_per_task) of every task, Philox key seed.
+ * Tallies and walks equal those of negf_run / negf_build_tables + negf_walk with the same
+ * seed and walker ids.  Asynchronous (with profiling enabled it waits for the launch and adds
+ * the kernel groups' device times to the context's profile). */
+negf_status negf_plan_launch(negf_ctx ctx, negf_plan plan, uint64_t seed,
+                             uint64_t walker_id_offset);
+/* Results of the last launch (synchronises): I, se [n_wires], T, T_se [n_tasks], counts
+ * [n_tasks][NEGF_TALLY_FIELDS]; any pointer may be NULL.  Returns NEGF_E_STEPCAP (results
+ * written) when walks were cut at max_steps, NEGF_E_INVALID / NEGF_E_NUMERIC for device-side
+ * input or numerical errors of the launch. */
+negf_status negf_plan_result(negf_ctx ctx, negf_plan plan, double* I, double* se, double* T,
+                             double* T_se, uint64_t* counts);
+negf_status negf_plan_get_tuning(negf_plan plan, negf_plan_tuning* out);
+int32_t negf_plan_num_tasks(negf_plan plan);
+int32_t negf_plan_num_waves(negf_plan plan);
+uint64_t negf_plan_device_bytes(negf_plan plan);
+void negf_plan_destroy(negf_plan plan);
+
 /* --- gradient (paper silent) ---------------------------------------------------------------- */
 
 /* negf_walk that also records score tallies: every walk absorbed at lead r is replayed and

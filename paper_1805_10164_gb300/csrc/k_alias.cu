@@ -230,15 +230,26 @@ __global__ void alias_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
 
 }  // namespace
 
+int alias_warps_max(int max_K) {
+  const int cap = max_K < 64 ? 64 : max_K;
+  const size_t per_warp = alias_warp_bytes(cap);
+  int w = 16;
+  while (w > 1 && per_warp * w > 200 * 1024) --w;
+  return w;
+}
+
 cudaError_t launch_alias_build(const TaskDesc* d_tasks, int n_tasks, uint32_t total_jobs,
                                int max_K, int precision, const void* d_weights,
                                double* d_rowsum, const double* d_mode_w, uint64_t* d_tab,
-                               uint64_t* d_mode_tab, int32_t* d_err, cudaStream_t s) {
+                               uint64_t* d_mode_tab, int32_t* d_err, cudaStream_t s,
+                               int warps_req) {
   if (total_jobs == 0) return cudaSuccess;
   const int cap = max_K < 64 ? 64 : max_K;
   const size_t per_warp = alias_warp_bytes(cap);
+  const int wmax = alias_warps_max(max_K);
   int warps = 8;
   while (warps > 1 && per_warp * warps > 96 * 1024) --warps;
+  if (warps_req > 0) warps = warps_req < wmax ? warps_req : wmax;
   const size_t smem = per_warp * warps;
   if (smem > 220 * 1024) return cudaErrorInvalidValue;   // rows beyond the shared-memory path
   int dev = 0, sms = 1;

@@ -665,6 +665,15 @@ int warps_for(size_t per_warp, int max_warps) {
   return w;
 }
 
+// Most warps per chain CTA that fit the opt-in shared memory (and 16 warps).
+template <typename C>
+int chain_max(int max_W) {
+  const size_t per = chain_warp_bytes<C>(max_W);
+  int w = 16;
+  while (w > 1 && per * w > 200 * 1024) --w;
+  return w;
+}
+
 template <typename C>
 cudaError_t sweep_impl(const TaskDesc* d_tasks, int n_tasks, int max_W, const double* d_wire,
                        const double* d_phi, const cd* d_sig, C* d_gL, C* d_gR, int32_t* d_err,
@@ -719,7 +728,8 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
                          const double* d_phi, const typename Real<C>::T* d_phiR, const cd* d_sig,
                          const double* d_gam, const C* d_gL, const C* d_gR, C* d_start,
                          typename Real<C>::T* d_w, double* d_rowsum, double* d_mode_w,
-                         double* d_c, int32_t* d_err, C* d_green, C* d_gphi, cudaStream_t s) {
+                         double* d_c, int32_t* d_err, C* d_green, C* d_gphi, cudaStream_t s,
+                         int chain_warps) {
   if (sizeof(C) == sizeof(cf) && max_W <= 16) {
     // register-resident diagonal blocks, 4 warps per block
     const int warps = 4;
@@ -752,7 +762,8 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
   }
   const uint32_t jobs = 2 * n_cols;
   const size_t per = chain_warp_bytes<C>(max_W);
-  const int warps = warps_for(per, 8);
+  int warps = warps_for(per, 8);
+  if (chain_warps > 0) warps = chain_warps < chain_max<C>(max_W) ? chain_warps : chain_max<C>(max_W);
   const size_t smem = per * warps;
   cudaError_t e = cudaFuncSetAttribute(chain_kernel<C>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -792,19 +803,25 @@ cudaError_t launch_block_columns(const TaskDesc* d_tasks, int n_tasks, uint32_t 
                                  const cd* d_sig, const double* d_gam, const void* d_gL,
                                  const void* d_gR, void* d_start, void* d_weights,
                                  double* d_rowsum, double* d_mode_w, double* d_c, int32_t* d_err,
-                                 void* d_green, void* d_gphi, cudaStream_t s) {
+                                 void* d_green, void* d_gphi, cudaStream_t s, int chain_warps) {
   if (n_tasks == 0 || n_cols == 0) return cudaSuccess;
   if (precision == NEGF_FP64)
     return columns_impl<cd>(d_tasks, n_tasks, n_cols, max_W, d_wire, d_wire, d_phi, d_phi,
                             d_sig, d_gam, static_cast<const cd*>(d_gL),
                             static_cast<const cd*>(d_gR), static_cast<cd*>(d_start),
                             static_cast<double*>(d_weights), d_rowsum, d_mode_w, d_c, d_err,
-                            static_cast<cd*>(d_green), static_cast<cd*>(d_gphi), s);
+                            static_cast<cd*>(d_green), static_cast<cd*>(d_gphi), s,
+                            chain_warps);
   return columns_impl<cf>(d_tasks, n_tasks, n_cols, max_W, d_wire, d_eta32, d_phi, d_phi32,
                           d_sig, d_gam, static_cast<const cf*>(d_gL),
                           static_cast<const cf*>(d_gR), static_cast<cf*>(d_start),
                           static_cast<float*>(d_weights), d_rowsum, d_mode_w, d_c, d_err,
-                          static_cast<cf*>(d_green), static_cast<cf*>(d_gphi), s);
+                          static_cast<cf*>(d_green), static_cast<cf*>(d_gphi), s,
+                          chain_warps);
+}
+
+int chain_warps_max(int max_W, int precision) {
+  return precision == NEGF_FP64 ? chain_max<cd>(max_W) : chain_max<cf>(max_W);
 }
 
 }  // namespace negf

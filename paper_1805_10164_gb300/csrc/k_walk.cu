@@ -64,8 +64,15 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
     const double* __restrict__ cvals, int start_lead, PhiloxKey key, uint64_t walkers_per_task,
     uint64_t id_offset, uint32_t max_steps,
     unsigned long long* __restrict__ counter, unsigned long long* __restrict__ tally /*window*/,
-    int32_t* __restrict__ trace_lead, uint32_t* __restrict__ trace_steps, ScoreOut score) {
+    int32_t* __restrict__ trace_lead, uint32_t* __restrict__ trace_steps, ScoreOut score,
+    const uint64_t* __restrict__ run) {
   extern __shared__ unsigned s_tally[];   // [n_tasks][kFields][lo, hi]
+  if (run) {
+    // seed and walker id offset supplied on the device (relaunched graphs)
+    const uint64_t seed = run[0];
+    key = PhiloxKey{(uint32_t)seed, (uint32_t)(seed >> 32)};
+    id_offset = run[1];
+  }
   for (int i = threadIdx.x; i < n_tasks * kFields * 2; i += blockDim.x) s_tally[i] = 0u;
   __syncthreads();
 
@@ -274,7 +281,7 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
                         uint64_t* d_tally, int32_t* d_trace_lead, uint32_t* d_trace_steps,
                         uint64_t* d_score, uint64_t score_stride, uint64_t* d_mode_score,
                         uint32_t mode_stride, int sm_count, int max_blocks_per_sm,
-                        cudaStream_t s) {
+                        cudaStream_t s, const uint64_t* d_run) {
   if (n_tasks <= 0 || walkers_per_task == 0) return cudaSuccess;
   const PhiloxKey key{(uint32_t)seed, (uint32_t)(seed >> 32)};
   unsigned long long* tally = reinterpret_cast<unsigned long long*>(d_tally);
@@ -300,7 +307,7 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
     kern<<<(unsigned)blocks, kThreads, smem, s>>>(
         d_tasks, task0 + w0, nt, id_base, d_tab, d_mode_tab, d_c, start_lead, key,
         walkers_per_task, id_offset, max_steps, d_counter, tally + (size_t)w0 * kFields,
-        d_trace_lead, d_trace_steps, so);
+        d_trace_lead, d_trace_steps, so, d_run);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

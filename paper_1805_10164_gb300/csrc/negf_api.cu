@@ -564,16 +564,24 @@ negf_status sweep_all(negf_ctx ctx, cudaStream_t s, const Plan& P, const Persist
 negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& w,
                        TaskDesc* d_wdesc, const Persist& q, int prec, const void* d_gL,
                        const void* d_gR, uint64_t* d_tab, double* d_rowsum, void** weights_out,
-                       void* d_green = nullptr, void* d_gphi = nullptr) {
+                       void* d_green = nullptr, void* d_gphi = nullptr,
+                       double* pre_start = nullptr, void* pre_weights = nullptr,
+                       int chain_warps = 0, int alias_warps = 0) {
   const int nt = w.t1 - w.t0;
   if (nt == 0) return NEGF_OK;
   const uint64_t cw = negf::block_bytes(prec) / sizeof(double);
   const size_t wsz = prec == NEGF_FP64 ? sizeof(double) : sizeof(float);
-  double* d_start = nullptr;
-  void* d_weights = nullptr;
-  cudaError_t e = dalloc(&d_start, w.start * cw, s, nullptr);
-  if (e == cudaSuccess) e = cudaMallocAsync(&d_weights, std::max<uint64_t>(w.tab, 1) * wsz, s);
+  // scratch: the caller's buffers when given (captured plans), else allocated on s
+  const bool own = pre_start == nullptr;
+  double* d_start = pre_start;
+  void* d_weights = pre_weights;
+  cudaError_t e = cudaSuccess;
+  if (own) {
+    e = dalloc(&d_start, w.start * cw, s, nullptr);
+    if (e == cudaSuccess) e = cudaMallocAsync(&d_weights, std::max<uint64_t>(w.tab, 1) * wsz, s);
+  }
   auto cleanup = [&]() {
+    if (!own) return;
     dfree(d_start, s);
     if (d_weights) cudaFreeAsync(d_weights, s);
     d_weights = nullptr;
@@ -589,18 +597,18 @@ negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& 
                                    q.d_phi, reinterpret_cast<float*>(q.d_phi + P.phi_total),
                                    q.d_sig, q.d_gam, d_gL, d_gR, d_start, d_weights, d_rowsum,
                                    q.d_mode_w, q.d_c + 2 * (size_t)w.t0, q.d_err, d_green,
-                                   d_gphi, s);
+                                   d_gphi, s, chain_warps);
   }
   if (e == cudaSuccess) {
     ProfScope ps(ctx, "alias_kernel", 1, s);
     e = negf::launch_alias_build(d_wdesc, nt, w.rows, P.max_K, prec, d_weights, d_rowsum,
-                                 q.d_mode_w, d_tab, q.d_mode_tab, q.d_err, s);
+                                 q.d_mode_w, d_tab, q.d_mode_tab, q.d_err, s, alias_warps);
   }
   if (e != cudaSuccess) {
     cleanup();
     return fail(ctx, NEGF_E_CUDA, "table build: %s", cudaGetErrorString(e));
   }
-  if (weights_out) {
+  if (weights_out && own) {
     *weights_out = d_weights;
     d_weights = nullptr;
   }
@@ -1358,6 +1366,576 @@ negf_status negf_current(negf_ctx ctx, negf_tables t, negf_tally tl, double mu_p
   if (h[m - 1] > 0.0)
     return fail(ctx, NEGF_E_STEPCAP, "negf_current: %.0f walks reached max_steps", h[m - 1]);
   return NEGF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------
+// Plans: the whole path (inputs -> lead modes -> RGF sweeps -> block columns -> alias tables ->
+// walks -> current) captured once into a CUDA graph over preallocated buffers and relaunched
+// with a new seed / walker range.  The launch shapes are picked by timing candidates on the
+// plan's own first wave before the capture.
+
+struct negf_plan_s {
+  negf_ctx ctx = nullptr;
+  int prec = NEGF_FP32;
+  bool dev_in = false;
+  int n_wires = 0;
+  Plan P;
+  Persist q;
+  std::vector<Wave> waves;
+  std::vector<size_t> wave_off;              // first rebased descriptor of each wave
+  TaskDesc* d_wdesc = nullptr;
+  void* d_gL = nullptr;
+  void* d_gR = nullptr;
+  int slots = 1;                             // waves whose tables exist at once
+  std::vector<uint64_t*> d_tab;              // per slot
+  std::vector<double*> d_rs, d_start;
+  std::vector<void*> d_weights;
+  uint64_t* d_counts = nullptr;              // [n_tasks][5]
+  double* d_out = nullptr;                   // current outputs (launch_current layout)
+  uint64_t* d_run = nullptr;                 // seed, walker id offset
+  uint64_t* h_ring = nullptr;                // pinned staging of the run parameters
+  std::vector<cudaEvent_t> ring_ev;
+  unsigned ring_next = 0;
+  std::vector<const double*> src_onsite, src_eta;
+  std::vector<int64_t> wire_n;               // sites per wire
+  negf_run_opts run{};
+  double mu_p = 0.0, mu_q = 0.0, kT = 0.0;
+  negf_plan_tuning tune{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<cudaEvent_t> sync_ev;          // fork/join events of the capture
+  struct Seg {
+    std::string name;
+    uint64_t kernels;
+    cudaEvent_t a, b;
+  };
+  std::vector<Seg> segs;                     // timed segments (event nodes in the graph)
+  uint64_t bytes = 0;
+  uint64_t launches = 0;
+};
+
+namespace {
+
+constexpr unsigned kRing = 64;
+
+void plan_release(negf_plan p) {
+  if (!p) return;
+  negf_ctx ctx = p->ctx;
+  cudaStream_t s = ctx ? ctx->stream : nullptr;
+  if (s) cudaStreamSynchronize(s);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  for (cudaEvent_t e : p->sync_ev) cudaEventDestroy(e);
+  for (auto& g : p->segs) {
+    cudaEventDestroy(g.a);
+    cudaEventDestroy(g.b);
+  }
+  for (cudaEvent_t e : p->ring_ev) cudaEventDestroy(e);
+  if (p->h_ring) cudaFreeHost(p->h_ring);
+  Persist& q = p->q;
+  dfree(q.d_tasks, s);
+  dfree(q.d_wire_task0, s);
+  dfree(q.d_wire, s);
+  dfree(q.d_sig, s);
+  dfree(q.d_gam, s);
+  dfree(q.d_phi, s);
+  dfree(q.d_eta32, s);
+  dfree(q.d_mode_tab, s);
+  dfree(q.d_mode_w, s);
+  dfree(q.d_c, s);
+  dfree(q.d_err, s);
+  dfree(p->d_wdesc, s);
+  if (p->d_gL) cudaFreeAsync(p->d_gL, s);
+  if (p->d_gR) cudaFreeAsync(p->d_gR, s);
+  for (auto& x : p->d_tab) dfree(x, s);
+  for (auto& x : p->d_rs) dfree(x, s);
+  for (auto& x : p->d_start) dfree(x, s);
+  for (auto& x : p->d_weights)
+    if (x) cudaFreeAsync(x, s);
+  dfree(p->d_counts, s);
+  dfree(p->d_out, s);
+  dfree(p->d_run, s);
+  if (s) cudaStreamSynchronize(s);
+  delete p;
+}
+
+// A timed segment inside the capture: external event-record nodes around the launches.
+struct SegScope {
+  negf_plan p;
+  cudaStream_t s;
+  int idx = -1;
+  SegScope(negf_plan plan, const char* name, uint64_t kernels, cudaStream_t st, bool on)
+      : p(plan), s(st) {
+    if (!on) return;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    p->segs.push_back(negf_plan_s::Seg{name, kernels, a, b});
+    idx = (int)p->segs.size() - 1;
+    cudaEventRecordWithFlags(a, s, cudaEventRecordExternal);
+  }
+  ~SegScope() {
+    if (idx >= 0) cudaEventRecordWithFlags(p->segs[idx].b, s, cudaEventRecordExternal);
+  }
+};
+
+// Enqueue every step that one launch repeats (inside the capture); `timed` adds event nodes
+// around the kernel groups.
+negf_status plan_enqueue(negf_plan p, bool timed) {
+  negf_ctx ctx = p->ctx;
+  cudaStream_t s = ctx->stream;
+  cudaStream_t sw = ctx->walk_stream;
+  const Plan& P = p->P;
+  Persist& q = p->q;
+  const int nt = (int)P.tasks.size();
+  const int prec = p->prec;
+  CUDA_TRY(ctx, cudaMemsetAsync(q.d_err, 0, sizeof(int32_t), s));
+  CUDA_TRY(ctx, cudaMemsetAsync(p->d_counts, 0,
+                                sizeof(uint64_t) * (size_t)std::max(1, nt) * NEGF_TALLY_FIELDS, s));
+  if (p->dev_in) {
+    // device inputs are re-read by every launch (same layout as the batch setup)
+    uint64_t off = 0;
+    for (int w = 0; w < p->n_wires; ++w) {
+      const int64_t n = p->wire_n[w];
+      CUDA_TRY(ctx, cudaMemcpyAsync(q.d_wire + off, p->src_onsite[w], sizeof(double) * n,
+                                    cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(ctx, cudaMemcpyAsync(q.d_wire + off + n, p->src_eta[w], sizeof(double) * n,
+                                    cudaMemcpyDeviceToDevice, s));
+      off += 2 * (uint64_t)n;
+    }
+  }
+  if (nt == 0) return NEGF_OK;
+  if (p->dev_in) {
+    SegScope sg(p, "validate_kernel", 2, s, timed);
+    CUDA_TRY(ctx, negf::launch_validate(q.d_tasks, nt, q.d_wire, q.d_err, s));
+  }
+  {
+    SegScope sg(p, "lead_modes_kernel", 1, s, timed);
+    CUDA_TRY(ctx, negf::launch_lead_modes(q.d_tasks, nt, P.max_W, q.d_wire, q.d_phi,
+                                          reinterpret_cast<float*>(q.d_phi + P.phi_total),
+                                          q.d_eta32, q.d_sig, q.d_gam, q.d_err, s));
+  }
+  {
+    SegScope sg(p, "rgf_sweep_kernel", 1, s, timed);
+    CUDA_TRY(ctx, negf::launch_rgf_sweep(q.d_tasks, nt, P.max_W, prec, q.d_wire, q.d_phi,
+                                         q.d_sig, p->d_gL, p->d_gR, q.d_err, s));
+  }
+  const bool split = p->waves.size() > 1;     // walks on the second stream, overlapped
+  for (size_t w = 0; w < p->waves.size(); ++w) {
+    const Wave& wv = p->waves[w];
+    const int slot = (int)(w % (size_t)p->slots);
+    cudaEvent_t built = split ? p->sync_ev[2 * w] : nullptr;
+    cudaEvent_t walked = split ? p->sync_ev[2 * w + 1] : nullptr;
+    if (split && w >= (size_t)p->slots)
+      CUDA_TRY(ctx, cudaStreamWaitEvent(s, p->sync_ev[2 * (w - p->slots) + 1], 0));
+    TaskDesc* dd = p->d_wdesc + p->wave_off[w];
+    const int ntw = wv.t1 - wv.t0;
+    {
+      SegScope sg(p, "diag_chain_kernels", 2, s, timed);
+      CUDA_TRY(ctx, negf::launch_block_columns(
+                        dd, ntw, wv.cols, P.max_W, prec, q.d_wire, q.d_eta32, q.d_phi,
+                        reinterpret_cast<float*>(q.d_phi + P.phi_total), q.d_sig, q.d_gam,
+                        p->d_gL, p->d_gR, p->d_start[slot], p->d_weights[slot], p->d_rs[slot],
+                        q.d_mode_w, q.d_c + 2 * (size_t)wv.t0, q.d_err, nullptr, nullptr, s,
+                        p->tune.chain_warps));
+    }
+    {
+      SegScope sg(p, "alias_kernel", 1, s, timed);
+      CUDA_TRY(ctx, negf::launch_alias_build(dd, ntw, wv.rows, P.max_K, prec, p->d_weights[slot],
+                                             p->d_rs[slot], q.d_mode_w, p->d_tab[slot],
+                                             q.d_mode_tab, q.d_err, s, p->tune.alias_warps));
+    }
+    cudaStream_t ws = s;
+    if (split) {
+      CUDA_TRY(ctx, cudaEventRecord(built, s));
+      CUDA_TRY(ctx, cudaStreamWaitEvent(sw, built, 0));
+      ws = sw;
+    }
+    {
+      SegScope sg(p, "walk_kernel", (uint64_t)(ntw + 1023) / 1024, ws, timed);
+      CUDA_TRY(ctx, negf::launch_walk(dd, 0, ntw, (uint32_t)wv.t0, p->d_tab[slot], q.d_mode_tab,
+                                      q.d_c + 2 * (size_t)wv.t0, p->run.start_lead, 0,
+                                      p->run.walkers_per_task, 0, p->run.max_steps,
+                                      ctx->d_counter,
+                                      p->d_counts + (size_t)wv.t0 * NEGF_TALLY_FIELDS, nullptr,
+                                      nullptr, nullptr, 0, nullptr, 0, ctx->sm_count,
+                                      p->tune.walk_blocks_per_sm, ws, p->d_run));
+    }
+    if (split) CUDA_TRY(ctx, cudaEventRecord(walked, sw));
+  }
+  if (split) CUDA_TRY(ctx, cudaStreamWaitEvent(s, p->sync_ev.back(), 0));
+  {
+    SegScope sg(p, "current_kernel", 1, s, timed);
+    CUDA_TRY(ctx, negf::launch_current(q.d_tasks, nt, p->n_wires, q.d_wire_task0, q.d_c,
+                                       p->d_counts, p->run.start_lead, p->mu_p, p->mu_q, p->kT,
+                                       p->d_out, s));
+  }
+  return NEGF_OK;
+}
+
+// Device time of `f` enqueued on s (best of `reps`).
+template <typename F>
+float time_on(cudaStream_t s, int reps, F f) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (cudaEventCreate(&a) != cudaSuccess) return -1.f;
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return -1.f;
+  }
+  float best = -1.f;
+  for (int r = 0; r < reps; ++r) {
+    cudaEventRecord(a, s);
+    const cudaError_t e = f();
+    cudaEventRecord(b, s);
+    float ms = 0.f;
+    if (e != cudaSuccess || cudaEventSynchronize(b) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
+      best = -1.f;
+      break;
+    }
+    if (best < 0.f || ms < best) best = ms;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return best;
+}
+
+// Pick chain warps, alias warps and walk CTAs per SM by timing candidates on wave 0 (its
+// inputs, lead modes and sweeps are already on the device).  Leaves wave 0 built.
+negf_status plan_autotune(negf_plan p) {
+  negf_ctx ctx = p->ctx;
+  cudaStream_t s = ctx->stream;
+  const Plan& P = p->P;
+  Persist& q = p->q;
+  const Wave& wv = p->waves[0];
+  TaskDesc* dd = p->d_wdesc;
+  const int prec = p->prec;
+  const int nt0 = wv.t1 - wv.t0;
+  auto columns = [&](int cw) {
+    return negf::launch_block_columns(dd, nt0, wv.cols, P.max_W, prec, q.d_wire, q.d_eta32,
+                                      q.d_phi, reinterpret_cast<float*>(q.d_phi + P.phi_total),
+                                      q.d_sig, q.d_gam, p->d_gL, p->d_gR, p->d_start[0],
+                                      p->d_weights[0], p->d_rs[0], q.d_mode_w, q.d_c, q.d_err,
+                                      nullptr, nullptr, s, cw);
+  };
+  auto alias = [&](int aw) {
+    // the alias kernel overwrites A in the row sums: restore them first (outside the timing)
+    return negf::launch_alias_build(dd, nt0, wv.rows, P.max_K, prec, p->d_weights[0],
+                                    p->d_rs[0], q.d_mode_w, p->d_tab[0], q.d_mode_tab, q.d_err,
+                                    s, aw);
+  };
+  // chain warps
+  int best_cw = 0;
+  float best_c = -1.f;
+  const int cmax = negf::chain_warps_max(P.max_W, prec);
+  for (int cw : {1, 2, 4, 8, 16}) {
+    if (cw > cmax) break;
+    const float ms = time_on(s, 2, [&]() { return columns(cw); });
+    if (ms < 0.f) return fail(ctx, NEGF_E_CUDA, "autotune: block columns failed");
+    if (best_c < 0.f || ms < best_c) best_c = ms, best_cw = cw;
+  }
+  // alias warps (each candidate runs on freshly computed row values)
+  int best_aw = 0;
+  float best_a = -1.f;
+  const int amax = negf::alias_warps_max(P.max_K);
+  for (int aw : {2, 4, 8, 12, 16}) {
+    if (aw > amax) break;
+    if (columns(best_cw) != cudaSuccess) return fail(ctx, NEGF_E_CUDA, "autotune: columns");
+    const float ms = time_on(s, 1, [&]() { return alias(aw); });
+    if (ms < 0.f) return fail(ctx, NEGF_E_CUDA, "autotune: alias build failed");
+    if (best_a < 0.f || ms < best_a) best_a = ms, best_aw = aw;
+  }
+  if (best_aw == 0) best_aw = amax;
+  // leave wave 0 built with the chosen shapes
+  if (columns(best_cw) != cudaSuccess || alias(best_aw) != cudaSuccess)
+    return fail(ctx, NEGF_E_CUDA, "autotune: rebuild failed");
+  // walk grid: CTAs per SM (the tally of the candidates is discarded)
+  int best_wb = 0;
+  float best_w = -1.f;
+  const uint64_t h_run[2] = {0x5eedull, 0ull};
+  CUDA_TRY(ctx, cudaMemcpyAsync(p->d_run, h_run, sizeof h_run, cudaMemcpyHostToDevice, s));
+  CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  for (int wb : {2, 3, 4, 5}) {
+    const float ms = time_on(s, 2, [&]() {
+      return negf::launch_walk(dd, 0, nt0, (uint32_t)wv.t0, p->d_tab[0], q.d_mode_tab, q.d_c,
+                               p->run.start_lead, 0, p->run.walkers_per_task, 0,
+                               p->run.max_steps, ctx->d_counter, p->d_counts, nullptr, nullptr,
+                               nullptr, 0, nullptr, 0, ctx->sm_count, wb, s, p->d_run);
+    });
+    if (ms < 0.f) return fail(ctx, NEGF_E_CUDA, "autotune: walk failed");
+    if (best_w < 0.f || ms < best_w) best_w = ms, best_wb = wb;
+  }
+  p->tune.chain_warps = best_cw;
+  p->tune.alias_warps = best_aw;
+  p->tune.walk_blocks_per_sm = best_wb;
+  p->tune.tuned = 1;
+  p->tune.chain_ms = best_c;
+  p->tune.alias_ms = best_a;
+  p->tune.walk_ms = best_w;
+  int32_t h_err = 0;
+  CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, q.d_err, sizeof h_err, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (h_err & negf::ERR_INPUT) return fail(ctx, NEGF_E_INVALID, "device check:%s", err_bits(h_err).c_str());
+  if (h_err) return fail(ctx, NEGF_E_NUMERIC, "device check:%s", err_bits(h_err).c_str());
+  return NEGF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
+                             const negf_build_opts* bopts, const negf_run_opts* ropts,
+                             double mu_p, double mu_q, double kT, int32_t autotune,
+                             negf_plan* out) {
+  if (!ctx) return NEGF_E_INVALID;
+  if (!out || !ropts) return fail(ctx, NEGF_E_INVALID, "negf_plan_create: NULL output or options");
+  *out = nullptr;
+  if (n_wires < 0 || (n_wires > 0 && !wires))
+    return fail(ctx, NEGF_E_INVALID, "negf_plan_create: bad wire list");
+  negf_build_opts o;
+  negf_status st = check_opts(ctx, bopts, o);
+  if (st != NEGF_OK) return st;
+  if (o.keep_weights || o.keep_green)
+    return fail(ctx, NEGF_E_INVALID, "negf_plan_create: keep_weights / keep_green must be 0");
+  const negf_run_opts& r = *ropts;
+  if (r.start_lead != 0 && r.start_lead != 1)
+    return fail(ctx, NEGF_E_INVALID, "negf_plan_create: start_lead must be 0 or 1");
+  if (r.max_steps < 1 || r.max_steps > NEGF_MAX_STEPS)
+    return fail(ctx, NEGF_E_INVALID, "negf_plan_create: max_steps must be in [1, %u]",
+                NEGF_MAX_STEPS);
+  if (r.walkers_per_task > (1ull << 40) || r.tasks_per_wave < 0 || r.waves_in_flight < 0 ||
+      r.walk_blocks_per_sm < 0 || r.reserved != 0)
+    return fail(ctx, NEGF_E_INVALID, "negf_plan_create: bad walker count, wave size, depth or reserved");
+  if (!isfinite(mu_p) || !isfinite(mu_q) || !(kT > 0.0) || !isfinite(kT))
+    return fail(ctx, NEGF_E_INVALID, "negf_plan_create: need finite mu and kT > 0");
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = ctx->stream;
+  negf_plan p = new (std::nothrow) negf_plan_s;
+  if (!p) return fail(ctx, NEGF_E_NOMEM, "negf_plan_create: host allocation");
+  p->ctx = ctx;
+  p->prec = o.precision == NEGF_FP64 ? NEGF_FP64 : NEGF_FP32;
+  p->dev_in = o.memspace == NEGF_MEM_DEVICE;
+  p->n_wires = n_wires;
+  p->run = r;
+  p->mu_p = mu_p;
+  p->mu_q = mu_q;
+  p->kT = kT;
+  auto bail = [&](negf_status code) {
+    plan_release(p);
+    return code;
+  };
+  st = make_plan(ctx, wires, n_wires, p->dev_in, p->P);
+  if (st != NEGF_OK) return bail(st);
+  const Plan& P = p->P;
+  const int nt = (int)P.tasks.size();
+  for (int w = 0; w < n_wires; ++w) {
+    p->wire_n.push_back((int64_t)wires[w].W * wires[w].L);
+    if (p->dev_in) {
+      p->src_onsite.push_back(wires[w].onsite);
+      p->src_eta.push_back(wires[w].eta);
+    }
+  }
+  if (!ctx->walk_stream &&
+      cudaStreamCreateWithFlags(&ctx->walk_stream, cudaStreamNonBlocking) != cudaSuccess)
+    return bail(fail(ctx, NEGF_E_CUDA, "negf_plan_create: stream creation failed"));
+  // persistent buffers (and a first fill of inputs and lead modes)
+  st = setup_batch(ctx, s, wires, n_wires, p->dev_in, P, p->q, &p->bytes);
+  if (st != NEGF_OK) return bail(st);
+  cudaError_t e = dalloc(&p->d_counts, (size_t)std::max(1, nt) * NEGF_TALLY_FIELDS, s, &p->bytes);
+  const size_t m_out = 2 * (size_t)n_wires + 2 * (size_t)nt + 1;
+  if (e == cudaSuccess) e = dalloc(&p->d_out, m_out, s, &p->bytes);
+  if (e == cudaSuccess) e = dalloc(&p->d_run, 2, s, &p->bytes);
+  if (e != cudaSuccess) return bail(fail(ctx, NEGF_E_NOMEM, "plan buffers: %s", cudaGetErrorString(e)));
+  // waves: as negf_run, but every slot's tables and scratch stay allocated
+  const int depth = r.waves_in_flight > 0 ? r.waves_in_flight : 2;
+  uint64_t budget = r.memory_budget;
+  if (budget == 0) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    budget = free_b / 2;
+  }
+  const int per_wave = r.tasks_per_wave > 0 ? r.tasks_per_wave : std::max(1, nt);
+  std::vector<uint64_t> task_bytes(nt);
+  for (int k = 0; k < nt; ++k) task_bytes[k] = wave_bytes(make_wave(P, k, k + 1), p->prec);
+  for (int k = 0; k < nt;) {
+    int k1 = k + 1;
+    uint64_t bytes_w = task_bytes[k];
+    while (k1 < nt && k1 - k < per_wave && (bytes_w + task_bytes[k1]) * depth <= budget)
+      bytes_w += task_bytes[k1++];
+    p->waves.push_back(make_wave(P, k, k1));
+    k = k1;
+  }
+  p->slots = p->waves.size() > 1 ? std::min<int>(depth, (int)p->waves.size()) : 1;
+  uint64_t max_tab = 1, max_rows = 1, max_start = 1;
+  std::vector<TaskDesc> all;
+  for (const Wave& w : p->waves) {
+    p->wave_off.push_back(all.size());
+    all.insert(all.end(), w.desc.begin(), w.desc.end());
+    max_tab = std::max(max_tab, w.tab);
+    max_rows = std::max<uint64_t>(max_rows, w.rows);
+    max_start = std::max(max_start, w.start);
+  }
+  if (nt > 0) {
+    e = dalloc(&p->d_wdesc, all.size(), s, &p->bytes);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->d_wdesc, all.data(), sizeof(TaskDesc) * all.size(),
+                          cudaMemcpyHostToDevice, s);
+    const uint64_t gb = std::max<uint64_t>(P.g_total, 1) * negf::block_bytes(p->prec);
+    if (e == cudaSuccess) e = cudaMallocAsync(&p->d_gL, gb, s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&p->d_gR, gb, s);
+    p->bytes += 2 * gb;
+    const uint64_t cw = negf::block_bytes(p->prec) / sizeof(double);
+    const size_t wsz = p->prec == NEGF_FP64 ? sizeof(double) : sizeof(float);
+    p->d_tab.assign(p->slots, nullptr);
+    p->d_rs.assign(p->slots, nullptr);
+    p->d_start.assign(p->slots, nullptr);
+    p->d_weights.assign(p->slots, nullptr);
+    for (int k = 0; k < p->slots && e == cudaSuccess; ++k) {
+      e = dalloc(&p->d_tab[k], max_tab, s, &p->bytes);
+      if (e == cudaSuccess) e = dalloc(&p->d_rs[k], max_rows, s, &p->bytes);
+      if (e == cudaSuccess) e = dalloc(&p->d_start[k], max_start * cw, s, &p->bytes);
+      if (e == cudaSuccess) e = cudaMallocAsync(&p->d_weights[k], max_tab * wsz, s);
+      p->bytes += max_tab * wsz;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // `all` dies here
+    if (e != cudaSuccess)
+      return bail(fail(ctx, e == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,
+                       "plan tables: %s", cudaGetErrorString(e)));
+  }
+  // staging ring of the per-launch run parameters
+  if (cudaMallocHost(reinterpret_cast<void**>(&p->h_ring), kRing * 2 * sizeof(uint64_t)) !=
+      cudaSuccess)
+    return bail(fail(ctx, NEGF_E_NOMEM, "plan: pinned staging"));
+  p->ring_ev.assign(kRing, nullptr);
+  for (unsigned k = 0; k < kRing; ++k)
+    if (cudaEventCreateWithFlags(&p->ring_ev[k], cudaEventDisableTiming) != cudaSuccess)
+      return bail(fail(ctx, NEGF_E_CUDA, "plan: events"));
+  if (p->waves.size() > 1) {
+    p->sync_ev.assign(2 * p->waves.size(), nullptr);
+    for (auto& ev : p->sync_ev)
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(ctx, NEGF_E_CUDA, "plan: events"));
+  }
+  // launch shapes: tuned on wave 0, or the caller's / built-in defaults
+  p->tune.walk_blocks_per_sm = r.walk_blocks_per_sm;
+  if (autotune && nt > 0) {
+    {
+      const bool prof = ctx->prof;
+      ctx->prof = false;
+      st = sweep_all(ctx, s, P, p->q, p->prec, p->d_gL, p->d_gR);
+      if (st == NEGF_OK) st = plan_autotune(p);
+      ctx->prof = prof;
+    }
+    if (st != NEGF_OK) return bail(st);
+    if (r.walk_blocks_per_sm > 0) p->tune.walk_blocks_per_sm = r.walk_blocks_per_sm;
+  }
+  // capture
+  {
+    const bool prof = ctx->prof;
+    ctx->prof = false;
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      ctx->prof = prof;
+      return bail(fail(ctx, NEGF_E_CUDA, "plan: begin capture: %s", cudaGetErrorString(e)));
+    }
+    st = plan_enqueue(p, true);
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(s, &g);
+    ctx->prof = prof;
+    p->graph = g;
+    if (st != NEGF_OK) return bail(st);
+    if (e != cudaSuccess) return bail(fail(ctx, NEGF_E_CUDA, "plan: capture: %s", cudaGetErrorString(e)));
+    e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (e != cudaSuccess)
+      return bail(fail(ctx, NEGF_E_CUDA, "plan: instantiate: %s", cudaGetErrorString(e)));
+  }
+  *out = p;
+  return NEGF_OK;
+}
+
+negf_status negf_plan_launch(negf_ctx ctx, negf_plan p, uint64_t seed, uint64_t walker_id_offset) {
+  if (!ctx || !p || p->ctx != ctx) return ctx ? fail(ctx, NEGF_E_INVALID, "negf_plan_launch: bad plan") : NEGF_E_INVALID;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = ctx->stream;
+  const unsigned k = p->ring_next++ % kRing;
+  // the slot's previous copy must have been consumed before it is overwritten
+  CUDA_TRY(ctx, cudaEventSynchronize(p->ring_ev[k]));
+  p->h_ring[2 * k] = seed;
+  p->h_ring[2 * k + 1] = walker_id_offset;
+  CUDA_TRY(ctx, cudaMemcpyAsync(p->d_run, p->h_ring + 2 * k, 2 * sizeof(uint64_t),
+                                cudaMemcpyHostToDevice, s));
+  CUDA_TRY(ctx, cudaEventRecord(p->ring_ev[k], s));
+  CUDA_TRY(ctx, cudaGraphLaunch(p->exec, s));
+  ++p->launches;
+  if (ctx->prof) {
+    // profiling: wait for this launch and add its segment times to the context's accounts
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
+    for (auto& g : p->segs) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, g.a, g.b) != cudaSuccess) ms = 0.f;
+      int idx = -1;
+      for (size_t i = 0; i < ctx->prof_entries.size(); ++i)
+        if (ctx->prof_entries[i].name == g.name) idx = (int)i;
+      if (idx < 0) {
+        ctx->prof_entries.push_back(ProfEntry{});
+        ctx->prof_entries.back().name = g.name;
+        idx = (int)ctx->prof_entries.size() - 1;
+      }
+      ctx->prof_entries[idx].launches += g.kernels;
+      ctx->prof_entries[idx].ms += ms;
+    }
+  }
+  return NEGF_OK;
+}
+
+negf_status negf_plan_result(negf_ctx ctx, negf_plan p, double* I, double* se, double* T,
+                             double* T_se, uint64_t* counts) {
+  if (!ctx || !p || p->ctx != ctx) return ctx ? fail(ctx, NEGF_E_INVALID, "negf_plan_result: bad plan") : NEGF_E_INVALID;
+  DeviceGuard guard(ctx->device);
+  cudaStream_t s = ctx->stream;
+  const size_t nw = (size_t)p->n_wires, nt = p->P.tasks.size();
+  const size_t m = 2 * nw + 2 * nt + 1;
+  std::vector<double> h(m, 0.0);
+  int32_t h_err = 0;
+  CUDA_TRY(ctx, cudaMemcpyAsync(h.data(), p->d_out, sizeof(double) * m, cudaMemcpyDeviceToHost, s));
+  if (counts)
+    CUDA_TRY(ctx, cudaMemcpyAsync(counts, p->d_counts, sizeof(uint64_t) * nt * NEGF_TALLY_FIELDS,
+                                  cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, p->q.d_err, sizeof h_err, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(ctx, cudaStreamSynchronize(s));
+  if (h_err & negf::ERR_INPUT) return fail(ctx, NEGF_E_INVALID, "device check:%s", err_bits(h_err).c_str());
+  if (h_err) return fail(ctx, NEGF_E_NUMERIC, "device check:%s", err_bits(h_err).c_str());
+  for (size_t w = 0; w < nw; ++w) {
+    if (I) I[w] = h[w];
+    if (se) se[w] = h[nw + w];
+  }
+  if (T) for (size_t k = 0; k < nt; ++k) T[k] = h[2 * nw + k];
+  if (T_se) for (size_t k = 0; k < nt; ++k) T_se[k] = h[2 * nw + nt + k];
+  if (h[m - 1] > 0.0)
+    return fail(ctx, NEGF_E_STEPCAP, "negf_plan_result: %.0f walks reached max_steps", h[m - 1]);
+  return NEGF_OK;
+}
+
+negf_status negf_plan_get_tuning(negf_plan p, negf_plan_tuning* out) {
+  if (!p || !out) return NEGF_E_INVALID;
+  *out = p->tune;
+  return NEGF_OK;
+}
+
+int32_t negf_plan_num_tasks(negf_plan p) { return p ? (int32_t)p->P.tasks.size() : 0; }
+int32_t negf_plan_num_waves(negf_plan p) { return p ? (int32_t)p->waves.size() : 0; }
+uint64_t negf_plan_device_bytes(negf_plan p) { return p ? p->bytes : 0; }
+
+void negf_plan_destroy(negf_plan p) {
+  if (!p) return;
+  DeviceGuard guard(p->ctx ? p->ctx->device : 0);
+  plan_release(p);
 }
 
 }  // extern "C"

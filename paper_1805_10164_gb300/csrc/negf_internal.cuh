@@ -85,18 +85,27 @@ cudaError_t launch_block_columns(const TaskDesc* d_tasks, int n_tasks, uint32_t 
                                  const cd* d_sig, const double* d_gam, const void* d_gL,
                                  const void* d_gR, void* d_start, void* d_weights,
                                  double* d_rowsum, double* d_mode_w, double* d_c, int32_t* d_err,
-                                 void* d_green, void* d_gphi, cudaStream_t s);
+                                 void* d_green, void* d_gphi, cudaStream_t s,
+                                 int chain_warps = 0);
+// Warps per CTA the chain kernel can use for max_W (shared memory bound), and its default.
+int chain_warps_max(int max_W, int precision);
 // Alias tables of every row (and mode row); replaces the A values in rowsum by the FP64 row
 // sums after checking them.
 cudaError_t launch_alias_build(const TaskDesc* d_tasks, int n_tasks, uint32_t total_jobs,
                                int max_K, int precision, const void* d_weights,
                                double* d_rowsum, const double* d_mode_w, uint64_t* d_tab,
-                               uint64_t* d_mode_tab, int32_t* d_err, cudaStream_t s);
+                               uint64_t* d_mode_tab, int32_t* d_err, cudaStream_t s,
+                               int warps = 0);
+// Warps per CTA the alias kernel can use for rows of max_K slots (shared memory bound).
+int alias_warps_max(int max_K);
 // Walks of tasks d_tasks[task0 .. task0 + n_tasks); d_c is indexed like d_tasks, d_tally holds
 // the counters of those tasks (index 0 = task0).  The Philox task number of d_tasks[k] is
 // id_base + k.  max_blocks_per_sm > 0 caps the persistent grid (leaving room for concurrent
 // kernels).  With d_score non-null every absorbed walk also adds its transitions to
 // d_score[lead][tab_off + a K + b] and its injection mode to d_mode_score[lead][mode_off + m].
+// With d_run non-null the seed and id_offset arguments are ignored and read on the device from
+// d_run[0] (seed) and d_run[1] (walker id offset), so a captured graph can be relaunched with
+// new values.
 cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_t id_base,
                         const uint64_t* d_tab, const uint64_t* d_mode_tab, const double* d_c,
                         int start_lead, uint64_t seed, uint64_t walkers_per_task,
@@ -104,7 +113,7 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
                         uint64_t* d_tally, int32_t* d_trace_lead, uint32_t* d_trace_steps,
                         uint64_t* d_score, uint64_t score_stride, uint64_t* d_mode_score,
                         uint32_t mode_stride, int sm_count, int max_blocks_per_sm,
-                        cudaStream_t s);
+                        cudaStream_t s, const uint64_t* d_run = nullptr);
 // Timed random 8-byte gathers over a table of table_bytes (see k_walk.cu); synchronises s.
 cudaError_t probe_gather(uint64_t table_bytes, int ilp, int chain, int sm_count,
                          uint64_t* gathers, float* ms, cudaStream_t s);

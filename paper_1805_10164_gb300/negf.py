@@ -58,6 +58,12 @@ class negf_run_opts(C.Structure):
 _lib = None
 
 
+class negf_plan_tuning(C.Structure):
+    _fields_ = [("walk_blocks_per_sm", C.c_int32), ("chain_warps", C.c_int32),
+                ("alias_warps", C.c_int32), ("tuned", C.c_int32), ("walk_ms", C.c_float),
+                ("chain_ms", C.c_float), ("alias_ms", C.c_float)]
+
+
 def library_path():
     return _build.LIB
 
@@ -105,6 +111,15 @@ def load():
         "negf_tally_score_size": (U64, [P]),
         "negf_tally_mode_size": (U32, [P]),
         "negf_current_backward": (I32, [P, P, P, D, D, D, P, P, P]),
+        "negf_plan_create": (I32, [P, C.POINTER(negf_wire), I32, C.POINTER(negf_build_opts),
+                                   C.POINTER(negf_run_opts), D, D, D, I32, C.POINTER(P)]),
+        "negf_plan_launch": (I32, [P, P, U64, U64]),
+        "negf_plan_result": (I32, [P, P, P, P, P, P, P]),
+        "negf_plan_get_tuning": (I32, [P, C.POINTER(negf_plan_tuning)]),
+        "negf_plan_num_tasks": (I32, [P]),
+        "negf_plan_num_waves": (I32, [P]),
+        "negf_plan_device_bytes": (U64, [P]),
+        "negf_plan_destroy": (None, [P]),
         "negf_profile_read": (I32, [P, I32, P, P, P, C.POINTER(I32)]),
     }
     for name, (res, args) in sig.items():
@@ -359,3 +374,72 @@ def negf_current_backward(ctx, tables, tally, mu_p, mu_q, kT, dI, n_sites):
                                                   float(kT), dI.ctypes.data, dV.ctypes.data,
                                                   dE.ctypes.data), allow=(NEGF_E_STEPCAP,))
     return dV[:n_sites], dE[:n_sites], st == NEGF_E_STEPCAP
+
+
+class Plan:
+    """Handle of a captured plan plus the arrays it re-reads (kept alive with it)."""
+
+    def __init__(self, handle, keep, n_wires, n_tasks):
+        self.handle, self.keep, self.n_wires, self.n_tasks = handle, keep, n_wires, n_tasks
+
+
+def negf_plan_create(ctx, wires, start_lead, walkers_per_task, mu_p, mu_q, kT, precision="fp32",
+                     memspace="host", max_steps=1 << 20, tasks_per_wave=0, waves_in_flight=0,
+                     memory_budget=0, walk_blocks_per_sm=0, autotune=True):
+    """Capture build + walk + current of a fixed batch into a CUDA graph; returns a Plan."""
+    lib = load()
+    keep = []
+    arr = _wire_array(wires, memspace, keep)
+    bopts = negf_build_opts(PRECISION[precision], 0 if memspace == "host" else 1, 0, 0)
+    ropts = negf_run_opts(int(start_lead), int(tasks_per_wave), 0, int(walkers_per_task), 0,
+                          int(max_steps), int(waves_in_flight), int(memory_budget),
+                          int(walk_blocks_per_sm), 0)
+    out = C.c_void_p()
+    _check(ctx, lib.negf_plan_create(ctx, arr, len(wires), C.byref(bopts), C.byref(ropts),
+                                     float(mu_p), float(mu_q), float(kT), 1 if autotune else 0,
+                                     C.byref(out)))
+    if memspace == "host":
+        keep = []          # host arrays were read during the call
+    return Plan(out, keep, len(wires), lib.negf_plan_num_tasks(out))
+
+
+def negf_plan_launch(ctx, plan, seed, walker_id_offset=0):
+    _check(ctx, load().negf_plan_launch(ctx, plan.handle, int(seed), int(walker_id_offset)))
+
+
+def negf_plan_result(ctx, plan):
+    """dict(I, se, T, T_se, counts, stepcap) of the last launch (synchronises)."""
+    nw, nt = max(plan.n_wires, 1), max(plan.n_tasks, 1)
+    I, se, T, Tse = np.zeros(nw), np.zeros(nw), np.zeros(nt), np.zeros(nt)
+    counts = np.zeros((nt, TALLY_FIELDS), dtype=np.uint64)
+    st = _check(ctx, load().negf_plan_result(ctx, plan.handle, I.ctypes.data, se.ctypes.data,
+                                             T.ctypes.data, Tse.ctypes.data, counts.ctypes.data),
+                allow=(NEGF_E_STEPCAP,))
+    return dict(I=I[:plan.n_wires], se=se[:plan.n_wires], T=T[:plan.n_tasks],
+                T_se=Tse[:plan.n_tasks], counts=counts[:plan.n_tasks],
+                stepcap=st == NEGF_E_STEPCAP)
+
+
+def negf_plan_get_tuning(plan):
+    t = negf_plan_tuning()
+    st = load().negf_plan_get_tuning(plan.handle, C.byref(t))
+    if st != NEGF_OK:
+        raise NegfError(st, "negf_plan_get_tuning")
+    return dict(walk_blocks_per_sm=t.walk_blocks_per_sm, chain_warps=t.chain_warps,
+                alias_warps=t.alias_warps, tuned=bool(t.tuned), walk_ms=t.walk_ms,
+                chain_ms=t.chain_ms, alias_ms=t.alias_ms)
+
+
+def negf_plan_num_waves(plan):
+    return load().negf_plan_num_waves(plan.handle)
+
+
+def negf_plan_device_bytes(plan):
+    return load().negf_plan_device_bytes(plan.handle)
+
+
+def negf_plan_destroy(plan):
+    if plan.handle:
+        load().negf_plan_destroy(plan.handle)
+        plan.handle = None
+        plan.keep = []

@@ -41,7 +41,7 @@ def test_binding_signatures_cover_header(lib_path):
     lib = negf.load()
     for n in declared_functions():
         assert getattr(lib, n).restype is not None or n in (
-            "negf_destroy", "negf_tables_free", "negf_tally_free"), n
+            "negf_destroy", "negf_tables_free", "negf_tally_free", "negf_plan_destroy"), n
 
 
 def test_status_codes_match_header():
@@ -64,8 +64,9 @@ def test_struct_layouts_match_header(lib_path):
     #include <stddef.h>
     #include "negf.h"
     int main(void) {
-      printf("%zu %zu %zu %zu\n", sizeof(negf_wire), offsetof(negf_wire, gamma_lead),
-             sizeof(negf_build_opts), sizeof(negf_task_info));
+      printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(negf_wire), offsetof(negf_wire, gamma_lead),
+             sizeof(negf_build_opts), sizeof(negf_task_info), sizeof(negf_run_opts),
+             offsetof(negf_run_opts, walk_blocks_per_sm), sizeof(negf_plan_tuning));
       return 0;
     }'''
     with tempfile.TemporaryDirectory() as d:
@@ -76,7 +77,9 @@ def test_struct_layouts_match_header(lib_path):
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     sizes = [int(x) for x in out]
     assert sizes == [ctypes.sizeof(negf.negf_wire), negf.negf_wire.gamma_lead.offset,
-                     ctypes.sizeof(negf.negf_build_opts), ctypes.sizeof(negf.negf_task_info)]
+                     ctypes.sizeof(negf.negf_build_opts), ctypes.sizeof(negf.negf_task_info),
+                     ctypes.sizeof(negf.negf_run_opts), negf.negf_run_opts.walk_blocks_per_sm.offset,
+                     ctypes.sizeof(negf.negf_plan_tuning)]
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
