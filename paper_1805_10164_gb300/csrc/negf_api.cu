@@ -34,6 +34,8 @@ struct negf_ctx_s {
   std::vector<ProfEntry> prof_entries;
   std::vector<cudaEvent_t> event_pool;
   cudaStream_t walk_stream = nullptr;        // second stream of negf_run (created on first use)
+  cudaStream_t capture_stream = nullptr;     // plans are captured here (the context stream may
+                                             // be the legacy default stream, which cannot be)
 };
 
 struct negf_tables_s {
@@ -271,6 +273,7 @@ void negf_destroy(negf_ctx ctx) {
     cudaStreamSynchronize(ctx->walk_stream);
     cudaStreamDestroy(ctx->walk_stream);
   }
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   cudaFree(ctx->d_counter);
   delete ctx;
 }
@@ -1486,9 +1489,8 @@ struct SegScope {
 
 // Enqueue every step that one launch repeats (inside the capture); `timed` adds event nodes
 // around the kernel groups.
-negf_status plan_enqueue(negf_plan p, bool timed) {
+negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
   negf_ctx ctx = p->ctx;
-  cudaStream_t s = ctx->stream;
   cudaStream_t sw = ctx->walk_stream;
   const Plan& P = p->P;
   Persist& q = p->q;
@@ -1741,8 +1743,10 @@ negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wir
       p->src_eta.push_back(wires[w].eta);
     }
   }
-  if (!ctx->walk_stream &&
-      cudaStreamCreateWithFlags(&ctx->walk_stream, cudaStreamNonBlocking) != cudaSuccess)
+  if ((!ctx->walk_stream &&
+       cudaStreamCreateWithFlags(&ctx->walk_stream, cudaStreamNonBlocking) != cudaSuccess) ||
+      (!ctx->capture_stream &&
+       cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess))
     return bail(fail(ctx, NEGF_E_CUDA, "negf_plan_create: stream creation failed"));
   // persistent buffers (and a first fill of inputs and lead modes)
   st = setup_batch(ctx, s, wires, n_wires, p->dev_in, P, p->q, &p->bytes);
@@ -1835,18 +1839,20 @@ negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wir
     if (st != NEGF_OK) return bail(st);
     if (r.walk_blocks_per_sm > 0) p->tune.walk_blocks_per_sm = r.walk_blocks_per_sm;
   }
-  // capture
+  // capture on the context's capture stream; launches go to the context stream
   {
+    cudaStream_t cs = ctx->capture_stream;
+    CUDA_TRY(ctx, cudaStreamSynchronize(s));
     const bool prof = ctx->prof;
     ctx->prof = false;
-    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) {
       ctx->prof = prof;
       return bail(fail(ctx, NEGF_E_CUDA, "plan: begin capture: %s", cudaGetErrorString(e)));
     }
-    st = plan_enqueue(p, true);
+    st = plan_enqueue(p, true, cs);
     cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(s, &g);
+    e = cudaStreamEndCapture(cs, &g);
     ctx->prof = prof;
     p->graph = g;
     if (st != NEGF_OK) return bail(st);
