@@ -88,3 +88,30 @@ def implied_distribution(entries, exact=False):
         p[c] += keep
         p[int(ali[c])] += m - keep
     return p
+
+
+def build_two_level(w, L, W):
+    """Two-level alias tables of a weight matrix [rows, L*W + 2] whose first L*W columns are the
+    sites of L slices of W sites each and whose last two are the leads.
+
+    The Step 6' draw over K = L*W + 2 outcomes factorises exactly: P(slice k, site a) =
+    P1(k) P2(a | k) with P1 over the L slice totals and the two lead weights, and P2 the slice's
+    own weights over its total.  Returns (level1 [rows, L + 2], level2 [rows, L, W]) uint64
+    entries; a slice of zero total gets all-full slots (never drawn).
+    Pinned by: the product of the two implied distributions equals weights / row sum.
+    """
+    w = np.asarray(w, dtype=np.float64)
+    rows = w.shape[0]
+    sites = w[:, :L * W].reshape(rows, L, W)
+    w1 = np.concatenate([sites.sum(axis=2), w[:, L * W:]], axis=1)
+    level1 = np.stack([vose(r) for r in w1])
+    level2 = np.stack([np.stack([vose(sites[i, k]) for k in range(L)]) for i in range(rows)])
+    return level1, level2
+
+
+def implied_two_level(level1_row, level2_row):
+    """Distribution over the L*W + 2 outcomes realised by one two-level row."""
+    p1 = implied_distribution(level1_row)
+    L = level2_row.shape[0]
+    out = [p1[k] * implied_distribution(level2_row[k]) for k in range(L)]
+    return np.concatenate(out + [p1[L:]])

@@ -77,3 +77,60 @@ def walk(entries, mode_entries, n, W, c_open, task, start_lead, seed, wids, max_
                 words = tuple(wd[sel] for wd in words)
         s += 1
     return lead, steps
+
+
+def walk_two_level(level1, level2, mode_entries, n, L, W, c_open, task, start_lead, seed, wids,
+                   max_steps):
+    """The same walk over two-level tables (level1 [n + 2W, L + 2], level2 [n + 2W, L, W]).
+
+    Random numbers: Philox block 0 of the walker is the injection draw (words x0, x1); block
+    s >= 1 is transition s: words (x0, x1) draw the slice or lead from the row's level-1 entries
+    (K1 = L + 2), and for a slice k the words (x2, x3) draw the site a from level-2 row (row, k)
+    of W entries; the next row is k*W + a.  Outcomes and step counts as in ``walk``.
+    Pinned by: absorption probabilities and mean steps against the exact chain expectation.
+    """
+    wids = np.asarray(wids, dtype=np.uint64)
+    m = wids.size
+    K1 = L + 2
+    lead = np.full(m, -2, dtype=np.int32)
+    steps = np.zeros(m, dtype=np.uint32)
+    if m == 0:
+        return lead, steps
+    if not c_open[start_lead]:
+        lead[:] = -1
+        return lead, steps
+    wlo = wids & MASK32
+    whi = wids >> np.uint64(32)
+    k0 = int(seed) & 0xFFFFFFFF
+    k1 = (int(seed) >> 32) & 0xFFFFFFFF
+    active = np.arange(m)
+    row = np.zeros(m, dtype=np.int64)
+    s = 0
+    while active.size:
+        if s >= 1 and s > max_steps:
+            break
+        b = np.full(active.size, s, dtype=np.uint64)
+        x0, x1, x2, x3 = (v.astype(np.uint64) for v in
+                          philox4x32_10(b, wlo[active], whi[active], np.full(active.size, task),
+                                        k0, k1))
+        if s == 0:
+            c = ((x0 * np.uint64(W)) >> np.uint64(32)).astype(np.int64)
+            e = mode_entries[start_lead][c]
+            mode = np.where(x1 < (e & MASK32), c, (e >> np.uint64(32)).astype(np.int64))
+            row[active] = n + start_lead * W + mode
+        else:
+            r = row[active]
+            c = ((x0 * np.uint64(K1)) >> np.uint64(32)).astype(np.int64)
+            e = level1[r, c]
+            k = np.where(x1 < (e & MASK32), c, (e >> np.uint64(32)).astype(np.int64))
+            steps[active] = s
+            done = k >= L
+            lead[active[done]] = (k[done] - L).astype(np.int32)
+            kk = np.where(done, 0, k)
+            c2 = ((x2 * np.uint64(W)) >> np.uint64(32)).astype(np.int64)
+            e2 = level2[r, kk, c2]
+            a = np.where(x3 < (e2 & MASK32), c2, (e2 >> np.uint64(32)).astype(np.int64))
+            row[active] = np.where(done, 0, kk * W + a)
+            active = active[~done]
+        s += 1
+    return lead, steps

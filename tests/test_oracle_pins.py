@@ -263,6 +263,42 @@ def test_walker_statistics_match_exact_chain():
     assert abs(steps.var() / var - 1.0) < 0.1
 
 
+def test_two_level_tables_realise_the_weights():
+    """Level 1 over slice totals and leads, level 2 within a slice: the product of the exact
+    implied distributions equals weights / row sum (zero slices included)."""
+    rng = np.random.default_rng(31)
+    L, W = 5, 4
+    w = rng.exponential(size=(6, L * W + 2))
+    w[1, 2 * W:3 * W] = 0.0                       # an empty slice
+    w[2, L * W:] = 0.0                            # no lead weight
+    l1, l2 = alias.build_two_level(w, L, W)
+    assert l1.shape == (6, L + 2) and l2.shape == (6, L, W)
+    for i in range(6):
+        p = alias.implied_two_level(l1[i], l2[i])
+        assert np.max(np.abs(p - w[i] / w[i].sum())) <= (L + W + 4) * 2.0**-32
+
+
+def test_two_level_walker_statistics_match_exact_chain():
+    on, et = _wire(5, 3, 8, 0.15)
+    r = pipeline.task_reference(on, et, 1.0, 0.45)
+    l1, l2 = alias.build_two_level(r["tab"]["w"], 8, 3)
+    N = 60000
+    lead, steps = walker.walk_two_level(l1, l2, r["mode_entries"], r["n"], 8, 3, r["c_open"],
+                                        task=3, start_lead=0, seed=1234, wids=np.arange(N),
+                                        max_steps=10**6)
+    assert np.all(lead >= 0)
+    P = r["exact"]["P_inj"][0, 1]
+    assert abs(np.mean(lead == 1) - P) < 4.5 * np.sqrt(P * (1 - P) / N)
+    m = r["exact"]["steps_inj"][0]
+    var = r["exact"]["steps2_inj"][0] - m * m
+    assert abs(steps.mean() - m) < 4.5 * np.sqrt(var / N)
+    # truncation as in the one-level walker
+    lead2, steps2 = walker.walk_two_level(l1, l2, r["mode_entries"], r["n"], 8, 3, r["c_open"],
+                                          3, 0, 1234, np.arange(2000), 2)
+    assert np.all((lead2 >= 0) | ((lead2 == -2) & (steps2 == 2)))
+    assert np.array_equal(lead2 >= 0, steps[:2000] <= 2)
+
+
 def test_step_moments_brute_force():
     """Second moment of the number of steps: the fundamental-matrix identity against direct
     iteration of the chain's step distribution P(S = k) on a small wire."""
