@@ -38,9 +38,10 @@
 extern "C" {
 #endif
 
-#define NEGF_ABI_VERSION 1
+#define NEGF_ABI_VERSION 2
 #define NEGF_MAX_W 64            /* widest supported slice (sites across the wire) */
-#define NEGF_MAX_SITES 6400      /* largest supported W*L per wire */
+#define NEGF_MAX_SITES 6400      /* largest W*L per wire with one-level tables */
+#define NEGF_MAX_SITES_TWO_LEVEL 65536 /* largest W*L per wire with two-level tables */
 #define NEGF_MAX_STEPS (1u << 24) /* largest accepted per-walk step cap */
 #define NEGF_TALLY_FIELDS 5      /* u64 counters per task, see negf_tally_counts */
 
@@ -80,7 +81,8 @@ typedef enum { NEGF_LEAD_STRIP = 0, NEGF_LEAD_WIDE_BAND = 1 } negf_lead_model;
  * Lead L couples to slice 0, lead R to slice L-1.  H has onsite[k*W+a] on the diagonal and -t
  * between nearest neighbours along and across the slices. */
 typedef struct {
-  int32_t W, L;                  /* 1 <= W <= NEGF_MAX_W, L >= 1, W*L <= NEGF_MAX_SITES */
+  int32_t W, L;                  /* 1 <= W <= NEGF_MAX_W, L >= 1, W*L <= NEGF_MAX_SITES
+                                    (one-level tables) or NEGF_MAX_SITES_TWO_LEVEL (two-level) */
   double t;                      /* hopping magnitude, > 0 */
   const double* onsite;          /* [L*W] onsite energies, finite */
   const double* eta;             /* [L*W] Buttiker gamma_i >= 0, finite */
@@ -98,7 +100,19 @@ typedef struct {
   int32_t keep_weights; /* nonzero: keep the FP transition weights for negf_export_tables */
   int32_t keep_green;   /* nonzero: also keep G (dense n x n per task), G Phi, the weights and
                            the transverse modes, as negf_current_backward needs them */
+  int32_t table_layout; /* negf_table_layout */
 } negf_build_opts;
+
+/* Layout of the Step 6' tables of a task.
+ * One-level: one alias row of K = n + 2 slots per table row (draw: one 8-byte entry).
+ * Two-level: the draw over the n + 2 outcomes factorises exactly into a level-1 draw over the L
+ * slices and the two leads (weights: the slice totals of the row and the lead weights) and,
+ * for a slice k, a level-2 draw over the W sites of that slice (weights: the row's weights of
+ * those sites).  Entries: level 2 u64 [rows][L][W], level 1 u64 [rows][L + 2].  Table memory
+ * is rows * (n + L + 2) entries either way; the build needs no per-row shared-memory pass over
+ * n + 2 entries, which makes it the layout of long wires.  NEGF_LAYOUT_AUTO: two-level when
+ * W*L > NEGF_MAX_SITES. */
+typedef enum { NEGF_LAYOUT_AUTO = 0, NEGF_LAYOUT_ONE_LEVEL = 1, NEGF_LAYOUT_TWO_LEVEL = 2 } negf_table_layout;
 
 /* Per-task facts, read back from the device (synchronises). */
 typedef struct {
@@ -106,7 +120,7 @@ typedef struct {
   int32_t W, L, n;       /* n = W*L sites */
   int32_t K;             /* row length = n + 2 (sites, then lead L, lead R) */
   int32_t rows;          /* n site rows, then W injection rows of lead L, W of lead R */
-  int32_t reserved;
+  int32_t table_layout;  /* NEGF_LAYOUT_ONE_LEVEL or NEGF_LAYOUT_TWO_LEVEL */
   double energy, energy_weight;
   double c[2];           /* Tr[Gamma_p A] for p = L (0) and R (1), Eq. elast_lin_xpq */
   uint64_t table_offset; /* first entry of this task's rows x K block (tables, score tallies) */
@@ -145,7 +159,9 @@ negf_status negf_get_task_info(negf_ctx ctx, negf_tables tables, int32_t task,
 void negf_tables_free(negf_tables tables);
 
 /* Copy one task's data to host memory.  `what`:
- *   NEGF_EXPORT_ALIAS       u64 [rows*K]  alias entries, row-major
+ *   NEGF_EXPORT_ALIAS       u64 [rows*K]  alias entries, row-major (two-level tasks: the level-2
+ *                                         entries u64 [rows][L][W])
+ *   NEGF_EXPORT_ALIAS_LEVEL1 u64 [rows][L+2] level-1 entries of a two-level task
  *   NEGF_EXPORT_MODE_ALIAS  u64 [2*W]     injection-mode alias entries, lead L then R
  *   NEGF_EXPORT_WEIGHTS     f64 [rows*K]  transition weights (needs keep_weights)
  *   NEGF_EXPORT_MODE_WEIGHTS f64 [2*W]    lambda_m <phi_m|A|phi_m> (Eq. lead_out_probability)
@@ -153,7 +169,7 @@ void negf_tables_free(negf_tables tables);
  * If host_buf is NULL, *bytes receives the size needed.  Otherwise *bytes must be at least
  * that size (NEGF_E_INVALID if not) and receives the bytes written.  Synchronises. */
 enum { NEGF_EXPORT_ALIAS = 0, NEGF_EXPORT_MODE_ALIAS = 1, NEGF_EXPORT_WEIGHTS = 2,
-       NEGF_EXPORT_MODE_WEIGHTS = 3, NEGF_EXPORT_ROWSUM = 4 };
+       NEGF_EXPORT_MODE_WEIGHTS = 3, NEGF_EXPORT_ROWSUM = 4, NEGF_EXPORT_ALIAS_LEVEL1 = 5 };
 negf_status negf_export_tables(negf_ctx ctx, negf_tables tables, int32_t task, int32_t what,
                                void* host_buf, size_t* bytes);
 

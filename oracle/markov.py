@@ -31,8 +31,9 @@ def transition_weights(g, lead_model_modes):
     n, L, W = g["n"], g["L"], g["W"]
     gamma = g["gamma"]
     Gam = [g["GamL"], g["GamR"]]
-    Gd = G.conj().T
-    A = 1j * (G - Gd)
+    # Gamma_L and Gamma_R vanish outside their boundary slices: every product with them is
+    # taken on those W x W blocks
+    sls = [slice(0, W), slice((L - 1) * W, L * W)]
     phi, gam = lead_model_modes
     K = n + 2
     rows = n + 2 * W
@@ -46,22 +47,24 @@ def transition_weights(g, lead_model_modes):
         sl = slice((0 if r == 0 else L - 1) * W, (1 if r == 0 else L) * W)
         Gs = G[sl, :]
         w[:n, n + r] = np.real(np.einsum("ai,ab,bi->i", Gs.conj(), Gam[r][sl, sl], Gs))
-    A_row[:n] = np.real(np.diag(A))
+    A_row[:n] = -2.0 * np.imag(np.diag(G))          # <i|A|i> with A = i (G - G^dag)
     # injection rows and mode distributions
     mode_w = np.zeros((2, W))
     c = np.zeros(2)
     for p, k in enumerate((0, L - 1)):
+        sk = sls[p]                                 # phi_m lives on slice k = 0 or L - 1
+        A_kk = 1j * (G[sk, sk] - G[sk, sk].conj().T)
+        Psi = G[:, sk] @ phi                        # psi_m = G |phi_m>, all modes
         for m in range(W):
-            v = np.zeros(n, dtype=np.complex128)
-            v[k * W:(k + 1) * W] = phi[:, m]
-            psi = G @ v
+            psi = Psi[:, m]
             row = n + p * W + m
             w[row, :n] = gamma * np.abs(psi) ** 2
             for r in range(2):
-                w[row, n + r] = np.real(np.vdot(psi, Gam[r] @ psi))
-            A_row[row] = np.real(np.vdot(v, A @ v))
+                sl = sls[r]
+                w[row, n + r] = np.real(np.vdot(psi[sl], Gam[r][sl, sl] @ psi[sl]))
+            A_row[row] = np.real(np.vdot(phi[:, m], A_kk @ phi[:, m]))
             mode_w[p, m] = gam[m] * A_row[row]
-        c[p] = np.real(np.trace(Gam[p] @ A))
+        c[p] = np.real(np.trace(Gam[p][sk, sk] @ A_kk))
     return dict(w=w, mode_w=mode_w, c=c, A_row=A_row, n=n, W=W, K=K)
 
 

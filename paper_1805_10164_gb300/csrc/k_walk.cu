@@ -90,11 +90,13 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
   // cached task: index window [t_first, t_first + walkers_per_task)
   int tl = -1;
   unsigned long long t_first = 0;
-  uint32_t task_id = 0, K = 0, n = 0, W = 0, inj_row0 = 0;
+  uint32_t task_id = 0, K = 0, n = 0, W = 0, inj_row0 = 0, L = 0;
+  bool two = false;                  // two-level tables (level 1 at l1row, level 2 at trow)
   uint64_t t_tab_off = 0;
   uint32_t t_mode_off = 0;
   bool t_open = false;
   const uint64_t* trow = nullptr;
+  const uint64_t* l1row = nullptr;
   const uint64_t* mrow = nullptr;
   unsigned a[kFields] = {0u, 0u, 0u, 0u, 0u};    // counts of task tl not yet in shared memory
   bool no_more = false;
@@ -116,6 +118,9 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
         t_tab_off = d.tab_off;
         t_mode_off = d.mode_off + start_lead * d.W;
         trow = tab + d.tab_off;
+        two = d.layout == NEGF_LAYOUT_TWO_LEVEL;
+        L = (uint32_t)d.L;
+        l1row = tab + d.l1_off;
         mrow = mode_tab + d.mode_off + start_lead * d.W;
         t_open = cvals[2 * (task0 + tl) + start_lead] > 0.0;
       }
@@ -154,6 +159,31 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
     // transition; later blocks: two Step 6' transitions.
     const uint4 r = philox4x32_10(make_uint4(b, wid_lo, wid_hi, task_id), key);
     int outcome = -3;                  // -3: continue, 0/1: absorbed at L/R, -2: truncated
+    if (two) {
+      // two-level tables: block 0 is the injection draw alone; block b >= 1 is transition b,
+      // words (x, y) for the slice or lead (level 1), (z, w) for the site in the slice
+      if (b == 0) {
+        const uint32_t c = __umulhi(r.x, W);
+        const uint64_t e = __ldg(mrow + c);
+        row = inj_row0 + (r.y < (uint32_t)e ? c : (uint32_t)(e >> 32));
+      } else {
+        const uint32_t K1 = L + 2;
+        const uint32_t c = __umulhi(r.x, K1);
+        const uint64_t e = __ldg(l1row + (uint64_t)row * K1 + c);
+        const uint32_t k = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+        ++steps;
+        if (k >= L) {
+          outcome = (int)(k - L);
+        } else {
+          const uint32_t c2 = __umulhi(r.z, W);
+          const uint64_t e2 = __ldg(trow + ((uint64_t)row * L + k) * W + c2);
+          const uint32_t a = r.w < (uint32_t)e2 ? c2 : (uint32_t)(e2 >> 32);
+          if (steps >= max_steps) outcome = -2;
+          else row = k * W + a;
+        }
+      }
+      ++b;
+    } else {
     if (b == 0) {
       const uint32_t c = __umulhi(r.x, W);
       const uint64_t e = __ldg(mrow + c);
@@ -177,6 +207,7 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
       else row = j;
     }
     ++b;
+    }
     if (kScore && outcome >= 0) {
       // replay the finished walk and count its transitions under its absorbing lead
       unsigned long long* cnt = score.cnt + (size_t)outcome * score.stride + t_tab_off;

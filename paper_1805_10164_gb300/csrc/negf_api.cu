@@ -58,6 +58,7 @@ struct negf_tables_s {
   int32_t* d_err = nullptr;
   uint64_t bytes = 0;
   bool tables_released = false;  // negf_run: alias tables freed wave by wave
+  bool any_two = false;          // some task has two-level tables
   int n_waves = 1;
   void* d_green = nullptr;       // keep_green: dense G per task, then G Phi per task
   void* d_gphi = nullptr;
@@ -317,13 +318,33 @@ struct Plan {
   std::vector<TaskDesc> tasks;
   std::vector<int32_t> wire_task0;
   uint64_t tab_total = 0, green_total = 0, gphi_total = 0, g_total = 0;
+  uint64_t wt_total = 0, l1w_total = 0;    // weights, level-1 weights (after the weights)
   uint64_t wire_total = 0;                 // doubles: onsite then eta per wire
   uint32_t lead_total = 0, mode_total = 0, phi_total = 0;
   int max_W = 1, max_L = 1, max_K = 3;
+  int max_KA = 3;                          // longest row the alias kernel builds
+  bool any_two = false;
 };
 
-negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool dev_in, Plan& P) {
+// Descriptors for the alias kernel: a two-level task's level-1 rows (K = L + 2 slots, weights at
+// l1w_off, entries at l1_off); one-level tasks unchanged.
+std::vector<TaskDesc> alias_descs(const std::vector<TaskDesc>& desc) {
+  std::vector<TaskDesc> a = desc;
+  for (TaskDesc& d : a)
+    if (d.layout == NEGF_LAYOUT_TWO_LEVEL) {
+      d.K = d.L + 2;
+      d.tab_off = d.l1_off;
+      d.wt_off = d.l1w_off;
+    }
+  return a;
+}
+
+negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool dev_in, Plan& P,
+                      int layout_opt = NEGF_LAYOUT_AUTO) {
+  if (layout_opt < NEGF_LAYOUT_AUTO || layout_opt > NEGF_LAYOUT_TWO_LEVEL)
+    return fail(ctx, NEGF_E_INVALID, "unknown table layout %d", layout_opt);
   uint64_t tab_off = 0, g_off = 0, wire_off = 0, start_off = 0, green_off = 0, gphi_off = 0;
+  uint64_t wt_off = 0, l1w_rel = 0;
   uint32_t mode_off = 0, lead_off = 0, row_base = 0, col_base = 0, phi_off = 0;
   P.wire_task0.assign(1, 0);
   for (int w = 0; w < n_wires; ++w) {
@@ -338,9 +359,14 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
       return fail(ctx, NEGF_E_INVALID, "wire %d: wide-band lead needs gamma_lead > 0", w);
     const int64_t n = (int64_t)wr.W * wr.L;
     const int64_t K = n + 2, rows = n + 2 * wr.W;
-    if (n > NEGF_MAX_SITES)
-      return fail(ctx, NEGF_E_INVALID, "wire %d: W*L = %lld exceeds the supported %d sites", w,
-                  (long long)n, NEGF_MAX_SITES);
+    const int layout = layout_opt != NEGF_LAYOUT_AUTO
+                           ? layout_opt
+                           : (n > NEGF_MAX_SITES ? NEGF_LAYOUT_TWO_LEVEL : NEGF_LAYOUT_ONE_LEVEL);
+    const int64_t max_n = layout == NEGF_LAYOUT_TWO_LEVEL ? NEGF_MAX_SITES_TWO_LEVEL : NEGF_MAX_SITES;
+    if (n > max_n)
+      return fail(ctx, NEGF_E_INVALID, "wire %d: W*L = %lld exceeds the %lld sites of %s tables", w,
+                  (long long)n, (long long)max_n,
+                  layout == NEGF_LAYOUT_TWO_LEVEL ? "two-level" : "one-level");
     if (!wr.onsite || !wr.eta || (wr.n_energy > 0 && !wr.energy))
       return fail(ctx, NEGF_E_INVALID, "wire %d: NULL array", w);
     if (!dev_in) {
@@ -381,8 +407,21 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
       d.t = wr.t;
       d.w_E = wE[k];
       d.gamma_lead = wr.gamma_lead;
+      d.layout = layout;
       d.tab_off = tab_off;
-      d.wt_off = tab_off;
+      d.wt_off = wt_off;
+      if (layout == NEGF_LAYOUT_TWO_LEVEL) {
+        d.l1_off = tab_off + (uint64_t)rows * n;
+        d.l1w_off = l1w_rel;               // rebased past the weights below
+        l1w_rel += (uint64_t)rows * (wr.L + 2);
+        tab_off += (uint64_t)rows * (n + wr.L + 2);
+        P.max_KA = std::max(P.max_KA, wr.L + 2);
+        P.any_two = true;
+      } else {
+        tab_off += (uint64_t)rows * K;
+        P.max_KA = std::max(P.max_KA, (int)K);
+      }
+      wt_off += (uint64_t)rows * K;
       d.g_off = g_off;
       d.mode_off = mode_off;
       d.lead_off = lead_off;
@@ -396,7 +435,6 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
       P.tasks.push_back(d);
       green_off += (uint64_t)n * n;
       gphi_off += (uint64_t)n * 2 * wr.W;
-      tab_off += (uint64_t)rows * K;
       g_off += (uint64_t)wr.L * wr.W * wr.W;
       mode_off += 2 * wr.W;
       lead_off += wr.W;
@@ -411,6 +449,10 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
     phi_off += (uint32_t)(wr.W * wr.W);
     P.wire_task0.push_back((int32_t)P.tasks.size());
   }
+  for (TaskDesc& d : P.tasks)
+    if (d.layout == NEGF_LAYOUT_TWO_LEVEL) d.l1w_off += wt_off;
+  P.wt_total = wt_off;
+  P.l1w_total = l1w_rel;
   P.wire_total = wire_off;
   P.tab_total = tab_off;
   P.g_total = g_off;
@@ -427,8 +469,11 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
 struct Wave {
   int t0 = 0, t1 = 0;
   uint64_t tab = 0, g = 0, start = 0, green = 0, gphi = 0;
+  uint64_t wt = 0, l1w = 0;          // weights and level-1 weights (elements)
   uint32_t rows = 0, cols = 0;
+  bool any_two = false;
   std::vector<TaskDesc> desc;
+  std::vector<TaskDesc> adesc;       // alias_descs(desc)
 };
 
 Wave make_wave(const Plan& P, int t0, int t1) {
@@ -437,9 +482,18 @@ Wave make_wave(const Plan& P, int t0, int t1) {
   w.t1 = t1;
   for (int k = t0; k < t1; ++k) {
     TaskDesc d = P.tasks[k];
-    const uint64_t sz = (uint64_t)d.rows * d.K;
+    const uint64_t sz = d.layout == NEGF_LAYOUT_TWO_LEVEL
+                            ? (uint64_t)d.rows * (d.n + d.L + 2)
+                            : (uint64_t)d.rows * d.K;
     d.tab_off = w.tab;
-    d.wt_off = w.tab;
+    d.wt_off = w.wt;
+    w.wt += (uint64_t)d.rows * d.K;
+    if (d.layout == NEGF_LAYOUT_TWO_LEVEL) {
+      d.l1_off = w.tab + (uint64_t)d.rows * d.n;
+      d.l1w_off = w.l1w;                 // rebased past the wave's weights below
+      w.l1w += (uint64_t)d.rows * (d.L + 2);
+      w.any_two = true;
+    }
     d.start_off = w.start;
     d.row_base = w.rows;
     d.col_base = w.cols;          // g_off stays global: the sweeps run once for the batch
@@ -454,6 +508,9 @@ Wave make_wave(const Plan& P, int t0, int t1) {
     w.cols += (uint32_t)(d.L + 2);
     w.desc.push_back(d);
   }
+  for (TaskDesc& d : w.desc)
+    if (d.layout == NEGF_LAYOUT_TWO_LEVEL) d.l1w_off += w.wt;
+  w.adesc = alias_descs(w.desc);
   return w;
 }
 
@@ -461,7 +518,7 @@ Wave make_wave(const Plan& P, int t0, int t1) {
 uint64_t wave_bytes(const Wave& w, int prec) {
   const uint64_t cb = negf::block_bytes(prec);
   const uint64_t wsz = prec == NEGF_FP64 ? 8 : 4;
-  return w.tab * (8 + wsz) + w.start * cb + 8ull * w.rows;
+  return w.tab * 8 + (w.wt + w.l1w) * wsz + w.start * cb + 8ull * w.rows;
 }
 
 // Buffers shared by every wave of a batch.
@@ -565,7 +622,8 @@ negf_status sweep_all(negf_ctx ctx, cudaStream_t s, const Plan& P, const Persist
 // weights go to *weights_out when it is non-null (kept), else they are freed too.  Row sums go
 // to d_rowsum.
 negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& w,
-                       TaskDesc* d_wdesc, const Persist& q, int prec, const void* d_gL,
+                       TaskDesc* d_wdesc, TaskDesc* d_adesc, const Persist& q, int prec,
+                       const void* d_gL,
                        const void* d_gR, uint64_t* d_tab, double* d_rowsum, void** weights_out,
                        void* d_green = nullptr, void* d_gphi = nullptr,
                        double* pre_start = nullptr, void* pre_weights = nullptr,
@@ -581,7 +639,8 @@ negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& 
   cudaError_t e = cudaSuccess;
   if (own) {
     e = dalloc(&d_start, w.start * cw, s, nullptr);
-    if (e == cudaSuccess) e = cudaMallocAsync(&d_weights, std::max<uint64_t>(w.tab, 1) * wsz, s);
+    if (e == cudaSuccess)
+      e = cudaMallocAsync(&d_weights, std::max<uint64_t>(w.wt + w.l1w, 1) * wsz, s);
   }
   auto cleanup = [&]() {
     if (!own) return;
@@ -602,9 +661,13 @@ negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& 
                                    q.d_mode_w, q.d_c + 2 * (size_t)w.t0, q.d_err, d_green,
                                    d_gphi, s, chain_warps);
   }
+  if (e == cudaSuccess && w.any_two) {
+    ProfScope ps(ctx, "two_level_kernel", 1, s);
+    e = negf::launch_two_level_split(d_wdesc, nt, w.rows, prec, d_weights, d_tab, q.d_err, s);
+  }
   if (e == cudaSuccess) {
     ProfScope ps(ctx, "alias_kernel", 1, s);
-    e = negf::launch_alias_build(d_wdesc, nt, w.rows, P.max_K, prec, d_weights, d_rowsum,
+    e = negf::launch_alias_build(d_adesc, nt, w.rows, P.max_KA, prec, d_weights, d_rowsum,
                                  q.d_mode_w, d_tab, q.d_mode_tab, q.d_err, s, alias_warps);
   }
   if (e != cudaSuccess) {
@@ -632,7 +695,7 @@ void adopt_persist(negf_tables t, const Persist& q) {
 }
 
 negf_status check_opts(negf_ctx ctx, const negf_build_opts* opts, negf_build_opts& o) {
-  o = negf_build_opts{NEGF_FP64, NEGF_MEM_HOST, 0, 0};
+  o = negf_build_opts{NEGF_FP64, NEGF_MEM_HOST, 0, 0, NEGF_LAYOUT_AUTO};
   if (opts) o = *opts;
   if (o.precision < NEGF_FP64 || o.precision > NEGF_SPLIT_TF32)
     return fail(ctx, NEGF_E_INVALID, "unknown precision %d", o.precision);
@@ -661,8 +724,10 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   DeviceGuard guard(ctx->device);
   cudaStream_t s = ctx->stream;
   Plan P;
-  st = make_plan(ctx, wires, n_wires, dev_in, P);
+  st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout);
   if (st != NEGF_OK) return st;
+  if (o.keep_green && P.any_two)
+    return fail(ctx, NEGF_E_INVALID, "keep_green needs one-level tables (the gradient keeps dense G)");
   negf_tables t = new (std::nothrow) negf_tables_s;
   if (!t) return fail(ctx, NEGF_E_NOMEM, "negf_build_tables: host allocation");
   t->ctx = ctx;
@@ -685,9 +750,17 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   // one wave holding every task: its rebased descriptors equal the global ones
   const Wave w = make_wave(P, 0, t->n_tasks);
   t->total_jobs = w.rows;
+  t->any_two = P.any_two;
+  TaskDesc* d_adesc = nullptr;
   cudaError_t e = dalloc(&t->d_tab, w.tab, s, &t->bytes);
   if (e == cudaSuccess) e = dalloc(&t->d_rowsum, w.rows, s, &t->bytes);
+  if (e == cudaSuccess && !w.adesc.empty()) e = dalloc(&d_adesc, w.adesc.size(), s, nullptr);
+  if (e == cudaSuccess && !w.adesc.empty())
+    e = cudaMemcpyAsync(d_adesc, w.adesc.data(), sizeof(TaskDesc) * w.adesc.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !w.adesc.empty()) e = cudaStreamSynchronize(s);   // host copy source
   if (e != cudaSuccess) {
+    dfree(d_adesc, s);
     free_persist_scratch(q, s);
     release_tables(t);
     return fail(ctx, e == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,
@@ -701,6 +774,7 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
     e = cudaMallocAsync(&t->d_green, std::max<uint64_t>(w.green, 1) * cb, s);
     if (e == cudaSuccess) e = cudaMallocAsync(&t->d_gphi, std::max<uint64_t>(w.gphi, 1) * cb, s);
     if (e != cudaSuccess) {
+      dfree(d_adesc, s);
       free_persist_scratch(q, s);
       release_tables(t);
       return fail(ctx, e == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,
@@ -720,8 +794,10 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   if (e != cudaSuccess) st = fail(ctx, NEGF_E_NOMEM, "RGF scratch: %s", cudaGetErrorString(e));
   if (st == NEGF_OK) st = sweep_all(ctx, s, P, q, prec, d_gL, d_gR);
   if (st == NEGF_OK)
-    st = build_wave(ctx, s, P, w, t->d_tasks, q, prec, d_gL, d_gR, t->d_tab, t->d_rowsum,
-                    (o.keep_weights || o.keep_green) ? &kept : nullptr, t->d_green, t->d_gphi);
+    st = build_wave(ctx, s, P, w, t->d_tasks, d_adesc, q, prec, d_gL, d_gR, t->d_tab,
+                    t->d_rowsum, (o.keep_weights || o.keep_green) ? &kept : nullptr, t->d_green,
+                    t->d_gphi);
+  dfree(d_adesc, s);
   if (d_gL) cudaFreeAsync(d_gL, s);
   if (d_gR) cudaFreeAsync(d_gR, s);
   if (o.keep_green) {
@@ -735,7 +811,7 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   }
   if (kept) {
     t->d_weights = kept;
-    t->bytes += std::max<uint64_t>(w.tab, 1) * (prec == NEGF_FP64 ? 8 : 4);
+    t->bytes += std::max<uint64_t>(w.wt + w.l1w, 1) * (prec == NEGF_FP64 ? 8 : 4);
   }
   *out = t;
   return NEGF_OK;
@@ -772,7 +848,7 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
     return fail(ctx, NEGF_E_CUDA, "negf_run: stream creation failed");
   cudaStream_t sw = ctx->walk_stream;
   Plan P;
-  st = make_plan(ctx, wires, n_wires, dev_in, P);
+  st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout);
   if (st != NEGF_OK) return st;
   const int nt = (int)P.tasks.size();
   negf_tables t = new (std::nothrow) negf_tables_s;
@@ -792,6 +868,7 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
   t->max_L = P.max_L;
   t->max_K = P.max_K;
   t->tables_released = true;
+  t->any_two = P.any_two;
   tl->ctx = ctx;
   tl->n_tasks = nt;
   tl->start_lead = r.start_lead;
@@ -827,12 +904,20 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
     k = k1;
   }
   TaskDesc* d_wdesc = nullptr;
+  TaskDesc* d_adesc = nullptr;
   if (st == NEGF_OK && nt > 0) {
-    std::vector<TaskDesc> all;
-    for (const Wave& w : waves) all.insert(all.end(), w.desc.begin(), w.desc.end());
+    std::vector<TaskDesc> all, alla;
+    for (const Wave& w : waves) {
+      all.insert(all.end(), w.desc.begin(), w.desc.end());
+      alla.insert(alla.end(), w.adesc.begin(), w.adesc.end());
+    }
     e = dalloc(&d_wdesc, all.size(), s, nullptr);
+    if (e == cudaSuccess) e = dalloc(&d_adesc, alla.size(), s, nullptr);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_wdesc, all.data(), sizeof(TaskDesc) * all.size(),
+                          cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_adesc, alla.data(), sizeof(TaskDesc) * alla.size(),
                           cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // `all` dies here
     if (e != cudaSuccess) st = fail(ctx, NEGF_E_CUDA, "negf_run: descriptors: %s", cudaGetErrorString(e));
@@ -870,7 +955,8 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
     }
     size_t off = 0;
     for (size_t v = 0; v < w; ++v) off += waves[v].desc.size();
-    st = build_wave(ctx, s, P, wv, d_wdesc + off, q, prec, d_gL, d_gR, d_tab, d_rs, nullptr);
+    st = build_wave(ctx, s, P, wv, d_wdesc + off, d_adesc + off, q, prec, d_gL, d_gR, d_tab, d_rs,
+                    nullptr);
     dfree(d_rs, s);
     if (st != NEGF_OK) {
       dfree(d_tab, s);
@@ -905,6 +991,7 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
     if (walked[w]) cudaEventDestroy(walked[w]);
   }
   dfree(d_wdesc, s);
+  dfree(d_adesc, s);
   if (d_gL) cudaFreeAsync(d_gL, s);
   if (d_gR) cudaFreeAsync(d_gR, s);
   free_persist_scratch(q, s);
@@ -962,7 +1049,7 @@ negf_status negf_get_task_info(negf_ctx ctx, negf_tables t, int32_t task, negf_t
   out->n = d.n;
   out->K = d.K;
   out->rows = d.rows;
-  out->reserved = 0;
+  out->table_layout = d.layout;
   out->table_offset = d.tab_off;
   out->mode_offset = d.mode_off;
   out->energy = d.E;
@@ -978,8 +1065,15 @@ negf_status negf_export_tables(negf_ctx ctx, negf_tables t, int32_t task, int32_
   if (task < 0 || task >= t->n_tasks) return fail(ctx, NEGF_E_INVALID, "task %d out of range", task);
   const TaskDesc& d = t->h_tasks[task];
   size_t need = 0;
+  const bool two = d.layout == NEGF_LAYOUT_TWO_LEVEL;
   switch (what) {
-    case NEGF_EXPORT_ALIAS: need = sizeof(uint64_t) * (size_t)d.rows * d.K; break;
+    case NEGF_EXPORT_ALIAS:
+      need = sizeof(uint64_t) * (size_t)d.rows * (two ? (size_t)d.n : (size_t)d.K);
+      break;
+    case NEGF_EXPORT_ALIAS_LEVEL1:
+      if (!two) return fail(ctx, NEGF_E_INVALID, "task %d has one-level tables", task);
+      need = sizeof(uint64_t) * (size_t)d.rows * (d.L + 2);
+      break;
     case NEGF_EXPORT_MODE_ALIAS: need = sizeof(uint64_t) * 2 * (size_t)d.W; break;
     case NEGF_EXPORT_WEIGHTS:
       if (!t->d_weights) return fail(ctx, NEGF_E_INVALID, "weights were not kept (keep_weights = 0)");
@@ -989,7 +1083,8 @@ negf_status negf_export_tables(negf_ctx ctx, negf_tables t, int32_t task, int32_
     case NEGF_EXPORT_ROWSUM: need = sizeof(double) * (size_t)d.rows; break;
     default: return fail(ctx, NEGF_E_INVALID, "unknown export kind %d", what);
   }
-  if (t->tables_released && (what == NEGF_EXPORT_ALIAS || what == NEGF_EXPORT_ROWSUM))
+  if (t->tables_released && (what == NEGF_EXPORT_ALIAS || what == NEGF_EXPORT_ALIAS_LEVEL1 ||
+                             what == NEGF_EXPORT_ROWSUM))
     return fail(ctx, NEGF_E_INVALID, "the alias tables of this handle were released (negf_run)");
   if (!host_buf) { *bytes = need; return NEGF_OK; }
   if (*bytes < need) return fail(ctx, NEGF_E_INVALID, "export buffer too small (%zu < %zu)", *bytes, need);
@@ -998,6 +1093,9 @@ negf_status negf_export_tables(negf_ctx ctx, negf_tables t, int32_t task, int32_
   switch (what) {
     case NEGF_EXPORT_ALIAS:
       CUDA_TRY(ctx, cudaMemcpyAsync(host_buf, t->d_tab + d.tab_off, need, cudaMemcpyDeviceToHost, s));
+      break;
+    case NEGF_EXPORT_ALIAS_LEVEL1:
+      CUDA_TRY(ctx, cudaMemcpyAsync(host_buf, t->d_tab + d.l1_off, need, cudaMemcpyDeviceToHost, s));
       break;
     case NEGF_EXPORT_MODE_ALIAS:
       CUDA_TRY(ctx, cudaMemcpyAsync(host_buf, t->d_mode_tab + d.mode_off, need, cudaMemcpyDeviceToHost, s));
@@ -1135,6 +1233,8 @@ negf_status negf_walk_score(negf_ctx ctx, negf_tables t, int32_t start_lead, uin
   *out = nullptr;
   if (t->tables_released || !t->d_tab)
     return fail(ctx, NEGF_E_INVALID, "negf_walk_score: the tables of this handle were released");
+  if (t->any_two)
+    return fail(ctx, NEGF_E_INVALID, "negf_walk_score: score tallies need one-level tables");
   if (walkers_per_task > (1ull << 40))
     return fail(ctx, NEGF_E_INVALID, "negf_walk_score: walkers_per_task above 2^40");
   DeviceGuard g(ctx->device);
@@ -1389,6 +1489,7 @@ struct negf_plan_s {
   std::vector<Wave> waves;
   std::vector<size_t> wave_off;              // first rebased descriptor of each wave
   TaskDesc* d_wdesc = nullptr;
+  TaskDesc* d_adesc = nullptr;               // alias descriptors of every wave
   void* d_gL = nullptr;
   void* d_gR = nullptr;
   int slots = 1;                             // waves whose tables exist at once
@@ -1450,6 +1551,7 @@ void plan_release(negf_plan p) {
   dfree(q.d_c, s);
   dfree(q.d_err, s);
   dfree(p->d_wdesc, s);
+  dfree(p->d_adesc, s);
   if (p->d_gL) cudaFreeAsync(p->d_gL, s);
   if (p->d_gR) cudaFreeAsync(p->d_gR, s);
   for (auto& x : p->d_tab) dfree(x, s);
@@ -1536,6 +1638,7 @@ negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
     if (split && w >= (size_t)p->slots)
       CUDA_TRY(ctx, cudaStreamWaitEvent(s, p->sync_ev[2 * (w - p->slots) + 1], 0));
     TaskDesc* dd = p->d_wdesc + p->wave_off[w];
+    TaskDesc* da = p->d_adesc + p->wave_off[w];
     const int ntw = wv.t1 - wv.t0;
     {
       SegScope sg(p, "diag_chain_kernels", 2, s, timed);
@@ -1546,9 +1649,14 @@ negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
                         q.d_mode_w, q.d_c + 2 * (size_t)wv.t0, q.d_err, nullptr, nullptr, s,
                         p->tune.chain_warps));
     }
+    if (wv.any_two) {
+      SegScope sg(p, "two_level_kernel", 1, s, timed);
+      CUDA_TRY(ctx, negf::launch_two_level_split(dd, ntw, wv.rows, prec, p->d_weights[slot],
+                                                 p->d_tab[slot], q.d_err, s));
+    }
     {
       SegScope sg(p, "alias_kernel", 1, s, timed);
-      CUDA_TRY(ctx, negf::launch_alias_build(dd, ntw, wv.rows, P.max_K, prec, p->d_weights[slot],
+      CUDA_TRY(ctx, negf::launch_alias_build(da, ntw, wv.rows, P.max_KA, prec, p->d_weights[slot],
                                              p->d_rs[slot], q.d_mode_w, p->d_tab[slot],
                                              q.d_mode_tab, q.d_err, s, p->tune.alias_warps));
     }
@@ -1616,6 +1724,7 @@ negf_status plan_autotune(negf_plan p) {
   Persist& q = p->q;
   const Wave& wv = p->waves[0];
   TaskDesc* dd = p->d_wdesc;
+  TaskDesc* da = p->d_adesc;
   const int prec = p->prec;
   const int nt0 = wv.t1 - wv.t0;
   auto columns = [&](int cw) {
@@ -1625,9 +1734,15 @@ negf_status plan_autotune(negf_plan p) {
                                       p->d_weights[0], p->d_rs[0], q.d_mode_w, q.d_c, q.d_err,
                                       nullptr, nullptr, s, cw);
   };
+  auto columns_split = [&](int cw) {
+    cudaError_t e = columns(cw);
+    if (e == cudaSuccess && wv.any_two)
+      e = negf::launch_two_level_split(dd, nt0, wv.rows, prec, p->d_weights[0], p->d_tab[0],
+                                       q.d_err, s);
+    return e;
+  };
   auto alias = [&](int aw) {
-    // the alias kernel overwrites A in the row sums: restore them first (outside the timing)
-    return negf::launch_alias_build(dd, nt0, wv.rows, P.max_K, prec, p->d_weights[0],
+    return negf::launch_alias_build(da, nt0, wv.rows, P.max_KA, prec, p->d_weights[0],
                                     p->d_rs[0], q.d_mode_w, p->d_tab[0], q.d_mode_tab, q.d_err,
                                     s, aw);
   };
@@ -1644,17 +1759,18 @@ negf_status plan_autotune(negf_plan p) {
   // alias warps (each candidate runs on freshly computed row values)
   int best_aw = 0;
   float best_a = -1.f;
-  const int amax = negf::alias_warps_max(P.max_K);
+  const int amax = negf::alias_warps_max(P.max_KA);
   for (int aw : {2, 4, 8, 12, 16}) {
     if (aw > amax) break;
-    if (columns(best_cw) != cudaSuccess) return fail(ctx, NEGF_E_CUDA, "autotune: columns");
+    // fresh row values (the alias kernel replaces A by the row sums)
+    if (columns_split(best_cw) != cudaSuccess) return fail(ctx, NEGF_E_CUDA, "autotune: columns");
     const float ms = time_on(s, 1, [&]() { return alias(aw); });
     if (ms < 0.f) return fail(ctx, NEGF_E_CUDA, "autotune: alias build failed");
     if (best_a < 0.f || ms < best_a) best_a = ms, best_aw = aw;
   }
   if (best_aw == 0) best_aw = amax;
   // leave wave 0 built with the chosen shapes
-  if (columns(best_cw) != cudaSuccess || alias(best_aw) != cudaSuccess)
+  if (columns_split(best_cw) != cudaSuccess || alias(best_aw) != cudaSuccess)
     return fail(ctx, NEGF_E_CUDA, "autotune: rebuild failed");
   // walk grid: CTAs per SM (the tally of the candidates is discarded)
   int best_wb = 0;
@@ -1732,7 +1848,7 @@ negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wir
     plan_release(p);
     return code;
   };
-  st = make_plan(ctx, wires, n_wires, p->dev_in, p->P);
+  st = make_plan(ctx, wires, n_wires, p->dev_in, p->P, o.table_layout);
   if (st != NEGF_OK) return bail(st);
   const Plan& P = p->P;
   const int nt = (int)P.tasks.size();
@@ -1776,19 +1892,25 @@ negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wir
     k = k1;
   }
   p->slots = p->waves.size() > 1 ? std::min<int>(depth, (int)p->waves.size()) : 1;
-  uint64_t max_tab = 1, max_rows = 1, max_start = 1;
-  std::vector<TaskDesc> all;
+  uint64_t max_tab = 1, max_rows = 1, max_start = 1, max_wt = 1;
+  std::vector<TaskDesc> all, alla;
   for (const Wave& w : p->waves) {
     p->wave_off.push_back(all.size());
     all.insert(all.end(), w.desc.begin(), w.desc.end());
+    alla.insert(alla.end(), w.adesc.begin(), w.adesc.end());
+    max_wt = std::max(max_wt, w.wt + w.l1w);
     max_tab = std::max(max_tab, w.tab);
     max_rows = std::max<uint64_t>(max_rows, w.rows);
     max_start = std::max(max_start, w.start);
   }
   if (nt > 0) {
     e = dalloc(&p->d_wdesc, all.size(), s, &p->bytes);
+    if (e == cudaSuccess) e = dalloc(&p->d_adesc, alla.size(), s, &p->bytes);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(p->d_wdesc, all.data(), sizeof(TaskDesc) * all.size(),
+                          cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(p->d_adesc, alla.data(), sizeof(TaskDesc) * alla.size(),
                           cudaMemcpyHostToDevice, s);
     const uint64_t gb = std::max<uint64_t>(P.g_total, 1) * negf::block_bytes(p->prec);
     if (e == cudaSuccess) e = cudaMallocAsync(&p->d_gL, gb, s);
@@ -1804,8 +1926,8 @@ negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wir
       e = dalloc(&p->d_tab[k], max_tab, s, &p->bytes);
       if (e == cudaSuccess) e = dalloc(&p->d_rs[k], max_rows, s, &p->bytes);
       if (e == cudaSuccess) e = dalloc(&p->d_start[k], max_start * cw, s, &p->bytes);
-      if (e == cudaSuccess) e = cudaMallocAsync(&p->d_weights[k], max_tab * wsz, s);
-      p->bytes += max_tab * wsz;
+      if (e == cudaSuccess) e = cudaMallocAsync(&p->d_weights[k], max_wt * wsz, s);
+      p->bytes += max_wt * wsz;
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // `all` dies here
     if (e != cudaSuccess)

@@ -33,6 +33,10 @@ struct TaskDesc {
   uint64_t start_off;    // start blocks [L + 2][W][W] complex
   uint64_t green_off;    // dense G [n][n] (kept for the gradient)
   uint64_t gphi_off;     // G Phi of both leads [n][2W] (kept for the gradient)
+  int32_t layout;        // NEGF_LAYOUT_ONE_LEVEL or NEGF_LAYOUT_TWO_LEVEL
+  int32_t pad_;
+  uint64_t l1_off;       // two-level: level-1 entries [rows][L + 2] (level 2 is at tab_off)
+  uint64_t l1w_off;      // two-level: level-1 weights [rows][L + 2] in the weights array
 };
 
 struct cd { double x, y; };
@@ -98,6 +102,13 @@ cudaError_t launch_alias_build(const TaskDesc* d_tasks, int n_tasks, uint32_t to
                                int warps = 0);
 // Warps per CTA the alias kernel can use for rows of max_K slots (shared memory bound).
 int alias_warps_max(int max_K);
+// Two-level tasks: from the weights [rows][K] of every table row, the level-1 weights (slice
+// totals, then the two lead weights; at l1w_off of the same weights array) and the level-2
+// alias rows (one per row and slice, W slots, at tab_off).  One-level tasks are skipped.
+// n_jobs = sum over tasks of rows + 2 (the row_base numbering).
+cudaError_t launch_two_level_split(const TaskDesc* d_tasks, int n_tasks, uint32_t n_jobs,
+                                   int precision, void* d_weights, uint64_t* d_tab,
+                                   int32_t* d_err, cudaStream_t s);
 // Walks of tasks d_tasks[task0 .. task0 + n_tasks); d_c is indexed like d_tasks, d_tally holds
 // the counters of those tasks (index 0 = task0).  The Philox task number of d_tasks[k] is
 // id_base + k.  max_blocks_per_sm > 0 caps the persistent grid (leaving room for concurrent

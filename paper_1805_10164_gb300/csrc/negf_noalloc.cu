@@ -103,6 +103,7 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
     TaskDesc& d = h_tasks[k];
     d.wire = 0;
     d.e_idx = k;
+    d.layout = NEGF_LAYOUT_ONE_LEVEL;
     d.W = wr.W;
     d.L = wr.L;
     d.n = (int)n;

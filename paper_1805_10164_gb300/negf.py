@@ -15,7 +15,9 @@ from . import build as _build
 
 NEGF_OK, NEGF_E_INVALID, NEGF_E_NOMEM, NEGF_E_CUDA, NEGF_E_NUMERIC, NEGF_E_STEPCAP, NEGF_E_TIMEOUT = range(7)
 PRECISION = {"fp64": 0, "fp32": 1, "split_tf32": 2}
-EXPORT = {"alias": 0, "mode_alias": 1, "weights": 2, "mode_weights": 3, "rowsum": 4}
+EXPORT = {"alias": 0, "mode_alias": 1, "weights": 2, "mode_weights": 3, "rowsum": 4,
+          "alias_level1": 5}
+LAYOUT = {"auto": 0, "one_level": 1, "two_level": 2}
 TALLY_FIELDS = 5
 MAX_STEPS = 1 << 24
 _STATUS = {0: "NEGF_OK", 1: "NEGF_E_INVALID", 2: "NEGF_E_NOMEM", 3: "NEGF_E_CUDA",
@@ -37,13 +39,13 @@ class negf_wire(C.Structure):
 
 class negf_build_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("memspace", C.c_int32), ("keep_weights", C.c_int32),
-                ("keep_green", C.c_int32)]
+                ("keep_green", C.c_int32), ("table_layout", C.c_int32)]
 
 
 class negf_task_info(C.Structure):
     _fields_ = [("wire", C.c_int32), ("energy_index", C.c_int32), ("W", C.c_int32),
                 ("L", C.c_int32), ("n", C.c_int32), ("K", C.c_int32), ("rows", C.c_int32),
-                ("reserved", C.c_int32), ("energy", C.c_double), ("energy_weight", C.c_double),
+                ("table_layout", C.c_int32), ("energy", C.c_double), ("energy_weight", C.c_double),
                 ("c", C.c_double * 2), ("table_offset", C.c_uint64), ("mode_offset", C.c_uint64)]
 
 
@@ -184,12 +186,13 @@ def _wire_array(wires, memspace, keep):
 
 def negf_run(ctx, wires, start_lead, seed, walkers_per_task, precision="fp32", memspace="host",
              walker_id_offset=0, max_steps=1 << 20, tasks_per_wave=0, waves_in_flight=0,
-             memory_budget=0, walk_blocks_per_sm=0):
+             memory_budget=0, walk_blocks_per_sm=0, layout="auto"):
     """Build + walk pipelined in waves.  Returns (tasks handle, tally handle)."""
     lib = load()
     keep = []
     arr = _wire_array(wires, memspace, keep)
-    bopts = negf_build_opts(PRECISION[precision], 0 if memspace == "host" else 1, 0, 0)
+    bopts = negf_build_opts(PRECISION[precision], 0 if memspace == "host" else 1, 0, 0,
+                            LAYOUT[layout])
     ropts = negf_run_opts(int(start_lead), int(tasks_per_wave), int(seed), int(walkers_per_task),
                           int(walker_id_offset), int(max_steps), int(waves_in_flight),
                           int(memory_budget), int(walk_blocks_per_sm), 0)
@@ -205,14 +208,14 @@ def negf_tables_num_waves(tables):
 
 
 def negf_build_tables(ctx, wires, precision="fp64", memspace="host", keep_weights=False,
-                      keep_green=False):
+                      keep_green=False, layout="auto"):
     """wires: objects with W, L, t, onsite, eta, energy, energy_weight, lead_model, gamma_lead
     (numpy float64 arrays for memspace 'host', torch CUDA float64 tensors for 'device')."""
     lib = load()
     keep = []
     arr = _wire_array(wires, memspace, keep)
     opts = negf_build_opts(PRECISION[precision], 0 if memspace == "host" else 1,
-                           1 if keep_weights else 0, 1 if keep_green else 0)
+                           1 if keep_weights else 0, 1 if keep_green else 0, LAYOUT[layout])
     out = C.c_void_p()
     _check(ctx, lib.negf_build_tables(ctx, arr, len(wires), C.byref(opts), C.byref(out)))
     del keep
@@ -233,6 +236,7 @@ def negf_get_task_info(ctx, tables, task):
     return dict(wire=info.wire, energy_index=info.energy_index, W=info.W, L=info.L, n=info.n,
                 K=info.K, rows=info.rows, energy=info.energy, energy_weight=info.energy_weight,
                 c=np.array([info.c[0], info.c[1]]), table_offset=info.table_offset,
+                layout={1: "one_level", 2: "two_level"}.get(info.table_layout, "unknown"),
                 mode_offset=info.mode_offset)
 
 
@@ -245,7 +249,7 @@ def negf_export_tables(ctx, tables, task, what):
     kind = EXPORT[what]
     nbytes = C.c_size_t(0)
     _check(ctx, lib.negf_export_tables(ctx, tables, int(task), kind, None, C.byref(nbytes)))
-    dtype = np.uint64 if what in ("alias", "mode_alias") else np.float64
+    dtype = np.uint64 if what in ("alias", "mode_alias", "alias_level1") else np.float64
     buf = np.empty(nbytes.value // 8, dtype=dtype)
     _check(ctx, lib.negf_export_tables(ctx, tables, int(task), kind, buf.ctypes.data,
                                        C.byref(nbytes)))
@@ -385,12 +389,13 @@ class Plan:
 
 def negf_plan_create(ctx, wires, start_lead, walkers_per_task, mu_p, mu_q, kT, precision="fp32",
                      memspace="host", max_steps=1 << 20, tasks_per_wave=0, waves_in_flight=0,
-                     memory_budget=0, walk_blocks_per_sm=0, autotune=True):
+                     memory_budget=0, walk_blocks_per_sm=0, autotune=True, layout="auto"):
     """Capture build + walk + current of a fixed batch into a CUDA graph; returns a Plan."""
     lib = load()
     keep = []
     arr = _wire_array(wires, memspace, keep)
-    bopts = negf_build_opts(PRECISION[precision], 0 if memspace == "host" else 1, 0, 0)
+    bopts = negf_build_opts(PRECISION[precision], 0 if memspace == "host" else 1, 0, 0,
+                            LAYOUT[layout])
     ropts = negf_run_opts(int(start_lead), int(tasks_per_wave), 0, int(walkers_per_task), 0,
                           int(max_steps), int(waves_in_flight), int(memory_budget),
                           int(walk_blocks_per_sm), 0)
