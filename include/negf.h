@@ -63,8 +63,11 @@ typedef enum {
  * NEGF_FP32: lead self-energies in FP64; the W x W inversions of the RGF sweeps and of the
  * diagonal blocks, the block-column propagation and the transition weights in complex64 /
  * FP32; the sum-rule values <i|A|i>, row sums, mode weights and c_p in FP64; alias thresholds
- * in exact integer arithmetic.  NEGF_SPLIT_TF32 is accepted and currently computed as
- * NEGF_FP32. */
+ * in exact integer arithmetic.  NEGF_SPLIT_TF32: as NEGF_FP32, except that wires of W = 64
+ * get two-level tables built by the tensor cores: each block-column step G_{k,m} = -t g_k
+ * G_{k+1,m} (Sec. III.B) runs as a real GEMM of the complex64 blocks split into TF32 high and
+ * low parts (three products, FP32 accumulation), fused with the emission of the level-2 alias
+ * rows, so no weight is written (NEGF_EXPORT_WEIGHTS is refused for those tasks). */
 typedef enum { NEGF_FP64 = 0, NEGF_FP32 = 1, NEGF_SPLIT_TF32 = 2 } negf_precision;
 
 /* Where the arrays of a negf_wire live. */
@@ -346,7 +349,7 @@ negf_status negf_current(negf_ctx ctx, negf_tables tables, negf_tally tally, dou
  *                                          rows = W*L + 2W, K = W*L + 2)
  *   d_mode_alias  u64 [n_energy][2][W]     injection-mode alias entries
  *   d_c           f64 [n_energy][2]        Tr[Gamma_p A] for p = L, R
- * precision: NEGF_FP64 or NEGF_FP32 (NEGF_SPLIT_TF32 computes as NEGF_FP32).
+ * precision: NEGF_FP64 or NEGF_FP32 (NEGF_SPLIT_TF32 computes as NEGF_FP32 here).
  * The call runs on `stream` (a cudaStream_t on the current device) and synchronises it before
  * returning, so device-side failures are reported by its status.
  * Limits and errors: 1 <= n_energy <= NEGF_NOALLOC_MAX_TASKS and W*L <= NEGF_MAX_SITES, else

@@ -1,0 +1,122 @@
+// Alias row of k <= 64 weights built by one thread in exact integer arithmetic (no scratch
+// memory): the level-2 rows of two-level Step 6' tables.
+//
+// Quantisation as in the warp-wide row build: the largest weight is scaled into [2^31, 2^32)
+// by a power of two and every weight truncated to an integer m_i; T = sum m_i.  Slot units
+// u_i = floor(m_i k 2^32 / T) are evaluated with the per-row reciprocal R0 = floor((2^64-1)/T)
+// (each low by at most 65 units), and the shortfall k 2^32 - sum u_i goes to the largest item,
+// so that every one of the k slots holds exactly 2^32 units.  Small items (u < 2^32) are then
+// paired with the current large item, lowest indices first; a large item whose remainder drops
+// below 2^32 is paired next.  u_i is recomputed from w_i when needed.  Zero rows get all-full
+// slots.  Entry = threshold (low 32 bits) | alias (high 32 bits); full slots alias themselves.
+#pragma once
+
+#include <stdint.h>
+
+namespace negf {
+
+__device__ __forceinline__ uint64_t small_pack(uint32_t thr, uint32_t alias) {
+  return (uint64_t)thr | ((uint64_t)alias << 32);
+}
+__device__ __forceinline__ uint32_t small_fixp(float w, int sh) {
+  return __float2uint_rz(ldexpf(w, sh));
+}
+__device__ __forceinline__ uint32_t small_fixp(double w, int sh) {
+  return __double2uint_rz(ldexp(w, sh));
+}
+
+// wget(i) returns weight i (float or double); put(i, entry) stores slot i.  Returns false when
+// a weight is negative or not finite (it is treated as 0).
+template <typename R, typename Get, typename Put>
+__device__ bool alias_small(int k, Get wget, Put put) {
+  constexpr uint64_t kSlot = 1ull << 32;
+  bool ok = true;
+  R wmax = 0;
+  int imax = 0;
+  for (int i = 0; i < k; ++i) {
+    const R v = wget(i);
+    if (!(v >= (R)0) || !isfinite(v)) {
+      ok = false;
+    } else if (v > wmax) {
+      wmax = v;
+      imax = i;
+    }
+  }
+  if (!(wmax > (R)0)) {
+    for (int i = 0; i < k; ++i) put(i, small_pack(0xffffffffu, (uint32_t)i));
+    return ok;
+  }
+  int e = 0;
+  frexp((double)wmax, &e);
+  const int sh = 32 - e;                         // wmax 2^sh in [2^31, 2^32)
+  auto m_of = [&](int i) -> uint64_t {
+    const R v = wget(i);
+    return (v >= (R)0 && isfinite(v)) ? (uint64_t)small_fixp(v, sh) : 0ull;
+  };
+  uint64_t T = 0;
+  for (int i = 0; i < k; ++i) T += m_of(i);
+  const uint64_t R0 = ~0ull / T;
+  auto u_base = [&](int i) -> uint64_t {
+    const uint64_t X = m_of(i) * (uint64_t)k;
+    return (__umul64hi(X, R0) << 32) | ((X * R0) >> 32);
+  };
+  uint64_t sum = 0;
+  for (int i = 0; i < k; ++i) sum += u_base(i);
+  const uint64_t rem = ((uint64_t)k << 32) - sum;
+  auto u_of = [&](int i) -> uint64_t { return u_base(i) + (i == imax ? rem : 0ull); };
+  uint64_t small = 0, large = 0;
+  for (int i = 0; i < k; ++i) {
+    if (u_of(i) < kSlot) small |= 1ull << i;
+    else large |= 1ull << i;
+  }
+  int cur = -1;
+  uint64_t ul = 0;
+  if (large) {
+    cur = __ffsll((long long)large) - 1;
+    large &= large - 1;
+    ul = u_of(cur);
+  }
+  int pend = -1;
+  uint64_t pv = 0;
+  while (true) {
+    int s;
+    uint64_t us;
+    if (pend >= 0) {
+      s = pend;
+      us = pv;
+      pend = -1;
+    } else if (small) {
+      s = __ffsll((long long)small) - 1;
+      small &= small - 1;
+      us = u_of(s);
+    } else {
+      break;
+    }
+    if (cur < 0) {
+      put(s, small_pack(0xffffffffu, (uint32_t)s));
+      continue;
+    }
+    put(s, small_pack((uint32_t)us, (uint32_t)cur));
+    ul -= kSlot - us;
+    if (ul < kSlot) {
+      pend = cur;
+      pv = ul;
+      if (large) {
+        cur = __ffsll((long long)large) - 1;
+        large &= large - 1;
+        ul = u_of(cur);
+      } else {
+        cur = -1;
+      }
+    }
+  }
+  if (cur >= 0) put(cur, small_pack(0xffffffffu, (uint32_t)cur));
+  while (large) {
+    const int i = __ffsll((long long)large) - 1;
+    large &= large - 1;
+    put(i, small_pack(0xffffffffu, (uint32_t)i));
+  }
+  return ok;
+}
+
+}  // namespace negf

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "alias_small.cuh"
 #include "negf_internal.cuh"
 
 namespace negf {
@@ -228,109 +229,6 @@ __global__ void alias_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
   }
 }
 
-// Alias row of k <= 64 weights built by one thread, in exact integer arithmetic: quantise as in
-// alias_row (largest weight scaled into [2^31, 2^32), truncated; T = sum of the m_i), slot units
-// u_i = floor(m_i k 2^32 / T) evaluated with a per-row reciprocal R0 = floor((2^64 - 1) / T)
-// (each u_i low by at most 65 units of 2^-32), the shortfall given to the largest item so that
-// sum u_i = k 2^32 exactly; then small items (u < 2^32) are paired with the current large item,
-// lowest indices first, and a large item whose remainder drops below 2^32 is paired next.
-// Zero rows get all-full slots.  u: scratch [k].  Returns false for a negative or non-finite
-// weight (treated as 0).
-template <typename R>
-__device__ bool alias_small(const R* __restrict__ w, int k, uint64_t* __restrict__ out,
-                            uint64_t* u) {
-  bool ok = true;
-  R wmax = 0;
-  int imax = 0;
-  for (int i = 0; i < k; ++i) {
-    R v = w[i];
-    if (!(v >= (R)0) || !isfinite(v)) {
-      ok = false;
-      v = 0;
-    }
-    if (v > wmax) {
-      wmax = v;
-      imax = i;
-    }
-  }
-  if (!(wmax > (R)0)) {
-    for (int i = 0; i < k; ++i) out[i] = pack(0xffffffffu, (uint32_t)i);
-    return ok;
-  }
-  int e = 0;
-  frexp((double)wmax, &e);
-  const int sh = 32 - e;
-  uint64_t T = 0;
-  for (int i = 0; i < k; ++i) {
-    R v = w[i];
-    if (!(v >= (R)0) || !isfinite(v)) v = 0;
-    const uint64_t m = fixp(v, sh);
-    u[i] = m;
-    T += m;
-  }
-  const uint64_t R0 = ~0ull / T;
-  uint64_t sum = 0, small = 0, large = 0;
-  for (int i = 0; i < k; ++i) {
-    const uint64_t X = u[i] * (uint64_t)k;
-    const uint64_t ui = (__umul64hi(X, R0) << 32) | ((X * R0) >> 32);
-    u[i] = ui;
-    sum += ui;
-  }
-  u[imax] += ((uint64_t)k << 32) - sum;
-  for (int i = 0; i < k; ++i) {
-    if (u[i] < kSlot) small |= 1ull << i;
-    else large |= 1ull << i;
-  }
-  int cur = -1;
-  uint64_t ul = 0;
-  if (large) {
-    cur = __ffsll((long long)large) - 1;
-    large &= large - 1;
-    ul = u[cur];
-  }
-  int pend = -1;
-  uint64_t pv = 0;
-  while (true) {
-    int sidx;
-    uint64_t us;
-    if (pend >= 0) {
-      sidx = pend;
-      us = pv;
-      pend = -1;
-    } else if (small) {
-      sidx = __ffsll((long long)small) - 1;
-      small &= small - 1;
-      us = u[sidx];
-    } else {
-      break;
-    }
-    if (cur < 0) {
-      out[sidx] = pack(0xffffffffu, (uint32_t)sidx);
-      continue;
-    }
-    out[sidx] = pack((uint32_t)us, (uint32_t)cur);
-    ul -= kSlot - us;
-    if (ul < kSlot) {
-      pend = cur;
-      pv = ul;
-      if (large) {
-        cur = __ffsll((long long)large) - 1;
-        large &= large - 1;
-        ul = u[cur];
-      } else {
-        cur = -1;
-      }
-    }
-  }
-  if (cur >= 0) out[cur] = pack(0xffffffffu, (uint32_t)cur);
-  while (large) {
-    const int i = __ffsll((long long)large) - 1;
-    large &= large - 1;
-    out[i] = pack(0xffffffffu, (uint32_t)i);
-  }
-  return ok;
-}
-
 // One warp per table row of a two-level task; lanes take the row's slices.
 template <typename R>
 __global__ void two_level_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
@@ -345,21 +243,22 @@ __global__ void two_level_kernel(const TaskDesc* __restrict__ tasks, int n_tasks
     if (tasks[mid].row_base <= job) lo = mid; else hi = mid - 1;
   }
   const TaskDesc& d = tasks[lo];
-  if (d.layout != NEGF_LAYOUT_TWO_LEVEL) return;
+  if (d.layout != NEGF_LAYOUT_TWO_LEVEL || d.fused) return;
   const int row = (int)(job - d.row_base);
   if (row >= d.rows) return;
   const int W = d.W, L = d.L, n = d.n;
   const R* wr = weights + d.wt_off + (uint64_t)row * d.K;
   R* l1 = weights + d.l1w_off + (uint64_t)row * (L + 2);
   uint64_t* l2 = tab + d.tab_off + (uint64_t)row * n;
-  uint64_t u[64];
   bool ok = true;
   for (int k = lane; k < L; k += 32) {
     const R* ws = wr + k * W;
     double S = 0.0;
     for (int a = 0; a < W; ++a) S += (double)ws[a];
     l1[k] = (R)S;
-    ok &= alias_small<R>(ws, W, l2 + (uint64_t)k * W, u);
+    uint64_t* out = l2 + (uint64_t)k * W;
+    ok &= alias_small<R>(W, [&](int i) { return ws[i]; },
+                         [&](int i, uint64_t e) { out[i] = e; });
   }
   if (lane == 0) {
     l1[L] = wr[n];

@@ -1,0 +1,417 @@
+// Block-column propagation of the RGF on the 5th-generation tensor cores (tcgen05, sm_103a) for
+// slices of W = 64 sites, fused with the emission of two-level Step 6' tables.
+//
+// Sec. III.B: with the left-connected blocks g^L_k the block column of start slice m obeys
+// G_{k,m} = -t g^L_k G_{k+1,m} for k < m (towards slice 0), and with the right-connected blocks
+// G_{k,m} = -t g^R_k G_{k-1,m} for k > m.  Table row b of block column y (site (m, b), or
+// injection mode b of a lead, whose start block is G_mm Phi) needs, for every slice k, the
+// weights w_a = eta_{k,a} |X_k[a][b]|^2 of X_k = G_{k,m} (Eq. draw_i_simult).  Two-level tables
+// keep them as a level-2 alias row over a and their total as the level-1 weight of slice k, so
+// no weight is ever written to memory.
+//
+// One CTA (4 warps) runs one job: a pair of block columns of one task in one direction.  Thread
+// t owns table row b = t mod 64 of column t / 64 of the pair and TMEM lane t.  A step k is the
+// complex 64 x 64 product for both columns at once, written as one real GEMM with M = 128
+// (2 columns x 64 rows b), N = K' = 128:
+//   A[t]  = (Re X_{k+1}[:, b], Im X_{k+1}[:, b])                 TMEM (the previous step's D)
+//   B     = [[Re G^T, Im G^T], [-Im G^T, Re G^T]],  G = -t g_k    shared memory, K-major
+//   D[t]  = (Re X_k[:, b], Im X_k[:, b])                          TMEM
+// 3xTF32: A = A_hi + A_lo and B = B_hi + B_lo with hi the operand rounded to TF32 and lo the
+// exact FP32 remainder; D = A_lo B_hi + A_hi B_lo + A_hi B_hi accumulated in FP32 (the dropped
+// A_lo B_lo term is below FP32 rounding).  The epilogue reads D, forms the row's 64 weights,
+// builds its level-2 alias row, writes the level-1 weight, and stores the TF32 split of D back
+// to TMEM as the next step's A.  The slice-0 and slice-(L-1) blocks of every column are also
+// written out (edge blocks): the lead weights of the level-1 rows are formed from them by
+// lead_weights_kernel.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "alias_small.cuh"
+#include "negf_internal.cuh"
+
+namespace negf {
+namespace {
+
+constexpr int kW = 64;
+constexpr int kThreads = 128;
+constexpr uint32_t kTmemCols = 512;           // D: 0..127, A_hi: 128..255, A_lo: 256..383
+constexpr uint32_t kColD = 0, kColAh = 128, kColAl = 256;
+constexpr size_t kBBytes = 128 * 128 * 4;     // one B split: N' = 128 rows x K' = 128 TF32
+constexpr size_t kWBytes = (size_t)kW * kThreads * 4;
+constexpr size_t kSmem = 2 * kBBytes + kWBytes + 64;
+constexpr uint32_t kWaitLimit = 1u << 20;     // bounded mbarrier wait (iterations)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---- tcgen05 / mbarrier primitives (PTX ISA, tensor core 5th generation) -------------------
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+               :: "r"(smem_u32(dst)), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;"
+               :: "r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+// D (+)= A B with A in TMEM (M = 128 lanes, K = 8 TF32 columns), B from a shared-memory
+// descriptor, FP32 accumulation; accumulate = 0 overwrites D.
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}"
+      :: "r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
+}
+// Arrive on the mbarrier once every MMA issued so far by this thread has completed.
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+               :: "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+      :
+      : "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15]), "r"(v[16]), "r"(v[17]), "r"(v[18]), "r"(v[19]), "r"(v[20]), "r"(v[21]), "r"(v[22]), "r"(v[23]), "r"(v[24]), "r"(v[25]), "r"(v[26]), "r"(v[27]), "r"(v[28]), "r"(v[29]), "r"(v[30]), "r"(v[31])
+      : "memory");
+}
+
+// Shared-memory matrix descriptor, K-major, no swizzle: core matrices of 8 rows x 16 bytes,
+// LBO = byte distance between core matrices adjacent along K, SBO = between 8-row groups.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Byte offset of B^T element (n', k') in the core-matrix layout: the 32 core matrices of an
+// 8-row group along K are contiguous (LBO = 128 B); groups are 4096 B apart (SBO).
+constexpr uint32_t kLBO = 128, kSBO = 4096;
+
+// B = split TF32 embedding of G = mt g (g: 64 x 64 complex64, row-major [a][c]).  Thread t
+// writes row n' = t of B^T: t < 64 (real output a = t): (Re G[a][c])_c, (-Im G[a][c])_c;
+// t >= 64 (imaginary output a = t - 64): (Im G[a][c])_c, (Re G[a][c])_c.
+__device__ __forceinline__ void build_b(const cf* __restrict__ g, float mt, unsigned char* bh,
+                                        unsigned char* bl, int t) {
+  const int a = t & 63, part = t >> 6;
+  const float4* grow = reinterpret_cast<const float4*>(g + (size_t)a * kW);
+  const uint32_t rowb = (uint32_t)(t >> 3) * 32u * 128u + (uint32_t)(t & 7) * 16u;
+  auto put = [&](int q, float v0, float v1, float v2, float v3) {
+    const uint32_t h0 = to_tf32(v0), h1 = to_tf32(v1), h2 = to_tf32(v2), h3 = to_tf32(v3);
+    uint4 hv = make_uint4(h0, h1, h2, h3);
+    uint4 lv = make_uint4(__float_as_uint(v0 - __uint_as_float(h0)),
+                          __float_as_uint(v1 - __uint_as_float(h1)),
+                          __float_as_uint(v2 - __uint_as_float(h2)),
+                          __float_as_uint(v3 - __uint_as_float(h3)));
+    *reinterpret_cast<uint4*>(bh + rowb + (uint32_t)q * 128u) = hv;
+    *reinterpret_cast<uint4*>(bl + rowb + (uint32_t)q * 128u) = lv;
+  };
+#pragma unroll 4
+  for (int c4 = 0; c4 < 16; ++c4) {
+    const float4 p = __ldg(grow + 2 * c4), r = __ldg(grow + 2 * c4 + 1);
+    const float re0 = mt * p.x, im0 = mt * p.y, re1 = mt * p.z, im1 = mt * p.w;
+    const float re2 = mt * r.x, im2 = mt * r.y, re3 = mt * r.z, im3 = mt * r.w;
+    if (part == 0) {
+      put(c4, re0, re1, re2, re3);
+      put(16 + c4, -im0, -im1, -im2, -im3);
+    } else {
+      put(c4, im0, im1, im2, im3);
+      put(16 + c4, re0, re1, re2, re3);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads, 1) chain_tc_kernel(
+    const TaskDesc* __restrict__ tasks, const TcJob* __restrict__ jobs,
+    const float* __restrict__ eta32, const cf* __restrict__ gL, const cf* __restrict__ gR,
+    const cf* __restrict__ start, float* __restrict__ l1w, uint64_t* __restrict__ tab,
+    cf* __restrict__ edge, int32_t* err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* bh = smem;
+  unsigned char* bl = smem + kBBytes;
+  float* wbuf = reinterpret_cast<float*>(smem + 2 * kBBytes);     // [a][thread]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * kBBytes + kWBytes);
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(mbar + 1);
+
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    tmem_alloc(s_tmem, kTmemCols);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(mbar, 1);
+    fence_mbar_init();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tbase = *s_tmem;
+  const uint32_t tlane = tbase + ((uint32_t)(warp * 32) << 16);   // this warp's lane quarter
+
+  const TcJob job = jobs[blockIdx.x];
+  const TaskDesc d = tasks[job.task];
+  const int L = d.L, n = d.n, K1 = d.L + 2;
+  const int dir = job.dir;
+  const int col = tid >> 6, b = tid & 63;
+  const int y = col == 0 ? job.y0 : job.y1;
+  const bool has = y >= 0;                      // warp-uniform (64 threads per column)
+  auto m0_of = [&](int yy) { return yy < L ? yy : (yy == L ? 0 : L - 1); };
+  const int m0 = has ? m0_of(y) : 0;
+  const uint64_t row = !has ? 0
+                       : (y < L ? (uint64_t)y * kW + b : (uint64_t)n + (uint64_t)(y - L) * kW + b);
+  const float mt = (float)(-d.t);
+  const float* eta = eta32 + d.onsite_off / 2;
+  const cf* gsrc = (dir == 0 ? gL : gR) + d.g_off;
+  const cf* st = start + d.start_off + (uint64_t)(has ? y : 0) * kW * kW;
+  uint64_t* l2 = tab + d.tab_off;
+  float* l1 = l1w + d.l1w_off;
+  cf* ed = edge + d.edge_off + (uint64_t)(has ? y : 0) * 2 * kW * kW;   // [slot][a][b]
+  bool ok = true;
+
+  // level-1 weight and level-2 alias row of slice k from the weights in wbuf
+  auto emit = [&](int k) {
+    float S = 0.f;
+    for (int a = 0; a < kW; ++a) S += wbuf[a * kThreads + tid];
+    l1[row * K1 + k] = S;
+    uint64_t* out = l2 + (row * L + k) * kW;
+    ok &= alias_small<float>(kW, [&](int i) { return wbuf[i * kThreads + tid]; },
+                             [&](int i, uint64_t e) { out[i] = e; });
+  };
+
+  // ---- direction 0 emits every column's start slice
+  if (dir == 0 && has) {
+    for (int a = 0; a < kW; ++a) {
+      const cf v = st[a * kW + b];
+      wbuf[a * kThreads + tid] = eta[m0 * kW + a] * (v.x * v.x + v.y * v.y);
+      if (m0 == 0) ed[(0 * kW + a) * kW + b] = v;
+      if (m0 == L - 1) ed[(1 * kW + a) * kW + b] = v;
+    }
+    emit(m0);
+  }
+
+  // ---- propagation over the union of the pair's slices
+  const int m0a = m0_of(job.y0), m0b = job.y1 >= 0 ? m0_of(job.y1) : m0a;
+  const int k_first = dir == 0 ? max(m0a, m0b) - 1 : min(m0a, m0b) + 1;
+  const int k_end = dir == 0 ? -1 : L;
+  const int kstep = dir == 0 ? -1 : 1;
+  // instruction descriptor: D F32, A and B TF32, K-major both, N = 128, M = 128
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) |
+                         ((128u >> 4) << 24);
+  const uint64_t dbh = smem_desc(smem_u32(bh), kLBO, kSBO);
+  const uint64_t dbl = smem_desc(smem_u32(bl), kLBO, kSBO);
+  uint32_t phase = 0;
+  bool timeout = false;
+  for (int k = k_first; k != k_end; k += kstep) {
+    const bool active = has && (dir == 0 ? k < m0 : k > m0);
+    const bool joining = has && (dir == 0 ? k == m0 - 1 : k == m0 + 1);
+    if (joining) {
+      // A = the split start block column b
+      for (int half = 0; half < 2; ++half) {
+        uint32_t rh[32], rl[32], ih[32], il[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const cf v = st[(half * 32 + i) * kW + b];
+          rh[i] = to_tf32(v.x);
+          rl[i] = __float_as_uint(v.x - __uint_as_float(rh[i]));
+          ih[i] = to_tf32(v.y);
+          il[i] = __float_as_uint(v.y - __uint_as_float(ih[i]));
+        }
+        tmem_st32(tlane + kColAh + half * 32, rh);
+        tmem_st32(tlane + kColAl + half * 32, rl);
+        tmem_st32(tlane + kColAh + 64 + half * 32, ih);
+        tmem_st32(tlane + kColAl + 64 + half * 32, il);
+      }
+    }
+    build_b(gsrc + (uint64_t)k * kW * kW, mt, bh, bl, tid);
+    tmem_st_wait();
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid == 0) {
+      uint32_t acc = 0;
+      for (int pass = 0; pass < 3; ++pass) {
+        const uint32_t acol = pass == 0 ? kColAl : kColAh;
+        const uint64_t bd = pass == 1 ? dbl : dbh;
+        for (int s = 0; s < 16; ++s) {
+          mma_tf32_ts(tbase + kColD, tbase + acol + (uint32_t)s * 8u,
+                      bd + (uint64_t)((s * 2 * kLBO) >> 4), idesc, acc);
+          acc = 1;
+        }
+      }
+      mma_commit(mbar);
+    }
+    bool done = false;
+    for (uint32_t it = 0; it < kWaitLimit && !done; ++it) done = mbar_try_wait(mbar, phase);
+    phase ^= 1u;
+    if (__syncthreads_or(!done)) {
+      timeout = true;
+      break;
+    }
+    tc_fence_after();
+    if (active) {
+      const bool more = k + kstep != k_end;
+      const int slot = (dir == 0 && k == 0) ? 0 : ((dir == 1 && k == L - 1) ? 1 : -1);
+      const float* ek = eta + k * kW;
+      for (int ch = 0; ch < 4; ++ch) {
+        uint32_t v[32];
+        tmem_ld32(tlane + kColD + ch * 32, v);
+        tmem_ld_wait();
+        const int a0 = (ch & 1) * 32;
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const float x = __uint_as_float(v[i]);
+          float* wp = wbuf + (a0 + i) * kThreads + tid;
+          if (ch < 2) *wp = x * x;
+          else *wp = ek[a0 + i] * (*wp + x * x);
+          if (slot >= 0) {
+            float* e = reinterpret_cast<float*>(ed + ((uint64_t)slot * kW + a0 + i) * kW + b);
+            e[ch < 2 ? 0 : 1] = x;
+          }
+        }
+        if (more) {
+          uint32_t h[32], l[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const float x = __uint_as_float(v[i]);
+            h[i] = to_tf32(x);
+            l[i] = __float_as_uint(x - __uint_as_float(h[i]));
+          }
+          tmem_st32(tlane + kColAh + ch * 32, h);
+          tmem_st32(tlane + kColAl + ch * 32, l);
+        }
+      }
+      emit(k);
+    }
+  }
+  if (__any_sync(0xffffffffu, !ok) && (tid & 31) == 0) atomicOr(err, ERR_NONFINITE);
+  if (timeout && tid == 0) atomicOr(err, ERR_TIMEOUT);
+  tmem_st_wait();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tbase, kTmemCols);
+}
+
+// Lead weights of the level-1 rows of fused tasks: row b of block column y gets, in slot s
+// (0: lead L, 1: lead R), sum_nu Gamma_nu |(Phi^T X)_{nu b}|^2 = <psi_b|Gamma|psi_b> from the
+// edge block X of that column (slice 0 or slice L - 1).  One warp per (task, column, slot).
+constexpr size_t kLeadSmem = sizeof(cf) * kW * kW + sizeof(float) * kW * kW + sizeof(float) * kW;
+
+__global__ void __launch_bounds__(32) lead_weights_kernel(
+    const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
+    const float* __restrict__ phi32, const double* __restrict__ gam,
+    const cf* __restrict__ edge, float* __restrict__ l1w) {
+  extern __shared__ __align__(16) unsigned char lsm[];
+  cf* s_x = reinterpret_cast<cf*>(lsm);                          // [a][b]
+  float* s_phi = reinterpret_cast<float*>(s_x + kW * kW);        // [a][nu]
+  float* s_gam = s_phi + kW * kW;
+  const int lane = threadIdx.x;
+  const uint32_t job = blockIdx.x;
+  if (job >= n_jobs) return;
+  int lo = 0, hi = n_tasks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (2 * tasks[mid].col_base <= job) lo = mid; else hi = mid - 1;
+  }
+  const TaskDesc& d = tasks[lo];
+  if (!d.fused) return;
+  const uint32_t local = job - 2 * d.col_base;
+  const int y = (int)(local >> 1), slot = (int)(local & 1);
+  const int L = d.L, n = d.n, K1 = d.L + 2;
+  const cf* X = edge + d.edge_off + ((uint64_t)y * 2 + slot) * kW * kW;
+  for (int i = lane; i < kW * kW; i += 32) {
+    s_x[i] = X[i];
+    s_phi[i] = phi32[d.phi_off + i];
+  }
+  for (int i = lane; i < kW; i += 32) s_gam[i] = (float)gam[d.lead_off + i];
+  __syncwarp();
+  for (int bb = lane; bb < kW; bb += 32) {
+    float sum = 0.f;
+    for (int nu = 0; nu < kW; ++nu) {
+      float zr = 0.f, zi = 0.f;
+      for (int a = 0; a < kW; ++a) {
+        const float p = s_phi[a * kW + nu];
+        const cf x = s_x[a * kW + bb];
+        zr += p * x.x;
+        zi += p * x.y;
+      }
+      sum += s_gam[nu] * (zr * zr + zi * zi);
+    }
+    const uint64_t row = y < L ? (uint64_t)y * kW + bb : (uint64_t)n + (uint64_t)(y - L) * kW + bb;
+    l1w[d.l1w_off + row * K1 + L + slot] = sum;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_chain_tc(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols,
+                            const TcJob* d_jobs, uint32_t n_jobs, const float* d_eta32,
+                            const float* d_phi32, const double* d_gam, const void* d_gL,
+                            const void* d_gR, const void* d_start, void* d_weights,
+                            uint64_t* d_tab, void* d_edge, int32_t* d_err, cudaStream_t s) {
+  if (n_jobs == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(chain_tc_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e != cudaSuccess) return e;
+  chain_tc_kernel<<<n_jobs, kThreads, kSmem, s>>>(
+      d_tasks, d_jobs, d_eta32, static_cast<const cf*>(d_gL), static_cast<const cf*>(d_gR),
+      static_cast<const cf*>(d_start), static_cast<float*>(d_weights), d_tab,
+      static_cast<cf*>(d_edge), d_err);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const uint32_t lead_jobs = 2 * n_cols;
+  e = cudaFuncSetAttribute(lead_weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kLeadSmem);
+  if (e != cudaSuccess) return e;
+  lead_weights_kernel<<<lead_jobs, 32, kLeadSmem, s>>>(
+      d_tasks, n_tasks, lead_jobs, d_phi32, d_gam, static_cast<const cf*>(d_edge),
+      static_cast<float*>(d_weights));
+  return cudaGetLastError();
+}
+
+}  // namespace negf

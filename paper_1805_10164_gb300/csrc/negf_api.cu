@@ -15,6 +15,7 @@
 
 using negf::cd;
 using negf::TaskDesc;
+using negf::TcJob;
 
 // Per-kernel device-time accounting (CUDA events on the context stream around each launch).
 struct ProfEntry {
@@ -208,7 +209,15 @@ std::string err_bits(int32_t e) {
   if (e & negf::ERR_ROWSUM) s += " table row does not sum to <i|A|i>;";
   if (e & negf::ERR_INPUT) s += " input value outside the domain (non-finite, eta < 0 or energy on a lead band edge);";
   if (e & negf::ERR_SINGULAR) s += " singular slice block;";
+  if (e & negf::ERR_TIMEOUT) s += " a bounded device wait gave up;";
   return s;
+}
+
+// Status for a device error word (input errors first, then timeouts, then numerics).
+negf_status err_status(int32_t e) {
+  if (e & negf::ERR_INPUT) return NEGF_E_INVALID;
+  if (e & negf::ERR_TIMEOUT) return NEGF_E_TIMEOUT;
+  return NEGF_E_NUMERIC;
 }
 
 // Synchronise and report any device-side error recorded for the tables.
@@ -216,8 +225,7 @@ negf_status check_device(negf_ctx ctx, negf_tables t) {
   int32_t e = 0;
   CUDA_TRY(ctx, cudaMemcpyAsync(&e, t->d_err, sizeof e, cudaMemcpyDeviceToHost, ctx->stream));
   CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
-  if (e & negf::ERR_INPUT) return fail(ctx, NEGF_E_INVALID, "device check:%s", err_bits(e).c_str());
-  if (e) return fail(ctx, NEGF_E_NUMERIC, "device check:%s", err_bits(e).c_str());
+  if (e) return fail(ctx, err_status(e), "device check:%s", err_bits(e).c_str());
   return NEGF_OK;
 }
 
@@ -324,6 +332,7 @@ struct Plan {
   int max_W = 1, max_L = 1, max_K = 3;
   int max_KA = 3;                          // longest row the alias kernel builds
   bool any_two = false;
+  uint64_t edge_total = 0;                 // fused tasks' edge blocks (complex64)
 };
 
 // Descriptors for the alias kernel: a two-level task's level-1 rows (K = L + 2 slots, weights at
@@ -340,11 +349,11 @@ std::vector<TaskDesc> alias_descs(const std::vector<TaskDesc>& desc) {
 }
 
 negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool dev_in, Plan& P,
-                      int layout_opt = NEGF_LAYOUT_AUTO) {
+                      int layout_opt = NEGF_LAYOUT_AUTO, bool tc = false) {
   if (layout_opt < NEGF_LAYOUT_AUTO || layout_opt > NEGF_LAYOUT_TWO_LEVEL)
     return fail(ctx, NEGF_E_INVALID, "unknown table layout %d", layout_opt);
   uint64_t tab_off = 0, g_off = 0, wire_off = 0, start_off = 0, green_off = 0, gphi_off = 0;
-  uint64_t wt_off = 0, l1w_rel = 0;
+  uint64_t wt_off = 0, l1w_rel = 0, edge_off = 0;
   uint32_t mode_off = 0, lead_off = 0, row_base = 0, col_base = 0, phi_off = 0;
   P.wire_task0.assign(1, 0);
   for (int w = 0; w < n_wires; ++w) {
@@ -359,9 +368,11 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
       return fail(ctx, NEGF_E_INVALID, "wire %d: wide-band lead needs gamma_lead > 0", w);
     const int64_t n = (int64_t)wr.W * wr.L;
     const int64_t K = n + 2, rows = n + 2 * wr.W;
-    const int layout = layout_opt != NEGF_LAYOUT_AUTO
-                           ? layout_opt
-                           : (n > NEGF_MAX_SITES ? NEGF_LAYOUT_TWO_LEVEL : NEGF_LAYOUT_ONE_LEVEL);
+    // the tensor-core chain (split-TF32 builds of W = 64 wires) emits two-level tables
+    const bool tc_wire = tc && wr.W == 64 && layout_opt != NEGF_LAYOUT_ONE_LEVEL;
+    const int layout = tc_wire || (layout_opt == NEGF_LAYOUT_AUTO && n > NEGF_MAX_SITES)
+                           ? NEGF_LAYOUT_TWO_LEVEL
+                           : (layout_opt == NEGF_LAYOUT_AUTO ? NEGF_LAYOUT_ONE_LEVEL : layout_opt);
     const int64_t max_n = layout == NEGF_LAYOUT_TWO_LEVEL ? NEGF_MAX_SITES_TWO_LEVEL : NEGF_MAX_SITES;
     if (n > max_n)
       return fail(ctx, NEGF_E_INVALID, "wire %d: W*L = %lld exceeds the %lld sites of %s tables", w,
@@ -408,8 +419,13 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
       d.w_E = wE[k];
       d.gamma_lead = wr.gamma_lead;
       d.layout = layout;
+      d.fused = tc_wire ? 1 : 0;
       d.tab_off = tab_off;
       d.wt_off = wt_off;
+      if (tc_wire) {
+        d.edge_off = edge_off;
+        edge_off += (uint64_t)(wr.L + 2) * 2 * wr.W * wr.W;
+      }
       if (layout == NEGF_LAYOUT_TWO_LEVEL) {
         d.l1_off = tab_off + (uint64_t)rows * n;
         d.l1w_off = l1w_rel;               // rebased past the weights below
@@ -421,7 +437,7 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
         tab_off += (uint64_t)rows * K;
         P.max_KA = std::max(P.max_KA, (int)K);
       }
-      wt_off += (uint64_t)rows * K;
+      if (!tc_wire) wt_off += (uint64_t)rows * K;      // fused tasks keep no weights
       d.g_off = g_off;
       d.mode_off = mode_off;
       d.lead_off = lead_off;
@@ -453,6 +469,7 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
     if (d.layout == NEGF_LAYOUT_TWO_LEVEL) d.l1w_off += wt_off;
   P.wt_total = wt_off;
   P.l1w_total = l1w_rel;
+  P.edge_total = edge_off;
   P.wire_total = wire_off;
   P.tab_total = tab_off;
   P.g_total = g_off;
@@ -470,11 +487,30 @@ struct Wave {
   int t0 = 0, t1 = 0;
   uint64_t tab = 0, g = 0, start = 0, green = 0, gphi = 0;
   uint64_t wt = 0, l1w = 0;          // weights and level-1 weights (elements)
+  uint64_t edge = 0;                 // edge blocks of fused tasks (complex64)
   uint32_t rows = 0, cols = 0;
   bool any_two = false;
   std::vector<TaskDesc> desc;
   std::vector<TaskDesc> adesc;       // alias_descs(desc)
+  std::vector<TcJob> tcjobs;         // tensor-core chain jobs (task = index into desc)
 };
+
+// Jobs of the tensor-core chain for fused task `k` (index in its wave): direction 0 takes every
+// block column (it also emits the start slices) in pairs of neighbouring start slices, from the
+// far end; direction 1 the columns that have slices beyond their start.
+void add_tc_jobs(std::vector<TcJob>& jobs, int k, int L) {
+  std::vector<std::pair<int, int>> cols;             // (m0, y)
+  for (int y = 0; y < L + 2; ++y) cols.emplace_back(y < L ? y : (y == L ? 0 : L - 1), y);
+  std::vector<std::pair<int, int>> d0 = cols, d1;
+  std::stable_sort(d0.begin(), d0.end(), [](auto a, auto b) { return a.first > b.first; });
+  for (auto& c : cols)
+    if (c.first < L - 1) d1.push_back(c);
+  std::stable_sort(d1.begin(), d1.end(), [](auto a, auto b) { return a.first < b.first; });
+  for (size_t i = 0; i < d0.size(); i += 2)
+    jobs.push_back(TcJob{k, 0, d0[i].second, i + 1 < d0.size() ? d0[i + 1].second : -1});
+  for (size_t i = 0; i < d1.size(); i += 2)
+    jobs.push_back(TcJob{k, 1, d1[i].second, i + 1 < d1.size() ? d1[i + 1].second : -1});
+}
 
 Wave make_wave(const Plan& P, int t0, int t1) {
   Wave w;
@@ -487,7 +523,12 @@ Wave make_wave(const Plan& P, int t0, int t1) {
                             : (uint64_t)d.rows * d.K;
     d.tab_off = w.tab;
     d.wt_off = w.wt;
-    w.wt += (uint64_t)d.rows * d.K;
+    if (!d.fused) w.wt += (uint64_t)d.rows * d.K;
+    if (d.fused) {
+      d.edge_off = w.edge;
+      w.edge += (uint64_t)(d.L + 2) * 2 * d.W * d.W;
+      add_tc_jobs(w.tcjobs, k - t0, d.L);
+    }
     if (d.layout == NEGF_LAYOUT_TWO_LEVEL) {
       d.l1_off = w.tab + (uint64_t)d.rows * d.n;
       d.l1w_off = w.l1w;                 // rebased past the wave's weights below
@@ -511,6 +552,15 @@ Wave make_wave(const Plan& P, int t0, int t1) {
   for (TaskDesc& d : w.desc)
     if (d.layout == NEGF_LAYOUT_TWO_LEVEL) d.l1w_off += w.wt;
   w.adesc = alias_descs(w.desc);
+  // longest chains first (the length of a job is the number of its steps)
+  auto len = [&](const TcJob& j) {
+    const TaskDesc& d = w.desc[j.task];
+    auto m0 = [&](int y) { return y < d.L ? y : (y == d.L ? 0 : d.L - 1); };
+    const int a = m0(j.y0), b = j.y1 >= 0 ? m0(j.y1) : a;
+    return j.dir == 0 ? std::max(a, b) : d.L - 1 - std::min(a, b);
+  };
+  std::stable_sort(w.tcjobs.begin(), w.tcjobs.end(),
+                   [&](const TcJob& x, const TcJob& y) { return len(x) > len(y); });
   return w;
 }
 
@@ -518,7 +568,7 @@ Wave make_wave(const Plan& P, int t0, int t1) {
 uint64_t wave_bytes(const Wave& w, int prec) {
   const uint64_t cb = negf::block_bytes(prec);
   const uint64_t wsz = prec == NEGF_FP64 ? 8 : 4;
-  return w.tab * 8 + (w.wt + w.l1w) * wsz + w.start * cb + 8ull * w.rows;
+  return w.tab * 8 + (w.wt + w.l1w) * wsz + w.start * cb + 8ull * w.rows + 8ull * w.edge;
 }
 
 // Buffers shared by every wave of a batch.
@@ -627,7 +677,8 @@ negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& 
                        const void* d_gR, uint64_t* d_tab, double* d_rowsum, void** weights_out,
                        void* d_green = nullptr, void* d_gphi = nullptr,
                        double* pre_start = nullptr, void* pre_weights = nullptr,
-                       int chain_warps = 0, int alias_warps = 0) {
+                       int chain_warps = 0, int alias_warps = 0,
+                       const TcJob* d_tcjobs = nullptr, void* pre_edge = nullptr) {
   const int nt = w.t1 - w.t0;
   if (nt == 0) return NEGF_OK;
   const uint64_t cw = negf::block_bytes(prec) / sizeof(double);
@@ -636,17 +687,21 @@ negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& 
   const bool own = pre_start == nullptr;
   double* d_start = pre_start;
   void* d_weights = pre_weights;
+  void* d_edge = pre_edge;
   cudaError_t e = cudaSuccess;
   if (own) {
     e = dalloc(&d_start, w.start * cw, s, nullptr);
     if (e == cudaSuccess)
       e = cudaMallocAsync(&d_weights, std::max<uint64_t>(w.wt + w.l1w, 1) * wsz, s);
+    if (e == cudaSuccess && w.edge) e = cudaMallocAsync(&d_edge, w.edge * sizeof(negf::cf), s);
   }
   auto cleanup = [&]() {
     if (!own) return;
     dfree(d_start, s);
     if (d_weights) cudaFreeAsync(d_weights, s);
+    if (d_edge) cudaFreeAsync(d_edge, s);
     d_weights = nullptr;
+    d_edge = nullptr;
   };
   if (e != cudaSuccess) {
     cleanup();
@@ -660,6 +715,12 @@ negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& 
                                    q.d_sig, q.d_gam, d_gL, d_gR, d_start, d_weights, d_rowsum,
                                    q.d_mode_w, q.d_c + 2 * (size_t)w.t0, q.d_err, d_green,
                                    d_gphi, s, chain_warps);
+  }
+  if (e == cudaSuccess && !w.tcjobs.empty()) {
+    ProfScope ps(ctx, "chain_tc_kernel", 2, s);
+    e = negf::launch_chain_tc(d_wdesc, nt, w.cols, d_tcjobs, (uint32_t)w.tcjobs.size(),
+                              q.d_eta32, reinterpret_cast<const float*>(q.d_phi + P.phi_total),
+                              q.d_gam, d_gL, d_gR, d_start, d_weights, d_tab, d_edge, q.d_err, s);
   }
   if (e == cudaSuccess && w.any_two) {
     ProfScope ps(ctx, "two_level_kernel", 1, s);
@@ -724,7 +785,7 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   DeviceGuard guard(ctx->device);
   cudaStream_t s = ctx->stream;
   Plan P;
-  st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout);
+  st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout, o.precision == NEGF_SPLIT_TF32);
   if (st != NEGF_OK) return st;
   if (o.keep_green && P.any_two)
     return fail(ctx, NEGF_E_INVALID, "keep_green needs one-level tables (the gradient keeps dense G)");
@@ -752,15 +813,21 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   t->total_jobs = w.rows;
   t->any_two = P.any_two;
   TaskDesc* d_adesc = nullptr;
+  TcJob* d_tcjobs = nullptr;
   cudaError_t e = dalloc(&t->d_tab, w.tab, s, &t->bytes);
   if (e == cudaSuccess) e = dalloc(&t->d_rowsum, w.rows, s, &t->bytes);
   if (e == cudaSuccess && !w.adesc.empty()) e = dalloc(&d_adesc, w.adesc.size(), s, nullptr);
   if (e == cudaSuccess && !w.adesc.empty())
     e = cudaMemcpyAsync(d_adesc, w.adesc.data(), sizeof(TaskDesc) * w.adesc.size(),
                         cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && !w.adesc.empty()) e = cudaStreamSynchronize(s);   // host copy source
+  if (e == cudaSuccess && !w.tcjobs.empty()) e = dalloc(&d_tcjobs, w.tcjobs.size(), s, nullptr);
+  if (e == cudaSuccess && !w.tcjobs.empty())
+    e = cudaMemcpyAsync(d_tcjobs, w.tcjobs.data(), sizeof(TcJob) * w.tcjobs.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !w.adesc.empty()) e = cudaStreamSynchronize(s);   // host copy sources
   if (e != cudaSuccess) {
     dfree(d_adesc, s);
+    dfree(d_tcjobs, s);
     free_persist_scratch(q, s);
     release_tables(t);
     return fail(ctx, e == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,
@@ -775,6 +842,7 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
     if (e == cudaSuccess) e = cudaMallocAsync(&t->d_gphi, std::max<uint64_t>(w.gphi, 1) * cb, s);
     if (e != cudaSuccess) {
       dfree(d_adesc, s);
+      dfree(d_tcjobs, s);
       free_persist_scratch(q, s);
       release_tables(t);
       return fail(ctx, e == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,
@@ -796,8 +864,9 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   if (st == NEGF_OK)
     st = build_wave(ctx, s, P, w, t->d_tasks, d_adesc, q, prec, d_gL, d_gR, t->d_tab,
                     t->d_rowsum, (o.keep_weights || o.keep_green) ? &kept : nullptr, t->d_green,
-                    t->d_gphi);
+                    t->d_gphi, nullptr, nullptr, 0, 0, d_tcjobs);
   dfree(d_adesc, s);
+  dfree(d_tcjobs, s);
   if (d_gL) cudaFreeAsync(d_gL, s);
   if (d_gR) cudaFreeAsync(d_gR, s);
   if (o.keep_green) {
@@ -848,7 +917,7 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
     return fail(ctx, NEGF_E_CUDA, "negf_run: stream creation failed");
   cudaStream_t sw = ctx->walk_stream;
   Plan P;
-  st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout);
+  st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout, o.precision == NEGF_SPLIT_TF32);
   if (st != NEGF_OK) return st;
   const int nt = (int)P.tasks.size();
   negf_tables t = new (std::nothrow) negf_tables_s;
@@ -905,14 +974,23 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
   }
   TaskDesc* d_wdesc = nullptr;
   TaskDesc* d_adesc = nullptr;
+  TcJob* d_tcjobs = nullptr;
+  std::vector<size_t> job_off;
   if (st == NEGF_OK && nt > 0) {
     std::vector<TaskDesc> all, alla;
+    std::vector<TcJob> jobs;
     for (const Wave& w : waves) {
       all.insert(all.end(), w.desc.begin(), w.desc.end());
       alla.insert(alla.end(), w.adesc.begin(), w.adesc.end());
+      job_off.push_back(jobs.size());
+      jobs.insert(jobs.end(), w.tcjobs.begin(), w.tcjobs.end());
     }
     e = dalloc(&d_wdesc, all.size(), s, nullptr);
     if (e == cudaSuccess) e = dalloc(&d_adesc, alla.size(), s, nullptr);
+    if (e == cudaSuccess && !jobs.empty()) e = dalloc(&d_tcjobs, jobs.size(), s, nullptr);
+    if (e == cudaSuccess && !jobs.empty())
+      e = cudaMemcpyAsync(d_tcjobs, jobs.data(), sizeof(TcJob) * jobs.size(),
+                          cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(d_wdesc, all.data(), sizeof(TaskDesc) * all.size(),
                           cudaMemcpyHostToDevice, s);
@@ -956,7 +1034,8 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
     size_t off = 0;
     for (size_t v = 0; v < w; ++v) off += waves[v].desc.size();
     st = build_wave(ctx, s, P, wv, d_wdesc + off, d_adesc + off, q, prec, d_gL, d_gR, d_tab, d_rs,
-                    nullptr);
+                    nullptr, nullptr, nullptr, nullptr, nullptr, 0, 0,
+                    d_tcjobs ? d_tcjobs + job_off[w] : nullptr);
     dfree(d_rs, s);
     if (st != NEGF_OK) {
       dfree(d_tab, s);
@@ -992,6 +1071,7 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
   }
   dfree(d_wdesc, s);
   dfree(d_adesc, s);
+  dfree(d_tcjobs, s);
   if (d_gL) cudaFreeAsync(d_gL, s);
   if (d_gR) cudaFreeAsync(d_gR, s);
   free_persist_scratch(q, s);
@@ -1077,6 +1157,8 @@ negf_status negf_export_tables(negf_ctx ctx, negf_tables t, int32_t task, int32_
     case NEGF_EXPORT_MODE_ALIAS: need = sizeof(uint64_t) * 2 * (size_t)d.W; break;
     case NEGF_EXPORT_WEIGHTS:
       if (!t->d_weights) return fail(ctx, NEGF_E_INVALID, "weights were not kept (keep_weights = 0)");
+      if (d.fused)
+        return fail(ctx, NEGF_E_INVALID, "task %d: the tensor-core build keeps no weights", task);
       need = sizeof(double) * (size_t)d.rows * d.K;
       break;
     case NEGF_EXPORT_MODE_WEIGHTS: need = sizeof(double) * 2 * (size_t)d.W; break;
@@ -1490,12 +1572,14 @@ struct negf_plan_s {
   std::vector<size_t> wave_off;              // first rebased descriptor of each wave
   TaskDesc* d_wdesc = nullptr;
   TaskDesc* d_adesc = nullptr;               // alias descriptors of every wave
+  TcJob* d_tcjobs = nullptr;                 // tensor-core chain jobs of every wave
+  std::vector<size_t> job_off;
   void* d_gL = nullptr;
   void* d_gR = nullptr;
   int slots = 1;                             // waves whose tables exist at once
   std::vector<uint64_t*> d_tab;              // per slot
   std::vector<double*> d_rs, d_start;
-  std::vector<void*> d_weights;
+  std::vector<void*> d_weights, d_edge;
   uint64_t* d_counts = nullptr;              // [n_tasks][5]
   double* d_out = nullptr;                   // current outputs (launch_current layout)
   uint64_t* d_run = nullptr;                 // seed, walker id offset
@@ -1552,6 +1636,9 @@ void plan_release(negf_plan p) {
   dfree(q.d_err, s);
   dfree(p->d_wdesc, s);
   dfree(p->d_adesc, s);
+  dfree(p->d_tcjobs, s);
+  for (auto& x : p->d_edge)
+    if (x) cudaFreeAsync(x, s);
   if (p->d_gL) cudaFreeAsync(p->d_gL, s);
   if (p->d_gR) cudaFreeAsync(p->d_gR, s);
   for (auto& x : p->d_tab) dfree(x, s);
@@ -1649,6 +1736,14 @@ negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
                         q.d_mode_w, q.d_c + 2 * (size_t)wv.t0, q.d_err, nullptr, nullptr, s,
                         p->tune.chain_warps));
     }
+    if (!wv.tcjobs.empty()) {
+      SegScope sg(p, "chain_tc_kernel", 2, s, timed);
+      CUDA_TRY(ctx, negf::launch_chain_tc(
+                        dd, ntw, wv.cols, p->d_tcjobs + p->job_off[w], (uint32_t)wv.tcjobs.size(),
+                        q.d_eta32, reinterpret_cast<const float*>(q.d_phi + P.phi_total),
+                        q.d_gam, p->d_gL, p->d_gR, p->d_start[slot], p->d_weights[slot],
+                        p->d_tab[slot], p->d_edge[slot], q.d_err, s));
+    }
     if (wv.any_two) {
       SegScope sg(p, "two_level_kernel", 1, s, timed);
       CUDA_TRY(ctx, negf::launch_two_level_split(dd, ntw, wv.rows, prec, p->d_weights[slot],
@@ -1736,6 +1831,11 @@ negf_status plan_autotune(negf_plan p) {
   };
   auto columns_split = [&](int cw) {
     cudaError_t e = columns(cw);
+    if (e == cudaSuccess && !wv.tcjobs.empty())
+      e = negf::launch_chain_tc(dd, nt0, wv.cols, p->d_tcjobs, (uint32_t)wv.tcjobs.size(),
+                                q.d_eta32, reinterpret_cast<const float*>(q.d_phi + P.phi_total),
+                                q.d_gam, p->d_gL, p->d_gR, p->d_start[0], p->d_weights[0],
+                                p->d_tab[0], p->d_edge[0], q.d_err, s);
     if (e == cudaSuccess && wv.any_two)
       e = negf::launch_two_level_split(dd, nt0, wv.rows, prec, p->d_weights[0], p->d_tab[0],
                                        q.d_err, s);
@@ -1798,8 +1898,7 @@ negf_status plan_autotune(negf_plan p) {
   int32_t h_err = 0;
   CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, q.d_err, sizeof h_err, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(ctx, cudaStreamSynchronize(s));
-  if (h_err & negf::ERR_INPUT) return fail(ctx, NEGF_E_INVALID, "device check:%s", err_bits(h_err).c_str());
-  if (h_err) return fail(ctx, NEGF_E_NUMERIC, "device check:%s", err_bits(h_err).c_str());
+  if (h_err) return fail(ctx, err_status(h_err), "device check:%s", err_bits(h_err).c_str());
   return NEGF_OK;
 }
 
@@ -1848,7 +1947,8 @@ negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wir
     plan_release(p);
     return code;
   };
-  st = make_plan(ctx, wires, n_wires, p->dev_in, p->P, o.table_layout);
+  st = make_plan(ctx, wires, n_wires, p->dev_in, p->P, o.table_layout,
+                 o.precision == NEGF_SPLIT_TF32);
   if (st != NEGF_OK) return bail(st);
   const Plan& P = p->P;
   const int nt = (int)P.tasks.size();
@@ -1892,12 +1992,16 @@ negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wir
     k = k1;
   }
   p->slots = p->waves.size() > 1 ? std::min<int>(depth, (int)p->waves.size()) : 1;
-  uint64_t max_tab = 1, max_rows = 1, max_start = 1, max_wt = 1;
+  uint64_t max_tab = 1, max_rows = 1, max_start = 1, max_wt = 1, max_edge = 0;
   std::vector<TaskDesc> all, alla;
+  std::vector<TcJob> jobs;
   for (const Wave& w : p->waves) {
     p->wave_off.push_back(all.size());
+    p->job_off.push_back(jobs.size());
     all.insert(all.end(), w.desc.begin(), w.desc.end());
     alla.insert(alla.end(), w.adesc.begin(), w.adesc.end());
+    jobs.insert(jobs.end(), w.tcjobs.begin(), w.tcjobs.end());
+    max_edge = std::max(max_edge, w.edge);
     max_wt = std::max(max_wt, w.wt + w.l1w);
     max_tab = std::max(max_tab, w.tab);
     max_rows = std::max<uint64_t>(max_rows, w.rows);
@@ -1912,6 +2016,10 @@ negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wir
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(p->d_adesc, alla.data(), sizeof(TaskDesc) * alla.size(),
                           cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && !jobs.empty()) e = dalloc(&p->d_tcjobs, jobs.size(), s, &p->bytes);
+    if (e == cudaSuccess && !jobs.empty())
+      e = cudaMemcpyAsync(p->d_tcjobs, jobs.data(), sizeof(TcJob) * jobs.size(),
+                          cudaMemcpyHostToDevice, s);
     const uint64_t gb = std::max<uint64_t>(P.g_total, 1) * negf::block_bytes(p->prec);
     if (e == cudaSuccess) e = cudaMallocAsync(&p->d_gL, gb, s);
     if (e == cudaSuccess) e = cudaMallocAsync(&p->d_gR, gb, s);
@@ -1922,7 +2030,12 @@ negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wir
     p->d_rs.assign(p->slots, nullptr);
     p->d_start.assign(p->slots, nullptr);
     p->d_weights.assign(p->slots, nullptr);
+    p->d_edge.assign(p->slots, nullptr);
     for (int k = 0; k < p->slots && e == cudaSuccess; ++k) {
+      if (max_edge) {
+        e = cudaMallocAsync(&p->d_edge[k], max_edge * sizeof(negf::cf), s);
+        p->bytes += max_edge * sizeof(negf::cf);
+      }
       e = dalloc(&p->d_tab[k], max_tab, s, &p->bytes);
       if (e == cudaSuccess) e = dalloc(&p->d_rs[k], max_rows, s, &p->bytes);
       if (e == cudaSuccess) e = dalloc(&p->d_start[k], max_start * cw, s, &p->bytes);
@@ -2037,8 +2150,7 @@ negf_status negf_plan_result(negf_ctx ctx, negf_plan p, double* I, double* se, d
                                   cudaMemcpyDeviceToHost, s));
   CUDA_TRY(ctx, cudaMemcpyAsync(&h_err, p->q.d_err, sizeof h_err, cudaMemcpyDeviceToHost, s));
   CUDA_TRY(ctx, cudaStreamSynchronize(s));
-  if (h_err & negf::ERR_INPUT) return fail(ctx, NEGF_E_INVALID, "device check:%s", err_bits(h_err).c_str());
-  if (h_err) return fail(ctx, NEGF_E_NUMERIC, "device check:%s", err_bits(h_err).c_str());
+  if (h_err) return fail(ctx, err_status(h_err), "device check:%s", err_bits(h_err).c_str());
   for (size_t w = 0; w < nw; ++w) {
     if (I) I[w] = h[w];
     if (se) se[w] = h[nw + w];

@@ -13,7 +13,8 @@ enum : int32_t {
   ERR_NONFINITE = 1,      // a Green's function block or weight is not finite
   ERR_ROWSUM = 2,         // a table row sums to <= 0 where the site is coupled
   ERR_INPUT = 4,          // device-resident input failed validation
-  ERR_SINGULAR = 8        // zero pivot in a block inversion
+  ERR_SINGULAR = 8,       // zero pivot in a block inversion
+  ERR_TIMEOUT = 16        // a bounded device wait gave up
 };
 
 // One (wire, energy) task.  Offsets are in elements of the array they index.
@@ -34,9 +35,17 @@ struct TaskDesc {
   uint64_t green_off;    // dense G [n][n] (kept for the gradient)
   uint64_t gphi_off;     // G Phi of both leads [n][2W] (kept for the gradient)
   int32_t layout;        // NEGF_LAYOUT_ONE_LEVEL or NEGF_LAYOUT_TWO_LEVEL
-  int32_t pad_;
+  int32_t fused;         // two-level tables emitted by the tensor-core chain (W = 64)
   uint64_t l1_off;       // two-level: level-1 entries [rows][L + 2] (level 2 is at tab_off)
   uint64_t l1w_off;      // two-level: level-1 weights [rows][L + 2] in the weights array
+  uint64_t edge_off;     // fused: slice-0 and slice-(L-1) blocks [L + 2][2][W][W] complex64
+};
+
+// One job of the tensor-core chain: block columns y0 and y1 (y1 = -1: none) of task `task`
+// (index into the descriptor array of the launch) propagated in direction dir (0: towards
+// slice 0 with g^L, which also emits the start slices; 1: towards slice L - 1 with g^R).
+struct TcJob {
+  int32_t task, dir, y0, y1;
 };
 
 struct cd { double x, y; };
@@ -100,6 +109,14 @@ cudaError_t launch_alias_build(const TaskDesc* d_tasks, int n_tasks, uint32_t to
                                double* d_rowsum, const double* d_mode_w, uint64_t* d_tab,
                                uint64_t* d_mode_tab, int32_t* d_err, cudaStream_t s,
                                int warps = 0);
+// Tensor-core block columns of fused tasks (W = 64, FP32 blocks as 3xTF32): level-2 alias
+// rows and level-1 site weights of every slice, then the level-1 lead weights from the edge
+// blocks (scratch [L + 2][2][W][W] complex64 at edge_off).  n_cols = sum over tasks of L + 2.
+cudaError_t launch_chain_tc(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols,
+                            const TcJob* d_jobs, uint32_t n_jobs, const float* d_eta32,
+                            const float* d_phi32, const double* d_gam, const void* d_gL,
+                            const void* d_gR, const void* d_start, void* d_weights,
+                            uint64_t* d_tab, void* d_edge, int32_t* d_err, cudaStream_t s);
 // Warps per CTA the alias kernel can use for rows of max_K slots (shared memory bound).
 int alias_warps_max(int max_K);
 // Two-level tasks: from the weights [rows][K] of every table row, the level-1 weights (slice

@@ -167,6 +167,7 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return NEGF_E_CUDA;
   if (h_err & negf::ERR_INPUT) return NEGF_E_INVALID;
+  if (h_err & negf::ERR_TIMEOUT) return NEGF_E_TIMEOUT;
   if (h_err) return NEGF_E_NUMERIC;
   return NEGF_OK;
 }
