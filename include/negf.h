@@ -175,6 +175,12 @@ enum { NEGF_EXPORT_ALIAS = 0, NEGF_EXPORT_MODE_ALIAS = 1, NEGF_EXPORT_WEIGHTS = 
        NEGF_EXPORT_MODE_WEIGHTS = 3, NEGF_EXPORT_ROWSUM = 4, NEGF_EXPORT_ALIAS_LEVEL1 = 5 };
 negf_status negf_export_tables(negf_ctx ctx, negf_tables tables, int32_t task, int32_t what,
                                void* host_buf, size_t* bytes);
+/* Rows [row0, row0 + n_rows) of one task's NEGF_EXPORT_ALIAS, NEGF_EXPORT_ALIAS_LEVEL1 or
+ * NEGF_EXPORT_ROWSUM data (same per-row layout as negf_export_tables), for tables too large
+ * to copy whole.  Buffer sizing and errors as negf_export_tables; rows outside [0, rows) or
+ * another kind give NEGF_E_INVALID.  Synchronises. */
+negf_status negf_export_table_rows(negf_ctx ctx, negf_tables tables, int32_t task, int32_t what,
+                                   int64_t row0, int64_t n_rows, void* host_buf, size_t* bytes);
 
 /* --- walks (Sec. II.D Steps 1-4, Sec. II.F Step 6') ------------------------------------ */
 

@@ -1208,6 +1208,51 @@ negf_status negf_export_tables(negf_ctx ctx, negf_tables t, int32_t task, int32_
   return NEGF_OK;
 }
 
+negf_status negf_export_table_rows(negf_ctx ctx, negf_tables t, int32_t task, int32_t what,
+                                  int64_t row0, int64_t n_rows, void* host_buf, size_t* bytes) {
+  if (!ctx || !t || !bytes || t->ctx != ctx)
+    return fail(ctx, NEGF_E_INVALID, "negf_export_table_rows: bad argument");
+  if (task < 0 || task >= t->n_tasks) return fail(ctx, NEGF_E_INVALID, "task %d out of range", task);
+  const TaskDesc& d = t->h_tasks[task];
+  if (row0 < 0 || n_rows < 0 || row0 + n_rows > d.rows)
+    return fail(ctx, NEGF_E_INVALID, "rows [%lld, %lld) outside [0, %d)", (long long)row0,
+                (long long)(row0 + n_rows), d.rows);
+  if (t->tables_released)
+    return fail(ctx, NEGF_E_INVALID, "the alias tables of this handle were released (negf_run)");
+  const bool two = d.layout == NEGF_LAYOUT_TWO_LEVEL;
+  size_t per_row = 0;       // entries per row
+  uint64_t first = 0;       // first element of row0
+  switch (what) {
+    case NEGF_EXPORT_ALIAS:
+      per_row = two ? (size_t)d.n : (size_t)d.K;
+      first = d.tab_off + (uint64_t)row0 * per_row;
+      break;
+    case NEGF_EXPORT_ALIAS_LEVEL1:
+      if (!two) return fail(ctx, NEGF_E_INVALID, "task %d has one-level tables", task);
+      per_row = (size_t)d.L + 2;
+      first = d.l1_off + (uint64_t)row0 * per_row;
+      break;
+    case NEGF_EXPORT_ROWSUM:
+      per_row = 1;
+      first = d.row_base + (uint64_t)row0;
+      break;
+    default:
+      return fail(ctx, NEGF_E_INVALID, "negf_export_table_rows: kind %d not supported", what);
+  }
+  const size_t need = sizeof(uint64_t) * per_row * (size_t)n_rows;
+  if (!host_buf) { *bytes = need; return NEGF_OK; }
+  if (*bytes < need) return fail(ctx, NEGF_E_INVALID, "export buffer too small (%zu < %zu)", *bytes, need);
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = ctx->stream;
+  const void* src = what == NEGF_EXPORT_ROWSUM ? static_cast<const void*>(t->d_rowsum + first)
+                                               : static_cast<const void*>(t->d_tab + first);
+  if (need) CUDA_TRY(ctx, cudaMemcpyAsync(host_buf, src, need, cudaMemcpyDeviceToHost, s));
+  negf_status st = check_device(ctx, t);
+  if (st != NEGF_OK) return st;
+  *bytes = need;
+  return NEGF_OK;
+}
+
 static negf_status walk_common(negf_ctx ctx, negf_tables t, int32_t start_lead, uint32_t max_steps,
                                const char* who) {
   if (!ctx || !t || t->ctx != ctx) return fail(ctx, NEGF_E_INVALID, "%s: bad handle", who);

@@ -94,6 +94,8 @@ def load():
         "negf_get_task_info": (I32, [P, P, I32, C.POINTER(negf_task_info)]),
         "negf_tables_free": (None, [P]),
         "negf_export_tables": (I32, [P, P, I32, I32, P, C.POINTER(C.c_size_t)]),
+        "negf_export_table_rows": (I32, [P, P, I32, I32, C.c_int64, C.c_int64, P,
+                                         C.POINTER(C.c_size_t)]),
         "negf_walk": (I32, [P, P, I32, U64, U64, U64, U32, C.POINTER(P)]),
         "negf_walk_trace": (I32, [P, P, I32, I32, U64, U64, U64, U32, P, P]),
         "negf_tally_counts": (I32, [P, P, P]),
@@ -253,6 +255,20 @@ def negf_export_tables(ctx, tables, task, what):
     buf = np.empty(nbytes.value // 8, dtype=dtype)
     _check(ctx, lib.negf_export_tables(ctx, tables, int(task), kind, buf.ctypes.data,
                                        C.byref(nbytes)))
+    return buf
+
+
+def negf_export_table_rows(ctx, tables, task, what, row0, n_rows):
+    """Rows [row0, row0 + n_rows) of one task's alias / alias_level1 (uint64) or rowsum
+    (float64) data."""
+    lib = load()
+    kind = EXPORT[what]
+    nbytes = C.c_size_t(0)
+    _check(ctx, lib.negf_export_table_rows(ctx, tables, int(task), kind, int(row0), int(n_rows),
+                                           None, C.byref(nbytes)))
+    buf = np.empty(nbytes.value // 8, dtype=np.float64 if what == "rowsum" else np.uint64)
+    _check(ctx, lib.negf_export_table_rows(ctx, tables, int(task), kind, int(row0), int(n_rows),
+                                           buf.ctypes.data, C.byref(nbytes)))
     return buf
 
 

@@ -6,6 +6,11 @@
   small tasks against the direct probe solve (within 4.5 standard errors).
 * Differentiation case (W = 16, L = 100, 16 energies): the score-function gradient of the
   current against the oracle's exact derivative on sampled sites (batch means, 4.5 SE).
+* Weak scattering (W = 64, L = 1000, eta = 0.005), two of its 256 energies at full size on the
+  tensor-core path: sampled table rows (sites and injection modes) against the oracle's sparse
+  column solves (realised two-level distribution within the quantisation bound + 1e-5 of the
+  row, row sums and c_p 1e-5), and the Monte Carlo transmission's reciprocity T_RL = T_LR
+  within 4.5 combined standard errors with every walker absorbed.
 """
 import numpy as np
 import pytest
@@ -13,7 +18,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-from oracle import adjoint, buttiker, current as ocur, wire as owire  # noqa: E402
+from oracle import adjoint, alias, buttiker, columns, current as ocur, wire as owire  # noqa: E402
 from paper_1805_10164_gb300 import inputs, negf  # noqa: E402
 
 
@@ -93,5 +98,48 @@ def test_differentiation_case_full_size(ctx):
         se = est.std(0, ddof=1) / np.sqrt(len(est))
         z = np.abs(mean - ref) / np.maximum(se, 1e-15)
         assert np.all(z <= 4.5), (mean, ref, se)
+    finally:
+        negf.negf_tables_free(tables)
+
+
+def test_weak_scattering_full_size(ctx):
+    wl = inputs.wire_64x1000()
+    w = wl.wires[0]
+    idx = [60, 131]
+    sub = inputs.Wire(W=w.W, L=w.L, t=w.t, onsite=w.onsite, eta=w.eta, energy=w.energy[idx],
+                      energy_weight=w.energy_weight[idx])
+    n, L, W = w.W * w.L, w.L, w.W
+    tables = negf.negf_build_tables(ctx, [sub], precision="split_tf32")
+    try:
+        rng = np.random.default_rng(64)
+        for task, k in enumerate(idx):
+            info = negf.negf_get_task_info(ctx, tables, task)
+            assert info["layout"] == "two_level" and info["n"] == n
+            rows = np.concatenate([rng.choice(n, size=4, replace=False),
+                                   [0, n - 1, n + 1, n + W + 7]])
+            ref = columns.sampled_rows(w.energy[k], w.onsite, w.eta, w.t, rows)
+            assert np.allclose(info["c"], ref["c"], rtol=1e-5)
+            quant = (L + W + 4) * 2.0**-32
+            for j, r in enumerate(rows):
+                l1 = negf.negf_export_table_rows(ctx, tables, task, "alias_level1", r, 1)
+                l2 = negf.negf_export_table_rows(ctx, tables, task, "alias", r, 1).reshape(L, W)
+                rs = negf.negf_export_table_rows(ctx, tables, task, "rowsum", r, 1)[0]
+                A = ref["w"][j].sum()
+                assert abs(rs - A) <= 1e-5 * A and abs(ref["A_row"][j] - A) <= 1e-9 * A
+                p = alias.implied_two_level(l1, l2)
+                err = np.max(np.abs(p - ref["w"][j] / A))
+                assert err <= quant + 1e-5, (k, r, err)
+        N = 1_000_000
+        T = {}
+        for lead0 in (0, 1):
+            tl = negf.negf_walk(ctx, tables, lead0, 1000 + lead0, N)
+            counts = negf.negf_tally_counts(ctx, tl, len(idx))
+            res = negf.negf_current(ctx, tables, tl, wl.mu_p, wl.mu_q, wl.kT)
+            negf.negf_tally_free(tl)
+            assert not res["stepcap"]
+            assert np.all(counts[:, 1] + counts[:, 2] == N) and np.all(counts[:, 3] == 0)
+            T[lead0] = (res["T"], res["T_se"])
+        se = np.hypot(T[0][1], T[1][1])
+        assert np.all(np.abs(T[0][0] - T[1][0]) <= 4.5 * se), (T, se)
     finally:
         negf.negf_tables_free(tables)

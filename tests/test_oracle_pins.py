@@ -299,6 +299,25 @@ def test_two_level_walker_statistics_match_exact_chain():
     assert np.array_equal(lead2 >= 0, steps[:2000] <= 2)
 
 
+@pytest.mark.parametrize("seed,W,L,E,lm", [(41, 3, 6, 0.3, 0), (42, 1, 9, -1.1, 0), (43, 4, 3, 0.8, 1)])
+def test_sparse_column_rows_match_dense(seed, W, L, E, lm):
+    """Sampled table rows from sparse LU column solves equal the dense transition weights."""
+    from oracle import columns
+    rng = np.random.default_rng(seed)
+    on = rng.uniform(-1, 1, (L, W))
+    et = rng.uniform(0.02, 0.3, (L, W))
+    g = wire.green_retarded(E, on, et, 1.0, lm, 0.7)
+    tab = markov.transition_weights(g, wire.lead_modes(E, W, 1.0, lm, 0.7)[0::2])
+    n = L * W
+    rows = np.array([0, n // 2, n - 1, n, n + W - 1, n + W, n + 2 * W - 1])
+    got = columns.sampled_rows(E, on, et, 1.0, rows, lm, 0.7)
+    scale = tab["w"].sum(1).max()
+    assert np.allclose(got["w"], tab["w"][rows], rtol=1e-10, atol=1e-13 * scale)
+    assert np.allclose(got["A_row"], tab["A_row"][rows], rtol=1e-10, atol=1e-13 * scale)
+    assert np.allclose(got["mode_w"], tab["mode_w"], rtol=1e-10, atol=1e-13 * scale)
+    assert np.allclose(got["c"], tab["c"], rtol=1e-10, atol=1e-13 * scale)
+
+
 def test_step_moments_brute_force():
     """Second moment of the number of steps: the fundamental-matrix identity against direct
     iteration of the chain's step distribution P(S = k) on a small wire."""
