@@ -1,0 +1,189 @@
+// Block-column propagation of the RGF for W = 64 slices in FP32 on the CUDA cores, one CTA per
+// pair of block columns (Sec. III.B): G_{k,m} = -t g^L_k G_{k+1,m} towards slice 0 and
+// G_{k,m} = -t g^R_k G_{k-1,m} towards slice L - 1, each block emitted as the Step 6' weights
+// w_{(m,b),(k,a)} = eta_{k,a} |G_{k,m}[a][b]|^2 of the column's W rows (Eq. draw_i_simult) and,
+// at the boundary slices, the lead weights <psi_b|Gamma|psi_b> = sum_nu Gamma_nu
+// |(Phi^T G_{k,m})_{nu b}|^2.  Same weights as chain_kernel (one warp per column), computed
+// by 256 threads with the two columns side by side: X_k [64][128] = (-t g_k) [64][64] X_{k+1}
+// in shared memory, FP32 fused multiply-adds, each thread a 4 x 8 block of outputs.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "negf_internal.cuh"
+
+namespace negf {
+namespace {
+
+constexpr int kW = 64;
+constexpr int kN = 2 * kW;                    // two columns side by side
+constexpr int kThreads = 256;
+constexpr int kWtPitch = kW + 1;              // padded row of the weight staging
+constexpr size_t kSmem = sizeof(cf) * (kW * kW + 2 * kW * kN) + sizeof(float) * kN * kWtPitch;
+
+__global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
+    const TaskDesc* __restrict__ tasks, const TcJob* __restrict__ jobs,
+    const float* __restrict__ eta32, const float* __restrict__ phi32,
+    const double* __restrict__ gam, const cf* __restrict__ gL, const cf* __restrict__ gR,
+    const cf* __restrict__ start, float* __restrict__ weights) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  cf* Gs = reinterpret_cast<cf*>(smem);                    // [a][c]; also Phi at the edges
+  cf* Xa = Gs + kW * kW;                                   // [c][b'] ping
+  cf* Xb = Xa + kW * kN;                                   // [c][b'] pong
+  float* Wt = reinterpret_cast<float*>(Xb + kW * kN);      // [b'][a] weights staging
+
+  const int tid = threadIdx.x;
+  const TcJob job = jobs[blockIdx.x];
+  const TaskDesc d = tasks[job.task];
+  const int L = d.L, n = d.n, K = d.K;
+  const int dir = job.dir;
+  auto m0_of = [&](int yy) { return yy < L ? yy : (yy == L ? 0 : L - 1); };
+  const int ys[2] = {job.y0, job.y1};
+  const float mt = (float)(-d.t);
+  const float* eta = eta32 + d.onsite_off / 2;
+  const cf* gsrc = (dir == 0 ? gL : gR) + d.g_off;
+  float* wt = weights + d.wt_off;
+  auto row_of = [&](int y, int b) -> uint64_t {
+    return y < L ? (uint64_t)y * kW + b : (uint64_t)n + (uint64_t)(y - L) * kW + b;
+  };
+  // start block of column slot col into X[:, col*64 .. col*64+63]
+  auto load_start = [&](cf* X, int col) {
+    const cf* st = start + d.start_off + (uint64_t)ys[col] * kW * kW;
+    for (int i = tid; i < kW * kW; i += kThreads) {
+      const int c = i / kW, b = i % kW;
+      X[c * kN + col * kW + b] = st[i];
+    }
+  };
+  // weights of slice k for the columns in `mask` from X (and lead weights at a boundary slice)
+  auto emit = [&](const cf* X, int k, unsigned mask) {
+    for (int i = tid; i < kN * kW; i += kThreads) {
+      const int r = i % kN, a = i / kN;                    // r consecutive across threads
+      const cf v = X[a * kN + r];
+      Wt[r * kWtPitch + a] = eta[k * kW + a] * (v.x * v.x + v.y * v.y);
+    }
+    __syncthreads();
+    for (int i = tid; i < kN * kW; i += kThreads) {
+      const int a = i % kW, r = i / kW;                    // a consecutive: coalesced rows
+      const int col = r / kW;
+      if (mask & (1u << col))
+        wt[row_of(ys[col], r % kW) * K + (uint64_t)k * kW + a] = Wt[r * kWtPitch + a];
+    }
+    if (k == 0 || k == L - 1) {
+      // lead weights: Phi (FP32) staged in Gs (free outside the product)
+      float* phis = reinterpret_cast<float*>(Gs);
+      float* gams = phis + kW * kW;
+      __syncthreads();
+      for (int i = tid; i < kW * kW; i += kThreads) phis[i] = phi32[d.phi_off + i];
+      for (int i = tid; i < kW; i += kThreads) gams[i] = (float)gam[d.lead_off + i];
+      __syncthreads();
+      const int r = tid % kN, h = tid / kN;                // two halves of the modes
+      float part = 0.f;
+      for (int nu = h * 32; nu < h * 32 + 32; ++nu) {
+        float zr = 0.f, zi = 0.f;
+        for (int a = 0; a < kW; ++a) {
+          const float p = phis[a * kW + nu];
+          const cf v = X[a * kN + r];
+          zr += p * v.x;
+          zi += p * v.y;
+        }
+        part += gams[nu] * (zr * zr + zi * zi);
+      }
+      Wt[r * kWtPitch + h] = part;                         // staging is free again
+      __syncthreads();
+      if (h == 0) {
+        const int col = r / kW;
+        if (mask & (1u << col)) {
+          const float lw = Wt[r * kWtPitch] + Wt[r * kWtPitch + 1];
+          const uint64_t base = row_of(ys[col], r % kW) * K + n;
+          if (k == 0) wt[base] = lw;
+          if (k == L - 1) wt[base + 1] = lw;
+        }
+      }
+    }
+    __syncthreads();
+  };
+
+  unsigned have = 0;
+  for (int col = 0; col < 2; ++col)
+    if (ys[col] >= 0) have |= 1u << col;
+  // direction 0 emits every column's start slice
+  if (dir == 0) {
+    for (int col = 0; col < 2; ++col) {
+      if (!(have & (1u << col))) continue;
+      load_start(Xa, col);
+      __syncthreads();
+      emit(Xa, m0_of(ys[col]), 1u << col);
+    }
+  }
+  const int m0a = m0_of(job.y0), m0b = job.y1 >= 0 ? m0_of(job.y1) : m0a;
+  const int k_first = dir == 0 ? max(m0a, m0b) - 1 : min(m0a, m0b) + 1;
+  const int k_end = dir == 0 ? -1 : L;
+  const int kstep = dir == 0 ? -1 : 1;
+  cf* Xc = Xa;
+  cf* Xn = Xb;
+  const int ty = tid / 16, tx = tid % 16;                  // outputs a = ty + 16i, b' = tx + 16j
+  for (int k = k_first; k != k_end; k += kstep) {
+    unsigned active = 0;
+    for (int col = 0; col < 2; ++col) {
+      if (!(have & (1u << col))) continue;
+      const int m0 = m0_of(ys[col]);
+      if (dir == 0 ? k < m0 : k > m0) active |= 1u << col;
+      if (dir == 0 ? k == m0 - 1 : k == m0 + 1) load_start(Xc, col);
+    }
+    const cf* gk = gsrc + (uint64_t)k * kW * kW;
+    for (int i = tid; i < kW * kW; i += kThreads) {
+      const cf v = gk[i];
+      Gs[i] = cf{mt * v.x, mt * v.y};
+    }
+    __syncthreads();
+    float accr[4][8], acci[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) accr[i][j] = acci[i][j] = 0.f;
+#pragma unroll 2
+    for (int c = 0; c < kW; ++c) {
+      cf g[4], x[8];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) g[i] = Gs[(ty + 16 * i) * kW + c];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) x[j] = Xc[c * kN + tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          accr[i][j] = fmaf(g[i].x, x[j].x, accr[i][j]);
+          accr[i][j] = fmaf(-g[i].y, x[j].y, accr[i][j]);
+          acci[i][j] = fmaf(g[i].x, x[j].y, acci[i][j]);
+          acci[i][j] = fmaf(g[i].y, x[j].x, acci[i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 8; ++j) Xn[(ty + 16 * i) * kN + tx + 16 * j] = cf{accr[i][j], acci[i][j]};
+    __syncthreads();
+    if (active) emit(Xn, k, active);
+    cf* tmp = Xc;
+    Xc = Xn;
+    Xn = tmp;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_chain_cta(const TaskDesc* d_tasks, const TcJob* d_jobs, uint32_t n_jobs,
+                             const float* d_eta32, const float* d_phi32, const double* d_gam,
+                             const void* d_gL, const void* d_gR, const void* d_start,
+                             void* d_weights, cudaStream_t s) {
+  if (n_jobs == 0) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(chain_cta_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
+  if (e != cudaSuccess) return e;
+  chain_cta_kernel<<<n_jobs, kThreads, kSmem, s>>>(
+      d_tasks, d_jobs, d_eta32, d_phi32, d_gam, static_cast<const cf*>(d_gL),
+      static_cast<const cf*>(d_gR), static_cast<const cf*>(d_start),
+      static_cast<float*>(d_weights));
+  return cudaGetLastError();
+}
+
+}  // namespace negf

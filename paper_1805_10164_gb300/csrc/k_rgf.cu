@@ -587,7 +587,7 @@ __global__ void chain_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
   if (job >= n_jobs) return;
   const int task = find_task(n_tasks, job, [&](int t) { return 2 * tasks[t].col_base; });
   const TaskDesc d = tasks[task];
-  if (d.fused) return;                           // emitted by the tensor-core chain
+  if (d.fused || d.cta_chain) return;            // emitted by the tensor-core / CTA chains
   const int W = d.W, L = d.L, n = d.n, K = d.K;
   const uint32_t local = job - 2 * d.col_base;
   const int y = (int)(local >> 1), dir = (int)(local & 1);

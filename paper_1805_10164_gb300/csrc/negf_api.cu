@@ -349,7 +349,7 @@ std::vector<TaskDesc> alias_descs(const std::vector<TaskDesc>& desc) {
 }
 
 negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool dev_in, Plan& P,
-                      int layout_opt = NEGF_LAYOUT_AUTO, bool tc = false) {
+                      int layout_opt = NEGF_LAYOUT_AUTO, bool tc = false, bool fp32 = false) {
   if (layout_opt < NEGF_LAYOUT_AUTO || layout_opt > NEGF_LAYOUT_TWO_LEVEL)
     return fail(ctx, NEGF_E_INVALID, "unknown table layout %d", layout_opt);
   uint64_t tab_off = 0, g_off = 0, wire_off = 0, start_off = 0, green_off = 0, gphi_off = 0;
@@ -420,6 +420,7 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
       d.gamma_lead = wr.gamma_lead;
       d.layout = layout;
       d.fused = tc_wire ? 1 : 0;
+      d.cta_chain = (fp32 && wr.W == 64 && !tc_wire) ? 1 : 0;
       d.tab_off = tab_off;
       d.wt_off = wt_off;
       if (tc_wire) {
@@ -492,7 +493,8 @@ struct Wave {
   bool any_two = false;
   std::vector<TaskDesc> desc;
   std::vector<TaskDesc> adesc;       // alias_descs(desc)
-  std::vector<TcJob> tcjobs;         // tensor-core chain jobs (task = index into desc)
+  std::vector<TcJob> tcjobs;         // tensor-core chain jobs (task = index into desc), then
+  size_t n_tc = 0;                   // the CTA-chain jobs: tcjobs[n_tc ..]
 };
 
 // Jobs of the tensor-core chain for fused task `k` (index in its wave): direction 0 takes every
@@ -514,6 +516,7 @@ void add_tc_jobs(std::vector<TcJob>& jobs, int k, int L) {
 
 Wave make_wave(const Plan& P, int t0, int t1) {
   Wave w;
+  std::vector<TcJob> cta;
   w.t0 = t0;
   w.t1 = t1;
   for (int k = t0; k < t1; ++k) {
@@ -529,6 +532,7 @@ Wave make_wave(const Plan& P, int t0, int t1) {
       w.edge += (uint64_t)(d.L + 2) * 2 * d.W * d.W;
       add_tc_jobs(w.tcjobs, k - t0, d.L);
     }
+    if (d.cta_chain) add_tc_jobs(cta, k - t0, d.L);
     if (d.layout == NEGF_LAYOUT_TWO_LEVEL) {
       d.l1_off = w.tab + (uint64_t)d.rows * d.n;
       d.l1w_off = w.l1w;                 // rebased past the wave's weights below
@@ -559,8 +563,11 @@ Wave make_wave(const Plan& P, int t0, int t1) {
     const int a = m0(j.y0), b = j.y1 >= 0 ? m0(j.y1) : a;
     return j.dir == 0 ? std::max(a, b) : d.L - 1 - std::min(a, b);
   };
-  std::stable_sort(w.tcjobs.begin(), w.tcjobs.end(),
-                   [&](const TcJob& x, const TcJob& y) { return len(x) > len(y); });
+  auto by_len = [&](const TcJob& x, const TcJob& y) { return len(x) > len(y); };
+  std::stable_sort(w.tcjobs.begin(), w.tcjobs.end(), by_len);
+  std::stable_sort(cta.begin(), cta.end(), by_len);
+  w.n_tc = w.tcjobs.size();
+  w.tcjobs.insert(w.tcjobs.end(), cta.begin(), cta.end());
   return w;
 }
 
@@ -716,9 +723,15 @@ negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& 
                                    q.d_mode_w, q.d_c + 2 * (size_t)w.t0, q.d_err, d_green,
                                    d_gphi, s, chain_warps);
   }
-  if (e == cudaSuccess && !w.tcjobs.empty()) {
+  if (e == cudaSuccess && w.tcjobs.size() > w.n_tc) {
+    ProfScope ps(ctx, "chain_cta_kernel", 1, s);
+    e = negf::launch_chain_cta(d_wdesc, d_tcjobs + w.n_tc, (uint32_t)(w.tcjobs.size() - w.n_tc),
+                               q.d_eta32, reinterpret_cast<const float*>(q.d_phi + P.phi_total),
+                               q.d_gam, d_gL, d_gR, d_start, d_weights, s);
+  }
+  if (e == cudaSuccess && w.n_tc) {
     ProfScope ps(ctx, "chain_tc_kernel", 2, s);
-    e = negf::launch_chain_tc(d_wdesc, nt, w.cols, d_tcjobs, (uint32_t)w.tcjobs.size(),
+    e = negf::launch_chain_tc(d_wdesc, nt, w.cols, d_tcjobs, (uint32_t)w.n_tc,
                               q.d_eta32, reinterpret_cast<const float*>(q.d_phi + P.phi_total),
                               q.d_gam, d_gL, d_gR, d_start, d_weights, d_tab, d_edge, q.d_err, s);
   }
@@ -785,7 +798,9 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   DeviceGuard guard(ctx->device);
   cudaStream_t s = ctx->stream;
   Plan P;
-  st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout, o.precision == NEGF_SPLIT_TF32);
+  // the gradient needs G itself, which only the warp-per-column chain keeps
+  st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout, o.precision == NEGF_SPLIT_TF32,
+                 o.precision != NEGF_FP64 && !o.keep_green);
   if (st != NEGF_OK) return st;
   if (o.keep_green && P.any_two)
     return fail(ctx, NEGF_E_INVALID, "keep_green needs one-level tables (the gradient keeps dense G)");
@@ -917,7 +932,8 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
     return fail(ctx, NEGF_E_CUDA, "negf_run: stream creation failed");
   cudaStream_t sw = ctx->walk_stream;
   Plan P;
-  st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout, o.precision == NEGF_SPLIT_TF32);
+  st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout, o.precision == NEGF_SPLIT_TF32,
+                 o.precision != NEGF_FP64);
   if (st != NEGF_OK) return st;
   const int nt = (int)P.tasks.size();
   negf_tables t = new (std::nothrow) negf_tables_s;
@@ -1781,10 +1797,18 @@ negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
                         q.d_mode_w, q.d_c + 2 * (size_t)wv.t0, q.d_err, nullptr, nullptr, s,
                         p->tune.chain_warps));
     }
-    if (!wv.tcjobs.empty()) {
+    if (wv.tcjobs.size() > wv.n_tc) {
+      SegScope sg(p, "chain_cta_kernel", 1, s, timed);
+      CUDA_TRY(ctx, negf::launch_chain_cta(
+                        dd, p->d_tcjobs + p->job_off[w] + wv.n_tc,
+                        (uint32_t)(wv.tcjobs.size() - wv.n_tc), q.d_eta32,
+                        reinterpret_cast<const float*>(q.d_phi + P.phi_total), q.d_gam, p->d_gL,
+                        p->d_gR, p->d_start[slot], p->d_weights[slot], s));
+    }
+    if (wv.n_tc) {
       SegScope sg(p, "chain_tc_kernel", 2, s, timed);
       CUDA_TRY(ctx, negf::launch_chain_tc(
-                        dd, ntw, wv.cols, p->d_tcjobs + p->job_off[w], (uint32_t)wv.tcjobs.size(),
+                        dd, ntw, wv.cols, p->d_tcjobs + p->job_off[w], (uint32_t)wv.n_tc,
                         q.d_eta32, reinterpret_cast<const float*>(q.d_phi + P.phi_total),
                         q.d_gam, p->d_gL, p->d_gR, p->d_start[slot], p->d_weights[slot],
                         p->d_tab[slot], p->d_edge[slot], q.d_err, s));
@@ -1876,8 +1900,13 @@ negf_status plan_autotune(negf_plan p) {
   };
   auto columns_split = [&](int cw) {
     cudaError_t e = columns(cw);
-    if (e == cudaSuccess && !wv.tcjobs.empty())
-      e = negf::launch_chain_tc(dd, nt0, wv.cols, p->d_tcjobs, (uint32_t)wv.tcjobs.size(),
+    if (e == cudaSuccess && wv.tcjobs.size() > wv.n_tc)
+      e = negf::launch_chain_cta(dd, p->d_tcjobs + wv.n_tc,
+                                 (uint32_t)(wv.tcjobs.size() - wv.n_tc), q.d_eta32,
+                                 reinterpret_cast<const float*>(q.d_phi + P.phi_total), q.d_gam,
+                                 p->d_gL, p->d_gR, p->d_start[0], p->d_weights[0], s);
+    if (e == cudaSuccess && wv.n_tc)
+      e = negf::launch_chain_tc(dd, nt0, wv.cols, p->d_tcjobs, (uint32_t)wv.n_tc,
                                 q.d_eta32, reinterpret_cast<const float*>(q.d_phi + P.phi_total),
                                 q.d_gam, p->d_gL, p->d_gR, p->d_start[0], p->d_weights[0],
                                 p->d_tab[0], p->d_edge[0], q.d_err, s);
@@ -1993,7 +2022,7 @@ negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wir
     return code;
   };
   st = make_plan(ctx, wires, n_wires, p->dev_in, p->P, o.table_layout,
-                 o.precision == NEGF_SPLIT_TF32);
+                 o.precision == NEGF_SPLIT_TF32, o.precision != NEGF_FP64);
   if (st != NEGF_OK) return bail(st);
   const Plan& P = p->P;
   const int nt = (int)P.tasks.size();

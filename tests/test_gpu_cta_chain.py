@@ -1,0 +1,90 @@
+"""FP32 block columns of W = 64 wires by the CTA-wide kernel (chain_cta_kernel) against the
+oracle: weights elementwise within 1e-5 of the row sum (the FP32 table bar), one-level and
+two-level tables, lead weights at both boundary slices, and bit-exact walks on the exported
+tables."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import alias, pipeline, walker  # noqa: E402
+from paper_1805_10164_gb300 import inputs, negf  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1805_10164_gb300 import build
+    build.build()
+    c = negf.negf_create(0)
+    yield c
+    negf.negf_destroy(c)
+
+
+def _wires():
+    return [inputs.small_wire(141, W=64, L=1, n_energy=1, eta=0.05, disorder=0.5),
+            inputs.small_wire(142, W=64, L=3, n_energy=2, eta=0.02, disorder=0.5, e_lo=-1.0,
+                              e_hi=1.0),
+            inputs.small_wire(143, W=64, L=40, n_energy=1, eta=0.005, disorder=0.5, e_lo=0.37,
+                              e_hi=0.37),
+            inputs.small_wire(144, W=64, L=6, n_energy=1, eta=0.1, lead_model=1, gamma_lead=0.8)]
+
+
+@pytest.fixture(scope="module")
+def batch(ctx):
+    wires = _wires()
+    refs = []
+    for w in wires:
+        for E in w.energy:
+            refs.append(pipeline.task_reference(w.onsite, w.eta, w.t, E, w.lead_model,
+                                                w.gamma_lead, with_alias=False))
+    return wires, refs
+
+
+@pytest.mark.parametrize("layout", ["one_level", "two_level"])
+def test_cta_chain_weights_match_oracle(ctx, batch, layout):
+    wires, refs = batch
+    tables = negf.negf_build_tables(ctx, wires, precision="fp32", keep_weights=True,
+                                    layout=layout)
+    try:
+        for task, ref in enumerate(refs):
+            w_ref = ref["tab"]["w"]
+            rs_ref = w_ref.sum(1)
+            w = negf.negf_export_tables(ctx, tables, task, "weights").reshape(w_ref.shape)
+            bad = np.abs(w - w_ref) > 1e-5 * rs_ref[:, None] + 1e-30
+            assert not bad.any(), (task, np.argwhere(bad)[:5])
+            rs = negf.negf_export_tables(ctx, tables, task, "rowsum")
+            assert np.allclose(rs, rs_ref, rtol=1e-5)
+            info = negf.negf_get_task_info(ctx, tables, task)
+            assert info["layout"] == layout
+            if layout == "two_level":
+                L, W = info["L"], info["W"]
+                l2 = negf.negf_export_tables(ctx, tables, task, "alias").reshape(info["rows"], L, W)
+                l1 = negf.negf_export_tables(ctx, tables, task, "alias_level1").reshape(info["rows"], L + 2)
+                for r in (0, info["n"] - 1, info["n"], info["rows"] - 1):
+                    p = alias.implied_two_level(l1[r], l2[r])
+                    assert np.max(np.abs(p - w_ref[r] / rs_ref[r])) <= (L + W + 4) * 2.0**-32 + 1e-5
+    finally:
+        negf.negf_tables_free(tables)
+
+
+def test_cta_chain_walks_bit_exact(ctx, batch):
+    wires, refs = batch
+    tables = negf.negf_build_tables(ctx, wires, precision="fp32", layout="one_level")
+    try:
+        n_w = 2000
+        for task in range(len(refs)):
+            info = negf.negf_get_task_info(ctx, tables, task)
+            ent = negf.negf_export_tables(ctx, tables, task, "alias").reshape(info["rows"], info["K"])
+            ment = negf.negf_export_tables(ctx, tables, task, "mode_alias").reshape(2, info["W"])
+            d_lead = torch.empty(n_w, dtype=torch.int32, device="cuda")
+            d_steps = torch.empty(n_w, dtype=torch.int32, device="cuda")
+            negf.negf_walk_trace(ctx, tables, task, 1, 0xF00D + task, 5, d_lead, d_steps)
+            lead, steps = walker.walk(ent, ment, info["n"], info["W"], info["c"] > 0, task, 1,
+                                      0xF00D + task, 5 + np.arange(n_w), 1 << 20)
+            assert np.array_equal(d_lead.cpu().numpy(), lead), task
+            assert np.array_equal(d_steps.cpu().numpy().astype(np.uint32), steps)
+    finally:
+        negf.negf_tables_free(tables)
