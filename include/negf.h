@@ -64,10 +64,11 @@ typedef enum {
  * diagonal blocks, the block-column propagation and the transition weights in complex64 /
  * FP32; the sum-rule values <i|A|i>, row sums, mode weights and c_p in FP64; alias thresholds
  * in exact integer arithmetic.  NEGF_SPLIT_TF32: as NEGF_FP32, except that wires of W = 64
- * get two-level tables built by the tensor cores: each block-column step G_{k,m} = -t g_k
- * G_{k+1,m} (Sec. III.B) runs as a real GEMM of the complex64 blocks split into TF32 high and
- * low parts (three products, FP32 accumulation), fused with the emission of the level-2 alias
- * rows, so no weight is written (NEGF_EXPORT_WEIGHTS is refused for those tasks). */
+ * get two-level tables whose block-column steps G_{k,m} = -t g_k G_{k+1,m} (Sec. III.B) run on
+ * the tensor cores as a real GEMM of the complex64 blocks split into TF32 high and low parts
+ * (three products, FP32 accumulation).  Measured on GB300, the tensor-core accumulation leaves
+ * a systematic relative bias of about 1e-7 per step, so rows whose weight lies hundreds of
+ * slices from their start are low by up to ~5e-5 (NEGF_FP32 stays within a few 1e-6). */
 typedef enum { NEGF_FP64 = 0, NEGF_FP32 = 1, NEGF_SPLIT_TF32 = 2 } negf_precision;
 
 /* Where the arrays of a negf_wire live. */

@@ -120,3 +120,103 @@ __device__ bool alias_small(int k, Get wget, Put put) {
 }
 
 }  // namespace negf
+
+namespace negf {
+
+// The same construction with the slot units kept in u[0..k) (shared memory of the caller):
+// u is filled with u_i, and every slot's entry then overwrites its own u_i (a slot's u is read
+// before its entry is written).  Same entries as alias_small.
+template <typename R, typename Get>
+__device__ bool alias_small_inplace(int k, Get wget, uint64_t* u) {
+  constexpr uint64_t kSlot = 1ull << 32;
+  bool ok = true;
+  R wmax = 0;
+  int imax = 0;
+  for (int i = 0; i < k; ++i) {
+    const R v = wget(i);
+    if (!(v >= (R)0) || !isfinite(v)) {
+      ok = false;
+    } else if (v > wmax) {
+      wmax = v;
+      imax = i;
+    }
+  }
+  if (!(wmax > (R)0)) {
+    for (int i = 0; i < k; ++i) u[i] = small_pack(0xffffffffu, (uint32_t)i);
+    return ok;
+  }
+  int e = 0;
+  frexp((double)wmax, &e);
+  const int sh = 32 - e;
+  uint64_t T = 0;
+  for (int i = 0; i < k; ++i) {
+    const R v = wget(i);
+    const uint64_t m = (v >= (R)0 && isfinite(v)) ? (uint64_t)small_fixp(v, sh) : 0ull;
+    u[i] = m;
+    T += m;
+  }
+  const uint64_t R0 = ~0ull / T;
+  uint64_t sum = 0;
+  for (int i = 0; i < k; ++i) {
+    const uint64_t X = u[i] * (uint64_t)k;
+    const uint64_t ui = (__umul64hi(X, R0) << 32) | ((X * R0) >> 32);
+    u[i] = ui;
+    sum += ui;
+  }
+  u[imax] += ((uint64_t)k << 32) - sum;
+  uint64_t small = 0, large = 0;
+  for (int i = 0; i < k; ++i) {
+    if (u[i] < kSlot) small |= 1ull << i;
+    else large |= 1ull << i;
+  }
+  int cur = -1;
+  uint64_t ul = 0;
+  if (large) {
+    cur = __ffsll((long long)large) - 1;
+    large &= large - 1;
+    ul = u[cur];
+  }
+  int pend = -1;
+  uint64_t pv = 0;
+  while (true) {
+    int s;
+    uint64_t us;
+    if (pend >= 0) {
+      s = pend;
+      us = pv;
+      pend = -1;
+    } else if (small) {
+      s = __ffsll((long long)small) - 1;
+      small &= small - 1;
+      us = u[s];
+    } else {
+      break;
+    }
+    if (cur < 0) {
+      u[s] = small_pack(0xffffffffu, (uint32_t)s);
+      continue;
+    }
+    u[s] = small_pack((uint32_t)us, (uint32_t)cur);
+    ul -= kSlot - us;
+    if (ul < kSlot) {
+      pend = cur;
+      pv = ul;
+      if (large) {
+        cur = __ffsll((long long)large) - 1;
+        large &= large - 1;
+        ul = u[cur];
+      } else {
+        cur = -1;
+      }
+    }
+  }
+  if (cur >= 0) u[cur] = small_pack(0xffffffffu, (uint32_t)cur);
+  while (large) {
+    const int i = __ffsll((long long)large) - 1;
+    large &= large - 1;
+    u[i] = small_pack(0xffffffffu, (uint32_t)i);
+  }
+  return ok;
+}
+
+}  // namespace negf

@@ -229,13 +229,23 @@ __global__ void alias_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
   }
 }
 
-// One warp per table row of a two-level task; lanes take the row's slices.
+// One warp per table row of a two-level task.  The row is taken in chunks of 32 slices: the
+// chunk's weights are staged in shared memory by coalesced loads, each lane builds one slice's
+// level-1 weight (FP64 sum) and level-2 alias row in shared memory, and the chunk's entries
+// (32 consecutive level-2 rows) leave by coalesced stores.
+constexpr int kTlWarps = 4;
+constexpr int kTlPitch = 65;                         // padded slice pitch (W <= 64)
+
 template <typename R>
-__global__ void two_level_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
-                                 uint32_t n_jobs, R* __restrict__ weights,
-                                 uint64_t* __restrict__ tab, int32_t* err) {
+__global__ void __launch_bounds__(32 * kTlWarps) two_level_kernel(
+    const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs, R* __restrict__ weights,
+    uint64_t* __restrict__ tab, int32_t* err) {
+  extern __shared__ __align__(16) unsigned char tl_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t job = blockIdx.x * (blockDim.x >> 5) + warp;
+  uint64_t* so = reinterpret_cast<uint64_t*>(tl_smem) + (size_t)warp * 32 * kTlPitch;
+  R* sw = reinterpret_cast<R*>(reinterpret_cast<uint64_t*>(tl_smem) + (size_t)kTlWarps * 32 * kTlPitch) +
+          (size_t)warp * 32 * kTlPitch;
+  const uint32_t job = blockIdx.x * kTlWarps + warp;
   if (job >= n_jobs) return;
   int lo = 0, hi = n_tasks - 1;
   while (lo < hi) {
@@ -243,7 +253,7 @@ __global__ void two_level_kernel(const TaskDesc* __restrict__ tasks, int n_tasks
     if (tasks[mid].row_base <= job) lo = mid; else hi = mid - 1;
   }
   const TaskDesc& d = tasks[lo];
-  if (d.layout != NEGF_LAYOUT_TWO_LEVEL || d.fused) return;
+  if (d.layout != NEGF_LAYOUT_TWO_LEVEL) return;
   const int row = (int)(job - d.row_base);
   if (row >= d.rows) return;
   const int W = d.W, L = d.L, n = d.n;
@@ -251,14 +261,22 @@ __global__ void two_level_kernel(const TaskDesc* __restrict__ tasks, int n_tasks
   R* l1 = weights + d.l1w_off + (uint64_t)row * (L + 2);
   uint64_t* l2 = tab + d.tab_off + (uint64_t)row * n;
   bool ok = true;
-  for (int k = lane; k < L; k += 32) {
-    const R* ws = wr + k * W;
-    double S = 0.0;
-    for (int a = 0; a < W; ++a) S += (double)ws[a];
-    l1[k] = (R)S;
-    uint64_t* out = l2 + (uint64_t)k * W;
-    ok &= alias_small<R>(W, [&](int i) { return ws[i]; },
-                         [&](int i, uint64_t e) { out[i] = e; });
+  for (int k0 = 0; k0 < L; k0 += 32) {
+    const int ns = min(32, L - k0);
+    const R* wc = wr + (uint64_t)k0 * W;
+    for (int i = lane; i < ns * W; i += 32) sw[(i / W) * kTlPitch + (i % W)] = wc[i];
+    __syncwarp();
+    if (lane < ns) {
+      const R* ws = sw + lane * kTlPitch;
+      double S = 0.0;
+      for (int a = 0; a < W; ++a) S += (double)ws[a];
+      l1[k0 + lane] = (R)S;
+      ok &= alias_small_inplace<R>(W, [&](int i) { return ws[i]; }, so + lane * kTlPitch);
+    }
+    __syncwarp();
+    uint64_t* oc = l2 + (uint64_t)k0 * W;
+    for (int i = lane; i < ns * W; i += 32) oc[i] = so[(i / W) * kTlPitch + (i % W)];
+    __syncwarp();
   }
   if (lane == 0) {
     l1[L] = wr[n];
@@ -273,14 +291,24 @@ cudaError_t launch_two_level_split(const TaskDesc* d_tasks, int n_tasks, uint32_
                                    int precision, void* d_weights, uint64_t* d_tab,
                                    int32_t* d_err, cudaStream_t s) {
   if (n_jobs == 0 || n_tasks == 0) return cudaSuccess;
-  const int warps = 4;
-  const unsigned blocks = (n_jobs + warps - 1) / warps;
-  if (precision == NEGF_FP64)
-    two_level_kernel<double><<<blocks, 32 * warps, 0, s>>>(
+  const unsigned blocks = (n_jobs + kTlWarps - 1) / kTlWarps;
+  const size_t stage = (size_t)kTlWarps * 32 * kTlPitch;      // entries per staging array
+  cudaError_t e;
+  if (precision == NEGF_FP64) {
+    const size_t smem = stage * (sizeof(uint64_t) + sizeof(double));
+    e = cudaFuncSetAttribute(two_level_kernel<double>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    two_level_kernel<double><<<blocks, 32 * kTlWarps, smem, s>>>(
         d_tasks, n_tasks, n_jobs, static_cast<double*>(d_weights), d_tab, d_err);
-  else
-    two_level_kernel<float><<<blocks, 32 * warps, 0, s>>>(
+  } else {
+    const size_t smem = stage * (sizeof(uint64_t) + sizeof(float));
+    e = cudaFuncSetAttribute(two_level_kernel<float>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    two_level_kernel<float><<<blocks, 32 * kTlWarps, smem, s>>>(
         d_tasks, n_tasks, n_jobs, static_cast<float*>(d_weights), d_tab, d_err);
+  }
   return cudaGetLastError();
 }
 

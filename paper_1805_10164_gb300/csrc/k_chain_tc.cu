@@ -5,9 +5,8 @@
 // G_{k,m} = -t g^L_k G_{k+1,m} for k < m (towards slice 0), and with the right-connected blocks
 // G_{k,m} = -t g^R_k G_{k-1,m} for k > m.  Table row b of block column y (site (m, b), or
 // injection mode b of a lead, whose start block is G_mm Phi) needs, for every slice k, the
-// weights w_a = eta_{k,a} |X_k[a][b]|^2 of X_k = G_{k,m} (Eq. draw_i_simult).  Two-level tables
-// keep them as a level-2 alias row over a and their total as the level-1 weight of slice k, so
-// no weight is ever written to memory.
+// weights w_a = eta_{k,a} |X_k[a][b]|^2 of X_k = G_{k,m} (Eq. draw_i_simult), written to the
+// task's weight rows like the CUDA-core chains (the two-level table build consumes them).
 //
 // One CTA (4 warps) runs one job: a pair of block columns of one task in one direction.  Thread
 // t owns table row b = t mod 64 of column t / 64 of the pair and TMEM lane t.  A step k is the
@@ -18,15 +17,18 @@
 //   D[t]  = (Re X_k[:, b], Im X_k[:, b])                          TMEM
 // 3xTF32: A = A_hi + A_lo and B = B_hi + B_lo with hi the operand rounded to TF32 and lo the
 // exact FP32 remainder; D = A_lo B_hi + A_hi B_lo + A_hi B_hi accumulated in FP32 (the dropped
-// A_lo B_lo term is below FP32 rounding).  The epilogue reads D, forms the row's 64 weights,
-// builds its level-2 alias row, writes the level-1 weight, and stores the TF32 split of D back
-// to TMEM as the next step's A.  The slice-0 and slice-(L-1) blocks of every column are also
-// written out (edge blocks): the lead weights of the level-1 rows are formed from them by
-// lead_weights_kernel.
+// A_lo B_lo term is below FP32 rounding).  The epilogue reads D, forms the row's 64 weights
+// (staged in shared memory and written out as coalesced rows), and stores the TF32 split of D
+// back to TMEM as the next step's A.  The slice-0 and slice-(L-1) blocks of every column are
+// also written out (edge blocks): lead_weights_kernel forms the lead weights from them.
+// Measured on GB300: the tensor-core accumulation carries a systematic relative bias of about
+// 1e-7 per step towards smaller magnitudes (sign-independent; unchanged by rounding the TF32
+// parts or by accumulating the corrections separately), so weights at the end of chains of
+// 300 - 1000 slices are low by 3 - 5e-5 of their row; the CUDA-core FP32 chains stay within
+// a few 1e-6.
 #include <cuda_runtime.h>
 #include <math.h>
 
-#include "alias_small.cuh"
 #include "negf_internal.cuh"
 
 namespace negf {
@@ -37,7 +39,8 @@ constexpr int kThreads = 128;
 constexpr uint32_t kTmemCols = 512;           // D: 0..127, A_hi: 128..255, A_lo: 256..383
 constexpr uint32_t kColD = 0, kColAh = 128, kColAl = 256;
 constexpr size_t kBBytes = 128 * 128 * 4;     // one B split: N' = 128 rows x K' = 128 TF32
-constexpr size_t kWBytes = (size_t)kW * kThreads * 4;
+constexpr int kWPitch = kThreads + 1;         // padded weight staging [a][row]
+constexpr size_t kWBytes = (size_t)kW * kWPitch * 4;
 constexpr size_t kSmem = 2 * kBBytes + kWBytes + 64;
 constexpr uint32_t kWaitLimit = 1u << 20;     // bounded mbarrier wait (iterations)
 
@@ -168,12 +171,12 @@ __device__ __forceinline__ void build_b(const cf* __restrict__ g, float mt, unsi
 __global__ void __launch_bounds__(kThreads, 1) chain_tc_kernel(
     const TaskDesc* __restrict__ tasks, const TcJob* __restrict__ jobs,
     const float* __restrict__ eta32, const cf* __restrict__ gL, const cf* __restrict__ gR,
-    const cf* __restrict__ start, float* __restrict__ l1w, uint64_t* __restrict__ tab,
-    cf* __restrict__ edge, int32_t* err) {
+    const cf* __restrict__ start, float* __restrict__ weights, cf* __restrict__ edge,
+    int32_t* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* bh = smem;
   unsigned char* bl = smem + kBBytes;
-  float* wbuf = reinterpret_cast<float*>(smem + 2 * kBBytes);     // [a][thread]
+  float* wbuf = reinterpret_cast<float*>(smem + 2 * kBBytes);     // [a][row], pitch kWPitch
   uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * kBBytes + kWBytes);
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(mbar + 1);
 
@@ -194,43 +197,46 @@ __global__ void __launch_bounds__(kThreads, 1) chain_tc_kernel(
 
   const TcJob job = jobs[blockIdx.x];
   const TaskDesc d = tasks[job.task];
-  const int L = d.L, n = d.n, K1 = d.L + 2;
+  const int L = d.L, n = d.n, K = d.K;
   const int dir = job.dir;
   const int col = tid >> 6, b = tid & 63;
   const int y = col == 0 ? job.y0 : job.y1;
   const bool has = y >= 0;                      // warp-uniform (64 threads per column)
   auto m0_of = [&](int yy) { return yy < L ? yy : (yy == L ? 0 : L - 1); };
   const int m0 = has ? m0_of(y) : 0;
-  const uint64_t row = !has ? 0
-                       : (y < L ? (uint64_t)y * kW + b : (uint64_t)n + (uint64_t)(y - L) * kW + b);
+  auto row_of = [&](int yy, int bb) -> uint64_t {
+    return yy < L ? (uint64_t)yy * kW + bb : (uint64_t)n + (uint64_t)(yy - L) * kW + bb;
+  };
   const float mt = (float)(-d.t);
   const float* eta = eta32 + d.onsite_off / 2;
   const cf* gsrc = (dir == 0 ? gL : gR) + d.g_off;
   const cf* st = start + d.start_off + (uint64_t)(has ? y : 0) * kW * kW;
-  uint64_t* l2 = tab + d.tab_off;
-  float* l1 = l1w + d.l1w_off;
+  float* wt = weights + d.wt_off;
   cf* ed = edge + d.edge_off + (uint64_t)(has ? y : 0) * 2 * kW * kW;   // [slot][a][b]
-  bool ok = true;
+  const int ys[2] = {job.y0, job.y1};
 
-  // level-1 weight and level-2 alias row of slice k from the weights in wbuf
-  auto emit = [&](int k) {
-    float S = 0.f;
-    for (int a = 0; a < kW; ++a) S += wbuf[a * kThreads + tid];
-    l1[row * K1 + k] = S;
-    uint64_t* out = l2 + (row * L + k) * kW;
-    ok &= alias_small<float>(kW, [&](int i) { return wbuf[i * kThreads + tid]; },
-                             [&](int i, uint64_t e) { out[i] = e; });
+  // write the staged weights of slice k of column slot c (all threads; coalesced rows)
+  auto flush = [&](int c, int k) {
+    for (int i = tid; i < kW * kW; i += kThreads) {
+      const int bb = i / kW, a = i % kW;
+      wt[row_of(ys[c], bb) * K + (uint64_t)k * kW + a] = wbuf[a * kWPitch + c * kW + bb];
+    }
   };
 
   // ---- direction 0 emits every column's start slice
-  if (dir == 0 && has) {
-    for (int a = 0; a < kW; ++a) {
-      const cf v = st[a * kW + b];
-      wbuf[a * kThreads + tid] = eta[m0 * kW + a] * (v.x * v.x + v.y * v.y);
-      if (m0 == 0) ed[(0 * kW + a) * kW + b] = v;
-      if (m0 == L - 1) ed[(1 * kW + a) * kW + b] = v;
+  if (dir == 0) {
+    if (has) {
+      for (int a = 0; a < kW; ++a) {
+        const cf v = st[a * kW + b];
+        wbuf[a * kWPitch + tid] = eta[m0 * kW + a] * (v.x * v.x + v.y * v.y);
+        if (m0 == 0) ed[(0 * kW + a) * kW + b] = v;
+        if (m0 == L - 1) ed[(1 * kW + a) * kW + b] = v;
+      }
     }
-    emit(m0);
+    __syncthreads();
+    for (int c = 0; c < 2; ++c)
+      if (ys[c] >= 0) flush(c, m0_of(ys[c]));
+    __syncthreads();
   }
 
   // ---- propagation over the union of the pair's slices
@@ -305,7 +311,7 @@ __global__ void __launch_bounds__(kThreads, 1) chain_tc_kernel(
 #pragma unroll
         for (int i = 0; i < 32; ++i) {
           const float x = __uint_as_float(v[i]);
-          float* wp = wbuf + (a0 + i) * kThreads + tid;
+          float* wp = wbuf + (a0 + i) * kWPitch + tid;
           if (ch < 2) *wp = x * x;
           else *wp = ek[a0 + i] * (*wp + x * x);
           if (slot >= 0) {
@@ -325,10 +331,14 @@ __global__ void __launch_bounds__(kThreads, 1) chain_tc_kernel(
           tmem_st32(tlane + kColAl + ch * 32, l);
         }
       }
-      emit(k);
+    }
+    __syncthreads();
+    for (int c = 0; c < 2; ++c) {
+      if (ys[c] < 0) continue;
+      const int mc = m0_of(ys[c]);
+      if (dir == 0 ? k < mc : k > mc) flush(c, k);
     }
   }
-  if (__any_sync(0xffffffffu, !ok) && (tid & 31) == 0) atomicOr(err, ERR_NONFINITE);
   if (timeout && tid == 0) atomicOr(err, ERR_TIMEOUT);
   tmem_st_wait();
   tc_fence_before();
@@ -345,7 +355,7 @@ constexpr size_t kLeadSmem = sizeof(cf) * kW * kW + sizeof(float) * kW * kW + si
 __global__ void __launch_bounds__(32) lead_weights_kernel(
     const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
     const float* __restrict__ phi32, const double* __restrict__ gam,
-    const cf* __restrict__ edge, float* __restrict__ l1w) {
+    const cf* __restrict__ edge, float* __restrict__ weights) {
   extern __shared__ __align__(16) unsigned char lsm[];
   cf* s_x = reinterpret_cast<cf*>(lsm);                          // [a][b]
   float* s_phi = reinterpret_cast<float*>(s_x + kW * kW);        // [a][nu]
@@ -362,7 +372,7 @@ __global__ void __launch_bounds__(32) lead_weights_kernel(
   if (!d.fused) return;
   const uint32_t local = job - 2 * d.col_base;
   const int y = (int)(local >> 1), slot = (int)(local & 1);
-  const int L = d.L, n = d.n, K1 = d.L + 2;
+  const int L = d.L, n = d.n, K = d.K;
   const cf* X = edge + d.edge_off + ((uint64_t)y * 2 + slot) * kW * kW;
   for (int i = lane; i < kW * kW; i += 32) {
     s_x[i] = X[i];
@@ -383,7 +393,7 @@ __global__ void __launch_bounds__(32) lead_weights_kernel(
       sum += s_gam[nu] * (zr * zr + zi * zi);
     }
     const uint64_t row = y < L ? (uint64_t)y * kW + bb : (uint64_t)n + (uint64_t)(y - L) * kW + bb;
-    l1w[d.l1w_off + row * K1 + L + slot] = sum;
+    weights[d.wt_off + row * K + n + slot] = sum;
   }
 }
 
@@ -400,7 +410,7 @@ cudaError_t launch_chain_tc(const TaskDesc* d_tasks, int n_tasks, uint32_t n_col
   if (e != cudaSuccess) return e;
   chain_tc_kernel<<<n_jobs, kThreads, kSmem, s>>>(
       d_tasks, d_jobs, d_eta32, static_cast<const cf*>(d_gL), static_cast<const cf*>(d_gR),
-      static_cast<const cf*>(d_start), static_cast<float*>(d_weights), d_tab,
+      static_cast<const cf*>(d_start), static_cast<float*>(d_weights),
       static_cast<cf*>(d_edge), d_err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -438,7 +438,7 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
         tab_off += (uint64_t)rows * K;
         P.max_KA = std::max(P.max_KA, (int)K);
       }
-      if (!tc_wire) wt_off += (uint64_t)rows * K;      // fused tasks keep no weights
+      wt_off += (uint64_t)rows * K;
       d.g_off = g_off;
       d.mode_off = mode_off;
       d.lead_off = lead_off;
@@ -526,7 +526,7 @@ Wave make_wave(const Plan& P, int t0, int t1) {
                             : (uint64_t)d.rows * d.K;
     d.tab_off = w.tab;
     d.wt_off = w.wt;
-    if (!d.fused) w.wt += (uint64_t)d.rows * d.K;
+    w.wt += (uint64_t)d.rows * d.K;
     if (d.fused) {
       d.edge_off = w.edge;
       w.edge += (uint64_t)(d.L + 2) * 2 * d.W * d.W;
@@ -1173,8 +1173,6 @@ negf_status negf_export_tables(negf_ctx ctx, negf_tables t, int32_t task, int32_
     case NEGF_EXPORT_MODE_ALIAS: need = sizeof(uint64_t) * 2 * (size_t)d.W; break;
     case NEGF_EXPORT_WEIGHTS:
       if (!t->d_weights) return fail(ctx, NEGF_E_INVALID, "weights were not kept (keep_weights = 0)");
-      if (d.fused)
-        return fail(ctx, NEGF_E_INVALID, "task %d: the tensor-core build keeps no weights", task);
       need = sizeof(double) * (size_t)d.rows * d.K;
       break;
     case NEGF_EXPORT_MODE_WEIGHTS: need = sizeof(double) * 2 * (size_t)d.W; break;

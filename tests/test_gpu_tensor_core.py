@@ -1,8 +1,10 @@
 """Tensor-core block columns (precision "split_tf32": W = 64 slices as 3xTF32 GEMMs on tcgen05,
-fused with the two-level table emission) against the oracle.
+two-level tables) against the oracle.
 
-Bars: realised two-level distributions within the quantisation bound (L + W + 4) 2^-32 plus
-1e-5 of the row (the FP32 table bar) of the oracle's FP64 weights; row sums (the sum rule,
+Bars: weights elementwise within 1e-5 of the row sum (the FP32 table bar; chains here are at
+most 40 slices, where the tensor-core accumulation bias stays below it); realised two-level
+distributions within the quantisation bound (L + W + 4) 2^-32 plus 1e-5 of the row of the
+oracle's FP64 weights; row sums (the sum rule,
 checked again by the alias build) 1e-5; walks bit-exact against the oracle's two-level walker on
 the exported tables; Monte Carlo T within 4 SE of the direct probe solve; negf_run and plans
 equal to build + walk for a batch mixing tensor-core and CUDA-core wires.
@@ -60,7 +62,7 @@ def _export(ctx, tables, task):
 
 def test_tensor_core_tables_realise_oracle_weights(ctx, batch):
     wires, refs = batch
-    tables = negf.negf_build_tables(ctx, wires, precision="split_tf32")
+    tables = negf.negf_build_tables(ctx, wires, precision="split_tf32", keep_weights=True)
     try:
         rng = np.random.default_rng(3)
         for task, ref in enumerate(refs):
@@ -75,12 +77,13 @@ def test_tensor_core_tables_realise_oracle_weights(ctx, batch):
             rows = np.concatenate([rng.choice(info["rows"], size=min(24, info["rows"]),
                                               replace=False),
                                    np.arange(info["n"], info["rows"], 17)])   # injection rows
+            w = negf.negf_export_tables(ctx, tables, task, "weights").reshape(w_ref.shape)
+            bad = np.abs(w - w_ref) > 1e-5 * rs_ref[:, None] + 1e-30
+            assert not bad.any(), (task, np.argwhere(bad)[:5])
             for r in rows:
                 p = alias.implied_two_level(l1[r], l2[r])
                 err = np.max(np.abs(p - w_ref[r] / rs_ref[r]))
                 assert err <= quant + 1e-5, (task, r, err)
-        with pytest.raises(negf.NegfError, match="NEGF_E_INVALID"):
-            negf.negf_export_tables(ctx, tables, 0, "weights")
     finally:
         negf.negf_tables_free(tables)
 
