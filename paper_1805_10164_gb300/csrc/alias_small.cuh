@@ -18,8 +18,13 @@ namespace negf {
 __device__ __forceinline__ uint64_t small_pack(uint32_t thr, uint32_t alias) {
   return (uint64_t)thr | ((uint64_t)alias << 32);
 }
+// 2^e as a float for e in [-126, 127]
+__device__ __forceinline__ float small_pow2f(int e) { return __int_as_float((e + 127) << 23); }
+// trunc(w 2^sh) for w 2^sh < 2^32: w scaled by two exact power-of-two factors (each within the
+// normal range for any finite float w and the sh of its row)
 __device__ __forceinline__ uint32_t small_fixp(float w, int sh) {
-  return __float2uint_rz(ldexpf(w, sh));
+  const int h = sh / 2;
+  return __float2uint_rz((w * small_pow2f(h)) * small_pow2f(sh - h));
 }
 __device__ __forceinline__ uint32_t small_fixp(double w, int sh) {
   return __double2uint_rz(ldexp(w, sh));
@@ -125,9 +130,10 @@ namespace negf {
 
 // The same construction with the slot units kept in u[0..k) (shared memory of the caller):
 // u is filled with u_i, and every slot's entry then overwrites its own u_i (a slot's u is read
-// before its entry is written).  Same entries as alias_small.
+// before its entry is written).  Same entries as alias_small.  *total receives the fixed-point
+// sum T 2^-sh of the weights (within k 2^-32 of the largest weight below the exact sum).
 template <typename R, typename Get>
-__device__ bool alias_small_inplace(int k, Get wget, uint64_t* u) {
+__device__ bool alias_small_inplace(int k, Get wget, uint64_t* u, double* total) {
   constexpr uint64_t kSlot = 1ull << 32;
   bool ok = true;
   R wmax = 0;
@@ -143,6 +149,7 @@ __device__ bool alias_small_inplace(int k, Get wget, uint64_t* u) {
   }
   if (!(wmax > (R)0)) {
     for (int i = 0; i < k; ++i) u[i] = small_pack(0xffffffffu, (uint32_t)i);
+    *total = 0.0;
     return ok;
   }
   int e = 0;
@@ -155,6 +162,7 @@ __device__ bool alias_small_inplace(int k, Get wget, uint64_t* u) {
     u[i] = m;
     T += m;
   }
+  *total = ldexp((double)T, -sh);
   const uint64_t R0 = ~0ull / T;
   uint64_t sum = 0;
   for (int i = 0; i < k; ++i) {

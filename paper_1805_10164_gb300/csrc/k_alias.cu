@@ -42,7 +42,7 @@ __host__ __device__ inline size_t alias_warp_bytes(int cap) {
   return (size_t)cap * (3 * sizeof(uint64_t) + 2 * sizeof(uint32_t));
 }
 
-__device__ __forceinline__ uint32_t fixp(float w, int sh) { return __float2uint_rz(ldexpf(w, sh)); }
+__device__ __forceinline__ uint32_t fixp(float w, int sh) { return small_fixp(w, sh); }
 __device__ __forceinline__ uint32_t fixp(double w, int sh) { return __double2uint_rz(ldexp(w, sh)); }
 
 // Build one row.  w: K weights; A: the value the row must sum to (checked when check_A);
@@ -269,9 +269,12 @@ __global__ void __launch_bounds__(32 * kTlWarps) two_level_kernel(
     if (lane < ns) {
       const R* ws = sw + lane * kTlPitch;
       double S = 0.0;
-      for (int a = 0; a < W; ++a) S += (double)ws[a];
-      l1[k0 + lane] = (R)S;
-      ok &= alias_small_inplace<R>(W, [&](int i) { return ws[i]; }, so + lane * kTlPitch);
+      ok &= alias_small_inplace<R>(W, [&](int i) { return ws[i]; }, so + lane * kTlPitch, &S);
+      if (sizeof(R) == 8) {            // FP64 tables: the FP64 sum
+        S = 0.0;
+        for (int a = 0; a < W; ++a) S += (double)ws[a];
+      }
+      l1[k0 + lane] = (R)S;            // FP32 tables: the exact fixed-point sum
     }
     __syncwarp();
     uint64_t* oc = l2 + (uint64_t)k0 * W;

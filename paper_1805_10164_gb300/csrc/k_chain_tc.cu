@@ -41,7 +41,9 @@ constexpr uint32_t kColD = 0, kColAh = 128, kColAl = 256;
 constexpr size_t kBBytes = 128 * 128 * 4;     // one B split: N' = 128 rows x K' = 128 TF32
 constexpr int kWPitch = kThreads + 1;         // padded weight staging [a][row]
 constexpr size_t kWBytes = (size_t)kW * kWPitch * 4;
-constexpr size_t kSmem = 2 * kBBytes + kWBytes + 64;
+constexpr uint32_t kStagePitch = 528;         // g_k rows staged with a padded pitch (16-B multiple)
+constexpr size_t kStageBytes = (size_t)kW * kStagePitch;
+constexpr size_t kSmem = 2 * kBBytes + kWBytes + kStageBytes + 64;
 constexpr uint32_t kWaitLimit = 1u << 20;     // bounded mbarrier wait (iterations)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -103,6 +105,17 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                :: "r"(smem_u32(bar)) : "memory");
 }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// Bulk asynchronous copy global -> shared (TMA engine), completion counted on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
@@ -135,13 +148,14 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 // 8-row group along K are contiguous (LBO = 128 B); groups are 4096 B apart (SBO).
 constexpr uint32_t kLBO = 128, kSBO = 4096;
 
-// B = split TF32 embedding of G = mt g (g: 64 x 64 complex64, row-major [a][c]).  Thread t
-// writes row n' = t of B^T: t < 64 (real output a = t): (Re G[a][c])_c, (-Im G[a][c])_c;
-// t >= 64 (imaginary output a = t - 64): (Im G[a][c])_c, (Re G[a][c])_c.
-__device__ __forceinline__ void build_b(const cf* __restrict__ g, float mt, unsigned char* bh,
+// B = split TF32 embedding of G = mt g (g: 64 x 64 complex64 staged in shared memory, row a
+// at stage + a * kStagePitch).  Thread t writes row n' = t of B^T: t < 64 (real output a = t):
+// (Re G[a][c])_c, (-Im G[a][c])_c; t >= 64 (imaginary output a = t - 64): (Im G[a][c])_c,
+// (Re G[a][c])_c.
+__device__ __forceinline__ void build_b(const unsigned char* stage, float mt, unsigned char* bh,
                                         unsigned char* bl, int t) {
   const int a = t & 63, part = t >> 6;
-  const float4* grow = reinterpret_cast<const float4*>(g + (size_t)a * kW);
+  const float4* grow = reinterpret_cast<const float4*>(stage + (size_t)a * kStagePitch);
   const uint32_t rowb = (uint32_t)(t >> 3) * 32u * 128u + (uint32_t)(t & 7) * 16u;
   auto put = [&](int q, float v0, float v1, float v2, float v3) {
     const uint32_t h0 = to_tf32(v0), h1 = to_tf32(v1), h2 = to_tf32(v2), h3 = to_tf32(v3);
@@ -155,7 +169,7 @@ __device__ __forceinline__ void build_b(const cf* __restrict__ g, float mt, unsi
   };
 #pragma unroll 4
   for (int c4 = 0; c4 < 16; ++c4) {
-    const float4 p = __ldg(grow + 2 * c4), r = __ldg(grow + 2 * c4 + 1);
+    const float4 p = grow[2 * c4], r = grow[2 * c4 + 1];
     const float re0 = mt * p.x, im0 = mt * p.y, re1 = mt * p.z, im1 = mt * p.w;
     const float re2 = mt * r.x, im2 = mt * r.y, re3 = mt * r.z, im3 = mt * r.w;
     if (part == 0) {
@@ -177,8 +191,10 @@ __global__ void __launch_bounds__(kThreads, 1) chain_tc_kernel(
   unsigned char* bh = smem;
   unsigned char* bl = smem + kBBytes;
   float* wbuf = reinterpret_cast<float*>(smem + 2 * kBBytes);     // [a][row], pitch kWPitch
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + 2 * kBBytes + kWBytes);
-  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(mbar + 1);
+  unsigned char* stage = smem + 2 * kBBytes + kWBytes;           // g_k, padded rows
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(stage + kStageBytes);   // MMA completion
+  uint64_t* mbar_g = mbar + 1;                                     // g_k arrival
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(mbar + 2);
 
   const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
@@ -187,6 +203,7 @@ __global__ void __launch_bounds__(kThreads, 1) chain_tc_kernel(
   }
   if (tid == 0) {
     mbar_init(mbar, 1);
+    mbar_init(mbar_g, 1);
     fence_mbar_init();
   }
   tc_fence_before();
@@ -249,8 +266,19 @@ __global__ void __launch_bounds__(kThreads, 1) chain_tc_kernel(
                          ((128u >> 4) << 24);
   const uint64_t dbh = smem_desc(smem_u32(bh), kLBO, kSBO);
   const uint64_t dbl = smem_desc(smem_u32(bl), kLBO, kSBO);
-  uint32_t phase = 0;
-  bool timeout = false;
+  uint32_t phase = 0, gphase = 0;
+  bool timeout = false, g_pending = false;
+  // one thread stages g_k: 64 row copies of 512 bytes into the padded rows
+  auto issue_g = [&](int k) {
+    if (tid == 0) {
+      mbar_expect_tx(mbar_g, kW * kW * (uint32_t)sizeof(cf));
+      const cf* g = gsrc + (uint64_t)k * kW * kW;
+      for (int a = 0; a < kW; ++a)
+        bulk_g2s(stage + (size_t)a * kStagePitch, g + (size_t)a * kW, kW * sizeof(cf), mbar_g);
+    }
+    g_pending = true;
+  };
+  if (k_first != k_end) issue_g(k_first);
   for (int k = k_first; k != k_end; k += kstep) {
     const bool active = has && (dir == 0 ? k < m0 : k > m0);
     const bool joining = has && (dir == 0 ? k == m0 - 1 : k == m0 + 1);
@@ -272,12 +300,22 @@ __global__ void __launch_bounds__(kThreads, 1) chain_tc_kernel(
         tmem_st32(tlane + kColAl + 64 + half * 32, il);
       }
     }
-    build_b(gsrc + (uint64_t)k * kW * kW, mt, bh, bl, tid);
+    bool got = false;
+    for (uint32_t it = 0; it < kWaitLimit && !got; ++it) got = mbar_try_wait(mbar_g, gphase);
+    gphase ^= 1u;
+    g_pending = !got;
+    if (__syncthreads_or(!got)) {
+      timeout = true;
+      break;
+    }
+    build_b(stage, mt, bh, bl, tid);
     tmem_st_wait();
     fence_proxy_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    // the stage is free: fetch the next step's block while this step computes
+    if (k + kstep != k_end) issue_g(k + kstep);
     if (tid == 0) {
       uint32_t acc = 0;
       for (int pass = 0; pass < 3; ++pass) {
@@ -340,6 +378,11 @@ __global__ void __launch_bounds__(kThreads, 1) chain_tc_kernel(
     }
   }
   if (timeout && tid == 0) atomicOr(err, ERR_TIMEOUT);
+  if (g_pending) {
+    // a staged copy may still be in flight after a timeout: wait for it (bounded)
+    bool got = false;
+    for (uint32_t it = 0; it < kWaitLimit && !got; ++it) got = mbar_try_wait(mbar_g, gphase);
+  }
   tmem_st_wait();
   tc_fence_before();
   __syncthreads();
