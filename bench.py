@@ -34,14 +34,37 @@ UNIT = "walker steps/s"
 L2_BYTES = 129 * 1024 * 1024
 
 
-def workload(name):
+def workload(name, energies=0):
     if name == "wire_10x50":
-        return inputs.wire_10x50()
-    if name == "chain_l20":
-        return inputs.chain_l20()
-    if name == "wire_16x100":
-        return inputs.wire_16x100(precision="fp32")
-    raise SystemExit(f"unknown workload {name}")
+        wl = inputs.wire_10x50()
+    elif name == "chain_l20":
+        wl = inputs.chain_l20()
+    elif name == "wire_16x100":
+        wl = inputs.wire_16x100(precision="fp32")
+    elif name == "wire_64x100":
+        wl = inputs.wire_64x100()
+    elif name == "wire_64x1000":
+        wl = inputs.wire_64x1000()
+    else:
+        raise SystemExit(f"unknown workload {name}")
+    if energies:
+        # an evenly spread subset of each wire's energy grid (same weights)
+        for w in wl.wires:
+            idx = np.unique(np.linspace(0, len(w.energy) - 1, energies).round().astype(int))
+            w.energy, w.energy_weight = w.energy[idx], w.energy_weight[idx]
+        wl.name += f"_sub{energies}E"
+    return wl
+
+
+def tensor_peak(kind):
+    """Dense tensor peak for TF32 from the measured BF16 burst peak and the nominal ratio
+    (1.1 / 2.25 PFLOP/s)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        return bf16 * 1.1 / 2.25, "measured BF16 burst x nominal TF32/BF16 ratio (1.1/2.25)"
+    except Exception:
+        return 1900.0 * 1.1 / 2.25, "fallback BF16 1.9 PFLOP/s x nominal TF32/BF16 ratio"
 
 
 def peaks():
@@ -141,19 +164,35 @@ def barrier(world):
 
 # ------------------------------------------------------------------ algorithmic bytes per kernel
 
+def two_level(W, L, precision):
+    """Layout the library picks by default (NEGF_LAYOUT_AUTO)."""
+    return (precision == "split_tf32" and W == 64) or W * L > 6400
+
+
 def algorithmic_bytes(kernel, wl, precision, counts):
     """Bytes a kernel must move per launch by its definition (tables in, tables out)."""
     tasks = [(w.W, w.L) for w in wl.wires for _ in w.energy]
-    entries = sum((W * L + 2 * W) * (W * L + 2) for W, L in tasks)
+    rows = [W * L + 2 * W for W, L in tasks]
+    one = [(r, W * L + 2) for r, (W, L) in zip(rows, tasks) if not two_level(W, L, precision)]
+    two = [(r, W, L) for r, (W, L) in zip(rows, tasks) if two_level(W, L, precision)]
     wsz = 8 if precision == "fp64" else 4
     if kernel == "walk_kernel":
         walkers = int(counts[:, 0].sum())
         steps = int(counts[:, 4].sum())
-        return 8 * (steps + walkers)            # one 8-byte alias entry per draw
-    if kernel == "alias_kernel":
-        return entries * (wsz + 8)              # read a weight, write an entry
-    if kernel == "diag_chain_kernels":
-        return entries * wsz                    # write every weight once
+        absorbed = int(counts[:, 1].sum() + counts[:, 2].sum())
+        # one 8-byte entry per draw; two-level tables: a level-1 entry per transition and a
+        # level-2 entry per transition that stays in the wire
+        if two and not one:
+            return 8 * (walkers + steps + (steps - absorbed))
+        if two:
+            return None
+        return 8 * (steps + walkers)
+    if kernel == "alias_kernel":           # one-level rows, or the level-1 rows
+        return sum(r * K for r, K in one) * (wsz + 8) + sum(r * (L + 2) for r, W, L in two) * (wsz + 8)
+    if kernel == "two_level_kernel":       # read the weights, write level-2 entries and level-1 weights
+        return sum(r * (W * L) * (wsz + 8) + r * L * wsz for r, W, L in two)
+    if kernel in ("diag_chain_kernels", "chain_cta_kernel", "chain_tc_kernel"):
+        return sum(r * K for r, K in one) * wsz + sum(r * (W * L + 2) for r, W, L in two) * wsz
     return None
 
 
@@ -166,7 +205,7 @@ def run_gpu(args):
     rank, world, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     build.build()
-    wl = workload(args.workload)
+    wl = workload(args.workload, args.energies)
     prec = args.precision or wl.precision
     N = args.walkers or wl.walkers_per_task
     dev_wires = [inputs.Wire(W=w.W, L=w.L, t=w.t, onsite=torch.from_numpy(w.onsite).cuda(),
@@ -195,12 +234,15 @@ def run_gpu(args):
             negf.negf_plan_launch(ctx, plan, args.seed, wid0)
             r = negf.negf_plan_result(ctx, plan)
             return r, r["counts"]
-        if args.mode == "pipeline":
+        if args.mode in ("pipeline", "graph"):
             # build wave w+1 while wave w walks; tables are freed wave by wave
             tables, tally = negf.negf_run(ctx, wires, 0, args.seed, N, precision=prec,
                                           memspace=memspace, walker_id_offset=wid0,
                                           max_steps=args.max_steps,
-                                          tasks_per_wave=args.tasks_per_wave,
+                                          # graph mode's host-buffer leg: waves only as
+                                          # the memory budget requires
+                                          tasks_per_wave=(args.tasks_per_wave
+                                                          if args.mode == "pipeline" else 1 << 30),
                                           walk_blocks_per_sm=args.walk_blocks_per_sm)
         else:
             tables = negf.negf_build_tables(ctx, wires, precision=prec, memspace=memspace)
@@ -270,12 +312,12 @@ def run_gpu(args):
     e2e_steps = sum_over_ranks(float(e2e_steps), world)
     # ceiling for the walk's 8-byte alias-entry gathers (measured, this GPU, this run)
     per_task_bytes = 8 * max((w.W * w.L + 2 * w.W) * (w.W * w.L + 2) for w in wl.wires)
-    probe_tab = 2 * per_task_bytes
+    probe_tab = min(2 * per_task_bytes, 16 << 30)
     probe_gps = negf.negf_probe_gather(ctx, probe_tab, ilp=8, chain=64)
     probe_gps1 = negf.negf_probe_gather(ctx, probe_tab, ilp=1, chain=64)
     probe_gbs = 8 * probe_gps / 1e9
     probe_src = (f"measured: negf_probe_gather, random 8-byte gathers over {probe_tab >> 20} MiB "
-                 f"(two tasks' alias tables), 8 independent chains per thread "
+                 f"(two tasks' alias tables, at most 16 GiB), 8 independent chains per thread "
                  f"({probe_gps:.3g}/s; 1 chain: {probe_gps1:.3g}/s)")
     # seconds per current at 1 % SE with FP64 tables (the plain FP64 form), for comparison
     fp64_cmp = None
@@ -305,11 +347,30 @@ def run_gpu(args):
                     "traffic": None, "algorithmic_bytes_per_launch": int(per_launch_bytes),
                     "avg_launch_ms": round(kms / klaunch, 5)}
         roof = dict(roof_hbm)
-        if kname == "walk_kernel" and probe_gbs:
+        if kname == "walk_kernel" and probe_gbs and (probe_tab < 2 * per_task_bytes):
+            # the probe could not cover two tasks' tables: HBM-resident gathers, keep the HBM
+            # copy peak
+            pass
+        elif kname == "walk_kernel" and probe_gbs:
             # the alias tables of the tasks in flight sit in L2: the ceiling is the measured
             # random 8-byte gather rate over a table of that size
             roof.update(bound="l2", peak=round(probe_gbs, 1), frac=round(ach / probe_gbs, 4),
                         peak_source=probe_src)
+    if kname == "chain_tc_kernel" and klaunch > 0:
+        # tensor-core roofline: TF32 operations of the 3xTF32 products (3 GEMMs of 128 x 128 x
+        # 128 real per CTA step, a pair of block columns advanced by one slice)
+        steps_ct = 0
+        for w in wl.wires:
+            if w.W == 64:
+                steps_ct += len(w.energy) * ((w.L + 2) * (w.L - 1) + 1) // 2
+        flops = 3 * 2 * 128 ** 3 * steps_ct / max(1, klaunch / args.steps / 2)
+        tflops = flops / (kms / 1e3 / (klaunch / 2)) / 1e12
+        tf32_peak = tensor_peak("tf32")
+        roof = {"kernel": kname, "bound": "tensor", "achieved": round(tflops, 1),
+                "peak": round(tf32_peak[0], 1), "unit": "TFLOP/s",
+                "frac": round(tflops / tf32_peak[0], 4), "peak_source": tf32_peak[1],
+                "traffic": None, "algorithmic_flops_per_launch": int(flops),
+                "avg_launch_ms": round(kms / klaunch * 2, 5)}
     # seconds per current at 1 % relative standard error: fixed table cost + walks scaled by
     # the binomial variance (N_needed = N (rel_se / 0.01)^2)
     walk_ms = prof.get("walk_kernel", (0, 0.0))[1] / args.steps
@@ -319,7 +380,11 @@ def run_gpu(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32 tables, u32 walks, f64 tally",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp64": "f64 tables, u32 walks, f64 tally",
+                  "fp32": "f32 tables, u32 walks, f64 tally",
+                  "split_tf32": "tf32x3 block products (f32 accumulate), f32 tables, u32 walks, "
+                                "f64 tally"}[prec],
         "data": "synthetic (seeded square-lattice wire standing in for the paper's CdTe nanowires)",
         "config": {"workload": wl.name, "wires": len(wl.wires), "tasks": n_tasks,
                    "walkers_per_task": N, "precision": prec, "start_lead": "L",
@@ -410,7 +475,7 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = workload(args.workload)
+    wl = workload(args.workload, args.energies)
     walkers = wl.walkers_per_task
     for i in range(args.warmup):
         cpu_sample(wl, 1, 1000, args.seed + i)
@@ -451,6 +516,8 @@ def main():
     ap.add_argument("--tasks-per-wave", type=int, default=8)
     ap.add_argument("--walk-blocks-per-sm", type=int, default=4)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
+    ap.add_argument("--energies", type=int, default=0,
+                    help="use an evenly spread subset of this many grid energies")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -91,13 +91,24 @@ def wire_16x100(seed=3, walkers=1_000_000, n_energy=16, precision="fp64"):
                     seed)
 
 
-def wire_64x1000(seed=4, n_energy=256, precision="split_tf32"):
-    """Weak scattering: W = 64 x L = 1000, onsite U[-0.5, 0.5], eta = 0.005, 256 energies."""
+def wire_64x1000(seed=4, n_energy=256, precision="split_tf32", walkers=32_000_000):
+    """Weak scattering: W = 64 x L = 1000, onsite U[-0.5, 0.5], eta = 0.005, 256 energies.
+    About 3.1 transitions per walk, so 3.2e7 walkers per energy give ~1e8 walker steps."""
     rng = np.random.default_rng(seed)
     E, wE = midpoint_grid(-3.5, 3.5, n_energy)
     w = random_wire(rng, 64, 1000, 1.0, 0.5, 0.005, E, wE)
-    return Workload("wire_W64_L1000_eta0.005_256E", [w], 0, 3.5, -3.5, 0.025, precision, seed,
-                    meta=dict(steps_per_task=100_000_000))
+    return Workload("wire_W64_L1000_eta0.005_256E", [w], walkers, 3.5, -3.5, 0.025, precision,
+                    seed, meta=dict(steps_per_task=100_000_000))
+
+
+def wire_64x100(seed=5, n_energy=8, precision="split_tf32", walkers=1_000_000):
+    """W = 64 x L = 100, onsite U[-0.5, 0.5], eta = 0.005, 8 energies: the wide-slice kernels
+    on a case small enough for full ncu captures (tables ~0.7 GB)."""
+    rng = np.random.default_rng(seed)
+    E, wE = midpoint_grid(-3.5, 3.5, n_energy)
+    w = random_wire(rng, 64, 100, 1.0, 0.5, 0.005, E, wE)
+    return Workload("wire_W64_L100_eta0.005_8E", [w], walkers, 3.5, -3.5, 0.025, precision,
+                    seed)
 
 
 def small_wire(seed, W, L, n_energy=3, eta=0.1, disorder=1.0, t=1.0, e_lo=-2.9, e_hi=2.9,
