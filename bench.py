@@ -166,7 +166,7 @@ def barrier(world):
 
 def two_level(W, L, precision):
     """Layout the library picks by default (NEGF_LAYOUT_AUTO)."""
-    return (precision == "split_tf32" and W == 64) or W * L > 6400
+    return (precision == "split_tf32" and W == 64) or W * L > 2048
 
 
 def algorithmic_bytes(kernel, wl, precision, counts):

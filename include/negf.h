@@ -42,6 +42,7 @@ extern "C" {
 #define NEGF_MAX_W 64            /* widest supported slice (sites across the wire) */
 #define NEGF_MAX_SITES 6400      /* largest W*L per wire with one-level tables */
 #define NEGF_MAX_SITES_TWO_LEVEL 65536 /* largest W*L per wire with two-level tables */
+#define NEGF_AUTO_TWO_LEVEL_SITES 2048 /* NEGF_LAYOUT_AUTO picks two-level tables above this */
 #define NEGF_MAX_STEPS (1u << 24) /* largest accepted per-walk step cap */
 #define NEGF_TALLY_FIELDS 5      /* u64 counters per task, see negf_tally_counts */
 
@@ -114,8 +115,10 @@ typedef struct {
  * for a slice k, a level-2 draw over the W sites of that slice (weights: the row's weights of
  * those sites).  Entries: level 2 u64 [rows][L][W], level 1 u64 [rows][L + 2].  Table memory
  * is rows * (n + L + 2) entries either way; the build needs no per-row shared-memory pass over
- * n + 2 entries, which makes it the layout of long wires.  NEGF_LAYOUT_AUTO: two-level when
- * W*L > NEGF_MAX_SITES. */
+ * n + 2 entries, which makes it the layout of long wires (a one-level row of K slots is
+ * built by one warp with 32 K bytes of shared memory, which leaves few warps per SM once K is
+ * in the thousands).  NEGF_LAYOUT_AUTO: two-level when W*L > NEGF_AUTO_TWO_LEVEL_SITES, or for
+ * W = 64 wires built with NEGF_SPLIT_TF32. */
 typedef enum { NEGF_LAYOUT_AUTO = 0, NEGF_LAYOUT_ONE_LEVEL = 1, NEGF_LAYOUT_TWO_LEVEL = 2 } negf_table_layout;
 
 /* Per-task facts, read back from the device (synchronises). */

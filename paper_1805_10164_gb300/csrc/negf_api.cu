@@ -349,7 +349,8 @@ std::vector<TaskDesc> alias_descs(const std::vector<TaskDesc>& desc) {
 }
 
 negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool dev_in, Plan& P,
-                      int layout_opt = NEGF_LAYOUT_AUTO, bool tc = false, bool fp32 = false) {
+                      int layout_opt = NEGF_LAYOUT_AUTO, bool tc = false, bool fp32 = false,
+                      bool one_level_first = false) {
   if (layout_opt < NEGF_LAYOUT_AUTO || layout_opt > NEGF_LAYOUT_TWO_LEVEL)
     return fail(ctx, NEGF_E_INVALID, "unknown table layout %d", layout_opt);
   uint64_t tab_off = 0, g_off = 0, wire_off = 0, start_off = 0, green_off = 0, gphi_off = 0;
@@ -370,7 +371,10 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
     const int64_t K = n + 2, rows = n + 2 * wr.W;
     // the tensor-core chain (split-TF32 builds of W = 64 wires) emits two-level tables
     const bool tc_wire = tc && wr.W == 64 && layout_opt != NEGF_LAYOUT_ONE_LEVEL;
-    const int layout = tc_wire || (layout_opt == NEGF_LAYOUT_AUTO && n > NEGF_MAX_SITES)
+    // automatic layout: two-level above the threshold, unless one-level tables are wanted
+    // (the gradient) and the wire still fits them
+    const int64_t auto_max = one_level_first ? NEGF_MAX_SITES : NEGF_AUTO_TWO_LEVEL_SITES;
+    const int layout = tc_wire || (layout_opt == NEGF_LAYOUT_AUTO && n > auto_max)
                            ? NEGF_LAYOUT_TWO_LEVEL
                            : (layout_opt == NEGF_LAYOUT_AUTO ? NEGF_LAYOUT_ONE_LEVEL : layout_opt);
     const int64_t max_n = layout == NEGF_LAYOUT_TWO_LEVEL ? NEGF_MAX_SITES_TWO_LEVEL : NEGF_MAX_SITES;
@@ -800,7 +804,7 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   Plan P;
   // the gradient needs G itself, which only the warp-per-column chain keeps
   st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout, o.precision == NEGF_SPLIT_TF32,
-                 o.precision != NEGF_FP64 && !o.keep_green);
+                 o.precision != NEGF_FP64 && !o.keep_green, o.keep_green != 0);
   if (st != NEGF_OK) return st;
   if (o.keep_green && P.any_two)
     return fail(ctx, NEGF_E_INVALID, "keep_green needs one-level tables (the gradient keeps dense G)");

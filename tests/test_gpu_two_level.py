@@ -159,7 +159,8 @@ def test_two_level_through_run_and_plan(ctx, batch):
 
 
 def test_auto_layout_for_long_wire(ctx):
-    """W = 64, L = 101 (6464 sites > the one-level limit) builds two-level tables by itself;
+    """W = 64, L = 101 (6464 sites, above the automatic two-level threshold and the one-level
+    limit) builds two-level tables by itself;
     sampled rows realise the oracle's weights and the transmission matches the direct solve."""
     w = inputs.small_wire(116, W=64, L=101, n_energy=1, eta=0.02, disorder=0.5, e_lo=-0.3,
                           e_hi=-0.3)
