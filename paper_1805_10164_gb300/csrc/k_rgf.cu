@@ -285,12 +285,14 @@ template <int MAXW>
 __device__ void build_col(cf (&a)[MAXW], int W, double E, double t, double onsite_j,
                           double eta_j, const cf (&x)[MAXW]) {
   const int j = threadIdx.x & 31;
+  const cf diag{(float)(E - onsite_j), (float)(0.5 * eta_j)};
+  const float tf = (float)t;
 #pragma unroll
   for (int i = 0; i < MAXW; ++i) {
     cf v{0.f, 0.f};
     if (j < W && i < W) {
-      if (i == j) v = cf{(float)(E - onsite_j), (float)(0.5 * eta_j)};
-      if (i - j == 1 || j - i == 1) v.x += (float)t;
+      if (i == j) v = diag;
+      if (i - j == 1 || j - i == 1) v.x += tf;
       v = v - x[i];
     } else if (j >= W && j < 2 * W) {
       v = cf{i == j - W ? 1.f : 0.f, 0.f};
@@ -326,14 +328,23 @@ __global__ void rgf_sweep_reg_kernel(const TaskDesc* __restrict__ tasks, int n_t
   if (L < 2) return;
   const double* onsite = wire + d.onsite_off;
   const double* eta = onsite + d.n;
-  const double tt = d.t * d.t;
+  const float ttf = (float)(d.t * d.t);     // FP32 on the serial path (FP64 is slow here)
   cf x[MAXW], a[MAXW];
   lead_col<MAXW>(phig + d.phi_off, sig + d.lead_off, W, x);
   cf* out = dir == 0 ? gL : gR;
   const int jc = lane < W ? lane : 0;
+  // the next slice's onsite energy and dephasing are fetched one step ahead
+  int k = dir == 0 ? 0 : L - 1;
+  double on_j = onsite[k * W + jc], eta_j = eta[k * W + jc];
   for (int s = 0; s < L - 1; ++s) {
-    const int k = dir == 0 ? s : L - 1 - s;
-    build_col<MAXW>(a, W, d.E, d.t, onsite[k * W + jc], eta[k * W + jc], x);
+    k = dir == 0 ? s : L - 1 - s;
+    const double on_cur = on_j, eta_cur = eta_j;
+    if (s + 1 < L - 1) {
+      const int kn = dir == 0 ? s + 1 : L - 2 - s;
+      on_j = onsite[kn * W + jc];
+      eta_j = eta[kn * W + jc];
+    }
+    build_col<MAXW>(a, W, d.E, d.t, on_cur, eta_cur, x);
     if (!gj_reg<MAXW>(a, W)) {
       if (lane == 0) atomicOr(err, ERR_SINGULAR);
       return;
@@ -350,7 +361,7 @@ __global__ void rgf_sweep_reg_kernel(const TaskDesc* __restrict__ tasks, int n_t
       }
       const float gx = __shfl_sync(0xffffffffu, a[i].x, src);
       const float gy = __shfl_sync(0xffffffffu, a[i].y, src);
-      x[i] = cf{(float)(tt * gx), (float)(tt * gy)};
+      x[i] = cf{ttf * gx, ttf * gy};
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
   }
@@ -715,6 +726,11 @@ cudaError_t sweep_impl<cf>(const TaskDesc* d_tasks, int n_tasks, int max_W,
                                                        d_gL, d_gR, d_err);
     return cudaGetLastError();
   }
+  if (max_W <= 12) {
+    rgf_sweep_reg_kernel<12><<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig,
+                                                        d_gL, d_gR, d_err);
+    return cudaGetLastError();
+  }
   if (max_W <= 16) {
     rgf_sweep_reg_kernel<16><<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig,
                                                         d_gL, d_gR, d_err);
@@ -742,6 +758,10 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
       diag_reg_kernel<8><<<blocks, 32 * warps, 0, s>>>(d_tasks, n_tasks, n_cols, d_wire, d_phi,
                                                        d_sig, d_gam, gl, gr, st, d_rowsum,
                                                        d_mode_w, d_c, d_err);
+    else if (max_W <= 12)
+      diag_reg_kernel<12><<<blocks, 32 * warps, 0, s>>>(d_tasks, n_tasks, n_cols, d_wire, d_phi,
+                                                        d_sig, d_gam, gl, gr, st, d_rowsum,
+                                                        d_mode_w, d_c, d_err);
     else
       diag_reg_kernel<16><<<blocks, 32 * warps, 0, s>>>(d_tasks, n_tasks, n_cols, d_wire, d_phi,
                                                         d_sig, d_gam, gl, gr, st, d_rowsum,
