@@ -279,80 +279,6 @@ __device__ bool gj_reg(cf (&a)[MAXW], int W) {
   return true;
 }
 
-// One pivot step of gj_reg on a register-held matrix (helper of gj_reg2).
-template <int MAXW>
-__device__ __forceinline__ void gj_reg_step(cf (&a)[MAXW], int W, int k, int p, bool failed) {
-  const unsigned FULL = 0xffffffffu;
-  if (p != k) {
-    cf vk = a[0], vp = a[0];
-#pragma unroll
-    for (int i = 0; i < MAXW; ++i) {
-      if (i == k) vk = a[i];
-      if (i == p) vp = a[i];
-    }
-#pragma unroll
-    for (int i = 0; i < MAXW; ++i) {
-      if (i == k) a[i] = vp;
-      if (i == p) a[i] = vk;
-    }
-  }
-  cf f[MAXW];
-#pragma unroll
-  for (int i = 0; i < MAXW; ++i) {
-    f[i].x = __shfl_sync(FULL, a[i].x, k);
-    f[i].y = __shfl_sync(FULL, a[i].y, k);
-  }
-  cf piv = f[0], pk = a[0];
-#pragma unroll
-  for (int i = 0; i < MAXW; ++i) {
-    if (i == k) { piv = f[i]; pk = a[i]; }
-  }
-  if (failed) piv = cf{1.f, 0.f};        // a failed chain runs on; its result is discarded
-  pk = pk * cdiv(cf{1.f, 0.f}, piv);
-#pragma unroll
-  for (int i = 0; i < MAXW; ++i) {
-    if (i == k) a[i] = pk;
-    else if (i < W) a[i] = a[i] - f[i] * pk;
-  }
-}
-
-// Pivot row of column k for gj_reg2 (lane k's argmax, broadcast).
-template <int MAXW>
-__device__ __forceinline__ int gj_reg_pivot(const cf (&a)[MAXW], int W, int k, bool& bad) {
-  float best = -1.f;
-  int p = k;
-#pragma unroll
-  for (int i = 0; i < MAXW; ++i) {
-    if (i >= k && i < W) {
-      const float v = norm2(a[i]);
-      if (v > best) { best = v; p = i; }
-    }
-  }
-  p = __shfl_sync(0xffffffffu, p, k);
-  best = __shfl_sync(0xffffffffu, best, k);
-  bad = !(best > 0.f) || !isfinite(best);
-  return p;
-}
-
-// Gauss-Jordan on two independent register-held augmented matrices at once (the left and the
-// right sweep of one task): the steps of gj_reg interleaved, so that each lane has two
-// independent dependency chains.  Bit c of the result is set when chain c met a zero or
-// non-finite pivot.
-template <int MAXW>
-__device__ unsigned gj_reg2(cf (&a0)[MAXW], cf (&a1)[MAXW], int W) {
-  unsigned failed = 0;
-  for (int k = 0; k < W; ++k) {
-    bool b0, b1;
-    const int p0 = gj_reg_pivot<MAXW>(a0, W, k, b0);
-    const int p1 = gj_reg_pivot<MAXW>(a1, W, k, b1);
-    failed |= (b0 ? 1u : 0u) | (b1 ? 2u : 0u);
-    if (failed == 3u) return failed;
-    gj_reg_step<MAXW>(a0, W, k, p0, failed & 1u);
-    gj_reg_step<MAXW>(a1, W, k, p1, failed & 2u);
-  }
-  return failed;
-}
-
 // Column j (lane j < W) of E - H_kk - Sigma_s(k) - x, where x is given as this lane's column;
 // lanes W <= j < 2W get identity columns, other lanes zeros.
 template <int MAXW>
@@ -436,62 +362,6 @@ __global__ void rgf_sweep_reg_kernel(const TaskDesc* __restrict__ tasks, int n_t
       const float gx = __shfl_sync(0xffffffffu, a[i].x, src);
       const float gy = __shfl_sync(0xffffffffu, a[i].y, src);
       x[i] = cf{ttf * gx, ttf * gy};
-    }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
-  }
-}
-
-// Both sweeps of one task in one warp (left: slices 0..L-2 with Sigma_L, right: L-1..1 with
-// Sigma_R), interleaved step by step; same arithmetic as rgf_sweep_reg_kernel.
-template <int MAXW>
-__global__ void rgf_sweep_reg2_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
-                                      const double* __restrict__ wire,
-                                      const double* __restrict__ phig, const cd* __restrict__ sig,
-                                      cf* gL, cf* gR, int32_t* err) {
-  const int task = blockIdx.x;
-  if (task >= n_tasks) return;
-  const TaskDesc d = tasks[task];
-  const int W = d.W, L = d.L;
-  const int lane = threadIdx.x & 31;
-  if (L < 2) return;
-  const double* onsite = wire + d.onsite_off;
-  const double* eta = onsite + d.n;
-  const float ttf = (float)(d.t * d.t);
-  cf x0[MAXW], x1[MAXW], a0[MAXW], a1[MAXW];
-  lead_col<MAXW>(phig + d.phi_off, sig + d.lead_off, W, x0);
-#pragma unroll
-  for (int i = 0; i < MAXW; ++i) x1[i] = x0[i];           // the two leads are alike
-  const int jc = lane < W ? lane : 0;
-  double on0 = onsite[jc], on1 = onsite[(L - 1) * W + jc];
-  double et0 = eta[jc], et1 = eta[(L - 1) * W + jc];
-  const int src = W + (lane < W ? lane : 0);
-  for (int s = 0; s < L - 1; ++s) {
-    build_col<MAXW>(a0, W, d.E, d.t, on0, et0, x0);
-    build_col<MAXW>(a1, W, d.E, d.t, on1, et1, x1);
-    if (s + 1 < L - 1) {
-      on0 = onsite[(s + 1) * W + jc];
-      et0 = eta[(s + 1) * W + jc];
-      on1 = onsite[(L - 2 - s) * W + jc];
-      et1 = eta[(L - 2 - s) * W + jc];
-    }
-    if (gj_reg2<MAXW>(a0, a1, W)) {
-      if (lane == 0) atomicOr(err, ERR_SINGULAR);
-      return;
-    }
-    bool bad = false;
-    cf* d0 = gL + d.g_off + (uint64_t)s * W * W;
-    cf* d1 = gR + d.g_off + (uint64_t)(L - 1 - s) * W * W;
-#pragma unroll
-    for (int i = 0; i < MAXW; ++i) {
-      if (lane >= W && lane < 2 * W && i < W) {
-        d0[i * W + (lane - W)] = a0[i];
-        d1[i * W + (lane - W)] = a1[i];
-        bad |= !finite_c(a0[i]) || !finite_c(a1[i]);
-      }
-      x0[i] = cf{ttf * __shfl_sync(0xffffffffu, a0[i].x, src),
-                 ttf * __shfl_sync(0xffffffffu, a0[i].y, src)};
-      x1[i] = cf{ttf * __shfl_sync(0xffffffffu, a1[i].x, src),
-                 ttf * __shfl_sync(0xffffffffu, a1[i].y, src)};
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
   }
@@ -851,15 +721,14 @@ template <>
 cudaError_t sweep_impl<cf>(const TaskDesc* d_tasks, int n_tasks, int max_W,
                            const double* d_wire, const double* d_phi, const cd* d_sig, cf* d_gL,
                            cf* d_gR, int32_t* d_err, cudaStream_t s) {
-  // W <= 12: both sweeps of a task interleaved in one warp (two independent chains per lane)
   if (max_W <= 8) {
-    rgf_sweep_reg2_kernel<8><<<n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig, d_gL,
-                                                    d_gR, d_err);
+    rgf_sweep_reg_kernel<8><<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig,
+                                                       d_gL, d_gR, d_err);
     return cudaGetLastError();
   }
   if (max_W <= 12) {
-    rgf_sweep_reg2_kernel<12><<<n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig,
-                                                     d_gL, d_gR, d_err);
+    rgf_sweep_reg_kernel<12><<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig,
+                                                        d_gL, d_gR, d_err);
     return cudaGetLastError();
   }
   if (max_W <= 16) {
