@@ -225,7 +225,7 @@ def run_gpu(args):
         # launch shapes picked by the library's autotuner on this workload
         plan = negf.negf_plan_create(ctx, dev_wires, 0, N, wl.mu_p, wl.mu_q, wl.kT,
                                      precision=prec, memspace="device", max_steps=args.max_steps,
-                                     autotune=True)
+                                     tasks_per_wave=args.plan_tasks_per_wave, autotune=True)
         tuning = negf.negf_plan_get_tuning(plan)
 
     def one_step(step_idx, wires, memspace, prec=prec):
@@ -390,7 +390,9 @@ def run_gpu(args):
                    "walkers_per_task": N, "precision": prec, "start_lead": "L",
                    "mu_p": wl.mu_p, "mu_q": wl.mu_q, "kT": wl.kT,
                    "l2": "flushed between timed steps (258 MiB write, outside the timed events)",
-                   "mode": args.mode, "tasks_per_wave": args.tasks_per_wave,
+                   "mode": args.mode,
+                   "tasks_per_wave": (args.plan_tasks_per_wave if args.mode == "graph"
+                                      else args.tasks_per_wave),
                    "launch_shapes": tuning,
                    "parallelism": f"tasks replicated per rank, walker ids disjoint ({world} GPU)"},
         "walker_steps_per_step": all_steps / args.steps / world,
@@ -516,6 +518,8 @@ def main():
     ap.add_argument("--tasks-per-wave", type=int, default=8)
     ap.add_argument("--walk-blocks-per-sm", type=int, default=4)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
+    ap.add_argument("--plan-tasks-per-wave", type=int, default=0,
+                    help="graph mode: tasks per wave (0: all tasks in one wave)")
     ap.add_argument("--energies", type=int, default=0,
                     help="use an evenly spread subset of this many grid energies")
     args = ap.parse_args()

@@ -624,9 +624,12 @@ __global__ void chain_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
   const int row0 = inj ? n + p * W : m0 * W;
   R* wrow = weights + d.wt_off;
   // weights of block k held in X (X[a][b] = G_{(k,a),(m0,b)} or (G Phi)_{(k,a),mu})
+  // idx / W without an integer division: (idx + 1/2) / W is at least 1/(2W) away from an
+  // integer, far above the float error for idx < W^2 <= 4096
+  const float rW = 1.0f / (float)W;
   auto emit = [&](const C* X, int k) {
     for (int idx = lane; idx < W * W; idx += 32) {
-      const int b = idx / W, a = idx % W;
+      const int b = (int)(((float)idx + 0.5f) * rW), a = idx - b * W;
       wrow[(uint64_t)(row0 + b) * K + k * W + a] = eta[k * W + a] * norm2(X[a * W + b]);
       if (green) {
         // keep G (site columns) or G Phi (injection columns) for the gradient
@@ -654,12 +657,34 @@ __global__ void chain_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
   const int k_end = dir == 0 ? -1 : L;
   const int step = dir == 0 ? -1 : 1;
   const C* gsrc = dir == 0 ? gL : gR;
-  for (int k = m0 + step; k != k_end; k += step) {
+  // the next block g_k is loaded into registers one step ahead (lane's entries idx = lane + 32 i)
+  constexpr int kPre = 4;                        // covers W * W <= 128 entries
+  const bool pre = W * W <= 32 * kPre;
+  C gpre[kPre];
+  auto fetch = [&](int k) {
     const C* gk = gsrc + d.g_off + (uint64_t)k * W * W;
-    for (int idx = lane; idx < W * W; idx += 32) Gb[idx] = gk[idx];
+#pragma unroll
+    for (int i = 0; i < kPre; ++i) {
+      const int idx = lane + 32 * i;
+      if (idx < W * W) gpre[i] = gk[idx];
+    }
+  };
+  if (pre && m0 + step != k_end) fetch(m0 + step);
+  for (int k = m0 + step; k != k_end; k += step) {
+    if (pre) {
+#pragma unroll
+      for (int i = 0; i < kPre; ++i) {
+        const int idx = lane + 32 * i;
+        if (idx < W * W) Gb[idx] = gpre[i];
+      }
+      if (k + step != k_end) fetch(k + step);
+    } else {
+      const C* gk = gsrc + d.g_off + (uint64_t)k * W * W;
+      for (int idx = lane; idx < W * W; idx += 32) Gb[idx] = gk[idx];
+    }
     __syncwarp();
     for (int idx = lane; idx < W * W; idx += 32) {
-      const int a = idx / W, b = idx % W;
+      const int a = (int)(((float)idx + 0.5f) * rW), b = idx - a * W;
       C acc = C{0, 0};
       for (int c = 0; c < W; ++c) acc = acc + Gb[a * W + c] * cur[c * W + b];
       nxt[idx] = mt * acc;
