@@ -159,56 +159,55 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
     // transition; later blocks: two Step 6' transitions.
     const uint4 r = philox4x32_10(make_uint4(b, wid_lo, wid_hi, task_id), key);
     int outcome = -3;                  // -3: continue, 0/1: absorbed at L/R, -2: truncated
-    // First draw of the block, one gather for every lane: the injection row of the start lead
-    // (block 0), else the current row (one-level) or its level-1 row (two-level).
-    const bool inj = b == 0;
-    const uint32_t K1 = L + 2;
-    const uint32_t size1 = inj ? W : (two ? K1 : K);
-    const uint64_t* base1 = inj ? mrow : (two ? l1row + (uint64_t)row * K1 : trow + (uint64_t)row * K);
-    const uint32_t c1 = __umulhi(r.x, size1);
-    const uint64_t e1 = __ldg(base1 + c1);
-    const uint32_t pick1 = r.y < (uint32_t)e1 ? c1 : (uint32_t)(e1 >> 32);
-    // Second draw: one-level, the next transition of a walk still in the wire; two-level, the
-    // site in the drawn slice (block 0 of two-level tables holds the injection draw alone).
-    bool second;
-    uint32_t slice = 0;
-    if (inj) {
-      row = inj_row0 + pick1;
-      second = !two;
-    } else {
-      ++steps;
-      const uint32_t lim = two ? L : n;
-      if (pick1 >= lim) {
-        outcome = (int)(pick1 - lim);
-        second = false;
-      } else if (two) {
-        slice = pick1;
-        second = true;                 // the level-2 draw (also when the step cap ends the walk)
-      } else if (steps >= max_steps) {
-        outcome = -2;
-        second = false;
+    if (two) {
+      // two-level tables: block 0 is the injection draw alone; block b >= 1 is transition b,
+      // words (x, y) for the slice or lead (level 1), (z, w) for the site in the slice
+      if (b == 0) {
+        const uint32_t c = __umulhi(r.x, W);
+        const uint64_t e = __ldg(mrow + c);
+        row = inj_row0 + (r.y < (uint32_t)e ? c : (uint32_t)(e >> 32));
       } else {
-        row = pick1;
-        second = true;
-      }
-    }
-    if (second) {
-      const uint32_t size2 = two ? W : K;
-      const uint64_t* base2 = two ? trow + ((uint64_t)row * L + slice) * W : trow + (uint64_t)row * K;
-      const uint32_t c2 = __umulhi(r.z, size2);
-      const uint64_t e2 = __ldg(base2 + c2);
-      const uint32_t pick2 = r.w < (uint32_t)e2 ? c2 : (uint32_t)(e2 >> 32);
-      if (two) {
-        if (steps >= max_steps) outcome = -2;
-        else row = slice * W + pick2;
-      } else {
+        const uint32_t K1 = L + 2;
+        const uint32_t c = __umulhi(r.x, K1);
+        const uint64_t e = __ldg(l1row + (uint64_t)row * K1 + c);
+        const uint32_t k = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
         ++steps;
-        if (pick2 >= n) outcome = (int)(pick2 - n);
-        else if (steps >= max_steps) outcome = -2;
-        else row = pick2;
+        if (k >= L) {
+          outcome = (int)(k - L);
+        } else {
+          const uint32_t c2 = __umulhi(r.z, W);
+          const uint64_t e2 = __ldg(trow + ((uint64_t)row * L + k) * W + c2);
+          const uint32_t a = r.w < (uint32_t)e2 ? c2 : (uint32_t)(e2 >> 32);
+          if (steps >= max_steps) outcome = -2;
+          else row = k * W + a;
+        }
       }
+      ++b;
+    } else {
+    if (b == 0) {
+      const uint32_t c = __umulhi(r.x, W);
+      const uint64_t e = __ldg(mrow + c);
+      row = inj_row0 + (r.y < (uint32_t)e ? c : (uint32_t)(e >> 32));
+    } else {
+      const uint32_t c = __umulhi(r.x, K);
+      const uint64_t e = __ldg(trow + (uint64_t)row * K + c);
+      const uint32_t j = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+      ++steps;
+      if (j >= n) outcome = (int)(j - n);
+      else if (steps >= max_steps) outcome = -2;
+      else row = j;
+    }
+    if (outcome == -3) {
+      const uint32_t c = __umulhi(r.z, K);
+      const uint64_t e = __ldg(trow + (uint64_t)row * K + c);
+      const uint32_t j = r.w < (uint32_t)e ? c : (uint32_t)(e >> 32);
+      ++steps;
+      if (j >= n) outcome = (int)(j - n);
+      else if (steps >= max_steps) outcome = -2;
+      else row = j;
     }
     ++b;
+    }
     if (kScore && outcome >= 0) {
       // replay the finished walk and count its transitions under its absorbing lead
       unsigned long long* cnt = score.cnt + (size_t)outcome * score.stride + t_tab_off;
