@@ -10,7 +10,7 @@
 // Columns n and n+1 are the leads: drawing one ends the walk, and the sample's estimator is
 // X_pq = Tr[Gamma_p A] delta_rq (Eq. elast_lin_xpq), tallied as counts per absorbing lead.
 // When a walk ends the lane starts the next walker of its own run of consecutive walker indices
-// (16 per lane) with no warp coordination; once enough lanes of a warp have run dry, one lane
+// (32 per lane) with no warp coordination; once enough lanes of a warp have run dry, one lane
 // claims a new range for all of them from a global counter.  Every loop iteration consumes one
 // whole Philox block (two draws: the injection and the first transition for a new walker, two
 // transitions afterwards), so the generator runs warp-uniformly.  Each lane counts its outcomes for
@@ -27,7 +27,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kFields = NEGF_TALLY_FIELDS;   // done, absorbed L, absorbed R, truncated, steps
 constexpr int kMaxWindow = 1024;             // tasks per launch (40 KB shared tally)
-constexpr unsigned kRun = 16;                // consecutive walkers handed to a lane at a time
+constexpr unsigned kRun = 32;                // consecutive walkers handed to a lane at a time
 constexpr int kClaimMin = 8;                 // dry lanes that trigger a claim
 constexpr unsigned kFlushAt = 1u << 26;      // flush a lane's counters before they can overflow
 
