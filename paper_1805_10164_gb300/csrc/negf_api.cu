@@ -1295,7 +1295,7 @@ negf_status negf_walk(negf_ctx ctx, negf_tables t, int32_t start_lead, uint64_t 
   tl->ctx = ctx;
   tl->n_tasks = t->n_tasks;
   tl->start_lead = start_lead;
-  cudaError_t e = dalloc(&tl->d_counts, (size_t)t->n_tasks * NEGF_TALLY_FIELDS, ctx->stream, nullptr);
+  cudaError_t e = dalloc(&tl->d_counts, (size_t)std::max(1, t->n_tasks) * NEGF_TALLY_FIELDS, ctx->stream, nullptr);
   if (e != cudaSuccess) {
     delete tl;
     return fail(ctx, NEGF_E_NOMEM, "negf_walk: tally allocation: %s", cudaGetErrorString(e));
