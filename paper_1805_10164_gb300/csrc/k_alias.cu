@@ -37,32 +37,95 @@ __device__ __forceinline__ uint64_t pack(uint32_t thr, uint32_t alias) {
   return (uint64_t)thr | ((uint64_t)alias << 32);
 }
 
-__host__ __device__ inline size_t alias_warp_bytes(int cap) {
-  // lc, hc, stage : u64 [cap] | li, hi : u32 [cap]
-  return (size_t)cap * (3 * sizeof(uint64_t) + 2 * sizeof(uint32_t));
+// Each lane owns a block of npl = ceil(K/32) consecutive items.  Per-item values live in shared
+// memory at slot (i / npl) * pitch + i % npl, with an odd pitch (npl or npl + 1) so that the 32
+// lanes walking their blocks in step touch 32 different banks.
+__host__ __device__ inline int alias_npl(int K) { return (K + 31) >> 5; }
+__host__ __device__ inline int alias_pitch(int K) { return alias_npl(K) | 1; }
+// Per-warp shared memory: s_u, s_c : u64 [32 pitch] | s_x : u32 [cap] | staging buffer for the
+// next row's weights (cap elements of `elem` bytes, or 64 FP64 mode weights), 16-byte aligned.
+__host__ __device__ inline size_t alias_stage_off(int cap) {
+  const size_t slots = (size_t)32 * alias_pitch(cap);
+  return (2 * slots * sizeof(uint64_t) + (size_t)cap * sizeof(uint32_t) + 15) & ~(size_t)15;
 }
+__host__ __device__ inline size_t alias_warp_bytes(int cap, int elem) {
+  const size_t stage = (size_t)cap * elem > 64 * sizeof(double) ? (size_t)cap * elem
+                                                                  : 64 * sizeof(double);
+  return alias_stage_off(cap) + ((stage + 15) & ~(size_t)15);
+}
+
+// Asynchronous global -> shared copies of 4 or 8 bytes (the weights of the next row).
+template <int kBytes>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(kBytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t fixp(float w, int sh) { return small_fixp(w, sh); }
 __device__ __forceinline__ uint32_t fixp(double w, int sh) { return __double2uint_rz(ldexp(w, sh)); }
 
-// Build one row.  w: K weights; A: the value the row must sum to (checked when check_A);
-// out: K entries; rowsum_out: receives the row sum.
-template <typename R>
-__device__ void alias_row(const R* __restrict__ w, int K, double A, bool check_A, double tol,
-                          uint64_t* __restrict__ out, double* rowsum_out, uint64_t* s_lc,
-                          uint64_t* s_hc, uint64_t* s_st, uint32_t* s_li, uint32_t* s_hi,
-                          int32_t* err) {
+// First index in [lo, hi) whose key is > x (pred gt) or >= x (pred ge); hi when none.  key(i) is
+// non-decreasing.  Starts with a gallop from lo, so that a cursor that moves little costs a few
+// loads.
+template <bool kStrict, typename Key>
+__device__ __forceinline__ int gallop_first(int lo, int hi, uint64_t x, Key key) {
+  auto past = [&](int i) { return kStrict ? key(i) > x : key(i) >= x; };
+  if (lo >= hi || past(lo)) return lo;
+  int step = 1;                                   // key(lo) fails the test
+  int a = lo;                                     // invariant: key(a) fails
+  while (a + step < hi && !past(a + step)) {
+    a += step;
+    step <<= 1;
+  }
+  int b = min(a + step, hi);                      // b == hi or key(b) passes
+  ++a;
+  while (a < b) {
+    const int mid = (a + b) >> 1;
+    if (past(mid)) b = mid; else a = mid + 1;
+  }
+  return a;
+}
+
+// Build one row.  w: the K weights, staged in shared memory; A: the value the row must sum to
+// (checked when check_A); out: K entries; rowsum_out: receives the row sum.  s_u, s_c:
+// 32 * alias_pitch(K) u64 each; s_x: K u32.  after_stage() is called by every lane once w has
+// been read (the caller reuses w's buffer for the next row).
+template <typename R, typename After>
+__device__ void alias_row(const R* w, int K, double A, bool check_A, double tol,
+                          uint64_t* __restrict__ out, double* rowsum_out, uint64_t* s_u,
+                          uint64_t* s_c, uint32_t* s_x, int32_t* err, After after_stage) {
   const int lane = threadIdx.x & 31;
   const unsigned FULL = 0xffffffffu;
-  const unsigned lt_mask = (1u << lane) - 1u;
-  // largest weight (non-finite or negative weights are reported; they are treated as 0)
+  const int npl = alias_npl(K), pitch = alias_pitch(K);
+  // slots of items lane, lane + 32, ...: (quotient, remainder) by npl, stepped by 32
+  const int q32 = 32 / npl, r32 = 32 - q32 * npl;
+  const int qlane = lane / npl, rlane = lane - qlane * npl;
+  const int i0 = lane * npl;                                    // this lane's items [i0, i1)
+  const int i1 = min(K, i0 + npl);
+  const int mine = max(0, i1 - i0);
+  uint64_t* my_u = s_u + lane * pitch;
+  R* s_w = reinterpret_cast<R*>(s_c);
+  R* my_w = s_w + lane * pitch;
+  // pass 1 (coalesced): stage the row, largest weight; FP64 rows also take their FP64 sum here
+  // (lane-strided order, tree to lane 0)
   R wmax = 0;
   bool bad = false;
-  for (int i = lane; i < K; i += 32) {
+  double part = 0.0;
+  for (int i = lane, q = qlane, rm = rlane; i < K; i += 32) {
     const R v = w[i];
+    s_w[q * pitch + rm] = v;
+    q += q32;
+    rm += r32;
+    if (rm >= npl) { rm -= npl; ++q; }
     bad |= !(v >= 0) || !isfinite(v);
     if (v > wmax && isfinite(v)) wmax = v;
+    if (sizeof(R) == 8) part += (double)v;
   }
+  __syncwarp();
+  after_stage();
   for (int off = 16; off > 0; off >>= 1) wmax = max(wmax, __shfl_xor_sync(FULL, wmax, off));
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
   if (!(wmax > 0)) {
@@ -72,43 +135,43 @@ __device__ void alias_row(const R* __restrict__ w, int K, double A, bool check_A
     return;
   }
   int ex = 0;
-  frexp((double)wmax, &ex);                   // wmax = f 2^ex, f in [0.5, 1)
-  const int sh = 32 - ex;                      // wmax 2^sh in [2^31, 2^32)
+  if (sizeof(R) == 4) frexpf((float)wmax, &ex);   // wmax = f 2^ex, f in [0.5, 1)
+  else frexp((double)wmax, &ex);
+  const int sh = 32 - ex;                          // wmax 2^sh in [2^31, 2^32)
+  // pass 2 (own block): integer weights m_i, T = sum m_i
   uint64_t T = 0;
-  for (int i = lane; i < K; i += 32) {
-    const R v = w[i];
+  for (int k = 0; k < mine; ++k) {
+    const R v = my_w[k];
     const uint32_t m = (v > 0 && isfinite(v)) ? fixp(v, sh) : 0u;
-    s_st[i] = m;
+    my_u[k] = m;
     T += m;
   }
   for (int off = 16; off > 0; off >>= 1) T += __shfl_xor_sync(FULL, T, off);
-  // row sum: FP64 weights are summed in FP64 (fixed order: lane-strided, tree to lane 0);
-  // FP32 weights use the exact fixed-point sum (within K 2^-32 of the largest weight)
-  double total = ldexp((double)T, -sh);
-  if (sizeof(R) == 8) {
-    double part = 0.0;
-    for (int i = lane; i < K; i += 32) part += (double)w[i];
+  // row sum: FP64 weights are summed in FP64; FP32 weights use the exact fixed-point sum
+  // (within K 2^-32 of the largest weight)
+  if (sizeof(R) == 8)
     for (int off = 16; off > 0; off >>= 1) part += __shfl_down_sync(FULL, part, off);
-    total = __shfl_sync(FULL, part, 0);
-  }
+  // the FP64 steps run on lane 0 only (FP64 throughput is low); the reciprocal is broadcast
+  uint64_t rcp = 0;
   if (lane == 0) {
+    const double total = sizeof(R) == 8 ? part : ldexp((double)T, -sh);
+    rcp = (uint64_t)(ldexp(1.0, 94) / (double)T);   // < 2^63 since T >= 2^31
     *rowsum_out = total;
     if (check_A && A > 1e-300 && fabs(total - A) > tol * A) atomicOr(err, ERR_ROWSUM);
   }
-  // u_i = floor(m_i K 2^32 / T) = (m_i K) (2^94 / T) / 2^62, with the 128-bit product
+  // pass 3: u_i = floor(m_i K 2^32 / T) = (m_i K) (2^94 / T) / 2^62, with the 128-bit product
+  rcp = __shfl_sync(FULL, rcp, 0);
   const uint64_t target = (uint64_t)K << 32;
-  const uint64_t rcp = (uint64_t)(ldexp(1.0, 94) / (double)T);   // < 2^63 since T >= 2^31
   uint64_t usum = 0, umax = 0;
   int imax = 0x7fffffff;
-  __syncwarp();
-  for (int i = lane; i < K; i += 32) {
-    const uint64_t q = s_st[i] * (uint64_t)K;
+  for (int k = 0; k < mine; ++k) {
+    const uint64_t q = my_u[k] * (uint64_t)K;
     const uint64_t hi = __umul64hi(q, rcp), lo = q * rcp;
     uint64_t u = (hi << 2) | (lo >> 62);
     if (u > target) u = target;
-    s_st[i] = u;
+    my_u[k] = u;
     usum += u;
-    if (u > umax || (u == umax && i < imax)) { umax = u; imax = i; }
+    if (u > umax) { umax = u; imax = i0 + k; }   // first index of the lane's maximum
   }
   for (int off = 16; off > 0; off >>= 1) {
     usum += __shfl_xor_sync(FULL, usum, off);
@@ -116,79 +179,90 @@ __device__ void alias_row(const R* __restrict__ w, int K, double A, bool check_A
     const int oi = __shfl_xor_sync(FULL, imax, off);
     if (om > umax || (om == umax && oi < imax)) { umax = om; imax = oi; }
   }
-  __syncwarp();
-  if (lane == 0) s_st[imax] += target - usum;   // two's-complement add of a signed remainder
-  __syncwarp();
-  // integer prefix sums of deficits (lights) and excesses (heavies), index order
-  int nl = 0, nh = 0;
-  uint64_t runl = 0, runh = 0;
-  for (int base = 0; base < K; base += 32) {
-    const int i = base + lane;
-    const bool valid = i < K;
-    const uint64_t u = valid ? s_st[i] : 0ull;
-    const bool heavy = valid && u >= kSlot;
-    const bool light = valid && !heavy;
-    const unsigned bh = __ballot_sync(FULL, heavy);
-    const unsigned bl = __ballot_sync(FULL, light);
-    uint64_t dl = light ? kSlot - u : 0ull;
-    uint64_t dh = heavy ? u - kSlot : 0ull;
-    for (int off = 1; off < 32; off <<= 1) {
-      const uint64_t ol = __shfl_up_sync(FULL, dl, off);
-      const uint64_t oh = __shfl_up_sync(FULL, dh, off);
-      if (lane >= off) { dl += ol; dh += oh; }
+  if (i0 <= imax && imax < i1) my_u[imax - i0] += target - usum;   // signed remainder
+  // pass 4: lights (u < 2^32) carry deficits 2^32 - u, heavies excesses u - 2^32; exclusive
+  // prefix over the lanes of counts and sums
+  uint32_t cnt = 0;                               // lights | heavies << 16
+  uint64_t dl = 0, dh = 0;
+  for (int k = 0; k < mine; ++k) {
+    const uint64_t u = my_u[k];
+    if (u >= kSlot) { cnt += 1u << 16; dh += u - kSlot; }
+    else { cnt += 1u; dl += kSlot - u; }
+  }
+  uint32_t cx = cnt;
+  uint64_t lx = dl, hx = dh;                      // inclusive scans
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t oc = __shfl_up_sync(FULL, cx, off);
+    const uint64_t ol = __shfl_up_sync(FULL, lx, off);
+    const uint64_t oh = __shfl_up_sync(FULL, hx, off);
+    if (lane >= off) { cx += oc; lx += ol; hx += oh; }
+  }
+  const uint32_t ctot = __shfl_sync(FULL, cx, 31);
+  const int nl = (int)(ctot & 0xffffu), nh = (int)(ctot >> 16);
+  int r = (int)((cx - cnt) & 0xffffu), j = (int)((cx - cnt) >> 16);   // first light / heavy
+  uint64_t runl = lx - dl, runh = hx - dh;                             // of this lane
+  __syncwarp();                                   // s_w (in s_c) is dead from here
+  // pass 5: Lc_r (inclusive deficit prefix, light order) from the front of s_c, Ec_j (inclusive
+  // excess prefix, heavy order) from the back; s_x holds the item index of each
+  for (int k = 0; k < mine; ++k) {
+    const uint64_t u = my_u[k];
+    if (u >= kSlot) {
+      runh += u - kSlot;
+      s_c[K - 1 - j] = runh;
+      s_x[K - 1 - j] = (uint32_t)(i0 + k);
+      ++j;
+    } else {
+      runl += kSlot - u;
+      s_c[r] = runl;
+      s_x[r] = (uint32_t)(i0 + k);
+      ++r;
     }
-    if (light) {
-      const int r = nl + __popc(bl & lt_mask);
-      s_lc[r] = runl + dl;
-      s_li[r] = (uint32_t)i;
-    }
-    if (heavy) {
-      const int j = nh + __popc(bh & lt_mask);
-      s_hc[j] = runh + dh;
-      s_hi[j] = (uint32_t)i;
-    }
-    runl += __shfl_sync(FULL, dl, 31);
-    runh += __shfl_sync(FULL, dh, 31);
-    nl += __popc(bl);
-    nh += __popc(bh);
   }
   __syncwarp();
   if (nh == 0) {   // cannot happen when sum(u) == K 2^32; keep the row drawable anyway
     for (int i = lane; i < K; i += 32) out[i] = pack(0xffffffffu, (uint32_t)i);
     return;
   }
-  // lights: alias = heavy whose interval [Ec_{j-1}, Ec_j) contains the light's start
-  for (int r = lane; r < nl; r += 32) {
-    const uint64_t st = r == 0 ? 0ull : s_lc[r - 1];
-    int lo = 0, hi = nh;                         // first j with Ec_j > st
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (s_hc[mid] > st) hi = mid; else lo = mid + 1;
+  auto Ec = [&](int jj) { return s_c[K - 1 - jj]; };
+  auto Lc = [&](int rr) { return s_c[rr]; };
+  // pass 6: entries, into s_u by item index (s_u is dead from here).  The lanes split the light
+  // list, then the heavy list, into contiguous ranges, each searched from a cursor that moves
+  // forward.
+  // Light r (start Lc_{r-1}, u_r = 2^32 - (Lc_r - Lc_{r-1})) aliases the heavy whose excess
+  // interval [Ec_{j-1}, Ec_j) contains its start.
+  {
+    const int ra = (lane * nl) >> 5, rb = ((lane + 1) * nl) >> 5;
+    uint64_t st = ra == 0 ? 0ull : Lc(ra - 1);
+    int jc = 0;
+    for (int rr = ra; rr < rb; ++rr) {
+      const uint64_t Lr = Lc(rr);
+      jc = gallop_first<true>(jc, nh, st, Ec);          // first j with Ec_j > st
+      const int jj = jc < nh ? jc : nh - 1;
+      s_u[s_x[rr]] = pack((uint32_t)(kSlot - (Lr - st)), s_x[K - 1 - jj]);
+      st = Lr;
     }
-    if (lo >= nh) lo = nh - 1;
-    const uint32_t i = s_li[r];
-    s_st[i] = pack((uint32_t)s_st[i], s_hi[lo]);
   }
-  // heavies
-  for (int j = lane; j < nh; j += 32) {
-    const uint32_t i = s_hi[j];
-    uint64_t e = pack(0xffffffffu, i);
-    const uint64_t Ej = s_hc[j];
-    if (j < nh - 1 && Ej > 0) {
-      int lo = 0, hi = nl;                       // first r with Lc_r >= Ej
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (s_lc[mid] >= Ej) hi = mid; else lo = mid + 1;
+  // Heavy j (not the last, Ec_j > 0) is consumed past its excess by the light interval
+  // (Lc_{r-1}, Lc_r] containing Ec_j: it keeps 2^32 - (Lc_r - Ec_j) and aliases heavy j + 1.
+  {
+    const int ja = (lane * nh) >> 5, jb = ((lane + 1) * nh) >> 5;
+    int rc = 0;
+    for (int jj = ja; jj < jb; ++jj) {
+      const uint32_t self = s_x[K - 1 - jj];
+      uint64_t e = pack(0xffffffffu, self);
+      const uint64_t Ej = Ec(jj);
+      if (jj < nh - 1 && Ej > 0) {
+        rc = gallop_first<false>(rc, nl, Ej, Lc);       // first r with Lc_r >= Ej
+        if (rc < nl) {
+          const uint64_t used = Lc(rc) - Ej;            // consumed beyond the excess, <= 2^32
+          if (used > 0) e = pack((uint32_t)(kSlot - used), s_x[K - 1 - (jj + 1)]);
+        }
       }
-      if (lo < nl) {
-        const uint64_t used = s_lc[lo] - Ej;     // consumed beyond the excess, <= 2^32
-        if (used > 0) e = pack((uint32_t)(kSlot - used), s_hi[j + 1]);
-      }
+      s_u[self] = e;
     }
-    s_st[i] = e;
   }
   __syncwarp();
-  for (int i = lane; i < K; i += 32) out[i] = s_st[i];
+  for (int i = lane; i < K; i += 32) out[i] = s_u[i];
 }
 
 template <typename R>
@@ -198,35 +272,65 @@ __global__ void alias_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
                              uint64_t* __restrict__ tab, uint64_t* __restrict__ mode_tab,
                              int32_t* err) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nwarps = blockDim.x >> 5;
-  unsigned char* base = smem_raw + (size_t)warp * alias_warp_bytes(cap);
-  uint64_t* s_lc = reinterpret_cast<uint64_t*>(base);
-  uint64_t* s_hc = s_lc + cap;
-  uint64_t* s_st = s_hc + cap;
-  uint32_t* s_li = reinterpret_cast<uint32_t*>(s_st + cap);
-  uint32_t* s_hi = s_li + cap;
-  for (uint32_t job = blockIdx.x * nwarps + warp; job < total_jobs; job += gridDim.x * nwarps) {
-    int lo = 0, hi = n_tasks - 1;                // task owning this job
+  unsigned char* base = smem_raw + (size_t)warp * alias_warp_bytes(cap, (int)sizeof(R));
+  uint64_t* s_u = reinterpret_cast<uint64_t*>(base);
+  uint64_t* s_c = s_u + (size_t)32 * alias_pitch(cap);
+  uint32_t* s_x = reinterpret_cast<uint32_t*>(s_c + (size_t)32 * alias_pitch(cap));
+  unsigned char* s_stage = base + alias_stage_off(cap);
+  const uint32_t stride = gridDim.x * nwarps;
+  // task owning a job: jobs of a warp only increase, so the search starts at the last task found
+  int hint = 0;
+  auto find = [&](uint32_t jb) {
+    int lo = hint, hi = n_tasks - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
-      if (tasks[mid].row_base <= job) lo = mid; else hi = mid - 1;
+      if (tasks[mid].row_base <= jb) lo = mid; else hi = mid - 1;
     }
-    const TaskDesc& d = tasks[lo];
+    return lo;
+  };
+  // the weights of job jb go to s_stage by asynchronous copies (one commit group)
+  auto stage = [&](uint32_t jb) {
+    const TaskDesc& d = tasks[find(jb)];
+    const int row = (int)(jb - d.row_base);
+    if (row < d.rows) {
+      const R* src = weights + d.wt_off + (uint64_t)row * d.K;
+      R* dst = reinterpret_cast<R*>(s_stage);
+      for (int i = lane; i < d.K; i += 32) cp_async<(int)sizeof(R)>(dst + i, src + i);
+    } else {
+      const double* src = mode_w + d.mode_off + (row - d.rows) * d.W;
+      double* dst = reinterpret_cast<double*>(s_stage);
+      for (int i = lane; i < d.W; i += 32) cp_async<8>(dst + i, src + i);
+    }
+    cp_async_commit();
+  };
+  uint32_t job = blockIdx.x * nwarps + warp;
+  if (job < total_jobs) stage(job);
+  for (; job < total_jobs; job += stride) {
+    hint = find(job);
+    const TaskDesc& d = tasks[hint];
     const int row = (int)(job - d.row_base);
     const double A = rowsum[job];                 // <i|A|i> (rows) or c_p (mode rows)
+    const uint32_t next = job + stride;
+    auto after = [&]() {
+      if (next < total_jobs) stage(next);
+    };
+    cp_async_wait_all();
+    __syncwarp();
     if (row < d.rows) {
-      alias_row<R>(weights + d.wt_off + (uint64_t)row * d.K, d.K, A, true, tol,
-                   tab + d.tab_off + (uint64_t)row * d.K, rowsum + job, s_lc, s_hc, s_st, s_li,
-                   s_hi, err);
+      alias_row<R>(reinterpret_cast<const R*>(s_stage), d.K, A, true, tol,
+                   tab + d.tab_off + (uint64_t)row * d.K, rowsum + job, s_u, s_c, s_x, err,
+                   after);
     } else {
       const int p = row - d.rows;
-      alias_row<double>(mode_w + d.mode_off + p * d.W, d.W, A, true, 1e-9,
-                        mode_tab + d.mode_off + p * d.W, rowsum + job, s_lc, s_hc, s_st, s_li,
-                        s_hi, err);
+      alias_row<double>(reinterpret_cast<const double*>(s_stage), d.W, A, true, 1e-9,
+                        mode_tab + d.mode_off + p * d.W, rowsum + job, s_u, s_c, s_x, err,
+                        after);
     }
     __syncwarp();
   }
+  cp_async_wait_all();
 }
 
 // One warp per table row of a two-level task.  The row is taken in chunks of 32 slices: the
@@ -317,7 +421,7 @@ cudaError_t launch_two_level_split(const TaskDesc* d_tasks, int n_tasks, uint32_
 
 int alias_warps_max(int max_K) {
   const int cap = max_K < 64 ? 64 : max_K;
-  const size_t per_warp = alias_warp_bytes(cap);
+  const size_t per_warp = alias_warp_bytes(cap, (int)sizeof(double));
   int w = 16;
   while (w > 1 && per_warp * w > 200 * 1024) --w;
   return w;
@@ -330,7 +434,8 @@ cudaError_t launch_alias_build(const TaskDesc* d_tasks, int n_tasks, uint32_t to
                                int warps_req) {
   if (total_jobs == 0) return cudaSuccess;
   const int cap = max_K < 64 ? 64 : max_K;
-  const size_t per_warp = alias_warp_bytes(cap);
+  const size_t per_warp =
+      alias_warp_bytes(cap, precision == NEGF_FP64 ? (int)sizeof(double) : (int)sizeof(float));
   const int wmax = alias_warps_max(max_K);
   int warps = 8;
   while (warps > 1 && per_warp * warps > 96 * 1024) --warps;
