@@ -222,86 +222,110 @@ __global__ void rgf_sweep_kernel(const TaskDesc* __restrict__ tasks, int n_tasks
   }
 }
 
-// ---- register-resident variants for complex64 blocks with W <= MAXW <= 16 -----------------
-// Lane j < W holds column j of the slice matrix and lane W + j column j of the identity (then
-// of the inverse), MAXW rows each in registers; Gauss-Jordan with partial pivoting runs with
-// shuffles only (no shared memory on the sequential sweep).
+// ---- register-resident variants for complex64 blocks with W <= 16 ------------------------
+// Lane i < W holds row i of the augmented matrix [M | I] in registers: a[0, MAXW) the slice
+// matrix, a[MAXW, 2 MAXW) the identity (then the inverse).  Gauss-Jordan pivots without moving
+// rows: at step k the pivot is the unused row with the largest |a_ik|^2 (one warp max-reduction
+// of a 32-bit key), the pivot lane publishes its row in shared memory (broadcast loads cost far
+// less than two shuffles per element), and every other row eliminates column k.  Row i of the inverse then sits in the lane that pivoted column i.  The kernels call
+// these with MAXW equal to the block width, so that every column index is a constant.
 
-// Gauss-Jordan on the register-held augmented matrix (rows i < W are live).  Returns false
-// uniformly on a zero or non-finite pivot.
-template <int MAXW>
-__device__ bool gj_reg(cf (&a)[MAXW], int W) {
+// Gauss-Jordan on the register-held rows; on return lane i < W holds row i of the inverse in
+// a[MAXW, MAXW + W).  Returns false uniformly on a zero or non-finite pivot.
+//
+// At step k the pivot lane computes 1 / a_pk itself and publishes it with its row as it stands;
+// every other row subtracts (a_ik / a_pk) times that row.  Pivot rows are not rescaled during
+// the elimination (a pivot row only ever changes by multiples of later pivot rows, so it stays
+// a_pk times its normalised form); each is divided by its own pivot at the end.  This keeps the
+// reciprocal off the other lanes' dependency chain.
+//
+// pivot == false eliminates in row order without a pivot search.  The caller takes it only when
+// every site of the slice dephases (eta_i > 0): the slice matrix E - H - Sigma is then complex
+// symmetric with imaginary part >= diag(eta / 2) > 0 (the lead and connected-block terms add
+// positive semidefinite imaginary parts, since Im G^r <= 0), its Schur complements keep that
+// property, so no pivot vanishes and elimination without pivoting is stable for this class.
+// The row goes through shared memory as 16-byte pairs of entries: on a lone warp each shared
+// memory (or shuffle) instruction costs about as much as a dozen arithmetic ones, so the
+// broadcast is made of as few, and as wide, accesses as possible.
+// srow: 2 W + 2 complex64 of this warp's shared memory, 16-byte aligned.
+template <int W>
+__device__ bool gj_rows(cf (&a)[2 * W], bool pivot, cf* srow) {
   const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  float4* row = reinterpret_cast<float4*>(srow);   // row[q]: entries 2q, 2q + 1; row[W]: 1/pivot
+  bool used = lane >= W;                           // lanes without a row never pivot
+  int src = lane;
+  cf own_inv{1.f, 0.f};                            // 1 / pivot of the step this lane pivoted
+#pragma unroll
   for (int k = 0; k < W; ++k) {
-    float best = -1.f;
     int p = k;
-#pragma unroll
-    for (int i = 0; i < MAXW; ++i) {
-      if (i >= k && i < W) {
-        const float v = norm2(a[i]);
-        if (v > best) { best = v; p = i; }
-      }
+    if (pivot) {
+      // key: |a_ik|^2 (non-negative, so its bits order like the value) with its low 5 mantissa
+      // bits replaced by 31 - lane: the largest candidate wins, lower lanes on near-ties
+      const float v = used ? 0.f : norm2(a[k]);
+      const unsigned key = (__float_as_uint(v) & ~31u) | (unsigned)(31 - lane);
+      const unsigned best = __reduce_max_sync(FULL, key);
+      const unsigned mag = best & ~31u;
+      if (mag == 0u || mag >= 0x7f800000u) return false;   // zero, inf or NaN pivot
+      p = 31 - (int)(best & 31u);
+      if (lane == k) src = p;
     }
-    p = __shfl_sync(FULL, p, k);
-    best = __shfl_sync(FULL, best, k);
-    if (!(best > 0.f) || !isfinite(best)) return false;
-    if (p != k) {
-      cf vk = a[0], vp = a[0];
+    const bool me = lane == p;
+    __syncwarp();                                  // the previous step's row has been read
+    if (me) {
+      const float rr = __frcp_rn(norm2(a[k]));      // inf for a zero pivot: caught below
+      own_inv = cf{a[k].x * rr, -a[k].y * rr};
+      row[W] = make_float4(own_inv.x, own_inv.y, 0.f, 0.f);
 #pragma unroll
-      for (int i = 0; i < MAXW; ++i) {
-        if (i == k) vk = a[i];
-        if (i == p) vp = a[i];
-      }
-#pragma unroll
-      for (int i = 0; i < MAXW; ++i) {
-        if (i == k) a[i] = vp;
-        if (i == p) a[i] = vk;
-      }
+      for (int q = (k + 1) / 2; q < W; ++q)
+        row[q] = make_float4(a[2 * q].x, a[2 * q].y, a[2 * q + 1].x, a[2 * q + 1].y);
     }
-    cf f[MAXW];
+    __syncwarp();
+    const float4 iv = row[W];
+    if (!pivot && !(isfinite(iv.x) && isfinite(iv.y) && (iv.x != 0.f || iv.y != 0.f)))
+      return false;
+    const cf f = me ? cf{0.f, 0.f} : a[k] * cf{iv.x, iv.y};
 #pragma unroll
-    for (int i = 0; i < MAXW; ++i) {
-      f[i].x = __shfl_sync(FULL, a[i].x, k);
-      f[i].y = __shfl_sync(FULL, a[i].y, k);
+    for (int q = (k + 1) / 2; q < W; ++q) {
+      const float4 r = row[q];
+      if (2 * q > k) a[2 * q] = a[2 * q] - f * cf{r.x, r.y};
+      a[2 * q + 1] = a[2 * q + 1] - f * cf{r.z, r.w};
     }
-    cf piv = f[0], pk = a[0];
+    used |= me;
+  }
 #pragma unroll
-    for (int i = 0; i < MAXW; ++i) {
-      if (i == k) { piv = f[i]; pk = a[i]; }
-    }
-    pk = pk * cdiv(cf{1.f, 0.f}, piv);
-#pragma unroll
-    for (int i = 0; i < MAXW; ++i) {
-      if (i == k) a[i] = pk;
-      else if (i < W) a[i] = a[i] - f[i] * pk;
+  for (int j = W; j < 2 * W; ++j) {
+    a[j] = a[j] * own_inv;
+    if (pivot) {
+      a[j].x = __shfl_sync(FULL, a[j].x, src);
+      a[j].y = __shfl_sync(FULL, a[j].y, src);
     }
   }
   return true;
 }
 
-// Column j (lane j < W) of E - H_kk - Sigma_s(k) - x, where x is given as this lane's column;
-// lanes W <= j < 2W get identity columns, other lanes zeros.
+// Row i (lane i < W) of [E - H_kk - Sigma_s(k) - x | I], where x is this lane's row; other
+// lanes get zero rows.
 template <int MAXW>
-__device__ void build_col(cf (&a)[MAXW], int W, double E, double t, double onsite_j,
-                          double eta_j, const cf (&x)[MAXW]) {
-  const int j = threadIdx.x & 31;
-  const cf diag{(float)(E - onsite_j), (float)(0.5 * eta_j)};
+__device__ void build_row(cf (&a)[2 * MAXW], int W, double E, double t, double onsite_i,
+                          double eta_i, const cf (&x)[MAXW]) {
+  const int i = threadIdx.x & 31;
+  const cf diag{(float)(E - onsite_i), (float)(0.5 * eta_i)};
   const float tf = (float)t;
 #pragma unroll
-  for (int i = 0; i < MAXW; ++i) {
+  for (int j = 0; j < MAXW; ++j) {
     cf v{0.f, 0.f};
-    if (j < W && i < W) {
+    if (i < W && j < W) {
       if (i == j) v = diag;
       if (i - j == 1 || j - i == 1) v.x += tf;
-      v = v - x[i];
-    } else if (j >= W && j < 2 * W) {
-      v = cf{i == j - W ? 1.f : 0.f, 0.f};
+      v = v - x[j];
     }
-    a[i] = v;
+    a[j] = v;
+    a[MAXW + j] = cf{(i < W && i == j) ? 1.f : 0.f, 0.f};
   }
 }
 
-// column j of the lead block Phi diag(sig) Phi^T (lanes j < W)
+// row (= column, the block is symmetric) j of the lead block Phi diag(sig) Phi^T (lanes j < W)
 template <int MAXW>
 __device__ void lead_col(const double* phi, const cd* sig, int W, cf (&x)[MAXW]) {
   const int j = threadIdx.x & 31;
@@ -314,57 +338,96 @@ __device__ void lead_col(const double* phi, const cd* sig, int W, cf (&x)[MAXW])
   }
 }
 
+// One sweep (task d, direction dir) with W == MAXW known at compile time.
 template <int MAXW>
+__device__ __forceinline__ void sweep_reg_body(const TaskDesc& d, int dir,
+                                               const double* __restrict__ wire,
+                                               const double* __restrict__ phig,
+                                               const cd* __restrict__ sig, cf* gL, cf* gR,
+                                               int32_t* err, cf* srow) {
+  constexpr int W = MAXW;
+  const int L = d.L;
+  const int lane = threadIdx.x & 31;
+  const double* onsite = wire + d.onsite_off;
+  const double* eta = onsite + d.n;
+  const float ttf = (float)(d.t * d.t);     // FP32 on the serial path (FP64 is slow here)
+  cf x[MAXW], a[2 * MAXW];
+  lead_col<MAXW>(phig + d.phi_off, sig + d.lead_off, W, x);
+  cf* out = dir == 0 ? gL : gR;
+  const int ic = lane < W ? lane : 0;
+  // the next slice's onsite energy and dephasing are fetched one step ahead
+  int k = dir == 0 ? 0 : L - 1;
+  double on_i = onsite[k * W + ic], eta_i = eta[k * W + ic];
+  for (int s = 0; s < L - 1; ++s) {
+    k = dir == 0 ? s : L - 1 - s;
+    const double on_cur = on_i, eta_cur = eta_i;
+    if (s + 1 < L - 1) {
+      const int kn = dir == 0 ? s + 1 : L - 2 - s;
+      on_i = onsite[kn * W + ic];
+      eta_i = eta[kn * W + ic];
+    }
+    build_row<MAXW>(a, W, d.E, d.t, on_cur, eta_cur, x);
+    const bool piv = !__all_sync(0xffffffffu, lane >= W || eta_cur > 0.0);
+    if (!gj_rows<MAXW>(a, piv, srow)) {
+      if (lane == 0) atomicOr(err, ERR_SINGULAR);
+      return;
+    }
+    // lane i holds row i of g_k: store it and keep t^2 g_k's row i for the next slice
+    cf* dst = out + d.g_off + (uint64_t)k * W * W + (uint64_t)ic * W;
+    bool bad = false;
+#pragma unroll
+    for (int j = 0; j < MAXW; ++j) {
+      if (lane < W && j < W) {
+        dst[j] = a[MAXW + j];
+        bad |= !finite_c(a[MAXW + j]);
+      }
+      x[j] = cf{ttf * a[MAXW + j].x, ttf * a[MAXW + j].y};
+    }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
+  }
+}
+
+// Calls Body<W>::run(args...) for the compile-time W equal to w (1 <= w <= 16).
+template <template <int> class Body, typename... Args>
+__device__ __forceinline__ void by_width(int w, Args&&... args) {
+  switch (w) {
+    case 1: Body<1>::run(args...); break;
+    case 2: Body<2>::run(args...); break;
+    case 3: Body<3>::run(args...); break;
+    case 4: Body<4>::run(args...); break;
+    case 5: Body<5>::run(args...); break;
+    case 6: Body<6>::run(args...); break;
+    case 7: Body<7>::run(args...); break;
+    case 8: Body<8>::run(args...); break;
+    case 9: Body<9>::run(args...); break;
+    case 10: Body<10>::run(args...); break;
+    case 11: Body<11>::run(args...); break;
+    case 12: Body<12>::run(args...); break;
+    case 13: Body<13>::run(args...); break;
+    case 14: Body<14>::run(args...); break;
+    case 15: Body<15>::run(args...); break;
+    case 16: Body<16>::run(args...); break;
+    default: break;
+  }
+}
+
+template <int W>
+struct SweepReg {
+  template <typename... A>
+  __device__ __forceinline__ static void run(A... a) { sweep_reg_body<W>(a...); }
+};
+
+// One warp per (task, direction), tasks of width W <= 16.
 __global__ void rgf_sweep_reg_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
                                      const double* __restrict__ wire,
                                      const double* __restrict__ phig, const cd* __restrict__ sig,
                                      cf* gL, cf* gR, int32_t* err) {
   const int job = blockIdx.x;
   if (job >= 2 * n_tasks) return;
+  __shared__ __align__(16) cf s_row[34];
   const TaskDesc d = tasks[job >> 1];
-  const int dir = job & 1;
-  const int W = d.W, L = d.L;
-  const int lane = threadIdx.x & 31;
-  if (L < 2) return;
-  const double* onsite = wire + d.onsite_off;
-  const double* eta = onsite + d.n;
-  const float ttf = (float)(d.t * d.t);     // FP32 on the serial path (FP64 is slow here)
-  cf x[MAXW], a[MAXW];
-  lead_col<MAXW>(phig + d.phi_off, sig + d.lead_off, W, x);
-  cf* out = dir == 0 ? gL : gR;
-  const int jc = lane < W ? lane : 0;
-  // the next slice's onsite energy and dephasing are fetched one step ahead
-  int k = dir == 0 ? 0 : L - 1;
-  double on_j = onsite[k * W + jc], eta_j = eta[k * W + jc];
-  for (int s = 0; s < L - 1; ++s) {
-    k = dir == 0 ? s : L - 1 - s;
-    const double on_cur = on_j, eta_cur = eta_j;
-    if (s + 1 < L - 1) {
-      const int kn = dir == 0 ? s + 1 : L - 2 - s;
-      on_j = onsite[kn * W + jc];
-      eta_j = eta[kn * W + jc];
-    }
-    build_col<MAXW>(a, W, d.E, d.t, on_cur, eta_cur, x);
-    if (!gj_reg<MAXW>(a, W)) {
-      if (lane == 0) atomicOr(err, ERR_SINGULAR);
-      return;
-    }
-    // lanes W..2W-1 hold the columns of g_k; store them and hand column j to lane j as t^2 g_k
-    cf* dst = out + d.g_off + (uint64_t)k * W * W;
-    bool bad = false;
-    const int src = W + (lane < W ? lane : 0);
-#pragma unroll
-    for (int i = 0; i < MAXW; ++i) {
-      if (lane >= W && lane < 2 * W && i < W) {
-        dst[i * W + (lane - W)] = a[i];
-        bad |= !finite_c(a[i]);
-      }
-      const float gx = __shfl_sync(0xffffffffu, a[i].x, src);
-      const float gy = __shfl_sync(0xffffffffu, a[i].y, src);
-      x[i] = cf{ttf * gx, ttf * gy};
-    }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
-  }
+  if (d.L < 2) return;
+  by_width<SweepReg>(d.W, d, job & 1, wire, phig, sig, gL, gR, err, s_row);
 }
 
 // last task whose first job index (`first(t)`) is <= job
@@ -470,22 +533,20 @@ __global__ void diag_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, uin
 // Register-resident diagonal-block kernel (complex64, W <= MAXW <= 16); same outputs as
 // diag_kernel.  Shared memory per warp: G (W x W complex64) and phi (W x W double).
 template <int MAXW>
-__global__ void diag_reg_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
-                                const double* __restrict__ wire, const double* __restrict__ phig,
-                                const cd* __restrict__ sig, const double* __restrict__ gam,
-                                const cf* __restrict__ gL, const cf* __restrict__ gR,
-                                cf* __restrict__ start, double* __restrict__ rowsum,
-                                double* __restrict__ mode_w, double* __restrict__ cvals,
-                                int32_t* err) {
-  __shared__ cf s_G[8][MAXW * MAXW];
-  __shared__ double s_phi[8][MAXW * MAXW];
-  __shared__ double s_mw[8][MAXW];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t job = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (job >= n_jobs) return;
-  const int task = find_task(n_tasks, job, [&](int t) { return tasks[t].col_base; });
-  const TaskDesc d = tasks[task];
-  const int W = d.W, L = d.L, n = d.n;
+__device__ __forceinline__ void diag_reg_body(const TaskDesc& d, int task, uint32_t job,
+                                              const double* __restrict__ wire,
+                                              const double* __restrict__ phig,
+                                              const cd* __restrict__ sig,
+                                              const double* __restrict__ gam,
+                                              const cf* __restrict__ gL,
+                                              const cf* __restrict__ gR, cf* __restrict__ start,
+                                              double* __restrict__ rowsum,
+                                              double* __restrict__ mode_w,
+                                              double* __restrict__ cvals, int32_t* err, cf* sG,
+                                              double* phi, double* s_mw, cf* srow) {
+  constexpr int W = MAXW;
+  const int lane = threadIdx.x & 31;
+  const int L = d.L, n = d.n;
   const int y = (int)(job - d.col_base);
   const bool inj = y >= L;
   const int p = y - L;
@@ -493,11 +554,9 @@ __global__ void diag_reg_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
   const double* onsite = wire + d.onsite_off;
   const double* eta = onsite + n;
   const double tt = d.t * d.t;
-  cf* sG = s_G[warp];
-  double* phi = s_phi[warp];
   for (int idx = lane; idx < W * W; idx += 32) phi[idx] = phig[d.phi_off + idx];
-  // this lane's column of left + right (lead block or t^2 g)
-  cf x[MAXW], a[MAXW];
+  // this lane's row of left + right (lead block or t^2 g)
+  cf x[MAXW], a[2 * MAXW];
   const bool lead_l = m0 == 0, lead_r = m0 == L - 1;
   if (lead_l || lead_r) {
     lead_col<MAXW>(phig + d.phi_off, sig + d.lead_off, W, x);
@@ -509,27 +568,29 @@ __global__ void diag_reg_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
 #pragma unroll
     for (int i = 0; i < MAXW; ++i) x[i] = cf{0.f, 0.f};
   }
-  const int jc = lane < W ? lane : 0;
+  const int ic = lane < W ? lane : 0;
   const cf* gl = lead_l ? nullptr : gL + d.g_off + (uint64_t)(m0 - 1) * W * W;
   const cf* gr = lead_r ? nullptr : gR + d.g_off + (uint64_t)(m0 + 1) * W * W;
 #pragma unroll
-  for (int i = 0; i < MAXW; ++i) {
-    if (i < W && lane < W) {
-      if (gl) x[i] = x[i] + (float)tt * gl[i * W + jc];
-      if (gr) x[i] = x[i] + (float)tt * gr[i * W + jc];
+  for (int j = 0; j < MAXW; ++j) {
+    if (j < W && lane < W) {
+      if (gl) x[j] = x[j] + (float)tt * gl[ic * W + j];
+      if (gr) x[j] = x[j] + (float)tt * gr[ic * W + j];
     }
   }
-  build_col<MAXW>(a, W, d.E, d.t, onsite[m0 * W + jc], eta[m0 * W + jc], x);
-  if (!gj_reg<MAXW>(a, W)) {
+  const double eta_i = eta[m0 * W + ic];
+  build_row<MAXW>(a, W, d.E, d.t, onsite[m0 * W + ic], eta_i, x);
+  const bool piv = !__all_sync(0xffffffffu, lane >= W || eta_i > 0.0);
+  if (!gj_rows<MAXW>(a, piv, srow)) {
     if (lane == 0) atomicOr(err, ERR_SINGULAR);
     return;
   }
   bool bad = false;
 #pragma unroll
-  for (int i = 0; i < MAXW; ++i) {
-    if (lane >= W && lane < 2 * W && i < W) {
-      sG[i * W + (lane - W)] = a[i];
-      bad |= !finite_c(a[i]);
+  for (int j = 0; j < MAXW; ++j) {
+    if (lane < W && j < W) {
+      sG[lane * W + j] = a[MAXW + j];
+      bad |= !finite_c(a[MAXW + j]);
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
@@ -562,16 +623,45 @@ __global__ void diag_reg_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
       rowsum[d.row_base + n + p * W + b] = A;
       const double mw = gam[d.lead_off + b] * A;
       mode_w[d.mode_off + p * W + b] = mw;
-      s_mw[warp][b] = mw;
+      s_mw[b] = mw;
     }
   }
   __syncwarp();
   if (inj && lane == 0) {
     double c = 0.0;
-    for (int b = 0; b < W; ++b) c += s_mw[warp][b];      // fixed order
+    for (int b = 0; b < W; ++b) c += s_mw[b];            // fixed order
     cvals[task * 2 + p] = c;
     rowsum[d.row_base + d.rows + p] = c;
   }
+}
+
+template <int W>
+struct DiagReg {
+  template <typename... A>
+  __device__ __forceinline__ static void run(A... a) { diag_reg_body<W>(a...); }
+};
+
+// Register-resident diagonal blocks (complex64, W <= 16), one warp per column job; same outputs
+// as diag_kernel.  Shared memory per warp: G (W x W complex64), phi (W x W double), the mode
+// weights.
+__global__ void diag_reg_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
+                                const double* __restrict__ wire, const double* __restrict__ phig,
+                                const cd* __restrict__ sig, const double* __restrict__ gam,
+                                const cf* __restrict__ gL, const cf* __restrict__ gR,
+                                cf* __restrict__ start, double* __restrict__ rowsum,
+                                double* __restrict__ mode_w, double* __restrict__ cvals,
+                                int32_t* err) {
+  __shared__ cf s_G[8][16 * 16];
+  __shared__ double s_phi[8][16 * 16];
+  __shared__ double s_mw[8][16];
+  __shared__ __align__(16) cf s_row[8][34];
+  const int warp = threadIdx.x >> 5;
+  const uint32_t job = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (job >= n_jobs) return;
+  const int task = find_task(n_tasks, job, [&](int t) { return tasks[t].col_base; });
+  const TaskDesc d = tasks[task];
+  by_width<DiagReg>(d.W, d, task, job, wire, phig, sig, gam, gL, gR, start, rowsum, mode_w,
+                    cvals, err, s_G[warp], s_phi[warp], s_mw[warp], s_row[warp]);
 }
 
 template <typename C>
@@ -746,19 +836,9 @@ template <>
 cudaError_t sweep_impl<cf>(const TaskDesc* d_tasks, int n_tasks, int max_W,
                            const double* d_wire, const double* d_phi, const cd* d_sig, cf* d_gL,
                            cf* d_gR, int32_t* d_err, cudaStream_t s) {
-  if (max_W <= 8) {
-    rgf_sweep_reg_kernel<8><<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig,
-                                                       d_gL, d_gR, d_err);
-    return cudaGetLastError();
-  }
-  if (max_W <= 12) {
-    rgf_sweep_reg_kernel<12><<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig,
-                                                        d_gL, d_gR, d_err);
-    return cudaGetLastError();
-  }
   if (max_W <= 16) {
-    rgf_sweep_reg_kernel<16><<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig,
-                                                        d_gL, d_gR, d_err);
+    rgf_sweep_reg_kernel<<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig, d_gL,
+                                                    d_gR, d_err);
     return cudaGetLastError();
   }
   return sweep_smem<cf>(d_tasks, n_tasks, max_W, d_wire, d_phi, d_sig, d_gL, d_gR, d_err, s);
@@ -779,18 +859,9 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
     const cf* gl = reinterpret_cast<const cf*>(d_gL);
     const cf* gr = reinterpret_cast<const cf*>(d_gR);
     cf* st = reinterpret_cast<cf*>(d_start);
-    if (max_W <= 8)
-      diag_reg_kernel<8><<<blocks, 32 * warps, 0, s>>>(d_tasks, n_tasks, n_cols, d_wire, d_phi,
-                                                       d_sig, d_gam, gl, gr, st, d_rowsum,
-                                                       d_mode_w, d_c, d_err);
-    else if (max_W <= 12)
-      diag_reg_kernel<12><<<blocks, 32 * warps, 0, s>>>(d_tasks, n_tasks, n_cols, d_wire, d_phi,
-                                                        d_sig, d_gam, gl, gr, st, d_rowsum,
-                                                        d_mode_w, d_c, d_err);
-    else
-      diag_reg_kernel<16><<<blocks, 32 * warps, 0, s>>>(d_tasks, n_tasks, n_cols, d_wire, d_phi,
-                                                        d_sig, d_gam, gl, gr, st, d_rowsum,
-                                                        d_mode_w, d_c, d_err);
+    diag_reg_kernel<<<blocks, 32 * warps, 0, s>>>(d_tasks, n_tasks, n_cols, d_wire, d_phi, d_sig,
+                                                  d_gam, gl, gr, st, d_rowsum, d_mode_w, d_c,
+                                                  d_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   } else {
