@@ -304,24 +304,87 @@ __device__ bool gj_rows(cf (&a)[2 * W], bool pivot, cf* srow) {
   return true;
 }
 
-// Row i (lane i < W) of [E - H_kk - Sigma_s(k) - x | I], where x is this lane's row; other
-// lanes get zero rows.
-template <int MAXW>
-__device__ void build_row(cf (&a)[2 * MAXW], int W, double E, double t, double onsite_i,
-                          double eta_i, const cf (&x)[MAXW]) {
-  const int i = threadIdx.x & 31;
-  const cf diag{(float)(E - onsite_i), (float)(0.5 * eta_i)};
+// In-place Gauss-Jordan inversion without pivoting: lane j < W holds column j of the matrix in
+// a[0, W) on entry and column j of its inverse on return.  At step k the pivot column is
+// broadcast through shared memory and every lane updates its own column from registers:
+//   lane j != k:  a_kj <- a_kj / a_kk,  a_ij <- a_ij - a_ik a_kj / a_kk  (i != k)
+//   lane k:       a_kk <- 1 / a_kk,     a_ik <- -a_ik / a_kk             (i != k)
+// (both written as a_ij - c_i piv with piv = a_kj / a_kk, or 1 + 1 / a_kk on lane k).  Only for
+// matrices whose imaginary part is positive definite (see gj_rows).  Returns false uniformly on
+// a zero or non-finite pivot.  scol: W + 1 complex64 of shared memory, 16-byte aligned.
+template <int W>
+__device__ bool gj_cols(cf (&a)[W], cf* scol) {
+  const int lane = threadIdx.x & 31;
+  float4* col = reinterpret_cast<float4*>(scol);
+  constexpr int W2 = (W + 1) / 2;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    __syncwarp();                                  // the previous column has been read
+    if (lane == k) {
+#pragma unroll
+      for (int q = 0; q < W2; ++q)
+        col[q] = make_float4(a[2 * q].x, a[2 * q].y, 2 * q + 1 < W ? a[2 * q + 1].x : 0.f,
+                             2 * q + 1 < W ? a[2 * q + 1].y : 0.f);
+    }
+    __syncwarp();
+    cf c[2 * W2];
+#pragma unroll
+    for (int q = 0; q < W2; ++q) {
+      const float4 v = col[q];
+      c[2 * q] = cf{v.x, v.y};
+      c[2 * q + 1] = cf{v.z, v.w};
+    }
+    const float m = norm2(c[k]);
+    if (!(m > 0.f) || !isfinite(m)) return false;
+    const float rr = __frcp_rn(m);
+    const cf inv{c[k].x * rr, -c[k].y * rr};
+    const bool me = lane == k;
+    const cf piv = me ? cf{1.f + inv.x, inv.y} : a[k] * inv;
+#pragma unroll
+    for (int i = 0; i < W; ++i)
+      if (i != k) a[i] = a[i] - c[i] * piv;
+    a[k] = me ? inv : piv;
+  }
+  return true;
+}
+
+// Inverse of the W x W slice matrix A held by columns (lane j < W: column j in a).  Slices where
+// every site dephases take gj_cols; the others the pivoted row routine applied to A^T (lane j's
+// column of A is row j of A^T, and row j of (A^T)^-1 is column j of A^-1).  Lanes >= W must hold
+// zeros.  buf: 2 W + 2 complex64 of shared memory, 16-byte aligned.
+template <int W>
+__device__ bool invert_slice(cf (&a)[W], bool all_dephase, cf* buf) {
+  if (all_dephase) return gj_cols<W>(a, buf);
+  const int lane = threadIdx.x & 31;
+  cf ar[2 * W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    ar[j] = a[j];
+    ar[W + j] = cf{(lane < W && lane == j) ? 1.f : 0.f, 0.f};
+  }
+  if (!gj_rows<W>(ar, true, buf)) return false;
+#pragma unroll
+  for (int j = 0; j < W; ++j) a[j] = ar[W + j];
+  return true;
+}
+
+// Column j (lane j < W) of E - H_kk - Sigma_s(k) - x, where x is this lane's column; other lanes
+// get zero columns.
+template <int W>
+__device__ void build_col(cf (&a)[W], double E, double t, double onsite_j, double eta_j,
+                          const cf (&x)[W]) {
+  const int j = threadIdx.x & 31;
+  const cf diag{(float)(E - onsite_j), (float)(0.5 * eta_j)};
   const float tf = (float)t;
 #pragma unroll
-  for (int j = 0; j < MAXW; ++j) {
+  for (int i = 0; i < W; ++i) {
     cf v{0.f, 0.f};
-    if (i < W && j < W) {
+    if (j < W) {
       if (i == j) v = diag;
       if (i - j == 1 || j - i == 1) v.x += tf;
-      v = v - x[j];
+      v = v - x[i];
     }
-    a[j] = v;
-    a[MAXW + j] = cf{(i < W && i == j) ? 1.f : 0.f, 0.f};
+    a[i] = v;
   }
 }
 
@@ -351,37 +414,38 @@ __device__ __forceinline__ void sweep_reg_body(const TaskDesc& d, int dir,
   const double* onsite = wire + d.onsite_off;
   const double* eta = onsite + d.n;
   const float ttf = (float)(d.t * d.t);     // FP32 on the serial path (FP64 is slow here)
-  cf x[MAXW], a[2 * MAXW];
-  lead_col<MAXW>(phig + d.phi_off, sig + d.lead_off, W, x);
+  cf x[MAXW], a[MAXW];
+  lead_col<MAXW>(phig + d.phi_off, sig + d.lead_off, W, x);   // column j of the lead block
   cf* out = dir == 0 ? gL : gR;
-  const int ic = lane < W ? lane : 0;
+  const int jc = lane < W ? lane : 0;
   // the next slice's onsite energy and dephasing are fetched one step ahead
   int k = dir == 0 ? 0 : L - 1;
-  double on_i = onsite[k * W + ic], eta_i = eta[k * W + ic];
+  double on_j = onsite[k * W + jc], eta_j = eta[k * W + jc];
   for (int s = 0; s < L - 1; ++s) {
     k = dir == 0 ? s : L - 1 - s;
-    const double on_cur = on_i, eta_cur = eta_i;
+    const double on_cur = on_j, eta_cur = eta_j;
     if (s + 1 < L - 1) {
       const int kn = dir == 0 ? s + 1 : L - 2 - s;
-      on_i = onsite[kn * W + ic];
-      eta_i = eta[kn * W + ic];
+      on_j = onsite[kn * W + jc];
+      eta_j = eta[kn * W + jc];
     }
-    build_row<MAXW>(a, W, d.E, d.t, on_cur, eta_cur, x);
-    const bool piv = !__all_sync(0xffffffffu, lane >= W || eta_cur > 0.0);
-    if (!gj_rows<MAXW>(a, piv, srow)) {
+    build_col<W>(a, d.E, d.t, on_cur, eta_cur, x);
+    const bool deph = __all_sync(0xffffffffu, lane >= W || eta_cur > 0.0);
+    if (!invert_slice<W>(a, deph, srow)) {
       if (lane == 0) atomicOr(err, ERR_SINGULAR);
       return;
     }
-    // lane i holds row i of g_k: store it and keep t^2 g_k's row i for the next slice
-    cf* dst = out + d.g_off + (uint64_t)k * W * W + (uint64_t)ic * W;
+    // lane j holds column j of g_k: store it (rows i at i W + j, coalesced over the lanes) and
+    // keep t^2 times it as the next slice's column j of x
+    cf* dst = out + d.g_off + (uint64_t)k * W * W + jc;
     bool bad = false;
 #pragma unroll
-    for (int j = 0; j < MAXW; ++j) {
-      if (lane < W && j < W) {
-        dst[j] = a[MAXW + j];
-        bad |= !finite_c(a[MAXW + j]);
+    for (int i = 0; i < W; ++i) {
+      if (lane < W) {
+        dst[(uint64_t)i * W] = a[i];
+        bad |= !finite_c(a[i]);
       }
-      x[j] = cf{ttf * a[MAXW + j].x, ttf * a[MAXW + j].y};
+      x[i] = cf{ttf * a[i].x, ttf * a[i].y};
     }
     if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
   }
@@ -555,8 +619,8 @@ __device__ __forceinline__ void diag_reg_body(const TaskDesc& d, int task, uint3
   const double* eta = onsite + n;
   const double tt = d.t * d.t;
   for (int idx = lane; idx < W * W; idx += 32) phi[idx] = phig[d.phi_off + idx];
-  // this lane's row of left + right (lead block or t^2 g)
-  cf x[MAXW], a[2 * MAXW];
+  // this lane's column of left + right (lead block or t^2 g)
+  cf x[MAXW], a[MAXW];
   const bool lead_l = m0 == 0, lead_r = m0 == L - 1;
   if (lead_l || lead_r) {
     lead_col<MAXW>(phig + d.phi_off, sig + d.lead_off, W, x);
@@ -568,29 +632,29 @@ __device__ __forceinline__ void diag_reg_body(const TaskDesc& d, int task, uint3
 #pragma unroll
     for (int i = 0; i < MAXW; ++i) x[i] = cf{0.f, 0.f};
   }
-  const int ic = lane < W ? lane : 0;
+  const int jc = lane < W ? lane : 0;
   const cf* gl = lead_l ? nullptr : gL + d.g_off + (uint64_t)(m0 - 1) * W * W;
   const cf* gr = lead_r ? nullptr : gR + d.g_off + (uint64_t)(m0 + 1) * W * W;
 #pragma unroll
-  for (int j = 0; j < MAXW; ++j) {
-    if (j < W && lane < W) {
-      if (gl) x[j] = x[j] + (float)tt * gl[ic * W + j];
-      if (gr) x[j] = x[j] + (float)tt * gr[ic * W + j];
+  for (int i = 0; i < MAXW; ++i) {
+    if (lane < W) {
+      if (gl) x[i] = x[i] + (float)tt * gl[i * W + jc];
+      if (gr) x[i] = x[i] + (float)tt * gr[i * W + jc];
     }
   }
-  const double eta_i = eta[m0 * W + ic];
-  build_row<MAXW>(a, W, d.E, d.t, onsite[m0 * W + ic], eta_i, x);
-  const bool piv = !__all_sync(0xffffffffu, lane >= W || eta_i > 0.0);
-  if (!gj_rows<MAXW>(a, piv, srow)) {
+  const double eta_j = eta[m0 * W + jc];
+  build_col<W>(a, d.E, d.t, onsite[m0 * W + jc], eta_j, x);
+  const bool deph = __all_sync(0xffffffffu, lane >= W || eta_j > 0.0);
+  if (!invert_slice<W>(a, deph, srow)) {
     if (lane == 0) atomicOr(err, ERR_SINGULAR);
     return;
   }
   bool bad = false;
 #pragma unroll
-  for (int j = 0; j < MAXW; ++j) {
-    if (lane < W && j < W) {
-      sG[lane * W + j] = a[MAXW + j];
-      bad |= !finite_c(a[MAXW + j]);
+  for (int i = 0; i < MAXW; ++i) {
+    if (lane < W) {
+      sG[i * W + lane] = a[i];
+      bad |= !finite_c(a[i]);
     }
   }
   if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
