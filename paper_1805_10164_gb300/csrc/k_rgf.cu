@@ -926,6 +926,21 @@ __device__ __forceinline__ void chain_cols_body(const TaskDesc& d, int y0, int d
   };
   if (k0 >= 0 && k0 < L) fetch(k0);
   __syncwarp();
+  // this lane's share of each step's weight writes: elements e = lane + 32 i of the (lane l,
+  // entry a) grid, fixed over the steps: their row offset, start slice and staging slot
+  constexpr int kEm = (Y * W * W + 31) / 32;
+  uint32_t em_off[kEm];          // row * K + a (the step adds k W)
+  int em_m0[kEm];                // start slice, or -1 - L (never written) for no column
+  int em_slot[kEm];
+#pragma unroll
+  for (int i = 0; i < kEm; ++i) {
+    const int e = lane + 32 * i;
+    const int l = e / W, a = e - l * W;
+    const int r = e < Y * W * W ? sm.row[l] : -1;
+    em_off[i] = r >= 0 ? (uint32_t)r * (uint32_t)K + (uint32_t)a : 0u;
+    em_m0[i] = r >= 0 ? sm.m0[l] : (dir == 0 ? -1 : 1 << 30);
+    em_slot[i] = l * (W + 1) + a;
+  }
   for (int k = k0; k != k1 && k >= 0 && k < L; k += step) {
     cf* sg = reinterpret_cast<cf*>(sm.g);
 #pragma unroll
@@ -976,12 +991,10 @@ __device__ __forceinline__ void chain_cols_body(const TaskDesc& d, int y0, int d
     }
     __syncwarp();
     // the step's weights: lane l's W entries go to row(l), columns k W .. k W + W - 1
-    for (int e = lane; e < Y * W * W; e += 32) {
-      const int l = e / W, a = e - l * W;
-      const int r = sm.row[l];
-      const int ml = sm.m0[l];
-      const bool al = r >= 0 && (dir == 0 ? k <= ml : k > ml);
-      if (al) wrow[(uint64_t)r * K + k * W + a] = sm.stage[l * (W + 1) + a];
+#pragma unroll
+    for (int i = 0; i < kEm; ++i) {
+      const bool al = dir == 0 ? k <= em_m0[i] : k > em_m0[i];
+      if (al) wrow[(uint64_t)em_off[i] + (uint32_t)(k * W)] = sm.stage[em_slot[i]];
     }
     __syncwarp();
   }
@@ -994,15 +1007,15 @@ struct ChainCols {
 };
 
 // Jobs as chain_kernel's, (task, y, dir); only those with y a multiple of 32 / W work, each for
-// 32 / W consecutive block columns.
-__global__ void __launch_bounds__(256) chain_cols_kernel(
+// 32 / W consecutive block columns.  One warp per CTA, so that the jobs that do no work free
+// their slot at once.
+__global__ void __launch_bounds__(32) chain_cols_kernel(
     const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
     const float* __restrict__ eta_all, const float* __restrict__ phig,
     const double* __restrict__ gam, const cf* __restrict__ gL, const cf* __restrict__ gR,
     const cf* __restrict__ start, float* __restrict__ weights) {
-  __shared__ ChainColsSmem s_cc[8];
-  const int warp = threadIdx.x >> 5;
-  const uint32_t job = blockIdx.x * (blockDim.x >> 5) + warp;
+  __shared__ ChainColsSmem s_cc;
+  const uint32_t job = blockIdx.x;
   if (job >= n_jobs) return;
   const int task = find_task(n_tasks, job, [&](int t) { return 2 * tasks[t].col_base; });
   const TaskDesc d = tasks[task];
@@ -1010,7 +1023,7 @@ __global__ void __launch_bounds__(256) chain_cols_kernel(
   const uint32_t local = job - 2 * d.col_base;
   const int y = (int)(local >> 1), dir = (int)(local & 1);
   if (d.W < 1 || d.W > 16 || y % (32 / d.W) != 0) return;
-  by_width<ChainCols>(d.W, d, y, dir, eta_all, phig, gam, gL, gR, start, weights, &s_cc[warp]);
+  by_width<ChainCols>(d.W, d, y, dir, eta_all, phig, gam, gL, gR, start, weights, &s_cc);
 }
 
 int warps_for(size_t per_warp, int max_warps) {
@@ -1106,7 +1119,7 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
   }
   const uint32_t jobs = 2 * n_cols;
   if (sizeof(C) == sizeof(cf) && max_W <= 16 && d_green == nullptr) {
-    chain_cols_kernel<<<(jobs + 7) / 8, 256, 0, s>>>(
+    chain_cols_kernel<<<jobs, 32, 0, s>>>(
         d_tasks, n_tasks, jobs, reinterpret_cast<const float*>(d_eta),
         reinterpret_cast<const float*>(d_phiR), d_gam, reinterpret_cast<const cf*>(d_gL),
         reinterpret_cast<const cf*>(d_gR), reinterpret_cast<const cf*>(d_start),
