@@ -174,51 +174,169 @@ __host__ __device__ inline size_t inv_warp_bytes(int W) {
   return sizeof(C) * (size_t)(3 * W * W + W) + sizeof(double) * (size_t)(W * W);
 }
 
-// One warp per (task, direction): direction 0 = left sweep g^L_0..g^L_{L-2} (Sigma_L at slice
-// 0); direction 1 = right sweep g^R_{L-1}..g^R_1 (Sigma_R at slice L-1).
+// ---- CTA-wide sweep (any W <= 64; complex128, and complex64 above W = 16) ------------------
+// One CTA of kSweepThreads threads per (task, direction); the slice block sits in shared memory
+// and is inverted in place by Gauss-Jordan (no augmented identity):
+//   pivot k:  a_kk <- 1/a_kk;  a_kj <- a_kj / a_kk;  a_ik <- -a_ik / a_kk;
+//             a_ij <- a_ij - (a_ik / a_kk) a_kj            (i, j != k)
+// with two barriers per pivot: the pivot row and the multipliers a_ik / a_kk are copied out,
+// then every thread updates its entries.  Thread t owns column t mod W of rows t / W, t / W + R,
+// ... (R = kSweepThreads / W), so that a warp touches consecutive entries of one row.  On a
+// slice where every site dephases no pivot search is needed (see gj_rows); otherwise rows are
+// interchanged by partial pivoting and the inverse's columns unscrambled at the end.  The next
+// slice's matrix E - H - Sigma_s - t^2 g_k is built in place while g_k is stored.
+constexpr int kSweepThreads = 256;
+
 template <typename C>
-__global__ void rgf_sweep_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, int max_W,
-                                 const double* __restrict__ wire, const double* __restrict__ phig,
-                                 const cd* __restrict__ sig, C* gL, C* gR, int32_t* err) {
+__host__ __device__ inline size_t sweep_cta_bytes(int W) {
+  // A W x W | pivot row W | multipliers W (complex) | phi W x W double | perm W, flag (int)
+  return sizeof(C) * (size_t)(W * W + 2 * W) + sizeof(double) * (size_t)(W * W) +
+         sizeof(int) * (size_t)(W + 2);
+}
+
+// E - H_kk - Sigma_s(k) entry (a, b) of slice k, in the precision of C
+template <typename C>
+__device__ __forceinline__ C slice_entry(int a, int b, int k, int W, double E, double t,
+                                         const double* onsite, const double* eta) {
+  using R = typename Real<C>::T;
+  C v = mkc(a == b ? E - onsite[k * W + a] : 0.0, a == b ? 0.5 * eta[k * W + a] : 0.0, C{});
+  if (a - b == 1 || b - a == 1) v.x += (R)t;
+  return v;
+}
+
+// In-place inverse of A (W x W, shared memory) by the whole CTA; false (uniformly) on a zero or
+// non-finite pivot.
+template <typename C>
+__device__ bool cta_gj(C* A, C* rowk, C* fcol, int* perm, int* flag, int W, bool pivot) {
+  using R = typename Real<C>::T;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int R_ = nth / W;                          // row groups
+  const int j = tid % W, rg = tid / W;             // this thread's column and row group
+  const bool own = rg < R_;
+  for (int k = 0; k < W; ++k) {
+    if (pivot) {
+      if (tid < 32) {
+        R best = -1;
+        int bi = k;
+        for (int i = k + tid; i < W; i += 32) {
+          const R v = norm2(A[i * W + k]);
+          if (v > best) { best = v; bi = i; }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+          const R ov = __shfl_xor_sync(0xffffffffu, best, off);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, off);
+          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (tid == 0) {
+          flag[0] = (best > 0 && isfinite(best)) ? bi : -1;
+          perm[k] = bi;
+        }
+      }
+      __syncthreads();
+      const int p = flag[0];
+      if (p < 0) return false;
+      if (p != k) {
+        for (int c = tid; c < W; c += nth) {
+          const C tmp = A[k * W + c];
+          A[k * W + c] = A[p * W + c];
+          A[p * W + c] = tmp;
+        }
+      }
+      __syncthreads();
+    }
+    const C piv = A[k * W + k];
+    const R m = norm2(piv);
+    if (!(m > 0) || !isfinite(m)) return false;    // every thread reads the same value
+    const C inv = cdiv(mkc(1.0, 0.0, C{}), piv);
+    for (int c = tid; c < 2 * W; c += nth) {
+      if (c < W) rowk[c] = A[k * W + c];
+      else fcol[c - W] = A[(c - W) * W + k] * inv;
+    }
+    __syncthreads();
+    if (own) {
+      const C rj = rowk[j];
+      for (int i = rg; i < W; i += R_) {
+        C v;
+        if (i == k) v = (j == k) ? inv : rj * inv;
+        else if (j == k) v = mkc(0.0, 0.0, C{}) - fcol[i];
+        else v = A[i * W + j] - fcol[i] * rj;
+        A[i * W + j] = v;
+      }
+    }
+    __syncthreads();
+  }
+  if (pivot) {
+    for (int k = W - 1; k >= 0; --k) {
+      const int p = perm[k];
+      if (p != k) {
+        for (int i = tid; i < W; i += nth) {
+          const C tmp = A[i * W + k];
+          A[i * W + k] = A[i * W + p];
+          A[i * W + p] = tmp;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  return true;
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kSweepThreads) rgf_sweep_cta_kernel(
+    const TaskDesc* __restrict__ tasks, int n_tasks, const double* __restrict__ wire,
+    const double* __restrict__ phig, const cd* __restrict__ sig, C* gL, C* gR, int32_t* err) {
+  using R = typename Real<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int job = blockIdx.x * (blockDim.x >> 5) + warp;
+  const int job = blockIdx.x;
   if (job >= 2 * n_tasks) return;
   const TaskDesc d = tasks[job >> 1];
   const int dir = job & 1;
-  const int W = d.W, L = d.L, W2 = 2 * W;
-  unsigned char* base = smem_raw + (size_t)warp * inv_warp_bytes<C>(max_W);
-  C* aug = reinterpret_cast<C*>(base);
-  C* lblk = aug + W * W2;          // lead block, then the previous connected block
-  C* fcol = lblk + W * W;
+  const int W = d.W, L = d.L, WW = W * W;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (L < 2 || W > 64) return;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* rowk = A + WW;
+  C* fcol = rowk + W;
   double* phi = reinterpret_cast<double*>(fcol + W);
+  int* perm = reinterpret_cast<int*>(phi + WW);
+  int* flag = perm + W;
   const double* onsite = wire + d.onsite_off;
   const double* eta = onsite + d.n;
-  if (L < 2) return;
-  for (int idx = lane; idx < W * W; idx += 32) phi[idx] = phig[d.phi_off + idx];
-  __syncwarp();
-  lead_block(phi, sig + d.lead_off, W, lblk);
-  __syncwarp();
+  const cd* sg = sig + d.lead_off;
+  for (int idx = tid; idx < WW; idx += nth) phi[idx] = phig[d.phi_off + idx];
+  __syncthreads();
+  // first slice of the sweep: E - H - Sigma_s - Phi diag(sigma) Phi^T (the lead block in FP64)
+  const int kf = dir == 0 ? 0 : L - 1;
+  for (int idx = tid; idx < WW; idx += nth) {
+    const int a = idx / W, b = idx - a * W;
+    cd acc = mk(0.0, 0.0);
+    for (int m = 0; m < W; ++m) acc = acc + (phi[a * W + m] * phi[b * W + m]) * sg[m];
+    A[idx] = slice_entry<C>(a, b, kf, W, d.E, d.t, onsite, eta) - to_c(acc, C{});
+  }
   C* out = dir == 0 ? gL : gR;
+  const R tt = (R)(d.t * d.t);
   for (int s = 0; s < L - 1; ++s) {
     const int k = dir == 0 ? s : L - 1 - s;
-    build_slice(aug, W, d.E, d.t, onsite, eta, k, lblk, s == 0 ? 1.0 : d.t * d.t,
-                (const C*)nullptr, 0.0);
-    __syncwarp();
-    if (!warp_gj(aug, W, fcol)) {
-      if (lane == 0) atomicOr(err, ERR_SINGULAR);
+    const bool deph = __syncthreads_and(tid >= W || eta[k * W + tid] > 0.0);
+    if (!cta_gj(A, rowk, fcol, perm, flag, W, !deph)) {
+      if (tid == 0) atomicOr(err, ERR_SINGULAR);
       return;
     }
-    C* dst = out + d.g_off + (uint64_t)k * W * W;
+    // store g_k; build the next slice in place: E - H - Sigma_s - t^2 g_k
+    C* dst = out + d.g_off + (uint64_t)k * WW;
+    const bool more = s + 1 < L - 1;
+    const int kn = dir == 0 ? s + 1 : L - 2 - s;
     bool bad = false;
-    for (int idx = lane; idx < W * W; idx += 32) {
-      const C v = aug[(idx / W) * W2 + W + idx % W];
-      lblk[idx] = v;
+    for (int idx = tid; idx < WW; idx += nth) {
+      const C v = A[idx];
       dst[idx] = v;
       bad |= !finite_c(v);
+      if (more) {
+        const int a = idx / W, b = idx - a * W;
+        A[idx] = slice_entry<C>(a, b, kn, W, d.E, d.t, onsite, eta) - tt * v;
+      }
     }
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
-    __syncwarp();
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(err, ERR_NONFINITE);
   }
 }
 
@@ -1055,13 +1173,14 @@ template <typename C>
 cudaError_t sweep_smem(const TaskDesc* d_tasks, int n_tasks, int max_W, const double* d_wire,
                        const double* d_phi, const cd* d_sig, C* d_gL, C* d_gR, int32_t* d_err,
                        cudaStream_t s) {
-  // one warp per CTA: each sweep is a serial chain, best spread one per SM
-  const size_t smem = inv_warp_bytes<C>(max_W);
-  cudaError_t e = cudaFuncSetAttribute(rgf_sweep_kernel<C>,
+  // one CTA per sweep: each sweep is a serial chain of W x W inversions, spread one per SM
+  const size_t smem = sweep_cta_bytes<C>(max_W);
+  cudaError_t e = cudaFuncSetAttribute(rgf_sweep_cta_kernel<C>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  rgf_sweep_kernel<C><<<2 * n_tasks, 32, smem, s>>>(d_tasks, n_tasks, max_W, d_wire, d_phi,
-                                                    d_sig, d_gL, d_gR, d_err);
+  rgf_sweep_cta_kernel<C><<<2 * n_tasks, kSweepThreads, smem, s>>>(d_tasks, n_tasks, d_wire,
+                                                                   d_phi, d_sig, d_gL, d_gR,
+                                                                   d_err);
   return cudaGetLastError();
 }
 
