@@ -5,22 +5,23 @@
 // row needs is produced once per (wire, energy) task:
 //   * lead_modes_kernel   - eigen self-energies Sigma_m and Gamma_m of the lead strips
 //                           (Sec. II.A lead self-energies; Sec. III.A model)
-//   * rgf_sweep_kernel    - left- and right-connected blocks g^L_k, g^R_k (one warp per task
-//                           and direction; the sweep is a chain of W x W inversions)
-//   * diag_kernel         - per slice m: G_mm by one more inversion (one warp each); for the
-//                           boundary slices also G Phi, the A of every row (for the sum-rule
-//                           check), the mode weights of Eq. lead_out_probability and
-//                           c_p = Tr[Gamma_p A] (Eq. elast_lin_xpq)
-//   * chain_kernel        - per slice m and direction, the block column
-//                           G_{k,m} = -t g^L_k G_{k+1,m} (k < m), -t g^R_k G_{k-1,m} (k > m)
-//                           (one warp each), emitted directly as Step 6' weights
-//                           (Eq. draw_i_simult and the lead probability of Step 6'); the two
-//                           injection columns propagate G Phi for the rows of Steps 4-5.
-// W x W block inversions are Gauss-Jordan with partial pivoting in shared memory, one warp per
-// matrix (no block-wide barriers on the latency-bound chains), lanes owning columns.  All of
-// it runs in the precision of the tables: complex128 for NEGF_FP64, complex64 for NEGF_FP32;
-// the lead self-energies, whose square roots are singular at the sub-band edges, are FP64 in
-// both and rounded once.
+//   * rgf_sweep_*_kernel  - left- and right-connected blocks g^L_k, g^R_k (one warp per task
+//                           and direction in registers for complex64 W <= 16, one CTA
+//                           otherwise; the sweep is a serial chain of W x W inversions)
+//   * diag_*_kernel       - per slice m: G_mm by one more inversion; for the boundary slices
+//                           also G Phi, the A of every row (for the sum-rule check), the mode
+//                           weights of Eq. lead_out_probability and c_p = Tr[Gamma_p A]
+//                           (Eq. elast_lin_xpq)
+//   * chain_*_kernel      - per slice m and direction, the block column
+//                           G_{k,m} = -t g^L_k G_{k+1,m} (k < m), -t g^R_k G_{k-1,m} (k > m),
+//                           emitted directly as Step 6' weights (Eq. draw_i_simult and the lead
+//                           probability of Step 6'); the two injection columns propagate G Phi
+//                           for the rows of Steps 4-5.
+// W x W block inversions are Gauss-Jordan: in registers by one warp for complex64 W <= 16, in
+// shared memory by one CTA otherwise; partial pivoting except on slices where every site
+// dephases (see gj_rows).  All of it runs in the precision of the tables: complex128 for
+// NEGF_FP64, complex64 for NEGF_FP32; the lead self-energies, whose square roots are singular
+// at the sub-band edges, are FP64 in both and rounded once.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -43,86 +44,6 @@ __device__ __forceinline__ bool finite_c(cf v) { return isfinite(v.x) && isfinit
 // Sine mode phi_m(a) of a W-site cross-section, m, a in [0, W).
 __device__ __forceinline__ double phi_mode(int a, int m, int W) {
   return sqrt(2.0 / (W + 1)) * sinpi((double)((m + 1) * (a + 1)) / (double)(W + 1));
-}
-
-// Gauss-Jordan inversion of the W x W left half of aug [W][2W] by one warp (right half holds
-// I on entry, the inverse on exit).  Partial pivoting by |a_ik|^2, lowest index on ties.
-// Lanes own columns of the pivot-row update, so each lane's W row updates are independent.
-// Returns false (uniformly across the warp) on an exactly zero or non-finite pivot column.
-template <typename C>
-__device__ bool warp_gj(C* aug, int W, C* fcol) {
-  using R = typename Real<C>::T;
-  const int W2 = 2 * W, lane = threadIdx.x & 31;
-  const unsigned FULL = 0xffffffffu;
-  for (int k = 0; k < W; ++k) {
-    R best = -1;
-    int bi = k;
-    for (int i = k + lane; i < W; i += 32) {
-      const R v = norm2(aug[i * W2 + k]);
-      if (v > best) { best = v; bi = i; }
-    }
-    for (int off = 16; off > 0; off >>= 1) {
-      const R ov = __shfl_xor_sync(FULL, best, off);
-      const int oi = __shfl_xor_sync(FULL, bi, off);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-    }
-    if (!(best > 0) || !isfinite(best)) return false;
-    if (bi != k) {
-      for (int j = k + lane; j < W2; j += 32) {
-        const C tmp = aug[k * W2 + j];
-        aug[k * W2 + j] = aug[bi * W2 + j];
-        aug[bi * W2 + j] = tmp;
-      }
-    }
-    __syncwarp();
-    const C inv = cdiv(mkc(1.0, 0.0, C{}), aug[k * W2 + k]);
-    for (int i = lane; i < W; i += 32) fcol[i] = aug[i * W2 + k];
-    __syncwarp();
-    for (int j = k + lane; j < W2; j += 32) {
-      const C pk = aug[k * W2 + j] * inv;
-      aug[k * W2 + j] = pk;
-#pragma unroll 4
-      for (int i = 0; i < W; ++i)
-        if (i != k) aug[i * W2 + j] = aug[i * W2 + j] - fcol[i] * pk;
-    }
-    __syncwarp();
-  }
-  return true;
-}
-
-// Boundary self-energy block Phi diag(sig) Phi^T of one lead into out [W][W] (one warp).
-template <typename C>
-__device__ void lead_block(const double* phi, const cd* sig, int W, C* out) {
-  for (int idx = threadIdx.x & 31; idx < W * W; idx += 32) {
-    const int a = idx / W, b = idx % W;
-    cd acc = mk(0.0, 0.0);
-    for (int m = 0; m < W; ++m) acc = acc + (phi[a * W + m] * phi[b * W + m]) * sig[m];
-    out[idx] = to_c(acc, C{});
-  }
-}
-
-// aug <- [E - H_kk - Sigma_s(k) - f1 x1 - f2 x2 | I] (one warp); x1/x2 are the lead block
-// (factor 1) or a connected block g (factor t^2), or null.
-template <typename C>
-__device__ void build_slice(C* aug, int W, double E, double t, const double* onsite,
-                            const double* eta, int k, const C* x1, double f1, const C* x2,
-                            double f2) {
-  using R = typename Real<C>::T;
-  const int W2 = 2 * W;
-  for (int idx = threadIdx.x & 31; idx < W * W2; idx += 32) {
-    const int a = idx / W2, j = idx % W2;
-    C v;
-    if (j < W) {
-      const int b = j;
-      v = mkc(a == b ? E - onsite[k * W + a] : 0.0, a == b ? 0.5 * eta[k * W + a] : 0.0, C{});
-      if (a - b == 1 || b - a == 1) v.x += (R)t;
-      if (x1) v = v - (R)f1 * x1[a * W + b];
-      if (x2) v = v - (R)f2 * x2[a * W + b];
-    } else {
-      v = mkc((j - W) == a ? 1.0 : 0.0, 0.0, C{});
-    }
-    aug[idx] = v;
-  }
 }
 
 __global__ void lead_modes_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
@@ -165,13 +86,6 @@ __global__ void lead_modes_kernel(const TaskDesc* __restrict__ tasks, int n_task
     sig[d.lead_off + m] = s;
     gam[d.lead_off + m] = g;
   }
-}
-
-// per-warp shared memory of the inversion kernels (FP64, W = 64: 225 KB)
-template <typename C>
-__host__ __device__ inline size_t inv_warp_bytes(int W) {
-  // aug W x 2W | lblk W x W | fcol W  (complex)  | phi W x W double
-  return sizeof(C) * (size_t)(3 * W * W + W) + sizeof(double) * (size_t)(W * W);
 }
 
 // ---- CTA-wide sweep (any W <= 64; complex128, and complex64 above W = 16) ------------------
@@ -623,88 +537,108 @@ __device__ __forceinline__ int find_task(int n_tasks, uint32_t job, F first) {
   return lo;
 }
 
-// One warp per (task, y): y in [0, L) site column m = y, y = L / L+1 injection columns of lead
-// L / R.  Computes G_mm, the start block S = G_mm or G_mm Phi, A of its W rows, and for
-// injection columns the mode weights and c_p.  A is stored where the row sums will go; the
-// alias build checks each row's sum against it and then overwrites it.
+// CTA-wide diagonal blocks (any W <= 64): one CTA of kSweepThreads threads per (task, y); same
+// outputs as diag_kernel, with the inversion of cta_gj.
 template <typename C>
-__global__ void diag_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
-                            int max_W, const double* __restrict__ wire,
-                            const double* __restrict__ phig, const cd* __restrict__ sig,
-                            const double* __restrict__ gam, const C* __restrict__ gL,
-                            const C* __restrict__ gR, C* __restrict__ start,
-                            double* __restrict__ rowsum, double* __restrict__ mode_w,
-                            double* __restrict__ cvals, int32_t* err) {
+__host__ __device__ inline size_t diag_cta_bytes(int W) {
+  // A, S (lead block, then start block) W x W | pivot row, multipliers W (complex) | phi W x W
+  // double | mode weights W double | perm W, flag (int)
+  return sizeof(C) * (size_t)(2 * W * W + 2 * W) + sizeof(double) * (size_t)(W * W + W) +
+         sizeof(int) * (size_t)(W + 2);
+}
+
+template <typename C>
+__global__ void __launch_bounds__(kSweepThreads) diag_cta_kernel(
+    const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
+    const double* __restrict__ wire, const double* __restrict__ phig, const cd* __restrict__ sig,
+    const double* __restrict__ gam, const C* __restrict__ gL, const C* __restrict__ gR,
+    C* __restrict__ start, double* __restrict__ rowsum, double* __restrict__ mode_w,
+    double* __restrict__ cvals, int32_t* err) {
   using R = typename Real<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t job = blockIdx.x * (blockDim.x >> 5) + warp;
+  const uint32_t job = blockIdx.x;
   if (job >= n_jobs) return;
   const int task = find_task(n_tasks, job, [&](int t) { return tasks[t].col_base; });
   const TaskDesc d = tasks[task];
-  const int W = d.W, L = d.L, n = d.n, W2 = 2 * W;
+  const int W = d.W, L = d.L, n = d.n, WW = W * W;
+  if (W > 64) return;
+  const int tid = threadIdx.x, nth = blockDim.x;
   const int y = (int)(job - d.col_base);
   const bool inj = y >= L;
   const int p = y - L;
   const int m0 = inj ? (p == 0 ? 0 : L - 1) : y;
-  unsigned char* base = smem_raw + (size_t)warp * inv_warp_bytes<C>(max_W);
-  C* aug = reinterpret_cast<C*>(base);
-  C* lblk = aug + W * W2;             // lead block, then the start block
-  C* fcol = lblk + W * W;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* S = A + WW;
+  C* rowk = S + WW;
+  C* fcol = rowk + W;
   double* phi = reinterpret_cast<double*>(fcol + W);
+  double* mw_s = phi + WW;
+  int* perm = reinterpret_cast<int*>(mw_s + W);
+  int* flag = perm + W;
   const double* onsite = wire + d.onsite_off;
   const double* eta = onsite + n;
-  const double t = d.t;
-  for (int idx = lane; idx < W * W; idx += 32) phi[idx] = phig[d.phi_off + idx];
-  __syncwarp();
-  if (m0 == 0 || m0 == L - 1) lead_block(phi, sig + d.lead_off, W, lblk);
-  __syncwarp();
-  const C* left = m0 == 0 ? lblk : gL + d.g_off + (uint64_t)(m0 - 1) * W * W;
-  const C* right = m0 == L - 1 ? lblk : gR + d.g_off + (uint64_t)(m0 + 1) * W * W;
-  build_slice(aug, W, d.E, t, onsite, eta, m0, left, m0 == 0 ? 1.0 : t * t, right,
-              m0 == L - 1 ? 1.0 : t * t);
-  __syncwarp();
-  if (!warp_gj(aug, W, fcol)) {
-    if (lane == 0) atomicOr(err, ERR_SINGULAR);
+  const R tt = (R)(d.t * d.t);
+  const bool lead_l = m0 == 0, lead_r = m0 == L - 1;
+  for (int idx = tid; idx < WW; idx += nth) phi[idx] = phig[d.phi_off + idx];
+  __syncthreads();
+  if (lead_l || lead_r) {
+    const cd* sg = sig + d.lead_off;
+    for (int idx = tid; idx < WW; idx += nth) {
+      const int a = idx / W, b = idx - a * W;
+      cd acc = mk(0.0, 0.0);
+      for (int m = 0; m < W; ++m) acc = acc + (phi[a * W + m] * phi[b * W + m]) * sg[m];
+      S[idx] = to_c(acc, C{});
+    }
+  }
+  __syncthreads();
+  // A = E - H - Sigma_s - (lead block or t^2 g^L_{m-1}) - (lead block or t^2 g^R_{m+1})
+  const C* gl = lead_l ? nullptr : gL + d.g_off + (uint64_t)(m0 - 1) * WW;
+  const C* gr = lead_r ? nullptr : gR + d.g_off + (uint64_t)(m0 + 1) * WW;
+  for (int idx = tid; idx < WW; idx += nth) {
+    const int a = idx / W, b = idx - a * W;
+    C v = slice_entry<C>(a, b, m0, W, d.E, d.t, onsite, eta);
+    v = v - (gl ? tt * gl[idx] : S[idx]);
+    v = v - (gr ? tt * gr[idx] : S[idx]);
+    A[idx] = v;
+  }
+  const bool deph = __syncthreads_and(tid >= W || eta[m0 * W + tid] > 0.0);
+  if (!cta_gj(A, rowk, fcol, perm, flag, W, !deph)) {
+    if (tid == 0) atomicOr(err, ERR_SINGULAR);
     return;
   }
-  C* dst = start + d.start_off + (uint64_t)y * W * W;
-  C* sblk = lblk;                     // the lead block is no longer needed
+  // start block: G_mm, or G_mm Phi for the injection columns
+  C* dst = start + d.start_off + (uint64_t)y * WW;
   bool bad = false;
-  for (int idx = lane; idx < W * W; idx += 32) {
-    const int a = idx / W, b = idx % W;
+  for (int idx = tid; idx < WW; idx += nth) {
     C v;
     if (!inj) {
-      v = aug[a * W2 + W + b];
+      v = A[idx];
     } else {
+      const int a = idx / W, b = idx - a * W;
       v = mkc(0.0, 0.0, C{});
-      for (int c = 0; c < W; ++c) v = v + (R)phi[c * W + b] * aug[a * W2 + W + c];
+      for (int c = 0; c < W; ++c) v = v + (R)phi[c * W + b] * A[a * W + c];
     }
-    sblk[idx] = v;
+    S[idx] = v;
     dst[idx] = v;
     bad |= !finite_c(v);
   }
-  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
-  __syncwarp();
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(err, ERR_NONFINITE);
   // A per row: site b: -2 Im G_bb;  mode mu: -2 Im (Phi^T G Phi)_{mu mu}
-  double* mw_s = reinterpret_cast<double*>(aug);      // aug is dead
-  for (int b = lane; b < W; b += 32) {
-    double A;
+  for (int b = tid; b < W; b += nth) {
     if (!inj) {
-      A = -2.0 * (double)sblk[b * W + b].y;
-      rowsum[d.row_base + m0 * W + b] = A;
+      rowsum[d.row_base + m0 * W + b] = -2.0 * (double)S[b * W + b].y;
     } else {
       double im = 0.0;
-      for (int a = 0; a < W; ++a) im += phi[a * W + b] * (double)sblk[a * W + b].y;
-      A = -2.0 * im;
-      rowsum[d.row_base + n + p * W + b] = A;
-      const double mw = gam[d.lead_off + b] * A;
+      for (int a = 0; a < W; ++a) im += phi[a * W + b] * (double)S[a * W + b].y;
+      const double Ab = -2.0 * im;
+      rowsum[d.row_base + n + p * W + b] = Ab;
+      const double mw = gam[d.lead_off + b] * Ab;
       mode_w[d.mode_off + p * W + b] = mw;
       mw_s[b] = mw;
     }
   }
-  __syncwarp();
-  if (inj && lane == 0) {
+  __syncthreads();
+  if (inj && tid == 0) {
     double c = 0.0;
     for (int b = 0; b < W; ++b) c += mw_s[b];      // fixed order
     cvals[task * 2 + p] = c;
@@ -1224,15 +1158,13 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   } else {
-    const size_t per = inv_warp_bytes<C>(max_W);
-    const int warps = warps_for(per, 4);
-    const size_t smem = per * warps;
-    cudaError_t e = cudaFuncSetAttribute(diag_kernel<C>,
+    const size_t smem = diag_cta_bytes<C>(max_W);
+    cudaError_t e = cudaFuncSetAttribute(diag_cta_kernel<C>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    diag_kernel<C><<<(n_cols + warps - 1) / warps, 32 * warps, smem, s>>>(
-        d_tasks, n_tasks, n_cols, max_W, d_wire, d_phi, d_sig, d_gam, d_gL, d_gR, d_start,
-        d_rowsum, d_mode_w, d_c, d_err);
+    diag_cta_kernel<C><<<n_cols, kSweepThreads, smem, s>>>(
+        d_tasks, n_tasks, n_cols, d_wire, d_phi, d_sig, d_gam, d_gL, d_gR, d_start, d_rowsum,
+        d_mode_w, d_c, d_err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
