@@ -89,17 +89,18 @@ __global__ void lead_modes_kernel(const TaskDesc* __restrict__ tasks, int n_task
 }
 
 // ---- CTA-wide sweep (any W <= 64; complex128, and complex64 above W = 16) ------------------
-// One CTA of kSweepThreads threads per (task, direction); the slice block sits in shared memory
+// One CTA of kSweepCtaThreads threads per (task, direction); the slice block sits in shared memory
 // and is inverted in place by Gauss-Jordan (no augmented identity):
 //   pivot k:  a_kk <- 1/a_kk;  a_kj <- a_kj / a_kk;  a_ik <- -a_ik / a_kk;
 //             a_ij <- a_ij - (a_ik / a_kk) a_kj            (i, j != k)
 // with two barriers per pivot: the pivot row and the multipliers a_ik / a_kk are copied out,
 // then every thread updates its entries.  Thread t owns column t mod W of rows t / W, t / W + R,
-// ... (R = kSweepThreads / W), so that a warp touches consecutive entries of one row.  On a
+// ... (R = threads / W), so that a warp touches consecutive entries of one row.  On a
 // slice where every site dephases no pivot search is needed (see gj_rows); otherwise rows are
 // interchanged by partial pivoting and the inverse's columns unscrambled at the end.  The next
 // slice's matrix E - H - Sigma_s - t^2 g_k is built in place while g_k is stored.
-constexpr int kSweepThreads = 256;
+constexpr int kSweepThreads = 256;       // diagonal blocks: many CTAs
+constexpr int kSweepCtaThreads = 1024;   // sweeps: few serial chains, so each gets a whole SM
 
 template <typename C>
 __host__ __device__ inline size_t sweep_cta_bytes(int W) {
@@ -196,7 +197,7 @@ __device__ bool cta_gj(C* A, C* rowk, C* fcol, int* perm, int* flag, int W, bool
 }
 
 template <typename C>
-__global__ void __launch_bounds__(kSweepThreads) rgf_sweep_cta_kernel(
+__global__ void __launch_bounds__(kSweepCtaThreads) rgf_sweep_cta_kernel(
     const TaskDesc* __restrict__ tasks, int n_tasks, const double* __restrict__ wire,
     const double* __restrict__ phig, const cd* __restrict__ sig, C* gL, C* gR, int32_t* err) {
   using R = typename Real<C>::T;
@@ -1112,7 +1113,7 @@ cudaError_t sweep_smem(const TaskDesc* d_tasks, int n_tasks, int max_W, const do
   cudaError_t e = cudaFuncSetAttribute(rgf_sweep_cta_kernel<C>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  rgf_sweep_cta_kernel<C><<<2 * n_tasks, kSweepThreads, smem, s>>>(d_tasks, n_tasks, d_wire,
+  rgf_sweep_cta_kernel<C><<<2 * n_tasks, kSweepCtaThreads, smem, s>>>(d_tasks, n_tasks, d_wire,
                                                                    d_phi, d_sig, d_gL, d_gR,
                                                                    d_err);
   return cudaGetLastError();
