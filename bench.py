@@ -45,6 +45,8 @@ def workload(name, energies=0):
         wl = inputs.wire_64x100()
     elif name == "wire_64x1000":
         wl = inputs.wire_64x1000()
+    elif name == "batched_uneven":
+        wl = inputs.batched_uneven()
     else:
         raise SystemExit(f"unknown workload {name}")
     if energies:
@@ -519,10 +521,13 @@ def main():
     ap.add_argument("--walk-blocks-per-sm", type=int, default=4)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--plan-tasks-per-wave", type=int, default=0,
-                    help="graph mode: tasks per wave (0: all tasks in one wave)")
+                    help="graph mode: tasks per wave (0: all tasks in one wave, or 1024 for "
+                         "the batched workload, whose 8192 tasks' tables need 548 GB)")
     ap.add_argument("--energies", type=int, default=0,
                     help="use an evenly spread subset of this many grid energies")
     args = ap.parse_args()
+    if args.workload == "batched_uneven" and args.plan_tasks_per_wave == 0:
+        args.plan_tasks_per_wave = 1024
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -199,7 +199,8 @@ __device__ bool cta_gj(C* A, C* rowk, C* fcol, int* perm, int* flag, int W, bool
 template <typename C>
 __global__ void __launch_bounds__(kSweepCtaThreads) rgf_sweep_cta_kernel(
     const TaskDesc* __restrict__ tasks, int n_tasks, const double* __restrict__ wire,
-    const double* __restrict__ phig, const cd* __restrict__ sig, C* gL, C* gR, int32_t* err) {
+    const double* __restrict__ phig, const cd* __restrict__ sig, C* gL, C* gR, int32_t* err,
+    int min_W) {
   using R = typename Real<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int job = blockIdx.x;
@@ -208,7 +209,7 @@ __global__ void __launch_bounds__(kSweepCtaThreads) rgf_sweep_cta_kernel(
   const int dir = job & 1;
   const int W = d.W, L = d.L, WW = W * W;
   const int tid = threadIdx.x, nth = blockDim.x;
-  if (L < 2 || W > 64) return;
+  if (L < 2 || W > 64 || W < min_W) return;       // narrower tasks: rgf_sweep_reg_kernel
   C* A = reinterpret_cast<C*>(smem_raw);
   C* rowk = A + WW;
   C* fcol = rowk + W;
@@ -554,7 +555,7 @@ __global__ void __launch_bounds__(kSweepThreads) diag_cta_kernel(
     const double* __restrict__ wire, const double* __restrict__ phig, const cd* __restrict__ sig,
     const double* __restrict__ gam, const C* __restrict__ gL, const C* __restrict__ gR,
     C* __restrict__ start, double* __restrict__ rowsum, double* __restrict__ mode_w,
-    double* __restrict__ cvals, int32_t* err) {
+    double* __restrict__ cvals, int32_t* err, int min_W) {
   using R = typename Real<C>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const uint32_t job = blockIdx.x;
@@ -562,7 +563,7 @@ __global__ void __launch_bounds__(kSweepThreads) diag_cta_kernel(
   const int task = find_task(n_tasks, job, [&](int t) { return tasks[t].col_base; });
   const TaskDesc d = tasks[task];
   const int W = d.W, L = d.L, n = d.n, WW = W * W;
-  if (W > 64) return;
+  if (W > 64 || W < min_W) return;                // narrower tasks: diag_reg_kernel
   const int tid = threadIdx.x, nth = blockDim.x;
   const int y = (int)(job - d.col_base);
   const bool inj = y >= L;
@@ -903,182 +904,6 @@ __global__ void chain_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
   }
 }
 
-// ---- block columns with one column per lane (complex64, W <= 16, no gradient outputs) ------
-// The warp of job (task, y0, dir) with y0 a multiple of Y = 32 / W carries the Y W columns
-// (y, b), y0 <= y < y0 + Y, b < W, of the task's block columns (y < L: site slice y; y = L, L + 1:
-// G Phi of the left / right lead), lane Y-major: lane = (y - y0) W + b.  Each lane keeps its
-// column of G_{k, y} in registers; per step the warp stages g_k (and eta of slice k) in shared
-// memory once, every lane forms its next column -t g_k X by broadcast reads, and the step's
-// weights leave through a shared-memory transpose so that each row's W entries are written
-// together.  Same weights as chain_kernel.
-struct ChainColsSmem {
-  float4 g[16 * 8];            // g_k, rows padded to an even number of entries
-  float eta[16];
-  float stage[32 * 17];        // lane l's W weights at l (W + 1)
-  int row[32];                 // weight row of lane l's column, -1 for none
-  int m0[32];                  // start slice of lane l's column
-};
-
-template <int W>
-__device__ __forceinline__ void chain_cols_body(const TaskDesc& d, int y0, int dir,
-                                                const float* __restrict__ eta_all,
-                                                const float* __restrict__ phig,
-                                                const double* __restrict__ gam,
-                                                const cf* __restrict__ gL,
-                                                const cf* __restrict__ gR,
-                                                const cf* __restrict__ start,
-                                                float* __restrict__ weights,
-                                                ChainColsSmem* smp) {
-  ChainColsSmem& sm = *smp;
-  constexpr int Y = 32 / W;
-  constexpr int Wp = (W + 1) & ~1;                 // padded row of g_k in shared memory
-  const int lane = threadIdx.x & 31;
-  const int L = d.L, n = d.n, K = d.K;
-  const int y = y0 + lane / W, b = lane % W;
-  const bool has = lane < Y * W && y < L + 2;
-  const bool inj = y >= L;
-  const int m0 = inj ? (y == L ? 0 : L - 1) : y;
-  const bool live = has && !(dir == 1 && m0 == L - 1);
-  sm.row[lane] = live ? (inj ? n + (y - L) * W : m0 * W) + b : -1;
-  sm.m0[lane] = m0;
-  // this lane's column of the start block: X[a] = start[y][a][b]
-  cf X[W];
-#pragma unroll
-  for (int a = 0; a < W; ++a)
-    X[a] = live ? start[d.start_off + ((uint64_t)y * W + a) * W + b] : cf{0.f, 0.f};
-  const float* eta = eta_all + d.onsite_off / 2;      // FP32 copy of eta
-  float* wrow = weights + d.wt_off;
-  const float mt = (float)(-d.t);
-  const cf* gsrc = dir == 0 ? gL : gR;
-  // steps: dir 0 from the largest start slice down to 0 (a lane emits its start block at k = m0
-  // and propagates below it); dir 1 from the smallest start slice + 1 up to L - 1
-  const unsigned FULL = 0xffffffffu;
-  if (!__any_sync(FULL, live)) return;
-  int k0, k1, step;
-  if (dir == 0) {
-    k0 = (int)__reduce_max_sync(FULL, live ? (unsigned)m0 : 0u);
-    k1 = -1;
-    step = -1;
-  } else {
-    k0 = (int)__reduce_min_sync(FULL, live ? (unsigned)m0 : 0x7fffffffu) + 1;
-    k1 = L;
-    step = 1;
-  }
-  // g_k and eta of slice k are fetched into registers one step ahead
-  constexpr int kPre = (W * W + 31) / 32;
-  cf gpre[kPre];
-  float epre = 0.f;
-  auto fetch = [&](int k) {
-    const cf* gk = gsrc + d.g_off + (uint64_t)k * W * W;
-#pragma unroll
-    for (int i = 0; i < kPre; ++i) {
-      const int idx = lane + 32 * i;
-      if (idx < W * W) gpre[i] = gk[idx];
-    }
-    if (lane < W) epre = eta[k * W + lane];
-  };
-  if (k0 >= 0 && k0 < L) fetch(k0);
-  __syncwarp();
-  // this lane's share of each step's weight writes: elements e = lane + 32 i of the (lane l,
-  // entry a) grid, fixed over the steps: their row offset, start slice and staging slot
-  constexpr int kEm = (Y * W * W + 31) / 32;
-  uint32_t em_off[kEm];          // row * K + a (the step adds k W)
-  int em_m0[kEm];                // start slice, or -1 - L (never written) for no column
-  int em_slot[kEm];
-#pragma unroll
-  for (int i = 0; i < kEm; ++i) {
-    const int e = lane + 32 * i;
-    const int l = e / W, a = e - l * W;
-    const int r = e < Y * W * W ? sm.row[l] : -1;
-    em_off[i] = r >= 0 ? (uint32_t)r * (uint32_t)K + (uint32_t)a : 0u;
-    em_m0[i] = r >= 0 ? sm.m0[l] : (dir == 0 ? -1 : 1 << 30);
-    em_slot[i] = l * (W + 1) + a;
-  }
-  for (int k = k0; k != k1 && k >= 0 && k < L; k += step) {
-    cf* sg = reinterpret_cast<cf*>(sm.g);
-#pragma unroll
-    for (int i = 0; i < kPre; ++i) {
-      const int idx = lane + 32 * i;
-      if (idx < W * W) {
-        const int a = idx / W, c = idx - a * W;
-        sg[a * Wp + c] = gpre[i];
-      }
-    }
-    if (lane < W) sm.eta[lane] = epre;
-    if (k + step != k1 && k + step >= 0 && k + step < L) fetch(k + step);
-    __syncwarp();
-    const bool act = live && (dir == 0 ? k <= m0 : k > m0);
-    const bool prop = live && (dir == 0 ? k < m0 : k > m0);
-    if (prop) {
-      cf Xn[W];
-#pragma unroll
-      for (int a = 0; a < W; ++a) {
-        cf acc{0.f, 0.f};
-#pragma unroll
-        for (int q = 0; q < Wp / 2; ++q) {
-          const float4 v = sm.g[(a * Wp) / 2 + q];
-          acc = acc + cf{v.x, v.y} * X[2 * q];
-          if (2 * q + 1 < W) acc = acc + cf{v.z, v.w} * X[2 * q + 1];
-        }
-        Xn[a] = cf{mt * acc.x, mt * acc.y};
-      }
-#pragma unroll
-      for (int a = 0; a < W; ++a) X[a] = Xn[a];
-    }
-    if (act) {
-#pragma unroll
-      for (int a = 0; a < W; ++a) sm.stage[lane * (W + 1) + a] = sm.eta[a] * norm2(X[a]);
-      if (k == 0 || k == L - 1) {
-        // lead weight: sum_nu Gamma_nu |(Phi^T X)_nu|^2
-        float sum = 0.f;
-        for (int nu = 0; nu < W; ++nu) {
-          cf acc{0.f, 0.f};
-#pragma unroll
-          for (int a = 0; a < W; ++a) acc = acc + phig[d.phi_off + a * W + nu] * X[a];
-          sum += (float)gam[d.lead_off + nu] * norm2(acc);
-        }
-        const int r = sm.row[lane];
-        if (k == 0) wrow[(uint64_t)r * K + n + 0] = sum;
-        if (k == L - 1) wrow[(uint64_t)r * K + n + 1] = sum;
-      }
-    }
-    __syncwarp();
-    // the step's weights: lane l's W entries go to row(l), columns k W .. k W + W - 1
-#pragma unroll
-    for (int i = 0; i < kEm; ++i) {
-      const bool al = dir == 0 ? k <= em_m0[i] : k > em_m0[i];
-      if (al) wrow[(uint64_t)em_off[i] + (uint32_t)(k * W)] = sm.stage[em_slot[i]];
-    }
-    __syncwarp();
-  }
-}
-
-template <int W>
-struct ChainCols {
-  template <typename... A>
-  __device__ __forceinline__ static void run(A... a) { chain_cols_body<W>(a...); }
-};
-
-// Jobs as chain_kernel's, (task, y, dir); only those with y a multiple of 32 / W work, each for
-// 32 / W consecutive block columns.  One warp per CTA, so that the jobs that do no work free
-// their slot at once.
-__global__ void __launch_bounds__(32) chain_cols_kernel(
-    const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
-    const float* __restrict__ eta_all, const float* __restrict__ phig,
-    const double* __restrict__ gam, const cf* __restrict__ gL, const cf* __restrict__ gR,
-    const cf* __restrict__ start, float* __restrict__ weights) {
-  __shared__ ChainColsSmem s_cc;
-  const uint32_t job = blockIdx.x;
-  if (job >= n_jobs) return;
-  const int task = find_task(n_tasks, job, [&](int t) { return 2 * tasks[t].col_base; });
-  const TaskDesc d = tasks[task];
-  if (d.fused || d.cta_chain) return;
-  const uint32_t local = job - 2 * d.col_base;
-  const int y = (int)(local >> 1), dir = (int)(local & 1);
-  if (d.W < 1 || d.W > 16 || y % (32 / d.W) != 0) return;
-  by_width<ChainCols>(d.W, d, y, dir, eta_all, phig, gam, gL, gR, start, weights, &s_cc);
-}
-
 int warps_for(size_t per_warp, int max_warps) {
   int w = max_warps;
   while (w > 1 && per_warp * w > 96 * 1024) --w;
@@ -1113,9 +938,8 @@ cudaError_t sweep_smem(const TaskDesc* d_tasks, int n_tasks, int max_W, const do
   cudaError_t e = cudaFuncSetAttribute(rgf_sweep_cta_kernel<C>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  rgf_sweep_cta_kernel<C><<<2 * n_tasks, kSweepCtaThreads, smem, s>>>(d_tasks, n_tasks, d_wire,
-                                                                   d_phi, d_sig, d_gL, d_gR,
-                                                                   d_err);
+  rgf_sweep_cta_kernel<C><<<2 * n_tasks, kSweepCtaThreads, smem, s>>>(
+      d_tasks, n_tasks, d_wire, d_phi, d_sig, d_gL, d_gR, d_err, sizeof(C) == sizeof(cf) ? 17 : 1);
   return cudaGetLastError();
 }
 
@@ -1130,11 +954,11 @@ template <>
 cudaError_t sweep_impl<cf>(const TaskDesc* d_tasks, int n_tasks, int max_W,
                            const double* d_wire, const double* d_phi, const cd* d_sig, cf* d_gL,
                            cf* d_gR, int32_t* d_err, cudaStream_t s) {
-  if (max_W <= 16) {
-    rgf_sweep_reg_kernel<<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig, d_gL,
-                                                    d_gR, d_err);
-    return cudaGetLastError();
-  }
+  // register kernel for the tasks of width <= 16 (it skips wider ones), CTA kernel for the rest
+  rgf_sweep_reg_kernel<<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig, d_gL,
+                                                  d_gR, d_err);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || max_W <= 16) return e;
   return sweep_smem<cf>(d_tasks, n_tasks, max_W, d_wire, d_phi, d_sig, d_gL, d_gR, d_err, s);
 }
 
@@ -1146,8 +970,9 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
                          typename Real<C>::T* d_w, double* d_rowsum, double* d_mode_w,
                          double* d_c, int32_t* d_err, C* d_green, C* d_gphi, cudaStream_t s,
                          int chain_warps) {
-  if (sizeof(C) == sizeof(cf) && max_W <= 16) {
-    // register-resident diagonal blocks, 4 warps per block
+  if (sizeof(C) == sizeof(cf)) {
+    // register-resident diagonal blocks for the tasks of width <= 16, 4 warps per block (the
+    // kernel skips wider tasks)
     const int warps = 4;
     const unsigned blocks = (n_cols + warps - 1) / warps;
     const cf* gl = reinterpret_cast<const cf*>(d_gL);
@@ -1158,26 +983,25 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
                                                   d_err);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-  } else {
+  }
+  if (sizeof(C) != sizeof(cf) || max_W > 16) {
     const size_t smem = diag_cta_bytes<C>(max_W);
     cudaError_t e = cudaFuncSetAttribute(diag_cta_kernel<C>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     diag_cta_kernel<C><<<n_cols, kSweepThreads, smem, s>>>(
         d_tasks, n_tasks, n_cols, d_wire, d_phi, d_sig, d_gam, d_gL, d_gR, d_start, d_rowsum,
-        d_mode_w, d_c, d_err);
+        d_mode_w, d_c, d_err, sizeof(C) == sizeof(cf) ? 17 : 1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   const uint32_t jobs = 2 * n_cols;
-  if (sizeof(C) == sizeof(cf) && max_W <= 16 && d_green == nullptr) {
-    chain_cols_kernel<<<jobs, 32, 0, s>>>(
-        d_tasks, n_tasks, jobs, reinterpret_cast<const float*>(d_eta),
-        reinterpret_cast<const float*>(d_phiR), d_gam, reinterpret_cast<const cf*>(d_gL),
-        reinterpret_cast<const cf*>(d_gR), reinterpret_cast<const cf*>(d_start),
-        reinterpret_cast<float*>(d_w));
-    return cudaGetLastError();
-  }
+  if (sizeof(C) == sizeof(cf) && max_W <= 32 && d_green == nullptr)
+    return launch_chain_cols(d_tasks, n_tasks, jobs, max_W, reinterpret_cast<const float*>(d_eta),
+                             reinterpret_cast<const float*>(d_phiR), d_gam,
+                             reinterpret_cast<const cf*>(d_gL), reinterpret_cast<const cf*>(d_gR),
+                             reinterpret_cast<const cf*>(d_start), reinterpret_cast<float*>(d_w),
+                             s);
   const size_t per = chain_warp_bytes<C>(max_W);
   int warps = warps_for(per, 8);
   if (chain_warps > 0) warps = chain_warps < chain_max<C>(max_W) ? chain_warps : chain_max<C>(max_W);

@@ -94,6 +94,12 @@ cudaError_t launch_rgf_sweep(const TaskDesc* d_tasks, int n_tasks, int max_W, in
 // Diagonal blocks (start blocks, A per row, mode weights, c_p) then the block-column chains
 // emitting the weights.  n_cols = sum over tasks of L + 2.  On return rowsum holds A of every
 // table row and c_p in the two mode-row slots; the alias build replaces them by the row sums.
+// Block columns with one column per lane (complex64, W <= 32, no gradient outputs; see
+// k_chain_cols.cu): jobs = 2 * sum over tasks of (L + 2).
+cudaError_t launch_chain_cols(const TaskDesc* d_tasks, int n_tasks, uint32_t n_jobs, int max_W,
+                              const float* d_eta32, const float* d_phi32, const double* d_gam,
+                              const cf* d_gL, const cf* d_gR, const cf* d_start, float* d_w,
+                              cudaStream_t s);
 cudaError_t launch_block_columns(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols,
                                  int max_W, int precision, const double* d_wire,
                                  const float* d_eta32, const double* d_phi, const float* d_phi32,
