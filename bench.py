@@ -69,6 +69,27 @@ def tensor_peak(kind):
         return 1900.0 * 1.1 / 2.25, "fallback BF16 1.9 PFLOP/s x nominal TF32/BF16 ratio"
 
 
+# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of a
+# timed launch, see profiles/) keyed by kernel, workload and a hash of the kernel's sources: a
+# kernel changed since its counters were taken reports null.
+MEASURED_TRAFFIC = {
+    ("walk_kernel", "wire_W10_L50_eta0.05_64E", "09feb201ed6fafea"): 131264512,
+}
+TRAFFIC_SOURCES = {"walk_kernel": ["k_walk.cu", "philox.cuh"]}
+
+
+def measured_traffic(kernel, workload):
+    import hashlib
+    files = TRAFFIC_SOURCES.get(kernel)
+    if not files:
+        return None
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1805_10164_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return MEASURED_TRAFFIC.get((kernel, workload, h.hexdigest()[:16]))
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -348,6 +369,7 @@ def run_gpu(args):
                     "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": src + " HBM copy",
                     "traffic": None, "algorithmic_bytes_per_launch": int(per_launch_bytes),
                     "avg_launch_ms": round(kms / klaunch, 5)}
+        roof_hbm["traffic"] = measured_traffic(kname, wl.name)
         roof = dict(roof_hbm)
         if kname == "walk_kernel" and probe_gbs and (probe_tab < 2 * per_task_bytes):
             # the probe could not cover two tasks' tables: HBM-resident gathers, keep the HBM
