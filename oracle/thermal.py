@@ -1,0 +1,197 @@
+"""Continuous-energy sampling of the linear-response conductance (oracle; test infrastructure
+only).
+
+Sec. II.E: the linear conductance is G_qp = (e^2/h) integral dE T_qp(E) Th(E) with
+Th(E) = -df/dE (Eq. Gqp_expression); drawing the energy E_0 of each Monte Carlo sample from
+h(E) = Th(E) makes the sampled variable X_pq = Tr[Gamma_p A](E_0) delta_rq (Eq. gpq_formula,
+Eq. elast_lin_xpq).  Sec. "Interpolation" (discussion) replaces the transition probabilities at
+E_0 by linear interpolation between two nearby energies where they were computed.
+
+Here the energies are restricted to the span [E_0, E_{M-1}] of a grid on which tables exist:
+  * Th(E) = 1 / (4 kT cosh^2((E - mu) / (2 kT))) is the logistic density with scale kT, CDF
+    F(E) = 1 / (1 + exp(-(E - mu) / kT)), inverse mu + kT log(p / (1 - p));
+  * G_grid = integral over [E_0, E_{M-1}] of Th(E) T(E) dE = (F(E_{M-1}) - F(E_0)) E[X] with E
+    drawn from Th restricted to the span;
+  * with E in grid interval i (E_i <= E < E_{i+1}, alpha = (E - E_i) / (E_{i+1} - E_i)) the walk
+    uses the transition probabilities (1 - alpha) p(E_i) + alpha p(E_{i+1}) (each draw picks the
+    table of E_{i+1} with probability alpha, else that of E_i), the injection distribution
+    likewise (from the open one alone when one of the two has Tr Gamma_p A = 0), and
+    X = c(E) = (1 - alpha) c_i + alpha c_{i+1} when absorbed at q = 1 - p.
+
+Random numbers of walker ``wid`` in wire ``wire`` (seed -> key (lo, hi)), Philox4x32-10 block
+b with counter (b, wid_lo, wid_hi, 0x80000000 | wire):
+  block 0: (x0, x1) -> u = (((x0 << 32 | x1) >> 11) + 1/2) / 2^53, the energy
+           E = F^-1(F(E_0) + u (F(E_{M-1}) - F(E_0))); x2 picks the injection table
+           (E_{i+1}'s iff x2 < a, a = min(floor(alpha 2^32), 2^32 - 1));
+  block 1: the injection mode draw (x0, x1) on the picked table's mode row;
+  block b >= 2: transition b - 1: (x0, x1) on the current row of the table picked by x2 < a.
+A draw with words (x, y) over a K-entry row picks c = (x K) >> 32 and keeps c if y < thr[c],
+else alias[c].
+"""
+import numpy as np
+
+from . import buttiker, markov, wire
+from .philox import philox4x32_10
+
+MASK32 = np.uint64(0xFFFFFFFF)
+TWO32 = float(2 ** 32)
+
+
+def th_density(E, mu, kT):
+    """Th(E) = -df/dE for the Fermi function f(E) = 1 / (1 + exp((E - mu) / kT))."""
+    x = (np.asarray(E, dtype=np.float64) - mu) / (2.0 * kT)
+    return 1.0 / (4.0 * kT * np.cosh(x) ** 2)
+
+
+def th_cdf(E, mu, kT):
+    """integral from -infinity to E of Th = 1 - f(E)."""
+    return 1.0 / (1.0 + np.exp(-(np.asarray(E, dtype=np.float64) - mu) / kT))
+
+
+def th_inverse(p, mu, kT):
+    return mu + kT * np.log(p / (1.0 - p))
+
+
+def energy_draw(x0, x1, grid, mu, kT):
+    """(E, interval i, a) of the energy words (x0, x1) (uint32 arrays) on an ascending grid."""
+    grid = np.asarray(grid, dtype=np.float64)
+    v = ((x0.astype(np.uint64) << np.uint64(32)) | x1.astype(np.uint64)) >> np.uint64(11)
+    u = (v.astype(np.float64) + 0.5) / 2.0 ** 53
+    F0, F1 = th_cdf(grid[0], mu, kT), th_cdf(grid[-1], mu, kT)
+    E = th_inverse(F0 + u * (F1 - F0), mu, kT)
+    i = np.clip(np.searchsorted(grid, E, side="right") - 1, 0, grid.size - 2)
+    alpha = np.clip((E - grid[i]) / (grid[i + 1] - grid[i]), 0.0, 1.0)
+    a = np.minimum(np.floor(alpha * TWO32), TWO32 - 1).astype(np.uint64)
+    return E, i, a
+
+
+def conductance_direct(onsite, eta, t, grid, mu, kT, n_quad=16, lead_model=0, gamma_lead=0.0,
+                       q=1, p=0):
+    """G_grid = integral over [grid[0], grid[-1]] of Th(E) T^eff_qp(E) dE (units e^2/h), by
+    Gauss-Legendre quadrature with n_quad nodes on each grid interval of the direct probe solve
+    (Eq. buteq)."""
+    grid = np.asarray(grid, dtype=np.float64)
+    xg, wg = np.polynomial.legendre.leggauss(n_quad)
+    total = 0.0
+    for i in range(grid.size - 1):
+        lo, hi = grid[i], grid[i + 1]
+        for x, wq in zip(xg, wg):
+            E = 0.5 * (hi - lo) * x + 0.5 * (hi + lo)
+            g = wire.green_retarded(E, onsite, eta, t, lead_model, gamma_lead)
+            T = buttiker.effective_transmission(g)[q, p]
+            total += 0.5 * (hi - lo) * wq * th_density(E, mu, kT) * T
+    return total
+
+
+def _chain(tab):
+    w, n = tab["w"], tab["n"]
+    tot = w.sum(axis=1)
+    P = np.zeros_like(w)
+    live = tot > 0
+    P[live] = w[live] / tot[live, None]
+    return P
+
+
+def interpolated_absorption(tab_i, tab_j, alpha, p=0):
+    """P(q | p) for q = 0, 1 of the chain whose transition probabilities are (1 - alpha) times
+    those of tab_i plus alpha times those of tab_j, injected from lead p with the interpolated
+    mode distribution (the open one alone if one side is closed)."""
+    n, W = tab_i["n"], tab_i["W"]
+    P = (1.0 - alpha) * _chain(tab_i) + alpha * _chain(tab_j)
+    mi, mj = tab_i["mode_w"][p], tab_j["mode_w"][p]
+    ui = mi / mi.sum() if mi.sum() > 0 else None
+    uj = mj / mj.sum() if mj.sum() > 0 else None
+    if ui is None and uj is None:
+        return np.zeros(2)
+    u = uj if ui is None else ui if uj is None else (1.0 - alpha) * ui + alpha * uj
+    Q, R = P[:n, :n], P[:n, n:]
+    P_site = np.linalg.solve(np.eye(n) - Q, R)
+    Pi = P[n + p * W:n + (p + 1) * W]
+    return u @ (Pi[:, n:] + Pi[:, :n] @ P_site)
+
+
+def conductance_interpolated(tabs, grid, mu, kT, n_quad=16, p=0):
+    """The exact expectation of the sampler: integral over the span of Th(E) c(E) P(q|p; E) dE
+    with c and the chain interpolated linearly between grid energies (q = 1 - p)."""
+    grid = np.asarray(grid, dtype=np.float64)
+    q = 1 - p
+    xg, wg = np.polynomial.legendre.leggauss(n_quad)
+    total = 0.0
+    for i in range(grid.size - 1):
+        lo, hi = grid[i], grid[i + 1]
+        ci, cj = tabs[i]["c"][p], tabs[i + 1]["c"][p]
+        for x, wq in zip(xg, wg):
+            alpha = 0.5 * (x + 1.0)
+            E = lo + alpha * (hi - lo)
+            c = (1.0 - alpha) * ci + alpha * cj
+            if c <= 0.0:
+                continue
+            P = interpolated_absorption(tabs[i], tabs[i + 1], alpha, p)
+            total += 0.5 * (hi - lo) * wq * th_density(E, mu, kT) * c * P[q]
+    return total
+
+
+def walk(entries, mode_entries, c, n, W, wire_index, start_lead, seed, wids, grid, mu, kT,
+         max_steps, energy=None):
+    """Replay walkers ``wids`` of the thermal sampler over integer alias tables.
+
+    entries[e] [n + 2W, n + 2] and mode_entries[e] [2, W] (uint64) and c[e] (Tr Gamma_p A at the
+    two leads) of every grid energy e.  ``energy``: optional (interval, a) arrays that replace the
+    energy draw (the replay of a trace).  Returns (lead int32: 0 / 1, -1 no open channel, -2
+    truncated; steps uint32; interval int64; a uint64).
+    """
+    wids = np.asarray(wids, dtype=np.uint64)
+    m = wids.size
+    wlo, whi = wids & MASK32, wids >> np.uint64(32)
+    k0, k1 = int(seed) & 0xFFFFFFFF, (int(seed) >> 32) & 0xFFFFFFFF
+    ctr3 = np.full(m, 0x80000000 | int(wire_index), dtype=np.uint64)
+    x = philox4x32_10(np.zeros(m, dtype=np.uint64), wlo, whi, ctr3, k0, k1)
+    if energy is None:
+        _, iv, a = energy_draw(x[0], x[1], grid, mu, kT)
+    else:
+        iv, a = np.asarray(energy[0], dtype=np.int64), np.asarray(energy[1], dtype=np.uint64)
+    K = n + 2
+    lead = np.full(m, -2, dtype=np.int32)
+    steps = np.zeros(m, dtype=np.uint32)
+    for w in range(m):
+        i = int(iv[w])
+        hi_pick = int(x[2][w]) < int(a[w])
+        t = i + 1 if hi_pick else i
+        if c[t][start_lead] <= 0.0:
+            t = i if t == i + 1 else i + 1
+            if c[t][start_lead] <= 0.0:
+                lead[w] = -1
+                continue
+        y = philox4x32_10(np.array([1], np.uint64), wlo[w:w + 1], whi[w:w + 1], ctr3[w:w + 1],
+                          k0, k1)
+        cc = (int(y[0][0]) * W) >> 32
+        e = int(mode_entries[t][start_lead][cc])
+        mode = cc if int(y[1][0]) < (e & 0xFFFFFFFF) else (e >> 32)
+        row = n + start_lead * W + mode
+        b = 2
+        while True:
+            z = philox4x32_10(np.array([b], np.uint64), wlo[w:w + 1], whi[w:w + 1],
+                              ctr3[w:w + 1], k0, k1)
+            t = i + 1 if int(z[2][0]) < int(a[w]) else i
+            cc = (int(z[0][0]) * K) >> 32
+            e = int(entries[t][row, cc])
+            j = cc if int(z[1][0]) < (e & 0xFFFFFFFF) else (e >> 32)
+            steps[w] += 1
+            if j >= n:
+                lead[w] = j - n
+                break
+            if steps[w] >= max_steps:
+                break
+            row = j
+            b += 1
+    return lead, steps, iv, a
+
+
+def estimate(lead, a, iv, c, window, start_lead=0):
+    """(G, SE) of the sampled X = c(E) 1[absorbed at q], scaled by the window F1 - F0."""
+    q = 1 - start_lead
+    alpha = a.astype(np.float64) / TWO32
+    cE = np.array([(1.0 - al) * c[i][start_lead] + al * c[i + 1][start_lead]
+                   for i, al in zip(iv, alpha)])
+    X = np.where(lead == q, cE, 0.0)
+    return window * X.mean(), window * X.std(ddof=0) / np.sqrt(X.size)
