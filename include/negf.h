@@ -342,6 +342,52 @@ negf_status negf_current(negf_ctx ctx, negf_tables tables, negf_tally tally, dou
                          double mu_q, double kT, double* I, double* se, double* T,
                          double* T_se);
 
+/* --- linear conductance with continuous energies (Eq. Gqp_expression, Eq. gpq_formula,
+ *     Eq. elast_lin_xpq; Sec. "Interpolation") ------------------------------------------- */
+
+/* Result of negf_walk_thermal.  G and se are in units of e^2/h. */
+typedef struct {
+  double G;              /* estimate of the integral over [E_0, E_{M-1}] of Th(E) T_qp(E) dE */
+  double se;             /* its standard error (sample standard deviation / sqrt(walkers)) */
+  double window;         /* F(E_{M-1}) - F(E_0): the share of Th inside the grid's span */
+  double mean_steps;     /* transitions per walker (absorbed or truncated) */
+  uint64_t walkers;      /* walkers run */
+  uint64_t absorbed[2];  /* absorbed at lead L, R */
+  uint64_t closed;       /* no open channel at either grid energy around E_0 (X = 0) */
+  uint64_t truncated;    /* reached max_steps */
+} negf_thermal_result;
+
+/* The linear conductance G_qp = integral dE T_qp(E) Th(E), Th = -df/dE (Eq. Gqp_expression),
+ * sampled as the paper does (Eq. gpq_formula, Eq. elast_lin_xpq): each walker draws its energy
+ * E_0 from Th, restricted to the span [E_0, E_{M-1}] of wire `wire`'s energy grid (the M >= 2
+ * energies of that wire in the tables, strictly ascending, one-level layout), and walks the
+ * Markov chain whose Step 6' transition probabilities are interpolated linearly between the two
+ * grid energies around E_0 (the paper's interpolation of the p_i, Sec. "Interpolation"): every
+ * draw uses the table of the upper grid energy with probability alpha = (E_0 - E_i) /
+ * (E_{i+1} - E_i), else the lower one; the injection mode likewise.  Where the start lead has
+ * no open channel at one end (Tr Gamma_p A = 0 there), the interval walks with the other end's
+ * tables alone (a chain without an open lead never absorbs); closed at both ends, X = 0.
+ * A walker absorbed at q = 1 - start_lead scores
+ * X = (1 - alpha) c_i + alpha c_{i+1} (c = Tr Gamma_p A); G = window * mean(X).
+ * Th is the logistic density with scale kT around mu (Fermi function at mu, kT).
+ * Random numbers: walker w (id walker_id_offset + w) takes Philox4x32-10 block b with counter
+ * (b, id_lo, id_hi, 0x80000000 | wire) and key (seed_lo, seed_hi): block 0 words (x0, x1) give
+ * u = (((x0 << 32 | x1) >> 11) + 1/2) / 2^53 and E_0 = F^-1(F(E_0) + u window), word x2 the
+ * injection table (upper iff x2 < a, a = min(floor(alpha 2^32), 2^32 - 1)); block 1 the injection
+ * mode (x0, x1); block b >= 2 transition b - 1 ((x0, x1) on the row, x2 < a picks the table).
+ * d_lead, d_steps, d_interval, d_a: optional caller-owned device arrays of `walkers` entries
+ * (any may be NULL) receiving each walker's outcome (0 / 1 lead, -1 closed, -2 truncated),
+ * transitions, grid interval i and a.  Allocates a small tally on the context stream, runs on it
+ * and synchronises.  Errors: NEGF_E_INVALID for bad handles, wire out of range, fewer than two
+ * energies, energies not strictly ascending, two-level tables, tables released by negf_run,
+ * kT <= 0, non-finite mu, walkers above 2^40, max_steps outside [1, NEGF_MAX_STEPS];
+ * NEGF_E_NOMEM; NEGF_E_CUDA. */
+negf_status negf_walk_thermal(negf_ctx ctx, negf_tables tables, int32_t wire, int32_t start_lead,
+                              uint64_t seed, uint64_t walkers, uint64_t walker_id_offset,
+                              double mu, double kT, uint32_t max_steps, int32_t* d_lead,
+                              uint32_t* d_steps, int32_t* d_interval, uint32_t* d_a,
+                              negf_thermal_result* out);
+
 /* --- table build without device allocation ------------------------------------------------ */
 
 /* The paper has no counterpart to this entry point; it exists for callers of this library that

@@ -15,8 +15,11 @@ Here the energies are restricted to the span [E_0, E_{M-1}] of a grid on which t
   * with E in grid interval i (E_i <= E < E_{i+1}, alpha = (E - E_i) / (E_{i+1} - E_i)) the walk
     uses the transition probabilities (1 - alpha) p(E_i) + alpha p(E_{i+1}) (each draw picks the
     table of E_{i+1} with probability alpha, else that of E_i), the injection distribution
-    likewise (from the open one alone when one of the two has Tr Gamma_p A = 0), and
-    X = c(E) = (1 - alpha) c_i + alpha c_{i+1} when absorbed at q = 1 - p.
+    likewise, and X = c(E) = (1 - alpha) c_i + alpha c_{i+1} when absorbed at q = 1 - p;
+  * an interval with no open channel of lead p at one end (c = 0 there) interpolates c only and
+    walks with the open end's probabilities alone: a chain without an open lead never absorbs,
+    so mixing it in would make the walks' mean length diverge as alpha approaches that end
+    (both ends closed: X = 0).
 
 Random numbers of walker ``wid`` in wire ``wire`` (seed -> key (lo, hi)), Philox4x32-10 block
 b with counter (b, wid_lo, wid_hi, 0x80000000 | wire):
@@ -95,15 +98,20 @@ def _chain(tab):
 def interpolated_absorption(tab_i, tab_j, alpha, p=0):
     """P(q | p) for q = 0, 1 of the chain whose transition probabilities are (1 - alpha) times
     those of tab_i plus alpha times those of tab_j, injected from lead p with the interpolated
-    mode distribution (the open one alone if one side is closed)."""
+    mode distribution; when lead p has no open channel at one end, the chain and injection of
+    the open end alone."""
     n, W = tab_i["n"], tab_i["W"]
-    P = (1.0 - alpha) * _chain(tab_i) + alpha * _chain(tab_j)
     mi, mj = tab_i["mode_w"][p], tab_j["mode_w"][p]
-    ui = mi / mi.sum() if mi.sum() > 0 else None
-    uj = mj / mj.sum() if mj.sum() > 0 else None
-    if ui is None and uj is None:
+    open_i, open_j = tab_i["c"][p] > 0.0, tab_j["c"][p] > 0.0
+    if not (open_i or open_j):
         return np.zeros(2)
-    u = uj if ui is None else ui if uj is None else (1.0 - alpha) * ui + alpha * uj
+    if open_i and open_j:
+        P = (1.0 - alpha) * _chain(tab_i) + alpha * _chain(tab_j)
+        u = (1.0 - alpha) * mi / mi.sum() + alpha * mj / mj.sum()
+    elif open_i:
+        P, u = _chain(tab_i), mi / mi.sum()
+    else:
+        P, u = _chain(tab_j), mj / mj.sum()
     Q, R = P[:n, :n], P[:n, n:]
     P_site = np.linalg.solve(np.eye(n) - Q, R)
     Pi = P[n + p * W:n + (p + 1) * W]
@@ -155,13 +163,17 @@ def walk(entries, mode_entries, c, n, W, wire_index, start_lead, seed, wids, gri
     steps = np.zeros(m, dtype=np.uint32)
     for w in range(m):
         i = int(iv[w])
-        hi_pick = int(x[2][w]) < int(a[w])
-        t = i + 1 if hi_pick else i
-        if c[t][start_lead] <= 0.0:
-            t = i if t == i + 1 else i + 1
-            if c[t][start_lead] <= 0.0:
-                lead[w] = -1
-                continue
+        open_lo, open_hi = c[i][start_lead] > 0.0, c[i + 1][start_lead] > 0.0
+        if not (open_lo or open_hi):
+            lead[w] = -1
+            continue
+
+        def pick(word):
+            # the table of the draw: mixed on an interval open at both ends, else the open end
+            if open_lo and open_hi:
+                return i + 1 if int(word) < int(a[w]) else i
+            return i if open_lo else i + 1
+        t = pick(x[2][w])
         y = philox4x32_10(np.array([1], np.uint64), wlo[w:w + 1], whi[w:w + 1], ctr3[w:w + 1],
                           k0, k1)
         cc = (int(y[0][0]) * W) >> 32
@@ -172,7 +184,7 @@ def walk(entries, mode_entries, c, n, W, wire_index, start_lead, seed, wids, gri
         while True:
             z = philox4x32_10(np.array([b], np.uint64), wlo[w:w + 1], whi[w:w + 1],
                               ctr3[w:w + 1], k0, k1)
-            t = i + 1 if int(z[2][0]) < int(a[w]) else i
+            t = pick(z[2][0])
             cc = (int(z[0][0]) * K) >> 32
             e = int(entries[t][row, cc])
             j = cc if int(z[1][0]) < (e & 0xFFFFFFFF) else (e >> 32)

@@ -1,0 +1,144 @@
+// Linear conductance with continuous energies: each walker draws its energy from the thermal
+// window Th(E) = -df/dE (Eq. Gqp_expression; the sampling density of Eq. gpq_formula) restricted
+// to the span of a wire's energy grid, and walks the Step 6' chain whose transition
+// probabilities are interpolated linearly between the two grid energies around it (the
+// interpolation of the p_i in the paper's Sec. "Interpolation"): each draw takes the upper grid
+// energy's alias table with probability alpha, else the lower one's (an interval where the start
+// lead has no open channel at one end walks with the other end's table).  A walker absorbed at
+// q = 1 - p scores c(E) = (1 - alpha) c_i + alpha c_{i+1} (Eq. elast_lin_xpq); the tally keeps,
+// per grid interval, the absorbed count, sum of a = floor(alpha 2^32) and sum of (a >> 16)^2 in
+// integers, from which the host forms the mean and variance of the score exactly.
+//
+// Random numbers (Philox4x32-10, counter (b, id_lo, id_hi, 0x80000000 | wire)): block 0 -> the
+// energy (x0, x1) and the injection table (x2); block 1 -> the injection mode (x0, x1); block
+// b >= 2 -> transition b - 1, (x0, x1) on the row and x2 < a for the table.  One thread per
+// walker (grid-stride); the block's tally sits in shared memory and is added to global memory
+// once.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "negf_internal.cuh"
+#include "philox.cuh"
+
+namespace negf {
+namespace {
+
+constexpr int kThermalThreads = 256;
+
+__device__ __forceinline__ void smem_add64(unsigned* lohi, unsigned v) {
+  const unsigned old = atomicAdd(lohi, v);
+  if (old + v < old) atomicAdd(lohi + 1, 1u);
+}
+
+__global__ void __launch_bounds__(kThermalThreads) thermal_walk_kernel(
+    const TaskDesc* __restrict__ tasks, int task0, int M, uint32_t wire,
+    const uint64_t* __restrict__ tab, const uint64_t* __restrict__ mode_tab,
+    const double* __restrict__ cvals, int p, PhiloxKey key, uint64_t walkers, uint64_t id_offset,
+    uint32_t max_steps, double mu, double kT, double F0, double window,
+    unsigned long long* __restrict__ tally, int32_t* __restrict__ t_lead,
+    uint32_t* __restrict__ t_steps, int32_t* __restrict__ t_interval, uint32_t* __restrict__ t_a) {
+  // shared tally: per interval (absorbed at q, sum a, sum (a >> 16)^2), then absorbed L, R,
+  // closed, truncated, steps; each a 64-bit counter kept as two 32-bit words
+  extern __shared__ unsigned s_t[];
+  const int n_fields = 3 * (M - 1) + 5;
+  for (int i = threadIdx.x; i < 2 * n_fields; i += blockDim.x) s_t[i] = 0u;
+  __syncthreads();
+  const int q = 1 - p;
+  const int G0 = 3 * (M - 1);
+  const uint32_t ctr3 = 0x80000000u | wire;
+  const TaskDesc& d0 = tasks[task0];
+  const uint32_t n = (uint32_t)d0.n, W = (uint32_t)d0.W, K = (uint32_t)d0.K;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < walkers; g += stride) {
+    const uint64_t wid = id_offset + g;
+    const uint32_t lo = (uint32_t)wid, hi = (uint32_t)(wid >> 32);
+    const uint4 r0 = philox4x32_10(make_uint4(0u, lo, hi, ctr3), key);
+    const uint64_t v = (((uint64_t)r0.x << 32) | r0.y) >> 11;
+    const double u = ((double)v + 0.5) * 0x1p-53;
+    const double pE = F0 + u * window;
+    const double E = mu + kT * log(pE / (1.0 - pE));
+    int lo_i = 0, hi_i = M - 1;                       // last grid index with E_e <= E
+    while (lo_i < hi_i) {
+      const int mid = (lo_i + hi_i + 1) >> 1;
+      if (tasks[task0 + mid].E <= E) lo_i = mid; else hi_i = mid - 1;
+    }
+    const int iv = lo_i < M - 2 ? lo_i : M - 2;
+    const double Ei = tasks[task0 + iv].E, Ej = tasks[task0 + iv + 1].E;
+    double alpha = (E - Ei) / (Ej - Ei);
+    alpha = alpha < 0.0 ? 0.0 : (alpha > 1.0 ? 1.0 : alpha);
+    const double af = floor(alpha * 4294967296.0);
+    const uint32_t a = af >= 4294967295.0 ? 0xffffffffu : (uint32_t)af;
+    // an interval open at both ends mixes the two tables; one open at a single end walks with
+    // that end's table alone (a chain without an open lead never absorbs)
+    const bool open_lo = cvals[2 * (task0 + iv) + p] > 0.0;
+    const bool open_hi = cvals[2 * (task0 + iv + 1) + p] > 0.0;
+    const bool mix = open_lo && open_hi;
+    auto upper = [&](uint32_t word) { return mix ? word < a : open_hi; };
+    const int t = upper(r0.z) ? iv + 1 : iv;
+    int outcome = (open_lo || open_hi) ? -3 : -1;
+    uint32_t steps = 0;
+    if (outcome == -3) {
+      const uint4 r1 = philox4x32_10(make_uint4(1u, lo, hi, ctr3), key);
+      const uint64_t* mrow = mode_tab + tasks[task0 + t].mode_off + p * W;
+      const uint32_t c = __umulhi(r1.x, W);
+      const uint64_t e = __ldg(mrow + c);
+      uint32_t row = n + p * W + (r1.y < (uint32_t)e ? c : (uint32_t)(e >> 32));
+      const uint64_t* tab_lo = tab + tasks[task0 + iv].tab_off;
+      const uint64_t* tab_hi = tab + tasks[task0 + iv + 1].tab_off;
+      for (uint32_t b = 2;; ++b) {
+        const uint4 r = philox4x32_10(make_uint4(b, lo, hi, ctr3), key);
+        const uint64_t* trow = upper(r.z) ? tab_hi : tab_lo;
+        const uint32_t cc = __umulhi(r.x, K);
+        const uint64_t ee = __ldg(trow + (uint64_t)row * K + cc);
+        const uint32_t j = r.y < (uint32_t)ee ? cc : (uint32_t)(ee >> 32);
+        ++steps;
+        if (j >= n) { outcome = (int)(j - n); break; }
+        if (steps >= max_steps) { outcome = -2; break; }
+        row = j;
+      }
+    }
+    if (outcome == q) {
+      smem_add64(&s_t[2 * (3 * iv + 0)], 1u);
+      smem_add64(&s_t[2 * (3 * iv + 1)], a);
+      const uint32_t a16 = a >> 16;
+      smem_add64(&s_t[2 * (3 * iv + 2)], a16 * a16);
+    }
+    if (outcome >= 0) smem_add64(&s_t[2 * (G0 + outcome)], 1u);
+    else if (outcome == -1) smem_add64(&s_t[2 * (G0 + 2)], 1u);
+    else smem_add64(&s_t[2 * (G0 + 3)], 1u);
+    smem_add64(&s_t[2 * (G0 + 4)], steps);
+    if (t_lead) t_lead[g] = outcome;
+    if (t_steps) t_steps[g] = steps;
+    if (t_interval) t_interval[g] = iv;
+    if (t_a) t_a[g] = a;
+  }
+  __syncthreads();
+  for (int f = threadIdx.x; f < n_fields; f += blockDim.x) {
+    const unsigned long long v = ((unsigned long long)s_t[2 * f + 1] << 32) | s_t[2 * f];
+    if (v) atomicAdd(tally + f, v);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_thermal_walk(const TaskDesc* d_tasks, int task0, int M, int wire,
+                                const uint64_t* d_tab, const uint64_t* d_mode_tab,
+                                const double* d_c, int start_lead, uint64_t seed,
+                                uint64_t walkers, uint64_t id_offset, uint32_t max_steps,
+                                double mu, double kT, double F0, double window,
+                                unsigned long long* d_tally, int32_t* d_lead, uint32_t* d_steps,
+                                int32_t* d_interval, uint32_t* d_a, int sm_count,
+                                cudaStream_t s) {
+  if (walkers == 0 || M < 2) return cudaSuccess;
+  const PhiloxKey key{(uint32_t)seed, (uint32_t)(seed >> 32)};
+  const size_t smem = sizeof(unsigned) * 2 * (size_t)(3 * (M - 1) + 5);
+  const uint64_t need = (walkers + kThermalThreads - 1) / kThermalThreads;
+  uint64_t blocks = (uint64_t)sm_count * 8;
+  if (blocks > need) blocks = need;
+  thermal_walk_kernel<<<(unsigned)blocks, kThermalThreads, smem, s>>>(
+      d_tasks, task0, M, (uint32_t)wire, d_tab, d_mode_tab, d_c, start_lead, key, walkers,
+      id_offset, max_steps, mu, kT, F0, window, d_tally, d_lead, d_steps, d_interval, d_a);
+  return cudaGetLastError();
+}
+
+}  // namespace negf

@@ -1616,6 +1616,92 @@ negf_status negf_current(negf_ctx ctx, negf_tables t, negf_tally tl, double mu_p
   return NEGF_OK;
 }
 
+negf_status negf_walk_thermal(negf_ctx ctx, negf_tables t, int32_t wire, int32_t start_lead,
+                              uint64_t seed, uint64_t walkers, uint64_t walker_id_offset,
+                              double mu, double kT, uint32_t max_steps, int32_t* d_lead,
+                              uint32_t* d_steps, int32_t* d_interval, uint32_t* d_a,
+                              negf_thermal_result* out) {
+  negf_status st = walk_common(ctx, t, start_lead, max_steps, "negf_walk_thermal");
+  if (st != NEGF_OK) return st;
+  if (!out) return fail(ctx, NEGF_E_INVALID, "negf_walk_thermal: out is NULL");
+  if (wire < 0 || wire >= t->n_wires)
+    return fail(ctx, NEGF_E_INVALID, "negf_walk_thermal: wire %d out of range", wire);
+  if (!(kT > 0.0) || !isfinite(kT) || !isfinite(mu))
+    return fail(ctx, NEGF_E_INVALID, "negf_walk_thermal: need finite mu and kT > 0");
+  if (walkers > (1ull << 40))
+    return fail(ctx, NEGF_E_INVALID, "negf_walk_thermal: walkers above 2^40");
+  if (t->tables_released || !t->d_tab)
+    return fail(ctx, NEGF_E_INVALID, "negf_walk_thermal: the tables were released");
+  const int task0 = t->h_wire_task0[wire];
+  const int task1 = wire + 1 < t->n_wires ? t->h_wire_task0[wire + 1] : t->n_tasks;
+  const int M = task1 - task0;
+  if (M < 2) return fail(ctx, NEGF_E_INVALID, "negf_walk_thermal: the wire needs two energies");
+  for (int e = 0; e < M; ++e) {
+    const TaskDesc& d = t->h_tasks[task0 + e];
+    if (d.layout != NEGF_LAYOUT_ONE_LEVEL)
+      return fail(ctx, NEGF_E_INVALID, "negf_walk_thermal: two-level tables are not supported");
+    if (e > 0 && !(d.E > t->h_tasks[task0 + e - 1].E))
+      return fail(ctx, NEGF_E_INVALID, "negf_walk_thermal: energies must be strictly ascending");
+  }
+  // the thermal window Th is the logistic density: CDF F(E) = 1 / (1 + exp(-(E - mu) / kT))
+  auto cdf = [&](double E) { return 1.0 / (1.0 + exp(-(E - mu) / kT)); };
+  const double F0 = cdf(t->h_tasks[task0].E), F1 = cdf(t->h_tasks[task1 - 1].E);
+  const double window = F1 - F0;
+  DeviceGuard g(ctx->device);
+  const size_t nf = 3 * (size_t)(M - 1) + 5;
+  unsigned long long* d_tally = nullptr;
+  CUDA_TRY(ctx, dalloc(&d_tally, nf, ctx->stream, nullptr));
+  cudaError_t e = cudaMemsetAsync(d_tally, 0, sizeof(unsigned long long) * nf, ctx->stream);
+  if (e == cudaSuccess && window > 0.0) {
+    ProfScope ps(ctx, "thermal_walk_kernel");
+    e = negf::launch_thermal_walk(t->d_tasks, task0, M, wire, t->d_tab, t->d_mode_tab, t->d_c,
+                                  start_lead, seed, walkers, walker_id_offset, max_steps, mu, kT,
+                                  F0, window, d_tally, d_lead, d_steps, d_interval, d_a,
+                                  ctx->sm_count, ctx->stream);
+  }
+  std::vector<unsigned long long> h(nf, 0ull);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h.data(), d_tally, sizeof(unsigned long long) * nf,
+                        cudaMemcpyDeviceToHost, ctx->stream);
+  cudaFreeAsync(d_tally, ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess)
+    return fail(ctx, NEGF_E_CUDA, "negf_walk_thermal: %s", cudaGetErrorString(e));
+  st = check_device(ctx, t);
+  if (st != NEGF_OK) return st;
+  // X = c_i + alpha (c_{i+1} - c_i) for walkers absorbed at q; alpha = a / 2^32 and
+  // alpha^2 ~ (a >> 16)^2 / 2^32 from the integer sums
+  std::vector<double> c(M);
+  for (int k = 0; k < M; ++k)
+    CUDA_TRY(ctx, cudaMemcpy(&c[k], t->d_c + 2 * (task0 + k) + start_lead, sizeof(double),
+                             cudaMemcpyDeviceToHost));
+  double S1 = 0.0, S2 = 0.0;
+  for (int i = 0; i < M - 1; ++i) {
+    const double nq = (double)h[3 * i], sa = (double)h[3 * i + 1] * 0x1p-32,
+                 sa2 = (double)h[3 * i + 2] * 0x1p-32;
+    const double ci = c[i] > 0.0 ? c[i] : 0.0, dc = (c[i + 1] > 0.0 ? c[i + 1] : 0.0) - ci;
+    S1 += nq * ci + sa * dc;
+    S2 += nq * ci * ci + 2.0 * ci * dc * sa + dc * dc * sa2;
+  }
+  const size_t G0 = 3 * (size_t)(M - 1);
+  const double N = (double)walkers;
+  const double mean = N > 0 ? S1 / N : 0.0;
+  const double var = N > 0 ? std::max(0.0, S2 / N - mean * mean) : 0.0;
+  out->G = window * mean;
+  out->se = N > 0 ? window * sqrt(var / N) : 0.0;
+  out->window = window;
+  out->mean_steps = N > 0 ? (double)h[G0 + 4] / N : 0.0;
+  out->walkers = walkers;
+  out->absorbed[0] = h[G0 + 0];
+  out->absorbed[1] = h[G0 + 1];
+  out->closed = h[G0 + 2];
+  out->truncated = h[G0 + 3];
+  if (out->truncated)
+    return fail(ctx, NEGF_E_STEPCAP, "negf_walk_thermal: %llu walks reached max_steps",
+                (unsigned long long)out->truncated);
+  return NEGF_OK;
+}
+
 }  // extern "C"
 
 // ------------------------------------------------------------------------------------------

@@ -66,6 +66,12 @@ class negf_plan_tuning(C.Structure):
                 ("chain_ms", C.c_float), ("alias_ms", C.c_float)]
 
 
+class negf_thermal_result(C.Structure):
+    _fields_ = [("G", C.c_double), ("se", C.c_double), ("window", C.c_double),
+                ("mean_steps", C.c_double), ("walkers", C.c_uint64),
+                ("absorbed", C.c_uint64 * 2), ("closed", C.c_uint64), ("truncated", C.c_uint64)]
+
+
 def library_path():
     return _build.LIB
 
@@ -125,6 +131,8 @@ def load():
         "negf_plan_device_bytes": (U64, [P]),
         "negf_plan_destroy": (None, [P]),
         "negf_profile_read": (I32, [P, I32, P, P, P, C.POINTER(I32)]),
+        "negf_walk_thermal": (I32, [P, P, I32, I32, U64, U64, U64, D, D, U32, P, P, P, P,
+                                    C.POINTER(negf_thermal_result)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -287,6 +295,24 @@ def negf_walk_trace(ctx, tables, task, start_lead, seed, walker_id_offset, d_lea
     _check(ctx, load().negf_walk_trace(ctx, tables, int(task), int(start_lead), int(seed),
                                        int(walker_id_offset), n, int(max_steps), _ptr(d_lead),
                                        _ptr(d_steps)))
+
+
+def negf_walk_thermal(ctx, tables, wire, start_lead, seed, walkers, mu, kT,
+                      walker_id_offset=0, max_steps=1 << 20, trace=None):
+    """Linear conductance G_qp (units e^2/h) with energies drawn from the thermal window and
+    transition probabilities interpolated on wire ``wire``'s energy grid.  trace: optional dict
+    of torch CUDA tensors 'lead' (int32), 'steps' (int32), 'interval' (int32), 'a' (int32,
+    read as uint32) of ``walkers`` entries each."""
+    out = negf_thermal_result()
+    tr = trace or {}
+    st = load().negf_walk_thermal(ctx, tables, int(wire), int(start_lead), int(seed),
+                                  int(walkers), int(walker_id_offset), float(mu), float(kT),
+                                  int(max_steps), _ptr(tr.get("lead")), _ptr(tr.get("steps")),
+                                  _ptr(tr.get("interval")), _ptr(tr.get("a")), C.byref(out))
+    _check(ctx, st, allow=(NEGF_E_STEPCAP,))
+    return dict(G=out.G, se=out.se, window=out.window, mean_steps=out.mean_steps,
+                walkers=out.walkers, absorbed=(out.absorbed[0], out.absorbed[1]),
+                closed=out.closed, truncated=out.truncated, stepcap=st == NEGF_E_STEPCAP)
 
 
 def negf_tally_counts(ctx, tally, n_tasks):

@@ -64,9 +64,11 @@ def test_struct_layouts_match_header(lib_path):
     #include <stddef.h>
     #include "negf.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(negf_wire), offsetof(negf_wire, gamma_lead),
-             sizeof(negf_build_opts), sizeof(negf_task_info), sizeof(negf_run_opts),
-             offsetof(negf_run_opts, walk_blocks_per_sm), sizeof(negf_plan_tuning));
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(negf_wire),
+             offsetof(negf_wire, gamma_lead), sizeof(negf_build_opts), sizeof(negf_task_info),
+             sizeof(negf_run_opts), offsetof(negf_run_opts, walk_blocks_per_sm),
+             sizeof(negf_plan_tuning), sizeof(negf_thermal_result),
+             offsetof(negf_thermal_result, truncated));
       return 0;
     }'''
     with tempfile.TemporaryDirectory() as d:
@@ -79,7 +81,8 @@ def test_struct_layouts_match_header(lib_path):
     assert sizes == [ctypes.sizeof(negf.negf_wire), negf.negf_wire.gamma_lead.offset,
                      ctypes.sizeof(negf.negf_build_opts), ctypes.sizeof(negf.negf_task_info),
                      ctypes.sizeof(negf.negf_run_opts), negf.negf_run_opts.walk_blocks_per_sm.offset,
-                     ctypes.sizeof(negf.negf_plan_tuning)]
+                     ctypes.sizeof(negf.negf_plan_tuning), ctypes.sizeof(negf.negf_thermal_result),
+                     negf.negf_thermal_result.truncated.offset]
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
