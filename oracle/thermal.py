@@ -23,8 +23,9 @@ Here the energies are restricted to the span [E_0, E_{M-1}] of a grid on which t
 
 Random numbers of walker ``wid`` in wire ``wire`` (seed -> key (lo, hi)), Philox4x32-10 block
 b with counter (b, wid_lo, wid_hi, 0x80000000 | wire):
-  block 0: (x0, x1) -> u = (((x0 << 32 | x1) >> 11) + 1/2) / 2^53, the energy
-           E = F^-1(F(E_0) + u (F(E_{M-1}) - F(E_0))); x2 picks the injection table
+  block 0: (x0, x1) -> u = (((x0 << 32 | x1) >> 11) + 1/2) / 2^53, the energy's CDF value
+           F = F(E_0) + u (F(E_{M-1}) - F(E_0)) (its interval: F(E_i) <= F < F(E_{i+1})) and
+           E = F^-1(F); x2 picks the injection table
            (E_{i+1}'s iff x2 < a, a = min(floor(alpha 2^32), 2^32 - 1));
   block 1: the injection mode draw (x0, x1) on the picked table's mode row;
   block b >= 2: transition b - 1: (x0, x1) on the current row of the table picked by x2 < a.
@@ -60,9 +61,11 @@ def energy_draw(x0, x1, grid, mu, kT):
     grid = np.asarray(grid, dtype=np.float64)
     v = ((x0.astype(np.uint64) << np.uint64(32)) | x1.astype(np.uint64)) >> np.uint64(11)
     u = (v.astype(np.float64) + 0.5) / 2.0 ** 53
-    F0, F1 = th_cdf(grid[0], mu, kT), th_cdf(grid[-1], mu, kT)
-    E = th_inverse(F0 + u * (F1 - F0), mu, kT)
-    i = np.clip(np.searchsorted(grid, E, side="right") - 1, 0, grid.size - 2)
+    F = th_cdf(grid, mu, kT)
+    pE = F[0] + u * (F[-1] - F[0])
+    E = th_inverse(pE, mu, kT)
+    # the interval: the CDF value placed among the grid's CDF values (F is increasing)
+    i = np.clip(np.searchsorted(F, pE, side="right") - 1, 0, grid.size - 2)
     alpha = np.clip((E - grid[i]) / (grid[i + 1] - grid[i]), 0.0, 1.0)
     a = np.minimum(np.floor(alpha * TWO32), TWO32 - 1).astype(np.uint64)
     return E, i, a

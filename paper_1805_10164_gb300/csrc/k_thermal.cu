@@ -10,7 +10,8 @@
 // integers, from which the host forms the mean and variance of the score exactly.
 //
 // Random numbers (Philox4x32-10, counter (b, id_lo, id_hi, 0x80000000 | wire)): block 0 -> the
-// energy (x0, x1) and the injection table (x2); block 1 -> the injection mode (x0, x1); block
+// energy (x0, x1: its CDF value, placed among the grid's CDF values for the interval) and the
+// injection table (x2); block 1 -> the injection mode (x0, x1); block
 // b >= 2 -> transition b - 1, (x0, x1) on the row and x2 < a for the table.  One thread per
 // walker (grid-stride); the block's tally sits in shared memory and is added to global memory
 // once.
@@ -29,13 +30,20 @@ __device__ __forceinline__ void smem_add64(unsigned* lohi, unsigned v) {
   const unsigned old = atomicAdd(lohi, v);
   if (old + v < old) atomicAdd(lohi + 1, 1u);
 }
+// 64-bit add to a shared counter kept as two 32-bit words
+__device__ __forceinline__ void add64(unsigned* lohi, uint64_t v) {
+  if (v == 0) return;
+  smem_add64(lohi, (unsigned)v);
+  if (v >> 32) atomicAdd(lohi + 1, (unsigned)(v >> 32));
+}
 
 __global__ void __launch_bounds__(kThermalThreads) thermal_walk_kernel(
     const TaskDesc* __restrict__ tasks, int task0, int M, uint32_t wire,
     const uint64_t* __restrict__ tab, const uint64_t* __restrict__ mode_tab,
     const double* __restrict__ cvals, int p, PhiloxKey key, uint64_t walkers, uint64_t id_offset,
     uint32_t max_steps, double mu, double kT, double F0, double window,
-    unsigned long long* __restrict__ tally, int32_t* __restrict__ t_lead,
+    const double* __restrict__ Fg, unsigned long long* __restrict__ tally,
+    int32_t* __restrict__ t_lead,
     uint32_t* __restrict__ t_steps, int32_t* __restrict__ t_interval, uint32_t* __restrict__ t_a) {
   // shared tally: per interval (absorbed at q, sum a, sum (a >> 16)^2), then absorbed L, R,
   // closed, truncated, steps; each a 64-bit counter kept as two 32-bit words
@@ -49,25 +57,28 @@ __global__ void __launch_bounds__(kThermalThreads) thermal_walk_kernel(
   const TaskDesc& d0 = tasks[task0];
   const uint32_t n = (uint32_t)d0.n, W = (uint32_t)d0.W, K = (uint32_t)d0.K;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  uint64_t my_abs0 = 0, my_abs1 = 0, my_closed = 0, my_trunc = 0, my_steps = 0;
   for (uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; g < walkers; g += stride) {
     const uint64_t wid = id_offset + g;
     const uint32_t lo = (uint32_t)wid, hi = (uint32_t)(wid >> 32);
     const uint4 r0 = philox4x32_10(make_uint4(0u, lo, hi, ctr3), key);
     const uint64_t v = (((uint64_t)r0.x << 32) | r0.y) >> 11;
     const double u = ((double)v + 0.5) * 0x1p-53;
-    const double pE = F0 + u * window;
-    const double E = mu + kT * log(pE / (1.0 - pE));
-    int lo_i = 0, hi_i = M - 1;                       // last grid index with E_e <= E
+    const double pE = F0 + u * window;                // F(E) of the drawn energy
+    int lo_i = 0, hi_i = M - 1;                       // last grid index with F(E_e) <= F(E)
     while (lo_i < hi_i) {
       const int mid = (lo_i + hi_i + 1) >> 1;
-      if (tasks[task0 + mid].E <= E) lo_i = mid; else hi_i = mid - 1;
+      if (Fg[mid] <= pE) lo_i = mid; else hi_i = mid - 1;
     }
     const int iv = lo_i < M - 2 ? lo_i : M - 2;
-    const double Ei = tasks[task0 + iv].E, Ej = tasks[task0 + iv + 1].E;
-    double alpha = (E - Ei) / (Ej - Ei);
-    alpha = alpha < 0.0 ? 0.0 : (alpha > 1.0 ? 1.0 : alpha);
-    const double af = floor(alpha * 4294967296.0);
-    const uint32_t a = af >= 4294967295.0 ? 0xffffffffu : (uint32_t)af;
+    // E - E_i = kT ln(F / (1 - F)) - (E_i - mu): the logarithms in FP32 of F and 1 - F (the
+    // latter formed in FP64, so that both keep their relative precision); alpha to ~2^-20
+    const float lnr = logf((float)pE) - logf((float)(1.0 - pE));
+    const float dE = (float)kT * lnr - (float)(tasks[task0 + iv].E - mu);
+    float alpha = dE / (float)(tasks[task0 + iv + 1].E - tasks[task0 + iv].E);
+    alpha = alpha < 0.f ? 0.f : (alpha > 1.f ? 1.f : alpha);
+    const float af = floorf(alpha * 4294967296.f);
+    const uint32_t a = af >= 4294967295.f ? 0xffffffffu : (uint32_t)af;
     // an interval open at both ends mixes the two tables; one open at a single end walks with
     // that end's table alone (a chain without an open lead never absorbs)
     const bool open_lo = cvals[2 * (task0 + iv) + p] > 0.0;
@@ -97,21 +108,38 @@ __global__ void __launch_bounds__(kThermalThreads) thermal_walk_kernel(
         row = j;
       }
     }
-    if (outcome == q) {
-      smem_add64(&s_t[2 * (3 * iv + 0)], 1u);
-      smem_add64(&s_t[2 * (3 * iv + 1)], a);
-      const uint32_t a16 = a >> 16;
-      smem_add64(&s_t[2 * (3 * iv + 2)], a16 * a16);
+    // per-interval sums: lanes with the same interval pool theirs and one of them adds them
+    {
+      const unsigned act = __activemask();
+      const int key_iv = outcome == q ? iv : -1;
+      const unsigned grp = __match_any_sync(act, key_iv);
+      if (key_iv >= 0) {
+        const uint32_t a16 = a >> 16, sq = a16 * a16;
+        const uint32_t cnt = __popc(grp);
+        const uint32_t a_hi = __reduce_add_sync(grp, a >> 16), a_lo = __reduce_add_sync(grp, a & 0xffffu);
+        const uint32_t s_hi = __reduce_add_sync(grp, sq >> 16), s_lo = __reduce_add_sync(grp, sq & 0xffffu);
+        if ((threadIdx.x & 31) == __ffs(grp) - 1) {
+          smem_add64(&s_t[2 * (3 * iv + 0)], cnt);
+          add64(&s_t[2 * (3 * iv + 1)], ((uint64_t)a_hi << 16) + a_lo);
+          add64(&s_t[2 * (3 * iv + 2)], ((uint64_t)s_hi << 16) + s_lo);
+        }
+      }
     }
-    if (outcome >= 0) smem_add64(&s_t[2 * (G0 + outcome)], 1u);
-    else if (outcome == -1) smem_add64(&s_t[2 * (G0 + 2)], 1u);
-    else smem_add64(&s_t[2 * (G0 + 3)], 1u);
-    smem_add64(&s_t[2 * (G0 + 4)], steps);
+    if (outcome == 0) ++my_abs0;
+    else if (outcome == 1) ++my_abs1;
+    else if (outcome == -1) ++my_closed;
+    else ++my_trunc;
+    my_steps += steps;
     if (t_lead) t_lead[g] = outcome;
     if (t_steps) t_steps[g] = steps;
     if (t_interval) t_interval[g] = iv;
     if (t_a) t_a[g] = a;
   }
+  add64(&s_t[2 * (G0 + 0)], my_abs0);
+  add64(&s_t[2 * (G0 + 1)], my_abs1);
+  add64(&s_t[2 * (G0 + 2)], my_closed);
+  add64(&s_t[2 * (G0 + 3)], my_trunc);
+  add64(&s_t[2 * (G0 + 4)], my_steps);
   __syncthreads();
   for (int f = threadIdx.x; f < n_fields; f += blockDim.x) {
     const unsigned long long v = ((unsigned long long)s_t[2 * f + 1] << 32) | s_t[2 * f];
@@ -126,9 +154,9 @@ cudaError_t launch_thermal_walk(const TaskDesc* d_tasks, int task0, int M, int w
                                 const double* d_c, int start_lead, uint64_t seed,
                                 uint64_t walkers, uint64_t id_offset, uint32_t max_steps,
                                 double mu, double kT, double F0, double window,
-                                unsigned long long* d_tally, int32_t* d_lead, uint32_t* d_steps,
-                                int32_t* d_interval, uint32_t* d_a, int sm_count,
-                                cudaStream_t s) {
+                                const double* d_Fg, unsigned long long* d_tally, int32_t* d_lead,
+                                uint32_t* d_steps, int32_t* d_interval, uint32_t* d_a,
+                                int sm_count, cudaStream_t s) {
   if (walkers == 0 || M < 2) return cudaSuccess;
   const PhiloxKey key{(uint32_t)seed, (uint32_t)(seed >> 32)};
   const size_t smem = sizeof(unsigned) * 2 * (size_t)(3 * (M - 1) + 5);
@@ -137,7 +165,7 @@ cudaError_t launch_thermal_walk(const TaskDesc* d_tasks, int task0, int M, int w
   if (blocks > need) blocks = need;
   thermal_walk_kernel<<<(unsigned)blocks, kThermalThreads, smem, s>>>(
       d_tasks, task0, M, (uint32_t)wire, d_tab, d_mode_tab, d_c, start_lead, key, walkers,
-      id_offset, max_steps, mu, kT, F0, window, d_tally, d_lead, d_steps, d_interval, d_a);
+      id_offset, max_steps, mu, kT, F0, window, d_Fg, d_tally, d_lead, d_steps, d_interval, d_a);
   return cudaGetLastError();
 }
 

@@ -1649,14 +1649,21 @@ negf_status negf_walk_thermal(negf_ctx ctx, negf_tables t, int32_t wire, int32_t
   const double window = F1 - F0;
   DeviceGuard g(ctx->device);
   const size_t nf = 3 * (size_t)(M - 1) + 5;
+  // one allocation: the tally, then the grid's CDF values
+  std::vector<double> Fg(M);
+  for (int k = 0; k < M; ++k) Fg[k] = cdf(t->h_tasks[task0 + k].E);
   unsigned long long* d_tally = nullptr;
-  CUDA_TRY(ctx, dalloc(&d_tally, nf, ctx->stream, nullptr));
+  CUDA_TRY(ctx, dalloc(&d_tally, nf + M, ctx->stream, nullptr));
+  const double* d_Fg = reinterpret_cast<const double*>(d_tally + nf);
   cudaError_t e = cudaMemsetAsync(d_tally, 0, sizeof(unsigned long long) * nf, ctx->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_tally + nf, Fg.data(), sizeof(double) * M, cudaMemcpyHostToDevice,
+                        ctx->stream);
   if (e == cudaSuccess && window > 0.0) {
     ProfScope ps(ctx, "thermal_walk_kernel");
     e = negf::launch_thermal_walk(t->d_tasks, task0, M, wire, t->d_tab, t->d_mode_tab, t->d_c,
                                   start_lead, seed, walkers, walker_id_offset, max_steps, mu, kT,
-                                  F0, window, d_tally, d_lead, d_steps, d_interval, d_a,
+                                  F0, window, d_Fg, d_tally, d_lead, d_steps, d_interval, d_a,
                                   ctx->sm_count, ctx->stream);
   }
   std::vector<unsigned long long> h(nf, 0ull);
