@@ -251,10 +251,14 @@ def run_gpu(args):
                                      tasks_per_wave=args.plan_tasks_per_wave, autotune=True)
         tuning = negf.negf_plan_get_tuning(plan)
 
-    def one_step(step_idx, wires, memspace, prec=prec):
+    def one_step(step_idx, wires, memspace, prec=prec, end_event=None):
+        """One step; `end_event` (if given) is recorded on the stream once the step's device work
+        is enqueued, before the host reads the results (the host path is timed by e2e)."""
         wid0 = ndist.weak_walker_offset(rank, step_idx, N)
         if plan is not None and memspace == "device" and prec == plan_prec:
             negf.negf_plan_launch(ctx, plan, args.seed, wid0)
+            if end_event is not None:
+                end_event.record(stream)
             r = negf.negf_plan_result(ctx, plan)
             return r, r["counts"]
         if args.mode in ("pipeline", "graph"):
@@ -272,6 +276,8 @@ def run_gpu(args):
             tally = negf.negf_walk(ctx, tables, 0, args.seed, N, walker_id_offset=wid0,
                                    max_steps=args.max_steps)
         res = negf.negf_current(ctx, tables, tally, wl.mu_p, wl.mu_q, wl.kT)
+        if end_event is not None:
+            end_event.record(stream)
         counts = negf.negf_tally_counts(ctx, tally, n_tasks)
         negf.negf_tally_free(tally)
         negf.negf_tables_free(tables)
@@ -292,8 +298,7 @@ def run_gpu(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res, counts = one_step(i, dev_wires, "device")
-        e1.record(stream)
+        res, counts = one_step(i, dev_wires, "device", end_event=e1)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
         tot_steps += int(counts[:, 4].sum())
@@ -455,8 +460,7 @@ def time_precision(prec, one_step, dev_wires, negf, ctx, stream, flush, args, st
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res, _ = one_step(41_000 + i, dev_wires, "device", prec)
-        e1.record(stream)
+        res, _ = one_step(41_000 + i, dev_wires, "device", prec, end_event=e1)
         e1.synchronize()
         tot += e0.elapsed_time(e1)
     prof = negf.negf_profile_read(ctx)
