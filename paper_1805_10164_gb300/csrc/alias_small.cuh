@@ -131,15 +131,20 @@ namespace negf {
 // The same construction with the slot units kept in u[0..k) (shared memory of the caller):
 // u is filled with u_i, and every slot's entry then overwrites its own u_i (a slot's u is read
 // before its entry is written).  Same entries as alias_small.  *total receives the fixed-point
-// sum T 2^-sh of the weights (within k 2^-32 of the largest weight below the exact sum).
+// sum T 2^-sh of the weights (within k 2^-32 of the largest weight below the exact sum), *sum64
+// (if given) their FP64 sum in index order.  The weights may live in u's memory (each row's
+// weights packed from its start): every weight is read before u overwrites it.
 template <typename R, typename Get>
-__device__ bool alias_small_inplace(int k, Get wget, uint64_t* u, double* total) {
+__device__ bool alias_small_inplace(int k, Get wget, uint64_t* u, double* total,
+                                    double* sum64 = nullptr) {
   constexpr uint64_t kSlot = 1ull << 32;
   bool ok = true;
   R wmax = 0;
   int imax = 0;
+  double s64 = 0.0;
   for (int i = 0; i < k; ++i) {
     const R v = wget(i);
+    s64 += (double)v;
     if (!(v >= (R)0) || !isfinite(v)) {
       ok = false;
     } else if (v > wmax) {
@@ -147,6 +152,7 @@ __device__ bool alias_small_inplace(int k, Get wget, uint64_t* u, double* total)
       imax = i;
     }
   }
+  if (sum64) *sum64 = s64;
   if (!(wmax > (R)0)) {
     for (int i = 0; i < k; ++i) u[i] = small_pack(0xffffffffu, (uint32_t)i);
     *total = 0.0;
@@ -156,7 +162,9 @@ __device__ bool alias_small_inplace(int k, Get wget, uint64_t* u, double* total)
   frexp((double)wmax, &e);
   const int sh = 32 - e;
   uint64_t T = 0;
-  for (int i = 0; i < k; ++i) {
+  // descending, so that u may share its memory with the weights: u[i] covers bytes [8i, 8i + 8)
+  // of the row, which hold weights of index >= i, all read by then
+  for (int i = k - 1; i >= 0; --i) {
     const R v = wget(i);
     const uint64_t m = (v >= (R)0 && isfinite(v)) ? (uint64_t)small_fixp(v, sh) : 0ull;
     u[i] = m;

@@ -335,8 +335,9 @@ __global__ void alias_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
 
 // One warp per table row of a two-level task.  The row is taken in chunks of 32 slices: the
 // chunk's weights are staged in shared memory by coalesced loads, each lane builds one slice's
-// level-1 weight (FP64 sum) and level-2 alias row in shared memory, and the chunk's entries
-// (32 consecutive level-2 rows) leave by coalesced stores.
+// level-1 weight and level-2 alias row in shared memory (in the memory of the slice's weights,
+// which it reads first), and the chunk's entries (32 consecutive level-2 rows) leave by
+// coalesced stores.
 constexpr int kTlWarps = 4;
 constexpr int kTlPitch = 65;                         // padded slice pitch (W <= 64)
 
@@ -346,9 +347,9 @@ __global__ void __launch_bounds__(32 * kTlWarps) two_level_kernel(
     uint64_t* __restrict__ tab, int32_t* err) {
   extern __shared__ __align__(16) unsigned char tl_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // one buffer per warp: slice s's weights, then its units and entries, at s * kTlPitch u64
   uint64_t* so = reinterpret_cast<uint64_t*>(tl_smem) + (size_t)warp * 32 * kTlPitch;
-  R* sw = reinterpret_cast<R*>(reinterpret_cast<uint64_t*>(tl_smem) + (size_t)kTlWarps * 32 * kTlPitch) +
-          (size_t)warp * 32 * kTlPitch;
+  auto sw = [&](int slice) { return reinterpret_cast<R*>(so + (size_t)slice * kTlPitch); };
   const uint32_t job = blockIdx.x * kTlWarps + warp;
   if (job >= n_jobs) return;
   int lo = 0, hi = n_tasks - 1;
@@ -368,17 +369,15 @@ __global__ void __launch_bounds__(32 * kTlWarps) two_level_kernel(
   for (int k0 = 0; k0 < L; k0 += 32) {
     const int ns = min(32, L - k0);
     const R* wc = wr + (uint64_t)k0 * W;
-    for (int i = lane; i < ns * W; i += 32) sw[(i / W) * kTlPitch + (i % W)] = wc[i];
+    for (int i = lane; i < ns * W; i += 32) sw(i / W)[i % W] = wc[i];
     __syncwarp();
     if (lane < ns) {
-      const R* ws = sw + lane * kTlPitch;
-      double S = 0.0;
-      ok &= alias_small_inplace<R>(W, [&](int i) { return ws[i]; }, so + lane * kTlPitch, &S);
-      if (sizeof(R) == 8) {            // FP64 tables: the FP64 sum
-        S = 0.0;
-        for (int a = 0; a < W; ++a) S += (double)ws[a];
-      }
-      l1[k0 + lane] = (R)S;            // FP32 tables: the exact fixed-point sum
+      const R* ws = sw(lane);
+      double S = 0.0, S64 = 0.0;
+      ok &= alias_small_inplace<R>(W, [&](int i) { return ws[i]; }, so + lane * kTlPitch, &S,
+                                   &S64);
+      // FP64 tables: the FP64 sum; FP32 tables: the exact fixed-point sum
+      l1[k0 + lane] = (R)(sizeof(R) == 8 ? S64 : S);
     }
     __syncwarp();
     uint64_t* oc = l2 + (uint64_t)k0 * W;
@@ -402,14 +401,14 @@ cudaError_t launch_two_level_split(const TaskDesc* d_tasks, int n_tasks, uint32_
   const size_t stage = (size_t)kTlWarps * 32 * kTlPitch;      // entries per staging array
   cudaError_t e;
   if (precision == NEGF_FP64) {
-    const size_t smem = stage * (sizeof(uint64_t) + sizeof(double));
+    const size_t smem = stage * sizeof(uint64_t);
     e = cudaFuncSetAttribute(two_level_kernel<double>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     two_level_kernel<double><<<blocks, 32 * kTlWarps, smem, s>>>(
         d_tasks, n_tasks, n_jobs, static_cast<double*>(d_weights), d_tab, d_err);
   } else {
-    const size_t smem = stage * (sizeof(uint64_t) + sizeof(float));
+    const size_t smem = stage * sizeof(uint64_t);
     e = cudaFuncSetAttribute(two_level_kernel<float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
