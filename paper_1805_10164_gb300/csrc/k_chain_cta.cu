@@ -169,21 +169,241 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
   }
 }
 
+// ---- 16 < W <= 32: the same recursion with the pair's 2W columns side by side --------------
+// One CTA of 128 threads per job (four CTAs fit an SM): X_k [W][2W] = (-t g_k) [W][W] X_{k+1}
+// in shared memory, thread (ty, tx) = (t / 16, t mod 16) owning the outputs a = ty + 8 i,
+// b' = tx + 16 j.  g_{k-1} (or g_{k+1}) comes into registers while step k multiplies, so the
+// step's only wait on global memory is hidden behind its products.
+constexpr int kNThreads = 128;
+constexpr int kNMax = 32;
+constexpr size_t kNSmem = sizeof(cf) * (kNMax * kNMax + 2 * kNMax * 2 * kNMax) +
+                          sizeof(float) * 2 * kNMax * (kNMax + 1);
+
+template <int W>
+__device__ __forceinline__ void chain_cta_narrow_body(const TaskDesc& d, const TcJob& job,
+                                                      const float* __restrict__ eta32,
+                                                      const float* __restrict__ phi32,
+                                                      const double* __restrict__ gam,
+                                                      const cf* __restrict__ gL,
+                                                      const cf* __restrict__ gR,
+                                                      const cf* __restrict__ start,
+                                                      float* __restrict__ weights,
+                                                      unsigned char* smem) {
+  constexpr int N = 2 * W;                    // the pair's columns
+  constexpr int RI = (W + 7) / 8;             // output rows a = ty + 8 i
+  constexpr int CJ = (N + 15) / 16;           // output columns b' = tx + 16 j
+  constexpr int WP = W + 1;                   // padded row of the weight staging
+  constexpr int kPre = (W * W + kNThreads - 1) / kNThreads;
+  cf* Gs = reinterpret_cast<cf*>(smem);                    // [a][c] (-t g_k); Phi at the edges
+  cf* Xa = Gs + kNMax * kNMax;                             // [c][b'] ping
+  cf* Xb = Xa + 2 * kNMax * kNMax;                         // [c][b'] pong
+  float* Wt = reinterpret_cast<float*>(Xb + 2 * kNMax * kNMax);   // [b'][a] weights staging
+
+  const int tid = threadIdx.x;
+  const int L = d.L, n = d.n, K = d.K;
+  const int dir = job.dir;
+  auto m0_of = [&](int yy) { return yy < L ? yy : (yy == L ? 0 : L - 1); };
+  const int ys[2] = {job.y0, job.y1};
+  const float mt = (float)(-d.t);
+  const float* eta = eta32 + d.onsite_off / 2;
+  const cf* gsrc = (dir == 0 ? gL : gR) + d.g_off;
+  float* wt = weights + d.wt_off;
+  auto row_of = [&](int y, int b) -> uint64_t {
+    return y < L ? (uint64_t)y * W + b : (uint64_t)n + (uint64_t)(y - L) * W + b;
+  };
+  auto load_start = [&](cf* X, int col) {
+    const cf* st = start + d.start_off + (uint64_t)ys[col] * W * W;
+    for (int i = tid; i < W * W; i += kNThreads) {
+      const int c = i / W, b = i - c * W;
+      X[c * N + col * W + b] = st[i];
+    }
+  };
+  auto emit = [&](const cf* X, int k, unsigned mask) {
+    for (int i = tid; i < N * W; i += kNThreads) {
+      const int a = i / N, r = i - a * N;                  // r consecutive across threads
+      const cf v = X[a * N + r];
+      Wt[r * WP + a] = eta[k * W + a] * (v.x * v.x + v.y * v.y);
+    }
+    __syncthreads();
+    for (int i = tid; i < N * W; i += kNThreads) {
+      const int r = i / W, a = i - r * W;                  // a consecutive: coalesced rows
+      const int col = r / W;
+      if (mask & (1u << col))
+        wt[row_of(ys[col], r - col * W) * K + (uint64_t)k * W + a] = Wt[r * WP + a];
+    }
+    if (k == 0 || k == L - 1) {
+      // lead weights sum_nu Gamma_nu |(Phi^T X)_nu b'|^2: Phi (FP32) staged in Gs, free outside
+      // the product; two threads per column, each half of the modes
+      float* phis = reinterpret_cast<float*>(Gs);
+      float* gams = phis + W * W;
+      __syncthreads();
+      for (int i = tid; i < W * W; i += kNThreads) phis[i] = phi32[d.phi_off + i];
+      for (int i = tid; i < W; i += kNThreads) gams[i] = (float)gam[d.lead_off + i];
+      __syncthreads();
+      const int r = tid % 64, h = tid / 64;
+      if (r < N) {
+        float part = 0.f;
+        for (int nu = h * (W / 2); nu < (h ? W : W / 2); ++nu) {
+          float zr = 0.f, zi = 0.f;
+#pragma unroll 8
+          for (int a = 0; a < W; ++a) {
+            const float p = phis[a * W + nu];
+            const cf v = X[a * N + r];
+            zr += p * v.x;
+            zi += p * v.y;
+          }
+          part += gams[nu] * (zr * zr + zi * zi);
+        }
+        Wt[r * WP + h] = part;                             // staging is free again
+      }
+      __syncthreads();
+      if (h == 0 && r < N) {
+        const int col = r / W;
+        if (mask & (1u << col)) {
+          const float lw = Wt[r * WP] + Wt[r * WP + 1];
+          const uint64_t base = row_of(ys[col], r - col * W) * K + n;
+          if (k == 0) wt[base] = lw;
+          if (k == L - 1) wt[base + 1] = lw;
+        }
+      }
+    }
+    __syncthreads();
+  };
+
+  unsigned have = 0;
+  for (int col = 0; col < 2; ++col)
+    if (ys[col] >= 0) have |= 1u << col;
+  if (dir == 0) {
+    for (int col = 0; col < 2; ++col) {
+      if (!(have & (1u << col))) continue;
+      load_start(Xa, col);
+      __syncthreads();
+      emit(Xa, m0_of(ys[col]), 1u << col);
+    }
+  }
+  const int m0a = m0_of(job.y0), m0b = job.y1 >= 0 ? m0_of(job.y1) : m0a;
+  const int k_first = dir == 0 ? max(m0a, m0b) - 1 : min(m0a, m0b) + 1;
+  const int k_end = dir == 0 ? -1 : L;
+  const int kstep = dir == 0 ? -1 : 1;
+  cf gp[kPre];
+  auto fetch = [&](int k) {
+    const cf* gk = gsrc + (uint64_t)k * W * W;
+#pragma unroll
+    for (int r = 0; r < kPre; ++r) {
+      const int i = tid + kNThreads * r;
+      if (i < W * W) gp[r] = gk[i];
+    }
+  };
+  if (k_first != k_end) fetch(k_first);
+  cf* Xc = Xa;
+  cf* Xn = Xb;
+  const int ty = tid / 16, tx = tid % 16;
+  for (int k = k_first; k != k_end; k += kstep) {
+    unsigned active = 0;
+    for (int col = 0; col < 2; ++col) {
+      if (!(have & (1u << col))) continue;
+      const int m0 = m0_of(ys[col]);
+      if (dir == 0 ? k < m0 : k > m0) active |= 1u << col;
+      if (dir == 0 ? k == m0 - 1 : k == m0 + 1) load_start(Xc, col);
+    }
+#pragma unroll
+    for (int r = 0; r < kPre; ++r) {
+      const int i = tid + kNThreads * r;
+      if (i < W * W) Gs[i] = cf{mt * gp[r].x, mt * gp[r].y};
+    }
+    __syncthreads();
+    if (k + kstep != k_end) fetch(k + kstep);
+    float accr[RI][CJ], acci[RI][CJ];
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+      for (int j = 0; j < CJ; ++j) accr[i][j] = acci[i][j] = 0.f;
+    // rows a >= W and columns b' >= N read in-bounds shared memory (a < 32, c N + b' < 64 W)
+    // and are never stored
+#pragma unroll 4
+    for (int c = 0; c < W; ++c) {
+      cf g[RI], x[CJ];
+#pragma unroll
+      for (int i = 0; i < RI; ++i) g[i] = Gs[(ty + 8 * i) * W + c];
+#pragma unroll
+      for (int j = 0; j < CJ; ++j) x[j] = Xc[c * N + tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < RI; ++i)
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) {
+          accr[i][j] = fmaf(g[i].x, x[j].x, accr[i][j]);
+          accr[i][j] = fmaf(-g[i].y, x[j].y, accr[i][j]);
+          acci[i][j] = fmaf(g[i].x, x[j].y, acci[i][j]);
+          acci[i][j] = fmaf(g[i].y, x[j].x, acci[i][j]);
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < RI; ++i)
+#pragma unroll
+      for (int j = 0; j < CJ; ++j) {
+        const int a = ty + 8 * i, b = tx + 16 * j;
+        if ((RI * 8 == W || a < W) && (CJ * 16 == N || b < N))
+          Xn[a * N + b] = cf{accr[i][j], acci[i][j]};
+      }
+    __syncthreads();
+    if (active) emit(Xn, k, active);
+    cf* tmp = Xc;
+    Xc = Xn;
+    Xn = tmp;
+  }
+}
+
+__global__ void __launch_bounds__(kNThreads, 4) chain_cta_narrow_kernel(
+    const TaskDesc* __restrict__ tasks, const TcJob* __restrict__ jobs,
+    const float* __restrict__ eta32, const float* __restrict__ phi32,
+    const double* __restrict__ gam, const cf* __restrict__ gL, const cf* __restrict__ gR,
+    const cf* __restrict__ start, float* __restrict__ weights) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const TcJob job = jobs[blockIdx.x];
+  const TaskDesc d = tasks[job.task];
+#define NEGF_CN_CASE(w)                                                                       \
+  case w:                                                                                     \
+    chain_cta_narrow_body<w>(d, job, eta32, phi32, gam, gL, gR, start, weights, smem);        \
+    break;
+  switch (d.W) {
+    NEGF_CN_CASE(17) NEGF_CN_CASE(18) NEGF_CN_CASE(19) NEGF_CN_CASE(20)
+    NEGF_CN_CASE(21) NEGF_CN_CASE(22) NEGF_CN_CASE(23) NEGF_CN_CASE(24)
+    NEGF_CN_CASE(25) NEGF_CN_CASE(26) NEGF_CN_CASE(27) NEGF_CN_CASE(28)
+    NEGF_CN_CASE(29) NEGF_CN_CASE(30) NEGF_CN_CASE(31) NEGF_CN_CASE(32)
+    default: break;
+  }
+#undef NEGF_CN_CASE
+}
+
 }  // namespace
 
-cudaError_t launch_chain_cta(const TaskDesc* d_tasks, const TcJob* d_jobs, uint32_t n_jobs,
-                             const float* d_eta32, const float* d_phi32, const double* d_gam,
-                             const void* d_gL, const void* d_gR, const void* d_start,
-                             void* d_weights, cudaStream_t s) {
-  if (n_jobs == 0) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(chain_cta_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem);
-  if (e != cudaSuccess) return e;
-  chain_cta_kernel<<<n_jobs, kThreads, kSmem, s>>>(
-      d_tasks, d_jobs, d_eta32, d_phi32, d_gam, static_cast<const cf*>(d_gL),
-      static_cast<const cf*>(d_gR), static_cast<const cf*>(d_start),
-      static_cast<float*>(d_weights));
-  return cudaGetLastError();
+cudaError_t launch_chain_cta(const TaskDesc* d_tasks, const TcJob* d_jobs, uint32_t n_wide,
+                             uint32_t n_narrow, const float* d_eta32, const float* d_phi32,
+                             const double* d_gam, const void* d_gL, const void* d_gR,
+                             const void* d_start, void* d_weights, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  if (n_wide) {
+    e = cudaFuncSetAttribute(chain_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kSmem);
+    if (e != cudaSuccess) return e;
+    chain_cta_kernel<<<n_wide, kThreads, kSmem, s>>>(
+        d_tasks, d_jobs, d_eta32, d_phi32, d_gam, static_cast<const cf*>(d_gL),
+        static_cast<const cf*>(d_gR), static_cast<const cf*>(d_start),
+        static_cast<float*>(d_weights));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  if (n_narrow) {
+    e = cudaFuncSetAttribute(chain_cta_narrow_kernel,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kNSmem);
+    if (e != cudaSuccess) return e;
+    chain_cta_narrow_kernel<<<n_narrow, kNThreads, kNSmem, s>>>(
+        d_tasks, d_jobs + n_wide, d_eta32, d_phi32, d_gam, static_cast<const cf*>(d_gL),
+        static_cast<const cf*>(d_gR), static_cast<const cf*>(d_start),
+        static_cast<float*>(d_weights));
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 }  // namespace negf

@@ -424,7 +424,7 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
       d.gamma_lead = wr.gamma_lead;
       d.layout = layout;
       d.fused = tc_wire ? 1 : 0;
-      d.cta_chain = (fp32 && wr.W == 64 && !tc_wire) ? 1 : 0;
+      d.cta_chain = (fp32 && (wr.W == 64 || (wr.W > 16 && wr.W <= 32)) && !tc_wire) ? 1 : 0;
       d.tab_off = tab_off;
       d.wt_off = wt_off;
       if (tc_wire) {
@@ -498,7 +498,9 @@ struct Wave {
   std::vector<TaskDesc> desc;
   std::vector<TaskDesc> adesc;       // alias_descs(desc)
   std::vector<TcJob> tcjobs;         // tensor-core chain jobs (task = index into desc), then
-  size_t n_tc = 0;                   // the CTA-chain jobs: tcjobs[n_tc ..]
+  size_t n_tc = 0;                   // the CTA-chain jobs: tcjobs[n_tc ..], those of W = 64
+  size_t n_cta_wide = 0;             // tasks first
+  uint32_t cta_narrow() const { return (uint32_t)(tcjobs.size() - n_tc - n_cta_wide); }
 };
 
 // Jobs of the tensor-core chain for fused task `k` (index in its wave): direction 0 takes every
@@ -520,7 +522,7 @@ void add_tc_jobs(std::vector<TcJob>& jobs, int k, int L) {
 
 Wave make_wave(const Plan& P, int t0, int t1) {
   Wave w;
-  std::vector<TcJob> cta;
+  std::vector<TcJob> cta, cta_n;
   w.t0 = t0;
   w.t1 = t1;
   for (int k = t0; k < t1; ++k) {
@@ -536,7 +538,7 @@ Wave make_wave(const Plan& P, int t0, int t1) {
       w.edge += (uint64_t)(d.L + 2) * 2 * d.W * d.W;
       add_tc_jobs(w.tcjobs, k - t0, d.L);
     }
-    if (d.cta_chain) add_tc_jobs(cta, k - t0, d.L);
+    if (d.cta_chain) add_tc_jobs(d.W == 64 ? cta : cta_n, k - t0, d.L);
     if (d.layout == NEGF_LAYOUT_TWO_LEVEL) {
       d.l1_off = w.tab + (uint64_t)d.rows * d.n;
       d.l1w_off = w.l1w;                 // rebased past the wave's weights below
@@ -570,8 +572,11 @@ Wave make_wave(const Plan& P, int t0, int t1) {
   auto by_len = [&](const TcJob& x, const TcJob& y) { return len(x) > len(y); };
   std::stable_sort(w.tcjobs.begin(), w.tcjobs.end(), by_len);
   std::stable_sort(cta.begin(), cta.end(), by_len);
+  std::stable_sort(cta_n.begin(), cta_n.end(), by_len);
   w.n_tc = w.tcjobs.size();
+  w.n_cta_wide = cta.size();
   w.tcjobs.insert(w.tcjobs.end(), cta.begin(), cta.end());
+  w.tcjobs.insert(w.tcjobs.end(), cta_n.begin(), cta_n.end());
   return w;
 }
 
@@ -729,8 +734,8 @@ negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& 
   }
   if (e == cudaSuccess && w.tcjobs.size() > w.n_tc) {
     ProfScope ps(ctx, "chain_cta_kernel", 1, s);
-    e = negf::launch_chain_cta(d_wdesc, d_tcjobs + w.n_tc, (uint32_t)(w.tcjobs.size() - w.n_tc),
-                               q.d_eta32, reinterpret_cast<const float*>(q.d_phi + P.phi_total),
+    e = negf::launch_chain_cta(d_wdesc, d_tcjobs + w.n_tc, (uint32_t)w.n_cta_wide,
+                               w.cta_narrow(), q.d_eta32, reinterpret_cast<const float*>(q.d_phi + P.phi_total),
                                q.d_gam, d_gL, d_gR, d_start, d_weights, s);
   }
   if (e == cudaSuccess && w.n_tc) {
@@ -1895,8 +1900,8 @@ negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
     if (wv.tcjobs.size() > wv.n_tc) {
       SegScope sg(p, "chain_cta_kernel", 1, s, timed);
       CUDA_TRY(ctx, negf::launch_chain_cta(
-                        dd, p->d_tcjobs + p->job_off[w] + wv.n_tc,
-                        (uint32_t)(wv.tcjobs.size() - wv.n_tc), q.d_eta32,
+                        dd, p->d_tcjobs + p->job_off[w] + wv.n_tc, (uint32_t)wv.n_cta_wide,
+                        wv.cta_narrow(), q.d_eta32,
                         reinterpret_cast<const float*>(q.d_phi + P.phi_total), q.d_gam, p->d_gL,
                         p->d_gR, p->d_start[slot], p->d_weights[slot], s));
     }
@@ -1996,8 +2001,8 @@ negf_status plan_autotune(negf_plan p) {
   auto columns_split = [&](int cw) {
     cudaError_t e = columns(cw);
     if (e == cudaSuccess && wv.tcjobs.size() > wv.n_tc)
-      e = negf::launch_chain_cta(dd, p->d_tcjobs + wv.n_tc,
-                                 (uint32_t)(wv.tcjobs.size() - wv.n_tc), q.d_eta32,
+      e = negf::launch_chain_cta(dd, p->d_tcjobs + wv.n_tc, (uint32_t)wv.n_cta_wide,
+                                 wv.cta_narrow(), q.d_eta32,
                                  reinterpret_cast<const float*>(q.d_phi + P.phi_total), q.d_gam,
                                  p->d_gL, p->d_gR, p->d_start[0], p->d_weights[0], s);
     if (e == cudaSuccess && wv.n_tc)

@@ -39,7 +39,7 @@ struct TaskDesc {
   uint64_t l1_off;       // two-level: level-1 entries [rows][L + 2] (level 2 is at tab_off)
   uint64_t l1w_off;      // two-level: level-1 weights [rows][L + 2] in the weights array
   uint64_t edge_off;     // fused: slice-0 and slice-(L-1) blocks [L + 2][2][W][W] complex64
-  int32_t cta_chain;     // block columns by the CTA-wide FP32 kernel (W = 64), weights kept
+  int32_t cta_chain;     // block columns by a CTA-wide FP32 kernel (W = 64 or 16 < W <= 32)
   int32_t pad_;
 };
 
@@ -125,12 +125,13 @@ cudaError_t launch_chain_tc(const TaskDesc* d_tasks, int n_tasks, uint32_t n_col
                             const float* d_phi32, const double* d_gam, const void* d_gL,
                             const void* d_gR, const void* d_start, void* d_weights,
                             uint64_t* d_tab, void* d_edge, int32_t* d_err, cudaStream_t s);
-// CTA-wide FP32 block columns of cta_chain tasks (W = 64): the Step 6' weights of every row,
-// lead weights included, as chain_kernel writes them.  Jobs as for launch_chain_tc.
-cudaError_t launch_chain_cta(const TaskDesc* d_tasks, const TcJob* d_jobs, uint32_t n_jobs,
-                             const float* d_eta32, const float* d_phi32, const double* d_gam,
-                             const void* d_gL, const void* d_gR, const void* d_start,
-                             void* d_weights, cudaStream_t s);
+// CTA-wide FP32 block columns of cta_chain tasks: the Step 6' weights of every row, lead
+// weights included, as chain_kernel writes them.  Jobs as for launch_chain_tc: the n_wide jobs
+// of W = 64 tasks, then the n_narrow jobs of 16 < W <= 32 tasks.
+cudaError_t launch_chain_cta(const TaskDesc* d_tasks, const TcJob* d_jobs, uint32_t n_wide,
+                             uint32_t n_narrow, const float* d_eta32, const float* d_phi32,
+                             const double* d_gam, const void* d_gL, const void* d_gR,
+                             const void* d_start, void* d_weights, cudaStream_t s);
 // Warps per CTA the alias kernel can use for rows of max_K slots (shared memory bound).
 int alias_warps_max(int max_K);
 // Two-level tasks: from the weights [rows][K] of every table row, the level-1 weights (slice

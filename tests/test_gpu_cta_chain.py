@@ -1,7 +1,8 @@
-"""FP32 block columns of W = 64 wires by the CTA-wide kernel (chain_cta_kernel) against the
-oracle: weights elementwise within 1e-5 of the row sum (the FP32 table bar), one-level and
-two-level tables, lead weights at both boundary slices, and bit-exact walks on the exported
-tables."""
+"""FP32 block columns by the CTA-wide kernels against the oracle: W = 64 wires
+(chain_cta_kernel) and 16 < W <= 32 wires (chain_cta_narrow_kernel, odd and even widths, both
+ends of the range, ragged lengths down to L = 1).  Bars: weights elementwise within 1e-5 of
+the row sum (the FP32 table bar), one-level and two-level tables, lead weights at both boundary
+slices, and bit-exact walks on the exported tables."""
 import numpy as np
 import pytest
 
@@ -23,7 +24,17 @@ def ctx():
     negf.negf_destroy(c)
 
 
-def _wires():
+def _wires(kind):
+    if kind == "narrow":
+        return [inputs.small_wire(151, W=17, L=1, n_energy=1, eta=0.05, disorder=0.5),
+                inputs.small_wire(152, W=20, L=7, n_energy=2, eta=0.03, disorder=0.8,
+                                  e_lo=-1.5, e_hi=1.2),
+                inputs.small_wire(153, W=25, L=2, n_energy=1, eta=0.1, disorder=0.5),
+                inputs.small_wire(154, W=31, L=12, n_energy=1, eta=0.01, disorder=0.5,
+                                  e_lo=0.41, e_hi=0.41),
+                inputs.small_wire(155, W=32, L=5, n_energy=1, eta=0.08, lead_model=1,
+                                  gamma_lead=0.7),
+                inputs.small_wire(156, W=24, L=9, n_energy=1, eta=0.05, disorder=1.0)]
     return [inputs.small_wire(141, W=64, L=1, n_energy=1, eta=0.05, disorder=0.5),
             inputs.small_wire(142, W=64, L=3, n_energy=2, eta=0.02, disorder=0.5, e_lo=-1.0,
                               e_hi=1.0),
@@ -32,9 +43,9 @@ def _wires():
             inputs.small_wire(144, W=64, L=6, n_energy=1, eta=0.1, lead_model=1, gamma_lead=0.8)]
 
 
-@pytest.fixture(scope="module")
-def batch(ctx):
-    wires = _wires()
+@pytest.fixture(scope="module", params=["wide", "narrow"])
+def batch(ctx, request):
+    wires = _wires(request.param)
     refs = []
     for w in wires:
         for E in w.energy:
