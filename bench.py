@@ -41,6 +41,8 @@ def workload(name, energies=0):
         wl = inputs.chain_l20()
     elif name == "wire_16x100":
         wl = inputs.wire_16x100(precision="fp32")
+    elif name == "wire_32x100":
+        wl = inputs.wire_32x100()
     elif name == "wire_64x100":
         wl = inputs.wire_64x100()
     elif name == "wire_64x1000":

@@ -144,7 +144,7 @@ __device__ bool alias_small_inplace(int k, Get wget, uint64_t* u, double* total,
   double s64 = 0.0;
   for (int i = 0; i < k; ++i) {
     const R v = wget(i);
-    s64 += (double)v;
+    if (sum64) s64 += (double)v;
     if (!(v >= (R)0) || !isfinite(v)) {
       ok = false;
     } else if (v > wmax) {

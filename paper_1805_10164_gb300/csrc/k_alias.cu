@@ -366,22 +366,37 @@ __global__ void __launch_bounds__(32 * kTlWarps) two_level_kernel(
   R* l1 = weights + d.l1w_off + (uint64_t)row * (L + 2);
   uint64_t* l2 = tab + d.tab_off + (uint64_t)row * n;
   bool ok = true;
+  const int dq = 32 / W, dr = 32 - (32 / W) * W;
   for (int k0 = 0; k0 < L; k0 += 32) {
     const int ns = min(32, L - k0);
     const R* wc = wr + (uint64_t)k0 * W;
-    for (int i = lane; i < ns * W; i += 32) sw(i / W)[i % W] = wc[i];
+    // element i = lane + 32 j of the chunk is entry r of slice q; (q, r) advance by (dq, dr)
+    int q = lane / W, r = lane - (lane / W) * W;
+    for (int i = lane; i < ns * W; i += 32) {
+      sw(q)[r] = wc[i];
+      q += dq;
+      r += dr;
+      if (r >= W) { r -= W; ++q; }
+    }
     __syncwarp();
     if (lane < ns) {
       const R* ws = sw(lane);
       double S = 0.0, S64 = 0.0;
-      ok &= alias_small_inplace<R>(W, [&](int i) { return ws[i]; }, so + lane * kTlPitch, &S,
-                                   &S64);
       // FP64 tables: the FP64 sum; FP32 tables: the exact fixed-point sum
+      ok &= alias_small_inplace<R>(W, [&](int i) { return ws[i]; }, so + lane * kTlPitch, &S,
+                                   sizeof(R) == 8 ? &S64 : nullptr);
       l1[k0 + lane] = (R)(sizeof(R) == 8 ? S64 : S);
     }
     __syncwarp();
     uint64_t* oc = l2 + (uint64_t)k0 * W;
-    for (int i = lane; i < ns * W; i += 32) oc[i] = so[(i / W) * kTlPitch + (i % W)];
+    q = lane / W;
+    r = lane - q * W;
+    for (int i = lane; i < ns * W; i += 32) {
+      oc[i] = so[q * kTlPitch + r];
+      q += dq;
+      r += dr;
+      if (r >= W) { r -= W; ++q; }
+    }
     __syncwarp();
   }
   if (lane == 0) {

@@ -101,6 +101,16 @@ def wire_64x1000(seed=4, n_energy=256, precision="split_tf32", walkers=32_000_00
                     seed, meta=dict(steps_per_task=100_000_000))
 
 
+def wire_32x100(seed=6, n_energy=8, precision="fp32", walkers=1_000_000):
+    """W = 32 x L = 100, onsite U[-1, 1], eta = 0.05, 8 energies: slices as wide as the widest
+    of the batched wires, on a case small enough for full ncu captures (tables ~0.7 GB)."""
+    rng = np.random.default_rng(seed)
+    E, wE = midpoint_grid(-3.5, 3.5, n_energy)
+    w = random_wire(rng, 32, 100, 1.0, 1.0, 0.05, E, wE)
+    return Workload("wire_W32_L100_eta0.05_8E", [w], walkers, 3.5, -3.5, 0.025, precision,
+                    seed)
+
+
 def wire_64x100(seed=5, n_energy=8, precision="split_tf32", walkers=1_000_000):
     """W = 64 x L = 100, onsite U[-0.5, 0.5], eta = 0.005, 8 energies: the wide-slice kernels
     on a case small enough for full ncu captures (tables ~0.7 GB)."""
