@@ -88,25 +88,39 @@ __global__ void lead_modes_kernel(const TaskDesc* __restrict__ tasks, int n_task
   }
 }
 
-// ---- CTA-wide sweep (any W <= 64; complex128, and complex64 above W = 16) ------------------
-// One CTA of kSweepCtaThreads threads per (task, direction); the slice block sits in shared memory
-// and is inverted in place by Gauss-Jordan (no augmented identity):
+// ---- CTA-wide inversions (any W <= 64; complex128, and complex64 above W = 16) -------------
+// cta_gj: the slice block sits in shared memory and is inverted in place by Gauss-Jordan (no
+// augmented identity):
 //   pivot k:  a_kk <- 1/a_kk;  a_kj <- a_kj / a_kk;  a_ik <- -a_ik / a_kk;
 //             a_ij <- a_ij - (a_ik / a_kk) a_kj            (i, j != k)
 // with two barriers per pivot: the pivot row and the multipliers a_ik / a_kk are copied out,
 // then every thread updates its entries.  Thread t owns column t mod W of rows t / W, t / W + R,
 // ... (R = threads / W), so that a warp touches consecutive entries of one row.  On a
 // slice where every site dephases no pivot search is needed (see gj_rows); otherwise rows are
-// interchanged by partial pivoting and the inverse's columns unscrambled at the end.  The next
-// slice's matrix E - H - Sigma_s - t^2 g_k is built in place while g_k is stored.
+// interchanged by partial pivoting and the inverse's columns unscrambled at the end.  The
+// diagonal blocks use it, and the sweeps on slices with an undephased site.
+//
+// The complex64 sweeps above W = 16 (rgf_sweep_cta_kernel) run it on the block in shared
+// memory with 1024 threads.  The complex128 sweeps (rgf_sweep_rows_kernel) keep the block in
+// registers instead: thread t owns column j = t mod W of rows g, g + RG, g + 2 RG, ...
+// (g = t / W, RG = ceil(W / RPT) row groups of at most RPT rows), and a pivot costs one
+// barrier: the owners of row k publish it, the owners of column k publish that column, and the
+// owner of a_kk publishes 1/a_kk, into one of two buffers (alternating with k, so that the next
+// pivot's writes cannot overtake this pivot's reads); then every thread updates its rows.  On
+// GB300's FP64 pipe the arithmetic of a pivot dominates, and this form computes the reciprocal
+// once per pivot instead of once per thread.  The next slice's matrix E - H - Sigma_s - t^2 g_k
+// is formed in the same registers while g_k is stored.
 constexpr int kSweepThreads = 256;       // diagonal blocks: many CTAs
-constexpr int kSweepCtaThreads = 1024;   // sweeps: few serial chains, so each gets a whole SM
+constexpr int kSweepCtaThreads = 1024;   // complex64 sweeps: few serial chains, one CTA per SM
+constexpr int kSweepRowsThreads = 256;   // complex128 sweeps
+constexpr int kSweepRegMaxW = 16;        // complex64 sweeps up to this width: one warp each
 
 template <typename C>
-__host__ __device__ inline size_t sweep_cta_bytes(int W) {
-  // A W x W | pivot row W | multipliers W (complex) | phi W x W double | perm W, flag (int)
-  return sizeof(C) * (size_t)(W * W + 2 * W) + sizeof(double) * (size_t)(W * W) +
-         sizeof(int) * (size_t)(W + 2);
+__host__ __device__ inline size_t sweep_rows_bytes(int W) {
+  // A W x W | pivot rows 2 x 64 | pivot columns 2 x 64 | 1/pivot 2 (complex) | phi W x W
+  // double | perm 64, flag (int)
+  return sizeof(C) * (size_t)(W * W + 4 * 64 + 2) + sizeof(double) * (size_t)(W * W) +
+         sizeof(int) * (size_t)(64 + 2);
 }
 
 // E - H_kk - Sigma_s(k) entry (a, b) of slice k, in the precision of C
@@ -196,12 +210,176 @@ __device__ bool cta_gj(C* A, C* rowk, C* fcol, int* perm, int* flag, int W, bool
   return true;
 }
 
+// In-place inverse of the register-held block (see above; no pivot search: the caller takes
+// it on slices where every site dephases, gj_rows says why that is safe).  i_m = g + RG m are
+// this thread's rows, valid while i_m < W; false (uniformly) on a zero or non-finite pivot.
+template <typename C, int RPT>
+__device__ bool gj_regcols(C (&a)[RPT], int W, int RG, int g, int j, bool own, C* rowk,
+                           C* fcol, C* sinv) {
+  int kr = 0, km = 0;                       // pivot k = kr + RG km: its row group and slot
+  for (int k = 0; k < W; ++k) {
+    const int b = k & 1;
+    C* rk = rowk + 64 * b;
+    C* fc = fcol + 64 * b;
+    if (own && g == kr) {
+      C v = a[0];
+#pragma unroll
+      for (int m = 1; m < RPT; ++m)
+        if (m == km) v = a[m];
+      rk[j] = v;
+      if (j == k) sinv[b] = cdiv(mkc(1.0, 0.0, C{}), v);
+    }
+    if (own && j == k) {
+#pragma unroll
+      for (int m = 0; m < RPT; ++m)
+        if (g + RG * m < W) fc[g + RG * m] = a[m];
+    }
+    __syncthreads();
+    const C inv = sinv[b];
+    if (!finite_c(inv)) return false;       // every thread reads the same value
+    if (own) {
+      if (j != k) {
+        const C t = rk[j] * inv;            // a_kj / a_kk
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+          const int i = g + RG * m;
+          if (i < W) {
+            const C v = a[m] - fc[i] * t;
+            a[m] = i == k ? t : v;
+          }
+        }
+      } else {
+#pragma unroll
+        for (int m = 0; m < RPT; ++m) {
+          const int i = g + RG * m;
+          if (i < W) {
+            const C v = mkc(0.0, 0.0, C{}) - fc[i] * inv;
+            a[m] = i == k ? inv : v;
+          }
+        }
+      }
+    }
+    if (++kr == RG) {
+      kr = 0;
+      ++km;
+    }
+  }
+  return true;
+}
+
+template <typename C, int RPT>
+__device__ __forceinline__ void sweep_rows_body(const TaskDesc& d, int dir,
+                                               const double* __restrict__ wire,
+                                               const double* __restrict__ phig,
+                                               const cd* __restrict__ sig, C* gL, C* gR,
+                                               int32_t* err, unsigned char* smem_raw) {
+  using R = typename Real<C>::T;
+  const int W = d.W, L = d.L, WW = W * W;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  const int RG = (W + RPT - 1) / RPT;
+  const int j = tid % W, g = tid / W;
+  const bool own = g < RG;
+  C* A = reinterpret_cast<C*>(smem_raw);   // the block, for the pivoted inversion only
+  C* rowk = A + WW;
+  C* fcol = rowk + 2 * 64;
+  C* sinv = fcol + 2 * 64;
+  double* phi = reinterpret_cast<double*>(sinv + 2);
+  int* perm = reinterpret_cast<int*>(phi + WW);
+  int* flag = perm + 64;
+  const double* onsite = wire + d.onsite_off;
+  const double* eta = onsite + d.n;
+  const cd* sg = sig + d.lead_off;
+  for (int idx = tid; idx < WW; idx += nth) phi[idx] = phig[d.phi_off + idx];
+  __syncthreads();
+  // first slice of the sweep: E - H - Sigma_s - Phi diag(sigma) Phi^T (the lead block in FP64)
+  const int kf = dir == 0 ? 0 : L - 1;
+  C a[RPT];
+#pragma unroll
+  for (int m = 0; m < RPT; ++m) {
+    const int i = g + RG * m;
+    a[m] = mkc(0.0, 0.0, C{});
+    if (own && i < W) {
+      cd acc = mk(0.0, 0.0);
+      for (int q = 0; q < W; ++q) acc = acc + (phi[i * W + q] * phi[j * W + q]) * sg[q];
+      a[m] = slice_entry<C>(i, j, kf, W, d.E, d.t, onsite, eta) - to_c(acc, C{});
+    }
+  }
+  C* out = dir == 0 ? gL : gR;
+  const R tt = (R)(d.t * d.t);
+  for (int s = 0; s < L - 1; ++s) {
+    const int k = dir == 0 ? s : L - 1 - s;
+    const bool deph = __syncthreads_and(tid >= W || eta[k * W + tid] > 0.0);
+    bool ok;
+    if (deph) {
+      ok = gj_regcols<C, RPT>(a, W, RG, g, j, own, rowk, fcol, sinv);
+    } else {
+      // an undephased site: partial pivoting on the block in shared memory
+#pragma unroll
+      for (int m = 0; m < RPT; ++m)
+        if (own && g + RG * m < W) A[(g + RG * m) * W + j] = a[m];
+      __syncthreads();
+      ok = cta_gj(A, rowk, fcol, perm, flag, W, true);
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < RPT; ++m)
+        if (own && g + RG * m < W) a[m] = A[(g + RG * m) * W + j];
+    }
+    if (!ok) {
+      if (tid == 0) atomicOr(err, ERR_SINGULAR);
+      return;
+    }
+    // store g_k; form the next slice: E - H - Sigma_s - t^2 g_k
+    C* dst = out + d.g_off + (uint64_t)k * WW;
+    const bool more = s + 1 < L - 1;
+    const int kn = dir == 0 ? s + 1 : L - 2 - s;
+    bool bad = false;
+#pragma unroll
+    for (int m = 0; m < RPT; ++m) {
+      const int i = g + RG * m;
+      if (own && i < W) {
+        const C v = a[m];
+        dst[i * W + j] = v;
+        bad |= !finite_c(v);
+        if (more) a[m] = slice_entry<C>(i, j, kn, W, d.E, d.t, onsite, eta) - tt * v;
+      }
+    }
+    if (__syncthreads_or(bad) && tid == 0) atomicOr(err, ERR_NONFINITE);
+  }
+}
+
+__global__ void __launch_bounds__(kSweepRowsThreads) rgf_sweep_rows_kernel(
+    const TaskDesc* __restrict__ tasks, int n_tasks, const double* __restrict__ wire,
+    const double* __restrict__ phig, const cd* __restrict__ sig, cd* gL, cd* gR, int32_t* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int job = blockIdx.x;
+  if (job >= 2 * n_tasks) return;
+  const TaskDesc d = tasks[job >> 1];
+  const int dir = job & 1;
+  if (d.L < 2 || d.W > 64) return;
+  // rows per thread: W <= 16 -> 4, W <= 32 -> 8, W <= 64 -> 16 (at most 4 row groups, so that
+  // kSweepRowsThreads = 256 threads cover every width)
+  if (d.W <= 16)
+    sweep_rows_body<cd, 4>(d, dir, wire, phig, sig, gL, gR, err, smem_raw);
+  else if (d.W <= 32)
+    sweep_rows_body<cd, 8>(d, dir, wire, phig, sig, gL, gR, err, smem_raw);
+  else
+    sweep_rows_body<cd, 16>(d, dir, wire, phig, sig, gL, gR, err, smem_raw);
+}
+
 template <typename C>
+__host__ __device__ inline size_t sweep_smem_bytes(int W) {
+  // A W x W | pivot row W | multipliers W (complex) | phi W x W double | perm W, flag (int)
+  return sizeof(C) * (size_t)(W * W + 2 * W) + sizeof(double) * (size_t)(W * W) +
+         sizeof(int) * (size_t)(W + 2);
+}
+
+// complex64 sweeps of width min_W .. 64 with the block in shared memory (cta_gj)
 __global__ void __launch_bounds__(kSweepCtaThreads) rgf_sweep_cta_kernel(
     const TaskDesc* __restrict__ tasks, int n_tasks, const double* __restrict__ wire,
-    const double* __restrict__ phig, const cd* __restrict__ sig, C* gL, C* gR, int32_t* err,
+    const double* __restrict__ phig, const cd* __restrict__ sig, cf* gL, cf* gR, int32_t* err,
     int min_W) {
-  using R = typename Real<C>::T;
+  using C = cf;
+  using R = float;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int job = blockIdx.x;
   if (job >= 2 * n_tasks) return;
@@ -515,7 +693,7 @@ struct SweepReg {
   __device__ __forceinline__ static void run(A... a) { sweep_reg_body<W>(a...); }
 };
 
-// One warp per (task, direction), tasks of width W <= 16.
+// One warp per (task, direction), tasks of width W <= kSweepRegMaxW.
 __global__ void rgf_sweep_reg_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
                                      const double* __restrict__ wire,
                                      const double* __restrict__ phig, const cd* __restrict__ sig,
@@ -929,37 +1107,37 @@ cudaError_t sweep_impl<cf>(const TaskDesc* d_tasks, int n_tasks, int max_W,
                            const double* d_wire, const double* d_phi, const cd* d_sig, cf* d_gL,
                            cf* d_gR, int32_t* d_err, cudaStream_t s);
 
-template <typename C>
-cudaError_t sweep_smem(const TaskDesc* d_tasks, int n_tasks, int max_W, const double* d_wire,
-                       const double* d_phi, const cd* d_sig, C* d_gL, C* d_gR, int32_t* d_err,
-                       cudaStream_t s) {
-  // one CTA per sweep: each sweep is a serial chain of W x W inversions, spread one per SM
-  const size_t smem = sweep_cta_bytes<C>(max_W);
-  cudaError_t e = cudaFuncSetAttribute(rgf_sweep_cta_kernel<C>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  rgf_sweep_cta_kernel<C><<<2 * n_tasks, kSweepCtaThreads, smem, s>>>(
-      d_tasks, n_tasks, d_wire, d_phi, d_sig, d_gL, d_gR, d_err, sizeof(C) == sizeof(cf) ? 17 : 1);
-  return cudaGetLastError();
-}
-
 template <>
 cudaError_t sweep_impl<cd>(const TaskDesc* d_tasks, int n_tasks, int max_W,
                            const double* d_wire, const double* d_phi, const cd* d_sig, cd* d_gL,
                            cd* d_gR, int32_t* d_err, cudaStream_t s) {
-  return sweep_smem<cd>(d_tasks, n_tasks, max_W, d_wire, d_phi, d_sig, d_gL, d_gR, d_err, s);
+  // one CTA per sweep: each sweep is a serial chain of W x W inversions, spread one per SM
+  const size_t smem = sweep_rows_bytes<cd>(max_W);
+  cudaError_t e = cudaFuncSetAttribute(rgf_sweep_rows_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  rgf_sweep_rows_kernel<<<2 * n_tasks, kSweepRowsThreads, smem, s>>>(
+      d_tasks, n_tasks, d_wire, d_phi, d_sig, d_gL, d_gR, d_err);
+  return cudaGetLastError();
 }
 
 template <>
 cudaError_t sweep_impl<cf>(const TaskDesc* d_tasks, int n_tasks, int max_W,
                            const double* d_wire, const double* d_phi, const cd* d_sig, cf* d_gL,
                            cf* d_gR, int32_t* d_err, cudaStream_t s) {
-  // register kernel for the tasks of width <= 16 (it skips wider ones), CTA kernel for the rest
+  // one warp per sweep for the tasks of width <= 32 (it skips wider ones), a CTA per sweep for
+  // the rest
   rgf_sweep_reg_kernel<<<2 * n_tasks, 32, 0, s>>>(d_tasks, n_tasks, d_wire, d_phi, d_sig, d_gL,
                                                   d_gR, d_err);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || max_W <= 16) return e;
-  return sweep_smem<cf>(d_tasks, n_tasks, max_W, d_wire, d_phi, d_sig, d_gL, d_gR, d_err, s);
+  if (e != cudaSuccess || max_W <= kSweepRegMaxW) return e;
+  const size_t smem = sweep_smem_bytes<cf>(max_W);
+  e = cudaFuncSetAttribute(rgf_sweep_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem);
+  if (e != cudaSuccess) return e;
+  rgf_sweep_cta_kernel<<<2 * n_tasks, kSweepCtaThreads, smem, s>>>(
+      d_tasks, n_tasks, d_wire, d_phi, d_sig, d_gL, d_gR, d_err, kSweepRegMaxW + 1);
+  return cudaGetLastError();
 }
 
 template <typename C>
