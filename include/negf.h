@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define NEGF_ABI_VERSION 2
+#define NEGF_ABI_VERSION 3
 #define NEGF_MAX_W 64            /* widest supported slice (sites across the wire) */
 #define NEGF_MAX_SITES 6400      /* largest W*L per wire with one-level tables */
 #define NEGF_MAX_SITES_TWO_LEVEL 65536 /* largest W*L per wire with two-level tables */
@@ -256,6 +256,8 @@ typedef struct {
   int32_t alias_warps;          /* warps per CTA of the alias kernel */
   int32_t tuned;                /* 1 when picked by the autotuner */
   float walk_ms, chain_ms, alias_ms;   /* device time of the chosen shapes while tuning */
+  int32_t walk_slots;           /* walks in flight per lane of the walk kernel (1 or 2); 0 =
+                                   by the wave's tables: 2 with two-level tables, else 1 */
 } negf_plan_tuning;
 
 /* A plan is the whole path of negf_run followed by negf_current — lead modes, RGF sweeps,

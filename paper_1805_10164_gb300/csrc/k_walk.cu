@@ -1,21 +1,24 @@
 // Persistent random-walk kernel (Sec. II.D Steps 1-4 with the start lead fixed as in Sec. II.E,
 // and Step 6' of Sec. II.F) and its tally.
 //
-// Each lane owns one walker at a time and keeps its state in registers: task, current table
-// row, draw index s and steps taken.  Draw s takes Philox4x32-10 block s/2 with counter
+// Each walker's state lives in registers: task, current table row, draw index s and steps
+// taken.  Draw s takes Philox4x32-10 block s/2 with counter
 // (s/2, id_lo, id_hi, task) and key (seed_lo, seed_hi), words (x0, x1) for even s, (x2, x3) for
 // odd s (the odd half is cached from the even draw).  Draw 0 picks the injection eigenvector of
 // Gamma_p from the mode alias row (Eq. lead_out_probability); every later draw is one Step 6'
 // transition from the current row: slot c = (x*K)>>32, keep c if y < thr[c] else alias[c].
 // Columns n and n+1 are the leads: drawing one ends the walk, and the sample's estimator is
 // X_pq = Tr[Gamma_p A] delta_rq (Eq. elast_lin_xpq), tallied as counts per absorbing lead.
-// When a walk ends the lane starts the next walker of its own run of consecutive walker indices
-// (32 per lane) with no warp coordination; once enough lanes of a warp have run dry, one lane
-// claims a new range for all of them from a global counter.  Every loop iteration consumes one
-// whole Philox block (two draws: the injection and the first transition for a new walker, two
-// transitions afterwards), so the generator runs warp-uniformly.  Each lane counts its outcomes for
-// its current task in registers and adds them to the block's shared tally when it moves to
-// another task; the block adds its tally to global memory once.
+// A lane carries one or two walkers at a time (kSlots; with two, the dependent gathers of the
+// two walks are in flight together, which pays when the gathers miss L2).  When a walk ends
+// the lane starts the next walker of its own run of consecutive walker indices (32 per lane)
+// with no warp coordination; once enough lanes of a warp have an idle slot and an empty run,
+// one lane claims a new range for all of them from a global counter.  Every loop iteration
+// consumes one whole Philox block per walker (two draws: the injection and the first
+// transition for a new walker, two transitions afterwards), so the generator runs
+// warp-uniformly.  Each lane counts its outcomes for its current task (shared by its slots) in
+// registers and adds them to the block's shared tally when it moves to another task; the block
+// adds its tally to global memory once.
 #include <cuda_runtime.h>
 
 #include "negf_internal.cuh"
@@ -57,8 +60,8 @@ struct ScoreOut {
   unsigned mode_stride;
 };
 
-template <bool kTrace, bool kScore>
-__global__ void __launch_bounds__(kThreads, 5) walk_kernel(
+template <bool kTrace, bool kScore, int kSlotsReq>
+__global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
     const TaskDesc* __restrict__ tasks, int task0, int n_tasks, uint32_t id_base,
     const uint64_t* __restrict__ tab, const uint64_t* __restrict__ mode_tab,
     const double* __restrict__ cvals, int start_lead, PhiloxKey key, uint64_t walkers_per_task,
@@ -81,13 +84,21 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
   const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned long long total = (unsigned long long)n_tasks * walkers_per_task;
 
-  // walker state (registers): b = next Philox block (draws 2b, 2b + 1)
-  bool has = false;
-  unsigned long long g = 0;
-  uint32_t row = 0, b = 0, steps = 0, wid_lo = 0, wid_hi = 0;
+  // kSlots walkers per lane (registers), so that their dependent gathers overlap (one when the
+  // transitions are also replayed for the score tally); b = next Philox block (draws 2b, 2b + 1)
+  constexpr int kSlots = kScore ? 1 : kSlotsReq;
+  bool has[kSlots];
+  unsigned long long g[kSlots];
+  uint32_t row[kSlots], b[kSlots], steps[kSlots], wid_lo[kSlots], wid_hi[kSlots];
+#pragma unroll
+  for (int sl = 0; sl < kSlots; ++sl) {
+    has[sl] = false;
+    g[sl] = 0;
+    row[sl] = b[sl] = steps[sl] = wid_lo[sl] = wid_hi[sl] = 0;
+  }
   // this lane's run of walker indices [r_next, r_end)
   unsigned long long r_next = 0, r_end = 0;
-  // cached task: index window [t_first, t_first + walkers_per_task)
+  // cached task (shared by the slots): index window [t_first, t_first + walkers_per_task)
   int tl = -1;
   unsigned long long t_first = 0;
   uint32_t task_id = 0, K = 0, n = 0, W = 0, inj_row0 = 0, L = 0;
@@ -102,153 +113,176 @@ __global__ void __launch_bounds__(kThreads, 5) walk_kernel(
   bool no_more = false;
 
   while (true) {
-    // ---- start walkers from the lane's own run (closed tasks are consumed on the spot)
-    while (!has && r_next < r_end) {
-      g = r_next++;
-      if (tl < 0 || g - t_first >= walkers_per_task) {
-        if (tl >= 0) flush_lane(s_tally, tl, a);
-        tl = (int)(g / walkers_per_task);
-        t_first = (unsigned long long)tl * walkers_per_task;
-        const TaskDesc& d = tasks[task0 + tl];
-        task_id = id_base + (uint32_t)(task0 + tl);
-        K = (uint32_t)d.K;
-        n = (uint32_t)d.n;
-        W = (uint32_t)d.W;
-        inj_row0 = (uint32_t)(d.n + start_lead * d.W);
-        t_tab_off = d.tab_off;
-        t_mode_off = d.mode_off + start_lead * d.W;
-        trow = tab + d.tab_off;
-        two = d.layout == NEGF_LAYOUT_TWO_LEVEL;
-        L = (uint32_t)d.L;
-        l1row = tab + d.l1_off;
-        mrow = mode_tab + d.mode_off + start_lead * d.W;
-        t_open = cvals[2 * (task0 + tl) + start_lead] > 0.0;
+    // ---- start walkers from the lane's own run (closed tasks are consumed on the spot); a
+    // slot takes a walker of another task only when the other slots are idle
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl) {
+      while (!has[sl] && r_next < r_end) {
+        const unsigned long long gn = r_next;
+        if (tl < 0 || gn - t_first >= walkers_per_task) {
+          bool others = false;
+#pragma unroll
+          for (int o = 0; o < kSlots; ++o)
+            if (o != sl) others |= has[o];
+          if (others) break;
+          if (tl >= 0) flush_lane(s_tally, tl, a);
+          tl = (int)(gn / walkers_per_task);
+          t_first = (unsigned long long)tl * walkers_per_task;
+          const TaskDesc& d = tasks[task0 + tl];
+          task_id = id_base + (uint32_t)(task0 + tl);
+          K = (uint32_t)d.K;
+          n = (uint32_t)d.n;
+          W = (uint32_t)d.W;
+          inj_row0 = (uint32_t)(d.n + start_lead * d.W);
+          t_tab_off = d.tab_off;
+          t_mode_off = d.mode_off + start_lead * d.W;
+          trow = tab + d.tab_off;
+          two = d.layout == NEGF_LAYOUT_TWO_LEVEL;
+          L = (uint32_t)d.L;
+          l1row = tab + d.l1_off;
+          mrow = mode_tab + d.mode_off + start_lead * d.W;
+          t_open = cvals[2 * (task0 + tl) + start_lead] > 0.0;
+        }
+        ++r_next;
+        if (!t_open) {
+          // no open channel in the start lead: nothing to inject (T = 0 exactly)
+          a[0] += 1u;
+          if (kTrace) { trace_lead[gn] = -1; trace_steps[gn] = 0; }
+          continue;
+        }
+        const uint64_t w = id_offset + (gn - t_first);
+        g[sl] = gn;
+        wid_lo[sl] = (uint32_t)w;
+        wid_hi[sl] = (uint32_t)(w >> 32);
+        b[sl] = 0;
+        steps[sl] = 0;
+        has[sl] = true;
       }
-      if (!t_open) {
-        // no open channel in the start lead: nothing to inject (T = 0 exactly)
-        a[0] += 1u;
-        if (kTrace) { trace_lead[g] = -1; trace_steps[g] = 0; }
-        continue;
-      }
-      const uint64_t w = id_offset + (g - t_first);
-      wid_lo = (uint32_t)w;
-      wid_hi = (uint32_t)(w >> 32);
-      b = 0;
-      steps = 0;
-      has = true;
     }
-    // ---- claim new runs once enough lanes are dry (or none has work left)
-    const unsigned dry = __ballot_sync(FULL, !has);
+    bool busy = false, idle = false;
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl) {
+      busy |= has[sl];
+      idle |= !has[sl];
+    }
+    // ---- claim new runs once enough lanes have an idle slot and an empty run (or none has
+    // work left)
+    const unsigned dry = __ballot_sync(FULL, idle && r_next >= r_end);
     if (dry && !no_more && (__popc(dry) >= kClaimMin || dry == FULL)) {
       unsigned long long base = 0;
       if (lane == 0) base = atomicAdd(counter, (unsigned long long)__popc(dry) * kRun);
       base = __shfl_sync(FULL, base, 0);
       if (base >= total) {
         no_more = true;
-      } else if (!has) {
+      } else if (dry & (1u << lane)) {
         const unsigned long long lo = base + (unsigned long long)__popc(dry & lt_mask) * kRun;
         r_next = lo < total ? lo : total;
         r_end = lo + kRun < total ? lo + kRun : total;
       }
       continue;      // start the new walkers first
     }
-    if (dry == FULL) break;           // nothing in flight and nothing left to claim
-    if (!has) continue;
+    if (!__any_sync(FULL, busy)) break;   // nothing in flight and nothing left to claim
+    if (!busy) continue;
 
-    // ---- one Philox block = two draws.  Block 0: the injection draw (Step 4) then the first
-    // transition; later blocks: two Step 6' transitions.
-    const uint4 r = philox4x32_10(make_uint4(b, wid_lo, wid_hi, task_id), key);
-    int outcome = -3;                  // -3: continue, 0/1: absorbed at L/R, -2: truncated
-    if (two) {
-      // two-level tables: block 0 is the injection draw alone; block b >= 1 is transition b,
-      // words (x, y) for the slice or lead (level 1), (z, w) for the site in the slice
-      if (b == 0) {
-        const uint32_t c = __umulhi(r.x, W);
-        const uint64_t e = __ldg(mrow + c);
-        row = inj_row0 + (r.y < (uint32_t)e ? c : (uint32_t)(e >> 32));
-      } else {
-        const uint32_t K1 = L + 2;
-        const uint32_t c = __umulhi(r.x, K1);
-        const uint64_t e = __ldg(l1row + (uint64_t)row * K1 + c);
-        const uint32_t k = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
-        ++steps;
-        if (k >= L) {
-          outcome = (int)(k - L);
-        } else {
-          const uint32_t c2 = __umulhi(r.z, W);
-          const uint64_t e2 = __ldg(trow + ((uint64_t)row * L + k) * W + c2);
-          const uint32_t a = r.w < (uint32_t)e2 ? c2 : (uint32_t)(e2 >> 32);
-          if (steps >= max_steps) outcome = -2;
-          else row = k * W + a;
-        }
-      }
-      ++b;
-    } else {
-    if (b == 0) {
-      const uint32_t c = __umulhi(r.x, W);
-      const uint64_t e = __ldg(mrow + c);
-      row = inj_row0 + (r.y < (uint32_t)e ? c : (uint32_t)(e >> 32));
-    } else {
-      const uint32_t c = __umulhi(r.x, K);
-      const uint64_t e = __ldg(trow + (uint64_t)row * K + c);
-      const uint32_t j = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
-      ++steps;
-      if (j >= n) outcome = (int)(j - n);
-      else if (steps >= max_steps) outcome = -2;
-      else row = j;
-    }
-    if (outcome == -3) {
-      const uint32_t c = __umulhi(r.z, K);
-      const uint64_t e = __ldg(trow + (uint64_t)row * K + c);
-      const uint32_t j = r.w < (uint32_t)e ? c : (uint32_t)(e >> 32);
-      ++steps;
-      if (j >= n) outcome = (int)(j - n);
-      else if (steps >= max_steps) outcome = -2;
-      else row = j;
-    }
-    ++b;
-    }
-    if (kScore && outcome >= 0) {
-      // replay the finished walk and count its transitions under its absorbing lead
-      unsigned long long* cnt = score.cnt + (size_t)outcome * score.stride + t_tab_off;
-      unsigned long long* mcnt = score.mode_cnt + (size_t)outcome * score.mode_stride + t_mode_off;
-      uint32_t rrow = 0;
-      bool live = true;
-      for (uint32_t bb = 0; live; ++bb) {
-        const uint4 q = philox4x32_10(make_uint4(bb, wid_lo, wid_hi, task_id), key);
-        if (bb == 0) {
-          const uint32_t c = __umulhi(q.x, W);
+    // ---- per walking slot one Philox block = two draws.  Block 0: the injection draw (Step 4)
+    // then the first transition; later blocks: two Step 6' transitions.
+#pragma unroll
+    for (int sl = 0; sl < kSlots; ++sl) {
+      if (!has[sl]) continue;
+      const uint4 r = philox4x32_10(make_uint4(b[sl], wid_lo[sl], wid_hi[sl], task_id), key);
+      int outcome = -3;                // -3: continue, 0/1: absorbed at L/R, -2: truncated
+      if (two) {
+        // two-level tables: block 0 is the injection draw alone; block b >= 1 is transition
+        // b, words (x, y) for the slice or lead (level 1), (z, w) for the site in the slice
+        if (b[sl] == 0) {
+          const uint32_t c = __umulhi(r.x, W);
           const uint64_t e = __ldg(mrow + c);
-          const uint32_t mode = q.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
-          atomicAdd(mcnt + mode, 1ull);
-          rrow = inj_row0 + mode;
+          row[sl] = inj_row0 + (r.y < (uint32_t)e ? c : (uint32_t)(e >> 32));
         } else {
-          const uint32_t c = __umulhi(q.x, K);
-          const uint64_t e = __ldg(trow + (uint64_t)rrow * K + c);
-          const uint32_t j = q.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
-          atomicAdd(cnt + (uint64_t)rrow * K + j, 1ull);
-          if (j >= n) live = false;
-          rrow = j;
+          const uint32_t K1 = L + 2;
+          const uint32_t c = __umulhi(r.x, K1);
+          const uint64_t e = __ldg(l1row + (uint64_t)row[sl] * K1 + c);
+          const uint32_t k = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+          ++steps[sl];
+          if (k >= L) {
+            outcome = (int)(k - L);
+          } else {
+            const uint32_t c2 = __umulhi(r.z, W);
+            const uint64_t e2 = __ldg(trow + ((uint64_t)row[sl] * L + k) * W + c2);
+            const uint32_t a2 = r.w < (uint32_t)e2 ? c2 : (uint32_t)(e2 >> 32);
+            if (steps[sl] >= max_steps) outcome = -2;
+            else row[sl] = k * W + a2;
+          }
         }
-        if (live) {
-          const uint32_t c = __umulhi(q.z, K);
-          const uint64_t e = __ldg(trow + (uint64_t)rrow * K + c);
-          const uint32_t j = q.w < (uint32_t)e ? c : (uint32_t)(e >> 32);
-          atomicAdd(cnt + (uint64_t)rrow * K + j, 1ull);
-          if (j >= n) live = false;
-          rrow = j;
+        ++b[sl];
+      } else {
+        if (b[sl] == 0) {
+          const uint32_t c = __umulhi(r.x, W);
+          const uint64_t e = __ldg(mrow + c);
+          row[sl] = inj_row0 + (r.y < (uint32_t)e ? c : (uint32_t)(e >> 32));
+        } else {
+          const uint32_t c = __umulhi(r.x, K);
+          const uint64_t e = __ldg(trow + (uint64_t)row[sl] * K + c);
+          const uint32_t j = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+          ++steps[sl];
+          if (j >= n) outcome = (int)(j - n);
+          else if (steps[sl] >= max_steps) outcome = -2;
+          else row[sl] = j;
+        }
+        if (outcome == -3) {
+          const uint32_t c = __umulhi(r.z, K);
+          const uint64_t e = __ldg(trow + (uint64_t)row[sl] * K + c);
+          const uint32_t j = r.w < (uint32_t)e ? c : (uint32_t)(e >> 32);
+          ++steps[sl];
+          if (j >= n) outcome = (int)(j - n);
+          else if (steps[sl] >= max_steps) outcome = -2;
+          else row[sl] = j;
+        }
+        ++b[sl];
+      }
+      if (kScore && outcome >= 0) {
+        // replay the finished walk and count its transitions under its absorbing lead
+        unsigned long long* cnt = score.cnt + (size_t)outcome * score.stride + t_tab_off;
+        unsigned long long* mcnt =
+            score.mode_cnt + (size_t)outcome * score.mode_stride + t_mode_off;
+        uint32_t rrow = 0;
+        bool live = true;
+        for (uint32_t bb = 0; live; ++bb) {
+          const uint4 q = philox4x32_10(make_uint4(bb, wid_lo[sl], wid_hi[sl], task_id), key);
+          if (bb == 0) {
+            const uint32_t c = __umulhi(q.x, W);
+            const uint64_t e = __ldg(mrow + c);
+            const uint32_t mode = q.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+            atomicAdd(mcnt + mode, 1ull);
+            rrow = inj_row0 + mode;
+          } else {
+            const uint32_t c = __umulhi(q.x, K);
+            const uint64_t e = __ldg(trow + (uint64_t)rrow * K + c);
+            const uint32_t j = q.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+            atomicAdd(cnt + (uint64_t)rrow * K + j, 1ull);
+            if (j >= n) live = false;
+            rrow = j;
+          }
+          if (live) {
+            const uint32_t c = __umulhi(q.z, K);
+            const uint64_t e = __ldg(trow + (uint64_t)rrow * K + c);
+            const uint32_t j = q.w < (uint32_t)e ? c : (uint32_t)(e >> 32);
+            atomicAdd(cnt + (uint64_t)rrow * K + j, 1ull);
+            if (j >= n) live = false;
+            rrow = j;
+          }
         }
       }
-    }
-    if (outcome != -3) {
-      a[0] += 1u;
-      if (outcome == 0) a[1] += 1u;
-      else if (outcome == 1) a[2] += 1u;
-      else a[3] += 1u;
-      a[4] += steps;
-      if (kTrace) { trace_lead[g] = outcome; trace_steps[g] = steps; }
-      has = false;
-      if (a[4] >= kFlushAt || a[0] >= kFlushAt) flush_lane(s_tally, tl, a);
+      if (outcome != -3) {
+        a[0] += 1u;
+        if (outcome == 0) a[1] += 1u;
+        else if (outcome == 1) a[2] += 1u;
+        else a[3] += 1u;
+        a[4] += steps[sl];
+        if (kTrace) { trace_lead[g[sl]] = outcome; trace_steps[g[sl]] = steps[sl]; }
+        has[sl] = false;
+        if (a[4] >= kFlushAt || a[0] >= kFlushAt) flush_lane(s_tally, tl, a);
+      }
     }
   }
   if (tl >= 0) flush_lane(s_tally, tl, a);
@@ -312,7 +346,7 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
                         uint64_t* d_tally, int32_t* d_trace_lead, uint32_t* d_trace_steps,
                         uint64_t* d_score, uint64_t score_stride, uint64_t* d_mode_score,
                         uint32_t mode_stride, int sm_count, int max_blocks_per_sm,
-                        cudaStream_t s, const uint64_t* d_run) {
+                        cudaStream_t s, const uint64_t* d_run, int slots) {
   if (n_tasks <= 0 || walkers_per_task == 0) return cudaSuccess;
   const PhiloxKey key{(uint32_t)seed, (uint32_t)(seed >> 32)};
   unsigned long long* tally = reinterpret_cast<unsigned long long*>(d_tally);
@@ -325,8 +359,10 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
     const ScoreOut so{reinterpret_cast<unsigned long long*>(d_score),
                       reinterpret_cast<unsigned long long*>(d_mode_score),
                       (unsigned long long)score_stride, mode_stride};
-    auto kern = d_trace_lead ? (d_score ? walk_kernel<true, true> : walk_kernel<true, false>)
-                             : (d_score ? walk_kernel<false, true> : walk_kernel<false, false>);
+    auto kern = d_score ? (d_trace_lead ? walk_kernel<true, true, 1> : walk_kernel<false, true, 1>)
+                : slots == 2
+                    ? (d_trace_lead ? walk_kernel<true, false, 2> : walk_kernel<false, false, 2>)
+                    : (d_trace_lead ? walk_kernel<true, false, 1> : walk_kernel<false, false, 1>);
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return e;

@@ -237,6 +237,12 @@ bool band_edge(double E, int W, double t) {
   return false;
 }
 
+// Walkers per lane of a walk launch when no tuning picked them: two when the launch has
+// two-level tables (tables far larger than L2, two dependent gathers per transition: more
+// walks in flight hide more of the latency), one otherwise (L2-resident one-level tables and
+// short walks, where the start and refill work of a second walker costs more than it hides).
+int walk_slots(bool any_two) { return any_two ? 2 : 1; }
+
 }  // namespace
 
 extern "C" {
@@ -1074,7 +1080,8 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
                             q.d_mode_tab, q.d_c + 2 * (size_t)wv.t0, r.start_lead, r.seed,
                             r.walkers_per_task, r.walker_id_offset, r.max_steps, ctx->d_counter,
                             tl->d_counts + (size_t)wv.t0 * NEGF_TALLY_FIELDS, nullptr, nullptr,
-                            nullptr, 0, nullptr, 0, ctx->sm_count, r.walk_blocks_per_sm, sw);
+                            nullptr, 0, nullptr, 0, ctx->sm_count, r.walk_blocks_per_sm, sw,
+                            nullptr, walk_slots(wv.any_two));
     }
     cudaFreeAsync(d_tab, sw);
     cudaEventRecord(walked[w], sw);
@@ -1312,7 +1319,7 @@ negf_status negf_walk(negf_ctx ctx, negf_tables t, int32_t start_lead, uint64_t 
     e = negf::launch_walk(t->d_tasks, 0, t->n_tasks, 0, t->d_tab, t->d_mode_tab, t->d_c,
                           start_lead, seed, walkers_per_task, walker_id_offset, max_steps,
                           ctx->d_counter, tl->d_counts, nullptr, nullptr, nullptr, 0, nullptr,
-                          0, ctx->sm_count, 0, ctx->stream);
+                          0, ctx->sm_count, 0, ctx->stream, nullptr, walk_slots(t->any_two));
   }
   if (e != cudaSuccess) {
     cudaFreeAsync(tl->d_counts, ctx->stream);
@@ -1339,7 +1346,7 @@ negf_status negf_walk_trace(negf_ctx ctx, negf_tables t, int32_t task, int32_t s
     e = negf::launch_walk(t->d_tasks, task, 1, 0, t->d_tab, t->d_mode_tab, t->d_c, start_lead,
                           seed, n_walkers, walker_id_offset, max_steps, ctx->d_counter, tmp,
                           d_lead, d_steps, nullptr, 0, nullptr, 0, ctx->sm_count, 0,
-                          ctx->stream);
+                          ctx->stream, nullptr, walk_slots(t->any_two));
   cudaFreeAsync(tmp, ctx->stream);
   if (e != cudaSuccess) return fail(ctx, NEGF_E_CUDA, "negf_walk_trace: %s", cudaGetErrorString(e));
   return NEGF_OK;
@@ -1938,7 +1945,9 @@ negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
                                       ctx->d_counter,
                                       p->d_counts + (size_t)wv.t0 * NEGF_TALLY_FIELDS, nullptr,
                                       nullptr, nullptr, 0, nullptr, 0, ctx->sm_count,
-                                      p->tune.walk_blocks_per_sm, ws, p->d_run));
+                                      p->tune.walk_blocks_per_sm, ws, p->d_run,
+                                      p->tune.walk_slots > 0 ? p->tune.walk_slots
+                                                             : walk_slots(wv.any_two)));
     }
     if (split) CUDA_TRY(ctx, cudaEventRecord(walked, sw));
   }
@@ -2052,19 +2061,24 @@ negf_status plan_autotune(negf_plan p) {
   const uint64_t h_run[2] = {0x5eedull, 0ull};
   CUDA_TRY(ctx, cudaMemcpyAsync(p->d_run, h_run, sizeof h_run, cudaMemcpyHostToDevice, s));
   CUDA_TRY(ctx, cudaStreamSynchronize(s));
-  for (int wb : {2, 3, 4, 5}) {
+  // (walkers per lane, CTAs per SM): two walkers per lane fit four CTAs per SM
+  int best_ws = 1;
+  const int cand[][2] = {{1, 2}, {1, 3}, {1, 4}, {1, 5}, {2, 2}, {2, 3}, {2, 4}};
+  for (const auto& c : cand) {
+    const int ws = c[0], wb = c[1];
     const float ms = time_on(s, 2, [&]() {
       return negf::launch_walk(dd, 0, nt0, (uint32_t)wv.t0, p->d_tab[0], q.d_mode_tab, q.d_c,
                                p->run.start_lead, 0, p->run.walkers_per_task, 0,
                                p->run.max_steps, ctx->d_counter, p->d_counts, nullptr, nullptr,
-                               nullptr, 0, nullptr, 0, ctx->sm_count, wb, s, p->d_run);
+                               nullptr, 0, nullptr, 0, ctx->sm_count, wb, s, p->d_run, ws);
     });
     if (ms < 0.f) return fail(ctx, NEGF_E_CUDA, "autotune: walk failed");
-    if (best_w < 0.f || ms < best_w) best_w = ms, best_wb = wb;
+    if (best_w < 0.f || ms < best_w) best_w = ms, best_wb = wb, best_ws = ws;
   }
   p->tune.chain_warps = best_cw;
   p->tune.alias_warps = best_aw;
   p->tune.walk_blocks_per_sm = best_wb;
+  p->tune.walk_slots = best_ws;
   p->tune.tuned = 1;
   p->tune.chain_ms = best_c;
   p->tune.alias_ms = best_a;

@@ -156,7 +156,7 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
                         uint64_t* d_tally, int32_t* d_trace_lead, uint32_t* d_trace_steps,
                         uint64_t* d_score, uint64_t score_stride, uint64_t* d_mode_score,
                         uint32_t mode_stride, int sm_count, int max_blocks_per_sm,
-                        cudaStream_t s, const uint64_t* d_run = nullptr);
+                        cudaStream_t s, const uint64_t* d_run = nullptr, int slots = 1);
 // Timed random 8-byte gathers over a table of table_bytes (see k_walk.cu); synchronises s.
 cudaError_t probe_gather(uint64_t table_bytes, int ilp, int chain, int sm_count,
                          uint64_t* gathers, float* ms, cudaStream_t s);

@@ -63,7 +63,7 @@ _lib = None
 class negf_plan_tuning(C.Structure):
     _fields_ = [("walk_blocks_per_sm", C.c_int32), ("chain_warps", C.c_int32),
                 ("alias_warps", C.c_int32), ("tuned", C.c_int32), ("walk_ms", C.c_float),
-                ("chain_ms", C.c_float), ("alias_ms", C.c_float)]
+                ("chain_ms", C.c_float), ("alias_ms", C.c_float), ("walk_slots", C.c_int32)]
 
 
 class negf_thermal_result(C.Structure):
@@ -474,7 +474,7 @@ def negf_plan_get_tuning(plan):
         raise NegfError(st, "negf_plan_get_tuning")
     return dict(walk_blocks_per_sm=t.walk_blocks_per_sm, chain_warps=t.chain_warps,
                 alias_warps=t.alias_warps, tuned=bool(t.tuned), walk_ms=t.walk_ms,
-                chain_ms=t.chain_ms, alias_ms=t.alias_ms)
+                chain_ms=t.chain_ms, alias_ms=t.alias_ms, walk_slots=t.walk_slots)
 
 
 def negf_plan_num_waves(plan):
