@@ -181,7 +181,9 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
       }
       continue;      // start the new walkers first
     }
-    if (!__any_sync(FULL, busy)) break;   // nothing in flight and nothing left to claim
+    // nothing in flight and nothing left to claim (with one slot an idle lane has an empty
+    // run, so the ballot above already says it)
+    if (kSlots == 1 ? dry == FULL : !__any_sync(FULL, busy)) break;
     if (!busy) continue;
 
     // ---- per walking slot one Philox block = two draws.  Block 0: the injection draw (Step 4)
