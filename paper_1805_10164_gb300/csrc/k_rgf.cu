@@ -1147,7 +1147,7 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
                          const double* d_gam, const C* d_gL, const C* d_gR, C* d_start,
                          typename Real<C>::T* d_w, double* d_rowsum, double* d_mode_w,
                          double* d_c, int32_t* d_err, C* d_green, C* d_gphi, cudaStream_t s,
-                         int chain_warps) {
+                         int chain_warps, int cols_max_W) {
   if (sizeof(C) == sizeof(cf)) {
     // register-resident diagonal blocks for the tasks of width <= 16, 4 warps per block (the
     // kernel skips wider tasks)
@@ -1174,8 +1174,10 @@ cudaError_t columns_impl(const TaskDesc* d_tasks, int n_tasks, uint32_t n_cols, 
     if (e != cudaSuccess) return e;
   }
   const uint32_t jobs = 2 * n_cols;
-  if (sizeof(C) == sizeof(cf) && max_W <= 32 && d_green == nullptr)
-    return launch_chain_cols(d_tasks, n_tasks, jobs, max_W, reinterpret_cast<const float*>(d_eta),
+  if (cols_max_W == 0) return cudaSuccess;      // every task's columns come from another kernel
+  if (sizeof(C) == sizeof(cf) && cols_max_W <= 32 && d_green == nullptr)
+    return launch_chain_cols(d_tasks, n_tasks, jobs, cols_max_W,
+                             reinterpret_cast<const float*>(d_eta),
                              reinterpret_cast<const float*>(d_phiR), d_gam,
                              reinterpret_cast<const cf*>(d_gL), reinterpret_cast<const cf*>(d_gR),
                              reinterpret_cast<const cf*>(d_start), reinterpret_cast<float*>(d_w),
@@ -1222,21 +1224,23 @@ cudaError_t launch_block_columns(const TaskDesc* d_tasks, int n_tasks, uint32_t 
                                  const cd* d_sig, const double* d_gam, const void* d_gL,
                                  const void* d_gR, void* d_start, void* d_weights,
                                  double* d_rowsum, double* d_mode_w, double* d_c, int32_t* d_err,
-                                 void* d_green, void* d_gphi, cudaStream_t s, int chain_warps) {
+                                 void* d_green, void* d_gphi, cudaStream_t s, int chain_warps,
+                                 int cols_max_W) {
   if (n_tasks == 0 || n_cols == 0) return cudaSuccess;
+  if (cols_max_W < 0) cols_max_W = max_W;
   if (precision == NEGF_FP64)
     return columns_impl<cd>(d_tasks, n_tasks, n_cols, max_W, d_wire, d_wire, d_phi, d_phi,
                             d_sig, d_gam, static_cast<const cd*>(d_gL),
                             static_cast<const cd*>(d_gR), static_cast<cd*>(d_start),
                             static_cast<double*>(d_weights), d_rowsum, d_mode_w, d_c, d_err,
                             static_cast<cd*>(d_green), static_cast<cd*>(d_gphi), s,
-                            chain_warps);
+                            chain_warps, cols_max_W);
   return columns_impl<cf>(d_tasks, n_tasks, n_cols, max_W, d_wire, d_eta32, d_phi, d_phi32,
                           d_sig, d_gam, static_cast<const cf*>(d_gL),
                           static_cast<const cf*>(d_gR), static_cast<cf*>(d_start),
                           static_cast<float*>(d_weights), d_rowsum, d_mode_w, d_c, d_err,
                           static_cast<cf*>(d_green), static_cast<cf*>(d_gphi), s,
-                          chain_warps);
+                          chain_warps, cols_max_W);
 }
 
 int chain_warps_max(int max_W, int precision) {

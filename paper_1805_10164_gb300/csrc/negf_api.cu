@@ -506,6 +506,7 @@ struct Wave {
   std::vector<TcJob> tcjobs;         // tensor-core chain jobs (task = index into desc), then
   size_t n_tc = 0;                   // the CTA-chain jobs: tcjobs[n_tc ..], those of W = 64
   size_t n_cta_wide = 0;             // tasks first
+  int cols_max_W = 0;                // widest task of the warp-per-column chains
   uint32_t cta_narrow() const { return (uint32_t)(tcjobs.size() - n_tc - n_cta_wide); }
 };
 
@@ -545,6 +546,7 @@ Wave make_wave(const Plan& P, int t0, int t1) {
       add_tc_jobs(w.tcjobs, k - t0, d.L);
     }
     if (d.cta_chain) add_tc_jobs(d.W == 64 ? cta : cta_n, k - t0, d.L);
+    if (!d.cta_chain && !d.fused) w.cols_max_W = std::max(w.cols_max_W, d.W);
     if (d.layout == NEGF_LAYOUT_TWO_LEVEL) {
       d.l1_off = w.tab + (uint64_t)d.rows * d.n;
       d.l1w_off = w.l1w;                 // rebased past the wave's weights below
@@ -736,7 +738,7 @@ negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& 
                                    q.d_phi, reinterpret_cast<float*>(q.d_phi + P.phi_total),
                                    q.d_sig, q.d_gam, d_gL, d_gR, d_start, d_weights, d_rowsum,
                                    q.d_mode_w, q.d_c + 2 * (size_t)w.t0, q.d_err, d_green,
-                                   d_gphi, s, chain_warps);
+                                   d_gphi, s, chain_warps, w.cols_max_W);
   }
   if (e == cudaSuccess && w.tcjobs.size() > w.n_tc) {
     ProfScope ps(ctx, "chain_cta_kernel", 1, s);
@@ -1902,7 +1904,7 @@ negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
                         reinterpret_cast<float*>(q.d_phi + P.phi_total), q.d_sig, q.d_gam,
                         p->d_gL, p->d_gR, p->d_start[slot], p->d_weights[slot], p->d_rs[slot],
                         q.d_mode_w, q.d_c + 2 * (size_t)wv.t0, q.d_err, nullptr, nullptr, s,
-                        p->tune.chain_warps));
+                        p->tune.chain_warps, wv.cols_max_W));
     }
     if (wv.tcjobs.size() > wv.n_tc) {
       SegScope sg(p, "chain_cta_kernel", 1, s, timed);
@@ -2005,7 +2007,7 @@ negf_status plan_autotune(negf_plan p) {
                                       q.d_phi, reinterpret_cast<float*>(q.d_phi + P.phi_total),
                                       q.d_sig, q.d_gam, p->d_gL, p->d_gR, p->d_start[0],
                                       p->d_weights[0], p->d_rs[0], q.d_mode_w, q.d_c, q.d_err,
-                                      nullptr, nullptr, s, cw);
+                                      nullptr, nullptr, s, cw, wv.cols_max_W);
   };
   auto columns_split = [&](int cw) {
     cudaError_t e = columns(cw);

@@ -94,6 +94,8 @@ cudaError_t launch_rgf_sweep(const TaskDesc* d_tasks, int n_tasks, int max_W, in
 // Diagonal blocks (start blocks, A per row, mode weights, c_p) then the block-column chains
 // emitting the weights.  n_cols = sum over tasks of L + 2.  On return rowsum holds A of every
 // table row and c_p in the two mode-row slots; the alias build replaces them by the row sums.
+// cols_max_W: the largest W among the tasks the warp-per-column chains take (neither fused nor
+// cta_chain; -1 = max_W), so that a chain instantiation with nothing to do is not launched.
 // Block columns with one column per lane (complex64, W <= 32, no gradient outputs; see
 // k_chain_cols.cu): jobs = 2 * sum over tasks of (L + 2).
 cudaError_t launch_chain_cols(const TaskDesc* d_tasks, int n_tasks, uint32_t n_jobs, int max_W,
@@ -107,7 +109,7 @@ cudaError_t launch_block_columns(const TaskDesc* d_tasks, int n_tasks, uint32_t 
                                  const void* d_gR, void* d_start, void* d_weights,
                                  double* d_rowsum, double* d_mode_w, double* d_c, int32_t* d_err,
                                  void* d_green, void* d_gphi, cudaStream_t s,
-                                 int chain_warps = 0);
+                                 int chain_warps = 0, int cols_max_W = -1);
 // Warps per CTA the chain kernel can use for max_W (shared memory bound), and its default.
 int chain_warps_max(int max_W, int precision);
 // Alias tables of every row (and mode row); replaces the A values in rowsum by the FP64 row

@@ -1,6 +1,7 @@
 """FP32 block columns by the CTA-wide kernels against the oracle: W = 64 wires
-(chain_cta_kernel) and 16 < W <= 32 wires (chain_cta_narrow_kernel, odd and even widths, both
-ends of the range, ragged lengths down to L = 1).  Bars: weights elementwise within 1e-5 of
+(chain_cta_kernel), 16 < W <= 32 wires (chain_cta_narrow_kernel, odd and even widths, both
+ends of the range, ragged lengths down to L = 1), and a batch mixing both with a W <= 16 wire
+(whose columns the column-per-lane chain builds in the same wave).  Bars: weights elementwise within 1e-5 of
 the row sum (the FP32 table bar), one-level and two-level tables, lead weights at both boundary
 slices, and bit-exact walks on the exported tables."""
 import numpy as np
@@ -25,6 +26,12 @@ def ctx():
 
 
 def _wires(kind):
+    if kind == "mixed":
+        # one batch whose tasks take three block-column kernels: W = 64 and 16 < W <= 32 the
+        # CTA chains, W <= 16 the column-per-lane chain
+        return [inputs.small_wire(161, W=64, L=3, n_energy=1, eta=0.05, disorder=0.5),
+                inputs.small_wire(162, W=9, L=6, n_energy=2, eta=0.04, disorder=0.7),
+                inputs.small_wire(163, W=19, L=4, n_energy=1, eta=0.06, disorder=0.6)]
     if kind == "narrow":
         return [inputs.small_wire(151, W=17, L=1, n_energy=1, eta=0.05, disorder=0.5),
                 inputs.small_wire(152, W=20, L=7, n_energy=2, eta=0.03, disorder=0.8,
@@ -43,7 +50,7 @@ def _wires(kind):
             inputs.small_wire(144, W=64, L=6, n_energy=1, eta=0.1, lead_model=1, gamma_lead=0.8)]
 
 
-@pytest.fixture(scope="module", params=["wide", "narrow"])
+@pytest.fixture(scope="module", params=["wide", "narrow", "mixed"])
 def batch(ctx, request):
     wires = _wires(request.param)
     refs = []
