@@ -493,6 +493,144 @@ def time_precision(prec, one_step, dev_wires, negf, ctx, stream, flush, args, st
             "kernel_ms_per_step": {k: round(v[1] / steps, 4) for k, v in prof.items()}}
 
 
+# ------------------------------------------------------------------ gradient (forward + backward)
+
+
+def run_gradient(args):
+    """One step = the differentiable current of the workload's first wire through the public
+    torch API (autograd.NegfCurrent: tables keeping G, walks with score tallies, current) and
+    its backward (negf_current_backward: the gradient w.r.t. every onsite energy and every
+    dephasing rate).  The API is synchronous (the current and the gradient come back to the
+    host), so the timed region is wall time on the device between the step's first launch and
+    the gradient's arrival."""
+    import torch
+    from paper_1805_10164_gb300 import autograd, build, negf
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    build.build()
+    name = args.workload if args.workload != "wire_10x50" else "wire_16x100"
+    wl = workload(name, args.energies)
+    prec = args.precision or wl.precision
+    w = wl.wires[0]
+    N = args.walkers or wl.walkers_per_task
+    stream = torch.cuda.current_stream()
+    ctx = negf.negf_create(local, stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    onsite_h = torch.from_numpy(w.onsite).pin_memory()
+    eta_h = torch.from_numpy(w.eta).pin_memory()
+
+    def spec_for(i):
+        return autograd.CurrentSpec(W=w.W, L=w.L, t=w.t, energy=w.energy,
+                                    energy_weight=w.energy_weight, mu_p=wl.mu_p, mu_q=wl.mu_q,
+                                    kT=wl.kT, start_lead=0, walkers_per_task=N, seed=args.seed,
+                                    walker_id_offset=ndist.weak_walker_offset(rank, i, N),
+                                    max_steps=args.max_steps, precision=prec)
+
+    def one_step(i, onsite, eta):
+        onsite = onsite.detach().requires_grad_(True)
+        eta = eta.detach().requires_grad_(True)
+        I, se = autograd.NegfCurrent.apply(onsite, eta, ctx, spec_for(i))
+        I.backward()
+        return float(I), float(se), onsite.grad, eta.grad
+
+    on_d = onsite_h.cuda()
+    eta_d = eta_h.cuda()
+    for i in range(args.warmup):
+        one_step(10_000 + i, on_d, eta_d)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = Clocks(local) if rank == 0 else None
+    negf.negf_profile_enable(ctx, True)
+    total_ms, res = 0.0, None
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = one_step(i, on_d, eta_d)
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+    prof = negf.negf_profile_read(ctx)
+    negf.negf_profile_enable(ctx, False)
+    if clocks is not None:
+        t_soak = time.perf_counter()
+        i = 0
+        while clocks.elapsed() < 1.2 and time.perf_counter() - t_soak < 10.0:
+            flush.fill_(float(i))
+            one_step(30_000 + i, on_d, eta_d)
+            torch.cuda.synchronize()
+            i += 1
+    clk = clocks.stop() if clocks else None
+    if clk is not None:
+        clk["window"] = "timed steps, then repeats of the same step until 1.2 s had passed"
+    # walker steps of one step: the same walks (same seed and walker ids) without score
+    # tallies, outside the timed region
+    dev = inputs.Wire(W=w.W, L=w.L, t=w.t, onsite=on_d, eta=eta_d,
+                      energy=torch.from_numpy(w.energy).cuda(),
+                      energy_weight=torch.from_numpy(w.energy_weight).cuda())
+    tab = negf.negf_build_tables(ctx, [dev], precision=prec, memspace="device")
+    steps_per_step = 0.0
+    for i in range(args.steps):
+        tl = negf.negf_walk(ctx, tab, 0, args.seed, N,
+                            walker_id_offset=ndist.weak_walker_offset(rank, i, N),
+                            max_steps=args.max_steps)
+        steps_per_step += float(negf.negf_tally_counts(ctx, tl, len(w.energy))[:, 4].sum())
+        negf.negf_tally_free(tl)
+    negf.negf_tables_free(tab)
+    steps_per_step /= args.steps
+    barrier(world)
+    t_max = max_over_ranks(total_ms, world)
+    # end to end: onsite and eta from pinned host memory, the gradient back to the host
+    e2e_ms = 0.0
+    n_e2e = max(1, min(args.steps, 3))
+    for i in range(n_e2e):
+        flush.fill_(float(i))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, gV, gE = one_step(20_000 + i, onsite_h.cuda(non_blocking=True),
+                                eta_h.cuda(non_blocking=True))
+        gV.cpu()
+        gE.cpu()
+        torch.cuda.synchronize()
+        e2e_ms += (time.perf_counter() - t0) * 1e3
+    negf.negf_destroy(ctx)
+    if rank != 0:
+        return
+    I, se, gV, gE = res
+    n_par = 2 * w.W * w.L
+    out = {
+        "metric": METRIC, "value": steps_per_step * world / (t_max / args.steps / 1e3),
+        "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64 tables and adjoint, u32 walks, f64 tally",
+                  "fp32": "f32 tables and adjoint, u32 walks, f64 tally"}.get(prec, prec),
+        "data": "synthetic (seeded square-lattice wire standing in for the paper's CdTe nanowires)",
+        "config": {"workload": wl.name + "_gradient", "walkers_per_task": N,
+                   "tasks": len(w.energy), "precision": prec,
+                   "parameters": n_par,
+                   "step": "forward (tables keeping G, walks with score tallies, current) + "
+                           "backward (gradient w.r.t. every onsite energy and dephasing rate) "
+                           "through autograd.NegfCurrent",
+                   "l2": "flushed between timed steps (258 MiB write, outside the timed events)",
+                   "mode": "gradient"},
+        "walker_steps_per_step": steps_per_step,
+        "gradient": {"ms_per_gradient": t_max / args.steps, "parameters": n_par, "I": I,
+                     "se": se, "dI_donsite_norm": float(gV.norm()),
+                     "dI_deta_norm": float(gE.norm())},
+        "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
+        "e2e": {"value": steps_per_step / (e2e_ms / n_e2e / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": int(2 * w.onsite.nbytes),
+                "d2h_bytes_per_step": int(2 * w.onsite.nbytes + 16)},
+        "gpu_launches": int(sum(v[0] for v in prof.values())),
+        "clocks": clk,
+    }
+    print(json.dumps(out), flush=True)
+
+
 # ------------------------------------------------------------------ thermal-window sampler
 
 THERMAL_GRID = 17          # grid energies spanning mu +- 8 kT
@@ -718,7 +856,7 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--mode", default="graph",
-                    choices=["graph", "pipeline", "separate", "thermal"])
+                    choices=["graph", "pipeline", "separate", "thermal", "gradient"])
     ap.add_argument("--tasks-per-wave", type=int, default=8)
     ap.add_argument("--walk-blocks-per-sm", type=int, default=4)
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
@@ -734,6 +872,8 @@ def main():
         run_reference(args)
     elif args.mode == "thermal":
         run_thermal(args)
+    elif args.mode == "gradient":
+        run_gradient(args)
     else:
         run_gpu(args)
 

@@ -65,19 +65,21 @@ __global__ void seeds_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
     const unsigned long long* C0 = score + off;
     const unsigned long long* C1 = score + stride + off;
     const unsigned long long* Cq = q == 0 ? C0 : C1;
+    // FP64 divisions are slow on this GPU: 1/N and S/rowsum once per row, s/w per entry
+    const double invN = N > 0.0 ? 1.0 / N : 0.0;
     double S = 0.0;
     for (int b = lane; b < K; b += 32)
-      S += N > 0.0 ? ((double)Cq[b] - Ph * ((double)C0[b] + (double)C1[b])) / N : 0.0;
+      S += ((double)Cq[b] - Ph * ((double)C0[b] + (double)C1[b])) * invN;
     for (int o = 16; o > 0; o >>= 1) S += __shfl_down_sync(0xffffffffu, S, o);
     S = __shfl_sync(0xffffffffu, S, 0);
     const double rs = rowsum[d.row_base + row];
+    const double Srs = rs > 0.0 ? S / rs : 0.0;
     for (int b = lane; b < K; b += 32) {
       const double wv = (double)weights[off + b];
-      const double s = N > 0.0 ? ((double)Cq[b] - Ph * ((double)C0[b] + (double)C1[b])) / N : 0.0;
+      const double s = ((double)Cq[b] - Ph * ((double)C0[b] + (double)C1[b])) * invN;
       double v = 0.0;
       if (wv > 0.0) v = s / wv;
-      if (rs > 0.0) v -= S / rs;
-      wbar[off + b] = c * v;
+      wbar[off + b] = c * (v - Srs);
     }
   } else if (row == d.rows && lane < d.W) {
     // injection modes of the start lead p
@@ -146,11 +148,48 @@ __global__ void gbar_leads_kernel(TaskDesc d, const C* __restrict__ G,
 // Pass C: injection rows (p, m): psi = G Phi_p[:, m] (gphi), psibar_b = wbar gamma_b conj(psi_b)
 // for sites, plus the lead-column terms on the boundary slices; then
 // Gbar[b][(p,y)] += sum_m psibar^(m)_b phi_m(y).  One thread per (b, y).
+// The lead-column term of injection row m at site x of the boundary slice sr (lead r) is
+// wbar_{(p,m),n+r} Tl[r][m][x], with z_nu = sum_x' phi_nu(x') psi_(sr,x') and
+// Tl[r][m][x] = sum_nu Gamma_nu phi_nu(x) conj(z_nu): it depends on neither the column y nor
+// the other sites, so gbar_inj_lead_kernel forms it once (one CTA per (r, m), z in shared
+// memory) before the per-element pass.  Tl: [nr][W][W] in the precision of G (nr = 1 when
+// L = 1: both leads then sit on slice 0 and share it).
+template <typename C>
+__global__ void gbar_inj_lead_kernel(TaskDesc d, const C* __restrict__ gphi,
+                                     const double* __restrict__ phi,
+                                     const double* __restrict__ gam, int p, C* __restrict__ Tl) {
+  __shared__ double sz[2 * 64];
+  const int W = d.W, L = d.L;
+  const int r = blockIdx.x / W, m = blockIdx.x % W;
+  const int sr = r == 0 ? 0 : L - 1;
+  for (int nu = threadIdx.x; nu < W; nu += blockDim.x) {
+    double zx = 0.0, zy = 0.0;
+    for (int xx = 0; xx < W; ++xx) {
+      const C g = gphi[(uint64_t)(sr * W + xx) * 2 * W + p * W + m];
+      zx += phi[xx * W + nu] * (double)g.x;
+      zy += phi[xx * W + nu] * (double)g.y;
+    }
+    sz[2 * nu] = zx;
+    sz[2 * nu + 1] = zy;
+  }
+  __syncthreads();
+  for (int x = threadIdx.x; x < W; x += blockDim.x) {
+    double tx = 0.0, ty = 0.0;
+    for (int nu = 0; nu < W; ++nu) {
+      const double f = gam[nu] * phi[x * W + nu];
+      tx += f * sz[2 * nu];
+      ty -= f * sz[2 * nu + 1];
+    }
+    using R = typename RealOf<C>::T;
+    Tl[((uint64_t)r * W + m) * W + x] = C{(R)tx, (R)ty};
+  }
+}
+
 template <typename C>
 __global__ void gbar_inj_kernel(TaskDesc d, const C* __restrict__ gphi,
                                 const double* __restrict__ wbar, const double* __restrict__ eta,
-                                const double* __restrict__ phi, const double* __restrict__ gam,
-                                int p, C* __restrict__ Gbar) {
+                                const double* __restrict__ phi, const C* __restrict__ Tl, int p,
+                                C* __restrict__ Gbar) {
   using R = typename RealOf<C>::T;
   const int n = d.n, W = d.W, K = d.K, L = d.L;
   const int total = n * W;
@@ -169,20 +208,9 @@ __global__ void gbar_inj_kernel(TaskDesc d, const C* __restrict__ gphi,
         if (sb != sr) continue;
         const double wl = wbar[roff + n + r];
         if (wl == 0.0) continue;
-        double tx = 0.0, ty = 0.0;
-        for (int nu = 0; nu < W; ++nu) {
-          double zx = 0.0, zy = 0.0;
-          for (int xx = 0; xx < W; ++xx) {
-            const C g = gphi[(uint64_t)(sr * W + xx) * 2 * W + p * W + m];
-            zx += phi[xx * W + nu] * (double)g.x;
-            zy += phi[xx * W + nu] * (double)g.y;
-          }
-          const double f = gam[nu] * phi[xb * W + nu];
-          tx += f * zx;
-          ty -= f * zy;
-        }
-        bx += wl * tx;
-        by += wl * ty;
+        const C t = Tl[((uint64_t)(L == 1 ? 0 : r) * W + m) * W + xb];
+        bx += wl * (double)t.x;
+        by += wl * (double)t.y;
       }
       ax += bx * phi[y * W + m];
       ay += by * phi[y * W + m];
@@ -212,46 +240,65 @@ __global__ void gbar_modes_kernel(TaskDesc d, const double* __restrict__ ubar,
   }
 }
 
-// ---- Y = A B for dense complex n x n (row-major), tiled in shared memory.
+// ---- Y = A B for dense complex n x n (row-major), tiled in shared memory: a 64 x 64 block of
+// Y per CTA, k in steps of 16; thread (ty, tx) of 16 x 16 owns rows ty + 16 i and columns
+// tx + 16 j (i, j < 4), so that each k costs 8 shared loads for 16 complex multiply-adds.  The
+// A tile is kept transposed ([k][row]) so that a warp's row loads are broadcasts.
+constexpr int kGemmM = 64, kGemmK = 16;
+
 template <typename C>
 __global__ void __launch_bounds__(256) cgemm_kernel(const C* __restrict__ A,
                                                     const C* __restrict__ B, C* __restrict__ Y,
                                                     int n) {
-  constexpr int T = 32;
-  __shared__ C sA[T][T + 1];
-  __shared__ C sB[T][T + 1];
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;     // 32 x 8 threads, 4 rows each
-  const int row0 = blockIdx.y * T, col = blockIdx.x * T + tx;
-  C acc[4];
+  using R = typename RealOf<C>::T;
+  __shared__ C sA[kGemmK][kGemmM + 1];
+  __shared__ C sB[kGemmK][kGemmM];
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  const int row0 = blockIdx.y * kGemmM, col0 = blockIdx.x * kGemmM;
+  R accr[4][4], acci[4][4];
 #pragma unroll
-  for (int r = 0; r < 4; ++r) acc[r] = C{0, 0};
-  for (int k0 = 0; k0 < n; k0 += T) {
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const int i = ty + 8 * r;
-      const int ar = row0 + i, ac = k0 + tx;
-      sA[i][tx] = (ar < n && ac < n) ? A[(uint64_t)ar * n + ac] : C{0, 0};
-      const int br = k0 + i;
-      sB[i][tx] = (br < n && col < n) ? B[(uint64_t)br * n + col] : C{0, 0};
+    for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = (R)0;
+  for (int k0 = 0; k0 < n; k0 += kGemmK) {
+    // A tile: 64 rows x 16 k (row r = e / 16, k = e % 16: 16 consecutive k of a row per
+    // half-warp); B tile: 16 k x 64 columns (consecutive columns per warp)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + 256 * q;
+      const int ar = e >> 4, ak = e & 15;
+      const int gr = row0 + ar, gk = k0 + ak;
+      sA[ak][ar] = (gr < n && gk < n) ? A[(uint64_t)gr * n + gk] : C{0, 0};
+      const int bk = e >> 6, bc = e & 63;
+      const int hk = k0 + bk, hc = col0 + bc;
+      sB[bk][bc] = (hk < n && hc < n) ? B[(uint64_t)hk * n + hc] : C{0, 0};
     }
     __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < T; ++k) {
-      const C b = sB[k][tx];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const C a = sA[ty + 8 * r][k];
-        acc[r].x += a.x * b.x - a.y * b.y;
-        acc[r].y += a.x * b.y + a.y * b.x;
-      }
+    for (int k = 0; k < kGemmK; ++k) {
+      C a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = sA[k][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = sB[k][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          accr[i][j] += a[i].x * b[j].x - a[i].y * b[j].y;
+          acci[i][j] += a[i].x * b[j].y + a[i].y * b[j].x;
+        }
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const int i = row0 + ty + 8 * r;
-    if (i < n && col < n) Y[(uint64_t)i * n + col] = acc[r];
-  }
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = row0 + ty + 16 * i, c = col0 + tx + 16 * j;
+      if (r < n && c < n) Y[(uint64_t)r * n + c] = C{accr[i][j], acci[i][j]};
+    }
 }
 
 // ---- dT/dV_k = 2 Re (G Y)_kk, dT/deta_k = Im (G Y)_kk + explicit gamma_k terms:
@@ -332,9 +379,11 @@ cudaError_t backward_task(const TaskDesc& d, const C* G, const C* gphi, const do
   const unsigned bl = (unsigned)((n * W + 255) / 256);
   gbar_leads_kernel<C><<<bl, 256, 0, s>>>(d, G, wbar, phi, gam, Gbar, 0);
   gbar_leads_kernel<C><<<bl, 256, 0, s>>>(d, G, wbar, phi, gam, Gbar, 1);
-  gbar_inj_kernel<C><<<bl, 256, 0, s>>>(d, gphi, wbar, eta, phi, gam, p, Gbar);
+  // the lead terms of the injection rows go through Y, which the product below overwrites
+  gbar_inj_lead_kernel<C><<<(d.L == 1 ? 1 : 2) * W, 64, 0, s>>>(d, gphi, phi, gam, p, Y);
+  gbar_inj_kernel<C><<<bl, 256, 0, s>>>(d, gphi, wbar, eta, phi, Y, p, Gbar);
   gbar_modes_kernel<C><<<1, 256, 0, s>>>(d, ubar, phi, gam, p, Gbar);
-  dim3 grid((n + 31) / 32, (n + 31) / 32);
+  dim3 grid((n + kGemmM - 1) / kGemmM, (n + kGemmM - 1) / kGemmM);
   cgemm_kernel<C><<<grid, 256, 0, s>>>(Gbar, G, Y, n);
   grad_diag_kernel<C><<<(n + 7) / 8, 256, 0, s>>>(d, G, Y, gphi, wbar, dV, dE);
   return cudaGetLastError();
