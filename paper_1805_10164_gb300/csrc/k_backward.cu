@@ -370,7 +370,7 @@ template <typename C>
 cudaError_t backward_task(const TaskDesc& d, const C* G, const C* gphi, const double* wbar,
                           const double* ubar, const double* eta, const double* phi,
                           const double* gam, int p, C* Gbar, C* Y, double* dV, double* dE,
-                          int sm_count, cudaStream_t s) {
+                          int sm_count, int32_t* err, cudaStream_t s) {
   const int n = d.n, W = d.W;
   const uint64_t nn = (uint64_t)n * n;
   unsigned blocks = (unsigned)((nn + 255) / 256);
@@ -383,8 +383,16 @@ cudaError_t backward_task(const TaskDesc& d, const C* G, const C* gphi, const do
   gbar_inj_lead_kernel<C><<<(d.L == 1 ? 1 : 2) * W, 64, 0, s>>>(d, gphi, phi, gam, p, Y);
   gbar_inj_kernel<C><<<bl, 256, 0, s>>>(d, gphi, wbar, eta, phi, Y, p, Gbar);
   gbar_modes_kernel<C><<<1, 256, 0, s>>>(d, ubar, phi, gam, p, Gbar);
-  dim3 grid((n + kGemmM - 1) / kGemmM, (n + kGemmM - 1) / kGemmM);
-  cgemm_kernel<C><<<grid, 256, 0, s>>>(Gbar, G, Y, n);
+  if constexpr (sizeof(C) == sizeof(cf)) {
+    // complex64: the product on the tensor cores (3xTF32, FP32 accumulation)
+    const cudaError_t e = launch_cgemm_tc(reinterpret_cast<const cf*>(Gbar),
+                                          reinterpret_cast<const cf*>(G),
+                                          reinterpret_cast<cf*>(Y), n, err, s);
+    if (e != cudaSuccess) return e;
+  } else {
+    dim3 grid((n + kGemmM - 1) / kGemmM, (n + kGemmM - 1) / kGemmM);
+    cgemm_kernel<C><<<grid, 256, 0, s>>>(Gbar, G, Y, n);
+  }
   grad_diag_kernel<C><<<(n + 7) / 8, 256, 0, s>>>(d, G, Y, gphi, wbar, dV, dE);
   return cudaGetLastError();
 }
@@ -420,14 +428,14 @@ cudaError_t launch_backward_task(const TaskDesc& d, int precision, const void* G
                                  const void* gphi, const double* wbar, const double* ubar,
                                  const double* eta, const double* phi, const double* gam,
                                  int start_lead, void* Gbar, void* Y, double* dV, double* dE,
-                                 int sm_count, cudaStream_t s) {
+                                 int sm_count, int32_t* d_err, cudaStream_t s) {
   if (precision == NEGF_FP64)
     return backward_task<cd>(d, static_cast<const cd*>(G), static_cast<const cd*>(gphi), wbar,
                              ubar, eta, phi, gam, start_lead, static_cast<cd*>(Gbar),
-                             static_cast<cd*>(Y), dV, dE, sm_count, s);
+                             static_cast<cd*>(Y), dV, dE, sm_count, d_err, s);
   return backward_task<cf>(d, static_cast<const cf*>(G), static_cast<const cf*>(gphi), wbar,
                            ubar, eta, phi, gam, start_lead, static_cast<cf*>(Gbar),
-                           static_cast<cf*>(Y), dV, dE, sm_count, s);
+                           static_cast<cf*>(Y), dV, dE, sm_count, d_err, s);
 }
 
 cudaError_t launch_grad_sum(const TaskDesc* d_tasks, int n_wires, const int32_t* d_wire_task0,

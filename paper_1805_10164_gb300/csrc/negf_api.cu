@@ -1538,7 +1538,7 @@ negf_status negf_current_backward(negf_ctx ctx, negf_tables t, negf_tally tl, do
         static_cast<const char*>(t->d_gphi) + d.gphi_off * cb, d_wbar, d_ubar,
         t->d_wire + d.onsite_off + d.n, t->d_phi + d.phi_off, t->d_gam + d.lead_off,
         tl->start_lead, d_Gbar, d_Y, d_dT + tso[k], d_dT + n_sites_tasks + tso[k],
-        ctx->sm_count, s);
+        ctx->sm_count, t->d_err, s);
   }
   if (e == cudaSuccess) {
     ProfScope ps(ctx, "grad_sum_kernel", 1);

@@ -191,7 +191,11 @@ cudaError_t launch_backward_task(const TaskDesc& d, int precision, const void* G
                                  const void* gphi, const double* wbar, const double* ubar,
                                  const double* eta, const double* phi, const double* gam,
                                  int start_lead, void* Gbar, void* Y, double* dV, double* dE,
-                                 int sm_count, cudaStream_t s);
+                                 int sm_count, int32_t* d_err, cudaStream_t s);
+// Y = A B for dense complex64 n x n matrices (row-major) on the tensor cores, 3xTF32 with FP32
+// accumulation (k_cgemm_tc.cu); a timed-out device wait sets ERR_TIMEOUT in err.
+cudaError_t launch_cgemm_tc(const cf* A, const cf* B, cf* Y, int n, int32_t* err,
+                            cudaStream_t s);
 cudaError_t launch_grad_sum(const TaskDesc* d_tasks, int n_wires, const int32_t* d_wire_task0,
                             const uint64_t* d_task_site_off, const uint64_t* d_wire_site_off,
                             const double* dT_V, const double* dT_E, const double* d_seed,
