@@ -4,7 +4,8 @@ the oracle's exact FP64 derivative (pinned to finite differences of the direct p
 * Deterministic: the score tallies are replaced by their exact expectations (N = 2^40 walkers'
   worth of counts, computed by the oracle from the absorbing chain), so the GPU result must
   equal the exact derivative: 1e-8 of the largest component in FP64, 1e-4 in FP32 (the bar
-  for gradients against finite differences).
+  for gradients against finite differences); a 15-site wire and a 161-site one whose
+  adjoint product spans several tiles of the tensor-core kernel with ragged tails.
 * Statistical: real walks; the gradient's projections on fixed directions must lie within 4.5
   standard errors (batch means over independent walker-id ranges) of the exact values.
 """
@@ -74,9 +75,18 @@ def _expected_counts(w, E, p, N):
             np.rint(N * mode).astype(np.uint64))
 
 
+def _exact_tally_wire(size):
+    if size == "multi_tile":
+        # n = 161 sites: the adjoint's dense product spans two row tiles, three column tiles
+        # and eleven k stages of the tensor-core kernel, each with a ragged tail
+        return inputs.small_wire(84, W=7, L=23, n_energy=2, eta=0.15, e_lo=-1.2, e_hi=0.9)
+    return inputs.small_wire(81, W=3, L=5, n_energy=2, eta=0.2, e_lo=-1.0, e_hi=1.0)
+
+
+@pytest.mark.parametrize("size", ["small", "multi_tile"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-8), ("fp32", 1e-4)])
-def test_gradient_with_exact_tallies(ctx, precision, tol):
-    w = inputs.small_wire(81, W=3, L=5, n_energy=2, eta=0.2, e_lo=-1.0, e_hi=1.0)
+def test_gradient_with_exact_tallies(ctx, precision, tol, size):
+    w = _exact_tally_wire(size)
     p, N = 0, float(2 ** 40)
     tables = negf.negf_build_tables(ctx, [w], precision=precision, keep_green=True)
     tally = negf.negf_walk_score(ctx, tables, p, 1, 0)      # allocated, all counts zero
