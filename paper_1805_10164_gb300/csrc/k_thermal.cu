@@ -10,8 +10,9 @@
 // integers, from which the host forms the mean and variance of the score exactly.
 //
 // Random numbers (Philox4x32-10, counter (b, id_lo, id_hi, 0x80000000 | wire)): block 0 -> the
-// energy (x0, x1: its CDF value, placed among the grid's CDF values for the interval) and the
-// injection table (x2); block 1 -> the injection mode (x0, x1); block
+// energy (x0, x1: a 53-bit word v whose CDF value F = F0 + (v + 1/2) 2^-53 window gives the
+// interval, found by comparing v with the host's integer thresholds of the grid points, and
+// the energy) and the injection table (x2); block 1 -> the injection mode (x0, x1); block
 // b >= 2 -> transition b - 1, (x0, x1) on the row and x2 < a for the table.  One thread per
 // walker (grid-stride); the block's tally sits in shared memory and is added to global memory
 // once.
@@ -42,7 +43,7 @@ __global__ void __launch_bounds__(kThermalThreads) thermal_walk_kernel(
     const uint64_t* __restrict__ tab, const uint64_t* __restrict__ mode_tab,
     const double* __restrict__ cvals, int p, PhiloxKey key, uint64_t walkers, uint64_t id_offset,
     uint32_t max_steps, double mu, double kT, double F0, double window,
-    const double* __restrict__ Fg, unsigned long long* __restrict__ tally,
+    const unsigned long long* __restrict__ thr, unsigned long long* __restrict__ tally,
     int32_t* __restrict__ t_lead,
     uint32_t* __restrict__ t_steps, int32_t* __restrict__ t_interval, uint32_t* __restrict__ t_a) {
   // shared tally: per interval (absorbed at q, sum a, sum (a >> 16)^2), then absorbed L, R,
@@ -65,10 +66,12 @@ __global__ void __launch_bounds__(kThermalThreads) thermal_walk_kernel(
     const uint64_t v = (((uint64_t)r0.x << 32) | r0.y) >> 11;
     const double u = ((double)v + 0.5) * 0x1p-53;
     const double pE = F0 + u * window;                // F(E) of the drawn energy
-    int lo_i = 0, hi_i = M - 1;                       // last grid index with F(E_e) <= F(E)
+    // last grid index with F(E_e) <= F(E): the number of grid points 1 .. M - 1 whose
+    // threshold v reaches (an integer search, no FP64 compares)
+    int lo_i = 0, hi_i = M - 1;
     while (lo_i < hi_i) {
-      const int mid = (lo_i + hi_i + 1) >> 1;
-      if (Fg[mid] <= pE) lo_i = mid; else hi_i = mid - 1;
+      const int mid = (lo_i + hi_i) >> 1;
+      if (thr[mid] <= v) lo_i = mid + 1; else hi_i = mid;
     }
     const int iv = lo_i < M - 2 ? lo_i : M - 2;
     // E - E_i = kT ln(F / (1 - F)) - (E_i - mu): the logarithms in FP32 of F and 1 - F (the
@@ -154,9 +157,9 @@ cudaError_t launch_thermal_walk(const TaskDesc* d_tasks, int task0, int M, int w
                                 const double* d_c, int start_lead, uint64_t seed,
                                 uint64_t walkers, uint64_t id_offset, uint32_t max_steps,
                                 double mu, double kT, double F0, double window,
-                                const double* d_Fg, unsigned long long* d_tally, int32_t* d_lead,
-                                uint32_t* d_steps, int32_t* d_interval, uint32_t* d_a,
-                                int sm_count, cudaStream_t s) {
+                                const unsigned long long* d_thr, unsigned long long* d_tally,
+                                int32_t* d_lead, uint32_t* d_steps, int32_t* d_interval,
+                                uint32_t* d_a, int sm_count, cudaStream_t s) {
   if (walkers == 0 || M < 2) return cudaSuccess;
   const PhiloxKey key{(uint32_t)seed, (uint32_t)(seed >> 32)};
   const size_t smem = sizeof(unsigned) * 2 * (size_t)(3 * (M - 1) + 5);
@@ -165,7 +168,8 @@ cudaError_t launch_thermal_walk(const TaskDesc* d_tasks, int task0, int M, int w
   if (blocks > need) blocks = need;
   thermal_walk_kernel<<<(unsigned)blocks, kThermalThreads, smem, s>>>(
       d_tasks, task0, M, (uint32_t)wire, d_tab, d_mode_tab, d_c, start_lead, key, walkers,
-      id_offset, max_steps, mu, kT, F0, window, d_Fg, d_tally, d_lead, d_steps, d_interval, d_a);
+      id_offset, max_steps, mu, kT, F0, window, d_thr, d_tally, d_lead, d_steps, d_interval,
+      d_a);
   return cudaGetLastError();
 }
 

@@ -1663,21 +1663,39 @@ negf_status negf_walk_thermal(negf_ctx ctx, negf_tables t, int32_t wire, int32_t
   const double window = F1 - F0;
   DeviceGuard g(ctx->device);
   const size_t nf = 3 * (size_t)(M - 1) + 5;
-  // one allocation: the tally, then the grid's CDF values
+  // The energy's interval: the last grid index i with F(E_i) <= F, F = F0 + u window,
+  // u = (v + 1/2) 2^-53 for the walker's 53-bit integer v (each step rounded in FP64).  F is
+  // non-decreasing in v, so the comparison with grid point i is v >= thr_i, thr_i the least
+  // such v (2^53 when none); the device compares integers only.
   std::vector<double> Fg(M);
   for (int k = 0; k < M; ++k) Fg[k] = cdf(t->h_tasks[task0 + k].E);
+  auto F_of = [&](uint64_t v) {
+    volatile double u = ((double)v + 0.5) * 0x1p-53;
+    volatile double du = u * window;                 // rounded before the sum, as written
+    return F0 + du;
+  };
+  std::vector<unsigned long long> thr(M - 1);
+  for (int i = 1; i < M; ++i) {
+    uint64_t lo = 0, hi = 1ull << 53;                  // least v in [lo, hi] with F >= Fg[i]
+    while (lo < hi) {
+      const uint64_t mid = lo + (hi - lo) / 2;
+      if (F_of(mid) >= Fg[i]) hi = mid; else lo = mid + 1;
+    }
+    thr[i - 1] = lo;
+  }
+  // one allocation: the tally, then the interval thresholds
   unsigned long long* d_tally = nullptr;
-  CUDA_TRY(ctx, dalloc(&d_tally, nf + M, ctx->stream, nullptr));
-  const double* d_Fg = reinterpret_cast<const double*>(d_tally + nf);
+  CUDA_TRY(ctx, dalloc(&d_tally, nf + (M - 1), ctx->stream, nullptr));
+  const unsigned long long* d_thr = d_tally + nf;
   cudaError_t e = cudaMemsetAsync(d_tally, 0, sizeof(unsigned long long) * nf, ctx->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(d_tally + nf, Fg.data(), sizeof(double) * M, cudaMemcpyHostToDevice,
-                        ctx->stream);
+    e = cudaMemcpyAsync(d_tally + nf, thr.data(), sizeof(unsigned long long) * (M - 1),
+                        cudaMemcpyHostToDevice, ctx->stream);
   if (e == cudaSuccess && window > 0.0) {
     ProfScope ps(ctx, "thermal_walk_kernel");
     e = negf::launch_thermal_walk(t->d_tasks, task0, M, wire, t->d_tab, t->d_mode_tab, t->d_c,
                                   start_lead, seed, walkers, walker_id_offset, max_steps, mu, kT,
-                                  F0, window, d_Fg, d_tally, d_lead, d_steps, d_interval, d_a,
+                                  F0, window, d_thr, d_tally, d_lead, d_steps, d_interval, d_a,
                                   ctx->sm_count, ctx->stream);
   }
   std::vector<unsigned long long> h(nf, 0ull);

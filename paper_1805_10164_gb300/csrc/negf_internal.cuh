@@ -167,8 +167,8 @@ cudaError_t launch_current(const TaskDesc* d_tasks, int n_tasks, int n_wires,
                            const uint64_t* d_tally, int start_lead, double mu_p, double mu_q,
                            double kT, double* d_out, cudaStream_t s);
 // Thermal-window walks over the interpolated chain of one wire's energy grid (k_thermal.cu):
-// tasks task0 .. task0 + M - 1 (ascending energies, one-level tables), d_Fg their thermal CDF
-// values F(E_e); tally
+// tasks task0 .. task0 + M - 1 (ascending energies, one-level tables); d_thr [M - 1]: the
+// least 53-bit energy word v whose CDF value reaches grid point e + 1 (non-decreasing); tally
 // [3 (M - 1) + 5] u64: per interval (absorbed at q, sum a, sum (a >> 16)^2), then absorbed L,
 // R, closed, truncated, steps.  Trace arrays optional (nullptr).
 cudaError_t launch_thermal_walk(const TaskDesc* d_tasks, int task0, int M, int wire,
@@ -176,9 +176,9 @@ cudaError_t launch_thermal_walk(const TaskDesc* d_tasks, int task0, int M, int w
                                 const double* d_c, int start_lead, uint64_t seed,
                                 uint64_t walkers, uint64_t id_offset, uint32_t max_steps,
                                 double mu, double kT, double F0, double window,
-                                const double* d_Fg, unsigned long long* d_tally, int32_t* d_lead,
-                                uint32_t* d_steps, int32_t* d_interval, uint32_t* d_a,
-                                int sm_count, cudaStream_t s);
+                                const unsigned long long* d_thr, unsigned long long* d_tally,
+                                int32_t* d_lead, uint32_t* d_steps, int32_t* d_interval,
+                                uint32_t* d_a, int sm_count, cudaStream_t s);
 // Backward (score-function gradient, see k_backward.cu).
 cudaError_t launch_backward_seeds(const TaskDesc* d_tasks, int n_tasks, uint32_t n_jobs,
                                   int precision, const void* d_weights, const double* d_rowsum,
