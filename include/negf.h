@@ -375,7 +375,8 @@ typedef struct {
  * Random numbers: walker w (id walker_id_offset + w) takes Philox4x32-10 block b with counter
  * (b, id_lo, id_hi, 0x80000000 | wire) and key (seed_lo, seed_hi): block 0 words (x0, x1) give
  * u = (((x0 << 32 | x1) >> 11) + 1/2) / 2^53, the CDF value F = F(E_0) + u window of the drawn
- * energy (its interval i: F(E_i) <= F < F(E_{i+1}); alpha from F^-1(F) in FP32, to ~2^-20), word x2 the
+ * energy (FP64, each operation rounded; its interval i: F(E_i) <= F < F(E_{i+1}), decided
+ * exactly; alpha from F^-1(F) in FP32, to ~2^-20), word x2 the
  * injection table (upper iff x2 < a, a = min(floor(alpha 2^32), 2^32 - 1)); block 1 the injection
  * mode (x0, x1); block b >= 2 transition b - 1 ((x0, x1) on the row, x2 < a picks the table).
  * d_lead, d_steps, d_interval, d_a: optional caller-owned device arrays of `walkers` entries
