@@ -93,8 +93,9 @@ __global__ void lead_modes_kernel(const TaskDesc* __restrict__ tasks, int n_task
 // augmented identity):
 //   pivot k:  a_kk <- 1/a_kk;  a_kj <- a_kj / a_kk;  a_ik <- -a_ik / a_kk;
 //             a_ij <- a_ij - (a_ik / a_kk) a_kj            (i, j != k)
-// with two barriers per pivot: the pivot row and the multipliers a_ik / a_kk are copied out,
-// then every thread updates its entries.  Thread t owns column t mod W of rows t / W, t / W + R,
+// with two barriers per pivot: the pivot row (1/a_kk formed once, in a_kk's slot) and the
+// pivot column are copied out, then every thread updates its entries with a_kj / a_kk formed
+// once per thread.  Thread t owns column t mod W of rows t / W, t / W + R,
 // ... (R = threads / W), so that a warp touches consecutive entries of one row.  On a
 // slice where every site dephases no pivot search is needed (see gj_rows); otherwise rows are
 // interchanged by partial pivoting and the inverse's columns unscrambled at the end.  The
@@ -173,22 +174,21 @@ __device__ bool cta_gj(C* A, C* rowk, C* fcol, int* perm, int* flag, int W, bool
       }
       __syncthreads();
     }
-    const C piv = A[k * W + k];
-    const R m = norm2(piv);
-    if (!(m > 0) || !isfinite(m)) return false;    // every thread reads the same value
-    const C inv = cdiv(mkc(1.0, 0.0, C{}), piv);
+    // the pivot row (with 1/a_kk in place of a_kk, formed once) and the pivot column
     for (int c = tid; c < 2 * W; c += nth) {
-      if (c < W) rowk[c] = A[k * W + c];
-      else fcol[c - W] = A[(c - W) * W + k] * inv;
+      if (c < W) rowk[c] = c == k ? cdiv(mkc(1.0, 0.0, C{}), A[k * W + k]) : A[k * W + c];
+      else fcol[c - W] = A[(c - W) * W + k];
     }
     __syncthreads();
+    const C inv = rowk[k];
+    if (!finite_c(inv)) return false;              // every thread reads the same value
     if (own) {
-      const C rj = rowk[j];
+      const C t = j == k ? inv : rowk[j] * inv;    // a_kj / a_kk
       for (int i = rg; i < W; i += R_) {
         C v;
-        if (i == k) v = (j == k) ? inv : rj * inv;
-        else if (j == k) v = mkc(0.0, 0.0, C{}) - fcol[i];
-        else v = A[i * W + j] - fcol[i] * rj;
+        if (i == k) v = t;
+        else if (j == k) v = mkc(0.0, 0.0, C{}) - fcol[i] * inv;
+        else v = A[i * W + j] - fcol[i] * t;
         A[i * W + j] = v;
       }
     }
