@@ -28,8 +28,6 @@ template <> struct RealOf<cd> { using T = double; };
 template <> struct RealOf<cf> { using T = float; };
 __device__ __forceinline__ cd conjc(cd a) { return cd{a.x, -a.y}; }
 __device__ __forceinline__ cf conjc(cf a) { return cf{a.x, -a.y}; }
-__device__ __forceinline__ cd addc(cd a, cd b) { return cd{a.x + b.x, a.y + b.y}; }
-__device__ __forceinline__ cf addc(cf a, cf b) { return cf{a.x + b.x, a.y + b.y}; }
 
 // ---- seeds: wbar_ab = c_p (s_ab / w_ab - S_a / rowsum_a) for every row; one warp per row.
 // Injection-mode seeds ubar_m = P_hat + c_p s_m / u_m (rows = rows + 2 jobs per task: the last
