@@ -111,33 +111,44 @@ __global__ void gbar_sites_kernel(TaskDesc d, const C* __restrict__ G,
 
 // Pass B: lead columns of the site rows: for row a and lead r, y_nu = sum_x phi_nu(x)
 // G[(r,x)][a]; Gbar[(r,x)][a] += wbar_{a,n+r} sum_nu Gamma_nu phi_nu(x) conj(y_nu).
-// One thread per (a, x); the two leads are done one after the other (L = 1 puts both on
-// slice 0, so they must not run concurrently).
+// A CTA takes 256 / W sites a: thread (a, q) first forms y_q of its site (shared memory), then
+// the Gbar element of x = q, so that y is formed once per site rather than once per (a, x).
+// The two leads are done one after the other (L = 1 puts both on slice 0, so they must not
+// run concurrently).
 template <typename C>
-__global__ void gbar_leads_kernel(TaskDesc d, const C* __restrict__ G,
-                                  const double* __restrict__ wbar, const double* __restrict__ phi,
-                                  const double* __restrict__ gam, C* __restrict__ Gbar, int r) {
+__global__ void __launch_bounds__(256) gbar_leads_kernel(TaskDesc d, const C* __restrict__ G,
+                                                         const double* __restrict__ wbar,
+                                                         const double* __restrict__ phi,
+                                                         const double* __restrict__ gam,
+                                                         C* __restrict__ Gbar, int r) {
   using R = typename RealOf<C>::T;
+  __shared__ double sy[256][2];
   const int n = d.n, W = d.W, K = d.K;
   const int k0 = (r == 0 ? 0 : d.L - 1) * W;
-  const int total = n * W;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const int a = idx / W, x = idx % W;
-    const double wb = wbar[d.tab_off + (uint64_t)a * K + n + r];
-    if (wb == 0.0) continue;
+  const int per = 256 / W;                       // sites per CTA (W <= 64)
+  const int t = threadIdx.x, al = t / W, q = t - al * W;
+  const int a = blockIdx.x * per + al;
+  const bool live = al < per && a < n;
+  const double wb = live ? wbar[d.tab_off + (uint64_t)a * K + n + r] : 0.0;
+  if (wb != 0.0) {
+    double yx = 0.0, yy = 0.0;
+    for (int xx = 0; xx < W; ++xx) {
+      const C g = G[(uint64_t)(k0 + xx) * n + a];
+      yx += phi[xx * W + q] * (double)g.x;
+      yy += phi[xx * W + q] * (double)g.y;
+    }
+    sy[t][0] = yx;
+    sy[t][1] = yy;
+  }
+  __syncthreads();
+  if (wb != 0.0) {
     double tx = 0.0, ty = 0.0;
     for (int nu = 0; nu < W; ++nu) {
-      double yx = 0.0, yy = 0.0;
-      for (int xx = 0; xx < W; ++xx) {
-        const C g = G[(uint64_t)(k0 + xx) * n + a];
-        yx += phi[xx * W + nu] * (double)g.x;
-        yy += phi[xx * W + nu] * (double)g.y;
-      }
-      const double f = gam[nu] * phi[x * W + nu];
-      tx += f * yx;
-      ty -= f * yy;                                          // conj(y)
+      const double f = gam[nu] * phi[q * W + nu];
+      tx += f * sy[al * W + nu][0];
+      ty -= f * sy[al * W + nu][1];                  // conj(y)
     }
-    C* o = Gbar + (uint64_t)(k0 + x) * n + a;
+    C* o = Gbar + (uint64_t)(k0 + q) * n + a;
     o->x += (R)(wb * tx);
     o->y += (R)(wb * ty);
   }
@@ -375,8 +386,9 @@ cudaError_t backward_task(const TaskDesc& d, const C* G, const C* gphi, const do
   if (blocks > (unsigned)sm_count * 32) blocks = (unsigned)sm_count * 32;
   gbar_sites_kernel<C><<<blocks, 256, 0, s>>>(d, G, wbar, eta, Gbar);
   const unsigned bl = (unsigned)((n * W + 255) / 256);
-  gbar_leads_kernel<C><<<bl, 256, 0, s>>>(d, G, wbar, phi, gam, Gbar, 0);
-  gbar_leads_kernel<C><<<bl, 256, 0, s>>>(d, G, wbar, phi, gam, Gbar, 1);
+  const unsigned bll = (unsigned)((n + 256 / W - 1) / (256 / W));
+  gbar_leads_kernel<C><<<bll, 256, 0, s>>>(d, G, wbar, phi, gam, Gbar, 0);
+  gbar_leads_kernel<C><<<bll, 256, 0, s>>>(d, G, wbar, phi, gam, Gbar, 1);
   // the lead terms of the injection rows go through Y, which the product below overwrites
   gbar_inj_lead_kernel<C><<<(d.L == 1 ? 1 : 2) * W, 64, 0, s>>>(d, gphi, phi, gam, p, Y);
   gbar_inj_kernel<C><<<bl, 256, 0, s>>>(d, gphi, wbar, eta, phi, Y, p, Gbar);
