@@ -38,13 +38,14 @@ constexpr uint32_t kTmemCols = 256;         // D: 0..127; stage s: A hi at 128 +
 constexpr uint32_t kColD = 0, kColA = 128;
 constexpr uint32_t kLBO = 128, kSBO = 1024; // 8 core matrices (K' = 32) per 8-row group
 constexpr size_t kBSplit = (size_t)2 * kTileC * 32 * 4;   // one B split of one stage: 16 KB
-// two stages x (hi, lo); sized so that at most two CTAs share an SM's 512 TMEM columns
 constexpr int kAPitch = kTileK + 1;         // A tile staging [row][k], padded
 constexpr size_t kABytes = (size_t)kTileM * kAPitch * sizeof(cf);
+// two stages x (hi, lo) of B, the A staging, two mbarriers and the TMEM address
 constexpr size_t kSmemUsed = 4 * kBSplit + kABytes + 64;
 // the output staging of the epilogue reuses the operand buffers
 static_assert((size_t)kTileM * (kTileC + 1) * sizeof(cf) <= 4 * kBSplit + kABytes,
               "epilogue staging must fit the operand buffers");
+// at least 100 KB, so that at most two CTAs (2 x 256 TMEM columns) share an SM
 constexpr size_t kSmem = kSmemUsed > 100 * 1024 ? kSmemUsed : 100 * 1024;
 constexpr uint32_t kWaitLimit = 1u << 20;
 
