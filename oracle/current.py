@@ -8,6 +8,10 @@ Monte Carlo (Eq. elast_lin_xpq and the binomial variance model of Sec. IV.B.2): 
 contributes X = c_p delta_{rq}, so with n_q of N walkers absorbed at q,
     T_qp = c_p n_q / N,   SE(T_qp) = c_p sqrt(P (1 - P) / N),  P = n_q / N,
 and SE(I)^2 = sum_E (w_E (f_p - f_q))^2 SE(T_qp(E))^2 (energies are sampled independently).
+
+Pinned by: the Fermi function against its closed form and the current against a hand-summed
+two-energy case (test_fermi_and_current); the binomial standard error against the spread of
+independent replicas (test_binomial_standard_error_is_honest).
 """
 import numpy as np
 

@@ -10,6 +10,9 @@ Only diagonals propagate: with d^(0) = diag(A_p) and d^(n)_j = sum_i |G_ji|^2 lt
     term_0 = Tr[Gamma_q A_p],   term_n = sum_i lt_i d^(n-1)_i (G^dag Gamma_q G)_ii  (n >= 1).
 This is an independent route to T^eff (the Appendix B identity makes it equal to the probe
 solve and to the walk's absorption probability); it is used only as a pin.
+
+Pinned by: agreement with the probe solve and the exact chain on wires and chains of several
+sizes (test_three_routes_agree), each of those routes pinned by closed forms of its own.
 """
 import numpy as np
 

@@ -3,6 +3,8 @@
 Composes the pieces in the paper's order: G^r (Eq. eq_for_gr) -> Step 6' weights and Step 4
 injection distribution -> Vose alias tables -> exact walk expectation and the direct probe
 solve (Eq. buteq).  Nothing here adds arithmetic of its own.
+
+Pinned by: the pins of the functions it composes (wire, markov, buttiker, alias).
 """
 import numpy as np
 

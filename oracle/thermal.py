@@ -31,6 +31,13 @@ b with counter (b, wid_lo, wid_hi, 0x80000000 | wire):
   block b >= 2: transition b - 1: (x0, x1) on the current row of the table picked by x2 < a.
 A draw with words (x, y) over a K-entry row picks c = (x K) >> 32 and keeps c if y < thr[c],
 else alias[c].
+
+Pinned by (tests/test_oracle_thermal.py): Th against the central difference of the Fermi
+function and its integral against the closed-form CDF; the direct conductance of a clean chain
+and of a clean wire's channel staircase in closed form; the interpolated chain equal to the
+exact absorbing chain at alpha = 0 and 1 and converging to the direct conductance at the h^2
+rate of linear interpolation; the replay walker within 4 SE of the interpolated chain's exact
+expectation and its energies Kolmogorov-Smirnov-consistent with Th; planted mistakes caught.
 """
 import numpy as np
 

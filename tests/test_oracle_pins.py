@@ -394,6 +394,22 @@ def test_fermi_and_current():
     assert abs(I - 0.2 * np.sum(np.abs(E) < 0.5) - 0.2 * 0.5 * 2 * 0) < 0.2 + 1e-12 and dI == 0
 
 
+def test_current_integrates_to_the_bias():
+    """With T = 1 at every energy the current is the integral of f_p - f_q, which equals
+    mu_p - mu_q exactly (Landauer: one open channel carries the bias window); a sharp window
+    with T = 0.2 inside it gives 0.2 per grid weight inside."""
+    h = 1e-3
+    E = np.arange(-6.0 + h / 2, 6.0, h)
+    for mu_p, mu_q, kT in ((0.3, -0.1, 0.05), (-0.2, 0.45, 0.1), (0.0, 0.0, 0.02)):
+        I, dI = current.current(E, np.full(E.size, h), np.ones(E.size), np.zeros(E.size),
+                                mu_p, mu_q, kT)
+        assert abs(I - (mu_p - mu_q)) < 1e-9, (mu_p, mu_q, I)
+        assert dI == 0.0
+    Eg = np.linspace(-1, 1, 11)
+    I, _ = current.current(Eg, np.full(11, 0.2), np.ones(11), np.zeros(11), 0.5, -0.5, 1e-3)
+    assert abs(I - 0.2 * 5) < 1e-12
+
+
 # ---------------------------------------------------------------- planted mistakes
 
 def test_pins_catch_a_dropped_scattering_term(monkeypatch):
