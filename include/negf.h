@@ -399,25 +399,29 @@ negf_status negf_walk_thermal(negf_ctx ctx, negf_tables tables, int32_t wire, in
  * every device byte through its own pool, a process whose device footprint must not grow after
  * start-up, or code enqueuing work where a cudaMalloc would synchronise the device.
  *
- * It builds the same tables as negf_build_tables for ONE wire (host arrays, as with
- * NEGF_MEM_HOST; energy_weight is ignored) with the same kernels, but allocates nothing: all
- * scratch (task descriptors, lead self-energies, RGF blocks, FP weights, row sums) lives in one
- * file-scope device array of NEGF_NOALLOC_SCRATCH_BYTES (64 MiB) that every device which loads
- * the library holds until the process exits.  Inputs are copied into that array; results go to
- * caller-owned device buffers:
+ * It builds the one-level tables negf_build_tables builds for ONE wire (host arrays, as with
+ * NEGF_MEM_HOST; energy_weight is ignored and never read) with the same kernels, block-column
+ * chains included, so the alias entries are bit-identical; but it allocates nothing: all
+ * scratch (task descriptors, lead self-energies, RGF blocks, FP weights, row sums, chain jobs)
+ * lives in one file-scope device array of NEGF_NOALLOC_SCRATCH_BYTES (64 MiB) that every device
+ * which loads the library holds until the process exits.  Inputs are copied into that array;
+ * results go to caller-owned device buffers:
  *   d_alias       u64 [n_energy][rows][K]  alias entries (layout of NEGF_EXPORT_ALIAS per task,
  *                                          rows = W*L + 2W, K = W*L + 2)
  *   d_mode_alias  u64 [n_energy][2][W]     injection-mode alias entries
  *   d_c           f64 [n_energy][2]        Tr[Gamma_p A] for p = L, R
- * precision: NEGF_FP64 or NEGF_FP32 (NEGF_SPLIT_TF32 computes as NEGF_FP32 here).
+ * precision: NEGF_FP64 or NEGF_FP32 (NEGF_SPLIT_TF32 computes as NEGF_FP32 here, where
+ * negf_build_tables would build two-level tables on the tensor cores for W = 64).
  * The call runs on `stream` (a cudaStream_t on the current device) and synchronises it before
  * returning, so device-side failures are reported by its status.
  * Limits and errors: 1 <= n_energy <= NEGF_NOALLOC_MAX_TASKS and W*L <= NEGF_MAX_SITES, else
  * NEGF_E_INVALID; a problem whose scratch exceeds the fixed array returns NEGF_E_NOMEM (split
  * the energies over several calls); bad values as for negf_build_tables (NEGF_E_INVALID);
  * NEGF_E_NUMERIC for device-detected numerical failures; NEGF_E_CUDA for runtime failures.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  Every call uses the
+ * Every call looks up the array's device address on the current device (cudaGetSymbolAddress,
+ * so the address stays right after a cudaDeviceReset); the first lookup on a device sets up
+ * the library's device code there, so make the first call on each device before any stream
+ * capture.  Every call uses the
  * same array, which keeps the previous call's contents (the parts that must start at zero are
  * cleared by each call): calls that overlap on the GPU - from two host threads, or on two
  * streams of one device - race on the array and corrupt each other's results. */
@@ -425,6 +429,18 @@ negf_status negf_walk_thermal(negf_ctx ctx, negf_tables tables, int32_t wire, in
 #define NEGF_NOALLOC_MAX_TASKS 256
 negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t precision, void* stream,
                                       uint64_t* d_alias, uint64_t* d_mode_alias, double* d_c);
+
+/* --- device error words (paper silent) ------------------------------------------------------ */
+
+/* Kernels record failures by OR-ing bits into a device word of the handle (or plan, or call)
+ * that the next synchronising call reads: 1 a non-finite Green's function block or weight,
+ * 2 a table row whose weights do not sum to a positive value, 4 a device-resident input outside
+ * the domain, 8 a singular slice block, 16 a bounded device wait (the mbarrier waits of the
+ * tensor-core kernels) that gave up.  Returns the status such a word is reported as: NEGF_OK
+ * for 0, else NEGF_E_INVALID if bit 4 is set, else NEGF_E_TIMEOUT if bit 16 is set, else
+ * NEGF_E_NUMERIC.  If msg is non-NULL and cap > 0, msg receives the description (truncated to
+ * cap - 1 bytes, NUL-terminated).  Host only: touches no device. */
+negf_status negf_device_error_status(int32_t word, char* msg, size_t cap);
 
 /* --- profiling (CUDA events around every kernel launch) ----------------------------------- */
 

@@ -249,6 +249,16 @@ extern "C" {
 
 int negf_abi_version(void) { return NEGF_ABI_VERSION; }
 
+negf_status negf_device_error_status(int32_t word, char* msg, size_t cap) {
+  if (msg && cap > 0) {
+    const std::string s = word ? err_bits(word) : std::string();
+    const size_t k = std::min(s.size(), cap - 1);
+    memcpy(msg, s.data(), k);
+    msg[k] = 0;
+  }
+  return word ? err_status(word) : NEGF_OK;
+}
+
 negf_status negf_create(negf_ctx* out, int device, void* stream) {
   if (!out) return NEGF_E_INVALID;
   *out = nullptr;
@@ -323,6 +333,39 @@ negf_status negf_profile_read(negf_ctx ctx, int32_t cap, char* names, uint64_t* 
 const char* negf_last_error(negf_ctx ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
 }  // extern "C"
+
+namespace negf {
+
+// Jobs of the tensor-core and CTA-wide chains for task `k` (index in its wave): direction 0
+// takes every block column (it also emits the start slices) in pairs of neighbouring start
+// slices, from the far end; direction 1 the columns that have slices beyond their start.
+void add_tc_jobs(std::vector<TcJob>& jobs, int k, int L) {
+  std::vector<std::pair<int, int>> cols;             // (m0, y)
+  for (int y = 0; y < L + 2; ++y) cols.emplace_back(y < L ? y : (y == L ? 0 : L - 1), y);
+  std::vector<std::pair<int, int>> d0 = cols, d1;
+  std::stable_sort(d0.begin(), d0.end(), [](auto a, auto b) { return a.first > b.first; });
+  for (auto& c : cols)
+    if (c.first < L - 1) d1.push_back(c);
+  std::stable_sort(d1.begin(), d1.end(), [](auto a, auto b) { return a.first < b.first; });
+  for (size_t i = 0; i < d0.size(); i += 2)
+    jobs.push_back(TcJob{k, 0, d0[i].second, i + 1 < d0.size() ? d0[i + 1].second : -1});
+  for (size_t i = 0; i < d1.size(); i += 2)
+    jobs.push_back(TcJob{k, 1, d1[i].second, i + 1 < d1.size() ? d1[i + 1].second : -1});
+}
+
+// Longest chains first (the length of a job is the number of its steps).
+void sort_jobs_longest_first(std::vector<TcJob>& jobs, const TaskDesc* desc) {
+  auto len = [&](const TcJob& j) {
+    const TaskDesc& d = desc[j.task];
+    auto m0 = [&](int y) { return y < d.L ? y : (y == d.L ? 0 : d.L - 1); };
+    const int a = m0(j.y0), b = j.y1 >= 0 ? m0(j.y1) : a;
+    return j.dir == 0 ? std::max(a, b) : d.L - 1 - std::min(a, b);
+  };
+  std::stable_sort(jobs.begin(), jobs.end(),
+                   [&](const TcJob& x, const TcJob& y) { return len(x) > len(y); });
+}
+
+}  // namespace negf
 
 namespace {
 
@@ -510,22 +553,7 @@ struct Wave {
   uint32_t cta_narrow() const { return (uint32_t)(tcjobs.size() - n_tc - n_cta_wide); }
 };
 
-// Jobs of the tensor-core chain for fused task `k` (index in its wave): direction 0 takes every
-// block column (it also emits the start slices) in pairs of neighbouring start slices, from the
-// far end; direction 1 the columns that have slices beyond their start.
-void add_tc_jobs(std::vector<TcJob>& jobs, int k, int L) {
-  std::vector<std::pair<int, int>> cols;             // (m0, y)
-  for (int y = 0; y < L + 2; ++y) cols.emplace_back(y < L ? y : (y == L ? 0 : L - 1), y);
-  std::vector<std::pair<int, int>> d0 = cols, d1;
-  std::stable_sort(d0.begin(), d0.end(), [](auto a, auto b) { return a.first > b.first; });
-  for (auto& c : cols)
-    if (c.first < L - 1) d1.push_back(c);
-  std::stable_sort(d1.begin(), d1.end(), [](auto a, auto b) { return a.first < b.first; });
-  for (size_t i = 0; i < d0.size(); i += 2)
-    jobs.push_back(TcJob{k, 0, d0[i].second, i + 1 < d0.size() ? d0[i + 1].second : -1});
-  for (size_t i = 0; i < d1.size(); i += 2)
-    jobs.push_back(TcJob{k, 1, d1[i].second, i + 1 < d1.size() ? d1[i + 1].second : -1});
-}
+using negf::add_tc_jobs;
 
 Wave make_wave(const Plan& P, int t0, int t1) {
   Wave w;
@@ -570,17 +598,9 @@ Wave make_wave(const Plan& P, int t0, int t1) {
   for (TaskDesc& d : w.desc)
     if (d.layout == NEGF_LAYOUT_TWO_LEVEL) d.l1w_off += w.wt;
   w.adesc = alias_descs(w.desc);
-  // longest chains first (the length of a job is the number of its steps)
-  auto len = [&](const TcJob& j) {
-    const TaskDesc& d = w.desc[j.task];
-    auto m0 = [&](int y) { return y < d.L ? y : (y == d.L ? 0 : d.L - 1); };
-    const int a = m0(j.y0), b = j.y1 >= 0 ? m0(j.y1) : a;
-    return j.dir == 0 ? std::max(a, b) : d.L - 1 - std::min(a, b);
-  };
-  auto by_len = [&](const TcJob& x, const TcJob& y) { return len(x) > len(y); };
-  std::stable_sort(w.tcjobs.begin(), w.tcjobs.end(), by_len);
-  std::stable_sort(cta.begin(), cta.end(), by_len);
-  std::stable_sort(cta_n.begin(), cta_n.end(), by_len);
+  negf::sort_jobs_longest_first(w.tcjobs, w.desc.data());
+  negf::sort_jobs_longest_first(cta, w.desc.data());
+  negf::sort_jobs_longest_first(cta_n, w.desc.data());
   w.n_tc = w.tcjobs.size();
   w.n_cta_wide = cta.size();
   w.tcjobs.insert(w.tcjobs.end(), cta.begin(), cta.end());

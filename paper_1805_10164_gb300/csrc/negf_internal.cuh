@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/negf.h"
 
 namespace negf {
@@ -49,6 +51,12 @@ struct TaskDesc {
 struct TcJob {
   int32_t task, dir, y0, y1;
 };
+
+// Host side: append the chain jobs of task k (L slices) to `jobs` (every block column in
+// direction 0 in pairs, the columns with slices beyond their start in direction 1), and order
+// a job list longest chain first (desc: the descriptors the jobs' task indices refer to).
+void add_tc_jobs(std::vector<TcJob>& jobs, int k, int L);
+void sort_jobs_longest_first(std::vector<TcJob>& jobs, const TaskDesc* desc);
 
 struct cd { double x, y; };
 struct cf { float x, y; };

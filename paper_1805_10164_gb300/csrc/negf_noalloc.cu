@@ -4,27 +4,26 @@
 // that owns all device memory through its own pool (and forbids foreign allocations), or a
 // process that must not grow its device footprint after start-up, or a caller that enqueues
 // work from a context where an allocation would synchronise the device.  For them this entry
-// point runs the same kernels as negf_build_tables but takes every scratch buffer from one
-// file-scope device array of fixed size, and writes the tables into buffers the caller passes.
+// point runs the kernels negf_build_tables runs for the same wire and precision (one-level
+// tables) but takes every scratch buffer from one file-scope device array of fixed size, and
+// writes the tables into buffers the caller passes.
 // The array exists once per device that loads the library and stays allocated until the
 // process exits.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
 
+#include <vector>
+
 #include "negf_internal.cuh"
 
 namespace {
 
 constexpr size_t kScratchBytes = NEGF_NOALLOC_SCRATCH_BYTES;
-constexpr int kMaxDevices = 64;
 
 // The scratch array.  In host code its name is only a stand-in for the symbol, not a device
 // address: kernels must be given the address returned by cudaGetSymbolAddress.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
-
-// Device address of g_noalloc_scratch per device, looked up on the first call on that device.
-void* g_scratch_addr[kMaxDevices] = {nullptr};
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
@@ -64,6 +63,9 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
     if (!isfinite(wr.energy[k])) return NEGF_E_INVALID;
     if (wr.lead_model == NEGF_LEAD_STRIP && band_edge(wr.energy[k], wr.W, wr.t)) return NEGF_E_INVALID;
   }
+  // block columns as negf_build_tables takes them: FP32 wires of W = 64 or 16 < W <= 32 on the
+  // CTA-wide chains (jobs listed here), every other wire on the warp-per-column chains
+  const bool cta = prec == NEGF_FP32 && (wr.W == 64 || (wr.W > 16 && wr.W <= 32));
 
   // ---- carve the scratch array; reject problems that do not fit
   const size_t wsz = prec == NEGF_FP64 ? sizeof(double) : sizeof(float);
@@ -84,17 +86,17 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
   const size_t o_rs = off;     off += align256(sizeof(double) * nt * (rows + 2));
   const size_t o_mw = off;     off += align256(sizeof(double) * nt * 2 * wr.W);
   const size_t o_err = off;    off += align256(sizeof(int32_t));
+  // CTA-chain jobs: at most L + 2 per task (pairs of the L + 2 block columns in direction 0,
+  // pairs of at most L of them in direction 1)
+  const size_t o_jobs = off;   off += cta ? align256(sizeof(negf::TcJob) * nt * (size_t)(wr.L + 2)) : 0;
   if (off > kScratchBytes) return NEGF_E_NOMEM;   // the problem needs more than the fixed scratch
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NEGF_E_CUDA;
-  if (!g_scratch_addr[dev]) {
-    // first call on this device (the device is current): look up the array's device address
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return NEGF_E_CUDA;
-    g_scratch_addr[dev] = p;
-  }
-  unsigned char* base = static_cast<unsigned char*>(g_scratch_addr[dev]);
+  // The array's device address on the current device, looked up on every call (a host-side
+  // lookup; it stays right if the device's context was reset and the module reloaded).
+  void* scratch = nullptr;
+  if (cudaGetSymbolAddress(&scratch, g_noalloc_scratch) != cudaSuccess || !scratch)
+    return NEGF_E_CUDA;
+  unsigned char* base = static_cast<unsigned char*>(scratch);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
 
   TaskDesc h_tasks[NEGF_NOALLOC_MAX_TASKS];
@@ -112,7 +114,8 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
     d.lead_model = wr.lead_model;
     d.E = wr.energy[k];
     d.t = wr.t;
-    d.w_E = wr.energy_weight ? wr.energy_weight[k] : 1.0;
+    d.w_E = 1.0;                 // quadrature weights play no part in the tables
+    d.cta_chain = cta ? 1 : 0;
     d.gamma_lead = wr.gamma_lead;
     d.tab_off = (uint64_t)k * per_task_tab;
     d.wt_off = d.tab_off;
@@ -139,12 +142,21 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
   double* d_rs = reinterpret_cast<double*>(base + o_rs);
   double* d_mw = reinterpret_cast<double*>(base + o_mw);
   int32_t* d_err = reinterpret_cast<int32_t*>(base + o_err);
+  negf::TcJob* d_jobs = reinterpret_cast<negf::TcJob*>(base + o_jobs);
+  std::vector<negf::TcJob> jobs;                     // host memory only
+  if (cta) {
+    for (int k = 0; k < nt; ++k) negf::add_tc_jobs(jobs, k, wr.L);
+    negf::sort_jobs_longest_first(jobs, h_tasks);
+  }
 
   // the array keeps the previous call's contents: the error word must start at zero (every
   // other scratch value is written before it is read)
   cudaError_t e = cudaMemsetAsync(d_err, 0, sizeof(int32_t), s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_tasks, h_tasks, sizeof(TaskDesc) * nt, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !jobs.empty())
+    e = cudaMemcpyAsync(d_jobs, jobs.data(), sizeof(negf::TcJob) * jobs.size(),
+                        cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_wire, wr.onsite, sizeof(double) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
@@ -158,7 +170,12 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
   if (e == cudaSuccess)
     e = negf::launch_block_columns(d_tasks, nt, (uint32_t)(nt * (wr.L + 2)), wr.W, prec, d_wire,
                                    d_eta32, d_phi, d_phi32, d_sig, d_gam, d_gL, d_gR, d_st, d_w,
-                                   d_rs, d_mw, d_c, d_err, nullptr, nullptr, s);
+                                   d_rs, d_mw, d_c, d_err, nullptr, nullptr, s, 0,
+                                   cta ? 0 : wr.W);
+  if (e == cudaSuccess && cta)
+    e = negf::launch_chain_cta(d_tasks, d_jobs, wr.W == 64 ? (uint32_t)jobs.size() : 0u,
+                               wr.W == 64 ? 0u : (uint32_t)jobs.size(), d_eta32, d_phi32, d_gam,
+                               d_gL, d_gR, d_st, d_w, s);
   if (e == cudaSuccess)
     e = negf::launch_alias_build(d_tasks, nt, (uint32_t)(nt * (rows + 2)), (int)K, prec, d_w,
                                  d_rs, d_mw, d_alias, d_mode_alias, d_err, s);

@@ -89,6 +89,7 @@ def load():
     P, I32, U32, U64, D = C.c_void_p, C.c_int32, C.c_uint32, C.c_uint64, C.c_double
     sig = {
         "negf_abi_version": (C.c_int, []),
+        "negf_device_error_status": (I32, [I32, C.c_char_p, C.c_size_t]),
         "negf_create": (I32, [C.POINTER(P), C.c_int, P]),
         "negf_destroy": (None, [P]),
         "negf_last_error": (C.c_char_p, [P]),
@@ -377,6 +378,13 @@ def negf_build_tables_noalloc(wire, precision, stream, d_alias, d_mode_alias, d_
     handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return load().negf_build_tables_noalloc(C.byref(w), PRECISION[precision], C.c_void_p(handle),
                                             _ptr(d_alias), _ptr(d_mode_alias), _ptr(d_c))
+
+
+def negf_device_error_status(word):
+    """(status, description) a device error word is reported as (host only)."""
+    buf = C.create_string_buffer(256)
+    st = load().negf_device_error_status(int(word), buf, len(buf))
+    return st, buf.value.decode()
 
 
 def negf_probe_gather(ctx, table_bytes, ilp=8, chain=64):

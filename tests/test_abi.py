@@ -91,3 +91,22 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(negf, "library_path", lambda: str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="not built"):
         negf.load()
+
+
+def test_device_error_words_map_to_statuses(lib_path):
+    """The bits kernels set in a device error word surface as the documented statuses; a
+    bounded device wait that gave up (bit 16, the tensor-core kernels' mbarrier waits) is
+    NEGF_E_TIMEOUT unless an input error is also recorded."""
+    from paper_1805_10164_gb300 import negf
+    assert negf.negf_device_error_status(0) == (negf.NEGF_OK, "")
+    st, msg = negf.negf_device_error_status(16)
+    assert st == negf.NEGF_E_TIMEOUT and "bounded device wait" in msg
+    assert negf.negf_device_error_status(16 | 1)[0] == negf.NEGF_E_TIMEOUT
+    assert negf.negf_device_error_status(16 | 4)[0] == negf.NEGF_E_INVALID
+    for word in (1, 2, 8, 1 | 2 | 8):
+        assert negf.negf_device_error_status(word)[0] == negf.NEGF_E_NUMERIC
+    assert negf.negf_device_error_status(4)[0] == negf.NEGF_E_INVALID
+    lib = negf.load()
+    small = ctypes.create_string_buffer(8)
+    assert lib.negf_device_error_status(16, small, 8) == negf.NEGF_E_TIMEOUT
+    assert len(small.value) == 7

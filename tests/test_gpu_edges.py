@@ -7,6 +7,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from mc_bars import z_bar  # noqa: E402
 from oracle import alias, columns, pipeline  # noqa: E402
 from paper_1805_10164_gb300 import inputs, negf  # noqa: E402
 
@@ -70,7 +71,7 @@ def test_zero_walkers_and_single_site(ctx):
         negf.negf_tally_free(tl)
         for k, E in enumerate(w.energy):
             ref = pipeline.task_reference(w.onsite, w.eta, w.t, E, with_alias=False)
-            assert abs(res["T"][k] - ref["T_direct"][0, 1]) <= 4.0 * res["T_se"][k] + 1e-12
+            assert abs(res["T"][k] - ref["T_direct"][0, 1]) <= z_bar(2) * res["T_se"][k] + 1e-12
     finally:
         negf.negf_tables_free(t)
 
@@ -89,14 +90,14 @@ def test_no_dephasing_ends_every_walk_on_its_first_draw(ctx):
         assert np.all(counts[:, 4] == counts[:, 1] + counts[:, 2])      # one step per walk
         for k, E in enumerate(w.energy):
             ref = pipeline.task_reference(w.onsite, w.eta, w.t, E, with_alias=False)
-            assert abs(res["T"][k] - ref["T_direct"][1, 0]) <= 4.0 * res["T_se"][k] + 1e-6
+            assert abs(res["T"][k] - ref["T_direct"][1, 0]) <= z_bar(2) * res["T_se"][k] + 1e-6
     finally:
         negf.negf_tables_free(t)
 
 
 def test_largest_one_level_wire(ctx):
     """W = 64, L = 100 (6400 sites) with one-level tables forced: sampled rows realise the
-    oracle's weights (1e-5 of the row plus quantisation), MC transmission within 4 SE."""
+    oracle's weights (1e-5 of the row plus quantisation), T_LR = T_RL within 3 SE."""
     w = inputs.small_wire(305, W=64, L=100, n_energy=1, eta=0.05, disorder=0.5, e_lo=0.21,
                           e_hi=0.21)
     n = 6400
@@ -118,7 +119,7 @@ def test_largest_one_level_wire(ctx):
         res1 = negf.negf_current(ctx, t, tl, *MU)
         negf.negf_tally_free(tl)
         # reciprocity at this size (the dense direct solve is left to the smaller cases)
-        assert abs(res["T"][0] - res1["T"][0]) <= 4.5 * np.hypot(res["T_se"][0], res1["T_se"][0])
+        assert abs(res["T"][0] - res1["T"][0]) <= 3.0 * np.hypot(res["T_se"][0], res1["T_se"][0])
     finally:
         negf.negf_tables_free(t)
 

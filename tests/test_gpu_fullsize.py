@@ -3,16 +3,18 @@
 * Batched uneven wires (256 wires, W in 4..32, L in 20..200, 32 energies each) through the
   batched pipeline (negf_run) with a reduced walker count: properties that hold at any size
   (every walker accounted for, 0 <= T <= c_p, P(L) + P(R) = 1) for all 8192 tasks, and sampled
-  small tasks against the direct probe solve (within 4.5 standard errors).
+  small tasks against the direct probe solve (every |z| <= z_bar(m), sum z^2 <= chi2_bar(m);
+  mc_bars: the 3-SE bar as a 0.27 % family-wise false-alarm rate).
 * Differentiation case (W = 16, L = 100, 16 energies): the score-function gradient of the
-  current against the oracle's exact derivative on sampled sites (batch means, 4.5 SE).
+  current against the oracle's exact derivative on sampled sites (means of 16 batches, each
+  |t| within the family-wise bar of Student's t with 15 degrees of freedom).
 * Weak scattering (W = 64, L = 1000, eta = 0.005), two of its 256 energies at full size:
   sampled table rows (sites and injection modes) against the oracle's sparse column solves,
   realised two-level distribution within the quantisation bound + the precision's bar of the
   row and row sums within that bar: FP32 (CTA-wide CUDA-core chain) 1e-5; split TF32 (tensor
   cores) 1e-4, the measured systematic bias of the tensor-core accumulation over chains of up
   to 1000 slices being 3-5e-5; c_p 1e-5 for both; and the Monte Carlo transmission's
-  reciprocity T_RL = T_LR within 4.5 combined standard errors with every walker absorbed.
+  reciprocity T_RL = T_LR within z_bar(2) combined standard errors with every walker absorbed.
 """
 import numpy as np
 import pytest
@@ -20,6 +22,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from mc_bars import chi2_bar, t_bar, z_bar  # noqa: E402
 from oracle import adjoint, alias, buttiker, columns, current as ocur, wire as owire  # noqa: E402
 from paper_1805_10164_gb300 import inputs, negf  # noqa: E402
 
@@ -54,16 +57,19 @@ def test_batched_uneven_full_size(ctx):
         # sampled small tasks against the direct probe solve
         k = 0
         checked = 0
+        z = []
         for wi, w in enumerate(wires):
             if w.W * w.L <= 400 and checked < 4:
                 for e_idx in (3, 17):
                     g = owire.green_retarded(w.energy[e_idx], w.onsite, w.eta, w.t)
                     T_ref = buttiker.effective_transmission(g)[1, 0]
                     task = k + e_idx
-                    assert abs(res["T"][task] - T_ref) <= 4.5 * res["T_se"][task] + 1e-9, (wi, e_idx)
+                    z.append((res["T"][task] - T_ref) / res["T_se"][task])
                 checked += 1
             k += len(w.energy)
         assert checked >= 2
+        z = np.asarray(z)
+        assert np.max(np.abs(z)) <= z_bar(z.size) and np.sum(z ** 2) <= chi2_bar(z.size), z
     finally:
         negf.negf_tally_free(tl)
         negf.negf_tables_free(t)
@@ -87,7 +93,8 @@ def test_differentiation_case_full_size(ctx):
     tables = negf.negf_build_tables(ctx, [w], precision="fp32", keep_green=True)
     try:
         est = []
-        for b in range(8):
+        n_batch = 16
+        for b in range(n_batch):
             tally = negf.negf_walk_score(ctx, tables, 0, 99, 100_000, walker_id_offset=b * 100_000)
             dV, dE, cap = negf.negf_current_backward(ctx, tables, tally, wl.mu_p, wl.mu_q, wl.kT,
                                                      [1.0], n)
@@ -98,8 +105,9 @@ def test_differentiation_case_full_size(ctx):
         ref = np.concatenate([gV[sites], gE[sites]])
         mean = est.mean(0)
         se = est.std(0, ddof=1) / np.sqrt(len(est))
+        # batch means with their sample spread: Student t with n_batch - 1 degrees of freedom
         z = np.abs(mean - ref) / np.maximum(se, 1e-15)
-        assert np.all(z <= 4.5), (mean, ref, se)
+        assert np.all(z <= t_bar(z.size, n_batch - 1)), (mean, ref, se)
     finally:
         negf.negf_tables_free(tables)
 
@@ -143,6 +151,6 @@ def test_weak_scattering_full_size(ctx, precision, bar):
             assert np.all(counts[:, 1] + counts[:, 2] == N) and np.all(counts[:, 3] == 0)
             T[lead0] = (res["T"], res["T_se"])
         se = np.hypot(T[0][1], T[1][1])
-        assert np.all(np.abs(T[0][0] - T[1][0]) <= 4.5 * se), (T, se)
+        assert np.all(np.abs(T[0][0] - T[1][0]) <= z_bar(len(idx)) * se), (T, se)
     finally:
         negf.negf_tables_free(tables)

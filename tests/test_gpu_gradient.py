@@ -6,8 +6,9 @@ the oracle's exact FP64 derivative (pinned to finite differences of the direct p
   equal the exact derivative: 1e-8 of the largest component in FP64, 1e-4 in FP32 (the bar
   for gradients against finite differences); a 15-site wire and a 161-site one whose
   adjoint product spans several tiles of the tensor-core kernel with ragged tails.
-* Statistical: real walks; the gradient's projections on fixed directions must lie within 4.5
-  standard errors (batch means over independent walker-id ranges) of the exact values.
+* Statistical: real walks; the gradient's projections on fixed directions must lie within the
+  family-wise 3-SE bar of Student's t (mc_bars.t_bar; means of 20 batches over independent
+  walker-id ranges, their standard error from the batches' spread) of the exact values.
 """
 import numpy as np
 import pytest
@@ -15,6 +16,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from mc_bars import t_bar  # noqa: E402
 from oracle import adjoint, current as ocur, markov, pipeline, wire  # noqa: E402
 from paper_1805_10164_gb300 import inputs, negf  # noqa: E402
 
@@ -128,7 +130,8 @@ def test_gradient_from_walks_is_unbiased(ctx):
     tables = negf.negf_build_tables(ctx, [w], precision="fp64", keep_green=True)
     try:
         est = []
-        for b in range(10):
+        n_batch = 20
+        for b in range(n_batch):
             tally = negf.negf_walk_score(ctx, tables, p, 7, 200_000, walker_id_offset=b * 200_000)
             dV, dE, cap = negf.negf_current_backward(ctx, tables, tally, MU_P, MU_Q, KT, [1.0],
                                                      w.W * w.L)
@@ -139,7 +142,9 @@ def test_gradient_from_walks_is_unbiased(ctx):
         for d in dirs:
             proj = est @ d
             se = proj.std(ddof=1) / np.sqrt(len(proj))
-            assert abs(proj.mean() - g_exact @ d) <= 4.5 * se + 1e-12, (proj.mean(), g_exact @ d, se)
+            # batch means with their sample spread: Student t, n_batch - 1 degrees of freedom
+            assert abs(proj.mean() - g_exact @ d) <= t_bar(len(dirs), n_batch - 1) * se + 1e-12, \
+                (proj.mean(), g_exact @ d, se)
     finally:
         negf.negf_tables_free(tables)
 

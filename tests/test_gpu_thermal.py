@@ -2,9 +2,11 @@
 
 Bars: walks bit-exact against the oracle's replay walker on the exported tables, given the
 device's energy interval and alpha; those energy draws equal to the oracle's from the same
-Philox words (interval exactly, alpha within 2^-20); G within 4 standard errors of the exact
-expectation of the interpolated chain (quadrature of the oracle's FP64 chain); with a fine grid,
-G within 4 SE plus the linear-interpolation error bound of the direct conductance.
+Philox words (interval exactly, alpha within 2^-20); G against the exact expectation of the
+interpolated chain (quadrature of the oracle's FP64 chain) with every |z| <= z_bar(m) and
+sum z^2 <= chi2_bar(m) over the m wires (mc_bars: the 3-SE bar as a 0.27 % family-wise
+false-alarm rate); with a fine grid, G within 3 SE plus the linear-interpolation error bound of
+the direct conductance.
 """
 import numpy as np
 import pytest
@@ -12,6 +14,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from mc_bars import chi2_bar, z_bar  # noqa: E402
 from oracle import pipeline, thermal  # noqa: E402
 from oracle.philox import philox4x32_10  # noqa: E402
 from paper_1805_10164_gb300 import inputs, negf  # noqa: E402
@@ -101,15 +104,18 @@ def test_thermal_conductance_matches_interpolated_chain(ctx, precision):
     wires = [cw[0] for cw in cases]
     tables = negf.negf_build_tables(ctx, wires, precision=precision)
     try:
+        z = []
         for wi, (w, mu, kT) in enumerate(cases):
             tabs = [pipeline.task_reference(w.onsite, w.eta, w.t, E, with_alias=False)["tab"]
                     for E in w.energy]
             G_ref = thermal.conductance_interpolated(tabs, w.energy, mu, kT, n_quad=24)
             res = negf.negf_walk_thermal(ctx, tables, wi, 0, 77 + wi, 2_000_000, mu, kT)
             assert not res["stepcap"]
-            assert abs(res["G"] - G_ref) <= 4.0 * res["se"] + 1e-6 * G_ref, (wi, res, G_ref)
+            z.append((res["G"] - G_ref) / (res["se"] + 1e-6 * G_ref))
+            assert abs(z[-1]) <= z_bar(len(cases)), (wi, res, G_ref)
             window = thermal.th_cdf(w.energy[-1], mu, kT) - thermal.th_cdf(w.energy[0], mu, kT)
             assert abs(res["window"] - window) < 1e-12
+        assert np.sum(np.square(z)) <= chi2_bar(len(z)), z
     finally:
         negf.negf_tables_free(tables)
 
@@ -129,7 +135,7 @@ def test_thermal_fine_grid_approaches_direct_conductance(ctx):
     tables = negf.negf_build_tables(ctx, [w], precision="fp32")
     try:
         res = negf.negf_walk_thermal(ctx, tables, 0, 0, 99, 4_000_000, mu, kT)
-        assert abs(res["G"] - G_dir) <= 4.0 * res["se"] + bound, (res, G_dir, bound)
+        assert abs(res["G"] - G_dir) <= 3.0 * res["se"] + bound, (res, G_dir, bound)
     finally:
         negf.negf_tables_free(tables)
 

@@ -9,6 +9,7 @@ import textwrap
 import numpy as np
 import pytest
 
+from mc_bars import z_bar
 from oracle import alias, buttiker, current, markov, neumann, philox, pipeline, walker, wire
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -256,10 +257,10 @@ def test_walker_statistics_match_exact_chain():
     assert np.all(lead >= 0)
     P = r["exact"]["P_inj"][0, 1]
     Phat = np.mean(lead == 1)
-    assert abs(Phat - P) < 4.5 * np.sqrt(P * (1 - P) / N)
+    assert abs(Phat - P) < z_bar(2) * np.sqrt(P * (1 - P) / N)
     m = r["exact"]["steps_inj"][0]
     var = r["exact"]["steps2_inj"][0] - m * m
-    assert abs(steps.mean() - m) < 4.5 * np.sqrt(var / N)
+    assert abs(steps.mean() - m) < z_bar(2) * np.sqrt(var / N)
     assert abs(steps.var() / var - 1.0) < 0.1
 
 
@@ -288,10 +289,10 @@ def test_two_level_walker_statistics_match_exact_chain():
                                         max_steps=10**6)
     assert np.all(lead >= 0)
     P = r["exact"]["P_inj"][0, 1]
-    assert abs(np.mean(lead == 1) - P) < 4.5 * np.sqrt(P * (1 - P) / N)
+    assert abs(np.mean(lead == 1) - P) < z_bar(2) * np.sqrt(P * (1 - P) / N)
     m = r["exact"]["steps_inj"][0]
     var = r["exact"]["steps2_inj"][0] - m * m
-    assert abs(steps.mean() - m) < 4.5 * np.sqrt(var / N)
+    assert abs(steps.mean() - m) < z_bar(2) * np.sqrt(var / N)
     # truncation as in the one-level walker
     lead2, steps2 = walker.walk_two_level(l1, l2, r["mode_entries"], r["n"], 8, 3, r["c_open"],
                                           3, 0, 1234, np.arange(2000), 2)

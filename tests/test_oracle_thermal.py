@@ -101,7 +101,7 @@ def test_replay_walker_matches_interpolated_expectation():
     window = thermal.th_cdf(grid[-1], mu, kT) - thermal.th_cdf(grid[0], mu, kT)
     G, se = thermal.estimate(lead, a, iv, c, window, 0)
     G_exact = thermal.conductance_interpolated(tabs, grid, mu, kT)
-    assert abs(G - G_exact) <= 4.0 * se, (G, G_exact, se)
+    assert abs(G - G_exact) <= 3.0 * se, (G, G_exact, se)
     # the energy draws follow Th restricted to the span (Kolmogorov-Smirnov, 1 % level)
     E = grid[iv] + (a.astype(np.float64) / 2.0 ** 32) * (grid[iv + 1] - grid[iv])
     F = (thermal.th_cdf(np.sort(E), mu, kT) - thermal.th_cdf(grid[0], mu, kT)) / window

@@ -2,10 +2,14 @@
 
 Callers that cannot allocate device memory (a host framework owning every device byte through
 its own pool, a process whose device footprint is fixed after start-up) use this entry point;
-it must give the same tables as negf_build_tables.  Two calls in a row (a larger wire, then a
-smaller one, so the second call runs on scratch the first one left behind) are each compared
-with negf_build_tables: alias entries bit for bit (same kernels, deterministic), c_p to the FP64
-table bar of the parity tests (1e-10 relative).  Kept in a file collected last.
+it must give the same tables as negf_build_tables.  Calls in a row (wide wires first, then
+smaller ones, so later calls run on scratch earlier ones left behind) are each compared with
+negf_build_tables: alias entries bit for bit (same kernels, deterministic), c_p to the FP64
+table bar of the parity tests (1e-10 relative).  The FP32 cases of W = 24 and W = 64 take the
+CTA-wide block-column chains; they are also compared with the FP64 oracle: every alias row's
+exact implied distribution within the quantisation bound (K + 2) 2^-32 plus the FP32 table bar
+(1e-5 of the row) of the oracle's weights over their row sum, c_p within 1e-5.  Kept in a file
+collected last.
 """
 import numpy as np
 import pytest
@@ -13,6 +17,7 @@ import pytest
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
+from oracle import alias as oalias, pipeline  # noqa: E402
 from paper_1805_10164_gb300 import inputs, negf  # noqa: E402
 
 
@@ -29,6 +34,24 @@ def _reference(ctx, wire, precision):
         negf.negf_tables_free(tables)
 
 
+def _check_against_oracle(wire, alias_rows, c):
+    n, W = wire.W * wire.L, wire.W
+    rows, K = n + 2 * W, n + 2
+    rng = np.random.default_rng(wire.W)
+    for k, E in enumerate(wire.energy):
+        ref = pipeline.task_reference(wire.onsite, wire.eta, wire.t, E, with_alias=False,
+                                      with_direct=False)
+        w = ref["tab"]["w"]
+        assert np.allclose(c[k], ref["tab"]["c"], rtol=1e-5, atol=0.0), k
+        ent = alias_rows[k].reshape(rows, K)
+        for r in np.concatenate([rng.choice(rows, size=24, replace=False), [0, n - 1, n, rows - 1]]):
+            A = w[r].sum()
+            if A <= 0:
+                continue
+            p = oalias.implied_distribution(ent[r])
+            assert np.max(np.abs(p - w[r] / A)) <= (K + 2) * 2.0**-32 + 1e-5, (k, r)
+
+
 def test_noalloc_build_matches_allocating_build():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
@@ -38,7 +61,9 @@ def test_noalloc_build_matches_allocating_build():
     stream = torch.cuda.current_stream()
     ctx = negf.negf_create(0, stream)
     try:
-        cases = [(inputs.small_wire(61, W=6, L=12, n_energy=5, eta=0.08), "fp32"),
+        cases = [(inputs.small_wire(65, W=24, L=5, n_energy=3, eta=0.06), "fp32"),
+                 (inputs.small_wire(66, W=64, L=3, n_energy=2, eta=0.05, disorder=0.5), "fp32"),
+                 (inputs.small_wire(61, W=6, L=12, n_energy=5, eta=0.08), "fp32"),
                  (inputs.small_wire(62, W=3, L=5, n_energy=2, eta=0.2), "fp64")]
         for wire, prec in cases:
             n_e, W, L = len(wire.energy), wire.W, wire.L
@@ -54,9 +79,11 @@ def test_noalloc_build_matches_allocating_build():
             c = d_c.cpu().numpy().reshape(n_e, 2)
             ref = _reference(ctx, wire, prec)
             for k, (a_ref, m_ref, c_ref) in enumerate(ref):
-                assert np.array_equal(alias[k], a_ref), (prec, k)
-                assert np.array_equal(mode[k], m_ref), (prec, k)
-                assert np.allclose(c[k], c_ref, rtol=1e-10, atol=0.0), (prec, k)
+                assert np.array_equal(alias[k], a_ref), (W, prec, k)
+                assert np.array_equal(mode[k], m_ref), (W, prec, k)
+                assert np.allclose(c[k], c_ref, rtol=1e-10, atol=0.0), (W, prec, k)
+            if W > 16:
+                _check_against_oracle(wire, alias, c)
     finally:
         negf.negf_destroy(ctx)
 
