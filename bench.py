@@ -194,6 +194,11 @@ def two_level(W, L, precision):
     return (precision == "split_tf32" and W == 64) or W * L > 2048
 
 
+def level2_words(W):
+    """u32 words of one level-2 inverse-CDF block (NEGF_LEVEL2_WORDS)."""
+    return 8 if W <= 8 else 8 + 8 * ((W + 7) // 8)
+
+
 def algorithmic_bytes(kernel, wl, precision, counts):
     """Bytes a kernel must move per launch by its definition (tables in, tables out)."""
     tasks = [(w.W, w.L) for w in wl.wires for _ in w.energy]
@@ -205,17 +210,22 @@ def algorithmic_bytes(kernel, wl, precision, counts):
         walkers = int(counts[:, 0].sum())
         steps = int(counts[:, 4].sum())
         absorbed = int(counts[:, 1].sum() + counts[:, 2].sum())
-        # one 8-byte entry per draw; two-level tables: a level-1 entry per transition and a
-        # level-2 entry per transition that stays in the wire
+        # one 8-byte entry per draw; two-level tables: a level-1 entry per transition and, per
+        # transition that stays in the wire, the level-2 guide and one octet (32 B each; the
+        # octet alone for W <= 8)
         if two and not one:
-            return 8 * (walkers + steps + (steps - absorbed))
+            Ws = {W for _, W, _ in two}
+            if len(Ws) != 1:
+                return None
+            l2 = 32 if min(Ws) <= 8 else 64
+            return 8 * (walkers + steps) + l2 * (steps - absorbed)
         if two:
             return None
         return 8 * (steps + walkers)
     if kernel == "alias_kernel":           # one-level rows, or the level-1 rows
         return sum(r * K for r, K in one) * (wsz + 8) + sum(r * (L + 2) for r, W, L in two) * (wsz + 8)
-    if kernel == "two_level_kernel":       # read the weights, write level-2 entries and level-1 weights
-        return sum(r * (W * L) * (wsz + 8) + r * L * wsz for r, W, L in two)
+    if kernel == "two_level_kernel":       # read the weights, write level-2 blocks and level-1 weights
+        return sum(r * (W * L) * wsz + r * L * (4 * level2_words(W) + wsz) for r, W, L in two)
     if kernel in ("diag_chain_kernels", "chain_cta_kernel", "chain_tc_kernel"):
         return sum(r * K for r, K in one) * wsz + sum(r * (W * L + 2) for r, W, L in two) * wsz
     return None

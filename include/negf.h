@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define NEGF_ABI_VERSION 3
+#define NEGF_ABI_VERSION 4
 #define NEGF_MAX_W 64            /* widest supported slice (sites across the wire) */
 #define NEGF_MAX_SITES 6400      /* largest W*L per wire with one-level tables */
 #define NEGF_MAX_SITES_TWO_LEVEL 65536 /* largest W*L per wire with two-level tables */
@@ -111,14 +111,22 @@ typedef struct {
 /* Layout of the Step 6' tables of a task.
  * One-level: one alias row of K = n + 2 slots per table row (draw: one 8-byte entry).
  * Two-level: the draw over the n + 2 outcomes factorises exactly into a level-1 draw over the L
- * slices and the two leads (weights: the slice totals of the row and the lead weights) and,
- * for a slice k, a level-2 draw over the W sites of that slice (weights: the row's weights of
- * those sites).  Entries: level 2 u64 [rows][L][W], level 1 u64 [rows][L + 2].  Table memory
- * is rows * (n + L + 2) entries either way; the build needs no per-row shared-memory pass over
- * n + 2 entries, which makes it the layout of long wires (a one-level row of K slots is
- * built by one warp with 32 K bytes of shared memory, which leaves few warps per SM once K is
- * in the thousands).  NEGF_LAYOUT_AUTO: two-level when W*L > NEGF_AUTO_TWO_LEVEL_SITES, or for
- * W = 64 wires built with NEGF_SPLIT_TF32. */
+ * slices and the two leads (weights: the slice totals of the row and the lead weights; an
+ * alias row of L + 2 slots) and, for a slice k, a level-2 draw over the W sites of that slice
+ * (weights: the row's weights of those sites) by the inverse-CDF search of Sec. III.B in
+ * integers.  A level-2 block holds G = ceil(W/8) octets of 31-bit cumulative thresholds
+ * c_a = floor(2^31 P_a / S) (P_a the sum of the slice's weights up to site a, S their total;
+ * c_{W-1} and the padding of the last octet are 2^31) and, for W > 8, an 8-word guide in front
+ * (guide_g = c_{8g+7} for g < G - 1, then 2^31): NEGF_LEVEL2_WORDS(W) = 8 (W <= 8) or 8 + 8G
+ * u32.  A draw with v uniform on [0, 2^31) takes g = #{guide words <= v}, then site
+ * 8g + #{words of octet g <= v}: site a has probability (c_a - c_{a-1}) / 2^31.  Entries:
+ * level 2 u32 [rows][L][NEGF_LEVEL2_WORDS(W)] (starting on a 32-byte boundary), level 1 u64
+ * [rows][L + 2].  The build needs no per-row shared-memory pass over n + 2 entries (a one-level
+ * row of K slots is built by one warp with 32 K bytes of shared memory, which leaves few warps
+ * per SM once K is in the thousands) and level 2 costs a prefix sum per slice, which makes it
+ * the layout of long wires.  NEGF_LAYOUT_AUTO: two-level when W*L > NEGF_AUTO_TWO_LEVEL_SITES,
+ * or for W = 64 wires built with NEGF_SPLIT_TF32. */
+#define NEGF_LEVEL2_WORDS(W) ((W) <= 8 ? 8 : 8 + 8 * (((W) + 7) / 8))
 typedef enum { NEGF_LAYOUT_AUTO = 0, NEGF_LAYOUT_ONE_LEVEL = 1, NEGF_LAYOUT_TWO_LEVEL = 2 } negf_table_layout;
 
 /* Per-task facts, read back from the device (synchronises). */
@@ -167,7 +175,7 @@ void negf_tables_free(negf_tables tables);
 
 /* Copy one task's data to host memory.  `what`:
  *   NEGF_EXPORT_ALIAS       u64 [rows*K]  alias entries, row-major (two-level tasks: the level-2
- *                                         entries u64 [rows][L][W])
+ *                                         blocks u32 [rows][L][NEGF_LEVEL2_WORDS(W)])
  *   NEGF_EXPORT_ALIAS_LEVEL1 u64 [rows][L+2] level-1 entries of a two-level task
  *   NEGF_EXPORT_MODE_ALIAS  u64 [2*W]     injection-mode alias entries, lead L then R
  *   NEGF_EXPORT_WEIGHTS     f64 [rows*K]  transition weights (needs keep_weights)
@@ -180,8 +188,8 @@ enum { NEGF_EXPORT_ALIAS = 0, NEGF_EXPORT_MODE_ALIAS = 1, NEGF_EXPORT_WEIGHTS = 
 negf_status negf_export_tables(negf_ctx ctx, negf_tables tables, int32_t task, int32_t what,
                                void* host_buf, size_t* bytes);
 /* Rows [row0, row0 + n_rows) of one task's NEGF_EXPORT_ALIAS, NEGF_EXPORT_ALIAS_LEVEL1 or
- * NEGF_EXPORT_ROWSUM data (same per-row layout as negf_export_tables), for tables too large
- * to copy whole.  Buffer sizing and errors as negf_export_tables; rows outside [0, rows) or
+ * NEGF_EXPORT_ROWSUM data (same per-row layout as negf_export_tables: a two-level row's level 2
+ * is L * NEGF_LEVEL2_WORDS(W) u32), for tables too large to copy whole.  Buffer sizing and errors as negf_export_tables; rows outside [0, rows) or
  * another kind give NEGF_E_INVALID.  Synchronises. */
 negf_status negf_export_table_rows(negf_ctx ctx, negf_tables tables, int32_t task, int32_t what,
                                    int64_t row0, int64_t n_rows, void* host_buf, size_t* bytes);

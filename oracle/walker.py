@@ -15,6 +15,7 @@ absorption (the walk is cut, the sample is counted as truncated).
 """
 import numpy as np
 
+from .alias import draw_level2
 from .philox import philox4x32_10
 
 MASK32 = np.uint64(0xFFFFFFFF)
@@ -81,12 +82,14 @@ def walk(entries, mode_entries, n, W, c_open, task, start_lead, seed, wids, max_
 
 def walk_two_level(level1, level2, mode_entries, n, L, W, c_open, task, start_lead, seed, wids,
                    max_steps):
-    """The same walk over two-level tables (level1 [n + 2W, L + 2], level2 [n + 2W, L, W]).
+    """The same walk over two-level tables (level1 [n + 2W, L + 2] alias entries, level2
+    [n + 2W, L, alias.level2_words(W)] inverse-CDF blocks).
 
     Random numbers: Philox block 0 of the walker is the injection draw (words x0, x1); block
     s >= 1 is transition s: words (x0, x1) draw the slice or lead from the row's level-1 entries
-    (K1 = L + 2), and for a slice k the words (x2, x3) draw the site a from level-2 row (row, k)
-    of W entries; the next row is k*W + a.  Outcomes and step counts as in ``walk``.
+    (K1 = L + 2), and for a slice k the word x2 draws the site a from level-2 block (row, k)
+    with v = x2 >> 1 (alias.draw_level2); the next row is k*W + a.  Outcomes and step counts as
+    in ``walk``.
     Pinned by: absorption probabilities and mean steps against the exact chain expectation.
     """
     wids = np.asarray(wids, dtype=np.uint64)
@@ -127,9 +130,8 @@ def walk_two_level(level1, level2, mode_entries, n, L, W, c_open, task, start_le
             done = k >= L
             lead[active[done]] = (k[done] - L).astype(np.int32)
             kk = np.where(done, 0, k)
-            c2 = ((x2 * np.uint64(W)) >> np.uint64(32)).astype(np.int64)
-            e2 = level2[r, kk, c2]
-            a = np.where(x3 < (e2 & MASK32), c2, (e2 >> np.uint64(32)).astype(np.int64))
+            v = (x2 >> np.uint64(1)).astype(np.int64)
+            a = draw_level2(level2[r, kk], W, v)
             row[active] = np.where(done, 0, kk * W + a)
             active = active[~done]
         s += 1

@@ -333,24 +333,120 @@ __global__ void alias_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
   cp_async_wait_all();
 }
 
-// One warp per table row of a two-level task.  The row is taken in chunks of 32 slices: the
-// chunk's weights are staged in shared memory by coalesced loads, each lane builds one slice's
-// level-1 weight and level-2 alias row in shared memory (in the memory of the slice's weights,
-// which it reads first), and the chunk's entries (32 consecutive level-2 rows) leave by
-// coalesced stores.
-constexpr int kTlWarps = 4;
-constexpr int kTlPitch = 65;                         // padded slice pitch (W <= 64)
+// ---- Level-2 inverse-CDF blocks of two-level tables --------------------------------------
+//
+// Within a slice the site is drawn by the paper's own categorical draw (Sec. III.B: cumulative
+// sum of the weights, normalised, the first entry above a uniform), in integers: for the W site
+// weights w_a of (table row, slice), c_a = floor(2^31 P_a / S) with P_a = sum_{b <= a} w_b and
+// S = P_{W-1}, for a < W - 1; c_{W-1} and the padding of the last octet are 2^31.  Octet g holds
+// c_{8g .. 8g+7}; for W > 8 an 8-word guide precedes the octets, guide_g = c_{8g+7} for
+// g < G - 1 and 2^31 after (G = ceil(W / 8)).  The walk draws v = x >> 1 (31 bits), takes
+// g = #{guide words <= v} and the site 8g + #{words of octet g <= v}, so site a has probability
+// (c_a - c_{a-1}) / 2^31 and a zero weight is never drawn.  A slice whose weights sum to zero
+// gets 2^31 everywhere (its level-1 weight is zero, so it is never drawn).
+// FP32 weights: s = 2^sh with (FP32 sum) s in [2^29, 2^30); m_a = floor(w_a s) (exact scaling
+// and truncation), P_a = sum m (exact integers, < 2^31), T = P_{W-1}, c_a = floor(P_a R / 2^31)
+// with R = floor(2^62 / T) (within one unit below floor(2^31 P_a / T), nondecreasing in P_a),
+// c_a = 2^31 where P_a = T; the slice's level-1 weight is T / s.  FP64 weights: P_a, S and c_a
+// in FP64, level-1 weight S.
+// One warp per table row, chunks of 32 slices: the chunk's weights are staged by coalesced loads,
+// each lane forms one slice's block in registers and writes it into its shared region (odd pitch
+// in 4-byte words), and the chunk's blocks (32 consecutive blocks of the row) leave by coalesced
+// stores.
+constexpr int kL2Warps = 4;
+constexpr uint32_t kCdfOne = 1u << 31;
+__device__ __forceinline__ float pow2f_l2(int e) { return __int_as_float((e + 127) << 23); }
 
+// Region pitch in 4-byte words: holds W weights of type R and a block of B2 words; odd for
+// 4-byte accesses, 2 mod 4 for 8-byte ones (conflict-free across a half-warp).
 template <typename R>
-__global__ void __launch_bounds__(32 * kTlWarps) two_level_kernel(
+__host__ __device__ inline int level2_pitch(int W, int B2) {
+  const int need = (int)(W * sizeof(R) / 4) > B2 ? (int)(W * sizeof(R) / 4) : B2;
+  if (sizeof(R) == 4) return need | 1;
+  int p = (need + 1) & ~1;
+  if ((p & 3) == 0) p += 2;
+  return p;
+}
+
+template <typename R, int WB>
+__device__ __forceinline__ bool level2_block(uint32_t* reg, int W, int B2, R* total) {
+  const R* wk = reinterpret_cast<const R*>(reg);
+  uint32_t c[WB];
+  bool ok = true;
+  R tot = 0;
+  if constexpr (sizeof(R) == 4) {
+    float S = 0.f;
+#pragma unroll
+    for (int a = 0; a < WB; ++a)
+      if (a < W) S += wk[a];
+    if (!(S >= 0.f && S < INFINITY)) ok = false;
+    if (S > 0.f && S < INFINITY) {
+      int e = 0;
+      frexpf(S, &e);                             // S = f 2^e, f in [1/2, 1)
+      const int sh = 30 - e, sh1 = sh / 2, sh2 = sh - sh / 2;
+      const float p1 = pow2f_l2(sh1), p2 = pow2f_l2(sh2);
+      uint32_t T = 0;
+#pragma unroll
+      for (int a = 0; a < WB; ++a) {
+        const float v = a < W ? wk[a] : 0.f;
+        const uint32_t m = v > 0.f ? __float2uint_rz((v * p1) * p2) : 0u;
+        c[a] = m;
+        T += m;
+      }
+      tot = (__uint2float_rn(T) * pow2f_l2(-sh1)) * pow2f_l2(-sh2);
+      const uint64_t Rr = (1ull << 62) / (uint64_t)T;   // T >= 2^29 - W
+      uint32_t P = 0;
+#pragma unroll
+      for (int a = 0; a < WB; ++a) {
+        P += c[a];
+        const uint32_t q = (uint32_t)(((uint64_t)P * Rr) >> 31);
+        c[a] = P == T ? kCdfOne : min(q, kCdfOne - 1u);
+      }
+    } else {
+#pragma unroll
+      for (int a = 0; a < WB; ++a) c[a] = kCdfOne;
+    }
+  } else {
+    double S = 0.0;
+#pragma unroll
+    for (int a = 0; a < WB; ++a)
+      if (a < W) S += wk[a];
+    if (!(S >= 0.0 && S < INFINITY)) ok = false;
+    if (S > 0.0 && S < INFINITY) {
+      const double scale = 2147483648.0 / S;
+      double P = 0.0;
+#pragma unroll
+      for (int a = 0; a < WB; ++a) {
+        P += a < W ? wk[a] : 0.0;
+        c[a] = P >= S ? kCdfOne : min(__double2uint_rz(P * scale), kCdfOne - 1u);
+      }
+      tot = S;
+    } else {
+#pragma unroll
+      for (int a = 0; a < WB; ++a) c[a] = kCdfOne;
+    }
+  }
+  // c_{W-1} and the padding of the last octet are 2^31 (the weights have been read)
+  const int G = (W + 7) >> 3;
+  uint32_t* oct = G > 1 ? reg + 8 : reg;
+#pragma unroll
+  for (int a = 0; a < WB; ++a)
+    if (a < 8 * G) oct[a] = a < W - 1 ? c[a] : kCdfOne;
+  if (G > 1) {
+#pragma unroll
+    for (int g = 0; g < 8; ++g) reg[g] = (g < G - 1 && 8 * g + 7 < WB) ? c[8 * g + 7] : kCdfOne;
+  }
+  *total = tot;
+  return ok;
+}
+
+template <typename R, int WB>
+__global__ void __launch_bounds__(32 * kL2Warps) level2_cdf_kernel(
     const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs, R* __restrict__ weights,
     uint64_t* __restrict__ tab, int32_t* err) {
-  extern __shared__ __align__(16) unsigned char tl_smem[];
+  extern __shared__ __align__(16) unsigned char l2_smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // one buffer per warp: slice s's weights, then its units and entries, at s * kTlPitch u64
-  uint64_t* so = reinterpret_cast<uint64_t*>(tl_smem) + (size_t)warp * 32 * kTlPitch;
-  auto sw = [&](int slice) { return reinterpret_cast<R*>(so + (size_t)slice * kTlPitch); };
-  const uint32_t job = blockIdx.x * kTlWarps + warp;
+  const uint32_t job = blockIdx.x * kL2Warps + warp;
   if (job >= n_jobs) return;
   int lo = 0, hi = n_tasks - 1;
   while (lo < hi) {
@@ -362,40 +458,61 @@ __global__ void __launch_bounds__(32 * kTlWarps) two_level_kernel(
   const int row = (int)(job - d.row_base);
   if (row >= d.rows) return;
   const int W = d.W, L = d.L, n = d.n;
+  const int B2 = level2_words(W);
+  const int PW = level2_pitch<R>(W, B2);
+  uint32_t* wbase = reinterpret_cast<uint32_t*>(l2_smem) + (size_t)warp * 32 * PW;
   const R* wr = weights + d.wt_off + (uint64_t)row * d.K;
   R* l1 = weights + d.l1w_off + (uint64_t)row * (L + 2);
-  uint64_t* l2 = tab + d.tab_off + (uint64_t)row * n;
+  uint32_t* l2 = reinterpret_cast<uint32_t*>(tab + d.tab_off) + (uint64_t)row * L * B2;
+  constexpr int EW = (int)(sizeof(R) / 4);          // words per weight
+  const int eq = 32 / W, er = 32 - (32 / W) * W;
   bool ok = true;
-  const int dq = 32 / W, dr = 32 - (32 / W) * W;
   for (int k0 = 0; k0 < L; k0 += 32) {
     const int ns = min(32, L - k0);
     const R* wc = wr + (uint64_t)k0 * W;
-    // element i = lane + 32 j of the chunk is entry r of slice q; (q, r) advance by (dq, dr)
-    int q = lane / W, r = lane - (lane / W) * W;
-    for (int i = lane; i < ns * W; i += 32) {
-      sw(q)[r] = wc[i];
-      q += dq;
-      r += dr;
-      if (r >= W) { r -= W; ++q; }
+    if (EW == 1 && (W & 1) == 0 && (reinterpret_cast<uintptr_t>(wc) & 7) == 0) {
+      // FP32 pairs (a pair never straddles two slices when W is even)
+      const int hw = W >> 1;
+      const int pq = 32 / hw, pr = 32 - (32 / hw) * hw;
+      int q = lane / hw, r = lane - q * hw;
+      for (int p = lane; p < ns * hw; p += 32) {
+        const float2 v = __ldg(reinterpret_cast<const float2*>(wc) + p);
+        float* dst = reinterpret_cast<float*>(wbase + q * PW) + 2 * r;
+        dst[0] = v.x;
+        dst[1] = v.y;
+        q += pq;
+        r += pr;
+        if (r >= hw) { r -= hw; ++q; }
+      }
+    } else {
+      int q = lane / W, r = lane - q * W;
+      for (int i = lane; i < ns * W; i += 32) {
+        reinterpret_cast<R*>(wbase + q * PW)[r] = wc[i];
+        q += eq;
+        r += er;
+        if (r >= W) { r -= W; ++q; }
+      }
     }
     __syncwarp();
     if (lane < ns) {
-      const R* ws = sw(lane);
-      double S = 0.0, S64 = 0.0;
-      // FP64 tables: the FP64 sum; FP32 tables: the exact fixed-point sum
-      ok &= alias_small_inplace<R>(W, [&](int i) { return ws[i]; }, so + lane * kTlPitch, &S,
-                                   sizeof(R) == 8 ? &S64 : nullptr);
-      l1[k0 + lane] = (R)(sizeof(R) == 8 ? S64 : S);
+      R tot = 0;
+      ok &= level2_block<R, WB>(wbase + lane * PW, W, B2, &tot);
+      l1[k0 + lane] = tot;
     }
     __syncwarp();
-    uint64_t* oc = l2 + (uint64_t)k0 * W;
-    q = lane / W;
-    r = lane - q * W;
-    for (int i = lane; i < ns * W; i += 32) {
-      oc[i] = so[q * kTlPitch + r];
-      q += dq;
-      r += dr;
-      if (r >= W) { r -= W; ++q; }
+    // the chunk's ns blocks are contiguous; blocks are multiples of 8 words, the row's level 2
+    // starts 32-byte aligned, so four consecutive words of one block leave as one 16-byte store
+    uint32_t* oc = l2 + (uint64_t)k0 * B2;
+    {
+      int q = (4 * lane) / B2, r = 4 * lane - q * B2;
+      const int sq = 128 / B2, sr = 128 - (128 / B2) * B2;
+      for (int i = 4 * lane; i < ns * B2; i += 128) {
+        const uint32_t* src = wbase + q * PW + r;
+        *reinterpret_cast<uint4*>(oc + i) = make_uint4(src[0], src[1], src[2], src[3]);
+        q += sq;
+        r += sr;
+        while (r >= B2) { r -= B2; ++q; }
+      }
     }
     __syncwarp();
   }
@@ -410,27 +527,33 @@ __global__ void __launch_bounds__(32 * kTlWarps) two_level_kernel(
 
 cudaError_t launch_two_level_split(const TaskDesc* d_tasks, int n_tasks, uint32_t n_jobs,
                                    int precision, void* d_weights, uint64_t* d_tab,
-                                   int32_t* d_err, cudaStream_t s) {
+                                   int32_t* d_err, cudaStream_t s, int max_W) {
   if (n_jobs == 0 || n_tasks == 0) return cudaSuccess;
-  const unsigned blocks = (n_jobs + kTlWarps - 1) / kTlWarps;
-  const size_t stage = (size_t)kTlWarps * 32 * kTlPitch;      // entries per staging array
-  cudaError_t e;
+  const unsigned blocks = (n_jobs + kL2Warps - 1) / kL2Warps;
+  auto run = [&](auto kernel, auto tag, int wb) -> cudaError_t {
+    using R = decltype(tag);
+    // shared memory for the widest slice the kernel instance takes (W <= wb)
+    int pw = 0;
+    for (int W = 1; W <= wb; ++W) {
+      const int p = level2_pitch<R>(W, level2_words(W));
+      pw = p > pw ? p : pw;
+    }
+    const size_t smem = (size_t)kL2Warps * 32 * pw * 4;
+    const cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<blocks, 32 * kL2Warps, smem, s>>>(d_tasks, n_tasks, n_jobs, static_cast<R*>(d_weights),
+                                               d_tab, d_err);
+    return cudaGetLastError();
+  };
   if (precision == NEGF_FP64) {
-    const size_t smem = stage * sizeof(uint64_t);
-    e = cudaFuncSetAttribute(two_level_kernel<double>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    two_level_kernel<double><<<blocks, 32 * kTlWarps, smem, s>>>(
-        d_tasks, n_tasks, n_jobs, static_cast<double*>(d_weights), d_tab, d_err);
-  } else {
-    const size_t smem = stage * sizeof(uint64_t);
-    e = cudaFuncSetAttribute(two_level_kernel<float>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    two_level_kernel<float><<<blocks, 32 * kTlWarps, smem, s>>>(
-        d_tasks, n_tasks, n_jobs, static_cast<float*>(d_weights), d_tab, d_err);
+    if (max_W <= 16) return run(level2_cdf_kernel<double, 16>, 0.0, 16);
+    if (max_W <= 32) return run(level2_cdf_kernel<double, 32>, 0.0, 32);
+    return run(level2_cdf_kernel<double, 64>, 0.0, 64);
   }
-  return cudaGetLastError();
+  if (max_W <= 16) return run(level2_cdf_kernel<float, 16>, 0.f, 16);
+  if (max_W <= 32) return run(level2_cdf_kernel<float, 32>, 0.f, 32);
+  return run(level2_cdf_kernel<float, 64>, 0.f, 64);
 }
 
 int alias_warps_max(int max_K) {

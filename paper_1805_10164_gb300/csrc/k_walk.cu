@@ -60,7 +60,8 @@ struct ScoreOut {
   unsigned mode_stride;
 };
 
-template <bool kTrace, bool kScore, int kSlotsReq>
+// kTwo: the launch may hold two-level tasks (one-level launches compile without that path).
+template <bool kTrace, bool kScore, int kSlotsReq, bool kTwo>
 __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
     const TaskDesc* __restrict__ tasks, int task0, int n_tasks, uint32_t id_base,
     const uint64_t* __restrict__ tab, const uint64_t* __restrict__ mode_tab,
@@ -101,7 +102,7 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
   // cached task (shared by the slots): index window [t_first, t_first + walkers_per_task)
   int tl = -1;
   unsigned long long t_first = 0;
-  uint32_t task_id = 0, K = 0, n = 0, W = 0, inj_row0 = 0, L = 0;
+  uint32_t task_id = 0, K = 0, n = 0, W = 0, inj_row0 = 0, L = 0, B2 = 0;
   bool two = false;                  // two-level tables (level 1 at l1row, level 2 at trow)
   uint64_t t_tab_off = 0;
   uint32_t t_mode_off = 0;
@@ -137,8 +138,9 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
           t_tab_off = d.tab_off;
           t_mode_off = d.mode_off + start_lead * d.W;
           trow = tab + d.tab_off;
-          two = d.layout == NEGF_LAYOUT_TWO_LEVEL;
+          two = kTwo && d.layout == NEGF_LAYOUT_TWO_LEVEL;
           L = (uint32_t)d.L;
+          B2 = (uint32_t)level2_words(d.W);
           l1row = tab + d.l1_off;
           mrow = mode_tab + d.mode_off + start_lead * d.W;
           t_open = cvals[2 * (task0 + tl) + start_lead] > 0.0;
@@ -193,9 +195,10 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
       if (!has[sl]) continue;
       const uint4 r = philox4x32_10(make_uint4(b[sl], wid_lo[sl], wid_hi[sl], task_id), key);
       int outcome = -3;                // -3: continue, 0/1: absorbed at L/R, -2: truncated
-      if (two) {
+      if (kTwo && two) {
         // two-level tables: block 0 is the injection draw alone; block b >= 1 is transition
-        // b, words (x, y) for the slice or lead (level 1), (z, w) for the site in the slice
+        // b, words (x, y) for the slice or lead (level 1, alias), z for the site in the slice
+        // (level 2: v = z >> 1 against the guide, then against the octet it points to)
         if (b[sl] == 0) {
           const uint32_t c = __umulhi(r.x, W);
           const uint64_t e = __ldg(mrow + c);
@@ -209,9 +212,19 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
           if (k >= L) {
             outcome = (int)(k - L);
           } else {
-            const uint32_t c2 = __umulhi(r.z, W);
-            const uint64_t e2 = __ldg(trow + ((uint64_t)row[sl] * L + k) * W + c2);
-            const uint32_t a2 = r.w < (uint32_t)e2 ? c2 : (uint32_t)(e2 >> 32);
+            const uint32_t v = r.z >> 1;
+            const uint4* blk = reinterpret_cast<const uint4*>(trow) +
+                               (((uint64_t)row[sl] * L + k) * B2 >> 2);
+            uint32_t g = 0;
+            if (W > 8) {
+              const uint4 q0 = __ldg(blk), q1 = __ldg(blk + 1);
+              g = (q0.x <= v) + (q0.y <= v) + (q0.z <= v) + (q0.w <= v) + (q1.x <= v) +
+                  (q1.y <= v) + (q1.z <= v) + (q1.w <= v);
+              blk += 2 + 2 * g;
+            }
+            const uint4 o0 = __ldg(blk), o1 = __ldg(blk + 1);
+            const uint32_t a2 = 8 * g + (o0.x <= v) + (o0.y <= v) + (o0.z <= v) + (o0.w <= v) +
+                                (o1.x <= v) + (o1.y <= v) + (o1.z <= v) + (o1.w <= v);
             if (steps[sl] >= max_steps) outcome = -2;
             else row[sl] = k * W + a2;
           }
@@ -348,7 +361,7 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
                         uint64_t* d_tally, int32_t* d_trace_lead, uint32_t* d_trace_steps,
                         uint64_t* d_score, uint64_t score_stride, uint64_t* d_mode_score,
                         uint32_t mode_stride, int sm_count, int max_blocks_per_sm,
-                        cudaStream_t s, const uint64_t* d_run, int slots) {
+                        cudaStream_t s, const uint64_t* d_run, int slots, bool two_level) {
   if (n_tasks <= 0 || walkers_per_task == 0) return cudaSuccess;
   const PhiloxKey key{(uint32_t)seed, (uint32_t)(seed >> 32)};
   unsigned long long* tally = reinterpret_cast<unsigned long long*>(d_tally);
@@ -361,10 +374,17 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
     const ScoreOut so{reinterpret_cast<unsigned long long*>(d_score),
                       reinterpret_cast<unsigned long long*>(d_mode_score),
                       (unsigned long long)score_stride, mode_stride};
-    auto kern = d_score ? (d_trace_lead ? walk_kernel<true, true, 1> : walk_kernel<false, true, 1>)
-                : slots == 2
-                    ? (d_trace_lead ? walk_kernel<true, false, 2> : walk_kernel<false, false, 2>)
-                    : (d_trace_lead ? walk_kernel<true, false, 1> : walk_kernel<false, false, 1>);
+    auto kern =
+        d_score ? (d_trace_lead ? walk_kernel<true, true, 1, false> : walk_kernel<false, true, 1, false>)
+        : two_level
+            ? (slots == 2 ? (d_trace_lead ? walk_kernel<true, false, 2, true>
+                                          : walk_kernel<false, false, 2, true>)
+                          : (d_trace_lead ? walk_kernel<true, false, 1, true>
+                                          : walk_kernel<false, false, 1, true>))
+            : (slots == 2 ? (d_trace_lead ? walk_kernel<true, false, 2, false>
+                                          : walk_kernel<false, false, 2, false>)
+                          : (d_trace_lead ? walk_kernel<true, false, 1, false>
+                                          : walk_kernel<false, false, 1, false>));
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
     if (e != cudaSuccess) return e;

@@ -474,6 +474,7 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
       d.layout = layout;
       d.fused = tc_wire ? 1 : 0;
       d.cta_chain = (fp32 && (wr.W == 64 || (wr.W > 16 && wr.W <= 32)) && !tc_wire) ? 1 : 0;
+      if (layout == NEGF_LAYOUT_TWO_LEVEL) tab_off = (tab_off + 3) & ~3ull;   // level 2: 32-byte aligned
       d.tab_off = tab_off;
       d.wt_off = wt_off;
       if (tc_wire) {
@@ -481,10 +482,11 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
         edge_off += (uint64_t)(wr.L + 2) * 2 * wr.W * wr.W;
       }
       if (layout == NEGF_LAYOUT_TWO_LEVEL) {
-        d.l1_off = tab_off + (uint64_t)rows * n;
+        const uint64_t l2_u64 = (uint64_t)rows * wr.L * negf::level2_words(wr.W) / 2;
+        d.l1_off = tab_off + l2_u64;
         d.l1w_off = l1w_rel;               // rebased past the weights below
         l1w_rel += (uint64_t)rows * (wr.L + 2);
-        tab_off += (uint64_t)rows * (n + wr.L + 2);
+        tab_off += l2_u64 + (uint64_t)rows * (wr.L + 2);
         P.max_KA = std::max(P.max_KA, wr.L + 2);
         P.any_two = true;
       } else {
@@ -550,6 +552,7 @@ struct Wave {
   size_t n_tc = 0;                   // the CTA-chain jobs: tcjobs[n_tc ..], those of W = 64
   size_t n_cta_wide = 0;             // tasks first
   int cols_max_W = 0;                // widest task of the warp-per-column chains
+  int two_max_W = 0;                 // widest task with two-level tables
   uint32_t cta_narrow() const { return (uint32_t)(tcjobs.size() - n_tc - n_cta_wide); }
 };
 
@@ -562,9 +565,11 @@ Wave make_wave(const Plan& P, int t0, int t1) {
   w.t1 = t1;
   for (int k = t0; k < t1; ++k) {
     TaskDesc d = P.tasks[k];
+    const uint64_t l2_u64 = (uint64_t)d.rows * d.L * negf::level2_words(d.W) / 2;
     const uint64_t sz = d.layout == NEGF_LAYOUT_TWO_LEVEL
-                            ? (uint64_t)d.rows * (d.n + d.L + 2)
+                            ? l2_u64 + (uint64_t)d.rows * (d.L + 2)
                             : (uint64_t)d.rows * d.K;
+    if (d.layout == NEGF_LAYOUT_TWO_LEVEL) w.tab = (w.tab + 3) & ~3ull;   // 32-byte aligned
     d.tab_off = w.tab;
     d.wt_off = w.wt;
     w.wt += (uint64_t)d.rows * d.K;
@@ -576,10 +581,11 @@ Wave make_wave(const Plan& P, int t0, int t1) {
     if (d.cta_chain) add_tc_jobs(d.W == 64 ? cta : cta_n, k - t0, d.L);
     if (!d.cta_chain && !d.fused) w.cols_max_W = std::max(w.cols_max_W, d.W);
     if (d.layout == NEGF_LAYOUT_TWO_LEVEL) {
-      d.l1_off = w.tab + (uint64_t)d.rows * d.n;
+      d.l1_off = w.tab + l2_u64;
       d.l1w_off = w.l1w;                 // rebased past the wave's weights below
       w.l1w += (uint64_t)d.rows * (d.L + 2);
       w.any_two = true;
+      w.two_max_W = std::max(w.two_max_W, d.W);
     }
     d.start_off = w.start;
     d.row_base = w.rows;
@@ -774,7 +780,8 @@ negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& 
   }
   if (e == cudaSuccess && w.any_two) {
     ProfScope ps(ctx, "two_level_kernel", 1, s);
-    e = negf::launch_two_level_split(d_wdesc, nt, w.rows, prec, d_weights, d_tab, q.d_err, s);
+    e = negf::launch_two_level_split(d_wdesc, nt, w.rows, prec, d_weights, d_tab, q.d_err, s,
+                                     w.two_max_W);
   }
   if (e == cudaSuccess) {
     ProfScope ps(ctx, "alias_kernel", 1, s);
@@ -1103,7 +1110,7 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
                             r.walkers_per_task, r.walker_id_offset, r.max_steps, ctx->d_counter,
                             tl->d_counts + (size_t)wv.t0 * NEGF_TALLY_FIELDS, nullptr, nullptr,
                             nullptr, 0, nullptr, 0, ctx->sm_count, r.walk_blocks_per_sm, sw,
-                            nullptr, walk_slots(wv.any_two));
+                            nullptr, walk_slots(wv.any_two), wv.any_two);
     }
     cudaFreeAsync(d_tab, sw);
     cudaEventRecord(walked[w], sw);
@@ -1202,7 +1209,8 @@ negf_status negf_export_tables(negf_ctx ctx, negf_tables t, int32_t task, int32_
   const bool two = d.layout == NEGF_LAYOUT_TWO_LEVEL;
   switch (what) {
     case NEGF_EXPORT_ALIAS:
-      need = sizeof(uint64_t) * (size_t)d.rows * (two ? (size_t)d.n : (size_t)d.K);
+      need = two ? sizeof(uint32_t) * (size_t)d.rows * d.L * negf::level2_words(d.W)
+                 : sizeof(uint64_t) * (size_t)d.rows * (size_t)d.K;
       break;
     case NEGF_EXPORT_ALIAS_LEVEL1:
       if (!two) return fail(ctx, NEGF_E_INVALID, "task %d has one-level tables", task);
@@ -1272,11 +1280,12 @@ negf_status negf_export_table_rows(negf_ctx ctx, negf_tables t, int32_t task, in
   if (t->tables_released)
     return fail(ctx, NEGF_E_INVALID, "the alias tables of this handle were released (negf_run)");
   const bool two = d.layout == NEGF_LAYOUT_TWO_LEVEL;
-  size_t per_row = 0;       // entries per row
+  size_t per_row = 0;       // 8-byte elements per row
   uint64_t first = 0;       // first element of row0
   switch (what) {
     case NEGF_EXPORT_ALIAS:
-      per_row = two ? (size_t)d.n : (size_t)d.K;
+      // two-level: the row's level-2 blocks, L * level2_words(W) u32 (an even count)
+      per_row = two ? (size_t)d.L * negf::level2_words(d.W) / 2 : (size_t)d.K;
       first = d.tab_off + (uint64_t)row0 * per_row;
       break;
     case NEGF_EXPORT_ALIAS_LEVEL1:
@@ -1341,7 +1350,8 @@ negf_status negf_walk(negf_ctx ctx, negf_tables t, int32_t start_lead, uint64_t 
     e = negf::launch_walk(t->d_tasks, 0, t->n_tasks, 0, t->d_tab, t->d_mode_tab, t->d_c,
                           start_lead, seed, walkers_per_task, walker_id_offset, max_steps,
                           ctx->d_counter, tl->d_counts, nullptr, nullptr, nullptr, 0, nullptr,
-                          0, ctx->sm_count, 0, ctx->stream, nullptr, walk_slots(t->any_two));
+                          0, ctx->sm_count, 0, ctx->stream, nullptr, walk_slots(t->any_two),
+                          t->any_two);
   }
   if (e != cudaSuccess) {
     cudaFreeAsync(tl->d_counts, ctx->stream);
@@ -1368,7 +1378,7 @@ negf_status negf_walk_trace(negf_ctx ctx, negf_tables t, int32_t task, int32_t s
     e = negf::launch_walk(t->d_tasks, task, 1, 0, t->d_tab, t->d_mode_tab, t->d_c, start_lead,
                           seed, n_walkers, walker_id_offset, max_steps, ctx->d_counter, tmp,
                           d_lead, d_steps, nullptr, 0, nullptr, 0, ctx->sm_count, 0,
-                          ctx->stream, nullptr, walk_slots(t->any_two));
+                          ctx->stream, nullptr, walk_slots(t->any_two), t->any_two);
   cudaFreeAsync(tmp, ctx->stream);
   if (e != cudaSuccess) return fail(ctx, NEGF_E_CUDA, "negf_walk_trace: %s", cudaGetErrorString(e));
   return NEGF_OK;
@@ -1963,7 +1973,7 @@ negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
     if (wv.any_two) {
       SegScope sg(p, "two_level_kernel", 1, s, timed);
       CUDA_TRY(ctx, negf::launch_two_level_split(dd, ntw, wv.rows, prec, p->d_weights[slot],
-                                                 p->d_tab[slot], q.d_err, s));
+                                                 p->d_tab[slot], q.d_err, s, wv.two_max_W));
     }
     {
       SegScope sg(p, "alias_kernel", 1, s, timed);
@@ -1987,7 +1997,8 @@ negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
                                       nullptr, nullptr, 0, nullptr, 0, ctx->sm_count,
                                       p->tune.walk_blocks_per_sm, ws, p->d_run,
                                       p->tune.walk_slots > 0 ? p->tune.walk_slots
-                                                             : walk_slots(wv.any_two)));
+                                                             : walk_slots(wv.any_two),
+                                      wv.any_two));
     }
     if (split) CUDA_TRY(ctx, cudaEventRecord(walked, sw));
   }
@@ -2061,7 +2072,7 @@ negf_status plan_autotune(negf_plan p) {
                                 p->d_tab[0], p->d_edge[0], q.d_err, s);
     if (e == cudaSuccess && wv.any_two)
       e = negf::launch_two_level_split(dd, nt0, wv.rows, prec, p->d_weights[0], p->d_tab[0],
-                                       q.d_err, s);
+                                       q.d_err, s, wv.two_max_W);
     return e;
   };
   auto alias = [&](int aw) {
@@ -2110,7 +2121,8 @@ negf_status plan_autotune(negf_plan p) {
       return negf::launch_walk(dd, 0, nt0, (uint32_t)wv.t0, p->d_tab[0], q.d_mode_tab, q.d_c,
                                p->run.start_lead, 0, p->run.walkers_per_task, 0,
                                p->run.max_steps, ctx->d_counter, p->d_counts, nullptr, nullptr,
-                               nullptr, 0, nullptr, 0, ctx->sm_count, wb, s, p->d_run, ws);
+                               nullptr, 0, nullptr, 0, ctx->sm_count, wb, s, p->d_run, ws,
+                               wv.any_two);
     });
     if (ms < 0.f) return fail(ctx, NEGF_E_CUDA, "autotune: walk failed");
     if (best_w < 0.f || ms < best_w) best_w = ms, best_wb = wb, best_ws = ws;

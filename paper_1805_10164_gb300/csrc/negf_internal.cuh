@@ -45,6 +45,13 @@ struct TaskDesc {
   int32_t pad_;
 };
 
+// u32 words of one level-2 block of a two-level table (slice of W sites): one octet of 31-bit
+// cumulative thresholds for W <= 8, else an 8-word guide and ceil(W / 8) octets.
+__host__ __device__ inline int level2_words(int W) {
+  const int G = (W + 7) >> 3;
+  return G == 1 ? 8 : 8 + 8 * G;
+}
+
 // One job of the tensor-core chain: block columns y0 and y1 (y1 = -1: none) of task `task`
 // (index into the descriptor array of the launch) propagated in direction dir (0: towards
 // slice 0 with g^L, which also emits the start slices; 1: towards slice L - 1 with g^R).
@@ -148,9 +155,10 @@ int alias_warps_max(int max_K);
 // totals, then the two lead weights; at l1w_off of the same weights array) and the level-2
 // alias rows (one per row and slice, W slots, at tab_off).  One-level tasks are skipped.
 // n_jobs = sum over tasks of rows + 2 (the row_base numbering).
+// max_W: the widest slice among the launch's tasks (sizes the FP32 kernel's registers).
 cudaError_t launch_two_level_split(const TaskDesc* d_tasks, int n_tasks, uint32_t n_jobs,
                                    int precision, void* d_weights, uint64_t* d_tab,
-                                   int32_t* d_err, cudaStream_t s);
+                                   int32_t* d_err, cudaStream_t s, int max_W);
 // Walks of tasks d_tasks[task0 .. task0 + n_tasks); d_c is indexed like d_tasks, d_tally holds
 // the counters of those tasks (index 0 = task0).  The Philox task number of d_tasks[k] is
 // id_base + k.  max_blocks_per_sm > 0 caps the persistent grid (leaving room for concurrent
@@ -158,7 +166,8 @@ cudaError_t launch_two_level_split(const TaskDesc* d_tasks, int n_tasks, uint32_
 // d_score[lead][tab_off + a K + b] and its injection mode to d_mode_score[lead][mode_off + m].
 // With d_run non-null the seed and id_offset arguments are ignored and read on the device from
 // d_run[0] (seed) and d_run[1] (walker id offset), so a captured graph can be relaunched with
-// new values.
+// new values.  two_level: some task of the launch has two-level tables (false: every task is
+// one-level, and the launch takes a kernel compiled without the two-level draw).
 cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_t id_base,
                         const uint64_t* d_tab, const uint64_t* d_mode_tab, const double* d_c,
                         int start_lead, uint64_t seed, uint64_t walkers_per_task,
@@ -166,7 +175,8 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
                         uint64_t* d_tally, int32_t* d_trace_lead, uint32_t* d_trace_steps,
                         uint64_t* d_score, uint64_t score_stride, uint64_t* d_mode_score,
                         uint32_t mode_stride, int sm_count, int max_blocks_per_sm,
-                        cudaStream_t s, const uint64_t* d_run = nullptr, int slots = 1);
+                        cudaStream_t s, const uint64_t* d_run = nullptr, int slots = 1,
+                        bool two_level = true);
 // Timed random 8-byte gathers over a table of table_bytes (see k_walk.cu); synchronises s.
 cudaError_t probe_gather(uint64_t table_bytes, int ilp, int chain, int sm_count,
                          uint64_t* gathers, float* ms, cudaStream_t s);

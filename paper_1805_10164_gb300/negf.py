@@ -255,6 +255,11 @@ def negf_tables_free(tables):
     load().negf_tables_free(tables)
 
 
+def level2_words(W):
+    """u32 words of one level-2 block of a two-level table (NEGF_LEVEL2_WORDS)."""
+    return 8 if W <= 8 else 8 + 8 * ((W + 7) // 8)
+
+
 def negf_export_tables(ctx, tables, task, what):
     lib = load()
     kind = EXPORT[what]
@@ -269,7 +274,7 @@ def negf_export_tables(ctx, tables, task, what):
 
 def negf_export_table_rows(ctx, tables, task, what, row0, n_rows):
     """Rows [row0, row0 + n_rows) of one task's alias / alias_level1 (uint64) or rowsum
-    (float64) data."""
+    (float64) data (the level-2 blocks of a two-level task: view the result as uint32)."""
     lib = load()
     kind = EXPORT[what]
     nbytes = C.c_size_t(0)

@@ -79,10 +79,11 @@ def test_cta_chain_weights_match_oracle(ctx, batch, layout):
             assert info["layout"] == layout
             if layout == "two_level":
                 L, W = info["L"], info["W"]
-                l2 = negf.negf_export_tables(ctx, tables, task, "alias").reshape(info["rows"], L, W)
+                l2 = negf.negf_export_tables(ctx, tables, task, "alias").view(np.uint32).reshape(
+                    info["rows"], L, negf.level2_words(W))
                 l1 = negf.negf_export_tables(ctx, tables, task, "alias_level1").reshape(info["rows"], L + 2)
                 for r in (0, info["n"] - 1, info["n"], info["rows"] - 1):
-                    p = alias.implied_two_level(l1[r], l2[r])
+                    p = alias.implied_two_level(l1[r], l2[r], W)
                     assert np.max(np.abs(p - w_ref[r] / rs_ref[r])) <= (L + W + 4) * 2.0**-32 + 1e-5
     finally:
         negf.negf_tables_free(tables)

@@ -133,11 +133,12 @@ def test_weak_scattering_full_size(ctx, precision, bar):
             quant = (L + W + 4) * 2.0**-32
             for j, r in enumerate(rows):
                 l1 = negf.negf_export_table_rows(ctx, tables, task, "alias_level1", r, 1)
-                l2 = negf.negf_export_table_rows(ctx, tables, task, "alias", r, 1).reshape(L, W)
+                l2 = negf.negf_export_table_rows(ctx, tables, task, "alias", r, 1).view(
+                    np.uint32).reshape(L, negf.level2_words(W))
                 rs = negf.negf_export_table_rows(ctx, tables, task, "rowsum", r, 1)[0]
                 A = ref["w"][j].sum()
                 assert abs(rs - A) <= bar * A and abs(ref["A_row"][j] - A) <= 1e-9 * A
-                p = alias.implied_two_level(l1, l2)
+                p = alias.implied_two_level(l1, l2, W)
                 err = np.max(np.abs(p - ref["w"][j] / A))
                 assert err <= quant + bar, (k, r, err)
         N = 1_000_000

@@ -57,7 +57,8 @@ def _export(ctx, tables, task):
     info = negf.negf_get_task_info(ctx, tables, task)
     assert info["layout"] == "two_level"
     rows, L, W = info["rows"], info["L"], info["W"]
-    l2 = negf.negf_export_tables(ctx, tables, task, "alias").reshape(rows, L, W)
+    l2 = negf.negf_export_tables(ctx, tables, task, "alias").view(np.uint32).reshape(
+        rows, L, negf.level2_words(W))
     l1 = negf.negf_export_tables(ctx, tables, task, "alias_level1").reshape(rows, L + 2)
     return info, l1, l2
 
@@ -83,7 +84,7 @@ def test_tensor_core_tables_realise_oracle_weights(ctx, batch):
             bad = np.abs(w - w_ref) > 1e-5 * rs_ref[:, None] + 1e-30
             assert not bad.any(), (task, np.argwhere(bad)[:5])
             for r in rows:
-                p = alias.implied_two_level(l1[r], l2[r])
+                p = alias.implied_two_level(l1[r], l2[r], W)
                 err = np.max(np.abs(p - w_ref[r] / rs_ref[r]))
                 assert err <= quant + 1e-5, (task, r, err)
     finally:

@@ -1,8 +1,8 @@
 """Two-level tables (slice or lead, then the site within the slice) on the GPU against the oracle.
 
 Bars:
-  * the distribution a two-level row realises (exact integer product of its level-1 and
-    level-2 alias rows) against the oracle's FP64 weights / row sum: the quantisation bound
+  * the distribution a two-level row realises (exact product of its level-1 alias row and its
+    level-2 inverse-CDF blocks) against the oracle's FP64 weights / row sum: the quantisation bound
     (L + W + 4) 2^-32 plus 1e-10 (FP64 build) or 1e-5 (FP32 build) of the row;
   * the same distribution against the kernel's own weights (keep_weights): within the
     quantisation bound (L + W + 4) 2^-32 + 4 eps;
@@ -58,7 +58,8 @@ def _export_two_level(ctx, tables, task):
     info = negf.negf_get_task_info(ctx, tables, task)
     assert info["layout"] == "two_level"
     rows, L, W = info["rows"], info["L"], info["W"]
-    l2 = negf.negf_export_tables(ctx, tables, task, "alias").reshape(rows, L, W)
+    l2 = negf.negf_export_tables(ctx, tables, task, "alias").view(np.uint32).reshape(
+        rows, L, negf.level2_words(W))
     l1 = negf.negf_export_tables(ctx, tables, task, "alias_level1").reshape(rows, L + 2)
     return info, l1, l2
 
@@ -81,7 +82,7 @@ def test_two_level_tables_realise_oracle_weights(ctx, batch, precision, tol):
             rows = rng.choice(info["rows"], size=min(10, info["rows"]), replace=False)
             quant = (L + W + 4) * 2.0**-32
             for r in rows:
-                p = alias.implied_two_level(l1[r], l2[r])
+                p = alias.implied_two_level(l1[r], l2[r], W)
                 assert np.max(np.abs(p - w_ref[r] / rs_ref[r])) <= quant + tol, (task, r)
                 own = w[r] / w[r].sum()
                 assert np.max(np.abs(p - own)) <= (L + W + 4) * 2.0**-32 + 4e-7, (task, r)
@@ -179,7 +180,7 @@ def test_auto_layout_for_long_wire(ctx):
         rs_ref = w_ref.sum(1)
         rng = np.random.default_rng(2)
         for r in rng.choice(info["rows"], size=6, replace=False):
-            p = alias.implied_two_level(l1[r], l2[r])
+            p = alias.implied_two_level(l1[r], l2[r], 64)
             assert np.max(np.abs(p - w_ref[r] / rs_ref[r])) <= (101 + 64 + 4) * 2.0**-32 + 1e-5, r
         N = 200_000
         tally = negf.negf_walk(ctx, tables, 0, 5, N)

@@ -264,19 +264,58 @@ def test_walker_statistics_match_exact_chain():
     assert abs(steps.var() / var - 1.0) < 0.1
 
 
-def test_two_level_tables_realise_the_weights():
-    """Level 1 over slice totals and leads, level 2 within a slice: the product of the exact
-    implied distributions equals weights / row sum (zero slices included)."""
-    rng = np.random.default_rng(31)
-    L, W = 5, 4
+@pytest.mark.parametrize("L,W", [(5, 4), (3, 13), (2, 64)])
+def test_two_level_tables_realise_the_weights(L, W):
+    """Level 1 over slice totals and leads, level 2 the inverse-CDF draw within a slice (a
+    guide for W > 8): the product of the exact implied distributions equals weights / row sum
+    (an empty slice, zero weights inside a slice and at its end, a row without lead weight)."""
+    rng = np.random.default_rng(31 + W)
     w = rng.exponential(size=(6, L * W + 2))
-    w[1, 2 * W:3 * W] = 0.0                       # an empty slice
+    w[1, W:2 * W] = 0.0                           # an empty slice
     w[2, L * W:] = 0.0                            # no lead weight
+    w[3, 1:W:3] = 0.0                             # zeros inside slice 0
+    w[4, W - 2:W] = 0.0                           # zeros at the end of slice 0
     l1, l2 = alias.build_two_level(w, L, W)
-    assert l1.shape == (6, L + 2) and l2.shape == (6, L, W)
+    assert l1.shape == (6, L + 2) and l2.shape == (6, L, alias.level2_words(W))
+    assert l2.dtype == np.uint32
     for i in range(6):
-        p = alias.implied_two_level(l1[i], l2[i])
+        p = alias.implied_two_level(l1[i], l2[i], W)
         assert np.max(np.abs(p - w[i] / w[i].sum())) <= (L + W + 4) * 2.0**-32
+        assert np.all(p[:L * W][w[i, :L * W] == 0] == 0.0)    # zero weight: never drawn
+
+
+@pytest.mark.parametrize("W", [1, 5, 8, 9, 16, 31, 64])
+def test_level2_guided_draw_is_the_inverse_cdf(W):
+    """The two-stage draw (guide, then octet) equals the plain inverse-CDF count
+    #{a < W - 1 : c_a <= v} of Sec. III.B's draw, for every v at and around each threshold."""
+    rng = np.random.default_rng(W)
+    wk = rng.exponential(size=W) * (rng.random(W) < 0.7)
+    wk[0] += 0.1
+    blk = alias.cdf_block(wk)
+    G = -(-W // 8)
+    c = blk.astype(np.int64)[8:] if G > 1 else blk.astype(np.int64)
+    v = np.unique(np.clip(np.concatenate([c[:W - 1] + d for d in (-1, 0, 1)]
+                                         + [rng.integers(0, 2**31, size=200), [0, 2**31 - 1]]),
+                          0, 2**31 - 1))
+    plain = (c[None, :W - 1] <= v[:, None]).sum(1)
+    assert np.array_equal(alias.draw_level2(np.broadcast_to(blk, (v.size, blk.size)), W, v), plain)
+
+
+def test_level2_planted_mistakes_are_caught():
+    """A wrong guide word or a shifted threshold changes the realised distribution beyond the
+    quantisation bound, so the implied-distribution check catches it."""
+    rng = np.random.default_rng(7)
+    W = 40
+    wk = rng.exponential(size=W)
+    blk = alias.cdf_block(wk)
+    ok = alias.implied_level2(blk, W)
+    assert np.max(np.abs(ok - wk / wk.sum())) <= 2.0**-30
+    bad = blk.copy()
+    bad[1] = bad[0]                               # guide of octet 1 replaced by octet 0's
+    assert np.max(np.abs(alias.implied_level2(bad, W) - wk / wk.sum())) > 1e-3
+    bad = blk.copy()
+    bad[8 + 3:8 + 8] = bad[8 + 4:8 + 9]           # thresholds shifted by one site
+    assert np.max(np.abs(alias.implied_level2(bad, W) - wk / wk.sum())) > 1e-3
 
 
 def test_two_level_walker_statistics_match_exact_chain():
