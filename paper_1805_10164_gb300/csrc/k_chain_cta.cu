@@ -6,6 +6,15 @@
 // |(Phi^T G_{k,m})_{nu b}|^2.  Same weights as chain_kernel (one warp per column), computed
 // by 256 threads with the two columns side by side: X_k [64][128] = (-t g_k) [64][64] X_{k+1}
 // in shared memory, FP32 fused multiply-adds, each thread a 4 x 8 block of outputs.
+//
+// W = 64 uses the symmetry G = G^T (H real symmetric, every self-energy a complex symmetric
+// matrix), which halves the products: only the chains towards slice 0 run (and the one of the
+// lead-L injection column towards slice L - 1).  A block G_{k,m} (k < m) of site column m gives
+// besides the rows (m, b) the rows (k, a) of slice k towards slice m:
+// w_{(k,a),(m,b)} = eta_{m,b} |G_{(m,b),(k,a)}|^2 = eta_{m,b} |G_{k,m}[a][b]|^2, and the block
+// (G Phi_R)_k of the lead-R injection column gives the lead-R weights of the rows of slice k:
+// <psi|Gamma_R|psi> = sum_nu Gamma_nu |(Phi_R^T G_{L-1,k})_{nu a}|^2 = sum_nu Gamma_nu
+// |(G Phi_R)_k[a][nu]|^2.  Every weight is written by exactly one job.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -163,6 +172,34 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
       for (int j = 0; j < 8; ++j) Xn[(ty + 16 * i) * kN + tx + 16 * j] = cf{accr[i][j], acci[i][j]};
     __syncthreads();
     if (active) emit(Xn, k, active);
+    if (dir == 0) {
+      for (int col = 0; col < 2; ++col) {
+        if (!(active & (1u << col))) continue;
+        const int y = ys[col];
+        if (y < L) {
+          // rows (k, a) towards the column's start slice m = y: eta_{m,b} |G_{k,m}[a][b]|^2
+          const float* em = eta + y * kW;
+          float* dst = wt + (uint64_t)k * kW * K + (uint64_t)y * kW;
+          for (int i = tid; i < kW * kW; i += kThreads) {
+            const int a = i / kW, b = i % kW;               // b consecutive: coalesced rows
+            const cf v = Xn[a * kN + col * kW + b];
+            dst[(uint64_t)a * K + b] = em[b] * (v.x * v.x + v.y * v.y);
+          }
+        } else if (y == L + 1) {
+          // lead-R weights of the rows of slice k from (G Phi_R)_k: four threads per row
+          const int a = tid >> 2, q = tid & 3;
+          float part = 0.f;
+#pragma unroll 4
+          for (int nu = q * 16; nu < q * 16 + 16; ++nu) {
+            const cf v = Xn[a * kN + col * kW + nu];
+            part += (float)gam[d.lead_off + nu] * (v.x * v.x + v.y * v.y);
+          }
+          part += __shfl_xor_sync(0xffffffffu, part, 1);
+          part += __shfl_xor_sync(0xffffffffu, part, 2);
+          if (q == 0) wt[(uint64_t)(k * kW + a) * K + n + 1] = part;
+        }
+      }
+    }
     cf* tmp = Xc;
     Xc = Xn;
     Xn = tmp;

@@ -353,6 +353,18 @@ void add_tc_jobs(std::vector<TcJob>& jobs, int k, int L) {
     jobs.push_back(TcJob{k, 1, d1[i].second, i + 1 < d1.size() ? d1[i + 1].second : -1});
 }
 
+// Jobs of the W = 64 CTA-wide FP32 chain, which uses G = G^T: every block column towards
+// slice 0 (pairs of neighbouring start slices, from the far end), and towards slice L - 1 only
+// the injection column of lead L (its rows need every slice and have no transposed partner).
+void add_sym_jobs(std::vector<TcJob>& jobs, int k, int L) {
+  std::vector<std::pair<int, int>> d0;               // (m0, y)
+  for (int y = 0; y < L + 2; ++y) d0.emplace_back(y < L ? y : (y == L ? 0 : L - 1), y);
+  std::stable_sort(d0.begin(), d0.end(), [](auto a, auto b) { return a.first > b.first; });
+  for (size_t i = 0; i < d0.size(); i += 2)
+    jobs.push_back(TcJob{k, 0, d0[i].second, i + 1 < d0.size() ? d0[i + 1].second : -1});
+  if (L > 1) jobs.push_back(TcJob{k, 1, L, -1});
+}
+
 // Longest chains first (the length of a job is the number of its steps).
 void sort_jobs_longest_first(std::vector<TcJob>& jobs, const TaskDesc* desc) {
   auto len = [&](const TcJob& j) {
@@ -578,7 +590,10 @@ Wave make_wave(const Plan& P, int t0, int t1) {
       w.edge += (uint64_t)(d.L + 2) * 2 * d.W * d.W;
       add_tc_jobs(w.tcjobs, k - t0, d.L);
     }
-    if (d.cta_chain) add_tc_jobs(d.W == 64 ? cta : cta_n, k - t0, d.L);
+    if (d.cta_chain) {
+      if (d.W == 64) negf::add_sym_jobs(cta, k - t0, d.L);
+      else add_tc_jobs(cta_n, k - t0, d.L);
+    }
     if (!d.cta_chain && !d.fused) w.cols_max_W = std::max(w.cols_max_W, d.W);
     if (d.layout == NEGF_LAYOUT_TWO_LEVEL) {
       d.l1_off = w.tab + l2_u64;

@@ -63,6 +63,9 @@ struct TcJob {
 // direction 0 in pairs, the columns with slices beyond their start in direction 1), and order
 // a job list longest chain first (desc: the descriptors the jobs' task indices refer to).
 void add_tc_jobs(std::vector<TcJob>& jobs, int k, int L);
+// The jobs of the W = 64 CTA-wide chain, which uses G = G^T (see k_chain_cta.cu): every block
+// column towards slice 0, and towards slice L - 1 only the injection column of lead L.
+void add_sym_jobs(std::vector<TcJob>& jobs, int k, int L);
 void sort_jobs_longest_first(std::vector<TcJob>& jobs, const TaskDesc* desc);
 
 struct cd { double x, y; };

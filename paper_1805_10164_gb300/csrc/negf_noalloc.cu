@@ -145,7 +145,10 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
   negf::TcJob* d_jobs = reinterpret_cast<negf::TcJob*>(base + o_jobs);
   std::vector<negf::TcJob> jobs;                     // host memory only
   if (cta) {
-    for (int k = 0; k < nt; ++k) negf::add_tc_jobs(jobs, k, wr.L);
+    for (int k = 0; k < nt; ++k) {
+      if (wr.W == 64) negf::add_sym_jobs(jobs, k, wr.L);
+      else negf::add_tc_jobs(jobs, k, wr.L);
+    }
     negf::sort_jobs_longest_first(jobs, h_tasks);
   }
 
