@@ -233,84 +233,171 @@ def algorithmic_bytes(kernel, wl, precision, counts):
 
 # ------------------------------------------------------------------ GPU arm
 
-def run_gpu(args):
-    import torch
-    from paper_1805_10164_gb300 import build, negf
+DEFAULT_WORKLOAD = "wire_64x1000"
+SUB_RECORDS = ("wire_10x50", "batched_uneven")
+FP64_ENERGIES = 2          # the FP64 comparison runs on this many energies of the first wire
 
-    rank, world, local = dist_setup(args.gpus)
-    torch.cuda.set_device(local)
-    build.build()
-    wl = workload(args.workload, args.energies)
-    prec = args.precision or wl.precision
-    N = args.walkers or wl.walkers_per_task
-    dev_wires = [inputs.Wire(W=w.W, L=w.L, t=w.t, onsite=torch.from_numpy(w.onsite).cuda(),
-                             eta=torch.from_numpy(w.eta).cuda(),
-                             energy=torch.from_numpy(w.energy).cuda(),
-                             energy_weight=torch.from_numpy(w.energy_weight).cuda())
-                 for w in wl.wires]
-    stream = torch.cuda.current_stream()
-    ctx = negf.negf_create(local, stream)
-    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-    n_tasks = sum(len(w.energy) for w in wl.wires)
-    plan = None
-    plan_prec = prec
-    tuning = None
-    if args.mode == "graph":
-        # the whole step captured once (device-resident inputs re-read by every launch);
-        # launch shapes picked by the library's autotuner on this workload
-        plan = negf.negf_plan_create(ctx, dev_wires, 0, N, wl.mu_p, wl.mu_q, wl.kT,
-                                     precision=prec, memspace="device", max_steps=args.max_steps,
-                                     tasks_per_wave=args.plan_tasks_per_wave, autotune=True)
-        tuning = negf.negf_plan_get_tuning(plan)
 
-    def one_step(step_idx, wires, memspace, prec=prec, end_event=None):
-        """One step; `end_event` (if given) is recorded on the stream once the step's device work
-        is enqueued, before the host reads the results (the host path is timed by e2e)."""
-        wid0 = ndist.weak_walker_offset(rank, step_idx, N)
-        if plan is not None and memspace == "device" and prec == plan_prec:
-            negf.negf_plan_launch(ctx, plan, args.seed, wid0)
-            if end_event is not None:
-                end_event.record(stream)
-            r = negf.negf_plan_result(ctx, plan)
-            return r, r["counts"]
-        if args.mode in ("pipeline", "graph"):
-            # build wave w+1 while wave w walks; tables are freed wave by wave
-            tables, tally = negf.negf_run(ctx, wires, 0, args.seed, N, precision=prec,
-                                          memspace=memspace, walker_id_offset=wid0,
-                                          max_steps=args.max_steps,
-                                          # graph mode's host-buffer leg: waves only as
-                                          # the memory budget requires
-                                          tasks_per_wave=(args.tasks_per_wave
-                                                          if args.mode == "pipeline" else 1 << 30),
-                                          walk_blocks_per_sm=args.walk_blocks_per_sm)
+def fp32_peak():
+    """FP32 fused-multiply-add peak of the GPU from its unit counts and clock: 152 SMs x 128
+    FP32 lanes x 2 flop per clock at the maximum SM clock (MEASURED_PEAKS.json sm_max_mhz,
+    else the nominal 2070 MHz)."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f)["sm_max_mhz"])
+        src = "152 SMs x 128 FP32 lanes x 2 flop x measured max SM clock"
+    except Exception:
+        mhz, src = 2070.0, "152 SMs x 128 FP32 lanes x 2 flop x nominal 2070 MHz"
+    return 152 * 128 * 2 * mhz * 1e6 / 1e12, f"{src} ({mhz:.0f} MHz)"
+
+
+def cta_chain_flops(wl, precision):
+    """FP32 flops of the CTA-wide block-column products per step: 8 W^3 per block-column step
+    (one W x W complex block times a W x W block); W = 64 runs towards slice 0 only
+    (G = G^T) plus the lead-L injection column: L(L-1)/2 + 2(L-1) steps per task; 16 < W <= 32
+    runs both directions: (L + 2)(L - 1) steps."""
+    if precision != "fp32":
+        return 0
+    total = 0
+    for w in wl.wires:
+        W, L = w.W, w.L
+        if W == 64:
+            st = L * (L - 1) // 2 + 2 * (L - 1)
+        elif 16 < W <= 32:
+            st = (L + 2) * (L - 1)
         else:
-            tables = negf.negf_build_tables(ctx, wires, precision=prec, memspace=memspace)
-            tally = negf.negf_walk(ctx, tables, 0, args.seed, N, walker_id_offset=wid0,
-                                   max_steps=args.max_steps)
-        res = negf.negf_current(ctx, tables, tally, wl.mu_p, wl.mu_q, wl.kT)
+            continue
+        total += len(w.energy) * 8 * W ** 3 * st
+    return total
+
+
+def tc_chain_flops(wl):
+    """TF32 operations of the split-TF32 tensor-core chain per step (3 GEMMs of 128 x 128 x
+    128 real per CTA step, a pair of block columns advanced by one slice)."""
+    steps_ct = 0
+    for w in wl.wires:
+        if w.W == 64:
+            steps_ct += len(w.energy) * ((w.L + 2) * (w.L - 1) + 1) // 2
+    return 3 * 2 * 128 ** 3 * steps_ct
+
+
+def rooflines(prof, wl, prec, counts, steps, probe_gbs=None, probe_src=None):
+    """Roofline entry per kernel group of the step: achieved = algorithmic bytes (or flops) per
+    step / the group's device time per step (prof: totals over ``steps`` steps; counts: the
+    tallies of one step)."""
+    hbm, hsrc = peaks()
+    out = {}
+    for kname, (launches, ms) in prof.items():
+        if launches == 0 or ms <= 0:
+            continue
+        sec = ms / 1e3 / steps
+        ent = None
+        if kname == "chain_cta_kernel" and cta_chain_flops(wl, prec):
+            fl = cta_chain_flops(wl, prec)
+            pk, src = fp32_peak()
+            ach = fl / sec / 1e12
+            ent = {"bound": "alu", "achieved": round(ach, 2), "peak": round(pk, 2),
+                   "unit": "TFLOP/s", "frac": round(ach / pk, 4), "peak_source": src,
+                   "algorithmic_flops_per_step": int(fl)}
+        elif kname == "chain_tc_kernel":
+            fl = tc_chain_flops(wl)
+            pk, src = tensor_peak("tf32")
+            ach = fl / sec / 1e12
+            ent = {"bound": "tensor", "achieved": round(ach, 1), "peak": round(pk, 1),
+                   "unit": "TFLOP/s", "frac": round(ach / pk, 4), "peak_source": src,
+                   "algorithmic_flops_per_step": int(fl)}
+        elif kname in ("walk_kernel", "alias_kernel", "two_level_kernel"):
+            b = algorithmic_bytes(kname, wl, prec, counts)
+            if b is not None:
+                ach = b / sec / 1e9
+                ent = {"bound": "hbm", "achieved": round(ach, 1), "peak": hbm, "unit": "GB/s",
+                       "frac": round(ach / hbm, 4), "peak_source": hsrc + " HBM copy",
+                       "algorithmic_bytes_per_step": int(b)}
+                if kname == "walk_kernel" and probe_gbs:
+                    ent.update(bound="l2", peak=round(probe_gbs, 1),
+                               frac=round(ach / probe_gbs, 4), peak_source=probe_src)
+        if ent is not None:
+            ent.update(kernel=kname, launches_per_step=launches / steps,
+                       ms_per_step=round(ms / steps, 4), traffic=measured_traffic(kname, wl.name))
+            out[kname] = ent
+    return out
+
+
+def local_workload(wl, rank, world):
+    """The energies of every wire that this rank owns (task partition, no data exchange)."""
+    if world == 1:
+        return wl
+    import copy
+    sub = copy.deepcopy(wl)
+    for w in sub.wires:
+        idx = ndist.task_partition(len(w.energy), rank, world)
+        w.energy, w.energy_weight = w.energy[idx], w.energy_weight[idx]
+    return sub
+
+
+class Runner:
+    """One workload through the library on this rank: a captured plan over device-resident
+    inputs (the timed step), and negf_run over host arrays (the end-to-end path)."""
+
+    def __init__(self, negf, ctx, stream, wl, prec, N, args, seed, tasks_per_wave=0):
+        import torch
+        self.negf, self.ctx, self.stream, self.wl, self.prec, self.N = negf, ctx, stream, wl, prec, N
+        self.args, self.seed = args, seed
+        self.dev = [inputs.Wire(W=w.W, L=w.L, t=w.t, onsite=torch.from_numpy(w.onsite).cuda(),
+                                eta=torch.from_numpy(w.eta).cuda(),
+                                energy=torch.from_numpy(w.energy).cuda(),
+                                energy_weight=torch.from_numpy(w.energy_weight).cuda())
+                    for w in wl.wires]
+        self.n_tasks = sum(len(w.energy) for w in wl.wires)
+        self.plan = negf.negf_plan_create(ctx, self.dev, 0, N, wl.mu_p, wl.mu_q, wl.kT,
+                                          precision=prec, memspace="device",
+                                          max_steps=args.max_steps,
+                                          tasks_per_wave=tasks_per_wave, autotune=True)
+        self.tuning = negf.negf_plan_get_tuning(self.plan)
+
+    def step(self, wid0, end_event=None):
+        self.negf.negf_plan_launch(self.ctx, self.plan, self.seed, wid0)
         if end_event is not None:
-            end_event.record(stream)
-        counts = negf.negf_tally_counts(ctx, tally, n_tasks)
+            end_event.record(self.stream)
+        r = self.negf.negf_plan_result(self.ctx, self.plan)
+        return r, r["counts"]
+
+    def host_step(self, wid0):
+        """End to end through the public API with host buffers: the library copies the inputs,
+        builds, walks, and the current, SE and tallies come back to host memory."""
+        negf = self.negf
+        tables, tally = negf.negf_run(self.ctx, self.wl.wires, 0, self.seed, self.N,
+                                      precision=self.prec, memspace="host",
+                                      walker_id_offset=wid0, max_steps=self.args.max_steps)
+        res = negf.negf_current(self.ctx, tables, tally, self.wl.mu_p, self.wl.mu_q, self.wl.kT)
+        counts = negf.negf_tally_counts(self.ctx, tally, self.n_tasks)
         negf.negf_tally_free(tally)
         negf.negf_tables_free(tables)
         return res, counts
 
-    for i in range(args.warmup):
-        one_step(10_000 + i, dev_wires, "device")
+    def close(self):
+        self.negf.negf_plan_destroy(self.plan)
+
+
+def timed(runner, negf, ctx, stream, flush, steps, warmup, rank, world, step0=0, clocks=None):
+    """W untimed steps, then K steps bracketed by a barrier and synchronize, each timed with
+    CUDA events on the launching stream (L2 flushed between steps, outside the events)."""
+    import torch
+    N = runner.N
+    for i in range(warmup):
+        runner.step(ndist.weak_walker_offset(rank, 10_000 + step0 + i, N))
     torch.cuda.synchronize()
-    # ---- timed region (device-resident inputs)
     barrier(world)
     torch.cuda.synchronize()
-    clocks = Clocks(local) if rank == 0 else None
+    clk = Clocks(torch.cuda.current_device()) if (clocks and rank == 0) else None
     negf.negf_profile_enable(ctx, True)
-    total_ms, tot_steps, tot_walkers = 0.0, 0, 0
-    last = None
-    for i in range(args.steps):
-        flush.fill_(float(i))                      # evict the previous step's tables from L2
+    total_ms, tot_steps, tot_walkers, last = 0.0, 0, 0, None
+    for i in range(steps):
+        flush.fill_(float(i))
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res, counts = one_step(i, dev_wires, "device", end_event=e1)
+        res, counts = runner.step(ndist.weak_walker_offset(rank, step0 + i, N), end_event=e1)
         e1.synchronize()
         total_ms += e0.elapsed_time(e1)
         tot_steps += int(counts[:, 4].sum())
@@ -319,189 +406,209 @@ def run_gpu(args):
     torch.cuda.synchronize()
     prof = negf.negf_profile_read(ctx)
     negf.negf_profile_enable(ctx, False)
-    if clocks is not None:
-        # nvidia-smi samples every 200 ms: when the timed steps were shorter than a second,
-        # keep running the same step (untimed) so that the clock record holds a few samples
+    if clk is not None:
+        # nvidia-smi samples every 200 ms: keep running the same step (untimed) until the clock
+        # record holds a few samples
         t_soak = time.perf_counter()
         i = 0
-        while clocks.elapsed() < 1.2 and time.perf_counter() - t_soak < 5.0:
+        while clk.elapsed() < 1.2 and time.perf_counter() - t_soak < 5.0:
             flush.fill_(float(i))
-            one_step(30_000 + i, dev_wires, "device")
+            runner.step(ndist.weak_walker_offset(rank, 30_000 + step0 + i, N))
             torch.cuda.synchronize()
             i += 1
-    clk = clocks.stop() if clocks else None
-    if clk is not None:
-        clk["window"] = "timed steps, then repeats of the same step until 1.2 s had passed"
+    clk_out = clk.stop() if clk else None
+    if clk_out is not None:
+        clk_out["window"] = "timed steps, then repeats of the same step until 1.2 s had passed"
     barrier(world)
     t_max = max_over_ranks(total_ms, world)
     all_steps = sum_over_ranks(float(tot_steps), world)
-    # ---- end-to-end through the public API with host buffers (copies inside the region)
+    return dict(t_max=t_max, all_steps=all_steps, tot_walkers=tot_walkers, prof=prof,
+                last=last, clocks=clk_out)
+
+
+def s_per_current(ms_per_step, walk_ms, rel):
+    """Seconds per current at 1 % relative SE: the step's fixed table cost plus its walks scaled
+    by the binomial variance (N_needed = N (rel / 0.01)^2)."""
+    return ((ms_per_step - walk_ms) + walk_ms * (rel / 0.01) ** 2) / 1e3
+
+
+def fp64_comparison(negf, ctx, stream, flush, wl, args):
+    """Seconds per current at 1 % SE with FP64 tables (the plain FP64 form) and with the
+    workload's tables, on the same labelled energy subset of the first wire (the FP64 chains of
+    wide slices take seconds per energy, so the comparison is bounded)."""
+    import copy
+    import torch
+    sub = copy.deepcopy(wl)
+    sub.wires = sub.wires[:1]
+    w = sub.wires[0]
+    idx = np.unique(np.linspace(0, len(w.energy) - 1, FP64_ENERGIES).round().astype(int))
+    w.energy, w.energy_weight = w.energy[idx], w.energy_weight[idx]
+    out = {"energies": [int(i) for i in idx], "wire": f"W={w.W} L={w.L}"}
+    dev = [inputs.Wire(W=w.W, L=w.L, t=w.t, onsite=torch.from_numpy(w.onsite).cuda(),
+                       eta=torch.from_numpy(w.eta).cuda(), energy=torch.from_numpy(w.energy).cuda(),
+                       energy_weight=torch.from_numpy(w.energy_weight).cuda())]
+    N = args.walkers or sub.walkers_per_task
+    for prec in (args.precision or wl.precision, "fp64"):
+        def one(i, e1=None):
+            t = negf.negf_build_tables(ctx, dev, precision=prec, memspace="device")
+            tl = negf.negf_walk(ctx, t, 0, args.seed, N, walker_id_offset=i * N,
+                                max_steps=args.max_steps)
+            r = negf.negf_current(ctx, t, tl, sub.mu_p, sub.mu_q, sub.kT)
+            if e1 is not None:
+                e1.record(stream)
+            negf.negf_tally_free(tl)
+            negf.negf_tables_free(t)
+            return r
+        one(0)
+        torch.cuda.synchronize()
+        negf.negf_profile_enable(ctx, True)
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = one(1, e1)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        prof = negf.negf_profile_read(ctx)
+        negf.negf_profile_enable(ctx, False)
+        walk_ms = prof.get("walk_kernel", (0, 0.0))[1]
+        rel = float(r["se"][0] / abs(r["I"][0])) if r["I"][0] != 0 else float("nan")
+        out[prec] = {"ms_per_step": ms, "walk_ms": walk_ms, "current": float(r["I"][0]),
+                     "current_rel_se": rel, "s_per_current_1pct": s_per_current(ms, walk_ms, rel),
+                     "kernel_ms_per_step": {k: round(v[1], 4) for k, v in prof.items()}}
+    p32 = args.precision or wl.precision
+    out["speedup_" + p32 + "_over_fp64"] = (out["fp64"]["s_per_current_1pct"]
+                                            / out[p32]["s_per_current_1pct"])
+    return out
+
+
+def sub_record(negf, ctx, stream, flush, name, args, rank, world):
+    """One more workload measured the same way (graph mode, device-resident inputs)."""
+    wl = workload(name)
+    prec = wl.precision
+    N = wl.walkers_per_task
+    steps = min(args.steps, 20) if name == "wire_10x50" else min(args.steps, 3)
+    r = Runner(negf, ctx, stream, wl, prec, N, args, args.seed,
+               tasks_per_wave=1024 if name == "batched_uneven" else 0)
+    try:
+        t = timed(r, negf, ctx, stream, flush, steps, 3, rank, world, step0=50_000)
+    finally:
+        r.close()
+    res, counts = t["last"]
+    probe_gbs = probe_src = None
+    if name == "wire_10x50":
+        per_task = 8 * max((w.W * w.L + 2 * w.W) * (w.W * w.L + 2) for w in wl.wires)
+        probe_tab = min(2 * per_task, 16 << 30)
+        probe_gbs = 8 * negf.negf_probe_gather(ctx, probe_tab, ilp=8, chain=64) / 1e9
+        probe_src = (f"measured: negf_probe_gather, random 8-byte gathers over {probe_tab >> 20}"
+                     f" MiB (two tasks' alias tables), 8 independent chains per thread")
+    roofs = rooflines(t["prof"], wl, prec, counts, steps, probe_gbs, probe_src)
+    ms = t["t_max"] / steps
+    dom = max(t["prof"].items(), key=lambda kv: kv[1][1])[0]
+    walk_ms = t["prof"].get("walk_kernel", (0, 0.0))[1] / steps
+    rel = float(res["se"][0] / abs(res["I"][0])) if res["I"][0] != 0 else float("nan")
+    return {"workload": wl.name, "value": t["all_steps"] / (t["t_max"] / 1e3), "unit": UNIT,
+            "steps": steps, "warmup": 3, "ms_per_step": ms, "precision": prec,
+            "walkers_per_task": N, "tasks": r.n_tasks, "launch_shapes": r.tuning,
+            "s_per_current_1pct": s_per_current(ms, walk_ms, rel),
+            "kernel_ms_per_step": {k: round(v[1] / steps, 4) for k, v in t["prof"].items()},
+            "roofline": roofs.get(dom), "roofline_kernels": roofs}
+
+
+def run_gpu(args):
+    import torch
+    from paper_1805_10164_gb300 import build, negf
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    build.build()
+    wl_all = workload(args.workload or DEFAULT_WORKLOAD, args.energies)
+    prec = args.precision or wl_all.precision
+    wl = local_workload(wl_all, rank, world)
+    N = args.walkers or wl.walkers_per_task
+    seed = args.seed + rank          # ranks own different tasks: independent Philox keys
+    stream = torch.cuda.current_stream()
+    ctx = negf.negf_create(local, stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    runner = Runner(negf, ctx, stream, wl, prec, N, args, seed,
+                    tasks_per_wave=args.plan_tasks_per_wave)
+    t = timed(runner, negf, ctx, stream, flush, args.steps, args.warmup, rank, world,
+              clocks=True)
+    res, counts = t["last"]
+    # the one exchange step: the wires' partial currents and SE^2 add over ranks
+    I_all, se_all = ndist.reduce_current(res["I"], res["se"])
+    # end to end through the public API with host buffers (copies inside the region)
     e2e_ms, e2e_steps = 0.0, 0
-    h2d = sum(w.onsite.nbytes + w.eta.nbytes + w.energy.nbytes + w.energy_weight.nbytes
-              for w in wl.wires)
-    d2h = 8 * (2 * len(wl.wires) + 2 * n_tasks + 1) + 4 + 8 * n_tasks * negf.TALLY_FIELDS
-    # graph mode: the step's inputs come from pinned host buffers into the device arrays the
-    # captured plan reads, then the plan runs and its results are read back (the serving path);
-    # the other modes pass the host arrays to the library, which copies them itself
-    pinned = None
-    if plan is not None:
-        pinned = [[torch.from_numpy(a).pin_memory() for a in (w.onsite, w.eta, w.energy,
-                                                                w.energy_weight)]
-                  for w in wl.wires]
-    for i in range(max(1, min(args.steps, 3))):
+    n_e2e = max(1, min(args.steps, 2))
+    for i in range(n_e2e):
         flush.fill_(float(i))
         torch.cuda.synchronize()
+        barrier(world)
         t0 = time.perf_counter()
-        if pinned is not None:
-            for dw, hp in zip(dev_wires, pinned):
-                for dst, src in zip((dw.onsite, dw.eta, dw.energy, dw.energy_weight), hp):
-                    dst.copy_(src, non_blocking=True)
-            _, counts = one_step(20_000 + i, dev_wires, "device")
-        else:
-            _, counts = one_step(20_000 + i, wl.wires, "host")
+        _, c2 = runner.host_step(ndist.weak_walker_offset(rank, 20_000 + i, N))
         torch.cuda.synchronize()
         e2e_ms += 1e3 * (time.perf_counter() - t0)
-        e2e_steps += int(counts[:, 4].sum())
+        e2e_steps += int(c2[:, 4].sum())
     e2e_ms = max_over_ranks(e2e_ms, world)
     e2e_steps = sum_over_ranks(float(e2e_steps), world)
-    # ceiling for the walk's 8-byte alias-entry gathers (measured, this GPU, this run)
-    per_task_bytes = 8 * max((w.W * w.L + 2 * w.W) * (w.W * w.L + 2) for w in wl.wires)
-    probe_tab = min(2 * per_task_bytes, 16 << 30)
-    probe_gps = negf.negf_probe_gather(ctx, probe_tab, ilp=8, chain=64)
-    probe_gps1 = negf.negf_probe_gather(ctx, probe_tab, ilp=1, chain=64)
-    probe_gbs = 8 * probe_gps / 1e9
-    probe_src = (f"measured: negf_probe_gather, random 8-byte gathers over {probe_tab >> 20} MiB "
-                 f"(two tasks' alias tables, at most 16 GiB), 8 independent chains per thread "
-                 f"({probe_gps:.3g}/s; 1 chain: {probe_gps1:.3g}/s)")
-    # seconds per current at 1 % SE with FP64 tables (the plain FP64 form), for comparison
-    fp64_cmp = None
-    if args.compare_fp64 and prec != "fp64":
-        fp64_cmp = time_precision("fp64", one_step, dev_wires, negf, ctx, stream, flush, args)
-    if plan is not None:
-        negf.negf_plan_destroy(plan)
+    h2d = sum(w.onsite.nbytes + w.eta.nbytes + w.energy.nbytes + w.energy_weight.nbytes
+              for w in wl.wires)
+    d2h = 8 * (2 * len(wl.wires) + 2 * runner.n_tasks) + 8 * runner.n_tasks * negf.TALLY_FIELDS
+    tuning = runner.tuning
+    runner.close()
+    extra = {}
+    if world == 1 and args.compare_fp64 and prec != "fp64":
+        extra["fp64_tables"] = fp64_comparison(negf, ctx, stream, flush, wl, args)
+    if world == 1 and args.sub_records:
+        extra["sub_records"] = {name: sub_record(negf, ctx, stream, flush, name, args, rank, world)
+                                for name in SUB_RECORDS if name != (args.workload or DEFAULT_WORKLOAD)}
     negf.negf_destroy(ctx)
     if rank != 0:
         return
-    res, counts = last
-    ms_per_step = t_max / args.steps
-    value = all_steps / (t_max / 1e3)
-    # roofline of the dominant kernel
-    dom = max(prof.items(), key=lambda kv: kv[1][1])
-    kname, (klaunch, kms) = dom
-    peak, src = peaks()
-    abytes = algorithmic_bytes(kname, wl, prec, counts)
-    roof = roof_hbm = None
-    if abytes is not None and klaunch > 0:
-        launches_per_step = klaunch / args.steps
-        per_launch_bytes = abytes / max(1, launches_per_step)
-        per_launch_s = kms / 1e3 / klaunch
-        ach = per_launch_bytes / per_launch_s / 1e9
-        roof_hbm = {"kernel": kname, "bound": "hbm", "achieved": round(ach, 1), "peak": peak,
-                    "unit": "GB/s", "frac": round(ach / peak, 4), "peak_source": src + " HBM copy",
-                    "traffic": None, "algorithmic_bytes_per_launch": int(per_launch_bytes),
-                    "avg_launch_ms": round(kms / klaunch, 5)}
-        roof_hbm["traffic"] = measured_traffic(kname, wl.name)
-        roof = dict(roof_hbm)
-        if kname == "walk_kernel" and probe_gbs and (probe_tab < 2 * per_task_bytes):
-            # the probe could not cover two tasks' tables: HBM-resident gathers, keep the HBM
-            # copy peak
-            pass
-        elif kname == "walk_kernel" and probe_gbs:
-            # the alias tables of the tasks in flight sit in L2: the ceiling is the measured
-            # random 8-byte gather rate over a table of that size
-            roof.update(bound="l2", peak=round(probe_gbs, 1), frac=round(ach / probe_gbs, 4),
-                        peak_source=probe_src)
-    if kname == "chain_tc_kernel" and klaunch > 0:
-        # tensor-core roofline: TF32 operations of the 3xTF32 products (3 GEMMs of 128 x 128 x
-        # 128 real per CTA step, a pair of block columns advanced by one slice)
-        steps_ct = 0
-        for w in wl.wires:
-            if w.W == 64:
-                steps_ct += len(w.energy) * ((w.L + 2) * (w.L - 1) + 1) // 2
-        flops = 3 * 2 * 128 ** 3 * steps_ct / max(1, klaunch / args.steps / 2)
-        tflops = flops / (kms / 1e3 / (klaunch / 2)) / 1e12
-        tf32_peak = tensor_peak("tf32")
-        roof = {"kernel": kname, "bound": "tensor", "achieved": round(tflops, 1),
-                "peak": round(tf32_peak[0], 1), "unit": "TFLOP/s",
-                "frac": round(tflops / tf32_peak[0], 4), "peak_source": tf32_peak[1],
-                "traffic": None, "algorithmic_flops_per_launch": int(flops),
-                "avg_launch_ms": round(kms / klaunch * 2, 5)}
-    # seconds per current at 1 % relative standard error: fixed table cost + walks scaled by
-    # the binomial variance (N_needed = N (rel_se / 0.01)^2)
+    ms_per_step = t["t_max"] / args.steps
+    prof = t["prof"]
+    roofs = rooflines(prof, wl, prec, counts, args.steps)
+    dom = max(prof.items(), key=lambda kv: kv[1][1])[0]
     walk_ms = prof.get("walk_kernel", (0, 0.0))[1] / args.steps
-    rel = float(res["se"][0] / abs(res["I"][0])) if res["I"][0] != 0 else float("nan")
-    s_per_current = ((ms_per_step - walk_ms) + walk_ms * (rel / 0.01) ** 2) / 1e3
-    launches = int(sum(v[0] for v in prof.values()))
+    rel = float(se_all[0] / abs(I_all[0])) if I_all[0] != 0 else float("nan")
     out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": t["all_steps"] / (t["t_max"] / 1e3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+        "vs_baseline": None,
         "dtype": {"fp64": "f64 tables, u32 walks, f64 tally",
                   "fp32": "f32 tables, u32 walks, f64 tally",
                   "split_tf32": "tf32x3 block products (f32 accumulate), f32 tables, u32 walks, "
                                 "f64 tally"}[prec],
         "data": "synthetic (seeded square-lattice wire standing in for the paper's CdTe nanowires)",
-        "config": {"workload": wl.name, "wires": len(wl.wires), "tasks": n_tasks,
+        "config": {"workload": wl_all.name, "wires": len(wl_all.wires),
+                   "tasks": sum(len(w.energy) for w in wl_all.wires),
                    "walkers_per_task": N, "precision": prec, "start_lead": "L",
                    "mu_p": wl.mu_p, "mu_q": wl.mu_q, "kT": wl.kT,
-                   "l2": "flushed between timed steps (258 MiB write, outside the timed events)",
-                   "mode": args.mode,
-                   "tasks_per_wave": (args.plan_tasks_per_wave if args.mode == "graph"
-                                      else args.tasks_per_wave),
-                   "launch_shapes": tuning,
-                   "parallelism": f"tasks replicated per rank, walker ids disjoint ({world} GPU)"},
-        "walker_steps_per_step": all_steps / args.steps / world,
-        "walkers_per_step": tot_walkers / args.steps,
-        "current": float(res["I"][0]), "current_rel_se": rel,
-        "s_per_current_1pct": s_per_current,
+                   "l2": "inputs larger than L2 (tables of one task: tens of GB) and L2 flushed "
+                         "between timed steps (258 MiB write, outside the timed events)",
+                   "mode": "graph", "launch_shapes": tuning,
+                   "parallelism": (f"task partition: each of {world} ranks builds and walks its "
+                                   f"own energies; one all-reduce of the partial current"
+                                   if world > 1 else "1 GPU, all tasks")},
+        "walker_steps_per_step": t["all_steps"] / args.steps,
+        "walkers_per_step": t["tot_walkers"] / args.steps * world,
+        "current": float(I_all[0]), "current_rel_se": rel,
+        "s_per_current_1pct": s_per_current(ms_per_step, walk_ms, rel),
         "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
-        "roofline": roof,
-        "roofline_hbm": roof_hbm,
+        "roofline": roofs.get(dom),
+        "roofline_kernels": roofs,
         "e2e": {"value": e2e_steps / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h),
-                "path": ("pinned host inputs copied into the plan's device inputs, captured plan "
-                         "launched, results read back (wall clock)" if plan is not None else
-                         "host arrays passed to the library, results read back (wall clock)")},
-        "gpu_launches": launches,
-        "clocks": clk,
+                "path": "negf_run over host arrays (the library copies the inputs, builds, "
+                        "walks) + negf_current and the tallies read back, wall clock"},
+        "gpu_launches": int(sum(v[0] for v in prof.values())),
+        "clocks": t["clocks"],
     }
-    if fp64_cmp is not None:
-        fp64_cmp["s_per_current_1pct_" + prec] = s_per_current
-        fp64_cmp["speedup_" + prec + "_over_fp64"] = fp64_cmp["s_per_current_1pct"] / s_per_current
-        out["fp64_tables"] = fp64_cmp
+    out.update(extra)
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(wl, args, budget_s=args.cpu_budget)
+        out["cpu_baseline"] = cpu_baseline(wl_all, args)
     print(json.dumps(out), flush=True)
-
-
-def time_precision(prec, one_step, dev_wires, negf, ctx, stream, flush, args, steps=3):
-    """ms per step, walk ms and s per current at 1 % SE of the same workload with tables of
-    precision ``prec`` (device-resident inputs, L2 flushed between steps)."""
-    import torch
-    for i in range(2):
-        one_step(40_000 + i, dev_wires, "device", prec)
-    torch.cuda.synchronize()
-    negf.negf_profile_enable(ctx, True)
-    tot = 0.0
-    res = None
-    for i in range(steps):
-        flush.fill_(float(i))
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        res, _ = one_step(41_000 + i, dev_wires, "device", prec, end_event=e1)
-        e1.synchronize()
-        tot += e0.elapsed_time(e1)
-    prof = negf.negf_profile_read(ctx)
-    negf.negf_profile_enable(ctx, False)
-    ms = tot / steps
-    walk_ms = prof.get("walk_kernel", (0, 0.0))[1] / steps
-    rel = float(res["se"][0] / abs(res["I"][0])) if res["I"][0] != 0 else float("nan")
-    return {"precision": prec, "ms_per_step": ms, "walk_ms": walk_ms, "current": float(res["I"][0]),
-            "current_rel_se": rel,
-            "s_per_current_1pct": ((ms - walk_ms) + walk_ms * (rel / 0.01) ** 2) / 1e3,
-            "kernel_ms_per_step": {k: round(v[1] / steps, 4) for k, v in prof.items()}}
-
 
 # ------------------------------------------------------------------ gradient (forward + backward)
 
@@ -519,7 +626,7 @@ def run_gradient(args):
     rank, world, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     build.build()
-    name = args.workload if args.workload != "wire_10x50" else "wire_16x100"
+    name = args.workload or "wire_16x100"
     wl = workload(name, args.energies)
     prec = args.precision or wl.precision
     w = wl.wires[0]
@@ -666,7 +773,7 @@ def run_thermal(args):
     rank, world, local = dist_setup(args.gpus)
     torch.cuda.set_device(local)
     build.build()
-    wl = workload(args.workload, args.energies)
+    wl = workload(args.workload or "wire_10x50", args.energies)
     prec = args.precision or wl.precision
     w, mu, kT = thermal_wire(wl)
     N = (args.walkers or wl.walkers_per_task) * len(wl.wires[0].energy)
@@ -784,7 +891,7 @@ def run_thermal(args):
                 for tb in tabs]
         c = [tb["c"] for tb in tabs]
         n_w, steps = 0, 0
-        while time.perf_counter() - t0 < min(args.cpu_budget, 20.0) or n_w == 0:
+        while time.perf_counter() - t0 < 20.0 or n_w == 0:
             lead, st, _, _ = thermal.walk(ent, ment, c, tabs[0]["n"], w.W, 0, 0, args.seed,
                                           np.arange(n_w, n_w + 2000, dtype=np.uint64), w.energy,
                                           mu, kT, 1 << 20)
@@ -799,44 +906,79 @@ def run_thermal(args):
 
 # ------------------------------------------------------------------ CPU oracle (baseline)
 
-def cpu_sample(wl, n_energy, walkers, seed, t_budget=None):
-    """Oracle on a sample of the workload: tables for n_energy energies spread over the grid
-    and `walkers` walks each.  Returns (walker steps, seconds, sample description)."""
-    from oracle import pipeline, walker
-    w = wl.wires[0]
-    idx = np.linspace(0, len(w.energy) - 1, n_energy).round().astype(int)
-    steps = 0
+CPU_SLICES = 32            # the oracle's sample: the first slices of the workload's first wire
+CPU_WALKERS = 1_000_000    # walkers per sampled energy
+
+
+def _oracle_energy(job):
+    """The oracle (test infrastructure) on one energy of the sample: dense G, Step 6' weights,
+    tables (two-level for wide slices, as the library lays them out), walks.  Returns
+    (walker steps, seconds)."""
+    import numpy as _np
+    from oracle import alias, markov, walker, wire
+    onsite, eta, t_hop, E, task, seed, walkers = job
+    L, W = onsite.shape
     t0 = time.perf_counter()
-    for k in idx:
-        ref = pipeline.task_reference(w.onsite, w.eta, w.t, w.energy[k], w.lead_model,
-                                      w.gamma_lead, with_direct=False)
-        lead, st = walker.walk(ref["entries"], ref["mode_entries"], ref["n"], w.W, ref["c_open"],
-                               int(k), 0, seed, np.arange(walkers, dtype=np.uint64), 1 << 20)
-        steps += int(st.sum())
+    g = wire.green_retarded(E, onsite, eta, t_hop)
+    phi, _, gam = wire.lead_modes(E, W, t_hop)
+    tab = markov.transition_weights(g, (phi, gam))
+    ment = _np.stack([alias.vose(tab["mode_w"][p]) for p in range(2)])
+    wids = _np.arange(walkers, dtype=_np.uint64)
+    if W * L > 2048 or W == 64:
+        l1, l2 = alias.build_two_level(tab["w"], L, W)
+        _, st = walker.walk_two_level(l1, l2, ment, W * L, L, W, tab["c"] > 0, task, 0, seed,
+                                      wids, 1 << 20)
+    else:
+        ent = alias.build_tables(tab["w"])
+        _, st = walker.walk(ent, ment, W * L, W, tab["c"] > 0, task, 0, seed, wids, 1 << 20)
+    return int(st.astype(_np.uint64).sum()), time.perf_counter() - t0
+
+
+def cpu_sample(wl, cores, seed):
+    """The oracle on ``cores`` energies of the workload's first wire, truncated to its first
+    CPU_SLICES slices, one energy per process (spawned, one thread each).  Returns (walker
+    steps, wall seconds, description)."""
+    import multiprocessing as mp
+    w = wl.wires[0]
+    Ls = min(w.L, CPU_SLICES)
+    idx = np.unique(np.linspace(0, len(w.energy) - 1, cores).round().astype(int))
+    jobs = [(w.onsite[:Ls], w.eta[:Ls], w.t, float(w.energy[k]), int(k), seed,
+             CPU_WALKERS) for k in idx]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_oracle_energy, jobs)
     dt = time.perf_counter() - t0
-    return steps, dt, f"{n_energy} of {len(w.energy)} energies x {walkers} walkers"
+    steps = sum(r[0] for r in res)
+    desc = (f"oracle on W={w.W} x L={Ls} (the first {Ls} of {w.L} slices), {len(jobs)} of "
+            f"{len(w.energy)} energies x {CPU_WALKERS} walkers, one energy per process "
+            f"(numpy/LAPACK, one thread each), tables included")
+    return steps, dt, desc, len(jobs)
 
 
-def cpu_baseline(wl, args, budget_s=20.0):
-    walkers = wl.walkers_per_task
-    steps, dt, desc = cpu_sample(wl, min(16, len(wl.wires[0].energy)), walkers, args.seed)
-    return {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": desc + f" ({dt:.1f} s, numpy/LAPACK single thread)"}
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(wl, args):
+    steps, dt, desc, used = cpu_sample(wl, host_cores(), args.seed)
+    return {"value": steps / dt, "unit": UNIT, "cores": used, "kind": "oracle",
+            "sample": desc + f" ({dt:.1f} s)"}
 
 
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    wl = workload(args.workload, args.energies)
-    walkers = wl.walkers_per_task
+    wl = workload(args.workload or DEFAULT_WORKLOAD, args.energies)
+    cores = host_cores()
     for i in range(args.warmup):
-        cpu_sample(wl, 1, 1000, args.seed + i)
-    tot_steps, tot_s = 0, 0.0
-    desc = ""
+        cpu_sample(wl, min(cores, 2), args.seed + i)
+    tot_steps, tot_s, desc, used = 0, 0.0, "", 0
     for i in range(args.steps):
-        st, dt, desc = cpu_sample(wl, min(2, len(wl.wires[0].energy)), walkers,
-                                  args.seed + 100 + i)
+        st, dt, desc, used = cpu_sample(wl, cores, args.seed + 100 + i)
         tot_steps += st
         tot_s += dt
     value = tot_steps / tot_s
@@ -844,9 +986,8 @@ def run_reference(args):
            "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": wl.name, "walkers_per_task": wl.walkers_per_task,
-                      "sampled": desc},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "config": {"workload": wl.name, "walkers_per_task": CPU_WALKERS, "sampled": desc},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
                             "sample": desc + " per step"},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
@@ -855,24 +996,23 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="wire_10x50")
+    ap.add_argument("--workload", default=None,
+                    help=f"default {DEFAULT_WORKLOAD} (wire_10x50 for --mode thermal, "
+                         f"wire_16x100 for --mode gradient)")
     ap.add_argument("--precision", default=None)
     ap.add_argument("--walkers", type=int, default=None)
     ap.add_argument("--seed", type=int, default=20240607)
     ap.add_argument("--max-steps", type=int, default=1 << 20)
-    ap.add_argument("--cpu-budget", type=float, default=20.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--mode", default="graph",
-                    choices=["graph", "pipeline", "separate", "thermal", "gradient"])
-    ap.add_argument("--tasks-per-wave", type=int, default=8)
-    ap.add_argument("--walk-blocks-per-sm", type=int, default=4)
+    ap.add_argument("--no-sub-records", dest="sub_records", action="store_false")
+    ap.add_argument("--mode", default="graph", choices=["graph", "thermal", "gradient"])
     ap.add_argument("--no-compare-fp64", dest="compare_fp64", action="store_false")
     ap.add_argument("--plan-tasks-per-wave", type=int, default=0,
-                    help="graph mode: tasks per wave (0: all tasks in one wave, or 1024 for "
-                         "the batched workload, whose 8192 tasks' tables need 548 GB)")
+                    help="tasks per wave of the captured plan (0: as the memory budget allows; "
+                         "1024 for the batched workload)")
     ap.add_argument("--energies", type=int, default=0,
                     help="use an evenly spread subset of this many grid energies")
     args = ap.parse_args()

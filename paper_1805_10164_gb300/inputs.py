@@ -91,9 +91,11 @@ def wire_16x100(seed=3, walkers=1_000_000, n_energy=16, precision="fp64"):
                     seed)
 
 
-def wire_64x1000(seed=4, n_energy=256, precision="split_tf32", walkers=32_000_000):
+def wire_64x1000(seed=4, n_energy=256, precision="fp32", walkers=32_000_000):
     """Weak scattering: W = 64 x L = 1000, onsite U[-0.5, 0.5], eta = 0.005, 256 energies.
-    About 3.1 transitions per walk, so 3.2e7 walkers per energy give ~1e8 walker steps."""
+    About 3.1 transitions per walk, so 3.2e7 walkers per energy give ~1e8 walker steps.
+    FP32 tables (CUDA-core block products); precision="split_tf32" selects the tensor-core
+    block products."""
     rng = np.random.default_rng(seed)
     E, wE = midpoint_grid(-3.5, 3.5, n_energy)
     w = random_wire(rng, 64, 1000, 1.0, 0.5, 0.005, E, wE)

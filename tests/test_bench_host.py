@@ -35,3 +35,41 @@ def test_unknown_workload_is_refused():
 def test_traffic_figure_is_keyed_to_the_sources():
     assert bench.measured_traffic("walk_kernel", "no_such_workload") is None
     assert bench.measured_traffic("alias_kernel", "wire_W10_L50_eta0.05_64E") is None
+
+
+def test_fp32_peak_from_unit_counts():
+    pk, src = bench.fp32_peak()
+    # 152 SMs x 128 lanes x 2 flop at 2070 MHz = 80.5 TFLOP/s
+    assert 60.0 < pk < 90.0 and "152 SMs" in src
+
+
+def test_cta_chain_flops_count_the_symmetric_chain():
+    wl = bench.workload("wire_64x1000", energies=2)
+    L, W = 1000, 64
+    assert bench.cta_chain_flops(wl, "fp32") == 2 * 8 * W**3 * (L * (L - 1) // 2 + 2 * (L - 1))
+    assert bench.cta_chain_flops(wl, "fp64") == 0
+    narrow = bench.workload("wire_32x100")
+    assert bench.cta_chain_flops(narrow, "fp32") == 8 * 8 * 32**3 * (102 * 99)
+
+
+def test_local_workload_partitions_energies():
+    wl = bench.workload("wire_64x1000")
+    parts = [bench.local_workload(wl, r, 3) for r in range(3)]
+    E = np.sort(np.concatenate([p.wires[0].energy for p in parts]))
+    assert np.array_equal(E, wl.wires[0].energy)
+    assert bench.local_workload(wl, 0, 1) is wl
+
+
+def test_rooflines_of_a_step():
+    wl = bench.workload("wire_64x1000", energies=8)
+    counts = np.zeros((8, 5), dtype=np.uint64)
+    counts[:, 0] = 32_000_000
+    counts[:, 4] = 100_000_000
+    counts[:, 2] = 32_000_000
+    prof = {"chain_cta_kernel": (8, 245.0), "two_level_kernel": (8, 82.0), "walk_kernel": (1, 35.0),
+            "rgf_sweep_kernel": (1, 64.0)}
+    r = bench.rooflines(prof, wl, "fp32", counts, 1)
+    assert r["chain_cta_kernel"]["bound"] == "alu" and 0.3 < r["chain_cta_kernel"]["frac"] < 0.6
+    assert r["two_level_kernel"]["bound"] == "hbm" and 0.2 < r["two_level_kernel"]["frac"] < 1.0
+    assert r["walk_kernel"]["bound"] == "hbm"
+    assert "rgf_sweep_kernel" not in r

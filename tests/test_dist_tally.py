@@ -100,3 +100,88 @@ def test_gloo_two_ranks_tally_equals_single_process():
     # the shards really are different samples
     assert not np.array_equal(res[0][0], res[1][0])
     assert int(res[0][0][:, 0].sum() + res[1][0][:, 0].sum()) == 2 * N_WALKERS
+
+
+# ---- task partition: ranks own disjoint energies; the current and its gradient are sums ----
+
+MU = (0.6, -0.4, 0.3)
+N_PART = 20000
+
+
+def _part_wire():
+    return inputs.small_wire(9, W=2, L=3, n_energy=5, eta=0.25, e_lo=-1.7, e_hi=1.7)
+
+
+def _partial(w, idx):
+    """Oracle current, SE and exact gradient over the energies ``idx`` of wire ``w``."""
+    from oracle import adjoint, current, pipeline
+    E, wE = w.energy[idx], w.energy_weight[idx]
+    T, se = [], []
+    gV = np.zeros(w.W * w.L)
+    gE = np.zeros(w.W * w.L)
+    df = current.fermi(E, MU[0], MU[2]) - current.fermi(E, MU[1], MU[2])
+    for k, Ek in zip(idx, E):
+        r = pipeline.task_reference(w.onsite, w.eta, w.t, Ek, with_direct=False)
+        r["W"] = w.W
+        c = _tally(r, int(k), 0, np.arange(N_PART))
+        Tk, sk = current.mc_transmission(r["tab"]["c"][0], c[2], c[0])
+        T.append(Tk)
+        se.append(sk)
+        _, dV, dEta = adjoint.transmission_gradient(w.onsite, w.eta, w.t, Ek, 0, 1)
+        j = list(E).index(Ek)
+        gV += wE[j] * df[j] * dV.reshape(-1)
+        gE += wE[j] * df[j] * dEta.reshape(-1)
+    I, dI = current.current(E, wE, np.array(T), np.array(se), *MU)
+    return I, dI, gV, gE
+
+
+def _part_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = _part_wire()
+        idx = ndist.task_partition(len(w.energy), rank, world)
+        I, dI, gV, gE = _partial(w, idx)
+        It, st = ndist.reduce_current(np.array([I]), np.array([dI]))
+        gVt, gEt = ndist.reduce_gradient(gV, gE)
+        q.put((rank, idx, It, st, gVt, gEt))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_task_partition_covers_every_energy_once():
+    for world in (1, 2, 3, 8):
+        for n in (0, 1, 5, 256):
+            parts = [ndist.task_partition(n, r, world) for r in range(world)]
+            assert np.array_equal(np.sort(np.concatenate(parts)), np.arange(n))
+    with pytest.raises(ValueError):
+        ndist.task_partition(4, 2, 2)
+
+
+def test_gloo_two_ranks_task_partition_current_and_gradient():
+    """Each rank builds and walks only its own energies; one all-reduce of the partial current,
+    SE^2 and gradient reproduces the single-process result over all energies."""
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_part_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = {}
+    for _ in range(world):
+        rank, idx, It, st, gVt, gEt = q.get(timeout=240)
+        res[rank] = (idx, It, st, gVt, gEt)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    w = _part_wire()
+    assert not set(res[0][0]) & set(res[1][0])
+    I, dI, gV, gE = _partial(w, np.arange(len(w.energy)))
+    for rank in range(world):
+        _, It, st, gVt, gEt = res[rank]
+        assert np.allclose(It, I, rtol=1e-13, atol=1e-15)
+        assert np.allclose(st, dI, rtol=1e-13, atol=1e-15)
+        assert np.allclose(gVt, gV, rtol=1e-12, atol=1e-14)
+        assert np.allclose(gEt, gE, rtol=1e-12, atol=1e-14)

@@ -12,8 +12,9 @@
   sampled table rows (sites and injection modes) against the oracle's sparse column solves,
   realised two-level distribution within the quantisation bound + the precision's bar of the
   row and row sums within that bar: FP32 (CTA-wide CUDA-core chain) 1e-5; split TF32 (tensor
-  cores) 1e-4, the measured systematic bias of the tensor-core accumulation over chains of up
-  to 1000 slices being 3-5e-5; c_p 1e-5 for both; and the Monte Carlo transmission's
+  cores) the same 1e-5, an expected failure (the measured systematic bias of the tensor-core
+  accumulation over chains of up to 1000 slices is 3-5e-5); c_p 1e-5; and the Monte Carlo
+  transmission's
   reciprocity T_RL = T_LR within z_bar(2) combined standard errors with every walker absorbed.
 """
 import numpy as np
@@ -112,7 +113,17 @@ def test_differentiation_case_full_size(ctx):
         negf.negf_tables_free(tables)
 
 
-@pytest.mark.parametrize("precision,bar", [("fp32", 1e-5), ("split_tf32", 1e-4)])
+SPLIT_TF32_BIAS = ("split-TF32 tensor-core block products accumulate a systematic bias of "
+                   "about -1e-7 per chain step (truncation inside the tensor cores' FP32 "
+                   "accumulation: compensating 1/2 or 1 ulp per step removes only 14 or 29 % of "
+                   "it), so rows 300-1000 slices from their start are low by 3-5e-5 of the row: "
+                   "the split path misses the 1e-5 table bar at L = 1000")
+
+
+@pytest.mark.parametrize("precision,bar", [
+    ("fp32", 1e-5),
+    pytest.param("split_tf32", 1e-5, marks=pytest.mark.xfail(reason=SPLIT_TF32_BIAS, strict=False)),
+])
 def test_weak_scattering_full_size(ctx, precision, bar):
     wl = inputs.wire_64x1000()
     w = wl.wires[0]
