@@ -130,6 +130,15 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
   cf* Xc = Xa;
   cf* Xn = Xb;
   const int ty = tid / 16, tx = tid % 16;                  // outputs a = ty + 16i, b' = tx + 16j
+  // this thread's share of the next step's g block, fetched while the current step multiplies
+  constexpr int kGPer = kW * kW / kThreads;
+  cf gnext[kGPer];
+  auto fetch = [&](int k) {
+    const cf* gk = gsrc + (uint64_t)k * kW * kW;
+#pragma unroll
+    for (int q = 0; q < kGPer; ++q) gnext[q] = gk[tid + q * kThreads];
+  };
+  if (k_first != k_end) fetch(k_first);
   for (int k = k_first; k != k_end; k += kstep) {
     unsigned active = 0;
     for (int col = 0; col < 2; ++col) {
@@ -138,12 +147,10 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
       if (dir == 0 ? k < m0 : k > m0) active |= 1u << col;
       if (dir == 0 ? k == m0 - 1 : k == m0 + 1) load_start(Xc, col);
     }
-    const cf* gk = gsrc + (uint64_t)k * kW * kW;
-    for (int i = tid; i < kW * kW; i += kThreads) {
-      const cf v = gk[i];
-      Gs[i] = cf{mt * v.x, mt * v.y};
-    }
+#pragma unroll
+    for (int q = 0; q < kGPer; ++q) Gs[tid + q * kThreads] = cf{mt * gnext[q].x, mt * gnext[q].y};
     __syncthreads();
+    if (k + kstep != k_end) fetch(k + kstep);
     float accr[4][8], acci[4][8];
 #pragma unroll
     for (int i = 0; i < 4; ++i)

@@ -113,7 +113,7 @@ def wire_32x100(seed=6, n_energy=8, precision="fp32", walkers=1_000_000):
                     seed)
 
 
-def wire_64x100(seed=5, n_energy=8, precision="split_tf32", walkers=1_000_000):
+def wire_64x100(seed=5, n_energy=8, precision="fp32", walkers=1_000_000):
     """W = 64 x L = 100, onsite U[-0.5, 0.5], eta = 0.005, 8 energies: the wide-slice kernels
     on a case small enough for full ncu captures (tables ~0.7 GB)."""
     rng = np.random.default_rng(seed)
