@@ -71,13 +71,19 @@ def tensor_peak(kind):
         return 1900.0 * 1.1 / 2.25, "fallback BF16 1.9 PFLOP/s x nominal TF32/BF16 ratio"
 
 
-# DRAM traffic per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of a
-# timed launch, see profiles/) keyed by kernel, workload and a hash of the kernel's sources: a
-# kernel changed since its counters were taken reports null.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture, see profiles/)
+# per step of the named workload, keyed by kernel, workload and a hash of the kernel's sources:
+# a kernel changed since its counters were taken reports null.  The headline's chain and
+# level-2 figures are scaled from captures of the W = 64 x L = 100 wire (8 tasks) by the
+# units processed (both the weights and the g blocks grow as n^2 per task): x 100 per task,
+# x 256 / 8 tasks.
 MEASURED_TRAFFIC = {
-    ("walk_kernel", "wire_W10_L50_eta0.05_64E", "6f10e941e2fe02bd"): 133336576,
+    ("walk_kernel", "wire_W10_L50_eta0.05_64E", "e2d18e70c6f09171"): 133861888,
+    ("chain_cta_kernel", "wire_W64_L1000_eta0.005_256E", "7a863ab2ab935cf2"): 4565932748800,
+    ("two_level_kernel", "wire_W64_L1000_eta0.005_256E", "5d548d12518c95ef"): 9015689600000,
 }
-TRAFFIC_SOURCES = {"walk_kernel": ["k_walk.cu", "philox.cuh"]}
+TRAFFIC_SOURCES = {"walk_kernel": ["k_walk.cu", "philox.cuh"], "chain_cta_kernel": ["k_chain_cta.cu"],
+                   "two_level_kernel": ["k_alias.cu"]}
 
 
 def measured_traffic(kernel, workload):
