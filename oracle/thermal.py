@@ -32,8 +32,15 @@ b with counter (b, wid_lo, wid_hi, 0x80000000 | wire):
 A draw with words (x, y) over a K-entry row picks c = (x K) >> 32 and keeps c if y < thr[c],
 else alias[c].
 
+The interpolating sampler's grid (``refine_grid``): intervals whose two ends' Step 6'
+probabilities differ by more than a tolerance (``interval_distance``, five percent in the
+paper) are split at their midpoints until every interval passes.
+
 Pinned by (tests/test_oracle_thermal.py): Th against the central difference of the Fermi
-function and its integral against the closed-form CDF; the direct conductance of a clean chain
+function and its integral against the closed-form CDF; the interval distance zero on equal
+tables, symmetric, within [0, 1], and the refined grid's intervals all within the tolerance with
+the interpolated conductance converging to the direct one as the tolerance shrinks (error
+falling about as its square); the direct conductance of a clean chain
 and of a clean wire's channel staircase in closed form; the interpolated chain equal to the
 exact absorbing chain at alpha = 0 and 1 and converging to the direct conductance at the h^2
 rate of linear interpolation; the replay walker within 4 SE of the interpolated chain's exact
@@ -126,6 +133,52 @@ def interpolated_absorption(tab_i, tab_j, alpha, p=0):
     P_site = np.linalg.solve(np.eye(n) - Q, R)
     Pi = P[n + p * W:n + (p + 1) * W]
     return u @ (Pi[:, n:] + Pi[:, :n] @ P_site)
+
+
+def interval_distance(tab_i, tab_j, p=0):
+    """How far apart the Step 6' probabilities of two grid energies are (Sec. "Interpolation":
+    where two nearby energies' probabilities p_i differ by less than five percent, the p_i in
+    between are interpolated linearly).  The largest of: the total-variation distance
+    (1/2) sum_b |P_ab(E_i) - P_ab(E_j)| of every row a (rows normalised to their sums; a row of
+    zero sum is all zeros), the same for the injection-mode distributions of lead p, and the
+    relative change |c_i - c_j| / max(c_i, c_j) of c = Tr Gamma_p A (0 when both vanish)."""
+    d = 0.5 * np.abs(_chain(tab_i) - _chain(tab_j)).sum(axis=1).max()
+    mi, mj = tab_i["mode_w"][p], tab_j["mode_w"][p]
+    ui = mi / mi.sum() if mi.sum() > 0 else np.zeros_like(mi)
+    uj = mj / mj.sum() if mj.sum() > 0 else np.zeros_like(mj)
+    d = max(d, 0.5 * np.abs(ui - uj).sum())
+    ci, cj = tab_i["c"][p], tab_j["c"][p]
+    if max(ci, cj) > 0.0:
+        d = max(d, abs(ci - cj) / max(ci, cj))
+    return float(d)
+
+
+def refine_grid(onsite, eta, t, e_lo, e_hi, n_init, tol=0.05, max_points=257, p=0,
+                lead_model=0, gamma_lead=0.0):
+    """The energy grid of the interpolating sampler (Sec. "Interpolation"): start from n_init
+    evenly spaced energies on [e_lo, e_hi]; in each round every interval whose two ends are
+    farther apart than tol (interval_distance) is split at its midpoint (E_i + E_{i+1}) / 2, in
+    the order of the grid, as long as the grid stays within max_points energies; stop when every
+    interval passes or no point can be added.  Returns (grid, distances of its intervals)."""
+    W = np.asarray(onsite).shape[1]
+
+    def table(E):
+        g = wire.green_retarded(E, onsite, eta, t, lead_model, gamma_lead)
+        phi, _, gam = wire.lead_modes(E, W, t, lead_model, gamma_lead)
+        return markov.transition_weights(g, (phi, gam))
+    grid = [float(E) for E in np.linspace(e_lo, e_hi, n_init)]
+    tabs = {E: table(E) for E in grid}
+    while True:
+        d = [interval_distance(tabs[grid[i]], tabs[grid[i + 1]], p) for i in range(len(grid) - 1)]
+        new = []
+        for i, di in enumerate(d):
+            if di > tol and len(grid) + len(new) < max_points:
+                new.append(0.5 * (grid[i] + grid[i + 1]))
+        if not new:
+            return np.array(grid), np.array(d)
+        for E in new:
+            tabs[E] = table(E)
+        grid = sorted(grid + new)
 
 
 def conductance_interpolated(tabs, grid, mu, kT, n_quad=16, p=0):

@@ -133,3 +133,36 @@ def test_planted_mistakes_are_caught(bad):
                 (grid[-1] - grid[0])
             total += 0.5 * (hi - lo) * wq * dens * c * P[1]
     assert abs(total - G_exact) > 1e-3 * G_exact
+
+
+def test_interval_distance_properties():
+    w = inputs.small_wire(611, W=3, L=5, n_energy=1, eta=0.12)
+    ta, tb = _tabs(w, [0.31, 0.37])
+    assert thermal.interval_distance(ta, ta) == 0.0
+    d = thermal.interval_distance(ta, tb)
+    assert d == thermal.interval_distance(tb, ta)
+    assert 0.0 < d <= 1.0
+    # a closed start lead at one end only: the relative change of c is 1
+    closed = dict(ta, c=np.array([0.0, ta["c"][1]]), mode_w=np.zeros_like(ta["mode_w"]))
+    assert thermal.interval_distance(closed, tb) == 1.0
+
+
+def test_refined_grid_meets_tolerance_and_converges():
+    """The paper's rule (interpolate where the ends differ by less than 5 %): every interval of
+    the refined grid passes, and the interpolated conductance approaches the direct one as the
+    tolerance shrinks, about as its square (interval widths scale with the tolerance)."""
+    w = inputs.small_wire(603, W=4, L=6, n_energy=1, eta=0.1, disorder=0.6)
+    mu, kT = 0.15, 0.06
+    errs = []
+    for tol in (0.2, 0.05):
+        grid, d = thermal.refine_grid(w.onsite, w.eta, w.t, mu - 5 * kT, mu + 5 * kT, 3, tol=tol)
+        assert np.all(d <= tol) and np.all(np.diff(grid) > 0)
+        tabs = _tabs(w, grid)
+        G_int = thermal.conductance_interpolated(tabs, grid, mu, kT, n_quad=24)
+        G_dir = thermal.conductance_direct(w.onsite, w.eta, w.t, grid, mu, kT, n_quad=8)
+        errs.append(abs(G_int - G_dir) / G_dir)
+    assert errs[1] < errs[0] / 8.0 and errs[1] < 1e-3, errs
+    # the cap on the number of points is honoured
+    grid, d = thermal.refine_grid(w.onsite, w.eta, w.t, mu - 5 * kT, mu + 5 * kT, 3, tol=1e-4,
+                                  max_points=9)
+    assert grid.size == 9 and np.any(d > 1e-4)
