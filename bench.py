@@ -756,16 +756,39 @@ def run_gradient(args):
 
 # ------------------------------------------------------------------ thermal-window sampler
 
-THERMAL_GRID = 17          # grid energies spanning mu +- 8 kT
+THERMAL_INIT = 9           # evenly spaced energies the adaptive grid starts from (mu +- 8 kT)
+THERMAL_TOL = 0.05         # split an interval whose ends' probabilities differ by more than 5 %
+THERMAL_MAX = 257          # at most this many grid energies
+PLAIN_ENERGIES = 256       # the plain sampler's drawn energies (tables built at each)
+PLAIN_WALKERS = 1 << 16    # walkers per drawn energy
 
 
-def thermal_wire(wl):
-    """The workload's first wire on a grid of THERMAL_GRID energies spanning mu +- 8 kT around
-    mu = 0 (the linear-response reading: E_F = 0) at the workload's kT."""
-    w = wl.wires[0]
-    grid = np.linspace(-8.0 * wl.kT, 8.0 * wl.kT, THERMAL_GRID)
+def on_grid(w, grid):
+    grid = np.asarray(grid, dtype=np.float64)
     return inputs.Wire(W=w.W, L=w.L, t=w.t, onsite=w.onsite, eta=w.eta, energy=grid,
-                       energy_weight=np.ones_like(grid)), 0.0, wl.kT
+                       energy_weight=np.ones_like(grid))
+
+
+def plain_thermal(ctx, negf, w, mu, kT, prec, seed):
+    """The plain sampler the interpolation replaces: PLAIN_ENERGIES energies drawn from Th on
+    mu +- 8 kT (inverse CDF of seeded uniforms), tables built at every drawn energy, walks there,
+    G = window x the mean transmission.  Returns (G, se, seconds) with the build, the walks and
+    the tally read inside the wall-clock region."""
+    F = lambda E: 1.0 / (1.0 + np.exp(-(E - mu) / kT))            # noqa: E731
+    F0, F1 = F(mu - 8 * kT), F(mu + 8 * kT)
+    u = np.sort(np.random.default_rng(seed).random(PLAIN_ENERGIES))
+    Fd = F0 + u * (F1 - F0)
+    wd = on_grid(w, mu + kT * np.log(Fd / (1.0 - Fd)))
+    import torch
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tables, tally = negf.negf_run(ctx, [wd], 0, seed, PLAIN_WALKERS, precision=prec)
+    cur = negf.negf_current(ctx, tables, tally, mu + 1.0, mu - 1.0, kT)
+    dt = time.perf_counter() - t0
+    negf.negf_tally_free(tally)
+    negf.negf_tables_free(tables)
+    T = cur["T"]
+    return (F1 - F0) * T.mean(), (F1 - F0) * T.std(ddof=1) / np.sqrt(T.size), dt
 
 
 def run_thermal(args):
@@ -781,13 +804,20 @@ def run_thermal(args):
     build.build()
     wl = workload(args.workload or "wire_10x50", args.energies)
     prec = args.precision or wl.precision
-    w, mu, kT = thermal_wire(wl)
+    mu, kT = 0.0, wl.kT                  # the linear-response reading: E_F = 0
+    stream = torch.cuda.current_stream()
+    ctx = negf.negf_create(local, stream)
+    # the interpolating sampler's grid (adaptive rule), once, outside the timed steps
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    grid = negf.negf_thermal_grid(ctx, wl.wires[0], mu - 8 * kT, mu + 8 * kT, THERMAL_INIT,
+                                  THERMAL_TOL, THERMAL_MAX, precision=prec)
+    grid_s = time.perf_counter() - t0
+    w = on_grid(wl.wires[0], grid)
     N = (args.walkers or wl.walkers_per_task) * len(wl.wires[0].energy)
     dev = inputs.Wire(W=w.W, L=w.L, t=w.t, onsite=torch.from_numpy(w.onsite).cuda(),
                       eta=torch.from_numpy(w.eta).cuda(), energy=torch.from_numpy(w.energy).cuda(),
                       energy_weight=torch.from_numpy(w.energy_weight).cuda())
-    stream = torch.cuda.current_stream()
-    ctx = negf.negf_create(local, stream)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
 
     def one_step(i, wire, memspace):
@@ -844,9 +874,52 @@ def run_thermal(args):
         e2e_ms += (time.perf_counter() - t0) * 1e3
         e2e_steps += r["mean_steps"] * r["walkers"]
     h2d = w.onsite.nbytes + w.eta.nbytes + w.energy.nbytes + w.energy_weight.nbytes
+    # seconds per conductance at 1 % SE: interpolating (grid once + tables on it + walks scaled
+    # to the walkers 1 % needs) against plain (tables at every drawn energy, scaled to the
+    # energies 1 % needs); both wall clock through the public calls
+    wall = []
+    for i in range(2):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tb = negf.negf_build_tables(ctx, [dev], precision=prec, memspace="device")
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = negf.negf_walk_thermal(ctx, tb, 0, 0, args.seed + 7, N, mu, kT,
+                                   walker_id_offset=(40_000 + i) * N, max_steps=args.max_steps)
+        t2 = time.perf_counter()
+        negf.negf_tables_free(tb)
+        wall.append((t1 - t0, t2 - t1, r))
+    tab_s, walk_s, ri = wall[-1]
+    Gp, sep, plain_s = plain_thermal(ctx, negf, wl.wires[0], mu, kT, prec, args.seed)
+    # s(eps) to a relative SE eps: interpolating = fixed (grid + tables) + walk_s (se/G)^2 /
+    # eps^2; plain = plain_s (se/G)^2 / eps^2 (its energies scale with 1 / eps^2)
+    fixed_i = grid_s + tab_s
+    coef_i = walk_s * (ri["se"] / ri["G"]) ** 2 if ri["G"] > 0 else float("inf")
+    coef_p = plain_s * (sep / Gp) ** 2 if Gp > 0 else float("inf")
+    s_i = lambda eps: fixed_i + coef_i / eps ** 2                  # noqa: E731
+    s_p = lambda eps: coef_p / eps ** 2                            # noqa: E731
+    comparison = {
+        "target": "seconds to G at relative standard error eps, wall clock through the public "
+                  "calls, scaled from the measured runs (walkers or drawn energies ~ 1 / eps^2)",
+        "interpolating": {
+            "grid_points": int(grid.size), "rule": f"split where the distance > {THERMAL_TOL}",
+            "grid_s": round(grid_s, 4), "tables_s": round(tab_s, 4),
+            "walkers": int(N), "walk_s": round(walk_s, 4), "G": ri["G"], "se": ri["se"],
+            "s_per_G_1pct": round(s_i(1e-2), 5), "s_per_G_0.1pct": round(s_i(1e-3), 5)},
+        "plain": {
+            "energies": PLAIN_ENERGIES, "walkers_per_energy": PLAIN_WALKERS,
+            "s": round(plain_s, 4), "G": Gp, "se": sep,
+            "s_per_G_1pct": round(s_p(1e-2), 5), "s_per_G_0.1pct": round(s_p(1e-3), 5)},
+        "z_interp_vs_plain": (ri["G"] - Gp) / np.hypot(ri["se"], sep),
+        "speedup_1pct": round(s_p(1e-2) / s_i(1e-2), 3),
+        "speedup_0.1pct": round(s_p(1e-3) / s_i(1e-3), 3),
+        # below this relative SE the interpolating sampler is the faster one
+        "crossover_eps": (float(np.sqrt((coef_p - coef_i) / fixed_i))
+                          if coef_p > coef_i else None),
+    }
     # roofline: one 8-byte alias entry per draw (injection + transitions); the grid's tables
     # sit in L2, so the ceiling is the measured random-gather rate over their size
-    tab_bytes = THERMAL_GRID * (w.W * w.L + 2 * w.W) * (w.W * w.L + 2) * 8
+    tab_bytes = grid.size * (w.W * w.L + 2 * w.W) * (w.W * w.L + 2) * 8
     probe_tab = min(tab_bytes, 16 << 30)
     gps = negf.negf_probe_gather(ctx, probe_tab, ilp=8, chain=64)
     negf.negf_destroy(ctx)
@@ -865,15 +938,16 @@ def run_thermal(args):
         "dtype": {"fp64": "f64 tables, u32 walks, integer tally",
                   "fp32": "f32 tables, u32 walks, integer tally"}.get(prec, prec),
         "data": "synthetic (seeded square-lattice wire standing in for the paper's CdTe nanowires)",
-        "config": {"workload": f"thermal_{wl.name.split('_64E')[0]}_{THERMAL_GRID}E_kT{kT}",
+        "config": {"workload": f"thermal_{wl.name.split('_64E')[0]}_adaptive_kT{kT}",
                    "sampler": "energies from Th = -df/dE on the grid span, chain interpolated "
                               "between grid energies",
-                   "grid": [float(w.energy[0]), float(w.energy[-1]), THERMAL_GRID], "mu": mu,
+                   "grid": [float(w.energy[0]), float(w.energy[-1]), int(grid.size)], "mu": mu,
                    "kT": kT, "walkers_per_step": walkers, "precision": prec,
                    "l2": "flushed between timed steps (258 MiB write, outside the timed events)",
                    "mode": "thermal"},
         "conductance": {"G": res["G"], "se": res["se"], "window": res["window"],
                         "unit": "e^2/h"},
+        "comparison": comparison,
         "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
         "roofline": {"kernel": kname, "bound": "l2", "achieved": round(ach, 1),
                      "peak": round(peak, 1), "unit": "GB/s",
@@ -905,7 +979,7 @@ def run_thermal(args):
             steps += int(st.sum())
         dt = time.perf_counter() - t0
         out["cpu_baseline"] = {"value": steps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                               "sample": f"{THERMAL_GRID} grid tables + {n_w} walkers "
+                               "sample": f"{grid.size} grid tables + {n_w} walkers "
                                          f"({dt:.1f} s, numpy/LAPACK single thread)"}
     print(json.dumps(out), flush=True)
 

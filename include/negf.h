@@ -370,7 +370,7 @@ typedef struct {
 /* The linear conductance G_qp = integral dE T_qp(E) Th(E), Th = -df/dE (Eq. Gqp_expression),
  * sampled as the paper does (Eq. gpq_formula, Eq. elast_lin_xpq): each walker draws its energy
  * E_0 from Th, restricted to the span [E_0, E_{M-1}] of wire `wire`'s energy grid (the M >= 2
- * energies of that wire in the tables, strictly ascending, one-level layout), and walks the
+ * energies of that wire in the tables, strictly ascending, all of one layout), and walks the
  * Markov chain whose Step 6' transition probabilities are interpolated linearly between the two
  * grid energies around E_0 (the paper's interpolation of the p_i, Sec. "Interpolation"): every
  * draw uses the table of the upper grid energy with probability alpha = (E_0 - E_i) /
@@ -386,12 +386,14 @@ typedef struct {
  * energy (FP64, each operation rounded; its interval i: F(E_i) <= F < F(E_{i+1}), decided
  * exactly; alpha from F^-1(F) in FP32, to ~2^-20), word x2 the
  * injection table (upper iff x2 < a, a = min(floor(alpha 2^32), 2^32 - 1)); block 1 the injection
- * mode (x0, x1); block b >= 2 transition b - 1 ((x0, x1) on the row, x2 < a picks the table).
+ * mode (x0, x1); block b >= 2 transition b - 1 ((x0, x1) on the row, x2 < a picks the table;
+ * two-level tables: (x0, x1) on the level-1 row and v = x3 >> 1 for the site of a drawn slice).
  * d_lead, d_steps, d_interval, d_a: optional caller-owned device arrays of `walkers` entries
  * (any may be NULL) receiving each walker's outcome (0 / 1 lead, -1 closed, -2 truncated),
  * transitions, grid interval i and a.  Allocates a small tally on the context stream, runs on it
  * and synchronises.  Errors: NEGF_E_INVALID for bad handles, wire out of range, fewer than two
- * energies, energies not strictly ascending, two-level tables, tables released by negf_run,
+ * energies, energies not strictly ascending, one- and two-level tables mixed, tables released
+ * by negf_run,
  * kT <= 0, non-finite mu, walkers above 2^40, max_steps outside [1, NEGF_MAX_STEPS];
  * NEGF_E_NOMEM; NEGF_E_CUDA. */
 negf_status negf_walk_thermal(negf_ctx ctx, negf_tables tables, int32_t wire, int32_t start_lead,
@@ -399,6 +401,31 @@ negf_status negf_walk_thermal(negf_ctx ctx, negf_tables tables, int32_t wire, in
                               double mu, double kT, uint32_t max_steps, int32_t* d_lead,
                               uint32_t* d_steps, int32_t* d_interval, uint32_t* d_a,
                               negf_thermal_result* out);
+
+/* Distances between the Step 6' probabilities of consecutive energies of wire `wire` (the
+ * paper interpolates the probabilities between two nearby energies where they differ by less
+ * than five percent, Sec. "Interpolation"): for energies e, e + 1 of the wire (in the order
+ * given), d[e] = the largest of (1) the total-variation distance (1/2) sum_b |P_ab(e) -
+ * P_ab(e+1)| of every table row a (P = weights / row sum; a row of zero sum counts as zero),
+ * (2) the same between the injection-mode distributions of lead start_lead, (3) |c_e -
+ * c_{e+1}| / max(c_e, c_{e+1}) for c = Tr[Gamma_p A] (0 when both vanish).  d: host array of
+ * n_energy - 1 doubles.  Needs tables built with keep_weights.  Synchronises.  Errors:
+ * NEGF_E_INVALID (bad handle or wire, fewer than two energies, weights not kept), NEGF_E_CUDA. */
+negf_status negf_interval_distance(negf_ctx ctx, negf_tables tables, int32_t wire,
+                                   int32_t start_lead, double* d);
+
+/* The energy grid of the interpolating sampler (Sec. "Interpolation"): start from n_init
+ * evenly spaced energies on [e_lo, e_hi] (the last one e_hi exactly); in each round, build the
+ * wire's tables on the current grid (host arrays, as NEGF_MEM_HOST; the wire's own energies
+ * and weights are ignored) and split every interval whose negf_interval_distance exceeds tol
+ * at its midpoint (E_i + E_{i+1}) / 2, in grid order, while the grid holds fewer than
+ * max_points energies; stop when every interval passes or no point can be added.  energies:
+ * host array of max_points doubles receiving the ascending grid, *n_out its length.  The
+ * grid is for negf_build_tables + negf_walk_thermal.  Synchronises.  Errors: NEGF_E_INVALID
+ * for e_lo >= e_hi, n_init < 2, max_points < n_init, tol <= 0, and as negf_build_tables. */
+negf_status negf_thermal_grid(negf_ctx ctx, const negf_wire* wire, int32_t precision, double e_lo,
+                              double e_hi, int32_t n_init, double tol, int32_t max_points,
+                              int32_t start_lead, double* energies, int32_t* n_out);
 
 /* --- table build without device allocation ------------------------------------------------ */
 

@@ -49,6 +49,7 @@ expectation and its energies Kolmogorov-Smirnov-consistent with Th; planted mist
 import numpy as np
 
 from . import buttiker, markov, wire
+from .alias import draw_level2
 from .philox import philox4x32_10
 
 MASK32 = np.uint64(0xFFFFFFFF)
@@ -203,13 +204,16 @@ def conductance_interpolated(tabs, grid, mu, kT, n_quad=16, p=0):
 
 
 def walk(entries, mode_entries, c, n, W, wire_index, start_lead, seed, wids, grid, mu, kT,
-         max_steps, energy=None):
+         max_steps, energy=None, level2=None):
     """Replay walkers ``wids`` of the thermal sampler over integer alias tables.
 
     entries[e] [n + 2W, n + 2] and mode_entries[e] [2, W] (uint64) and c[e] (Tr Gamma_p A at the
     two leads) of every grid energy e.  ``energy``: optional (interval, a) arrays that replace the
-    energy draw (the replay of a trace).  Returns (lead int32: 0 / 1, -1 no open channel, -2
-    truncated; steps uint32; interval int64; a uint64).
+    energy draw (the replay of a trace).  ``level2``: for two-level tables, (blocks, L) with
+    blocks[e] [n + 2W, L, alias.level2_words(W)] the level-2 inverse-CDF blocks, entries[e] then
+    being the level-1 alias rows [n + 2W, L + 2]; a transition draws the slice or lead with
+    (x0, x1) and the site of a drawn slice with v = x3 >> 1 (alias.draw_level2).  Returns
+    (lead int32: 0 / 1, -1 no open channel, -2 truncated; steps uint32; interval int64; a uint64).
     """
     wids = np.asarray(wids, dtype=np.uint64)
     m = wids.size
@@ -248,9 +252,17 @@ def walk(entries, mode_entries, c, n, W, wire_index, start_lead, seed, wids, gri
             z = philox4x32_10(np.array([b], np.uint64), wlo[w:w + 1], whi[w:w + 1],
                               ctr3[w:w + 1], k0, k1)
             t = pick(z[2][0])
-            cc = (int(z[0][0]) * K) >> 32
-            e = int(entries[t][row, cc])
-            j = cc if int(z[1][0]) < (e & 0xFFFFFFFF) else (e >> 32)
+            if level2 is None:
+                cc = (int(z[0][0]) * K) >> 32
+                e = int(entries[t][row, cc])
+                j = cc if int(z[1][0]) < (e & 0xFFFFFFFF) else (e >> 32)
+            else:
+                blocks, L = level2
+                cc = (int(z[0][0]) * (L + 2)) >> 32
+                e = int(entries[t][row, cc])
+                k = cc if int(z[1][0]) < (e & 0xFFFFFFFF) else (e >> 32)
+                j = n + (k - L) if k >= L else \
+                    k * W + int(draw_level2(blocks[t][row, k], W, [int(z[3][0]) >> 1])[0])
             steps[w] += 1
             if j >= n:
                 lead[w] = j - n

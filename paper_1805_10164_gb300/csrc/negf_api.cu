@@ -1675,6 +1675,74 @@ negf_status negf_current(negf_ctx ctx, negf_tables t, negf_tally tl, double mu_p
   return NEGF_OK;
 }
 
+negf_status negf_interval_distance(negf_ctx ctx, negf_tables t, int32_t wire, int32_t start_lead,
+                                  double* d) {
+  if (!ctx || !t || t->ctx != ctx || !d)
+    return fail(ctx, NEGF_E_INVALID, "negf_interval_distance: bad argument");
+  if (wire < 0 || wire >= t->n_wires)
+    return fail(ctx, NEGF_E_INVALID, "negf_interval_distance: wire %d out of range", wire);
+  if (start_lead != 0 && start_lead != 1)
+    return fail(ctx, NEGF_E_INVALID, "negf_interval_distance: start_lead must be 0 or 1");
+  if (!t->d_weights)
+    return fail(ctx, NEGF_E_INVALID, "negf_interval_distance: build the tables with keep_weights");
+  const int task0 = t->h_wire_task0[wire], task1 = t->h_wire_task0[wire + 1];
+  const int M = task1 - task0;
+  if (M < 2) return fail(ctx, NEGF_E_INVALID, "negf_interval_distance: the wire needs two energies");
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = ctx->stream;
+  double* d_out = nullptr;
+  CUDA_TRY(ctx, dalloc(&d_out, (size_t)(M - 1), s, nullptr));
+  cudaError_t e = negf::launch_interval_distance(t->d_tasks, task0, M, t->h_tasks[task0].rows,
+                                                 t->precision, t->d_weights, t->d_rowsum,
+                                                 t->d_mode_w, t->d_c, start_lead, d_out, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d, d_out, sizeof(double) * (M - 1), cudaMemcpyDeviceToHost, s);
+  dfree(d_out, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(ctx, NEGF_E_CUDA, "negf_interval_distance: %s", cudaGetErrorString(e));
+  return check_device(ctx, t);
+}
+
+negf_status negf_thermal_grid(negf_ctx ctx, const negf_wire* wire, int32_t precision, double e_lo,
+                              double e_hi, int32_t n_init, double tol, int32_t max_points,
+                              int32_t start_lead, double* energies, int32_t* n_out) {
+  if (!ctx) return NEGF_E_INVALID;
+  if (!wire || !energies || !n_out)
+    return fail(ctx, NEGF_E_INVALID, "negf_thermal_grid: NULL argument");
+  if (!(e_hi > e_lo) || !isfinite(e_lo) || !isfinite(e_hi) || n_init < 2 || max_points < n_init ||
+      !(tol > 0.0) || !isfinite(tol))
+    return fail(ctx, NEGF_E_INVALID,
+                "negf_thermal_grid: need e_lo < e_hi, 2 <= n_init <= max_points, tol > 0");
+  // evenly spaced as i * step + e_lo with step = (e_hi - e_lo) / (n_init - 1), the last e_hi
+  std::vector<double> grid(n_init);
+  const double step = (e_hi - e_lo) / (n_init - 1);
+  for (int i = 0; i < n_init; ++i) grid[i] = i + 1 == n_init ? e_hi : i * step + e_lo;
+  negf_build_opts o{precision, NEGF_MEM_HOST, 1, 0, NEGF_LAYOUT_AUTO};
+  while (true) {
+    negf_wire w = *wire;
+    w.n_energy = (int32_t)grid.size();
+    w.energy = grid.data();
+    w.energy_weight = nullptr;
+    negf_tables t = nullptr;
+    negf_status st = negf_build_tables(ctx, &w, 1, &o, &t);
+    if (st != NEGF_OK) return st;
+    std::vector<double> d(grid.size() - 1);
+    st = negf_interval_distance(ctx, t, 0, start_lead, d.data());
+    negf_tables_free(t);
+    if (st != NEGF_OK) return st;
+    std::vector<double> add;
+    for (size_t i = 0; i < d.size(); ++i)
+      if (d[i] > tol && (int)(grid.size() + add.size()) < max_points)
+        add.push_back(0.5 * (grid[i] + grid[i + 1]));
+    if (add.empty()) break;
+    grid.insert(grid.end(), add.begin(), add.end());
+    std::sort(grid.begin(), grid.end());
+  }
+  for (size_t i = 0; i < grid.size(); ++i) energies[i] = grid[i];
+  *n_out = (int32_t)grid.size();
+  return NEGF_OK;
+}
+
 negf_status negf_walk_thermal(negf_ctx ctx, negf_tables t, int32_t wire, int32_t start_lead,
                               uint64_t seed, uint64_t walkers, uint64_t walker_id_offset,
                               double mu, double kT, uint32_t max_steps, int32_t* d_lead,
@@ -1695,10 +1763,11 @@ negf_status negf_walk_thermal(negf_ctx ctx, negf_tables t, int32_t wire, int32_t
   const int task1 = wire + 1 < t->n_wires ? t->h_wire_task0[wire + 1] : t->n_tasks;
   const int M = task1 - task0;
   if (M < 2) return fail(ctx, NEGF_E_INVALID, "negf_walk_thermal: the wire needs two energies");
+  const bool two = t->h_tasks[task0].layout == NEGF_LAYOUT_TWO_LEVEL;
   for (int e = 0; e < M; ++e) {
     const TaskDesc& d = t->h_tasks[task0 + e];
-    if (d.layout != NEGF_LAYOUT_ONE_LEVEL)
-      return fail(ctx, NEGF_E_INVALID, "negf_walk_thermal: two-level tables are not supported");
+    if ((d.layout == NEGF_LAYOUT_TWO_LEVEL) != two)
+      return fail(ctx, NEGF_E_INVALID, "negf_walk_thermal: the grid mixes one- and two-level tables");
     if (e > 0 && !(d.E > t->h_tasks[task0 + e - 1].E))
       return fail(ctx, NEGF_E_INVALID, "negf_walk_thermal: energies must be strictly ascending");
   }
@@ -1741,7 +1810,7 @@ negf_status negf_walk_thermal(negf_ctx ctx, negf_tables t, int32_t wire, int32_t
     e = negf::launch_thermal_walk(t->d_tasks, task0, M, wire, t->d_tab, t->d_mode_tab, t->d_c,
                                   start_lead, seed, walkers, walker_id_offset, max_steps, mu, kT,
                                   F0, window, d_thr, d_tally, d_lead, d_steps, d_interval, d_a,
-                                  ctx->sm_count, ctx->stream);
+                                  ctx->sm_count, ctx->stream, two);
   }
   std::vector<unsigned long long> h(nf, 0ull);
   if (e == cudaSuccess)

@@ -188,7 +188,8 @@ cudaError_t launch_current(const TaskDesc* d_tasks, int n_tasks, int n_wires,
                            const uint64_t* d_tally, int start_lead, double mu_p, double mu_q,
                            double kT, double* d_out, cudaStream_t s);
 // Thermal-window walks over the interpolated chain of one wire's energy grid (k_thermal.cu):
-// tasks task0 .. task0 + M - 1 (ascending energies, one-level tables); d_thr [M - 1]: the
+// tasks task0 .. task0 + M - 1 (ascending energies; all one-level, or all two-level with
+// two_level set); d_thr [M - 1]: the
 // least 53-bit energy word v whose CDF value reaches grid point e + 1 (non-decreasing); tally
 // [3 (M - 1) + 5] u64: per interval (absorbed at q, sum a, sum (a >> 16)^2), then absorbed L,
 // R, closed, truncated, steps.  Trace arrays optional (nullptr).
@@ -199,7 +200,16 @@ cudaError_t launch_thermal_walk(const TaskDesc* d_tasks, int task0, int M, int w
                                 double mu, double kT, double F0, double window,
                                 const unsigned long long* d_thr, unsigned long long* d_tally,
                                 int32_t* d_lead, uint32_t* d_steps, int32_t* d_interval,
-                                uint32_t* d_a, int sm_count, cudaStream_t s);
+                                uint32_t* d_a, int sm_count, cudaStream_t s,
+                                bool two_level = false);
+// Distances between the Step 6' probabilities of consecutive grid energies task0 .. task0 + M - 1
+// of one wire (k_thermal.cu): d_out[e] for energies e, e + 1 (M - 1 doubles); rows = the tasks'
+// table rows; needs the FP weights.
+cudaError_t launch_interval_distance(const TaskDesc* d_tasks, int task0, int M, int rows,
+                                     int precision, const void* d_weights,
+                                     const double* d_rowsum, const double* d_mode_w,
+                                     const double* d_c, int start_lead, double* d_out,
+                                     cudaStream_t s);
 // Backward (score-function gradient, see k_backward.cu).
 cudaError_t launch_backward_seeds(const TaskDesc* d_tasks, int n_tasks, uint32_t n_jobs,
                                   int precision, const void* d_weights, const double* d_rowsum,

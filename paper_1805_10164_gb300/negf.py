@@ -134,6 +134,9 @@ def load():
         "negf_profile_read": (I32, [P, I32, P, P, P, C.POINTER(I32)]),
         "negf_walk_thermal": (I32, [P, P, I32, I32, U64, U64, U64, D, D, U32, P, P, P, P,
                                     C.POINTER(negf_thermal_result)]),
+        "negf_interval_distance": (I32, [P, P, I32, I32, P]),
+        "negf_thermal_grid": (I32, [P, C.POINTER(negf_wire), I32, D, D, I32, D, I32, I32, P,
+                                    C.POINTER(I32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -383,6 +386,27 @@ def negf_build_tables_noalloc(wire, precision, stream, d_alias, d_mode_alias, d_
     handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return load().negf_build_tables_noalloc(C.byref(w), PRECISION[precision], C.c_void_p(handle),
                                             _ptr(d_alias), _ptr(d_mode_alias), _ptr(d_c))
+
+
+def negf_interval_distance(ctx, tables, wire, n_energy, start_lead=0):
+    """Distances of the wire's consecutive energies' Step 6' probabilities (n_energy - 1)."""
+    d = np.zeros(max(n_energy - 1, 1))
+    _check(ctx, load().negf_interval_distance(ctx, tables, int(wire), int(start_lead),
+                                              d.ctypes.data))
+    return d[:n_energy - 1]
+
+
+def negf_thermal_grid(ctx, wire, e_lo, e_hi, n_init, tol=0.05, max_points=257,
+                      precision="fp64", start_lead=0):
+    """The interpolating sampler's grid on [e_lo, e_hi] (ascending energies)."""
+    keep = []
+    arr = _wire_array([wire], "host", keep)
+    out = np.zeros(int(max_points))
+    n = C.c_int32(0)
+    _check(ctx, load().negf_thermal_grid(ctx, arr, PRECISION[precision], float(e_lo),
+                                         float(e_hi), int(n_init), float(tol), int(max_points),
+                                         int(start_lead), out.ctypes.data, C.byref(n)))
+    return out[:n.value].copy()
 
 
 def negf_device_error_status(word):

@@ -11,7 +11,7 @@ def test_workloads_are_seeded_and_shaped():
         (inputs.wire_10x50, 10, 50, 1.0, 0.05, 64, "fp32"),
         (inputs.wire_16x100, 16, 100, 1.0, 0.05, 16, "fp64"),
         (inputs.wire_32x100, 32, 100, 1.0, 0.05, 8, "fp32"),
-        (inputs.wire_64x100, 64, 100, 0.5, 0.005, 8, "split_tf32"),
+        (inputs.wire_64x100, 64, 100, 0.5, 0.005, 8, "fp32"),
     ]
     for make, W, L, dis, eta, ne, prec in cases:
         a, b = make(), make()
