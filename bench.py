@@ -257,6 +257,20 @@ def fp32_peak():
     return 152 * 128 * 2 * mhz * 1e6 / 1e12, f"{src} ({mhz:.0f} MHz)"
 
 
+CKPT_STRIDE = 10          # the gradient's RGF blocks kept every this many slices
+
+
+def adjoint_flops(w):
+    """Flops of the block-column adjoint's block products for one task of wire w: per column
+    m, the chain of G[:, m] (L - 1 products), the elimination and back substitution (2 L - 1),
+    the lead-column products of the two boundary slices (2), and for the start lead's column
+    also G Phi and the injection seeds' products (2 L); 8 W^3 flops per W x W complex
+    product."""
+    W, L = w.W, w.L
+    prods = L * (3 * L - 2 + 2) + 2 * L
+    return 8.0 * W ** 3 * prods
+
+
 def cta_chain_flops(wl, precision):
     """FP32 flops of the CTA-wide block-column products per step: 8 W^3 per block-column step
     (one W x W complex block times a W x W block); W = 64 runs towards slice 0 only
@@ -621,9 +635,10 @@ def run_gpu(args):
 
 def run_gradient(args):
     """One step = the differentiable current of the workload's first wire through the public
-    torch API (autograd.NegfCurrent: tables keeping G, walks with score tallies, current) and
-    its backward (negf_current_backward: the gradient w.r.t. every onsite energy and every
-    dephasing rate).  The API is synchronous (the current and the gradient come back to the
+    torch API (autograd.NegfCurrent: tables keeping their weights, walks with score tallies,
+    current) and its backward (negf_current_backward_rgf: the block-column adjoint with the
+    RGF blocks checkpointed every CKPT_STRIDE slices; the gradient w.r.t. every onsite energy
+    and every dephasing rate).  The API is synchronous (the current and the gradient come back to the
     host), so the timed region is wall time on the device between the step's first launch and
     the gradient's arrival."""
     import torch
@@ -643,17 +658,18 @@ def run_gradient(args):
     onsite_h = torch.from_numpy(w.onsite).pin_memory()
     eta_h = torch.from_numpy(w.eta).pin_memory()
 
-    def spec_for(i):
+    def spec_for(i, adjoint="rgf"):
         return autograd.CurrentSpec(W=w.W, L=w.L, t=w.t, energy=w.energy,
                                     energy_weight=w.energy_weight, mu_p=wl.mu_p, mu_q=wl.mu_q,
                                     kT=wl.kT, start_lead=0, walkers_per_task=N, seed=args.seed,
                                     walker_id_offset=ndist.weak_walker_offset(rank, i, N),
-                                    max_steps=args.max_steps, precision=prec)
+                                    max_steps=args.max_steps, precision=prec, adjoint=adjoint,
+                                    ckpt_stride=CKPT_STRIDE)
 
-    def one_step(i, onsite, eta):
+    def one_step(i, onsite, eta, adjoint="rgf"):
         onsite = onsite.detach().requires_grad_(True)
         eta = eta.detach().requires_grad_(True)
-        I, se = autograd.NegfCurrent.apply(onsite, eta, ctx, spec_for(i))
+        I, se = autograd.NegfCurrent.apply(onsite, eta, ctx, spec_for(i, adjoint))
         I.backward()
         return float(I), float(se), onsite.grad, eta.grad
 
@@ -719,11 +735,33 @@ def run_gradient(args):
         gE.cpu()
         torch.cuda.synchronize()
         e2e_ms += (time.perf_counter() - t0) * 1e3
+    # context: the same step with the dense adjoint (n x n G kept per task), one-level wires only
+    dense_ms = None
+    if w.W * w.L <= 6400:
+        for i in range(2):
+            flush.fill_(float(i))
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one_step(40_000 + i, on_d, eta_d, adjoint="dense")
+            e1.record(stream)
+            e1.synchronize()
+            dense_ms = e0.elapsed_time(e1)
     negf.negf_destroy(ctx)
     if rank != 0:
         return
     I, se, gV, gE = res
     n_par = 2 * w.W * w.L
+    kname = "adjoint_column_kernel"
+    klaunch, kms = prof.get(kname, (0, 0.0))
+    fl = adjoint_flops(w) * len(w.energy)
+    per_launch = fl * args.steps / max(klaunch, 1)
+    ach = per_launch / (kms / 1e3 / max(klaunch, 1)) / 1e12 if klaunch else 0.0
+    if prec == "fp32":
+        peak, psrc = fp32_peak()
+    else:
+        peak, psrc = 1.25, "nominal FP64 rate of the part (no measured FP64 peak)"
     out = {
         "metric": METRIC, "value": steps_per_step * world / (t_max / args.steps / 1e3),
         "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -735,15 +773,23 @@ def run_gradient(args):
         "config": {"workload": wl.name + "_gradient", "walkers_per_task": N,
                    "tasks": len(w.energy), "precision": prec,
                    "parameters": n_par,
-                   "step": "forward (tables keeping G, walks with score tallies, current) + "
-                           "backward (gradient w.r.t. every onsite energy and dephasing rate) "
-                           "through autograd.NegfCurrent",
+                   "step": "forward (tables keeping their weights, walks with score tallies, "
+                           "current) + backward (block-column adjoint: gradient w.r.t. every "
+                           "onsite energy and dephasing rate) through autograd.NegfCurrent",
+                   "adjoint": "block-column RGF adjoint, no dense G",
+                   "ckpt_stride": CKPT_STRIDE,
                    "l2": "flushed between timed steps (258 MiB write, outside the timed events)",
                    "mode": "gradient"},
         "walker_steps_per_step": steps_per_step,
         "gradient": {"ms_per_gradient": t_max / args.steps, "parameters": n_par, "I": I,
                      "se": se, "dI_donsite_norm": float(gV.norm()),
-                     "dI_deta_norm": float(gE.norm())},
+                     "dI_deta_norm": float(gE.norm()),
+                     "dense_adjoint_ms_per_step": dense_ms},
+        "roofline": {"kernel": kname, "bound": "alu", "achieved": round(ach, 3),
+                     "peak": peak, "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                     "traffic": None, "peak_source": psrc,
+                     "algorithmic_flops_per_launch": per_launch,
+                     "avg_launch_ms": round(kms / max(klaunch, 1), 4)},
         "kernel_ms_per_step": {k: round(v[1] / args.steps, 4) for k, v in prof.items()},
         "e2e": {"value": steps_per_step / (e2e_ms / n_e2e / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": int(2 * w.onsite.nbytes),

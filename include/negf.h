@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define NEGF_ABI_VERSION 4
+#define NEGF_ABI_VERSION 5
 #define NEGF_MAX_W 64            /* widest supported slice (sites across the wire) */
 #define NEGF_MAX_SITES 6400      /* largest W*L per wire with one-level tables */
 #define NEGF_MAX_SITES_TWO_LEVEL 65536 /* largest W*L per wire with two-level tables */
@@ -102,7 +102,8 @@ typedef struct {
 typedef struct {
   int32_t precision;    /* negf_precision */
   int32_t memspace;     /* negf_memspace of every array in the wires */
-  int32_t keep_weights; /* nonzero: keep the FP transition weights for negf_export_tables */
+  int32_t keep_weights; /* nonzero: keep the FP transition weights (negf_export_tables) and
+                           the transverse modes, as negf_current_backward_rgf needs them */
   int32_t keep_green;   /* nonzero: also keep G (dense n x n per task), G Phi, the weights and
                            the transverse modes, as negf_current_backward needs them */
   int32_t table_layout; /* negf_table_layout */
@@ -138,7 +139,8 @@ typedef struct {
   int32_t table_layout;  /* NEGF_LAYOUT_ONE_LEVEL or NEGF_LAYOUT_TWO_LEVEL */
   double energy, energy_weight;
   double c[2];           /* Tr[Gamma_p A] for p = L (0) and R (1), Eq. elast_lin_xpq */
-  uint64_t table_offset; /* first entry of this task's rows x K block (tables, score tallies) */
+  uint64_t table_offset; /* first entry of this task's rows x K block (weights, score
+                            tallies; either layout) */
   uint64_t mode_offset;  /* first entry of this task's 2 x W block (mode tables / tallies) */
 } negf_task_info;
 
@@ -308,7 +310,8 @@ void negf_plan_destroy(negf_plan plan);
 /* --- gradient (paper silent) ---------------------------------------------------------------- */
 
 /* negf_walk that also records score tallies: every walk absorbed at lead r is replayed and
- * each transition a -> b adds 1 to counts[r][table_offset + a K + b] of its task, its injection
+ * each transition a -> b adds 1 to counts[r][table_offset + a K + b] of its task (b a site, or
+ * n + r' for lead r'; the same rows x K numbering for one- and two-level tables), its injection
  * mode m to mode_counts[r][mode_offset + p W + m] (offsets from negf_get_task_info).  Replaying
  * doubles the walk work.  The tables must still hold their alias rows (negf_build_tables). */
 negf_status negf_walk_score(negf_ctx ctx, negf_tables tables, int32_t start_lead, uint64_t seed,
@@ -338,6 +341,22 @@ uint32_t negf_tally_mode_size(negf_tally tally);
 negf_status negf_current_backward(negf_ctx ctx, negf_tables tables, negf_tally tally,
                                   double mu_p, double mu_q, double kT, const double* dI,
                                   double* d_onsite, double* d_eta);
+
+/* The same gradient (same arguments, outputs, seeds and errors as negf_current_backward)
+ * without any dense G: per block column m of slice m, G[:, m] from the RGF relations of
+ * Sec. III.B (G_{k,m} = -t g^L_k G_{k+1,m} below m, -t g^R_k G_{k-1,m} above), the matching
+ * column of the seed matrix, G times it by block-tridiagonal elimination with the
+ * left-connected blocks, and the diagonal of G Gbar G accumulated column by column (about
+ * 3 L^2 W^3 complex multiply-adds per task).  The left- and right-connected blocks are swept
+ * once and kept only at every ckpt_stride-th slice (0: NEGF_CKPT_STRIDE_DEFAULT); the blocks
+ * between are recomputed per segment before a task's columns run.  Requires tables built with
+ * keep_weights (FP64 or FP32, one- or two-level layout; split-TF32 tables keep no weights:
+ * NEGF_E_INVALID) and a tally from negf_walk_score on them.  ckpt_stride < 0: NEGF_E_INVALID.
+ * Device scratch: at most half the free device memory (16 GiB at most).  Synchronises. */
+#define NEGF_CKPT_STRIDE_DEFAULT 10
+negf_status negf_current_backward_rgf(negf_ctx ctx, negf_tables tables, negf_tally tally,
+                                      double mu_p, double mu_q, double kT, const double* dI,
+                                      int32_t ckpt_stride, double* d_onsite, double* d_eta);
 
 /* --- current (Eq. iqof_t_el_db, Eq. elast_lin_xpq, Sec. IV.B.2) --------------------------- */
 

@@ -1,9 +1,11 @@
 """torch.autograd.Function over the Monte Carlo current of one wire.
 
-Forward: negf_build_tables (keeping G when a gradient is wanted), negf_walk_score (negf_walk
-when not), negf_current.  Backward: negf_current_backward, the score-function gradient of the
-Monte Carlo current w.r.t. the onsite energies and the Buttiker dephasing of every site.  All
-arithmetic runs in libnegf's CUDA kernels; this module only marshals arguments.
+Forward: negf_build_tables (keeping the weights when a gradient is wanted, or the dense G for
+the dense adjoint), negf_walk_score (negf_walk when not), negf_current.  Backward:
+negf_current_backward_rgf (block-column adjoint, left- and right-connected blocks checkpointed
+every ckpt_stride slices) or negf_current_backward (dense G), the score-function gradient of
+the Monte Carlo current w.r.t. the onsite energies and the Buttiker dephasing of every site.
+All arithmetic runs in libnegf's CUDA kernels; this module only marshals arguments.
 
 The current follows Eq. iqof_t_el_db with the estimator of Eq. elast_lin_xpq:
 I = sum_E w_E (f(E; mu_p) - f(E; mu_q)) T_qp(E).
@@ -15,6 +17,7 @@ import torch
 from . import negf
 
 PRECISIONS = ("fp64", "fp32")
+ADJOINTS = ("rgf", "dense")
 
 
 @dataclass
@@ -36,6 +39,9 @@ class CurrentSpec:
     precision: str = "fp32"
     lead_model: int = 0
     gamma_lead: float = 0.0
+    adjoint: str = "rgf"           # "rgf": block-column adjoint; "dense": keeps the n x n G
+    ckpt_stride: int = 0           # rgf: keep g^L, g^R every this many slices (0: default 10)
+    layout: str = "auto"           # table layout (the dense adjoint needs one-level tables)
 
 
 @dataclass
@@ -87,6 +93,8 @@ class NegfCurrent(torch.autograd.Function):
     def forward(fctx, onsite, eta, ctx, spec):
         if spec.precision not in PRECISIONS:
             raise ValueError(f"precision must be one of {PRECISIONS}")
+        if spec.adjoint not in ADJOINTS:
+            raise ValueError(f"adjoint must be one of {ADJOINTS}")
         if not (onsite.is_cuda and eta.is_cuda):
             raise ValueError("onsite and eta must be CUDA tensors")
         if tuple(onsite.shape) != (spec.L, spec.W) or tuple(eta.shape) != (spec.L, spec.W):
@@ -97,8 +105,10 @@ class NegfCurrent(torch.autograd.Function):
                      _as_device(spec.energy, dev), _as_device(spec.energy_weight, dev),
                      spec.lead_model, spec.gamma_lead)
         grad = any(fctx.needs_input_grad[:2])
+        dense = spec.adjoint == "dense"
         tables = negf.negf_build_tables(ctx, [wire], precision=spec.precision, memspace="device",
-                                        keep_green=grad)
+                                        keep_weights=grad and not dense,
+                                        keep_green=grad and dense, layout=spec.layout)
         walk = negf.negf_walk_score if grad else negf.negf_walk
         try:
             tally = walk(ctx, tables, spec.start_lead, spec.seed, spec.walkers_per_task,
@@ -129,8 +139,13 @@ class NegfCurrent(torch.autograd.Function):
             raise RuntimeError("NegfCurrent.backward called twice (retain_graph is not supported)")
         dI = [float(gI.item())]
         try:
-            dV, dE, cap = negf.negf_current_backward(fctx.ctx, h.tables, h.tally, spec.mu_p,
-                                                     spec.mu_q, spec.kT, dI, spec.W * spec.L)
+            if spec.adjoint == "dense":
+                dV, dE, cap = negf.negf_current_backward(fctx.ctx, h.tables, h.tally, spec.mu_p,
+                                                         spec.mu_q, spec.kT, dI, spec.W * spec.L)
+            else:
+                dV, dE, cap = negf.negf_current_backward_rgf(fctx.ctx, h.tables, h.tally,
+                                                             spec.mu_p, spec.mu_q, spec.kT, dI,
+                                                             spec.W * spec.L, spec.ckpt_stride)
         finally:
             h.release()
         if cap:

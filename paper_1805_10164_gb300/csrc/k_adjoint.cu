@@ -1,0 +1,624 @@
+// Block-column adjoint of the transmission's gradient: no n x n array anywhere.
+//
+// The derivative target and the seeds are those of k_backward.cu (score-function seeds wbar of
+// every Step 6' weight, ubar of every injection-mode weight): with Gbar the Wirtinger seed of
+// every element of G = (E - H - Sigma)^{-1},
+//   dT/dV_k = 2 Re (G Gbar G)_kk,   dT/deta_k = Im (G Gbar G)_kk + the explicit gamma_k terms.
+// Here (G Gbar G)_kk is accumulated one block column m (the W sites of slice m) at a time:
+//   X = G[:, m]     G_mm by one inversion, then the RGF relations of Sec. III.B:
+//                   G_{k,m} = -t g^L_k G_{k+1,m} (k < m),  G_{k,m} = -t g^R_k G_{k-1,m} (k > m);
+//   U = Gbar[:, m]  each column of Gbar needs only the same column of G (site seeds, the lead
+//                   columns of the site rows), and, in the start lead's boundary slice s_p, the
+//                   injection rows' psi = G Phi_p = X Phi (column m = s_p alone);
+//   Z = G U         by block-tridiagonal elimination with the left-connected blocks
+//                   (g^L_{L-1} taken as G_{L-1,L-1}):
+//                     y_0 = g^L_0 U_0,  y_k = g^L_k (U_k - t y_{k-1}),
+//                     z_{L-1} = y_{L-1},  z_k = y_k - t g^L_k z_{k+1};
+//   (G Gbar G)_kk += sum_{j in slice m} Z[k, j] G[j, k] = sum_j Z[k, j] X[k, j]   (G = G^T).
+// A column costs about 3 L block products (W x W x W), a task 3 L^2 W^3 complex multiply-adds
+// (5 L for the column s_p), against the n^3 of the dense adjoint product; its memory is two
+// block columns per CTA in flight.
+//
+// Checkpoints (ckpt_stride s): adj_sweep_kernel runs both RGF sweeps of every task once and keeps
+// only every s-th block (left: g^L_k at k = 0, s, 2s, ...; right: g^R_k at k = L-1, L-1-s, ...).
+// Before a group of tasks runs its columns, adj_expand_kernel recomputes the blocks between
+// checkpoints, one CTA per segment of s slices (s serial inversions each, the segments in
+// parallel), into buffers that live only while that group's columns run.  The kept blocks take
+// 1/s of the memory of all tasks' sweeps; the recompute is one more inversion per block.
+//
+// Thread layout of the block products: 256 threads as 16 x 16; thread (ty, tx) owns rows
+// ty + 16 a and columns tx + 16 b (a, b < RT = ceil(W / 16)) of the W x W result, blocks row-major
+// with stride W in shared memory.  Every W x W block is in the precision of the tables
+// (complex64 or complex128); seeds and the accumulated gradient are FP64.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "gj.cuh"
+#include "negf_internal.cuh"
+
+namespace negf {
+namespace {
+
+constexpr int kAdjThreads = 256;
+
+__device__ __forceinline__ cd conj_(cd a) { return cd{a.x, -a.y}; }
+__device__ __forceinline__ cf conj_(cf a) { return cf{a.x, -a.y}; }
+__device__ __forceinline__ cd widen(cd a) { return a; }
+__device__ __forceinline__ cd widen(cf a) { return cd{(double)a.x, (double)a.y}; }
+
+// Lead self-energy Sigma_r = Phi diag(sigma) Phi^T, entry (a, b) (FP64; both leads alike)
+__device__ __forceinline__ cd lead_sigma(int a, int b, int W, const double* phi, const cd* sg) {
+  cd acc = mk(0.0, 0.0);
+  for (int m = 0; m < W; ++m) acc = acc + (phi[a * W + m] * phi[b * W + m]) * sg[m];
+  return acc;
+}
+
+// A <- E - H_kk - Sigma_s(k) - [lead terms] - t^2 P (P = the block in A, in place; P absent when
+// !with_prev): the slice matrix of the left (right) sweep at slice k.
+template <typename C>
+__device__ void form_slice(C* A, int k, int W, const TaskDesc& d, const double* onsite,
+                           const double* eta, const double* phi, const cd* sg, bool lead_l,
+                           bool lead_r, bool with_prev) {
+  using R = typename Real<C>::T;
+  const R tt = (R)(d.t * d.t);
+  for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
+    const int a = idx / W, b = idx - a * W;
+    C v = slice_entry<C>(a, b, k, W, d.E, d.t, onsite, eta);
+    if (lead_l || lead_r) {
+      const cd s = lead_sigma(a, b, W, phi, sg);
+      const int nl = (lead_l ? 1 : 0) + (lead_r ? 1 : 0);
+      v = v - to_c(mk((double)nl * s.x, (double)nl * s.y), C{});
+    }
+    if (with_prev) v = v - tt * A[idx];
+    A[idx] = v;
+  }
+}
+
+// every site of slice k dephases: inversion without a pivot search (see gj_rows)
+__device__ __forceinline__ bool slice_dephased(const double* eta, int k, int W) {
+  return __syncthreads_and(threadIdx.x >= W || eta[k * W + threadIdx.x] > 0.0);
+}
+
+// ---- checkpointed sweeps: one CTA per (task, direction) --------------------------------------
+// Left (dir 0): k = 0 .. L-1, the last block the full G_{L-1,L-1} (right lead included).
+// Right (dir 1): k = L-1 .. 1.  Kept: every s-th block of each direction, at ck + task's
+// offset + (index along the sweep / s) W^2.
+template <typename C>
+__global__ void __launch_bounds__(kAdjThreads) adj_sweep_kernel(
+    const TaskDesc* __restrict__ tasks, int n_tasks, const double* __restrict__ wire,
+    const double* __restrict__ phig, const cd* __restrict__ sig,
+    const uint64_t* __restrict__ ck_off, int s, C* __restrict__ ck, int32_t* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int job = blockIdx.x;
+  if (job >= 2 * n_tasks) return;
+  const int task = job >> 1, dir = job & 1;
+  const TaskDesc d = tasks[task];
+  const int W = d.W, L = d.L, WW = W * W;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* rowk = A + WW;
+  C* fcol = rowk + W;
+  int* perm = reinterpret_cast<int*>(fcol + W);
+  int* flag = perm + W;
+  const double* onsite = wire + d.onsite_off;
+  const double* eta = onsite + d.n;
+  const double* phi = phig + d.phi_off;
+  const cd* sg = sig + d.lead_off;
+  const int nck = (L + s - 1) / s;
+  C* out = ck + ck_off[task] + (uint64_t)dir * nck * WW;
+  const int steps = dir == 0 ? L : L - 1;
+  for (int i = 0; i < steps; ++i) {
+    const int k = dir == 0 ? i : L - 1 - i;
+    form_slice(A, k, W, d, onsite, eta, phi, sg, dir == 0 && k == 0, k == L - 1, i > 0);
+    __syncthreads();
+    const bool deph = slice_dephased(eta, k, W);
+    if (!cta_gj(A, rowk, fcol, perm, flag, W, !deph)) {
+      if (threadIdx.x == 0) atomicOr(err, ERR_SINGULAR);
+      return;
+    }
+    if (i % s == 0) {
+      C* dst = out + (uint64_t)(i / s) * WW;
+      for (int idx = threadIdx.x; idx < WW; idx += blockDim.x) dst[idx] = A[idx];
+    }
+    __syncthreads();
+  }
+}
+
+// ---- recompute between checkpoints: one CTA per (task of the group, direction, segment) -----
+// gl[k] (k = 0 .. L-1) and gr[k] (k = 1 .. L-1) of each task of the group, W^2 each.
+template <typename C>
+__global__ void __launch_bounds__(kAdjThreads) adj_expand_kernel(
+    const TaskDesc* __restrict__ tasks, int task0, int n_group, const double* __restrict__ wire,
+    const double* __restrict__ phig, const cd* __restrict__ sig,
+    const uint64_t* __restrict__ ck_off, int s, const C* __restrict__ ck, C* __restrict__ gl,
+    C* __restrict__ gr, int32_t* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const TaskDesc d0 = tasks[task0];
+  const int L = d0.L, W = d0.W, WW = W * W;
+  const int nck = (L + s - 1) / s;
+  const int job = blockIdx.x;
+  if (job >= n_group * 2 * nck) return;
+  const int tl = job / (2 * nck), rem = job - tl * 2 * nck, dir = rem / nck, c = rem - dir * nck;
+  const int task = task0 + tl;
+  const TaskDesc d = tasks[task];
+  const int steps = dir == 0 ? L : L - 1;
+  const int i0 = c * s;
+  if (i0 >= steps) return;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* rowk = A + WW;
+  C* fcol = rowk + W;
+  int* perm = reinterpret_cast<int*>(fcol + W);
+  int* flag = perm + W;
+  const double* onsite = wire + d.onsite_off;
+  const double* eta = onsite + d.n;
+  const double* phi = phig + d.phi_off;
+  const cd* sg = sig + d.lead_off;
+  const C* src = ck + ck_off[task] + ((uint64_t)dir * nck + c) * WW;
+  C* out = (dir == 0 ? gl : gr) + (uint64_t)tl * L * WW;
+  for (int idx = threadIdx.x; idx < WW; idx += blockDim.x) A[idx] = src[idx];
+  const int i_end = min(i0 + s, steps);
+  for (int i = i0;; ++i) {
+    const int k = dir == 0 ? i : L - 1 - i;
+    __syncthreads();
+    C* dst = out + (uint64_t)k * WW;
+    for (int idx = threadIdx.x; idx < WW; idx += blockDim.x) dst[idx] = A[idx];
+    if (i + 1 >= i_end) break;
+    const int kn = dir == 0 ? k + 1 : k - 1;
+    __syncthreads();
+    form_slice(A, kn, W, d, onsite, eta, phi, sg, false, kn == L - 1 && dir == 0, true);
+    __syncthreads();
+    const bool deph = slice_dephased(eta, kn, W);
+    if (!cta_gj(A, rowk, fcol, perm, flag, W, !deph)) {
+      if (threadIdx.x == 0) atomicOr(err, ERR_SINGULAR);
+      return;
+    }
+  }
+}
+
+// ---- block products ------------------------------------------------------------------------
+template <typename C, int RT>
+__device__ __forceinline__ void cta_prod(const C* __restrict__ A, const C* __restrict__ B, int W,
+                                         C (&acc)[RT][RT]) {
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+  for (int a = 0; a < RT; ++a)
+#pragma unroll
+    for (int b = 0; b < RT; ++b) acc[a][b] = mkc(0.0, 0.0, C{});
+  int ra[RT], cb[RT];
+#pragma unroll
+  for (int a = 0; a < RT; ++a) {
+    const int r = ty + 16 * a, c = tx + 16 * a;
+    ra[a] = (r < W ? r : W - 1) * W;                // clamped: rows/columns >= W are discarded
+    cb[a] = c < W ? c : W - 1;
+  }
+  for (int l = 0; l < W; ++l) {
+    C av[RT], bv[RT];
+#pragma unroll
+    for (int a = 0; a < RT; ++a) av[a] = A[ra[a] + l];
+#pragma unroll
+    for (int b = 0; b < RT; ++b) bv[b] = B[l * W + cb[b]];
+#pragma unroll
+    for (int a = 0; a < RT; ++a)
+#pragma unroll
+      for (int b = 0; b < RT; ++b) {
+        acc[a][b].x += av[a].x * bv[b].x - av[a].y * bv[b].y;
+        acc[a][b].y += av[a].x * bv[b].y + av[a].y * bv[b].x;
+      }
+  }
+}
+
+// visit this thread's valid entries (i, j) of a W x W product tile
+template <int RT, typename F>
+__device__ __forceinline__ void for_tile(int W, F f) {
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+#pragma unroll
+  for (int a = 0; a < RT; ++a)
+#pragma unroll
+    for (int b = 0; b < RT; ++b) {
+      const int i = ty + 16 * a, j = tx + 16 * b;
+      if (i < W && j < W) f(a, b, i, j);
+    }
+}
+
+template <typename C>
+__device__ __forceinline__ void load_block(C* dst, const C* __restrict__ src, int WW) {
+  for (int idx = threadIdx.x; idx < WW; idx += blockDim.x) dst[idx] = src[idx];
+}
+
+struct AdjArgs {
+  const TaskDesc* tasks;
+  int task0, n_group, p;
+  const double* wire;
+  const double* phi;
+  const cd* sig;
+  const double* gam;
+  const double* wbar;        // [rows x K] per task at wt_off
+  const double* ubar;        // per task at mode_off
+  uint64_t site_off0;        // dT of the group's first task (sites of earlier tasks before it)
+  double* dV;
+  double* dE;
+  int32_t* err;
+};
+
+// One job per (task of the group, block column m); the start lead's boundary columns first
+// (they carry the injection work).  Scratch: X and Y (L W^2 each) per CTA; gl, gr, Psi
+// (L W^2) and Tl (2 W^2) per task of the group.
+template <typename C, int RT>
+__global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, const C* __restrict__ gl_all,
+                                                                 const C* __restrict__ gr_all,
+                                                                 C* __restrict__ psi_all,
+                                                                 C* __restrict__ tl_all,
+                                                                 C* __restrict__ xs_all,
+                                                                 C* __restrict__ ys_all) {
+  using R = typename Real<C>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const TaskDesc d0 = g.tasks[g.task0];
+  const int W = d0.W, L = d0.L, WW = W * W, n = d0.n, K = d0.K;
+  C* sA = reinterpret_cast<C*>(smem_raw);
+  C* sB = sA + WW;
+  C* sT = sB + WW;
+  C* rowk = sT + WW;
+  C* fcol = rowk + W;
+  int* perm = reinterpret_cast<int*>(fcol + W);
+  int* flag = perm + W;
+  const int p = g.p;
+  const int sp = p == 0 ? 0 : L - 1;
+  const R t = (R)d0.t;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  C* X = xs_all + (uint64_t)blockIdx.x * L * WW;
+  C* Y = ys_all + (uint64_t)blockIdx.x * L * WW;
+  const int n_jobs = g.n_group * L;
+  for (int job = blockIdx.x; job < n_jobs; job += gridDim.x) {
+    const int tl = job % g.n_group, mm = job / g.n_group;
+    const int m = p == 0 ? mm : L - 1 - mm;
+    const bool inj = m == sp;                         // the start lead's boundary column
+    const TaskDesc d = g.tasks[g.task0 + tl];
+    const double* onsite = g.wire + d.onsite_off;
+    const double* eta = onsite + n;
+    const double* phi = g.phi + d.phi_off;
+    const cd* sg = g.sig + d.lead_off;
+    const double* gam = g.gam + d.lead_off;
+    const double* wb = g.wbar + d.wt_off;
+    const double* ub = g.ubar + d.mode_off + p * W;
+    const C* gl = gl_all + (uint64_t)tl * L * WW;
+    const C* gr = gr_all + (uint64_t)tl * L * WW;
+    C* Psi = psi_all + (uint64_t)tl * L * WW;
+    C* Tl = tl_all + (uint64_t)tl * 2 * WW;
+    const uint64_t so = g.site_off0 + (uint64_t)tl * n;
+    C acc[RT][RT];
+
+    // ---- G_mm = (E - H_mm - Sigma_s - [leads] - t^2 g^L_{m-1} - t^2 g^R_{m+1})^{-1}
+    __syncthreads();
+    {
+      const R tt = t * t;
+      for (int idx = tid; idx < WW; idx += blockDim.x) {
+        const int a = idx / W, b = idx - a * W;
+        C v = slice_entry<C>(a, b, m, W, d.E, d.t, onsite, eta);
+        const int nl = (m == 0 ? 1 : 0) + (m == L - 1 ? 1 : 0);
+        if (nl) {
+          const cd s = lead_sigma(a, b, W, phi, sg);
+          v = v - to_c(mk(nl * s.x, nl * s.y), C{});
+        }
+        if (m > 0) v = v - tt * gl[(uint64_t)(m - 1) * WW + idx];
+        if (m < L - 1) v = v - tt * gr[(uint64_t)(m + 1) * WW + idx];
+        sA[idx] = v;
+      }
+    }
+    __syncthreads();
+    const bool deph = slice_dephased(eta, m, W);
+    if (!cta_gj(sA, rowk, fcol, perm, flag, W, !deph)) {
+      if (tid == 0) atomicOr(g.err, ERR_SINGULAR);
+      return;
+    }
+    for (int idx = tid; idx < WW; idx += blockDim.x) {
+      sB[idx] = sA[idx];
+      X[(uint64_t)m * WW + idx] = sA[idx];
+    }
+    // ---- the block column X_k = G_{k,m}: toward slice 0, then toward slice L-1
+    for (int k = m - 1; k >= 0; --k) {
+      __syncthreads();
+      load_block(sA, gl + (uint64_t)k * WW, WW);
+      __syncthreads();
+      cta_prod<C, RT>(sA, sB, W, acc);
+      __syncthreads();
+      for_tile<RT>(W, [&](int a, int b, int i, int j) {
+        const C v = (R)(-1) * t * acc[a][b];
+        sB[i * W + j] = v;
+        X[(uint64_t)k * WW + i * W + j] = v;
+      });
+    }
+    if (m < L - 1) {
+      __syncthreads();
+      load_block(sB, X + (uint64_t)m * WW, WW);
+      for (int k = m + 1; k < L; ++k) {
+        __syncthreads();
+        load_block(sA, gr + (uint64_t)k * WW, WW);
+        __syncthreads();
+        cta_prod<C, RT>(sA, sB, W, acc);
+        __syncthreads();
+        for_tile<RT>(W, [&](int a, int b, int i, int j) {
+          const C v = (R)(-1) * t * acc[a][b];
+          sB[i * W + j] = v;
+          X[(uint64_t)k * WW + i * W + j] = v;
+        });
+      }
+    }
+    // ---- column s_p: psi = X Phi (the injection rows' G Phi_p), the lead-column terms Tl_r of
+    // the injection rows, and their contribution Cc_k = psibar_k Phi^T to U (kept in Y)
+    if (inj) {
+      __syncthreads();
+      for (int idx = tid; idx < WW; idx += blockDim.x) {
+        const int a = idx / W, b = idx - a * W;
+        sT[idx] = mkc(phi[idx], 0.0, C{});                         // Phi [x][m']
+        sB[idx] = mkc(phi[b * W + a], 0.0, C{});                   // Phi^T [m'][y]
+      }
+      for (int k = 0; k < L; ++k) {
+        __syncthreads();
+        load_block(sA, X + (uint64_t)k * WW, WW);
+        __syncthreads();
+        cta_prod<C, RT>(sA, sT, W, acc);
+        for_tile<RT>(W, [&](int a, int b, int i, int j) { Psi[(uint64_t)k * WW + i * W + j] = acc[a][b]; });
+      }
+      // Tl_r[x][m'] = sum_nu Gamma_nu phi_nu(x) conj(z_nu^(m')), z = Phi^T psi_{s_r}
+      for (int r = 0; r < 2; ++r) {
+        const int sr = r == 0 ? 0 : L - 1;
+        __syncthreads();
+        for (int idx = tid; idx < WW; idx += blockDim.x) {
+          const int nu = idx / W, mp = idx - nu * W;
+          cd z = mk(0.0, 0.0);
+          for (int x = 0; x < W; ++x)
+            z = z + phi[x * W + nu] * widen(Psi[(uint64_t)sr * WW + x * W + mp]);
+          sA[idx] = to_c(z, C{});
+        }
+        __syncthreads();
+        for (int idx = tid; idx < WW; idx += blockDim.x) {
+          const int x = idx / W, mp = idx - x * W;
+          double tx = 0.0, ty = 0.0;
+          for (int nu = 0; nu < W; ++nu) {
+            const double f = gam[nu] * phi[x * W + nu];
+            const cd z = widen(sA[nu * W + mp]);
+            tx += f * z.x;
+            ty -= f * z.y;
+          }
+          Tl[(uint64_t)r * WW + idx] = to_c(mk(tx, ty), C{});
+        }
+      }
+      __syncthreads();
+      for (int k = 0; k < L; ++k) {
+        __syncthreads();
+        for (int idx = tid; idx < WW; idx += blockDim.x) {
+          const int mp = idx / W, i = idx - mp * W;              // psibar_k [i][m']
+          const double* wrow = wb + (uint64_t)(n + p * W + mp) * K;
+          const int b = k * W + i;
+          const cd ps = widen(Psi[(uint64_t)k * WW + i * W + mp]);
+          const double f = wrow[b] * eta[b];
+          double vx = f * ps.x, vy = -f * ps.y;
+          for (int r = 0; r < 2; ++r) {
+            const int sr = r == 0 ? 0 : L - 1;
+            if (k != sr) continue;
+            const double wl = wrow[n + r];
+            if (wl == 0.0) continue;
+            const cd tv = widen(Tl[(uint64_t)r * WW + i * W + mp]);
+            vx += wl * tv.x;
+            vy += wl * tv.y;
+          }
+          sA[i * W + mp] = to_c(mk(vx, vy), C{});
+        }
+        __syncthreads();
+        cta_prod<C, RT>(sA, sB, W, acc);
+        for_tile<RT>(W, [&](int a, int b, int i, int j) { Y[(uint64_t)k * WW + i * W + j] = acc[a][b]; });
+      }
+      // the lead broadening of the boundary slices, Gamma_lead = Phi diag(Gamma) Phi^T (real)
+    }
+    __syncthreads();
+    for (int idx = tid; idx < WW; idx += blockDim.x) {
+      const int a = idx / W, b = idx - a * W;
+      double v = 0.0;
+      for (int nu = 0; nu < W; ++nu) v += gam[nu] * phi[a * W + nu] * phi[b * W + nu];
+      sT[idx] = mkc(v, 0.0, C{});
+    }
+    // ---- forward elimination: y_k = g^L_k (U_k - t y_{k-1}), U_k = Gbar[k-block, m-block]
+    for (int k = 0; k < L; ++k) {
+      const bool edge = k == 0 || k == L - 1;
+      __syncthreads();
+      if (edge) {
+        // lead columns of the site rows: U[x][j] += (sum_r wbar_{(m,j), n+r}) conj(Gamma_lead X_k)[x][j]
+        load_block(sA, X + (uint64_t)k * WW, WW);
+        __syncthreads();
+        cta_prod<C, RT>(sT, sA, W, acc);
+        __syncthreads();
+        for_tile<RT>(W, [&](int a, int b, int i, int j) { sA[i * W + j] = conj_(acc[a][b]); });
+        __syncthreads();
+      }
+      for (int idx = tid; idx < WW; idx += blockDim.x) {
+        const int j = idx / W, i = idx - j * W;               // U_k [i][j]: row (k, i), column (m, j)
+        const double* wrow = wb + (uint64_t)(m * W + j) * K;
+        const int b = k * W + i;
+        const cd xv = widen(X[(uint64_t)k * WW + i * W + j]);
+        const double f = wrow[b] * eta[b];
+        double ux = f * xv.x, uy = -f * xv.y;
+        if (edge) {
+          double wl = 0.0;
+          if (k == 0) wl += wrow[n];
+          if (k == L - 1) wl += wrow[n + 1];
+          if (wl != 0.0) {
+            const cd tb = widen(sA[i * W + j]);
+            ux += wl * tb.x;
+            uy += wl * tb.y;
+          }
+        }
+        if (inj) {
+          const cd cc = widen(Y[(uint64_t)k * WW + i * W + j]);
+          ux += cc.x;
+          uy += cc.y;
+          if (k == sp) {
+            // mode weights u_m' = lambda_m' <phi_m'|A|phi_m'>: i sum ubar Gamma phi phi
+            double v = 0.0;
+            for (int mp = 0; mp < W; ++mp) v += ub[mp] * gam[mp] * phi[i * W + mp] * phi[j * W + mp];
+            uy += v;
+          }
+        }
+        C u = to_c(mk(ux, uy), C{});
+        if (k > 0) u = u - t * sB[i * W + j];
+        sB[i * W + j] = u;
+      }
+      __syncthreads();
+      load_block(sA, gl + (uint64_t)k * WW, WW);
+      __syncthreads();
+      cta_prod<C, RT>(sA, sB, W, acc);
+      __syncthreads();
+      for_tile<RT>(W, [&](int a, int b, int i, int j) {
+        sB[i * W + j] = acc[a][b];
+        Y[(uint64_t)k * WW + i * W + j] = acc[a][b];
+      });
+    }
+    // ---- back substitution z_k = y_k - t g^L_k z_{k+1}, and the diagonal of G Gbar G
+    for (int k = L - 1; k >= 0; --k) {
+      if (k < L - 1) {
+        __syncthreads();
+        load_block(sA, gl + (uint64_t)k * WW, WW);
+        __syncthreads();
+        cta_prod<C, RT>(sA, sB, W, acc);
+        __syncthreads();
+        for_tile<RT>(W, [&](int a, int b, int i, int j) {
+          sB[i * W + j] = Y[(uint64_t)k * WW + i * W + j] - t * acc[a][b];
+        });
+      }
+      __syncthreads();
+      // site (k, a): warp per row; sum_j z[a][j] X[a][j] and the explicit gamma terms
+      for (int a = warp; a < W; a += kAdjThreads / 32) {
+        const int site = k * W + a;
+        double zx = 0.0, zy = 0.0, ex = 0.0;
+        for (int j = lane; j < W; j += 32) {
+          const cd z = widen(sB[a * W + j]);
+          const cd x = widen(X[(uint64_t)k * WW + a * W + j]);
+          zx += z.x * x.x - z.y * x.y;
+          zy += z.x * x.y + z.y * x.x;
+          ex += wb[(uint64_t)(m * W + j) * K + site] * (x.x * x.x + x.y * x.y);
+          if (inj) {
+            const cd ps = widen(Psi[(uint64_t)k * WW + a * W + j]);
+            ex += wb[(uint64_t)(n + p * W + j) * K + site] * (ps.x * ps.x + ps.y * ps.y);
+          }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          zx += __shfl_down_sync(0xffffffffu, zx, o);
+          zy += __shfl_down_sync(0xffffffffu, zy, o);
+          ex += __shfl_down_sync(0xffffffffu, ex, o);
+        }
+        if (lane == 0) {
+          atomicAdd(g.dV + so + site, 2.0 * zx);
+          atomicAdd(g.dE + so + site, zy + ex);
+        }
+      }
+    }
+  }
+}
+
+template <typename C>
+size_t gj_smem(int W) {
+  return sizeof(C) * (size_t)(W * W + 2 * W) + sizeof(int) * (size_t)(W + 2);
+}
+template <typename C>
+size_t column_smem(int W) {
+  return sizeof(C) * (size_t)(3 * W * W + 2 * W) + sizeof(int) * (size_t)(W + 2);
+}
+
+template <typename C, int RT>
+cudaError_t columns_rt(const AdjArgs& a, int W, const C* gl, const C* gr, C* psi, C* tl, C* xs,
+                       C* ys, int slots, cudaStream_t s) {
+  const size_t smem = column_smem<C>(W);
+  cudaError_t e = cudaFuncSetAttribute(adj_column_kernel<C, RT>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  adj_column_kernel<C, RT><<<slots, kAdjThreads, smem, s>>>(a, gl, gr, psi, tl, xs, ys);
+  return cudaGetLastError();
+}
+
+template <typename C>
+cudaError_t columns_impl(const AdjArgs& a, int W, const void* gl, const void* gr, void* psi,
+                         void* tl, void* xs, void* ys, int slots, cudaStream_t s) {
+  const C* cgl = static_cast<const C*>(gl);
+  const C* cgr = static_cast<const C*>(gr);
+  C* cpsi = static_cast<C*>(psi);
+  C* ctl = static_cast<C*>(tl);
+  C* cxs = static_cast<C*>(xs);
+  C* cys = static_cast<C*>(ys);
+  switch ((W + 15) / 16) {
+    case 1: return columns_rt<C, 1>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
+    case 2: return columns_rt<C, 2>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
+    case 3: return columns_rt<C, 3>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
+    default: return columns_rt<C, 4>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
+  }
+}
+
+}  // namespace
+
+size_t adjoint_column_smem(int W, int precision) {
+  return precision == NEGF_FP64 ? column_smem<cd>(W) : column_smem<cf>(W);
+}
+
+cudaError_t launch_adjoint_sweep(const TaskDesc* d_tasks, int n_tasks, int max_W, int precision,
+                                 const double* d_wire, const double* d_phi, const cd* d_sig,
+                                 const uint64_t* d_ck_off, int stride, void* d_ck,
+                                 int32_t* d_err, cudaStream_t s) {
+  if (n_tasks == 0) return cudaSuccess;
+  if (precision == NEGF_FP64) {
+    const size_t smem = gj_smem<cd>(max_W);
+    cudaError_t e = cudaFuncSetAttribute(adj_sweep_kernel<cd>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    adj_sweep_kernel<cd><<<2 * n_tasks, kAdjThreads, smem, s>>>(
+        d_tasks, n_tasks, d_wire, d_phi, d_sig, d_ck_off, stride, static_cast<cd*>(d_ck), d_err);
+  } else {
+    const size_t smem = gj_smem<cf>(max_W);
+    cudaError_t e = cudaFuncSetAttribute(adj_sweep_kernel<cf>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    adj_sweep_kernel<cf><<<2 * n_tasks, kAdjThreads, smem, s>>>(
+        d_tasks, n_tasks, d_wire, d_phi, d_sig, d_ck_off, stride, static_cast<cf*>(d_ck), d_err);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_expand(const TaskDesc* d_tasks, int task0, int n_group, int W, int L,
+                                  int precision, const double* d_wire, const double* d_phi,
+                                  const cd* d_sig, const uint64_t* d_ck_off, int stride,
+                                  const void* d_ck, void* d_gl, void* d_gr, int32_t* d_err,
+                                  cudaStream_t s) {
+  if (n_group == 0) return cudaSuccess;
+  const int nck = (L + stride - 1) / stride;
+  const unsigned blocks = (unsigned)(n_group * 2 * nck);
+  cudaError_t e = precision == NEGF_FP64
+                      ? cudaFuncSetAttribute(adj_expand_kernel<cd>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)gj_smem<cd>(W))
+                      : cudaFuncSetAttribute(adj_expand_kernel<cf>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)gj_smem<cf>(W));
+  if (e != cudaSuccess) return e;
+  if (precision == NEGF_FP64)
+    adj_expand_kernel<cd><<<blocks, kAdjThreads, gj_smem<cd>(W), s>>>(
+        d_tasks, task0, n_group, d_wire, d_phi, d_sig, d_ck_off, stride,
+        static_cast<const cd*>(d_ck), static_cast<cd*>(d_gl), static_cast<cd*>(d_gr), d_err);
+  else
+    adj_expand_kernel<cf><<<blocks, kAdjThreads, gj_smem<cf>(W), s>>>(
+        d_tasks, task0, n_group, d_wire, d_phi, d_sig, d_ck_off, stride,
+        static_cast<const cf*>(d_ck), static_cast<cf*>(d_gl), static_cast<cf*>(d_gr), d_err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_columns(const TaskDesc* d_tasks, int task0, int n_group, int W,
+                                   int precision, int start_lead, const double* d_wire,
+                                   const double* d_phi, const cd* d_sig, const double* d_gam,
+                                   const double* d_wbar, const double* d_ubar, uint64_t site_off0,
+                                   double* d_dV, double* d_dE, const void* d_gl, const void* d_gr,
+                                   void* d_psi, void* d_tl, void* d_xs, void* d_ys, int slots,
+                                   int32_t* d_err, cudaStream_t s) {
+  if (n_group == 0 || slots == 0) return cudaSuccess;
+  AdjArgs a{d_tasks, task0, n_group, start_lead, d_wire, d_phi, d_sig, d_gam, d_wbar, d_ubar,
+            site_off0, d_dV, d_dE, d_err};
+  if (precision == NEGF_FP64)
+    return columns_impl<cd>(a, W, d_gl, d_gr, d_psi, d_tl, d_xs, d_ys, slots, s);
+  return columns_impl<cf>(a, W, d_gl, d_gr, d_psi, d_tl, d_xs, d_ys, slots, s);
+}
+
+}  // namespace negf

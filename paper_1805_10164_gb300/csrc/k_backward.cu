@@ -59,7 +59,7 @@ __global__ void seeds_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
   const int row = (int)(job - d.row_base);
   if (row < d.rows) {
     const int K = d.K;
-    const uint64_t off = d.tab_off + (uint64_t)row * K;
+    const uint64_t off = d.wt_off + (uint64_t)row * K;
     const unsigned long long* C0 = score + off;
     const unsigned long long* C1 = score + stride + off;
     const unsigned long long* Cq = q == 0 ? C0 : C1;
@@ -79,15 +79,16 @@ __global__ void seeds_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
       if (wv > 0.0) v = s / wv;
       wbar[off + b] = c * (v - Srs);
     }
-  } else if (row == d.rows && lane < d.W) {
-    // injection modes of the start lead p
-    const int m = lane;
-    const uint32_t mo = d.mode_off + p * d.W + m;
-    const double u = mode_w[mo];
-    const double C0 = (double)mode_score[mo], C1 = (double)mode_score[mode_stride + mo];
-    const double Cq = q == 0 ? C0 : C1;
-    const double s = N > 0.0 ? (Cq - Ph * (C0 + C1)) / N : 0.0;
-    ubar[d.mode_off + p * d.W + m] = Ph + (u > 0.0 ? c * s / u : 0.0);
+  } else if (row == d.rows) {
+    // injection modes of the start lead p (W up to 64: two per lane)
+    for (int m = lane; m < d.W; m += 32) {
+      const uint32_t mo = d.mode_off + p * d.W + m;
+      const double u = mode_w[mo];
+      const double C0 = (double)mode_score[mo], C1 = (double)mode_score[mode_stride + mo];
+      const double Cq = q == 0 ? C0 : C1;
+      const double s = N > 0.0 ? (Cq - Ph * (C0 + C1)) / N : 0.0;
+      ubar[d.mode_off + p * d.W + m] = Ph + (u > 0.0 ? c * s / u : 0.0);
+    }
   }
 }
 
@@ -103,7 +104,7 @@ __global__ void gbar_sites_kernel(TaskDesc d, const C* __restrict__ G,
   for (uint64_t idx = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (uint64_t)gridDim.x * blockDim.x) {
     const int b = (int)(idx / n), a = (int)(idx % n);      // element (b, a)
-    const R s = (R)(wbar[d.tab_off + (uint64_t)a * K + b] * eta[b]);
+    const R s = (R)(wbar[d.wt_off + (uint64_t)a * K + b] * eta[b]);
     const C g = conjc(G[idx]);
     Gbar[idx] = C{s * g.x, s * g.y};
   }
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(256) gbar_leads_kernel(TaskDesc d, const C* __
   const int t = threadIdx.x, al = t / W, q = t - al * W;
   const int a = blockIdx.x * per + al;
   const bool live = al < per && a < n;
-  const double wb = live ? wbar[d.tab_off + (uint64_t)a * K + n + r] : 0.0;
+  const double wb = live ? wbar[d.wt_off + (uint64_t)a * K + n + r] : 0.0;
   if (wb != 0.0) {
     double yx = 0.0, yy = 0.0;
     for (int xx = 0; xx < W; ++xx) {
@@ -208,7 +209,7 @@ __global__ void gbar_inj_kernel(TaskDesc d, const C* __restrict__ gphi,
     const int sb = b / W, xb = b % W;                         // slice and row of site b
     double ax = 0.0, ay = 0.0;
     for (int m = 0; m < W; ++m) {
-      const uint64_t roff = d.tab_off + (uint64_t)(n + p * W + m) * K;
+      const uint64_t roff = d.wt_off + (uint64_t)(n + p * W + m) * K;
       const C ps = gphi[(uint64_t)b * 2 * W + p * W + m];
       double bx = wbar[roff + b] * eta[b] * (double)ps.x;     // psibar_b = wbar gamma conj(psi)
       double by = -wbar[roff + b] * eta[b] * (double)ps.y;
@@ -327,11 +328,11 @@ __global__ void grad_diag_kernel(TaskDesc d, const C* __restrict__ G, const C* _
     const C y = Y[(uint64_t)i * n + k];
     zx += (double)g.x * y.x - (double)g.y * y.y;
     zy += (double)g.x * y.y + (double)g.y * y.x;
-    ex += wbar[d.tab_off + (uint64_t)i * K + k] * ((double)g.x * g.x + (double)g.y * g.y);
+    ex += wbar[d.wt_off + (uint64_t)i * K + k] * ((double)g.x * g.x + (double)g.y * g.y);
   }
   for (int j = lane; j < 2 * W; j += 32) {
     const C ps = gphi[(uint64_t)k * 2 * W + j];
-    ex += wbar[d.tab_off + (uint64_t)(n + j) * K + k] * ((double)ps.x * ps.x + (double)ps.y * ps.y);
+    ex += wbar[d.wt_off + (uint64_t)(n + j) * K + k] * ((double)ps.x * ps.x + (double)ps.y * ps.y);
   }
   for (int o = 16; o > 0; o >>= 1) {
     zx += __shfl_down_sync(0xffffffffu, zx, o);

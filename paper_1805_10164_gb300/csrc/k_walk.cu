@@ -54,11 +54,37 @@ __device__ __forceinline__ void flush_lane(unsigned* s_tally, int task_local, un
 // (and the injection mode to mode_score[r][m]); these are the counts the score-function
 // gradient needs.
 struct ScoreOut {
-  unsigned long long* cnt;        // [2][stride] at each task's tab_off (rows x K)
+  unsigned long long* cnt;        // [2][stride] at each task's wt_off (rows x K, either layout)
   unsigned long long* mode_cnt;   // [2][mode_stride] at each task's mode_off (2 x W)
   unsigned long long stride;
   unsigned mode_stride;
 };
+
+// One Step 6' transition from table row `row` of a two-level task: words (x, y) draw the slice
+// or lead on the level-1 alias row, v = z >> 1 the site within a drawn slice (level 2: against
+// the guide, then against the octet it points to).  Returns the next row: a site k W + a, or
+// n + r for lead r.
+__device__ __forceinline__ uint32_t two_level_draw(const uint64_t* __restrict__ l1row,
+                                                   const uint64_t* __restrict__ trow, uint32_t row,
+                                                   uint32_t L, uint32_t W, uint32_t B2, uint4 r) {
+  const uint32_t K1 = L + 2;
+  const uint32_t c = __umulhi(r.x, K1);
+  const uint64_t e = __ldg(l1row + (uint64_t)row * K1 + c);
+  const uint32_t k = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+  if (k >= L) return W * L + (k - L);
+  const uint32_t v = r.z >> 1;
+  const uint4* blk = reinterpret_cast<const uint4*>(trow) + (((uint64_t)row * L + k) * B2 >> 2);
+  uint32_t g = 0;
+  if (W > 8) {
+    const uint4 q0 = __ldg(blk), q1 = __ldg(blk + 1);
+    g = (q0.x <= v) + (q0.y <= v) + (q0.z <= v) + (q0.w <= v) + (q1.x <= v) + (q1.y <= v) +
+        (q1.z <= v) + (q1.w <= v);
+    blk += 2 + 2 * g;
+  }
+  const uint4 o0 = __ldg(blk), o1 = __ldg(blk + 1);
+  return k * W + 8 * g + (o0.x <= v) + (o0.y <= v) + (o0.z <= v) + (o0.w <= v) + (o1.x <= v) +
+         (o1.y <= v) + (o1.z <= v) + (o1.w <= v);
+}
 
 // kTwo: the launch may hold two-level tasks (one-level launches compile without that path).
 template <bool kTrace, bool kScore, int kSlotsReq, bool kTwo>
@@ -104,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
   unsigned long long t_first = 0;
   uint32_t task_id = 0, K = 0, n = 0, W = 0, inj_row0 = 0, L = 0, B2 = 0;
   bool two = false;                  // two-level tables (level 1 at l1row, level 2 at trow)
-  uint64_t t_tab_off = 0;
+  uint64_t t_wt_off = 0;
   uint32_t t_mode_off = 0;
   bool t_open = false;
   const uint64_t* trow = nullptr;
@@ -135,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
           n = (uint32_t)d.n;
           W = (uint32_t)d.W;
           inj_row0 = (uint32_t)(d.n + start_lead * d.W);
-          t_tab_off = d.tab_off;
+          t_wt_off = d.wt_off;
           t_mode_off = d.mode_off + start_lead * d.W;
           trow = tab + d.tab_off;
           two = kTwo && d.layout == NEGF_LAYOUT_TWO_LEVEL;
@@ -204,30 +230,11 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
           const uint64_t e = __ldg(mrow + c);
           row[sl] = inj_row0 + (r.y < (uint32_t)e ? c : (uint32_t)(e >> 32));
         } else {
-          const uint32_t K1 = L + 2;
-          const uint32_t c = __umulhi(r.x, K1);
-          const uint64_t e = __ldg(l1row + (uint64_t)row[sl] * K1 + c);
-          const uint32_t k = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+          const uint32_t j = two_level_draw(l1row, trow, row[sl], L, W, B2, r);
           ++steps[sl];
-          if (k >= L) {
-            outcome = (int)(k - L);
-          } else {
-            const uint32_t v = r.z >> 1;
-            const uint4* blk = reinterpret_cast<const uint4*>(trow) +
-                               (((uint64_t)row[sl] * L + k) * B2 >> 2);
-            uint32_t g = 0;
-            if (W > 8) {
-              const uint4 q0 = __ldg(blk), q1 = __ldg(blk + 1);
-              g = (q0.x <= v) + (q0.y <= v) + (q0.z <= v) + (q0.w <= v) + (q1.x <= v) +
-                  (q1.y <= v) + (q1.z <= v) + (q1.w <= v);
-              blk += 2 + 2 * g;
-            }
-            const uint4 o0 = __ldg(blk), o1 = __ldg(blk + 1);
-            const uint32_t a2 = 8 * g + (o0.x <= v) + (o0.y <= v) + (o0.z <= v) + (o0.w <= v) +
-                                (o1.x <= v) + (o1.y <= v) + (o1.z <= v) + (o1.w <= v);
-            if (steps[sl] >= max_steps) outcome = -2;
-            else row[sl] = k * W + a2;
-          }
+          if (j >= n) outcome = (int)(j - n);
+          else if (steps[sl] >= max_steps) outcome = -2;
+          else row[sl] = j;
         }
         ++b[sl];
       } else {
@@ -257,13 +264,29 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
       }
       if (kScore && outcome >= 0) {
         // replay the finished walk and count its transitions under its absorbing lead
-        unsigned long long* cnt = score.cnt + (size_t)outcome * score.stride + t_tab_off;
+        unsigned long long* cnt = score.cnt + (size_t)outcome * score.stride + t_wt_off;
         unsigned long long* mcnt =
             score.mode_cnt + (size_t)outcome * score.mode_stride + t_mode_off;
         uint32_t rrow = 0;
         bool live = true;
         for (uint32_t bb = 0; live; ++bb) {
           const uint4 q = philox4x32_10(make_uint4(bb, wid_lo[sl], wid_hi[sl], task_id), key);
+          if (kTwo && two) {
+            // two-level: block 0 the injection, block bb >= 1 transition bb (as walked above)
+            if (bb == 0) {
+              const uint32_t c = __umulhi(q.x, W);
+              const uint64_t e = __ldg(mrow + c);
+              const uint32_t mode = q.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+              atomicAdd(mcnt + mode, 1ull);
+              rrow = inj_row0 + mode;
+            } else {
+              const uint32_t j = two_level_draw(l1row, trow, rrow, L, W, B2, q);
+              atomicAdd(cnt + (uint64_t)rrow * K + j, 1ull);
+              if (j >= n) live = false;
+              rrow = j;
+            }
+            continue;
+          }
           if (bb == 0) {
             const uint32_t c = __umulhi(q.x, W);
             const uint64_t e = __ldg(mrow + c);
@@ -375,7 +398,10 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
                       reinterpret_cast<unsigned long long*>(d_mode_score),
                       (unsigned long long)score_stride, mode_stride};
     auto kern =
-        d_score ? (d_trace_lead ? walk_kernel<true, true, 1, false> : walk_kernel<false, true, 1, false>)
+        d_score ? (two_level ? (d_trace_lead ? walk_kernel<true, true, 1, true>
+                                             : walk_kernel<false, true, 1, true>)
+                             : (d_trace_lead ? walk_kernel<true, true, 1, false>
+                                             : walk_kernel<false, true, 1, false>))
         : two_level
             ? (slots == 2 ? (d_trace_lead ? walk_kernel<true, false, 2, true>
                                           : walk_kernel<false, false, 2, true>)

@@ -63,7 +63,7 @@ struct negf_tables_s {
   int n_waves = 1;
   void* d_green = nullptr;       // keep_green: dense G per task, then G Phi per task
   void* d_gphi = nullptr;
-  double* d_phi = nullptr;       // keep_green: transverse modes (the gradient needs them)
+  double* d_phi = nullptr;       // keep_green / keep_weights: transverse modes (the gradient)
   uint64_t green_total = 0, gphi_total = 0, score_stride = 0;
   uint32_t mode_stride = 0;
 };
@@ -908,7 +908,7 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
                 "table allocation: %s", cudaGetErrorString(e));
   }
   void* kept = nullptr;
-  t->score_stride = w.tab;
+  t->score_stride = w.wt;         // score tallies and seeds share the weights' rows x K layout
   t->mode_stride = P.mode_total;
   if (o.keep_green) {
     const uint64_t cb = negf::block_bytes(prec);
@@ -943,7 +943,7 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   dfree(d_tcjobs, s);
   if (d_gL) cudaFreeAsync(d_gL, s);
   if (d_gR) cudaFreeAsync(d_gR, s);
-  if (o.keep_green) {
+  if (o.keep_green || o.keep_weights) {
     t->d_phi = q.d_phi;          // the gradient needs the transverse modes
     q.d_phi = nullptr;
   }
@@ -1206,7 +1206,7 @@ negf_status negf_get_task_info(negf_ctx ctx, negf_tables t, int32_t task, negf_t
   out->K = d.K;
   out->rows = d.rows;
   out->table_layout = d.layout;
-  out->table_offset = d.tab_off;
+  out->table_offset = d.wt_off;
   out->mode_offset = d.mode_off;
   out->energy = d.E;
   out->energy_weight = d.w_E;
@@ -1437,8 +1437,6 @@ negf_status negf_walk_score(negf_ctx ctx, negf_tables t, int32_t start_lead, uin
   *out = nullptr;
   if (t->tables_released || !t->d_tab)
     return fail(ctx, NEGF_E_INVALID, "negf_walk_score: the tables of this handle were released");
-  if (t->any_two)
-    return fail(ctx, NEGF_E_INVALID, "negf_walk_score: score tallies need one-level tables");
   if (walkers_per_task > (1ull << 40))
     return fail(ctx, NEGF_E_INVALID, "negf_walk_score: walkers_per_task above 2^40");
   DeviceGuard g(ctx->device);
@@ -1466,7 +1464,7 @@ negf_status negf_walk_score(negf_ctx ctx, negf_tables t, int32_t start_lead, uin
                           start_lead, seed, walkers_per_task, walker_id_offset, max_steps,
                           ctx->d_counter, tl->d_counts, nullptr, nullptr, tl->d_score,
                           tl->score_stride, tl->d_mode_score, tl->mode_stride, ctx->sm_count, 0,
-                          s);
+                          s, nullptr, 1, t->any_two);
   }
   if (e != cudaSuccess) {
     negf_tally_free(tl);
@@ -1627,6 +1625,194 @@ negf_status negf_current_backward(negf_ctx ctx, negf_tables t, negf_tally tl, do
     for (int k = 0; k < nt; ++k)
       if (cnt[(size_t)k * NEGF_TALLY_FIELDS + 3] > 0)
         return fail(ctx, NEGF_E_STEPCAP, "negf_current_backward: truncated walks bias the gradient");
+  }
+  return NEGF_OK;
+}
+
+negf_status negf_current_backward_rgf(negf_ctx ctx, negf_tables t, negf_tally tl, double mu_p,
+                                      double mu_q, double kT, const double* dI,
+                                      int32_t ckpt_stride, double* d_onsite, double* d_eta) {
+  if (!ctx || !t || !tl || t->ctx != ctx || tl->ctx != ctx || tl->n_tasks != t->n_tasks)
+    return fail(ctx, NEGF_E_INVALID, "negf_current_backward_rgf: bad or mismatched handles");
+  if (!t->d_weights || !t->d_phi)
+    return fail(ctx, NEGF_E_INVALID, "negf_current_backward_rgf: build the tables with keep_weights");
+  if (!tl->d_score)
+    return fail(ctx, NEGF_E_INVALID, "negf_current_backward_rgf: tally has no score counts (use negf_walk_score)");
+  if (!(kT > 0.0) || !isfinite(mu_p) || !isfinite(mu_q) || !isfinite(kT))
+    return fail(ctx, NEGF_E_INVALID, "negf_current_backward_rgf: need finite mu and kT > 0");
+  if (ckpt_stride < 0)
+    return fail(ctx, NEGF_E_INVALID, "negf_current_backward_rgf: ckpt_stride < 0");
+  if (t->n_wires > 0 && (!dI || !d_onsite || !d_eta))
+    return fail(ctx, NEGF_E_INVALID, "negf_current_backward_rgf: NULL seed or output");
+  for (const TaskDesc& d : t->h_tasks)
+    if (d.fused)
+      return fail(ctx, NEGF_E_INVALID,
+                  "negf_current_backward_rgf: split-TF32 tables keep no weights (use FP32 or FP64)");
+  const int stride = ckpt_stride == 0 ? NEGF_CKPT_STRIDE_DEFAULT : ckpt_stride;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = ctx->stream;
+  const int nt = t->n_tasks, nw = t->n_wires, prec = t->precision;
+  const uint64_t cb = negf::block_bytes(prec);
+  std::vector<uint64_t> tso(nt), wso(nw), ck_off(nt);
+  uint64_t n_sites_tasks = 0, n_sites_wires = 0, ck_total = 0;
+  for (int k = 0; k < nt; ++k) {
+    const TaskDesc& d = t->h_tasks[k];
+    tso[k] = n_sites_tasks;
+    n_sites_tasks += d.n;
+    ck_off[k] = ck_total;
+    ck_total += 2ull * ((d.L + stride - 1) / stride) * d.W * d.W;
+  }
+  for (int w = 0; w < nw; ++w) {
+    wso[w] = n_sites_wires;
+    const int k0 = t->h_wire_task0[w];
+    if (k0 < t->h_wire_task0[w + 1]) n_sites_wires += t->h_tasks[k0].n;
+  }
+  // groups: runs of tasks of one wire (same W, L), as many as the scratch budget holds
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 1ull << 30;
+  const uint64_t budget = std::max<uint64_t>(std::min<uint64_t>(free_b / 2, 16ull << 30), 64ull << 20);
+  struct Group { int t0, n, slots; };
+  std::vector<Group> groups;
+  uint64_t max_task_buf = 0, max_slot_buf = 0;
+  int max_slots = 0;
+  for (int w = 0; w < nw; ++w) {
+    const int k0 = t->h_wire_task0[w], k1 = t->h_wire_task0[w + 1];
+    if (k0 == k1) continue;
+    const TaskDesc& d = t->h_tasks[k0];
+    const uint64_t blk = (uint64_t)d.W * d.W * cb;
+    const uint64_t per_task = (3ull * d.L + 2) * blk;   // gl, gr, Psi, Tl
+    const uint64_t per_slot = 2ull * d.L * blk;          // X, Y
+    const size_t smem = negf::adjoint_column_smem(d.W, prec);
+    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227u << 10) / smem));
+    for (int k = k0; k < k1;) {
+      int n = std::min(k1 - k, 64);
+      int slots = 0;
+      while (true) {
+        slots = (int)std::min<uint64_t>((uint64_t)n * d.L, (uint64_t)ctx->sm_count * per_sm);
+        if (n == 1 || n * per_task + slots * per_slot <= budget) break;
+        n = std::max(1, n / 2);
+      }
+      while (slots > 1 && n * per_task + slots * per_slot > budget) slots /= 2;
+      groups.push_back(Group{k, n, slots});
+      max_task_buf = std::max(max_task_buf, (uint64_t)n * per_task);
+      max_slot_buf = std::max(max_slot_buf, (uint64_t)slots * per_slot);
+      max_slots = std::max(max_slots, slots);
+      k += n;
+    }
+  }
+  double* d_wbar = nullptr;
+  double* d_ubar = nullptr;
+  double* d_dT = nullptr;
+  double* d_seed = nullptr;
+  double* d_out = nullptr;
+  uint64_t* d_tso = nullptr;
+  uint64_t* d_wso = nullptr;
+  uint64_t* d_ck_off = nullptr;
+  unsigned char* d_ck = nullptr;
+  unsigned char* d_tbuf = nullptr;
+  unsigned char* d_sbuf = nullptr;
+  cudaError_t e = dalloc(&d_wbar, std::max<uint64_t>(t->score_stride, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_ubar, std::max<uint32_t>(t->mode_stride, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_dT, 2 * std::max<uint64_t>(n_sites_tasks, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_seed, std::max(nw, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_out, 2 * std::max<uint64_t>(n_sites_wires, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_tso, std::max(nt, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_wso, std::max(nw, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_ck_off, std::max(nt, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_ck, std::max<uint64_t>(ck_total * cb, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_tbuf, std::max<uint64_t>(max_task_buf, 1), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(&d_sbuf, std::max<uint64_t>(max_slot_buf, 1), s, nullptr);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_ubar, 0, sizeof(double) * std::max<uint32_t>(t->mode_stride, 1), s);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(d_dT, 0, sizeof(double) * 2 * std::max<uint64_t>(n_sites_tasks, 1), s);
+  if (e == cudaSuccess && nt > 0) {
+    e = cudaMemcpyAsync(d_tso, tso.data(), sizeof(uint64_t) * nt, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_ck_off, ck_off.data(), sizeof(uint64_t) * nt, cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess && nw > 0) {
+    e = cudaMemcpyAsync(d_wso, wso.data(), sizeof(uint64_t) * nw, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(d_seed, dI, sizeof(double) * nw, cudaMemcpyHostToDevice, s);
+  }
+  if (e == cudaSuccess) {
+    ProfScope ps(ctx, "backward_seeds_kernel", 1);
+    e = negf::launch_backward_seeds(t->d_tasks, nt, t->total_jobs, prec, t->d_weights, t->d_rowsum,
+                                    t->d_mode_w, t->d_c, tl->d_counts, tl->d_score,
+                                    tl->score_stride, tl->d_mode_score, tl->mode_stride,
+                                    tl->start_lead, d_wbar, d_ubar, s);
+  }
+  if (e == cudaSuccess) {
+    ProfScope ps(ctx, "adjoint_sweep_kernel", 1);
+    e = negf::launch_adjoint_sweep(t->d_tasks, nt, t->max_W, prec, t->d_wire, t->d_phi, t->d_sig,
+                                   d_ck_off, stride, d_ck, t->d_err, s);
+  }
+  for (const Group& gr : groups) {
+    if (e != cudaSuccess) break;
+    const TaskDesc& d = t->h_tasks[gr.t0];
+    const uint64_t blk = (uint64_t)d.W * d.W * cb;
+    unsigned char* gl = d_tbuf;
+    unsigned char* grr = gl + (uint64_t)gr.n * d.L * blk;
+    unsigned char* psi = grr + (uint64_t)gr.n * d.L * blk;
+    unsigned char* tlb = psi + (uint64_t)gr.n * d.L * blk;
+    unsigned char* xs = d_sbuf;
+    unsigned char* ys = xs + (uint64_t)gr.slots * d.L * blk;
+    {
+      ProfScope ps(ctx, "adjoint_expand_kernel", 1);
+      e = negf::launch_adjoint_expand(t->d_tasks, gr.t0, gr.n, d.W, d.L, prec, t->d_wire,
+                                      t->d_phi, t->d_sig, d_ck_off, stride, d_ck, gl, grr,
+                                      t->d_err, s);
+    }
+    if (e != cudaSuccess) break;
+    ProfScope ps(ctx, "adjoint_column_kernel", 1);
+    e = negf::launch_adjoint_columns(t->d_tasks, gr.t0, gr.n, d.W, prec, tl->start_lead,
+                                     t->d_wire, t->d_phi, t->d_sig, t->d_gam, d_wbar, d_ubar,
+                                     tso[gr.t0], d_dT, d_dT + n_sites_tasks, gl, grr, psi, tlb,
+                                     xs, ys, gr.slots, t->d_err, s);
+  }
+  if (e == cudaSuccess) {
+    ProfScope ps(ctx, "grad_sum_kernel", 1);
+    e = negf::launch_grad_sum(t->d_tasks, nw, t->d_wire_task0, d_tso, d_wso, d_dT,
+                              d_dT + n_sites_tasks, d_seed, mu_p, mu_q, kT, d_out,
+                              d_out + n_sites_wires, s);
+  }
+  std::vector<double> h(2 * n_sites_wires);
+  if (e == cudaSuccess && n_sites_wires > 0)
+    e = cudaMemcpyAsync(h.data(), d_out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dfree(d_wbar, s);
+  dfree(d_ubar, s);
+  dfree(d_dT, s);
+  dfree(d_seed, s);
+  dfree(d_out, s);
+  dfree(d_tso, s);
+  dfree(d_wso, s);
+  dfree(d_ck_off, s);
+  dfree(d_ck, s);
+  dfree(d_tbuf, s);
+  dfree(d_sbuf, s);
+  if (e != cudaSuccess)
+    return fail(ctx, e == cudaErrorMemoryAllocation ? NEGF_E_NOMEM : NEGF_E_CUDA,
+                "negf_current_backward_rgf: %s", cudaGetErrorString(e));
+  negf_status st = check_device(ctx, t);
+  if (st != NEGF_OK) return st;
+  uint64_t off = 0;
+  for (int w = 0; w < nw; ++w) {
+    const int k0 = t->h_wire_task0[w];
+    const int n = k0 < t->h_wire_task0[w + 1] ? t->h_tasks[k0].n : 0;
+    for (int i = 0; i < n; ++i) {
+      d_onsite[off + i] = h[wso[w] + i];
+      d_eta[off + i] = h[n_sites_wires + wso[w] + i];
+    }
+    off += n;
+  }
+  std::vector<uint64_t> cnt((size_t)nt * NEGF_TALLY_FIELDS);
+  if (nt > 0) {
+    st = negf_tally_counts(ctx, tl, cnt.data());
+    if (st != NEGF_OK) return st;
+    for (int k = 0; k < nt; ++k)
+      if (cnt[(size_t)k * NEGF_TALLY_FIELDS + 3] > 0)
+        return fail(ctx, NEGF_E_STEPCAP, "negf_current_backward_rgf: truncated walks bias the gradient");
   }
   return NEGF_OK;
 }

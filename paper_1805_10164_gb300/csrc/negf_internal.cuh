@@ -227,6 +227,25 @@ cudaError_t launch_backward_task(const TaskDesc& d, int precision, const void* G
 // accumulation (k_cgemm_tc.cu); a timed-out device wait sets ERR_TIMEOUT in err.
 cudaError_t launch_cgemm_tc(const cf* A, const cf* B, cf* Y, int n, int32_t* err,
                             cudaStream_t s);
+// Block-column adjoint (k_adjoint.cu): checkpointed sweeps of every task, the recompute of the
+// blocks between checkpoints for a group of tasks of one wire, and the column jobs of the group.
+size_t adjoint_column_smem(int W, int precision);
+cudaError_t launch_adjoint_sweep(const TaskDesc* d_tasks, int n_tasks, int max_W, int precision,
+                                 const double* d_wire, const double* d_phi, const cd* d_sig,
+                                 const uint64_t* d_ck_off, int stride, void* d_ck,
+                                 int32_t* d_err, cudaStream_t s);
+cudaError_t launch_adjoint_expand(const TaskDesc* d_tasks, int task0, int n_group, int W, int L,
+                                  int precision, const double* d_wire, const double* d_phi,
+                                  const cd* d_sig, const uint64_t* d_ck_off, int stride,
+                                  const void* d_ck, void* d_gl, void* d_gr, int32_t* d_err,
+                                  cudaStream_t s);
+cudaError_t launch_adjoint_columns(const TaskDesc* d_tasks, int task0, int n_group, int W,
+                                   int precision, int start_lead, const double* d_wire,
+                                   const double* d_phi, const cd* d_sig, const double* d_gam,
+                                   const double* d_wbar, const double* d_ubar, uint64_t site_off0,
+                                   double* d_dV, double* d_dE, const void* d_gl, const void* d_gr,
+                                   void* d_psi, void* d_tl, void* d_xs, void* d_ys, int slots,
+                                   int32_t* d_err, cudaStream_t s);
 cudaError_t launch_grad_sum(const TaskDesc* d_tasks, int n_wires, const int32_t* d_wire_task0,
                             const uint64_t* d_task_site_off, const uint64_t* d_wire_site_off,
                             const double* dT_V, const double* dT_E, const double* d_seed,

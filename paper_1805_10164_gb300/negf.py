@@ -122,6 +122,7 @@ def load():
         "negf_tally_score_size": (U64, [P]),
         "negf_tally_mode_size": (U32, [P]),
         "negf_current_backward": (I32, [P, P, P, D, D, D, P, P, P]),
+        "negf_current_backward_rgf": (I32, [P, P, P, D, D, D, P, I32, P, P]),
         "negf_plan_create": (I32, [P, C.POINTER(negf_wire), I32, C.POINTER(negf_build_opts),
                                    C.POINTER(negf_run_opts), D, D, D, I32, C.POINTER(P)]),
         "negf_plan_launch": (I32, [P, P, U64, U64]),
@@ -456,6 +457,19 @@ def negf_current_backward(ctx, tables, tally, mu_p, mu_q, kT, dI, n_sites):
     st = _check(ctx, load().negf_current_backward(ctx, tables, tally, float(mu_p), float(mu_q),
                                                   float(kT), dI.ctypes.data, dV.ctypes.data,
                                                   dE.ctypes.data), allow=(NEGF_E_STEPCAP,))
+    return dV[:n_sites], dE[:n_sites], st == NEGF_E_STEPCAP
+
+
+def negf_current_backward_rgf(ctx, tables, tally, mu_p, mu_q, kT, dI, n_sites, ckpt_stride=0):
+    """As negf_current_backward, by the block-column adjoint (tables with keep_weights; g^L
+    and g^R kept every ckpt_stride slices, 0 for the library default)."""
+    dI = np.ascontiguousarray(dI, dtype=np.float64)
+    dV = np.zeros(max(n_sites, 1))
+    dE = np.zeros(max(n_sites, 1))
+    st = _check(ctx, load().negf_current_backward_rgf(ctx, tables, tally, float(mu_p), float(mu_q),
+                                                      float(kT), dI.ctypes.data, int(ckpt_stride),
+                                                      dV.ctypes.data, dE.ctypes.data),
+                allow=(NEGF_E_STEPCAP,))
     return dV[:n_sites], dE[:n_sites], st == NEGF_E_STEPCAP
 
 

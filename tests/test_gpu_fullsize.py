@@ -6,8 +6,9 @@
   small tasks against the direct probe solve (every |z| <= z_bar(m), sum z^2 <= chi2_bar(m);
   mc_bars: the 3-SE bar as a 0.27 % family-wise false-alarm rate).
 * Differentiation case (W = 16, L = 100, 16 energies): the score-function gradient of the
-  current against the oracle's exact derivative on sampled sites (means of 16 batches, each
-  |t| within the family-wise bar of Student's t with 15 degrees of freedom).
+  current by the block-column adjoint with the RGF blocks checkpointed every 10 slices (as
+  the benchmark runs it) against the oracle's exact derivative on sampled sites (means of 16
+  batches, each |t| within the family-wise bar of Student's t with 15 degrees of freedom).
 * Weak scattering (W = 64, L = 1000, eta = 0.005), two of its 256 energies at full size:
   sampled table rows (sites and injection modes) against the oracle's sparse column solves,
   realised two-level distribution within the quantisation bound + the precision's bar of the
@@ -91,14 +92,14 @@ def test_differentiation_case_full_size(ctx):
         _, dV, dE = adjoint.transmission_gradient(w.onsite, w.eta, w.t, E, 0, 1, sites=sites)
         gV += w.energy_weight[k] * df[k] * dV.reshape(-1)
         gE += w.energy_weight[k] * df[k] * dE.reshape(-1)
-    tables = negf.negf_build_tables(ctx, [w], precision="fp32", keep_green=True)
+    tables = negf.negf_build_tables(ctx, [w], precision="fp32", keep_weights=True)
     try:
         est = []
         n_batch = 16
         for b in range(n_batch):
             tally = negf.negf_walk_score(ctx, tables, 0, 99, 100_000, walker_id_offset=b * 100_000)
-            dV, dE, cap = negf.negf_current_backward(ctx, tables, tally, wl.mu_p, wl.mu_q, wl.kT,
-                                                     [1.0], n)
+            dV, dE, cap = negf.negf_current_backward_rgf(ctx, tables, tally, wl.mu_p, wl.mu_q,
+                                                         wl.kT, [1.0], n, ckpt_stride=10)
             negf.negf_tally_free(tally)
             assert not cap
             est.append(np.concatenate([dV[sites], dE[sites]]))

@@ -196,12 +196,6 @@ def test_two_level_refusals(ctx):
     w = inputs.small_wire(117, W=3, L=4, n_energy=1)
     with pytest.raises(negf.NegfError, match="NEGF_E_INVALID"):
         negf.negf_build_tables(ctx, [w], layout="two_level", keep_green=True)
-    t = negf.negf_build_tables(ctx, [w], layout="two_level")
-    try:
-        with pytest.raises(negf.NegfError, match="NEGF_E_INVALID"):
-            negf.negf_walk_score(ctx, t, 0, 1, 10)
-    finally:
-        negf.negf_tables_free(t)
     t = negf.negf_build_tables(ctx, [w], layout="one_level")
     try:
         with pytest.raises(negf.NegfError, match="NEGF_E_INVALID"):
