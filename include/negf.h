@@ -97,6 +97,16 @@ typedef struct {
   const double* energy_weight;   /* [n_energy] quadrature weights, or NULL for all 1 */
   int32_t lead_model;            /* negf_lead_model */
   double gamma_lead;             /* Gamma_l for NEGF_LEAD_WIDE_BAND, > 0 */
+  const double* slice_h;         /* NULL: the square-lattice cross-section above.  Else a
+                                    multi-orbital slice (the "more orbitals per atom"
+                                    generalisation of the Hamiltonian; W counts orbitals):
+                                    [W*W] row-major real symmetric block h, and H_kk = h +
+                                    diag(onsite of slice k); the coupling between slices stays
+                                    -t between the same orbital of neighbouring slices.  The
+                                    exact strip lead is then the clean strip of h: its modes
+                                    are h's eigenvectors (computed on the device), eps_m its
+                                    eigenvalues.  Same memspace as the other arrays; must be
+                                    finite and exactly symmetric (NEGF_E_INVALID). */
 } negf_wire;
 
 typedef struct {

@@ -61,14 +61,15 @@ def _weights_tangent(g, phi, gam, Psi, alpha, col, dgamma):
     return dw, du
 
 
-def transmission_gradient(onsite, eta, t, E, p, q, lead_model=0, gamma_lead=0.0, sites=None):
+def transmission_gradient(onsite, eta, t, E, p, q, lead_model=0, gamma_lead=0.0, sites=None,
+                          slice_h=None):
     """T_qp and its exact derivatives dT/dV [L, W] and dT/deta [L, W] (only the flat site
     indices in ``sites`` when given; the others are left at 0)."""
     onsite = np.asarray(onsite, dtype=np.float64)
     L, W = onsite.shape
     n = L * W
-    g = wire.green_retarded(E, onsite, eta, t, lead_model, gamma_lead)
-    phi, _, gam = wire.lead_modes(E, W, t, lead_model, gamma_lead)
+    g = wire.green_retarded(E, onsite, eta, t, lead_model, gamma_lead, slice_h)
+    phi, _, gam = wire.lead_modes(E, W, t, lead_model, gamma_lead, slice_h)
     tab = markov.transition_weights(g, (phi, gam))
     w = tab["w"]
     rs = w.sum(1)

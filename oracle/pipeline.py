@@ -12,11 +12,11 @@ from . import alias, buttiker, markov, wire
 
 
 def task_reference(onsite, eta, t, E, lead_model=0, gamma_lead=0.0, with_alias=True,
-                   with_direct=True):
+                   with_direct=True, slice_h=None):
     onsite = np.asarray(onsite, dtype=np.float64)
     L, W = onsite.shape
-    g = wire.green_retarded(E, onsite, eta, t, lead_model, gamma_lead)
-    phi, sig, gam = wire.lead_modes(E, W, t, lead_model, gamma_lead)
+    g = wire.green_retarded(E, onsite, eta, t, lead_model, gamma_lead, slice_h)
+    phi, sig, gam = wire.lead_modes(E, W, t, lead_model, gamma_lead, slice_h)
     tab = markov.transition_weights(g, (phi, gam))
     out = dict(g=g, tab=tab, sigma_modes=sig, gamma_modes=gam, W=W, L=L, n=L * W, K=L * W + 2)
     out["exact"] = markov.absorption(tab)

@@ -13,29 +13,44 @@ Model (Sec. III.A and the lead/scattering self-energies of Sec. II.A):
   g_s is the surface Green's function of a semi-infinite chain.  lead_model 1 is the paper's
   wide-band model Sigma_p = -(i/2) Gamma_l P_p (Sec. III.A), which has the same eigenvectors.
 * G^r = (E - H - Sigma_L - Sigma_R - Sigma_s)^{-1}   (Eq. eq_for_gr), by dense LU.
+* Multi-orbital slices (the "more orbitals per atom" generalisation of the Hamiltonian, Sec.
+  "Generalizations of the Hamiltonian", and the s and p orbitals of the paper's tight-binding
+  model, Sec. III.A): ``slice_h`` [W, W] real symmetric replaces the square-lattice
+  cross-section: H_kk = slice_h + diag(onsite_k), W now counting orbitals (atoms x orbitals per
+  atom).  The coupling between slices stays -t between the same orbital of neighbouring slices
+  (orbital-diagonal).  The exact lead is then the clean strip of slice_h: its modes are the
+  eigenvectors of slice_h (numpy eigh, a library step), eps their eigenvalues, and
+  Sigma_m = t^2 g_s(E - eps_m) as before.
 """
 import numpy as np
 
 
-def hamiltonian(onsite, t):
-    """Dense real-symmetric tight-binding H for an [L, W] array of onsite energies."""
+def hamiltonian(onsite, t, slice_h=None):
+    """Dense real-symmetric tight-binding H for an [L, W] array of onsite energies (with
+    ``slice_h``: the multi-orbital slice block on every slice, plus the onsite energies)."""
     onsite = np.asarray(onsite, dtype=np.float64)
     L, W = onsite.shape
     n = L * W
     H = np.zeros((n, n), dtype=np.float64)
     for k in range(L):
+        if slice_h is not None:
+            H[k * W:(k + 1) * W, k * W:(k + 1) * W] = np.asarray(slice_h, dtype=np.float64)
         for a in range(W):
             i = k * W + a
-            H[i, i] = onsite[k, a]
-            if a + 1 < W:
+            H[i, i] += onsite[k, a]
+            if slice_h is None and a + 1 < W:
                 H[i, i + 1] = H[i + 1, i] = -t
             if k + 1 < L:
                 H[i, i + W] = H[i + W, i] = -t
     return H
 
 
-def transverse_modes(W, t):
-    """Sine modes of a W-site cross-section with hopping -t: phi[a, m], eps[m], m = 1..W."""
+def transverse_modes(W, t, slice_h=None):
+    """Modes of a W-site cross-section: the sine modes of the hopping -t chain (phi[a, m],
+    eps[m], m = 1..W), or with ``slice_h`` its eigenvectors and eigenvalues (ascending)."""
+    if slice_h is not None:
+        eps, phi = np.linalg.eigh(np.asarray(slice_h, dtype=np.float64))
+        return phi, eps
     a = np.arange(1, W + 1, dtype=np.float64)[:, None]
     m = np.arange(1, W + 1, dtype=np.float64)[None, :]
     phi = np.sqrt(2.0 / (W + 1)) * np.sin(m * np.pi * a / (W + 1))
@@ -58,13 +73,13 @@ def chain_surface_self_energy(e, t):
     return s, -2.0 * s.imag
 
 
-def lead_modes(E, W, t, lead_model=0, gamma_lead=0.0):
+def lead_modes(E, W, t, lead_model=0, gamma_lead=0.0, slice_h=None):
     """Eigen-decomposition of one lead's self-energy on its boundary slice.
 
     Returns phi [W, W] (columns = eigenvectors |i> of Gamma_p, Sec. II.D Step 3), sigma [W]
     complex eigenvalues of Sigma_p and gam [W] real eigenvalues of Gamma_p (lambda_i).
     """
-    phi, eps = transverse_modes(W, t)
+    phi, eps = transverse_modes(W, t, slice_h)
     if lead_model == 0:
         sig = np.empty(W, dtype=np.complex128)
         gam = np.empty(W, dtype=np.float64)
@@ -78,10 +93,10 @@ def lead_modes(E, W, t, lead_model=0, gamma_lead=0.0):
     return phi, sig, gam
 
 
-def lead_matrices(E, L, W, t, lead_model=0, gamma_lead=0.0):
+def lead_matrices(E, L, W, t, lead_model=0, gamma_lead=0.0, slice_h=None):
     """Sigma_L, Sigma_R, Gamma_L, Gamma_R embedded as dense n x n matrices (Eq. sigmas_comp_r)."""
     n = L * W
-    phi, sig, gam = lead_modes(E, W, t, lead_model, gamma_lead)
+    phi, sig, gam = lead_modes(E, W, t, lead_model, gamma_lead, slice_h)
     s_blk = phi @ np.diag(sig) @ phi.T
     g_blk = phi @ np.diag(gam) @ phi.T
     out = []
@@ -95,7 +110,7 @@ def lead_matrices(E, L, W, t, lead_model=0, gamma_lead=0.0):
     return SL, SR, GL, GR
 
 
-def green_retarded(E, onsite, eta, t, lead_model=0, gamma_lead=0.0):
+def green_retarded(E, onsite, eta, t, lead_model=0, gamma_lead=0.0, slice_h=None):
     """Dense G^r(E) = (E - H - Sigma^r)^{-1} (Eq. eq_for_gr) with
     Sigma^r = Sigma_L + Sigma_R + Sigma_s (Eq. sigmas_comp_r), Sigma_s = -i eta/2 per site.
 
@@ -107,8 +122,8 @@ def green_retarded(E, onsite, eta, t, lead_model=0, gamma_lead=0.0):
     eta = np.asarray(eta, dtype=np.float64)
     L, W = onsite.shape
     n = L * W
-    H = hamiltonian(onsite, t)
-    SL, SR, GL, GR = lead_matrices(E, L, W, t, lead_model, gamma_lead)
+    H = hamiltonian(onsite, t, slice_h)
+    SL, SR, GL, GR = lead_matrices(E, L, W, t, lead_model, gamma_lead, slice_h)
     gamma = eta.reshape(n)
     Ss = np.diag(-0.5j * gamma)
     M = E * np.eye(n) - H - SL - SR - Ss

@@ -21,11 +21,22 @@ __device__ __forceinline__ cf mkc(double a, double b, cf) { return cf{(float)a, 
 __device__ __forceinline__ bool finite_c(cd v) { return isfinite(v.x) && isfinite(v.y); }
 __device__ __forceinline__ bool finite_c(cf v) { return isfinite(v.x) && isfinite(v.y); }
 
-// E - H_kk - Sigma_s(k) entry (a, b) of slice k, in the precision of C
+// The task's multi-orbital slice block h [W][W] (it follows eta in the wire data), or nullptr
+// for the square-lattice cross-section.
+__device__ __forceinline__ const double* slice_block(const TaskDesc& d, const double* onsite) {
+  return d.slice_h ? onsite + 2 * (uint64_t)d.n : nullptr;
+}
+
+// E - H_kk - Sigma_s(k) entry (a, b) of slice k, in the precision of C; H_kk = h + diag(onsite)
+// for a multi-orbital slice block h, else diag(onsite) with -t between neighbours
 template <typename C>
 __device__ __forceinline__ C slice_entry(int a, int b, int k, int W, double E, double t,
-                                         const double* onsite, const double* eta) {
+                                         const double* onsite, const double* eta,
+                                         const double* h = nullptr) {
   using R = typename Real<C>::T;
+  if (h)
+    return mkc((a == b ? E - onsite[k * W + a] : 0.0) - h[a * W + b],
+               a == b ? 0.5 * eta[k * W + a] : 0.0, C{});
   C v = mkc(a == b ? E - onsite[k * W + a] : 0.0, a == b ? 0.5 * eta[k * W + a] : 0.0, C{});
   if (a - b == 1 || b - a == 1) v.x += (R)t;
   return v;

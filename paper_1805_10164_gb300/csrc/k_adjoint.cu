@@ -63,7 +63,7 @@ __device__ void form_slice(C* A, int k, int W, const TaskDesc& d, const double* 
   const R tt = (R)(d.t * d.t);
   for (int idx = threadIdx.x; idx < W * W; idx += blockDim.x) {
     const int a = idx / W, b = idx - a * W;
-    C v = slice_entry<C>(a, b, k, W, d.E, d.t, onsite, eta);
+    C v = slice_entry<C>(a, b, k, W, d.E, d.t, onsite, eta, slice_block(d, onsite));
     if (lead_l || lead_r) {
       const cd s = lead_sigma(a, b, W, phi, sg);
       const int nl = (lead_l ? 1 : 0) + (lead_r ? 1 : 0);
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, cons
       const R tt = t * t;
       for (int idx = tid; idx < WW; idx += blockDim.x) {
         const int a = idx / W, b = idx - a * W;
-        C v = slice_entry<C>(a, b, m, W, d.E, d.t, onsite, eta);
+        C v = slice_entry<C>(a, b, m, W, d.E, d.t, onsite, eta, slice_block(d, onsite));
         const int nl = (m == 0 ? 1 : 0) + (m == L - 1 ? 1 : 0);
         if (nl) {
           const cd s = lead_sigma(a, b, W, phi, sg);

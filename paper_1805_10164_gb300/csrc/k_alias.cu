@@ -90,11 +90,13 @@ __device__ __forceinline__ int gallop_first(int lo, int hi, uint64_t x, Key key)
 }
 
 // Build one row.  w: the K weights, staged in shared memory; A: the value the row must sum to
-// (checked when check_A); out: K entries; rowsum_out: receives the row sum.  s_u, s_c:
+// (checked when check_A, to tol A + atol: a row whose spectral weight is at the rounding level
+// of G, such as an orbital no open channel reaches, carries only rounding noise); out: K
+// entries; rowsum_out: receives the row sum.  s_u, s_c:
 // 32 * alias_pitch(K) u64 each; s_x: K u32.  after_stage() is called by every lane once w has
 // been read (the caller reuses w's buffer for the next row).
 template <typename R, typename After>
-__device__ void alias_row(const R* w, int K, double A, bool check_A, double tol,
+__device__ void alias_row(const R* w, int K, double A, bool check_A, double tol, double atol,
                           uint64_t* __restrict__ out, double* rowsum_out, uint64_t* s_u,
                           uint64_t* s_c, uint32_t* s_x, int32_t* err, After after_stage) {
   const int lane = threadIdx.x & 31;
@@ -130,7 +132,7 @@ __device__ void alias_row(const R* w, int K, double A, bool check_A, double tol,
   if (__any_sync(FULL, bad) && lane == 0) atomicOr(err, ERR_NONFINITE);
   if (!(wmax > 0)) {
     if (lane == 0) *rowsum_out = 0.0;
-    if (lane == 0 && check_A && A > 1e-300) atomicOr(err, ERR_ROWSUM);
+    if (lane == 0 && check_A && A > 1e-300 && A > atol) atomicOr(err, ERR_ROWSUM);
     for (int i = lane; i < K; i += 32) out[i] = pack(0xffffffffu, (uint32_t)i);
     return;
   }
@@ -157,7 +159,7 @@ __device__ void alias_row(const R* w, int K, double A, bool check_A, double tol,
     const double total = sizeof(R) == 8 ? part : ldexp((double)T, -sh);
     rcp = (uint64_t)(ldexp(1.0, 94) / (double)T);   // < 2^63 since T >= 2^31
     *rowsum_out = total;
-    if (check_A && A > 1e-300 && fabs(total - A) > tol * A) atomicOr(err, ERR_ROWSUM);
+    if (check_A && A > 1e-300 && fabs(total - A) > tol * A + atol) atomicOr(err, ERR_ROWSUM);
   }
   // pass 3: u_i = floor(m_i K 2^32 / T) = (m_i K) (2^94 / T) / 2^62, with the 128-bit product
   rcp = __shfl_sync(FULL, rcp, 0);
@@ -319,12 +321,12 @@ __global__ void alias_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
     cp_async_wait_all();
     __syncwarp();
     if (row < d.rows) {
-      alias_row<R>(reinterpret_cast<const R*>(s_stage), d.K, A, true, tol,
+      alias_row<R>(reinterpret_cast<const R*>(s_stage), d.K, A, true, tol, 1e-13 / d.t,
                    tab + d.tab_off + (uint64_t)row * d.K, rowsum + job, s_u, s_c, s_x, err,
                    after);
     } else {
       const int p = row - d.rows;
-      alias_row<double>(reinterpret_cast<const double*>(s_stage), d.W, A, true, 1e-9,
+      alias_row<double>(reinterpret_cast<const double*>(s_stage), d.W, A, true, 1e-9, 1e-13 / d.t,
                         mode_tab + d.mode_off + p * d.W, rowsum + job, s_u, s_c, s_x, err,
                         after);
     }

@@ -80,6 +80,14 @@ __global__ void validate_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
   bool bad = false;
   for (int i = threadIdx.x; i < d.n; i += blockDim.x)
     bad |= !isfinite(onsite[i]) || !isfinite(eta[i]) || !(eta[i] >= 0.0);
+  if (d.slice_h) {
+    // a multi-orbital slice block must be finite and exactly symmetric
+    const double* h = eta + d.n;
+    for (int i = threadIdx.x; i < d.W * d.W; i += blockDim.x) {
+      const int a = i / d.W, b = i - a * d.W;
+      bad |= !isfinite(h[i]) || h[i] != h[b * d.W + a];
+    }
+  }
   if (bad) atomicOr(err, ERR_INPUT);
   if (threadIdx.x == 0 && !(isfinite(d.E) && isfinite(d.w_E))) atomicOr(err, ERR_INPUT);
 }

@@ -43,12 +43,14 @@ __global__ void lead_modes_kernel(const TaskDesc* __restrict__ tasks, int n_task
   if (task >= n_tasks) return;
   const TaskDesc d = tasks[task];
   if (d.e_idx == 0) {
-    // once per wire: transverse modes and the FP32 copy of eta
-    for (int idx = threadIdx.x; idx < d.W * d.W; idx += blockDim.x) {
-      const double v = phi_mode(idx / d.W, idx % d.W, d.W);
-      phi[d.phi_off + idx] = v;
-      phi32[d.phi_off + idx] = (float)v;
-    }
+    // once per wire: transverse modes (a multi-orbital slice's come from slice_modes_kernel)
+    // and the FP32 copy of eta
+    if (!d.slice_h)
+      for (int idx = threadIdx.x; idx < d.W * d.W; idx += blockDim.x) {
+        const double v = phi_mode(idx / d.W, idx % d.W, d.W);
+        phi[d.phi_off + idx] = v;
+        phi32[d.phi_off + idx] = (float)v;
+      }
     const double* eta = wire + d.onsite_off + d.n;
     for (int i = threadIdx.x; i < d.n; i += blockDim.x) eta32[d.onsite_off / 2 + i] = (float)eta[i];
   }
@@ -59,8 +61,11 @@ __global__ void lead_modes_kernel(const TaskDesc* __restrict__ tasks, int n_task
       s = mk(0.0, -0.5 * d.gamma_lead);
       g = d.gamma_lead;
     } else {
-      // eps_m = -2t cos((m+1) pi / (W+1)); Sigma_m = t^2 g_s(E - eps_m), retarded branch
-      const double eps = -2.0 * d.t * cospi((double)(m + 1) / (double)(d.W + 1));
+      // eps_m = -2t cos((m+1) pi / (W+1)) (a slice block: its m-th eigenvalue);
+      // Sigma_m = t^2 g_s(E - eps_m), retarded branch
+      const double eps = d.slice_h
+                             ? wire[d.onsite_off + 2 * (uint64_t)d.n + (uint64_t)d.W * d.W + m]
+                             : -2.0 * d.t * cospi((double)(m + 1) / (double)(d.W + 1));
       const double e = d.E - eps, two_t = 2.0 * d.t;
       if (fabs(fabs(e) - two_t) <= 1e-12 * d.t) atomicOr(err, ERR_INPUT);
       if (fabs(e) < two_t) {
@@ -205,7 +210,7 @@ __device__ __forceinline__ void sweep_rows_body(const TaskDesc& d, int dir,
     if (own && i < W) {
       cd acc = mk(0.0, 0.0);
       for (int q = 0; q < W; ++q) acc = acc + (phi[i * W + q] * phi[j * W + q]) * sg[q];
-      a[m] = slice_entry<C>(i, j, kf, W, d.E, d.t, onsite, eta) - to_c(acc, C{});
+      a[m] = slice_entry<C>(i, j, kf, W, d.E, d.t, onsite, eta, slice_block(d, onsite)) - to_c(acc, C{});
     }
   }
   C* out = dir == 0 ? gL : gR;
@@ -244,7 +249,7 @@ __device__ __forceinline__ void sweep_rows_body(const TaskDesc& d, int dir,
         const C v = a[m];
         dst[i * W + j] = v;
         bad |= !finite_c(v);
-        if (more) a[m] = slice_entry<C>(i, j, kn, W, d.E, d.t, onsite, eta) - tt * v;
+        if (more) a[m] = slice_entry<C>(i, j, kn, W, d.E, d.t, onsite, eta, slice_block(d, onsite)) - tt * v;
       }
     }
     if (__syncthreads_or(bad) && tid == 0) atomicOr(err, ERR_NONFINITE);
@@ -309,7 +314,7 @@ __global__ void __launch_bounds__(kSweepCtaThreads) rgf_sweep_cta_kernel(
     const int a = idx / W, b = idx - a * W;
     cd acc = mk(0.0, 0.0);
     for (int m = 0; m < W; ++m) acc = acc + (phi[a * W + m] * phi[b * W + m]) * sg[m];
-    A[idx] = slice_entry<C>(a, b, kf, W, d.E, d.t, onsite, eta) - to_c(acc, C{});
+    A[idx] = slice_entry<C>(a, b, kf, W, d.E, d.t, onsite, eta, slice_block(d, onsite)) - to_c(acc, C{});
   }
   C* out = dir == 0 ? gL : gR;
   const R tt = (R)(d.t * d.t);
@@ -331,7 +336,7 @@ __global__ void __launch_bounds__(kSweepCtaThreads) rgf_sweep_cta_kernel(
       bad |= !finite_c(v);
       if (more) {
         const int a = idx / W, b = idx - a * W;
-        A[idx] = slice_entry<C>(a, b, kn, W, d.E, d.t, onsite, eta) - tt * v;
+        A[idx] = slice_entry<C>(a, b, kn, W, d.E, d.t, onsite, eta, slice_block(d, onsite)) - tt * v;
       }
     }
     if (__syncthreads_or(bad) && tid == 0) atomicOr(err, ERR_NONFINITE);
@@ -488,8 +493,20 @@ __device__ bool invert_slice(cf (&a)[W], bool all_dephase, cf* buf) {
 // get zero columns.
 template <int W>
 __device__ void build_col(cf (&a)[W], double E, double t, double onsite_j, double eta_j,
-                          const cf (&x)[W]) {
+                          const cf (&x)[W], const double* h = nullptr) {
   const int j = threadIdx.x & 31;
+  if (h) {
+    // multi-orbital slice block: column j of E - h - diag(onsite) + i eta / 2 - x
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+      cf v{0.f, 0.f};
+      if (j < W)
+        v = cf{(float)((i == j ? E - onsite_j : 0.0) - h[i * W + j]),
+               i == j ? (float)(0.5 * eta_j) : 0.f} - x[i];
+      a[i] = v;
+    }
+    return;
+  }
   const cf diag{(float)(E - onsite_j), (float)(0.5 * eta_j)};
   const float tf = (float)t;
 #pragma unroll
@@ -545,7 +562,7 @@ __device__ __forceinline__ void sweep_reg_body(const TaskDesc& d, int dir,
       on_j = onsite[kn * W + jc];
       eta_j = eta[kn * W + jc];
     }
-    build_col<W>(a, d.E, d.t, on_cur, eta_cur, x);
+    build_col<W>(a, d.E, d.t, on_cur, eta_cur, x, slice_block(d, onsite));
     const bool deph = __all_sync(0xffffffffu, lane >= W || eta_cur > 0.0);
     if (!invert_slice<W>(a, deph, srow)) {
       if (lane == 0) atomicOr(err, ERR_SINGULAR);
@@ -680,7 +697,7 @@ __global__ void __launch_bounds__(kSweepThreads) diag_cta_kernel(
   const C* gr = lead_r ? nullptr : gR + d.g_off + (uint64_t)(m0 + 1) * WW;
   for (int idx = tid; idx < WW; idx += nth) {
     const int a = idx / W, b = idx - a * W;
-    C v = slice_entry<C>(a, b, m0, W, d.E, d.t, onsite, eta);
+    C v = slice_entry<C>(a, b, m0, W, d.E, d.t, onsite, eta, slice_block(d, onsite));
     v = v - (gl ? tt * gl[idx] : S[idx]);
     v = v - (gr ? tt * gr[idx] : S[idx]);
     A[idx] = v;
@@ -779,7 +796,7 @@ __device__ __forceinline__ void diag_reg_body(const TaskDesc& d, int task, uint3
     }
   }
   const double eta_j = eta[m0 * W + jc];
-  build_col<W>(a, d.E, d.t, onsite[m0 * W + jc], eta_j, x);
+  build_col<W>(a, d.E, d.t, onsite[m0 * W + jc], eta_j, x, slice_block(d, onsite));
   const bool deph = __all_sync(0xffffffffu, lane >= W || eta_j > 0.0);
   if (!invert_slice<W>(a, deph, srow)) {
     if (lane == 0) atomicOr(err, ERR_SINGULAR);

@@ -393,6 +393,7 @@ struct Plan {
   int max_W = 1, max_L = 1, max_K = 3;
   int max_KA = 3;                          // longest row the alias kernel builds
   bool any_two = false;
+  bool any_slice_h = false;                // some wire has a multi-orbital slice block
   uint64_t edge_total = 0;                 // fused tasks' edge blocks (complex64)
 };
 
@@ -450,6 +451,13 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
         if (!isfinite(wr.onsite[i]) || !isfinite(wr.eta[i]) || !(wr.eta[i] >= 0.0))
           return fail(ctx, NEGF_E_INVALID, "wire %d: site %lld: onsite/eta not finite or eta < 0",
                       w, (long long)i);
+      if (wr.slice_h)
+        for (int a = 0; a < wr.W; ++a)
+          for (int b = 0; b < wr.W; ++b)
+            if (!isfinite(wr.slice_h[a * wr.W + b]) ||
+                wr.slice_h[a * wr.W + b] != wr.slice_h[b * wr.W + a])
+              return fail(ctx, NEGF_E_INVALID,
+                          "wire %d: slice_h[%d][%d] not finite or not symmetric", w, a, b);
     }
     // energies and weights are always brought to the host (they become task scalars)
     std::vector<double> E(wr.n_energy), wE(wr.n_energy, 1.0);
@@ -468,7 +476,9 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
     for (int k = 0; k < wr.n_energy; ++k) {
       if (!isfinite(E[k]) || !isfinite(wE[k]))
         return fail(ctx, NEGF_E_INVALID, "wire %d: energy %d not finite", w, k);
-      if (wr.lead_model == NEGF_LEAD_STRIP && band_edge(E[k], wr.W, wr.t))
+      // (the levels of a slice block are known on the device only: there the lead-mode kernel
+      // reports an energy on a band edge as NEGF_E_INVALID)
+      if (wr.lead_model == NEGF_LEAD_STRIP && !wr.slice_h && band_edge(E[k], wr.W, wr.t))
         return fail(ctx, NEGF_E_INVALID, "wire %d: energy %.17g lies on a lead band edge", w, E[k]);
       TaskDesc d{};
       d.wire = w;
@@ -486,6 +496,7 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
       d.layout = layout;
       d.fused = tc_wire ? 1 : 0;
       d.cta_chain = (fp32 && (wr.W == 64 || (wr.W > 16 && wr.W <= 32)) && !tc_wire) ? 1 : 0;
+      d.slice_h = wr.slice_h ? 1 : 0;
       if (layout == NEGF_LAYOUT_TWO_LEVEL) tab_off = (tab_off + 3) & ~3ull;   // level 2: 32-byte aligned
       d.tab_off = tab_off;
       d.wt_off = wt_off;
@@ -529,9 +540,12 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
       P.max_L = std::max(P.max_L, wr.L);
       P.max_K = std::max(P.max_K, (int)K);
     }
-    wire_off += 2 * (uint64_t)n;
+    // onsite, eta, then (multi-orbital slices) the block h and its eigenvalues: W (W + 1) is
+    // even, so onsite_off / 2 still indexes each wire's own FP32 copy of eta
+    wire_off += 2 * (uint64_t)n + (wr.slice_h ? (uint64_t)wr.W * (wr.W + 1) : 0);
     phi_off += (uint32_t)(wr.W * wr.W);
     P.wire_task0.push_back((int32_t)P.tasks.size());
+    if (wr.slice_h) P.any_slice_h = true;
   }
   for (TaskDesc& d : P.tasks)
     if (d.layout == NEGF_LAYOUT_TWO_LEVEL) d.l1w_off += wt_off;
@@ -691,16 +705,24 @@ negf_status setup_batch(negf_ctx ctx, cudaStream_t s, const negf_wire* wires, in
   uint64_t off = 0;
   for (int w = 0; w < n_wires; ++w) {
     const int64_t n = (int64_t)wires[w].W * wires[w].L;
+    const int64_t hw = wires[w].slice_h ? (int64_t)wires[w].W * wires[w].W : 0;
     if (dev_in) {
       CUDA_TRY(ctx, cudaMemcpyAsync(q.d_wire + off, wires[w].onsite, sizeof(double) * n,
                                     cudaMemcpyDeviceToDevice, s));
       CUDA_TRY(ctx, cudaMemcpyAsync(q.d_wire + off + n, wires[w].eta, sizeof(double) * n,
                                     cudaMemcpyDeviceToDevice, s));
+      if (hw)
+        CUDA_TRY(ctx, cudaMemcpyAsync(q.d_wire + off + 2 * n, wires[w].slice_h,
+                                      sizeof(double) * hw, cudaMemcpyDeviceToDevice, s));
     } else {
       stage.insert(stage.end(), wires[w].onsite, wires[w].onsite + n);
       stage.insert(stage.end(), wires[w].eta, wires[w].eta + n);
+      if (hw) {
+        stage.insert(stage.end(), wires[w].slice_h, wires[w].slice_h + hw);
+        stage.insert(stage.end(), (size_t)wires[w].W, 0.0);      // eigenvalues, set on device
+      }
     }
-    off += 2 * n;
+    off += 2 * n + (hw ? hw + wires[w].W : 0);
   }
   if (!dev_in && off > 0) {
     CUDA_TRY(ctx, cudaMemcpyAsync(q.d_wire, stage.data(), sizeof(double) * off,
@@ -711,6 +733,12 @@ negf_status setup_batch(negf_ctx ctx, cudaStream_t s, const negf_wire* wires, in
     if (dev_in) {
       ProfScope ps(ctx, "validate_kernel", 2, s);
       CUDA_TRY(ctx, negf::launch_validate(q.d_tasks, nt, q.d_wire, q.d_err, s));
+    }
+    if (P.any_slice_h) {
+      ProfScope ps(ctx, "slice_modes_kernel", 1, s);
+      CUDA_TRY(ctx, negf::launch_slice_modes(q.d_tasks, nt, P.max_W, q.d_wire, q.d_phi,
+                                             reinterpret_cast<float*>(q.d_phi + P.phi_total),
+                                             q.d_err, s));
     }
     ProfScope ps(ctx, "lead_modes_kernel", 1, s);
     CUDA_TRY(ctx, negf::launch_lead_modes(q.d_tasks, nt, P.max_W, q.d_wire, q.d_phi,
@@ -2074,7 +2102,8 @@ struct negf_plan_s {
   uint64_t* h_ring = nullptr;                // pinned staging of the run parameters
   std::vector<cudaEvent_t> ring_ev;
   unsigned ring_next = 0;
-  std::vector<const double*> src_onsite, src_eta;
+  std::vector<const double*> src_onsite, src_eta, src_slice_h;
+  std::vector<int32_t> wire_W;
   std::vector<int64_t> wire_n;               // sites per wire
   negf_run_opts run{};
   double mu_p = 0.0, mu_q = 0.0, kT = 0.0;
@@ -2185,13 +2214,23 @@ negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
                                     cudaMemcpyDeviceToDevice, s));
       CUDA_TRY(ctx, cudaMemcpyAsync(q.d_wire + off + n, p->src_eta[w], sizeof(double) * n,
                                     cudaMemcpyDeviceToDevice, s));
-      off += 2 * (uint64_t)n;
+      const int64_t W = p->wire_W[w];
+      if (p->src_slice_h[w])
+        CUDA_TRY(ctx, cudaMemcpyAsync(q.d_wire + off + 2 * n, p->src_slice_h[w],
+                                      sizeof(double) * W * W, cudaMemcpyDeviceToDevice, s));
+      off += 2 * (uint64_t)n + (p->src_slice_h[w] ? (uint64_t)W * (W + 1) : 0);
     }
   }
   if (nt == 0) return NEGF_OK;
   if (p->dev_in) {
     SegScope sg(p, "validate_kernel", 2, s, timed);
     CUDA_TRY(ctx, negf::launch_validate(q.d_tasks, nt, q.d_wire, q.d_err, s));
+  }
+  if (P.any_slice_h) {
+    SegScope sg(p, "slice_modes_kernel", 1, s, timed);
+    CUDA_TRY(ctx, negf::launch_slice_modes(q.d_tasks, nt, P.max_W, q.d_wire, q.d_phi,
+                                           reinterpret_cast<float*>(q.d_phi + P.phi_total),
+                                           q.d_err, s));
   }
   {
     SegScope sg(p, "lead_modes_kernel", 1, s, timed);
@@ -2464,9 +2503,11 @@ negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wir
   const int nt = (int)P.tasks.size();
   for (int w = 0; w < n_wires; ++w) {
     p->wire_n.push_back((int64_t)wires[w].W * wires[w].L);
+    p->wire_W.push_back(wires[w].W);
     if (p->dev_in) {
       p->src_onsite.push_back(wires[w].onsite);
       p->src_eta.push_back(wires[w].eta);
+      p->src_slice_h.push_back(wires[w].slice_h);
     }
   }
   if ((!ctx->walk_stream &&

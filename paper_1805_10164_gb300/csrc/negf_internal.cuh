@@ -42,7 +42,8 @@ struct TaskDesc {
   uint64_t l1w_off;      // two-level: level-1 weights [rows][L + 2] in the weights array
   uint64_t edge_off;     // fused: slice-0 and slice-(L-1) blocks [L + 2][2][W][W] complex64
   int32_t cta_chain;     // block columns by a CTA-wide FP32 kernel (W = 64 or 16 < W <= 32)
-  int32_t pad_;
+  int32_t slice_h;       // multi-orbital slice block: h [W][W] at onsite + 2n, then the
+                         // eigenvalues of h [W] (written on the device) at onsite + 2n + W^2
 };
 
 // u32 words of one level-2 block of a two-level table (slice of W sites): one octet of 31-bit
@@ -99,6 +100,10 @@ __host__ __device__ inline cf cdiv(cf a, cf b) {
 // Launchers (each returns the cudaError_t of its launch).
 // Per wire: transverse modes phi (FP64 and FP32 copies, [W][W] at phi_off) and an FP32 copy of
 // eta ([n] at onsite_off / 2); per task: lead eigen self-energies.
+// Eigenvectors and eigenvalues of the multi-orbital slice blocks (k_slice.cu): phi (FP64 and
+// FP32) and eps after each block in the wire data; before launch_lead_modes.
+cudaError_t launch_slice_modes(const TaskDesc* d_tasks, int n_tasks, int max_W, double* d_wire,
+                               double* d_phi, float* d_phi32, int32_t* d_err, cudaStream_t s);
 cudaError_t launch_lead_modes(const TaskDesc* d_tasks, int n_tasks, int max_W,
                               const double* d_wire, double* d_phi, float* d_phi32,
                               float* d_eta32, cd* d_sig, double* d_gam, int32_t* d_err,

@@ -58,10 +58,18 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
   if (n > NEGF_MAX_SITES) return NEGF_E_INVALID;
   for (int64_t i = 0; i < n; ++i)
     if (!isfinite(wr.onsite[i]) || !isfinite(wr.eta[i]) || !(wr.eta[i] >= 0.0)) return NEGF_E_INVALID;
+  if (wr.slice_h)
+    for (int a = 0; a < wr.W; ++a)
+      for (int b = 0; b < wr.W; ++b)
+        if (!isfinite(wr.slice_h[a * wr.W + b]) ||
+            wr.slice_h[a * wr.W + b] != wr.slice_h[b * wr.W + a])
+          return NEGF_E_INVALID;
+  const int64_t hw = wr.slice_h ? (int64_t)wr.W * (wr.W + 1) : 0;   // block, then eigenvalues
   const int nt = wr.n_energy;
   for (int k = 0; k < nt; ++k) {
     if (!isfinite(wr.energy[k])) return NEGF_E_INVALID;
-    if (wr.lead_model == NEGF_LEAD_STRIP && band_edge(wr.energy[k], wr.W, wr.t)) return NEGF_E_INVALID;
+    if (wr.lead_model == NEGF_LEAD_STRIP && !wr.slice_h && band_edge(wr.energy[k], wr.W, wr.t))
+      return NEGF_E_INVALID;
   }
   // block columns as negf_build_tables takes them: FP32 wires of W = 64 or 16 < W <= 32 on the
   // CTA-wide chains (jobs listed here), every other wire on the warp-per-column chains
@@ -72,7 +80,7 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
   const size_t per_task_tab = (size_t)rows * K;
   size_t off = 0;
   const size_t o_tasks = off;  off += align256(sizeof(TaskDesc) * nt);
-  const size_t o_wire = off;   off += align256(sizeof(double) * 2 * n);
+  const size_t o_wire = off;   off += align256(sizeof(double) * (2 * n + hw));
   const size_t o_sig = off;    off += align256(sizeof(cd) * nt * wr.W);
   const size_t o_gam = off;    off += align256(sizeof(double) * nt * wr.W);
   const size_t cb = negf::block_bytes(prec);      // bytes per complex block element
@@ -116,6 +124,7 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
     d.t = wr.t;
     d.w_E = 1.0;                 // quadrature weights play no part in the tables
     d.cta_chain = cta ? 1 : 0;
+    d.slice_h = wr.slice_h ? 1 : 0;
     d.gamma_lead = wr.gamma_lead;
     d.tab_off = (uint64_t)k * per_task_tab;
     d.wt_off = d.tab_off;
@@ -164,6 +173,11 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
     e = cudaMemcpyAsync(d_wire, wr.onsite, sizeof(double) * n, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(d_wire + n, wr.eta, sizeof(double) * n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && wr.slice_h)
+    e = cudaMemcpyAsync(d_wire + 2 * n, wr.slice_h, sizeof(double) * wr.W * wr.W,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && wr.slice_h)
+    e = negf::launch_slice_modes(d_tasks, nt, wr.W, d_wire, d_phi, d_phi32, d_err, s);
   if (e == cudaSuccess)
     e = negf::launch_lead_modes(d_tasks, nt, wr.W, d_wire, d_phi, d_phi32, d_eta32, d_sig, d_gam,
                                 d_err, s);

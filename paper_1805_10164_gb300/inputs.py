@@ -21,6 +21,7 @@ class Wire:
     energy_weight: np.ndarray   # [n_energy] float64 quadrature weights
     lead_model: int = 0
     gamma_lead: float = 0.0
+    slice_h: np.ndarray = None  # [W, W] multi-orbital slice block (None: square lattice)
 
 
 @dataclass
@@ -129,3 +130,85 @@ def small_wire(seed, W, L, n_energy=3, eta=0.1, disorder=1.0, t=1.0, e_lo=-2.9, 
     rng = np.random.default_rng(seed)
     E, wE = midpoint_grid(e_lo, e_hi, n_energy)
     return random_wire(rng, W, L, t, disorder, eta, E, wE, lead_model, gamma_lead)
+
+
+# ---------------------------------------------------------------- multi-orbital slices, k-points
+
+# Synthetic sp3-like parameters (units of the slice-to-slice hopping t): onsite energies of the
+# s, px, py, pz orbitals (the p levels split so that no two slice modes are degenerate) and the
+# two-centre couplings of neighbouring atoms along the slice (ss sigma, sp sigma, pp sigma,
+# pp pi).  The paper's CdTe parameters are not available.
+SP3 = dict(Es=-1.0, Epx=1.2, Epy=1.5, Epz=1.8, ss=-0.6, sp=0.5, pps=0.7, ppp=-0.25)
+
+
+def sp3_slice(n_atoms, params=None):
+    """[4 n_atoms, 4 n_atoms] block of a slice: n_atoms atoms in a row along y, orbitals
+    (s, px, py, pz) per atom (index 4 a + orbital); neighbouring atoms coupled by the
+    two-centre blocks of the bond direction y (direction cosines (0, 1, 0))."""
+    p = dict(SP3, **(params or {}))
+    W = 4 * n_atoms
+    h = np.zeros((W, W))
+    for a in range(n_atoms):
+        o = 4 * a
+        h[o, o], h[o + 1, o + 1], h[o + 2, o + 2], h[o + 3, o + 3] = (
+            p["Es"], p["Epx"], p["Epy"], p["Epz"])
+        if a + 1 < n_atoms:
+            q = o + 4
+            blk = np.zeros((4, 4))
+            blk[0, 0] = p["ss"]
+            blk[0, 2] = p["sp"]          # s on a, py on a + 1
+            blk[2, 0] = -p["sp"]         # py on a, s on a + 1
+            blk[1, 1] = p["ppp"]
+            blk[2, 2] = p["pps"]
+            blk[3, 3] = p["ppp"]
+            h[o:o + 4, q:q + 4] = blk
+            h[q:q + 4, o:o + 4] = blk.T
+    return h
+
+
+def sp3_wire(seed, n_atoms, L, n_energy=3, eta=0.1, disorder=0.5, t=1.0, e_lo=-2.5, e_hi=3.5,
+             lead_model=0, gamma_lead=0.0, params=None):
+    """Multi-orbital wire: the sp3-like slice block on every slice (W = 4 n_atoms orbitals),
+    onsite disorder U[-disorder, disorder] per orbital, Buttiker rate eta per orbital,
+    orbital-diagonal hopping -t between slices."""
+    rng = np.random.default_rng(seed)
+    E, wE = midpoint_grid(e_lo, e_hi, n_energy)
+    w = random_wire(rng, 4 * n_atoms, L, t, disorder, eta, E, wE, lead_model, gamma_lead)
+    w.slice_h = sp3_slice(n_atoms, params)
+    return w
+
+
+def film_kpoints(w, t_z, n_k):
+    """A film periodic along z (period one slice cross-section; hopping -t_z between the same
+    orbital of z-neighbours, t_z a scalar or one value per orbital): its Bloch Hamiltonian at
+    k_j = 2 pi j / n_k, leads included, is the wire's with the slice block shifted by
+    diag(-2 t_z cos k_j).  Returns one wire per k-point, energy weights divided by n_k (the
+    k-average), for the batch."""
+    h0 = w.slice_h
+    if h0 is None:                      # the square-lattice cross-section as a slice block
+        h0 = np.zeros((w.W, w.W))
+        for a in range(w.W - 1):
+            h0[a, a + 1] = h0[a + 1, a] = -w.t
+    tz = np.broadcast_to(np.asarray(t_z, dtype=np.float64), (w.W,))
+    out = []
+    for j in range(n_k):
+        hk = h0 + np.diag(-2.0 * tz * np.cos(2.0 * np.pi * j / n_k))
+        out.append(Wire(W=w.W, L=w.L, t=w.t, onsite=w.onsite, eta=w.eta, energy=w.energy,
+                        energy_weight=w.energy_weight / n_k, lead_model=w.lead_model,
+                        gamma_lead=w.gamma_lead, slice_h=hk))
+    return out
+
+
+def film_slab_slice(slice_h, n_z, t_z):
+    """The slice block of the same film in real space over n_z periods along z (periodic):
+    n_z copies of slice_h (index z W + a) with -t_z between the same orbital of z-neighbours."""
+    W = slice_h.shape[0]
+    h = np.kron(np.eye(n_z), slice_h)
+    for z in range(n_z):
+        z2 = (z + 1) % n_z
+        if z2 == z:
+            continue
+        for a in range(W):
+            h[z * W + a, z2 * W + a] += -t_z
+            h[z2 * W + a, z * W + a] += -t_z
+    return h

@@ -34,7 +34,8 @@ class negf_wire(C.Structure):
     _fields_ = [("W", C.c_int32), ("L", C.c_int32), ("t", C.c_double),
                 ("onsite", C.c_void_p), ("eta", C.c_void_p), ("n_energy", C.c_int32),
                 ("energy", C.c_void_p), ("energy_weight", C.c_void_p),
-                ("lead_model", C.c_int32), ("gamma_lead", C.c_double)]
+                ("lead_model", C.c_int32), ("gamma_lead", C.c_double),
+                ("slice_h", C.c_void_p)]
 
 
 class negf_build_opts(C.Structure):
@@ -183,19 +184,21 @@ def negf_destroy(ctx):
 def _wire_array(wires, memspace, keep):
     arr = (negf_wire * max(1, len(wires)))()
     for i, w in enumerate(wires):
+        sh = getattr(w, "slice_h", None)
         if memspace == "host":
             on = np.ascontiguousarray(w.onsite, dtype=np.float64).reshape(-1)
             et = np.ascontiguousarray(w.eta, dtype=np.float64).reshape(-1)
             E = np.ascontiguousarray(w.energy, dtype=np.float64).reshape(-1)
             wE = None if w.energy_weight is None else np.ascontiguousarray(
                 w.energy_weight, dtype=np.float64).reshape(-1)
+            sh = None if sh is None else np.ascontiguousarray(sh, dtype=np.float64).reshape(-1)
         else:
-            on, et, E, wE = (t.contiguous() if t is not None else None
-                             for t in (w.onsite, w.eta, w.energy, w.energy_weight))
-        keep.extend([on, et, E, wE])
+            on, et, E, wE, sh = (t.contiguous() if t is not None else None
+                                 for t in (w.onsite, w.eta, w.energy, w.energy_weight, sh))
+        keep.extend([on, et, E, wE, sh])
         arr[i] = negf_wire(int(w.W), int(w.L), float(w.t), _ptr(on), _ptr(et), int(len(E)),
                            _ptr(E), _ptr(wE), int(getattr(w, "lead_model", 0)),
-                           float(getattr(w, "gamma_lead", 0.0)))
+                           float(getattr(w, "gamma_lead", 0.0)), _ptr(sh))
     return arr
 
 
@@ -381,9 +384,11 @@ def negf_build_tables_noalloc(wire, precision, stream, d_alias, d_mode_alias, d_
     on = np.ascontiguousarray(wire.onsite, dtype=np.float64).reshape(-1)
     et = np.ascontiguousarray(wire.eta, dtype=np.float64).reshape(-1)
     E = np.ascontiguousarray(wire.energy, dtype=np.float64).reshape(-1)
+    sh = getattr(wire, "slice_h", None)
+    sh = None if sh is None else np.ascontiguousarray(sh, dtype=np.float64).reshape(-1)
     w = negf_wire(int(wire.W), int(wire.L), float(wire.t), _ptr(on), _ptr(et), int(len(E)),
                   _ptr(E), None, int(getattr(wire, "lead_model", 0)),
-                  float(getattr(wire, "gamma_lead", 0.0)))
+                  float(getattr(wire, "gamma_lead", 0.0)), _ptr(sh))
     handle = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
     return load().negf_build_tables_noalloc(C.byref(w), PRECISION[precision], C.c_void_p(handle),
                                             _ptr(d_alias), _ptr(d_mode_alias), _ptr(d_c))

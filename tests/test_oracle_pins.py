@@ -456,8 +456,8 @@ def test_pins_catch_a_dropped_scattering_term(monkeypatch):
     """Plant a mistake in the oracle (drop Sigma_s from G): the sum-rule pin must fail."""
     orig = wire.green_retarded
 
-    def broken(E, onsite, eta, t, lead_model=0, gamma_lead=0.0):
-        g = orig(E, onsite, np.zeros_like(np.asarray(eta)), t, lead_model, gamma_lead)
+    def broken(E, onsite, eta, t, lead_model=0, gamma_lead=0.0, slice_h=None):
+        g = orig(E, onsite, np.zeros_like(np.asarray(eta)), t, lead_model, gamma_lead, slice_h)
         g["gamma"] = np.asarray(eta, dtype=np.float64).reshape(-1)
         return g
 

@@ -64,7 +64,9 @@ def test_noalloc_build_matches_allocating_build():
         cases = [(inputs.small_wire(65, W=24, L=5, n_energy=3, eta=0.06), "fp32"),
                  (inputs.small_wire(66, W=64, L=3, n_energy=2, eta=0.05, disorder=0.5), "fp32"),
                  (inputs.small_wire(61, W=6, L=12, n_energy=5, eta=0.08), "fp32"),
-                 (inputs.small_wire(62, W=3, L=5, n_energy=2, eta=0.2), "fp64")]
+                 (inputs.small_wire(62, W=3, L=5, n_energy=2, eta=0.2), "fp64"),
+                 # a multi-orbital slice block (its modes from the device eigensolver)
+                 (inputs.sp3_wire(67, 3, 4, n_energy=2, eta=0.1), "fp32")]
         for wire, prec in cases:
             n_e, W, L = len(wire.energy), wire.W, wire.L
             n = W * L
