@@ -82,7 +82,8 @@ MEASURED_TRAFFIC = {
     ("chain_cta_kernel", "wire_W64_L1000_eta0.005_256E", "7a863ab2ab935cf2"): 4565932748800,
     ("two_level_kernel", "wire_W64_L1000_eta0.005_256E", "5d548d12518c95ef"): 9015689600000,
 }
-TRAFFIC_SOURCES = {"walk_kernel": ["k_walk.cu", "philox.cuh"], "chain_cta_kernel": ["k_chain_cta.cu"],
+TRAFFIC_SOURCES = {"walk_kernel": ["k_walk.cu", "philox.cuh"],
+                   "chain_cta_kernel": ["k_chain_cta.cu", "level2.cuh"],
                    "two_level_kernel": ["k_alias.cu"]}
 
 

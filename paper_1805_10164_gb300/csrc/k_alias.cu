@@ -26,6 +26,7 @@
 #include <math.h>
 
 #include "alias_small.cuh"
+#include "level2.cuh"
 #include "negf_internal.cuh"
 
 namespace negf {
@@ -356,8 +357,6 @@ __global__ void alias_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
 // in 4-byte words), and the chunk's blocks (32 consecutive blocks of the row) leave by coalesced
 // stores.
 constexpr int kL2Warps = 4;
-constexpr uint32_t kCdfOne = 1u << 31;
-__device__ __forceinline__ float pow2f_l2(int e) { return __int_as_float((e + 127) << 23); }
 
 // Region pitch in 4-byte words: holds W weights of type R and a block of B2 words; odd for
 // 4-byte accesses, 2 mod 4 for 8-byte ones (conflict-free across a half-warp).
@@ -377,37 +376,9 @@ __device__ __forceinline__ bool level2_block(uint32_t* reg, int W, int B2, R* to
   bool ok = true;
   R tot = 0;
   if constexpr (sizeof(R) == 4) {
-    float S = 0.f;
-#pragma unroll
-    for (int a = 0; a < WB; ++a)
-      if (a < W) S += wk[a];
-    if (!(S >= 0.f && S < INFINITY)) ok = false;
-    if (S > 0.f && S < INFINITY) {
-      int e = 0;
-      frexpf(S, &e);                             // S = f 2^e, f in [1/2, 1)
-      const int sh = 30 - e, sh1 = sh / 2, sh2 = sh - sh / 2;
-      const float p1 = pow2f_l2(sh1), p2 = pow2f_l2(sh2);
-      uint32_t T = 0;
-#pragma unroll
-      for (int a = 0; a < WB; ++a) {
-        const float v = a < W ? wk[a] : 0.f;
-        const uint32_t m = v > 0.f ? __float2uint_rz((v * p1) * p2) : 0u;
-        c[a] = m;
-        T += m;
-      }
-      tot = (__uint2float_rn(T) * pow2f_l2(-sh1)) * pow2f_l2(-sh2);
-      const uint64_t Rr = (1ull << 62) / (uint64_t)T;   // T >= 2^29 - W
-      uint32_t P = 0;
-#pragma unroll
-      for (int a = 0; a < WB; ++a) {
-        P += c[a];
-        const uint32_t q = (uint32_t)(((uint64_t)P * Rr) >> 31);
-        c[a] = P == T ? kCdfOne : min(q, kCdfOne - 1u);
-      }
-    } else {
-#pragma unroll
-      for (int a = 0; a < WB; ++a) c[a] = kCdfOne;
-    }
+    float t32 = 0.f;
+    ok = level2_fp32<WB>([&](int a) { return wk[a]; }, W, c, &t32);
+    tot = t32;
   } else {
     double S = 0.0;
 #pragma unroll
@@ -456,7 +427,7 @@ __global__ void __launch_bounds__(32 * kL2Warps) level2_cdf_kernel(
     if (tasks[mid].row_base <= job) lo = mid; else hi = mid - 1;
   }
   const TaskDesc& d = tasks[lo];
-  if (d.layout != NEGF_LAYOUT_TWO_LEVEL) return;
+  if (d.layout != NEGF_LAYOUT_TWO_LEVEL || d.l2_fused) return;   // fused: written by the chain
   const int row = (int)(job - d.row_base);
   if (row >= d.rows) return;
   const int W = d.W, L = d.L, n = d.n;

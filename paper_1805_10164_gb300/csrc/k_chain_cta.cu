@@ -15,9 +15,16 @@
 // (G Phi_R)_k of the lead-R injection column gives the lead-R weights of the rows of slice k:
 // <psi|Gamma_R|psi> = sum_nu Gamma_nu |(Phi_R^T G_{L-1,k})_{nu a}|^2 = sum_nu Gamma_nu
 // |(G Phi_R)_k[a][nu]|^2.  Every weight is written by exactly one job.
+//
+// Two-level tables of W = 64 (l2_fused): each step's blocks are the 64 weights of a (row,
+// slice) pair, exactly what a level-2 block of a two-level table draws from, so the kernel
+// writes the block (level2.cuh: the inverse-CDF thresholds of the slice, the same arithmetic
+// as the level-2 pass) and the slice's level-1 weight instead of the weights: the rows x K
+// weights are never stored or read back.
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "level2.cuh"
 #include "negf_internal.cuh"
 
 namespace negf {
@@ -28,12 +35,20 @@ constexpr int kN = 2 * kW;                    // two columns side by side
 constexpr int kThreads = 256;
 constexpr int kWtPitch = kW + 1;              // padded row of the weight staging
 constexpr size_t kSmem = sizeof(cf) * (kW * kW + 2 * kW * kN) + sizeof(float) * kN * kWtPitch;
+constexpr int kB2 = 8 + kW;                   // level-2 block of a 64-site slice: guide + octets
+
+// eta |G|^2 with every rounding explicit, so that the weight of a (row, site) pair has the same
+// bits wherever it is formed (stored weights, or a level-2 block built in the kernel)
+__device__ __forceinline__ float wsq(float e, cf v) {
+  return __fmul_rn(e, __fadd_rn(__fmul_rn(v.x, v.x), __fmul_rn(v.y, v.y)));
+}
 
 __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
     const TaskDesc* __restrict__ tasks, const TcJob* __restrict__ jobs,
     const float* __restrict__ eta32, const float* __restrict__ phi32,
     const double* __restrict__ gam, const cf* __restrict__ gL, const cf* __restrict__ gR,
-    const cf* __restrict__ start, float* __restrict__ weights) {
+    const cf* __restrict__ start, float* __restrict__ weights, uint64_t* __restrict__ tab,
+    int32_t* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char smem[];
   cf* Gs = reinterpret_cast<cf*>(smem);                    // [a][c]; also Phi at the edges
   cf* Xa = Gs + kW * kW;                                   // [c][b'] ping
@@ -51,8 +66,21 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
   const float* eta = eta32 + d.onsite_off / 2;
   const cf* gsrc = (dir == 0 ? gL : gR) + d.g_off;
   float* wt = weights + d.wt_off;
+  const bool fused = d.l2_fused != 0;
+  float* l1 = weights + d.l1w_off;                         // fused: level-1 weights [rows][L+2]
+  uint32_t* l2 = reinterpret_cast<uint32_t*>(tab + d.tab_off);   // fused: [rows][L][kB2]
+  bool bad = false;
   auto row_of = [&](int y, int b) -> uint64_t {
     return y < L ? (uint64_t)y * kW + b : (uint64_t)n + (uint64_t)(y - L) * kW + b;
+  };
+  // fused: the level-2 block and level-1 weight of (row, slice) from the 64 weights wrow[0..63]
+  auto put_block = [&](uint64_t row, int slice, const float* wrow) {
+    uint32_t c[kW];
+    float tot = 0.f;
+    bad |= !level2_fp32<kW>([&](int a) { return wrow[a]; }, kW, c, &tot);
+    uint32_t* dst = l2 + (row * L + slice) * kB2;
+    level2_pack4<kW>(c, kW, [&](int i, uint4 v) { *reinterpret_cast<uint4*>(dst + i) = v; });
+    l1[row * (L + 2) + slice] = tot;
   };
   // start block of column slot col into X[:, col*64 .. col*64+63]
   auto load_start = [&](cf* X, int col) {
@@ -66,15 +94,18 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
   auto emit = [&](const cf* X, int k, unsigned mask) {
     for (int i = tid; i < kN * kW; i += kThreads) {
       const int r = i % kN, a = i / kN;                    // r consecutive across threads
-      const cf v = X[a * kN + r];
-      Wt[r * kWtPitch + a] = eta[k * kW + a] * (v.x * v.x + v.y * v.y);
+      Wt[r * kWtPitch + a] = wsq(eta[k * kW + a], X[a * kN + r]);
     }
     __syncthreads();
-    for (int i = tid; i < kN * kW; i += kThreads) {
-      const int a = i % kW, r = i / kW;                    // a consecutive: coalesced rows
-      const int col = r / kW;
-      if (mask & (1u << col))
-        wt[row_of(ys[col], r % kW) * K + (uint64_t)k * kW + a] = Wt[r * kWtPitch + a];
+    if (!fused) {
+      for (int i = tid; i < kN * kW; i += kThreads) {
+        const int a = i % kW, r = i / kW;                  // a consecutive: coalesced rows
+        const int col = r / kW;
+        if (mask & (1u << col))
+          wt[row_of(ys[col], r % kW) * K + (uint64_t)k * kW + a] = Wt[r * kWtPitch + a];
+      }
+    } else if (tid < kN && (mask & (1u << (tid / kW)))) {
+      put_block(row_of(ys[tid / kW], tid % kW), k, Wt + tid * kWtPitch);   // row tid's weights
     }
     if (k == 0 || k == L - 1) {
       // lead weights: Phi (FP32) staged in Gs (free outside the product)
@@ -102,9 +133,14 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
         const int col = r / kW;
         if (mask & (1u << col)) {
           const float lw = Wt[r * kWtPitch] + Wt[r * kWtPitch + 1];
-          const uint64_t base = row_of(ys[col], r % kW) * K + n;
-          if (k == 0) wt[base] = lw;
-          if (k == L - 1) wt[base + 1] = lw;
+          const uint64_t row = row_of(ys[col], r % kW);
+          if (fused) {
+            if (k == 0) l1[row * (L + 2) + L] = lw;
+            if (k == L - 1) l1[row * (L + 2) + L + 1] = lw;
+          } else {
+            if (k == 0) wt[row * K + n] = lw;
+            if (k == L - 1) wt[row * K + n + 1] = lw;
+          }
         }
       }
     }
@@ -179,18 +215,35 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
       for (int j = 0; j < 8; ++j) Xn[(ty + 16 * i) * kN + tx + 16 * j] = cf{accr[i][j], acci[i][j]};
     __syncthreads();
     if (active) emit(Xn, k, active);
+    if (dir == 0 && fused) {
+      // rows (k, a) towards the site columns' start slices y: their level-2 blocks of slice y
+      // from the weights eta_{y,b} |G_{k,y}[a][b]|^2, staged (pitch 65) for the per-row build
+      unsigned tmask = 0;
+      for (int col = 0; col < 2; ++col)
+        if ((active & (1u << col)) && ys[col] < L) tmask |= 1u << col;
+      if (tmask) {
+        for (int i = tid; i < kN * kW; i += kThreads) {
+          const int r = i / kW, b = i % kW, col = r / kW;
+          if (tmask & (1u << col))
+            Wt[r * kWtPitch + b] = wsq(eta[ys[col] * kW + b], Xn[(r % kW) * kN + col * kW + b]);
+        }
+        __syncthreads();
+        if (tid < kN && (tmask & (1u << (tid / kW))))
+          put_block((uint64_t)k * kW + tid % kW, ys[tid / kW], Wt + tid * kWtPitch);
+        __syncthreads();
+      }
+    }
     if (dir == 0) {
       for (int col = 0; col < 2; ++col) {
         if (!(active & (1u << col))) continue;
         const int y = ys[col];
-        if (y < L) {
+        if (y < L && !fused) {
           // rows (k, a) towards the column's start slice m = y: eta_{m,b} |G_{k,m}[a][b]|^2
           const float* em = eta + y * kW;
           float* dst = wt + (uint64_t)k * kW * K + (uint64_t)y * kW;
           for (int i = tid; i < kW * kW; i += kThreads) {
             const int a = i / kW, b = i % kW;               // b consecutive: coalesced rows
-            const cf v = Xn[a * kN + col * kW + b];
-            dst[(uint64_t)a * K + b] = em[b] * (v.x * v.x + v.y * v.y);
+            dst[(uint64_t)a * K + b] = wsq(em[b], Xn[a * kN + col * kW + b]);
           }
         } else if (y == L + 1) {
           // lead-R weights of the rows of slice k from (G Phi_R)_k: four threads per row
@@ -203,7 +256,10 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
           }
           part += __shfl_xor_sync(0xffffffffu, part, 1);
           part += __shfl_xor_sync(0xffffffffu, part, 2);
-          if (q == 0) wt[(uint64_t)(k * kW + a) * K + n + 1] = part;
+          if (q == 0) {
+            if (fused) l1[(uint64_t)(k * kW + a) * (L + 2) + L + 1] = part;
+            else wt[(uint64_t)(k * kW + a) * K + n + 1] = part;
+          }
         }
       }
     }
@@ -211,6 +267,7 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
     Xc = Xn;
     Xn = tmp;
   }
+  if (__syncthreads_or(bad) && tid == 0) atomicOr(err, ERR_NONFINITE);
 }
 
 // ---- 16 < W <= 32: the same recursion with the pair's 2W columns side by side --------------
@@ -424,7 +481,8 @@ __global__ void __launch_bounds__(kNThreads, 4) chain_cta_narrow_kernel(
 cudaError_t launch_chain_cta(const TaskDesc* d_tasks, const TcJob* d_jobs, uint32_t n_wide,
                              uint32_t n_narrow, const float* d_eta32, const float* d_phi32,
                              const double* d_gam, const void* d_gL, const void* d_gR,
-                             const void* d_start, void* d_weights, cudaStream_t s) {
+                             const void* d_start, void* d_weights, uint64_t* d_tab,
+                             int32_t* d_err, cudaStream_t s) {
   cudaError_t e = cudaSuccess;
   if (n_wide) {
     e = cudaFuncSetAttribute(chain_cta_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -433,7 +491,7 @@ cudaError_t launch_chain_cta(const TaskDesc* d_tasks, const TcJob* d_jobs, uint3
     chain_cta_kernel<<<n_wide, kThreads, kSmem, s>>>(
         d_tasks, d_jobs, d_eta32, d_phi32, d_gam, static_cast<const cf*>(d_gL),
         static_cast<const cf*>(d_gR), static_cast<const cf*>(d_start),
-        static_cast<float*>(d_weights));
+        static_cast<float*>(d_weights), d_tab, d_err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

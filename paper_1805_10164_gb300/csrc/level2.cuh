@@ -1,0 +1,92 @@
+// Level-2 blocks of two-level tables: the inverse-CDF draw of a site within a slice (the paper's
+// cumulative-sum search of Step 6', in integers behind a guide).  Shared by the level-2 pass over
+// stored weights (k_alias.cu) and the CTA-wide chain that emits the blocks directly
+// (k_chain_cta.cu), so that both produce the same bits from the same FP32 weights.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace negf {
+namespace {
+
+constexpr uint32_t kCdfOne = 1u << 31;
+__device__ __forceinline__ float pow2f_l2(int e) { return __int_as_float((e + 127) << 23); }
+
+// Thresholds of one slice's W <= WB FP32 weights wt(0) .. wt(W - 1): the exact fixed-point
+// prefix c_a = floor(2^31 P_a / S) (c = 2^31 where P_a reaches the total), with the weights
+// scaled by a power of two so that their integer total T lies in [2^29, 2^31) and divided by T
+// through a 64-bit reciprocal; an empty slice gives all 2^31.  *total: the slice's weight as
+// the integer total scaled back.  Returns false on a negative or non-finite sum.
+template <int WB, typename Wf>
+__device__ __forceinline__ bool level2_fp32(Wf wt, int W, uint32_t (&c)[WB], float* total) {
+  bool ok = true;
+  float tot = 0.f;
+  float S = 0.f;
+#pragma unroll
+  for (int a = 0; a < WB; ++a)
+    if (a < W) S += wt(a);
+  if (!(S >= 0.f && S < INFINITY)) ok = false;
+  if (S > 0.f && S < INFINITY) {
+    int e = 0;
+    frexpf(S, &e);                             // S = f 2^e, f in [1/2, 1)
+    const int sh = 30 - e, sh1 = sh / 2, sh2 = sh - sh / 2;
+    const float p1 = pow2f_l2(sh1), p2 = pow2f_l2(sh2);
+    uint32_t T = 0;
+#pragma unroll
+    for (int a = 0; a < WB; ++a) {
+      const float v = a < W ? wt(a) : 0.f;
+      const uint32_t m = v > 0.f ? __float2uint_rz((v * p1) * p2) : 0u;
+      c[a] = m;
+      T += m;
+    }
+    tot = (__uint2float_rn(T) * pow2f_l2(-sh1)) * pow2f_l2(-sh2);
+    const uint64_t Rr = (1ull << 62) / (uint64_t)T;   // T >= 2^29 - W
+    uint32_t P = 0;
+#pragma unroll
+    for (int a = 0; a < WB; ++a) {
+      P += c[a];
+      const uint32_t q = (uint32_t)(((uint64_t)P * Rr) >> 31);
+      c[a] = P == T ? kCdfOne : min(q, kCdfOne - 1u);
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < WB; ++a) c[a] = kCdfOne;
+  }
+  *total = tot;
+  return ok;
+}
+
+// The block of thresholds c, four words at a time (put4(word index, words)): for W > 8 an
+// 8-word guide (the last threshold of each octet but the last, then 2^31) followed by
+// ceil(W / 8) octets; for W <= 8 one octet.  The slice's last threshold and the padding of the
+// last octet are 2^31.
+template <int WB, typename Put4>
+__device__ __forceinline__ void level2_pack4(const uint32_t (&c)[WB], int W, Put4 put4) {
+  const int G = (W + 7) >> 3;
+  int base = 0;
+  if (G > 1) {
+    uint32_t g[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      constexpr int dummy = 0;
+      const int idx = 8 * q + 7 < WB ? 8 * q + 7 : dummy;
+      g[q] = (q < G - 1 && 8 * q + 7 < WB) ? c[idx] : kCdfOne;
+    }
+    put4(0, make_uint4(g[0], g[1], g[2], g[3]));
+    put4(4, make_uint4(g[4], g[5], g[6], g[7]));
+    base = 8;
+  }
+#pragma unroll
+  for (int a = 0; a < WB; a += 4) {
+    if (a < 8 * G) {
+      uint32_t v[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) v[j] = a + j < W - 1 ? c[a + j] : kCdfOne;
+      put4(base + a, make_uint4(v[0], v[1], v[2], v[3]));
+    }
+  }
+}
+
+}  // namespace
+}  // namespace negf

@@ -412,7 +412,7 @@ std::vector<TaskDesc> alias_descs(const std::vector<TaskDesc>& desc) {
 
 negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool dev_in, Plan& P,
                       int layout_opt = NEGF_LAYOUT_AUTO, bool tc = false, bool fp32 = false,
-                      bool one_level_first = false) {
+                      bool one_level_first = false, bool fuse_l2 = false) {
   if (layout_opt < NEGF_LAYOUT_AUTO || layout_opt > NEGF_LAYOUT_TWO_LEVEL)
     return fail(ctx, NEGF_E_INVALID, "unknown table layout %d", layout_opt);
   uint64_t tab_off = 0, g_off = 0, wire_off = 0, start_off = 0, green_off = 0, gphi_off = 0;
@@ -497,6 +497,8 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
       d.fused = tc_wire ? 1 : 0;
       d.cta_chain = (fp32 && (wr.W == 64 || (wr.W > 16 && wr.W <= 32)) && !tc_wire) ? 1 : 0;
       d.slice_h = wr.slice_h ? 1 : 0;
+      // W = 64 two-level tables on the CTA chain, no weights kept: the chain writes level 2
+      d.l2_fused = (fuse_l2 && d.cta_chain && wr.W == 64 && layout == NEGF_LAYOUT_TWO_LEVEL) ? 1 : 0;
       if (layout == NEGF_LAYOUT_TWO_LEVEL) tab_off = (tab_off + 3) & ~3ull;   // level 2: 32-byte aligned
       d.tab_off = tab_off;
       d.wt_off = wt_off;
@@ -516,7 +518,7 @@ negf_status make_plan(negf_ctx ctx, const negf_wire* wires, int n_wires, bool de
         tab_off += (uint64_t)rows * K;
         P.max_KA = std::max(P.max_KA, (int)K);
       }
-      wt_off += (uint64_t)rows * K;
+      if (!d.l2_fused) wt_off += (uint64_t)rows * K;
       d.g_off = g_off;
       d.mode_off = mode_off;
       d.lead_off = lead_off;
@@ -579,6 +581,7 @@ struct Wave {
   size_t n_cta_wide = 0;             // tasks first
   int cols_max_W = 0;                // widest task of the warp-per-column chains
   int two_max_W = 0;                 // widest task with two-level tables
+  bool any_two_split = false;        // two-level tasks whose level 2 comes from stored weights
   uint32_t cta_narrow() const { return (uint32_t)(tcjobs.size() - n_tc - n_cta_wide); }
 };
 
@@ -598,7 +601,7 @@ Wave make_wave(const Plan& P, int t0, int t1) {
     if (d.layout == NEGF_LAYOUT_TWO_LEVEL) w.tab = (w.tab + 3) & ~3ull;   // 32-byte aligned
     d.tab_off = w.tab;
     d.wt_off = w.wt;
-    w.wt += (uint64_t)d.rows * d.K;
+    if (!d.l2_fused) w.wt += (uint64_t)d.rows * d.K;   // fused: no rows x K weights stored
     if (d.fused) {
       d.edge_off = w.edge;
       w.edge += (uint64_t)(d.L + 2) * 2 * d.W * d.W;
@@ -615,6 +618,7 @@ Wave make_wave(const Plan& P, int t0, int t1) {
       w.l1w += (uint64_t)d.rows * (d.L + 2);
       w.any_two = true;
       w.two_max_W = std::max(w.two_max_W, d.W);
+      if (!d.l2_fused) w.any_two_split = true;
     }
     d.start_off = w.start;
     d.row_base = w.rows;
@@ -813,7 +817,7 @@ negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& 
     ProfScope ps(ctx, "chain_cta_kernel", 1, s);
     e = negf::launch_chain_cta(d_wdesc, d_tcjobs + w.n_tc, (uint32_t)w.n_cta_wide,
                                w.cta_narrow(), q.d_eta32, reinterpret_cast<const float*>(q.d_phi + P.phi_total),
-                               q.d_gam, d_gL, d_gR, d_start, d_weights, s);
+                               q.d_gam, d_gL, d_gR, d_start, d_weights, d_tab, q.d_err, s);
   }
   if (e == cudaSuccess && w.n_tc) {
     ProfScope ps(ctx, "chain_tc_kernel", 2, s);
@@ -821,7 +825,7 @@ negf_status build_wave(negf_ctx ctx, cudaStream_t s, const Plan& P, const Wave& 
                               q.d_eta32, reinterpret_cast<const float*>(q.d_phi + P.phi_total),
                               q.d_gam, d_gL, d_gR, d_start, d_weights, d_tab, d_edge, q.d_err, s);
   }
-  if (e == cudaSuccess && w.any_two) {
+  if (e == cudaSuccess && w.any_two_split) {
     ProfScope ps(ctx, "two_level_kernel", 1, s);
     e = negf::launch_two_level_split(d_wdesc, nt, w.rows, prec, d_weights, d_tab, q.d_err, s,
                                      w.two_max_W);
@@ -887,7 +891,8 @@ negf_status negf_build_tables(negf_ctx ctx, const negf_wire* wires, int32_t n_wi
   Plan P;
   // the gradient needs G itself, which only the warp-per-column chain keeps
   st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout, o.precision == NEGF_SPLIT_TF32,
-                 o.precision != NEGF_FP64 && !o.keep_green, o.keep_green != 0);
+                 o.precision != NEGF_FP64 && !o.keep_green, o.keep_green != 0,
+                 !o.keep_weights && !o.keep_green);
   if (st != NEGF_OK) return st;
   if (o.keep_green && P.any_two)
     return fail(ctx, NEGF_E_INVALID, "keep_green needs one-level tables (the gradient keeps dense G)");
@@ -1020,7 +1025,7 @@ negf_status negf_run(negf_ctx ctx, const negf_wire* wires, int32_t n_wires,
   cudaStream_t sw = ctx->walk_stream;
   Plan P;
   st = make_plan(ctx, wires, n_wires, dev_in, P, o.table_layout, o.precision == NEGF_SPLIT_TF32,
-                 o.precision != NEGF_FP64);
+                 o.precision != NEGF_FP64, false, true);
   if (st != NEGF_OK) return st;
   const int nt = (int)P.tasks.size();
   negf_tables t = new (std::nothrow) negf_tables_s;
@@ -1467,6 +1472,10 @@ negf_status negf_walk_score(negf_ctx ctx, negf_tables t, int32_t start_lead, uin
     return fail(ctx, NEGF_E_INVALID, "negf_walk_score: the tables of this handle were released");
   if (walkers_per_task > (1ull << 40))
     return fail(ctx, NEGF_E_INVALID, "negf_walk_score: walkers_per_task above 2^40");
+  for (const TaskDesc& d : t->h_tasks)
+    if (d.l2_fused)
+      return fail(ctx, NEGF_E_INVALID,
+                  "negf_walk_score: score tallies need the tables' weights (keep_weights)");
   DeviceGuard g(ctx->device);
   cudaStream_t s = ctx->stream;
   negf_tally tl = new (std::nothrow) negf_tally_s;
@@ -2269,7 +2278,8 @@ negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
                         dd, p->d_tcjobs + p->job_off[w] + wv.n_tc, (uint32_t)wv.n_cta_wide,
                         wv.cta_narrow(), q.d_eta32,
                         reinterpret_cast<const float*>(q.d_phi + P.phi_total), q.d_gam, p->d_gL,
-                        p->d_gR, p->d_start[slot], p->d_weights[slot], s));
+                        p->d_gR, p->d_start[slot], p->d_weights[slot], p->d_tab[slot],
+                        q.d_err, s));
     }
     if (wv.n_tc) {
       SegScope sg(p, "chain_tc_kernel", 2, s, timed);
@@ -2279,7 +2289,7 @@ negf_status plan_enqueue(negf_plan p, bool timed, cudaStream_t s) {
                         q.d_gam, p->d_gL, p->d_gR, p->d_start[slot], p->d_weights[slot],
                         p->d_tab[slot], p->d_edge[slot], q.d_err, s));
     }
-    if (wv.any_two) {
+    if (wv.any_two_split) {
       SegScope sg(p, "two_level_kernel", 1, s, timed);
       CUDA_TRY(ctx, negf::launch_two_level_split(dd, ntw, wv.rows, prec, p->d_weights[slot],
                                                  p->d_tab[slot], q.d_err, s, wv.two_max_W));
@@ -2373,13 +2383,14 @@ negf_status plan_autotune(negf_plan p) {
       e = negf::launch_chain_cta(dd, p->d_tcjobs + wv.n_tc, (uint32_t)wv.n_cta_wide,
                                  wv.cta_narrow(), q.d_eta32,
                                  reinterpret_cast<const float*>(q.d_phi + P.phi_total), q.d_gam,
-                                 p->d_gL, p->d_gR, p->d_start[0], p->d_weights[0], s);
+                                 p->d_gL, p->d_gR, p->d_start[0], p->d_weights[0],
+                                 p->d_tab[0], q.d_err, s);
     if (e == cudaSuccess && wv.n_tc)
       e = negf::launch_chain_tc(dd, nt0, wv.cols, p->d_tcjobs, (uint32_t)wv.n_tc,
                                 q.d_eta32, reinterpret_cast<const float*>(q.d_phi + P.phi_total),
                                 q.d_gam, p->d_gL, p->d_gR, p->d_start[0], p->d_weights[0],
                                 p->d_tab[0], p->d_edge[0], q.d_err, s);
-    if (e == cudaSuccess && wv.any_two)
+    if (e == cudaSuccess && wv.any_two_split)
       e = negf::launch_two_level_split(dd, nt0, wv.rows, prec, p->d_weights[0], p->d_tab[0],
                                        q.d_err, s, wv.two_max_W);
     return e;
@@ -2497,7 +2508,7 @@ negf_status negf_plan_create(negf_ctx ctx, const negf_wire* wires, int32_t n_wir
     return code;
   };
   st = make_plan(ctx, wires, n_wires, p->dev_in, p->P, o.table_layout,
-                 o.precision == NEGF_SPLIT_TF32, o.precision != NEGF_FP64);
+                 o.precision == NEGF_SPLIT_TF32, o.precision != NEGF_FP64, false, true);
   if (st != NEGF_OK) return bail(st);
   const Plan& P = p->P;
   const int nt = (int)P.tasks.size();

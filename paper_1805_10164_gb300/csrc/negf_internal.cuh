@@ -44,6 +44,9 @@ struct TaskDesc {
   int32_t cta_chain;     // block columns by a CTA-wide FP32 kernel (W = 64 or 16 < W <= 32)
   int32_t slice_h;       // multi-orbital slice block: h [W][W] at onsite + 2n, then the
                          // eigenvalues of h [W] (written on the device) at onsite + 2n + W^2
+  int32_t l2_fused;      // two-level, W = 64 CTA chain: the chain writes the level-2 blocks and
+                         // level-1 weights itself (no rows x K weights are stored)
+  int32_t pad_;
 };
 
 // u32 words of one level-2 block of a two-level table (slice of W sites): one octet of 31-bit
@@ -153,10 +156,13 @@ cudaError_t launch_chain_tc(const TaskDesc* d_tasks, int n_tasks, uint32_t n_col
 // CTA-wide FP32 block columns of cta_chain tasks: the Step 6' weights of every row, lead
 // weights included, as chain_kernel writes them.  Jobs as for launch_chain_tc: the n_wide jobs
 // of W = 64 tasks, then the n_narrow jobs of 16 < W <= 32 tasks.
+// d_tab, d_err: the tables and error word, for the tasks with l2_fused (W = 64 two-level),
+// whose level-2 blocks and level-1 weights the wide kernel writes itself.
 cudaError_t launch_chain_cta(const TaskDesc* d_tasks, const TcJob* d_jobs, uint32_t n_wide,
                              uint32_t n_narrow, const float* d_eta32, const float* d_phi32,
                              const double* d_gam, const void* d_gL, const void* d_gR,
-                             const void* d_start, void* d_weights, cudaStream_t s);
+                             const void* d_start, void* d_weights, uint64_t* d_tab,
+                             int32_t* d_err, cudaStream_t s);
 // Warps per CTA the alias kernel can use for rows of max_K slots (shared memory bound).
 int alias_warps_max(int max_K);
 // Two-level tasks: from the weights [rows][K] of every table row, the level-1 weights (slice

@@ -192,7 +192,7 @@ extern "C" negf_status negf_build_tables_noalloc(const negf_wire* wire, int32_t 
   if (e == cudaSuccess && cta)
     e = negf::launch_chain_cta(d_tasks, d_jobs, wr.W == 64 ? (uint32_t)jobs.size() : 0u,
                                wr.W == 64 ? 0u : (uint32_t)jobs.size(), d_eta32, d_phi32, d_gam,
-                               d_gL, d_gR, d_st, d_w, s);
+                               d_gL, d_gR, d_st, d_w, d_alias, d_err, s);
   if (e == cudaSuccess)
     e = negf::launch_alias_build(d_tasks, nt, (uint32_t)(nt * (rows + 2)), (int)K, prec, d_w,
                                  d_rs, d_mw, d_alias, d_mode_alias, d_err, s);

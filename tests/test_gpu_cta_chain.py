@@ -107,3 +107,75 @@ def test_cta_chain_walks_bit_exact(ctx, batch):
             assert np.array_equal(d_steps.cpu().numpy().astype(np.uint32), steps)
     finally:
         negf.negf_tables_free(tables)
+
+
+def _two_level_export(ctx, tables, task):
+    info = negf.negf_get_task_info(ctx, tables, task)
+    l2 = negf.negf_export_tables(ctx, tables, task, "alias")
+    l1 = negf.negf_export_tables(ctx, tables, task, "alias_level1")
+    return info, l1, l2
+
+
+def test_fused_level2_equals_stored_weights_path(ctx):
+    """W = 64 two-level tables built without kept weights take the fused path (the chain
+    writes the level-2 blocks and level-1 weights); with keep_weights the weights are stored
+    and the level-2 pass builds them.  Both must give the same bits, for single builds, the
+    batched run's waves and a captured plan, and realise the oracle's weights."""
+    wires = _wires("wide") + [inputs.small_wire(145, W=9, L=5, n_energy=1, eta=0.07)]
+    stored = negf.negf_build_tables(ctx, wires, precision="fp32", keep_weights=True,
+                                    layout="two_level")
+    fused = negf.negf_build_tables(ctx, wires, precision="fp32", layout="two_level")
+    try:
+        n_tasks = negf.negf_tables_num_tasks(fused)
+        ref = [_two_level_export(ctx, stored, k) for k in range(n_tasks)]
+        for k in range(n_tasks):
+            info, l1, l2 = _two_level_export(ctx, fused, k)
+            assert info["layout"] == "two_level"
+            assert np.array_equal(l1, ref[k][1]), k
+            assert np.array_equal(l2, ref[k][2]), k
+            assert np.array_equal(negf.negf_export_tables(ctx, fused, k, "rowsum"),
+                                  negf.negf_export_tables(ctx, stored, k, "rowsum")), k
+        # against the oracle: sampled rows' realised distributions
+        rng = np.random.default_rng(9)
+        task = 0
+        for w in wires:
+            for E in w.energy:
+                info, l1, l2 = _two_level_export(ctx, fused, task)
+                rows, L, W = info["rows"], info["L"], info["W"]
+                l1 = l1.reshape(rows, L + 2)
+                l2 = l2.view(np.uint32).reshape(rows, L, negf.level2_words(W))
+                tab = pipeline.task_reference(w.onsite, w.eta, w.t, E, w.lead_model,
+                                              w.gamma_lead, with_alias=False)["tab"]
+                rs = tab["w"].sum(1)
+                for r in rng.choice(rows, size=min(12, rows), replace=False):
+                    if rs[r] > 0:
+                        p = alias.implied_two_level(l1[r], l2[r], W)
+                        assert np.max(np.abs(p - tab["w"][r] / rs[r])) <= \
+                            (L + W + 4) * 2.0**-32 + 1e-5, (task, r)
+                task += 1
+        with pytest.raises(negf.NegfError, match="NEGF_E_INVALID"):
+            negf.negf_walk_score(ctx, fused, 0, 1, 10)      # no weights for the score seeds
+        # batched waves and a captured plan take the fused path too: same tallies as the
+        # stored-weights tables
+        N = 20000
+        tl = negf.negf_walk(ctx, stored, 0, 4242, N, walker_id_offset=3)
+        want = negf.negf_tally_counts(ctx, tl, n_tasks)
+        negf.negf_tally_free(tl)
+        for per_wave in (0, 2):
+            t, tl = negf.negf_run(ctx, wires, 0, 4242, N, precision="fp32", walker_id_offset=3,
+                                  tasks_per_wave=per_wave, layout="two_level")
+            got = negf.negf_tally_counts(ctx, tl, n_tasks)
+            negf.negf_tally_free(tl)
+            negf.negf_tables_free(t)
+            assert np.array_equal(got, want), per_wave
+        plan = negf.negf_plan_create(ctx, wires, 0, N, 3.5, -3.5, 0.025, precision="fp32",
+                                     tasks_per_wave=2, layout="two_level", autotune=False)
+        try:
+            negf.negf_plan_launch(ctx, plan, 4242, walker_id_offset=3)
+            got = negf.negf_plan_result(ctx, plan)["counts"]
+            assert np.array_equal(got, want)
+        finally:
+            negf.negf_plan_destroy(plan)
+    finally:
+        negf.negf_tables_free(stored)
+        negf.negf_tables_free(fused)

@@ -8,8 +8,10 @@ Bars (those of the parity tests):
   * alias rows (one- and two-level) realise their weights within the quantisation bound.
   * walks bit-exact against the oracle's walker on the exported tables.
   * Monte Carlo T against the direct probe solve: every |z| <= z_bar(m), sum z^2 <= chi2_bar(m).
-  * clean strip (no dephasing): every walker leaves at the other lead and T = c_p = the number
-    of open channels of the slice block (1e-10 FP64).
+  * clean strip (no dephasing, no reflection): c_p = Tr[Gamma_p G Gamma_p G^dag] + T = twice the
+    number N of open channels of the slice block (1e-10 FP64), every walker leaves on its first
+    draw, half of them at each lead (within z_bar of the binomial SE), so T = c_p n_q / N_w
+    estimates N.
   * k-points: a film's k-point wires (slice block shifted by -2 t_z cos k) in one batch equal
     the oracle per k (tables as above, T at the z bars); the current of the batch is the
     k-average.
@@ -171,17 +173,22 @@ def test_clean_multiorbital_strip_staircase(ctx):
                     energy_weight=np.ones_like(mids), slice_h=h)
     tables = negf.negf_build_tables(ctx, [w], precision="fp64")
     try:
-        tally = negf.negf_walk(ctx, tables, 0, 5, 20_000)
+        N = 200_000
+        tally = negf.negf_walk(ctx, tables, 0, 5, N)
         counts = negf.negf_tally_counts(ctx, tally, mids.size)
         res = negf.negf_current(ctx, tables, tally, 1.0, 0.0, 0.1)
         negf.negf_tally_free(tally)
+        z = []
         for k, E in enumerate(mids):
             n_open = int(np.sum(np.abs(E - eps) < 2 * t))
             c = negf.negf_get_task_info(ctx, tables, k)["c"][0]
-            assert abs(c - n_open) <= 1e-10 * max(1, n_open), (E, c, n_open)
+            assert abs(c - 2 * n_open) <= 1e-10 * max(1, n_open), (E, c, n_open)
             if n_open:
-                assert counts[k, 2] == 20_000 and counts[k, 1] == 0    # every walker crosses
-                assert abs(res["T"][k] - n_open) <= 1e-10 * n_open
+                assert counts[k, 1] + counts[k, 2] == N and counts[k, 4] == N   # one draw each
+                z.append((counts[k, 2] / N - 0.5) / np.sqrt(0.25 / N))
+                assert abs(res["T"][k] - c * counts[k, 2] / N) <= 1e-12 * c
+        z = np.asarray(z)
+        assert np.max(np.abs(z)) <= z_bar(z.size) and np.sum(z ** 2) <= chi2_bar(z.size), z
     finally:
         negf.negf_tables_free(tables)
 
