@@ -175,53 +175,59 @@ __global__ void __launch_bounds__(kAdjThreads) adj_expand_kernel(
 }
 
 // ---- block products ------------------------------------------------------------------------
-template <typename C, int RT>
+// out = A B with A a W x W block (stride W) and B a W x N panel (stride N, N <= 64): thread
+// (ty, tx) owns rows ty + 16 a (a < RT) and columns tx + 16 b (b < RTN).
+template <typename C, int RT, int RTN>
 __device__ __forceinline__ void cta_prod(const C* __restrict__ A, const C* __restrict__ B, int W,
-                                         C (&acc)[RT][RT]) {
+                                         int N, C (&acc)[RT][RTN]) {
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
   for (int a = 0; a < RT; ++a)
 #pragma unroll
-    for (int b = 0; b < RT; ++b) acc[a][b] = mkc(0.0, 0.0, C{});
-  int ra[RT], cb[RT];
+    for (int b = 0; b < RTN; ++b) acc[a][b] = mkc(0.0, 0.0, C{});
+  int ra[RT], cb[RTN];
 #pragma unroll
   for (int a = 0; a < RT; ++a) {
-    const int r = ty + 16 * a, c = tx + 16 * a;
-    ra[a] = (r < W ? r : W - 1) * W;                // clamped: rows/columns >= W are discarded
-    cb[a] = c < W ? c : W - 1;
+    const int r = ty + 16 * a;
+    ra[a] = (r < W ? r : W - 1) * W;                // clamped: rows/columns beyond are discarded
+  }
+#pragma unroll
+  for (int b = 0; b < RTN; ++b) {
+    const int c = tx + 16 * b;
+    cb[b] = c < N ? c : N - 1;
   }
   for (int l = 0; l < W; ++l) {
-    C av[RT], bv[RT];
+    C av[RT], bv[RTN];
 #pragma unroll
     for (int a = 0; a < RT; ++a) av[a] = A[ra[a] + l];
 #pragma unroll
-    for (int b = 0; b < RT; ++b) bv[b] = B[l * W + cb[b]];
+    for (int b = 0; b < RTN; ++b) bv[b] = B[l * N + cb[b]];
 #pragma unroll
     for (int a = 0; a < RT; ++a)
 #pragma unroll
-      for (int b = 0; b < RT; ++b) {
+      for (int b = 0; b < RTN; ++b) {
         acc[a][b].x += av[a].x * bv[b].x - av[a].y * bv[b].y;
         acc[a][b].y += av[a].x * bv[b].y + av[a].y * bv[b].x;
       }
   }
 }
 
-// visit this thread's valid entries (i, j) of a W x W product tile
-template <int RT, typename F>
-__device__ __forceinline__ void for_tile(int W, F f) {
+// visit this thread's valid entries (i, j) of a W x N product tile
+template <int RT, int RTN, typename F>
+__device__ __forceinline__ void for_tile(int W, int N, F f) {
   const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
 #pragma unroll
   for (int a = 0; a < RT; ++a)
 #pragma unroll
-    for (int b = 0; b < RT; ++b) {
+    for (int b = 0; b < RTN; ++b) {
       const int i = ty + 16 * a, j = tx + 16 * b;
-      if (i < W && j < W) f(a, b, i, j);
+      if (i < W && j < N) f(a, b, i, j);
     }
 }
 
 template <typename C>
-__device__ __forceinline__ void load_block(C* dst, const C* __restrict__ src, int WW) {
-  for (int idx = threadIdx.x; idx < WW; idx += blockDim.x) dst[idx] = src[idx];
+__device__ __forceinline__ void load_block(C* dst, const C* __restrict__ src, int count) {
+  for (int idx = threadIdx.x; idx < count; idx += blockDim.x) dst[idx] = src[idx];
 }
 
 struct AdjArgs {
@@ -239,10 +245,18 @@ struct AdjArgs {
   int32_t* err;
 };
 
-// One job per (task of the group, block column m); the start lead's boundary columns first
-// (they carry the injection work).  Scratch: X and Y (L W^2 each) per CTA; gl, gr, Psi
-// (L W^2) and Tl (2 W^2) per task of the group.
-template <typename C, int RT>
+// Block columns per job: NC = 64 / W of them side by side (at most 8), so that each step's
+// product is a W x (NC W) panel; the start lead's boundary column, which carries the injection
+// work, is a job of its own.
+__host__ __device__ inline int adj_ncols(int W) {
+  const int nc = 64 / W;
+  return nc < 1 ? 1 : (nc > 8 ? 8 : nc);
+}
+
+// One job per (task of the group, column set): the boundary column s_p of every task first,
+// then the other columns NC at a time in increasing order.  Scratch per CTA: X and Y
+// [L][W][NC W]; per task of the group: gl, gr, Psi [L][W][W], Tl [2][W][W].
+template <typename C, int RT, int RTN>
 __global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, const C* __restrict__ gl_all,
                                                                  const C* __restrict__ gr_all,
                                                                  C* __restrict__ psi_all,
@@ -253,9 +267,11 @@ __global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, cons
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const TaskDesc d0 = g.tasks[g.task0];
   const int W = d0.W, L = d0.L, WW = W * W, n = d0.n, K = d0.K;
-  C* sA = reinterpret_cast<C*>(smem_raw);
-  C* sB = sA + WW;
-  C* sT = sB + WW;
+  const int NC = adj_ncols(W), NP = NC * W;            // panel width
+  const int PA = WW > W * NP ? WW : W * NP;
+  C* sA = reinterpret_cast<C*>(smem_raw);              // g block / X_k panel / seeds
+  C* sB = sA + PA;                                     // the running panel
+  C* sT = sB + W * NP;                                 // Gamma_lead, Phi
   C* rowk = sT + WW;
   C* fcol = rowk + W;
   int* perm = reinterpret_cast<int*>(fcol + W);
@@ -264,13 +280,18 @@ __global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, cons
   const int sp = p == 0 ? 0 : L - 1;
   const R t = (R)d0.t;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  C* X = xs_all + (uint64_t)blockIdx.x * L * WW;
-  C* Y = ys_all + (uint64_t)blockIdx.x * L * WW;
-  const int n_jobs = g.n_group * L;
+  const int other = L - 1;                             // columns besides s_p
+  const int per_task = 1 + (other + NC - 1) / NC;
+  C* X = xs_all + (uint64_t)blockIdx.x * L * W * NP;
+  C* Y = ys_all + (uint64_t)blockIdx.x * L * W * NP;
+  const int n_jobs = g.n_group * per_task;
   for (int job = blockIdx.x; job < n_jobs; job += gridDim.x) {
-    const int tl = job % g.n_group, mm = job / g.n_group;
-    const int m = p == 0 ? mm : L - 1 - mm;
-    const bool inj = m == sp;                         // the start lead's boundary column
+    const int tl = job % g.n_group, jj = job / g.n_group;
+    const bool inj = jj == 0;                          // the start lead's boundary column
+    const int ncols = inj ? 1 : min(NC, other - (jj - 1) * NC);
+    const int first = inj ? sp : (jj - 1) * NC + (p == 0 ? 1 : 0);   // columns first .. + ncols
+    const int N = inj ? W : NP;                        // this job's panel stride
+    auto col_m = [&](int c) { return first + c; };
     const TaskDesc d = g.tasks[g.task0 + tl];
     const double* onsite = g.wire + d.onsite_off;
     const double* eta = onsite + n;
@@ -284,11 +305,13 @@ __global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, cons
     C* Psi = psi_all + (uint64_t)tl * L * WW;
     C* Tl = tl_all + (uint64_t)tl * 2 * WW;
     const uint64_t so = g.site_off0 + (uint64_t)tl * n;
-    C acc[RT][RT];
+    const uint64_t XS = (uint64_t)W * N;               // one slice of a panel
+    C acc[RT][RTN];
 
-    // ---- G_mm = (E - H_mm - Sigma_s - [leads] - t^2 g^L_{m-1} - t^2 g^R_{m+1})^{-1}
-    __syncthreads();
-    {
+    // ---- G_mm of every column: (E - H_mm - Sigma_s - [leads] - t^2 g^L_{m-1} - t^2 g^R_{m+1})^-1
+    for (int c = 0; c < ncols; ++c) {
+      const int m = col_m(c);
+      __syncthreads();
       const R tt = t * t;
       for (int idx = tid; idx < WW; idx += blockDim.x) {
         const int a = idx / W, b = idx - a * W;
@@ -302,45 +325,53 @@ __global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, cons
         if (m < L - 1) v = v - tt * gr[(uint64_t)(m + 1) * WW + idx];
         sA[idx] = v;
       }
-    }
-    __syncthreads();
-    const bool deph = slice_dephased(eta, m, W);
-    if (!cta_gj(sA, rowk, fcol, perm, flag, W, !deph)) {
-      if (tid == 0) atomicOr(g.err, ERR_SINGULAR);
-      return;
-    }
-    for (int idx = tid; idx < WW; idx += blockDim.x) {
-      sB[idx] = sA[idx];
-      X[(uint64_t)m * WW + idx] = sA[idx];
-    }
-    // ---- the block column X_k = G_{k,m}: toward slice 0, then toward slice L-1
-    for (int k = m - 1; k >= 0; --k) {
       __syncthreads();
+      const bool deph = slice_dephased(eta, m, W);
+      if (!cta_gj(sA, rowk, fcol, perm, flag, W, !deph)) {
+        if (tid == 0) atomicOr(g.err, ERR_SINGULAR);
+        return;
+      }
+      for (int idx = tid; idx < WW; idx += blockDim.x) {
+        const int a = idx / W, b = idx - a * W;
+        X[(uint64_t)m * XS + a * N + c * W + b] = sA[idx];
+      }
+    }
+    // ---- the block columns X_k = G_{k,m}: towards slice 0 (columns with m > k, each joining
+    // at k = m - 1 with G_mm), then towards slice L - 1 (columns with m < k)
+    const int m_lo = col_m(0), m_hi = col_m(ncols - 1);
+    auto inject = [&](int c, int m) {                  // panel block c <- G_mm
+      for (int idx = tid; idx < WW; idx += blockDim.x) {
+        const int a = idx / W, b = idx - a * W;
+        sB[a * N + c * W + b] = X[(uint64_t)m * XS + a * N + c * W + b];
+      }
+    };
+    for (int k = m_hi - 1; k >= 0; --k) {
+      __syncthreads();
+      for (int c = 0; c < ncols; ++c)
+        if (col_m(c) == k + 1) inject(c, col_m(c));
       load_block(sA, gl + (uint64_t)k * WW, WW);
       __syncthreads();
-      cta_prod<C, RT>(sA, sB, W, acc);
+      cta_prod<C, RT, RTN>(sA, sB, W, N, acc);
       __syncthreads();
-      for_tile<RT>(W, [&](int a, int b, int i, int j) {
+      for_tile<RT, RTN>(W, N, [&](int a, int b, int i, int j) {
         const C v = (R)(-1) * t * acc[a][b];
-        sB[i * W + j] = v;
-        X[(uint64_t)k * WW + i * W + j] = v;
+        sB[i * N + j] = v;
+        if (col_m(j / W) > k) X[(uint64_t)k * XS + i * N + j] = v;
       });
     }
-    if (m < L - 1) {
+    for (int k = m_lo + 1; k < L; ++k) {
       __syncthreads();
-      load_block(sB, X + (uint64_t)m * WW, WW);
-      for (int k = m + 1; k < L; ++k) {
-        __syncthreads();
-        load_block(sA, gr + (uint64_t)k * WW, WW);
-        __syncthreads();
-        cta_prod<C, RT>(sA, sB, W, acc);
-        __syncthreads();
-        for_tile<RT>(W, [&](int a, int b, int i, int j) {
-          const C v = (R)(-1) * t * acc[a][b];
-          sB[i * W + j] = v;
-          X[(uint64_t)k * WW + i * W + j] = v;
-        });
-      }
+      for (int c = 0; c < ncols; ++c)
+        if (col_m(c) == k - 1) inject(c, col_m(c));
+      load_block(sA, gr + (uint64_t)k * WW, WW);
+      __syncthreads();
+      cta_prod<C, RT, RTN>(sA, sB, W, N, acc);
+      __syncthreads();
+      for_tile<RT, RTN>(W, N, [&](int a, int b, int i, int j) {
+        const C v = (R)(-1) * t * acc[a][b];
+        sB[i * N + j] = v;
+        if (col_m(j / W) < k) X[(uint64_t)k * XS + i * N + j] = v;
+      });
     }
     // ---- column s_p: psi = X Phi (the injection rows' G Phi_p), the lead-column terms Tl_r of
     // the injection rows, and their contribution Cc_k = psibar_k Phi^T to U (kept in Y)
@@ -355,8 +386,8 @@ __global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, cons
         __syncthreads();
         load_block(sA, X + (uint64_t)k * WW, WW);
         __syncthreads();
-        cta_prod<C, RT>(sA, sT, W, acc);
-        for_tile<RT>(W, [&](int a, int b, int i, int j) { Psi[(uint64_t)k * WW + i * W + j] = acc[a][b]; });
+        cta_prod<C, RT, RTN>(sA, sT, W, W, acc);
+        for_tile<RT, RTN>(W, W, [&](int a, int b, int i, int j) { Psi[(uint64_t)k * WW + i * W + j] = acc[a][b]; });
       }
       // Tl_r[x][m'] = sum_nu Gamma_nu phi_nu(x) conj(z_nu^(m')), z = Phi^T psi_{s_r}
       for (int r = 0; r < 2; ++r) {
@@ -404,11 +435,11 @@ __global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, cons
           sA[i * W + mp] = to_c(mk(vx, vy), C{});
         }
         __syncthreads();
-        cta_prod<C, RT>(sA, sB, W, acc);
-        for_tile<RT>(W, [&](int a, int b, int i, int j) { Y[(uint64_t)k * WW + i * W + j] = acc[a][b]; });
+        cta_prod<C, RT, RTN>(sA, sB, W, W, acc);
+        for_tile<RT, RTN>(W, W, [&](int a, int b, int i, int j) { Y[(uint64_t)k * WW + i * W + j] = acc[a][b]; });
       }
-      // the lead broadening of the boundary slices, Gamma_lead = Phi diag(Gamma) Phi^T (real)
     }
+    // the lead broadening of the boundary slices, Gamma_lead = Phi diag(Gamma) Phi^T (real)
     __syncthreads();
     for (int idx = tid; idx < WW; idx += blockDim.x) {
       const int a = idx / W, b = idx - a * W;
@@ -416,59 +447,64 @@ __global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, cons
       for (int nu = 0; nu < W; ++nu) v += gam[nu] * phi[a * W + nu] * phi[b * W + nu];
       sT[idx] = mkc(v, 0.0, C{});
     }
-    // ---- forward elimination: y_k = g^L_k (U_k - t y_{k-1}), U_k = Gbar[k-block, m-block]
+    // ---- forward elimination: y_k = g^L_k (U_k - t y_{k-1}), U_k = Gbar[k-block, columns]
     for (int k = 0; k < L; ++k) {
       const bool edge = k == 0 || k == L - 1;
       __syncthreads();
       if (edge) {
         // lead columns of the site rows: U[x][j] += (sum_r wbar_{(m,j), n+r}) conj(Gamma_lead X_k)[x][j]
-        load_block(sA, X + (uint64_t)k * WW, WW);
+        load_block(sA, X + (uint64_t)k * XS, W * N);
         __syncthreads();
-        cta_prod<C, RT>(sT, sA, W, acc);
+        cta_prod<C, RT, RTN>(sT, sA, W, N, acc);
         __syncthreads();
-        for_tile<RT>(W, [&](int a, int b, int i, int j) { sA[i * W + j] = conj_(acc[a][b]); });
+        for_tile<RT, RTN>(W, N, [&](int a, int b, int i, int j) { sA[i * N + j] = conj_(acc[a][b]); });
         __syncthreads();
       }
-      for (int idx = tid; idx < WW; idx += blockDim.x) {
-        const int j = idx / W, i = idx - j * W;               // U_k [i][j]: row (k, i), column (m, j)
-        const double* wrow = wb + (uint64_t)(m * W + j) * K;
-        const int b = k * W + i;
-        const cd xv = widen(X[(uint64_t)k * WW + i * W + j]);
-        const double f = wrow[b] * eta[b];
-        double ux = f * xv.x, uy = -f * xv.y;
-        if (edge) {
-          double wl = 0.0;
-          if (k == 0) wl += wrow[n];
-          if (k == L - 1) wl += wrow[n + 1];
-          if (wl != 0.0) {
-            const cd tb = widen(sA[i * W + j]);
-            ux += wl * tb.x;
-            uy += wl * tb.y;
+      for (int idx = tid; idx < W * N; idx += blockDim.x) {
+        const int jj2 = idx / W, i = idx - jj2 * W;   // panel column jj2 = c W + j, row (k, i)
+        const int c = jj2 / W, j = jj2 - c * W;
+        C u = mkc(0.0, 0.0, C{});
+        if (c < ncols) {
+          const int m = col_m(c);
+          const double* wrow = wb + (uint64_t)(m * W + j) * K;
+          const int b = k * W + i;
+          const cd xv = widen(X[(uint64_t)k * XS + i * N + jj2]);
+          const double f = wrow[b] * eta[b];
+          double ux = f * xv.x, uy = -f * xv.y;
+          if (edge) {
+            double wl = 0.0;
+            if (k == 0) wl += wrow[n];
+            if (k == L - 1) wl += wrow[n + 1];
+            if (wl != 0.0) {
+              const cd tb = widen(sA[i * N + jj2]);
+              ux += wl * tb.x;
+              uy += wl * tb.y;
+            }
           }
-        }
-        if (inj) {
-          const cd cc = widen(Y[(uint64_t)k * WW + i * W + j]);
-          ux += cc.x;
-          uy += cc.y;
-          if (k == sp) {
-            // mode weights u_m' = lambda_m' <phi_m'|A|phi_m'>: i sum ubar Gamma phi phi
-            double v = 0.0;
-            for (int mp = 0; mp < W; ++mp) v += ub[mp] * gam[mp] * phi[i * W + mp] * phi[j * W + mp];
-            uy += v;
+          if (inj) {
+            const cd cc = widen(Y[(uint64_t)k * WW + i * W + j]);
+            ux += cc.x;
+            uy += cc.y;
+            if (k == sp) {
+              // mode weights u_m' = lambda_m' <phi_m'|A|phi_m'>: i sum ubar Gamma phi phi
+              double v = 0.0;
+              for (int mp = 0; mp < W; ++mp) v += ub[mp] * gam[mp] * phi[i * W + mp] * phi[j * W + mp];
+              uy += v;
+            }
           }
+          u = to_c(mk(ux, uy), C{});
         }
-        C u = to_c(mk(ux, uy), C{});
-        if (k > 0) u = u - t * sB[i * W + j];
-        sB[i * W + j] = u;
+        if (k > 0) u = u - t * sB[i * N + jj2];
+        sB[i * N + jj2] = u;
       }
       __syncthreads();
       load_block(sA, gl + (uint64_t)k * WW, WW);
       __syncthreads();
-      cta_prod<C, RT>(sA, sB, W, acc);
+      cta_prod<C, RT, RTN>(sA, sB, W, N, acc);
       __syncthreads();
-      for_tile<RT>(W, [&](int a, int b, int i, int j) {
-        sB[i * W + j] = acc[a][b];
-        Y[(uint64_t)k * WW + i * W + j] = acc[a][b];
+      for_tile<RT, RTN>(W, N, [&](int a, int b, int i, int j) {
+        sB[i * N + j] = acc[a][b];
+        Y[(uint64_t)k * XS + i * N + j] = acc[a][b];
       });
     }
     // ---- back substitution z_k = y_k - t g^L_k z_{k+1}, and the diagonal of G Gbar G
@@ -477,24 +513,28 @@ __global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, cons
         __syncthreads();
         load_block(sA, gl + (uint64_t)k * WW, WW);
         __syncthreads();
-        cta_prod<C, RT>(sA, sB, W, acc);
+        cta_prod<C, RT, RTN>(sA, sB, W, N, acc);
         __syncthreads();
-        for_tile<RT>(W, [&](int a, int b, int i, int j) {
-          sB[i * W + j] = Y[(uint64_t)k * WW + i * W + j] - t * acc[a][b];
+        for_tile<RT, RTN>(W, N, [&](int a, int b, int i, int j) {
+          sB[i * N + j] = Y[(uint64_t)k * XS + i * N + j] - t * acc[a][b];
         });
       }
       __syncthreads();
-      // site (k, a): warp per row; sum_j z[a][j] X[a][j] and the explicit gamma terms
+      // site (k, a): warp per row; sum over the columns of z[a][.] X[a][.] and the explicit
+      // gamma terms
       for (int a = warp; a < W; a += kAdjThreads / 32) {
         const int site = k * W + a;
         double zx = 0.0, zy = 0.0, ex = 0.0;
-        for (int j = lane; j < W; j += 32) {
-          const cd z = widen(sB[a * W + j]);
-          const cd x = widen(X[(uint64_t)k * WW + a * W + j]);
+        for (int jj2 = lane; jj2 < ncols * W; jj2 += 32) {
+          const int c = jj2 / W, j = jj2 - c * W;
+          const cd z = widen(sB[a * N + jj2]);
+          const cd x = widen(X[(uint64_t)k * XS + a * N + jj2]);
           zx += z.x * x.x - z.y * x.y;
           zy += z.x * x.y + z.y * x.x;
-          ex += wb[(uint64_t)(m * W + j) * K + site] * (x.x * x.x + x.y * x.y);
-          if (inj) {
+          ex += wb[(uint64_t)(col_m(c) * W + j) * K + site] * (x.x * x.x + x.y * x.y);
+        }
+        if (inj) {
+          for (int j = lane; j < W; j += 32) {
             const cd ps = widen(Psi[(uint64_t)k * WW + a * W + j]);
             ex += wb[(uint64_t)(n + p * W + j) * K + site] * (ps.x * ps.x + ps.y * ps.y);
           }
@@ -519,18 +559,47 @@ size_t gj_smem(int W) {
 }
 template <typename C>
 size_t column_smem(int W) {
-  return sizeof(C) * (size_t)(3 * W * W + 2 * W) + sizeof(int) * (size_t)(W + 2);
+  const size_t NP = (size_t)adj_ncols(W) * W;
+  const size_t PA = (size_t)W * W > W * NP ? (size_t)W * W : W * NP;
+  return sizeof(C) * (PA + W * NP + (size_t)W * W + 2 * W) + sizeof(int) * (size_t)(W + 2);
 }
 
-template <typename C, int RT>
+template <typename C, int RT, int RTN>
 cudaError_t columns_rt(const AdjArgs& a, int W, const C* gl, const C* gr, C* psi, C* tl, C* xs,
                        C* ys, int slots, cudaStream_t s) {
   const size_t smem = column_smem<C>(W);
-  cudaError_t e = cudaFuncSetAttribute(adj_column_kernel<C, RT>,
+  cudaError_t e = cudaFuncSetAttribute(adj_column_kernel<C, RT, RTN>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  adj_column_kernel<C, RT><<<slots, kAdjThreads, smem, s>>>(a, gl, gr, psi, tl, xs, ys);
+  adj_column_kernel<C, RT, RTN><<<slots, kAdjThreads, smem, s>>>(a, gl, gr, psi, tl, xs, ys);
   return cudaGetLastError();
+}
+
+// CTAs of the column kernel for width W that one SM holds (registers and shared memory)
+template <typename C, int RT, int RTN>
+int occupancy_rt(int W) {
+  const size_t smem = column_smem<C>(W);
+  if (cudaFuncSetAttribute(adj_column_kernel<C, RT, RTN>,
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 1;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj_column_kernel<C, RT, RTN>,
+                                                    kAdjThreads, smem) != cudaSuccess)
+    return 1;
+  return per_sm < 1 ? 1 : per_sm;
+}
+
+template <typename C>
+int occupancy_impl(int W) {
+  const int rt = (W + 15) / 16, rtn = (adj_ncols(W) * W + 15) / 16;
+  if (rt == 1 && rtn <= 1) return occupancy_rt<C, 1, 1>(W);
+  if (rt == 1 && rtn <= 2) return occupancy_rt<C, 1, 2>(W);
+  if (rt == 1 && rtn <= 3) return occupancy_rt<C, 1, 3>(W);
+  if (rt == 1) return occupancy_rt<C, 1, 4>(W);
+  if (rt == 2 && rtn <= 3) return occupancy_rt<C, 2, 3>(W);
+  if (rt == 2) return occupancy_rt<C, 2, 4>(W);
+  if (rt == 3) return occupancy_rt<C, 3, 3>(W);
+  return occupancy_rt<C, 4, 4>(W);
 }
 
 template <typename C>
@@ -542,18 +611,29 @@ cudaError_t columns_impl(const AdjArgs& a, int W, const void* gl, const void* gr
   C* ctl = static_cast<C*>(tl);
   C* cxs = static_cast<C*>(xs);
   C* cys = static_cast<C*>(ys);
-  switch ((W + 15) / 16) {
-    case 1: return columns_rt<C, 1>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
-    case 2: return columns_rt<C, 2>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
-    case 3: return columns_rt<C, 3>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
-    default: return columns_rt<C, 4>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
-  }
+  // RT = ceil(W / 16) row tiles; RTN = ceil(NC W / 16) column tiles of the panel (>= RT, so
+  // that the injection column's W x W products fit too)
+  const int rt = (W + 15) / 16, rtn = (adj_ncols(W) * W + 15) / 16;
+  if (rt == 1 && rtn <= 1) return columns_rt<C, 1, 1>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
+  if (rt == 1 && rtn <= 2) return columns_rt<C, 1, 2>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
+  if (rt == 1 && rtn <= 3) return columns_rt<C, 1, 3>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
+  if (rt == 1) return columns_rt<C, 1, 4>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
+  if (rt == 2 && rtn <= 3) return columns_rt<C, 2, 3>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
+  if (rt == 2) return columns_rt<C, 2, 4>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
+  if (rt == 3) return columns_rt<C, 3, 3>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
+  return columns_rt<C, 4, 4>(a, W, cgl, cgr, cpsi, ctl, cxs, cys, slots, s);
 }
 
 }  // namespace
 
 size_t adjoint_column_smem(int W, int precision) {
   return precision == NEGF_FP64 ? column_smem<cd>(W) : column_smem<cf>(W);
+}
+
+int adjoint_cols_per_job(int W) { return adj_ncols(W); }
+
+int adjoint_column_occupancy(int W, int precision) {
+  return precision == NEGF_FP64 ? occupancy_impl<cd>(W) : occupancy_impl<cf>(W);
 }
 
 cudaError_t launch_adjoint_sweep(const TaskDesc* d_tasks, int n_tasks, int max_W, int precision,

@@ -34,7 +34,9 @@ constexpr int kW = 64;
 constexpr int kN = 2 * kW;                    // two columns side by side
 constexpr int kThreads = 256;
 constexpr int kWtPitch = kW + 1;              // padded row of the weight staging
-constexpr size_t kSmem = sizeof(cf) * (kW * kW + 2 * kW * kN) + sizeof(float) * kN * kWtPitch;
+// Gs, the X ping-pong pair, the weights staging and (level-2 blocks built in the kernel) the
+// staging of the transposed rows' weights
+constexpr size_t kSmem = sizeof(cf) * (kW * kW + 2 * kW * kN) + 2 * sizeof(float) * kN * kWtPitch;
 constexpr int kB2 = 8 + kW;                   // level-2 block of a 64-site slice: guide + octets
 
 // eta |G|^2 with every rounding explicit, so that the weight of a (row, site) pair has the same
@@ -54,6 +56,7 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
   cf* Xa = Gs + kW * kW;                                   // [c][b'] ping
   cf* Xb = Xa + kW * kN;                                   // [c][b'] pong
   float* Wt = reinterpret_cast<float*>(Xb + kW * kN);      // [b'][a] weights staging
+  float* Wt2 = Wt + kN * kWtPitch;                         // fused: transposed rows [r][b]
 
   const int tid = threadIdx.x;
   const TcJob job = jobs[blockIdx.x];
@@ -73,14 +76,39 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
   auto row_of = [&](int y, int b) -> uint64_t {
     return y < L ? (uint64_t)y * kW + b : (uint64_t)n + (uint64_t)(y - L) * kW + b;
   };
-  // fused: the level-2 block and level-1 weight of (row, slice) from the 64 weights wrow[0..63]
-  auto put_block = [&](uint64_t row, int slice, const float* wrow) {
+  // fused: the level-2 blocks of a step, one per thread (the thread's row and slice, `have`,
+  // the thresholds of its 64 weights wrow[0..63] in registers); staged in shared memory 128 at
+  // a time (the two weight stagings, free once read) and written block by block, 18 lanes per
+  // 288-byte block, so that the stores stay contiguous
+  uint64_t* blk_row = reinterpret_cast<uint64_t*>(Gs);     // Gs is free outside the product
+  int* blk_slice = reinterpret_cast<int*>(blk_row + kN);
+  auto put_blocks = [&](bool have, uint64_t row, int slice, const float* wrow) {
     uint32_t c[kW];
     float tot = 0.f;
-    bad |= !level2_fp32<kW>([&](int a) { return wrow[a]; }, kW, c, &tot);
-    uint32_t* dst = l2 + (row * L + slice) * kB2;
-    level2_pack4<kW>(c, kW, [&](int i, uint4 v) { *reinterpret_cast<uint4*>(dst + i) = v; });
-    l1[row * (L + 2) + slice] = tot;
+    if (have) bad |= !level2_fp32<kW>([&](int a) { return wrow[a]; }, kW, c, &tot);
+    __syncthreads();                                       // every weight row has been read
+    uint32_t* stage = reinterpret_cast<uint32_t*>(Wt);     // 2 x 128 x 65 >= 128 x 72 words
+    for (int half = 0; half < 2; ++half) {
+      const int b = tid & (kN - 1);
+      if ((tid >> 7) == half) {
+        blk_row[b] = have ? row : ~0ull;
+        blk_slice[b] = slice;
+        if (have) {
+          uint32_t* dst = stage + b * kB2;
+          level2_pack4<kW>(c, kW, [&](int i, uint4 v) { *reinterpret_cast<uint4*>(dst + i) = v; });
+          l1[row * (L + 2) + slice] = tot;
+        }
+      }
+      __syncthreads();
+      for (int i = tid; i < kN * (kB2 / 4); i += kThreads) {
+        const int bb = i / (kB2 / 4), q = i - bb * (kB2 / 4);
+        const uint64_t r = blk_row[bb];
+        if (r != ~0ull)
+          *reinterpret_cast<uint4*>(l2 + (r * L + blk_slice[bb]) * kB2 + 4 * q) =
+              *reinterpret_cast<const uint4*>(stage + bb * kB2 + 4 * q);
+      }
+      __syncthreads();
+    }
   };
   // start block of column slot col into X[:, col*64 .. col*64+63]
   auto load_start = [&](cf* X, int col) {
@@ -90,11 +118,21 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
       X[c * kN + col * kW + b] = st[i];
     }
   };
-  // weights of slice k for the columns in `mask` from X (and lead weights at a boundary slice)
-  auto emit = [&](const cf* X, int k, unsigned mask) {
+  // weights of slice k for the columns in `mask` from X (and lead weights at a boundary slice);
+  // fused, also the level-2 blocks of the rows (k, a) towards the site columns in `tmask`
+  // (their slice ys[col], weights eta_{y,b} |G_{k,y}[a][b]|^2): one block per thread, the
+  // columns' rows on threads 0..127 and the transposed rows on 128..255
+  auto emit = [&](const cf* X, int k, unsigned mask, unsigned tmask) {
     for (int i = tid; i < kN * kW; i += kThreads) {
       const int r = i % kN, a = i / kN;                    // r consecutive across threads
       Wt[r * kWtPitch + a] = wsq(eta[k * kW + a], X[a * kN + r]);
+    }
+    if (tmask) {
+      for (int i = tid; i < kN * kW; i += kThreads) {
+        const int r = i / kW, b = i % kW, col = r / kW;
+        if (tmask & (1u << col))
+          Wt2[r * kWtPitch + b] = wsq(eta[ys[col] * kW + b], X[(r % kW) * kN + col * kW + b]);
+      }
     }
     __syncthreads();
     if (!fused) {
@@ -104,8 +142,26 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
         if (mask & (1u << col))
           wt[row_of(ys[col], r % kW) * K + (uint64_t)k * kW + a] = Wt[r * kWtPitch + a];
       }
-    } else if (tid < kN && (mask & (1u << (tid / kW)))) {
-      put_block(row_of(ys[tid / kW], tid % kW), k, Wt + tid * kWtPitch);   // row tid's weights
+    } else {
+      // every thread takes part (the stores go through barriers): threads 0..127 a row of the
+      // columns, 128..255 a transposed row
+      bool have;
+      uint64_t row;
+      int slice;
+      const float* wrow;
+      if (tid < kN) {
+        have = mask & (1u << (tid / kW));
+        row = have ? row_of(ys[tid / kW], tid % kW) : 0;
+        slice = k;
+        wrow = Wt + tid * kWtPitch;
+      } else {
+        const int r = tid - kN, col = r / kW;
+        have = tmask & (1u << col);
+        row = (uint64_t)k * kW + r % kW;
+        slice = have ? ys[col] : 0;
+        wrow = Wt2 + r * kWtPitch;
+      }
+      put_blocks(have, row, slice, wrow);
     }
     if (k == 0 || k == L - 1) {
       // lead weights: Phi (FP32) staged in Gs (free outside the product)
@@ -156,7 +212,7 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
       if (!(have & (1u << col))) continue;
       load_start(Xa, col);
       __syncthreads();
-      emit(Xa, m0_of(ys[col]), 1u << col);
+      emit(Xa, m0_of(ys[col]), 1u << col, 0u);
     }
   }
   const int m0a = m0_of(job.y0), m0b = job.y1 >= 0 ? m0_of(job.y1) : m0a;
@@ -214,25 +270,11 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
 #pragma unroll
       for (int j = 0; j < 8; ++j) Xn[(ty + 16 * i) * kN + tx + 16 * j] = cf{accr[i][j], acci[i][j]};
     __syncthreads();
-    if (active) emit(Xn, k, active);
-    if (dir == 0 && fused) {
-      // rows (k, a) towards the site columns' start slices y: their level-2 blocks of slice y
-      // from the weights eta_{y,b} |G_{k,y}[a][b]|^2, staged (pitch 65) for the per-row build
-      unsigned tmask = 0;
+    unsigned tmask = 0;                                    // fused: transposed rows' blocks
+    if (dir == 0 && fused)
       for (int col = 0; col < 2; ++col)
         if ((active & (1u << col)) && ys[col] < L) tmask |= 1u << col;
-      if (tmask) {
-        for (int i = tid; i < kN * kW; i += kThreads) {
-          const int r = i / kW, b = i % kW, col = r / kW;
-          if (tmask & (1u << col))
-            Wt[r * kWtPitch + b] = wsq(eta[ys[col] * kW + b], Xn[(r % kW) * kN + col * kW + b]);
-        }
-        __syncthreads();
-        if (tid < kN && (tmask & (1u << (tid / kW))))
-          put_block((uint64_t)k * kW + tid % kW, ys[tid / kW], Wt + tid * kWtPitch);
-        __syncthreads();
-      }
-    }
+    if (active) emit(Xn, k, active, tmask);
     if (dir == 0) {
       for (int col = 0; col < 2; ++col) {
         if (!(active & (1u << col))) continue;

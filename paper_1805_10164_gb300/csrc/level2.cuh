@@ -13,39 +13,50 @@ namespace {
 constexpr uint32_t kCdfOne = 1u << 31;
 __device__ __forceinline__ float pow2f_l2(int e) { return __int_as_float((e + 127) << 23); }
 
-// Thresholds of one slice's W <= WB FP32 weights wt(0) .. wt(W - 1): the exact fixed-point
-// prefix c_a = floor(2^31 P_a / S) (c = 2^31 where P_a reaches the total), with the weights
-// scaled by a power of two so that their integer total T lies in [2^29, 2^31) and divided by T
-// through a 64-bit reciprocal; an empty slice gives all 2^31.  *total: the slice's weight as
+// Thresholds of one slice's W <= WB FP32 weights wt(0) .. wt(W - 1) (WB a multiple of 16, or
+// below 16): the exact fixed-point prefix c_a = floor(2^31 P_a / T) (c = 2^31 where P_a
+// reaches the total), with the weights scaled by a power of two so that their integer total T
+// lies in [2^29, 2^31) and divided by T through a 64-bit reciprocal; an empty slice gives all
+// 2^31.  *total: the slice's weight as
 // the integer total scaled back.  Returns false on a negative or non-finite sum.
 template <int WB, typename Wf>
 __device__ __forceinline__ bool level2_fp32(Wf wt, int W, uint32_t (&c)[WB], float* total) {
   bool ok = true;
   float tot = 0.f;
-  float S = 0.f;
+  // the float sum S (it only sets the scale) in four interleaved partial sums, and the integer
+  // total and prefix in chunks of 16 (exact in any order): independent chains for the pipes
+  float s4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
   for (int a = 0; a < WB; ++a)
-    if (a < W) S += wt(a);
+    if (a < W) s4[a & 3] += wt(a);
+  const float S = (s4[0] + s4[1]) + (s4[2] + s4[3]);
   if (!(S >= 0.f && S < INFINITY)) ok = false;
   if (S > 0.f && S < INFINITY) {
     int e = 0;
     frexpf(S, &e);                             // S = f 2^e, f in [1/2, 1)
     const int sh = 30 - e, sh1 = sh / 2, sh2 = sh - sh / 2;
     const float p1 = pow2f_l2(sh1), p2 = pow2f_l2(sh2);
-    uint32_t T = 0;
 #pragma unroll
     for (int a = 0; a < WB; ++a) {
       const float v = a < W ? wt(a) : 0.f;
-      const uint32_t m = v > 0.f ? __float2uint_rz((v * p1) * p2) : 0u;
-      c[a] = m;
-      T += m;
+      c[a] = v > 0.f ? __float2uint_rz((v * p1) * p2) : 0u;
     }
+    // prefix within chunks of 16, then the chunks' offsets
+    constexpr int kCh = WB < 16 ? WB : 16;
+    constexpr int nCh = WB / kCh;
+#pragma unroll
+    for (int a = 0; a < WB; ++a)
+      if (a % kCh) c[a] += c[a - 1];
+    uint32_t off[nCh];
+    off[0] = 0;
+#pragma unroll
+    for (int h = 1; h < nCh; ++h) off[h] = off[h - 1] + c[h * kCh - 1];
+    const uint32_t T = off[nCh - 1] + c[WB - 1];
     tot = (__uint2float_rn(T) * pow2f_l2(-sh1)) * pow2f_l2(-sh2);
     const uint64_t Rr = (1ull << 62) / (uint64_t)T;   // T >= 2^29 - W
-    uint32_t P = 0;
 #pragma unroll
     for (int a = 0; a < WB; ++a) {
-      P += c[a];
+      const uint32_t P = off[a / kCh] + c[a];
       const uint32_t q = (uint32_t)(((uint64_t)P * Rr) >> 31);
       c[a] = P == T ? kCdfOne : min(q, kCdfOne - 1u);
     }

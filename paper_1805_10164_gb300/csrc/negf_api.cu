@@ -1717,15 +1717,17 @@ negf_status negf_current_backward_rgf(negf_ctx ctx, negf_tables t, negf_tally tl
     if (k0 == k1) continue;
     const TaskDesc& d = t->h_tasks[k0];
     const uint64_t blk = (uint64_t)d.W * d.W * cb;
+    const int nc = negf::adjoint_cols_per_job(d.W);
+    const uint64_t jobs_per_task = 1 + (uint64_t)(d.L - 1 + nc - 1) / nc;
     const uint64_t per_task = (3ull * d.L + 2) * blk;   // gl, gr, Psi, Tl
-    const uint64_t per_slot = 2ull * d.L * blk;          // X, Y
-    const size_t smem = negf::adjoint_column_smem(d.W, prec);
-    const int per_sm = (int)std::max<size_t>(1, std::min<size_t>(4, (227u << 10) / smem));
+    const uint64_t per_slot = 2ull * d.L * blk * nc;     // X, Y panels of nc block columns
+    const int per_sm = negf::adjoint_column_occupancy(d.W, prec);
     for (int k = k0; k < k1;) {
       int n = std::min(k1 - k, 64);
       int slots = 0;
       while (true) {
-        slots = (int)std::min<uint64_t>((uint64_t)n * d.L, (uint64_t)ctx->sm_count * per_sm);
+        slots = (int)std::min<uint64_t>((uint64_t)n * jobs_per_task,
+                                        (uint64_t)ctx->sm_count * per_sm);
         if (n == 1 || n * per_task + slots * per_slot <= budget) break;
         n = std::max(1, n / 2);
       }
@@ -1793,7 +1795,7 @@ negf_status negf_current_backward_rgf(negf_ctx ctx, negf_tables t, negf_tally tl
     unsigned char* psi = grr + (uint64_t)gr.n * d.L * blk;
     unsigned char* tlb = psi + (uint64_t)gr.n * d.L * blk;
     unsigned char* xs = d_sbuf;
-    unsigned char* ys = xs + (uint64_t)gr.slots * d.L * blk;
+    unsigned char* ys = xs + (uint64_t)gr.slots * d.L * blk * negf::adjoint_cols_per_job(d.W);
     {
       ProfScope ps(ctx, "adjoint_expand_kernel", 1);
       e = negf::launch_adjoint_expand(t->d_tasks, gr.t0, gr.n, d.W, d.L, prec, t->d_wire,

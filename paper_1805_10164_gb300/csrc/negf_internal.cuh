@@ -241,6 +241,8 @@ cudaError_t launch_cgemm_tc(const cf* A, const cf* B, cf* Y, int n, int32_t* err
 // Block-column adjoint (k_adjoint.cu): checkpointed sweeps of every task, the recompute of the
 // blocks between checkpoints for a group of tasks of one wire, and the column jobs of the group.
 size_t adjoint_column_smem(int W, int precision);
+int adjoint_cols_per_job(int W);                 // block columns side by side in one job
+int adjoint_column_occupancy(int W, int precision);   // column-kernel CTAs one SM holds
 cudaError_t launch_adjoint_sweep(const TaskDesc* d_tasks, int n_tasks, int max_W, int precision,
                                  const double* d_wire, const double* d_phi, const cd* d_sig,
                                  const uint64_t* d_ck_off, int stride, void* d_ck,
