@@ -78,7 +78,7 @@ def tensor_peak(kind):
 # units processed (both the weights and the g blocks grow as n^2 per task): x 100 per task,
 # x 256 / 8 tasks.
 MEASURED_TRAFFIC = {
-    ("walk_kernel", "wire_W10_L50_eta0.05_64E", "e2d18e70c6f09171"): 133861888,
+    ("walk_kernel", "wire_W10_L50_eta0.05_64E", "2175f1dcd66360d9"): 133278464,
     ("chain_cta_kernel", "wire_W64_L1000_eta0.005_256E", "7a863ab2ab935cf2"): 4565932748800,
     ("two_level_kernel", "wire_W64_L1000_eta0.005_256E", "5d548d12518c95ef"): 9015689600000,
 }

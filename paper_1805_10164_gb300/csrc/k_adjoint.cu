@@ -257,7 +257,7 @@ __host__ __device__ inline int adj_ncols(int W) {
 // then the other columns NC at a time in increasing order.  Scratch per CTA: X and Y
 // [L][W][NC W]; per task of the group: gl, gr, Psi [L][W][W], Tl [2][W][W].
 template <typename C, int RT, int RTN>
-__global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, const C* __restrict__ gl_all,
+__global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : 2) adj_column_kernel(AdjArgs g, const C* __restrict__ gl_all,
                                                                  const C* __restrict__ gr_all,
                                                                  C* __restrict__ psi_all,
                                                                  C* __restrict__ tl_all,
@@ -460,8 +460,10 @@ __global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, cons
         for_tile<RT, RTN>(W, N, [&](int a, int b, int i, int j) { sA[i * N + j] = conj_(acc[a][b]); });
         __syncthreads();
       }
-      for (int idx = tid; idx < W * N; idx += blockDim.x) {
-        const int jj2 = idx / W, i = idx - jj2 * W;   // panel column jj2 = c W + j, row (k, i)
+      // in the products' thread layout (row i, panel column jj2 = c W + j): the panel's shared
+      // and global accesses stay conflict-free and coalesced; the seeds wbar_{(m,j),(k,i)} are
+      // read two rows of 16 per warp
+      for_tile<RT, RTN>(W, N, [&](int, int, int i, int jj2) {
         const int c = jj2 / W, j = jj2 - c * W;
         C u = mkc(0.0, 0.0, C{});
         if (c < ncols) {
@@ -496,7 +498,7 @@ __global__ void __launch_bounds__(kAdjThreads) adj_column_kernel(AdjArgs g, cons
         }
         if (k > 0) u = u - t * sB[i * N + jj2];
         sB[i * N + jj2] = u;
-      }
+      });
       __syncthreads();
       load_block(sA, gl + (uint64_t)k * WW, WW);
       __syncthreads();

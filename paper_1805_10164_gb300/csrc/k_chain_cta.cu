@@ -87,14 +87,17 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
     float tot = 0.f;
     if (have) bad |= !level2_fp32<kW>([&](int a) { return wrow[a]; }, kW, c, &tot);
     __syncthreads();                                       // every weight row has been read
-    uint32_t* stage = reinterpret_cast<uint32_t*>(Wt);     // 2 x 128 x 65 >= 128 x 72 words
+    // 2 x 128 x 65 >= 128 x 76 words; pitch 76 (not 72): 16-byte stores of eight neighbouring
+    // threads then start on eight different bank groups
+    constexpr int kSP = kB2 + 4;
+    uint32_t* stage = reinterpret_cast<uint32_t*>(Wt);
     for (int half = 0; half < 2; ++half) {
       const int b = tid & (kN - 1);
       if ((tid >> 7) == half) {
         blk_row[b] = have ? row : ~0ull;
         blk_slice[b] = slice;
         if (have) {
-          uint32_t* dst = stage + b * kB2;
+          uint32_t* dst = stage + b * kSP;
           level2_pack4<kW>(c, kW, [&](int i, uint4 v) { *reinterpret_cast<uint4*>(dst + i) = v; });
           l1[row * (L + 2) + slice] = tot;
         }
@@ -105,7 +108,7 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
         const uint64_t r = blk_row[bb];
         if (r != ~0ull)
           *reinterpret_cast<uint4*>(l2 + (r * L + blk_slice[bb]) * kB2 + 4 * q) =
-              *reinterpret_cast<const uint4*>(stage + bb * kB2 + 4 * q);
+              *reinterpret_cast<const uint4*>(stage + bb * kSP + 4 * q);
       }
       __syncthreads();
     }

@@ -13,6 +13,31 @@ namespace {
 constexpr uint32_t kCdfOne = 1u << 31;
 __device__ __forceinline__ float pow2f_l2(int e) { return __int_as_float((e + 127) << 23); }
 
+// floor(2^62 / T) for T in [2^29 - 64, 2^31), exactly, without a 64-bit division (its emulation
+// runs on the FP64 pipe, narrow on this GPU): q0 from a float reciprocal (within ~2^11 of the
+// quotient), one correction by the remainder r = 2^62 - q T divided in floats (|r| < 2^42, so
+// r / 2^10 fits 32 bits; the corrected q is within one), then unit steps until 0 <= r < T.
+__device__ __forceinline__ uint64_t recip_2p62(uint32_t T) {
+  const float rt = __frcp_rn((float)T);
+  uint64_t q = (uint64_t)__float2uint_rz(rt * 2305843009213693952.0f) << 1;   // 2 (2^61 / T)
+  const uint64_t two62 = 1ull << 62;
+  int64_t r = (int64_t)(two62 - q * (uint64_t)T);
+  const float rf = (float)(int32_t)(r >> 10) * 1024.0f;
+  q += (uint64_t)(int64_t)__float2int_rz(rf * rt);
+  r = (int64_t)(two62 - q * (uint64_t)T);
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    if (r < 0) {
+      --q;
+      r += T;
+    } else if (r >= (int64_t)T) {
+      ++q;
+      r -= T;
+    }
+  }
+  return q;
+}
+
 // Thresholds of one slice's W <= WB FP32 weights wt(0) .. wt(W - 1) (WB a multiple of 16, or
 // below 16): the exact fixed-point prefix c_a = floor(2^31 P_a / T) (c = 2^31 where P_a
 // reaches the total), with the weights scaled by a power of two so that their integer total T
@@ -53,7 +78,7 @@ __device__ __forceinline__ bool level2_fp32(Wf wt, int W, uint32_t (&c)[WB], flo
     for (int h = 1; h < nCh; ++h) off[h] = off[h - 1] + c[h * kCh - 1];
     const uint32_t T = off[nCh - 1] + c[WB - 1];
     tot = (__uint2float_rn(T) * pow2f_l2(-sh1)) * pow2f_l2(-sh2);
-    const uint64_t Rr = (1ull << 62) / (uint64_t)T;   // T >= 2^29 - W
+    const uint64_t Rr = recip_2p62(T);                 // floor(2^62 / T), T >= 2^29 - W
 #pragma unroll
     for (int a = 0; a < WB; ++a) {
       const uint32_t P = off[a / kCh] + c[a];
