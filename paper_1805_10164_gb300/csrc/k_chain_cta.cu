@@ -4,8 +4,9 @@
 // w_{(m,b),(k,a)} = eta_{k,a} |G_{k,m}[a][b]|^2 of the column's W rows (Eq. draw_i_simult) and,
 // at the boundary slices, the lead weights <psi_b|Gamma|psi_b> = sum_nu Gamma_nu
 // |(Phi^T G_{k,m})_{nu b}|^2.  Same weights as chain_kernel (one warp per column), computed
-// by 256 threads with the two columns side by side: X_k [64][128] = (-t g_k) [64][64] X_{k+1}
-// in shared memory, FP32 fused multiply-adds, each thread a 4 x 8 block of outputs.
+// by 512 threads with the two columns side by side: X_k [64][128] = (-t g_k) [64][64] X_{k+1}
+// in shared memory, FP32 fused multiply-adds, each thread a 4 x 4 block of outputs (four warps
+// per scheduler to hide the shared-memory and dependency latencies).
 //
 // W = 64 uses the symmetry G = G^T (H real symmetric, every self-energy a complex symmetric
 // matrix), which halves the products: only the chains towards slice 0 run (and the one of the
@@ -32,7 +33,7 @@ namespace {
 
 constexpr int kW = 64;
 constexpr int kN = 2 * kW;                    // two columns side by side
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kWtPitch = kW + 1;              // padded row of the weight staging
 // Gs, the X ping-pong pair, the weights staging and (level-2 blocks built in the kernel) the
 // staging of the transposed rows' weights
@@ -76,30 +77,43 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
   auto row_of = [&](int y, int b) -> uint64_t {
     return y < L ? (uint64_t)y * kW + b : (uint64_t)n + (uint64_t)(y - L) * kW + b;
   };
-  // fused: the level-2 blocks of a step, one per thread (the thread's row and slice, `have`,
-  // the thresholds of its 64 weights wrow[0..63] in registers); staged in shared memory 128 at
-  // a time (the two weight stagings, free once read) and written block by block, 18 lanes per
-  // 288-byte block, so that the stores stay contiguous
+  // fused: the level-2 blocks of a step, one per pair of adjacent threads (block bi = tid / 2,
+  // half h = tid % 2: the block's weights wrow[0..63], the pair's `have`, row and slice), their
+  // thresholds in registers (level2_fp32_pair); staged in shared memory 128 at a time (the two
+  // weight stagings, free once read) and written block by block, 18 lanes per 288-byte block,
+  // so that the stores stay contiguous
   uint64_t* blk_row = reinterpret_cast<uint64_t*>(Gs);     // Gs is free outside the product
   int* blk_slice = reinterpret_cast<int*>(blk_row + kN);
   auto put_blocks = [&](bool have, uint64_t row, int slice, const float* wrow) {
-    uint32_t c[kW];
+    const int h = tid & 1, bi = tid >> 1;
+    uint32_t c[32];
     float tot = 0.f;
-    if (have) bad |= !level2_fp32<kW>([&](int a) { return wrow[a]; }, kW, c, &tot);
+    const bool ok = level2_fp32_pair([&](int a) { return wrow[32 * h + a]; }, h, c, &tot);
+    if (have) bad |= !ok;
     __syncthreads();                                       // every weight row has been read
-    // 2 x 128 x 65 >= 128 x 76 words; pitch 76 (not 72): 16-byte stores of eight neighbouring
-    // threads then start on eight different bank groups
+    // 2 x 128 x 65 >= 128 x 76 words; pitch 76 (not 72): 16-byte stores of neighbouring
+    // blocks start on different bank groups
     constexpr int kSP = kB2 + 4;
     uint32_t* stage = reinterpret_cast<uint32_t*>(Wt);
     for (int half = 0; half < 2; ++half) {
-      const int b = tid & (kN - 1);
-      if ((tid >> 7) == half) {
-        blk_row[b] = have ? row : ~0ull;
-        blk_slice[b] = slice;
+      const int b = bi & (kN - 1);
+      if ((bi >> 7) == half) {
+        if (h == 0) {
+          blk_row[b] = have ? row : ~0ull;
+          blk_slice[b] = slice;
+          if (have) l1[row * (L + 2) + slice] = tot;
+        }
         if (have) {
           uint32_t* dst = stage + b * kSP;
-          level2_pack4<kW>(c, kW, [&](int i, uint4 v) { *reinterpret_cast<uint4*>(dst + i) = v; });
-          l1[row * (L + 2) + slice] = tot;
+          // guide: the last threshold of octets 0..6 (octet 7's is 2^31); lane h holds octets
+          // 4h .. 4h + 3
+          *reinterpret_cast<uint4*>(dst + 4 * h) =
+              make_uint4(c[7], c[15], c[23], h == 0 ? c[31] : kCdfOne);
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            *reinterpret_cast<uint4*>(dst + 8 + 32 * h + 4 * i) =
+                make_uint4(c[4 * i], c[4 * i + 1], c[4 * i + 2],
+                           (h == 1 && i == 7) ? kCdfOne : c[4 * i + 3]);
         }
       }
       __syncthreads();
@@ -146,19 +160,20 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
           wt[row_of(ys[col], r % kW) * K + (uint64_t)k * kW + a] = Wt[r * kWtPitch + a];
       }
     } else {
-      // every thread takes part (the stores go through barriers): threads 0..127 a row of the
+      // every thread takes part (the stores go through barriers): pairs 0..127 a row of the
       // columns, 128..255 a transposed row
+      const int bi = tid >> 1;
       bool have;
       uint64_t row;
       int slice;
       const float* wrow;
-      if (tid < kN) {
-        have = mask & (1u << (tid / kW));
-        row = have ? row_of(ys[tid / kW], tid % kW) : 0;
+      if (bi < kN) {
+        have = mask & (1u << (bi / kW));
+        row = have ? row_of(ys[bi / kW], bi % kW) : 0;
         slice = k;
-        wrow = Wt + tid * kWtPitch;
+        wrow = Wt + bi * kWtPitch;
       } else {
-        const int r = tid - kN, col = r / kW;
+        const int r = bi - kN, col = r / kW;
         have = tmask & (1u << col);
         row = (uint64_t)k * kW + r % kW;
         slice = have ? ys[col] : 0;
@@ -174,9 +189,9 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
       for (int i = tid; i < kW * kW; i += kThreads) phis[i] = phi32[d.phi_off + i];
       for (int i = tid; i < kW; i += kThreads) gams[i] = (float)gam[d.lead_off + i];
       __syncthreads();
-      const int r = tid % kN, h = tid / kN;                // two halves of the modes
+      const int r = tid % kN, h = tid / kN;                // four quarters of the modes
       float part = 0.f;
-      for (int nu = h * 32; nu < h * 32 + 32; ++nu) {
+      for (int nu = h * 16; nu < h * 16 + 16; ++nu) {
         float zr = 0.f, zi = 0.f;
         for (int a = 0; a < kW; ++a) {
           const float p = phis[a * kW + nu];
@@ -191,7 +206,8 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
       if (h == 0) {
         const int col = r / kW;
         if (mask & (1u << col)) {
-          const float lw = Wt[r * kWtPitch] + Wt[r * kWtPitch + 1];
+          const float lw = (Wt[r * kWtPitch] + Wt[r * kWtPitch + 1]) +
+                           (Wt[r * kWtPitch + 2] + Wt[r * kWtPitch + 3]);
           const uint64_t row = row_of(ys[col], r % kW);
           if (fused) {
             if (k == 0) l1[row * (L + 2) + L] = lw;
@@ -224,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
   const int kstep = dir == 0 ? -1 : 1;
   cf* Xc = Xa;
   cf* Xn = Xb;
-  const int ty = tid / 16, tx = tid % 16;                  // outputs a = ty + 16i, b' = tx + 16j
+  const int ty = tid / 32, tx = tid % 32;                  // outputs a = ty + 16i, b' = tx + 32j
   // this thread's share of the next step's g block, fetched while the current step multiplies
   constexpr int kGPer = kW * kW / kThreads;
   cf gnext[kGPer];
@@ -246,22 +262,22 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
     for (int q = 0; q < kGPer; ++q) Gs[tid + q * kThreads] = cf{mt * gnext[q].x, mt * gnext[q].y};
     __syncthreads();
     if (k + kstep != k_end) fetch(k + kstep);
-    float accr[4][8], acci[4][8];
+    float accr[4][4], acci[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) accr[i][j] = acci[i][j] = 0.f;
-#pragma unroll 2
+      for (int j = 0; j < 4; ++j) accr[i][j] = acci[i][j] = 0.f;
+#pragma unroll 4
     for (int c = 0; c < kW; ++c) {
-      cf g[4], x[8];
+      cf g[4], x[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) g[i] = Gs[(ty + 16 * i) * kW + c];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) x[j] = Xc[c * kN + tx + 16 * j];
+      for (int j = 0; j < 4; ++j) x[j] = Xc[c * kN + tx + 32 * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 4; ++j) {
           accr[i][j] = fmaf(g[i].x, x[j].x, accr[i][j]);
           accr[i][j] = fmaf(-g[i].y, x[j].y, accr[i][j]);
           acci[i][j] = fmaf(g[i].x, x[j].y, acci[i][j]);
@@ -271,7 +287,7 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) Xn[(ty + 16 * i) * kN + tx + 16 * j] = cf{accr[i][j], acci[i][j]};
+      for (int j = 0; j < 4; ++j) Xn[(ty + 16 * i) * kN + tx + 32 * j] = cf{accr[i][j], acci[i][j]};
     __syncthreads();
     unsigned tmask = 0;                                    // fused: transposed rows' blocks
     if (dir == 0 && fused)
@@ -291,16 +307,17 @@ __global__ void __launch_bounds__(kThreads, 1) chain_cta_kernel(
             dst[(uint64_t)a * K + b] = wsq(em[b], Xn[a * kN + col * kW + b]);
           }
         } else if (y == L + 1) {
-          // lead-R weights of the rows of slice k from (G Phi_R)_k: four threads per row
-          const int a = tid >> 2, q = tid & 3;
+          // lead-R weights of the rows of slice k from (G Phi_R)_k: eight threads per row
+          const int a = tid >> 3, q = tid & 7;
           float part = 0.f;
 #pragma unroll 4
-          for (int nu = q * 16; nu < q * 16 + 16; ++nu) {
+          for (int nu = q * 8; nu < q * 8 + 8; ++nu) {
             const cf v = Xn[a * kN + col * kW + nu];
             part += (float)gam[d.lead_off + nu] * (v.x * v.x + v.y * v.y);
           }
           part += __shfl_xor_sync(0xffffffffu, part, 1);
           part += __shfl_xor_sync(0xffffffffu, part, 2);
+          part += __shfl_xor_sync(0xffffffffu, part, 4);
           if (q == 0) {
             if (fused) l1[(uint64_t)(k * kW + a) * (L + 2) + L + 1] = part;
             else wt[(uint64_t)(k * kW + a) * K + n + 1] = part;

@@ -48,13 +48,19 @@ template <int WB, typename Wf>
 __device__ __forceinline__ bool level2_fp32(Wf wt, int W, uint32_t (&c)[WB], float* total) {
   bool ok = true;
   float tot = 0.f;
-  // the float sum S (it only sets the scale) in four interleaved partial sums, and the integer
-  // total and prefix in chunks of 16 (exact in any order): independent chains for the pipes
-  float s4[4] = {0.f, 0.f, 0.f, 0.f};
+  // chunks of 16 weights: the float sum S (it only sets the scale) as the sum of the chunks'
+  // sums combined pairwise, and the integer total and prefix chunk by chunk (exact in any order)
+  constexpr int kCh = WB < 16 ? WB : 16;
+  constexpr int nCh = WB / kCh;
+  float cs[nCh];
+#pragma unroll
+  for (int h = 0; h < nCh; ++h) cs[h] = 0.f;
 #pragma unroll
   for (int a = 0; a < WB; ++a)
-    if (a < W) s4[a & 3] += wt(a);
-  const float S = (s4[0] + s4[1]) + (s4[2] + s4[3]);
+    if (a < W) cs[a / kCh] += wt(a);
+  float S = cs[0];
+  if (nCh == 2) S = cs[0] + cs[1];
+  if (nCh == 4) S = (cs[0] + cs[1]) + (cs[2 % nCh] + cs[3 % nCh]);
   if (!(S >= 0.f && S < INFINITY)) ok = false;
   if (S > 0.f && S < INFINITY) {
     int e = 0;
@@ -67,8 +73,6 @@ __device__ __forceinline__ bool level2_fp32(Wf wt, int W, uint32_t (&c)[WB], flo
       c[a] = v > 0.f ? __float2uint_rz((v * p1) * p2) : 0u;
     }
     // prefix within chunks of 16, then the chunks' offsets
-    constexpr int kCh = WB < 16 ? WB : 16;
-    constexpr int nCh = WB / kCh;
 #pragma unroll
     for (int a = 0; a < WB; ++a)
       if (a % kCh) c[a] += c[a - 1];
@@ -88,6 +92,70 @@ __device__ __forceinline__ bool level2_fp32(Wf wt, int W, uint32_t (&c)[WB], flo
   } else {
 #pragma unroll
     for (int a = 0; a < WB; ++a) c[a] = kCdfOne;
+  }
+  *total = tot;
+  return ok;
+}
+
+// level2_fp32 for a 64-weight slice on a pair of adjacent lanes (lane parity h): each takes
+// weights 32 h .. 32 h + 31 (wt(a) for a < 32 gives the lane's own a + 32 h); the chunk sums and
+// chunk totals are exchanged so that both lanes form the same S, T and offsets as level2_fp32
+// does alone, hence the same thresholds, of which c holds the lane's half.  Every lane of the
+// warp must call it (shuffles).
+template <typename Wf>
+__device__ __forceinline__ bool level2_fp32_pair(Wf wt, int h, uint32_t (&c)[32], float* total) {
+  bool ok = true;
+  float tot = 0.f;
+  float cs0 = 0.f, cs1 = 0.f;                   // the lane's chunks 2h, 2h + 1
+#pragma unroll
+  for (int a = 0; a < 16; ++a) cs0 += wt(a);
+#pragma unroll
+  for (int a = 16; a < 32; ++a) cs1 += wt(a);
+  const float mine = cs0 + cs1;                 // (cs[0] + cs[1]) or (cs[2] + cs[3])
+  const float other = __shfl_xor_sync(0xffffffffu, mine, 1);
+  const float S = h == 0 ? mine + other : other + mine;
+  if (!(S >= 0.f && S < INFINITY)) ok = false;
+  uint32_t t0 = 0, t1 = 0;
+  int sh1 = 0, sh2 = 0;
+  const bool pos = S > 0.f && S < INFINITY;
+  if (pos) {
+    int e = 0;
+    frexpf(S, &e);
+    const int sh = 30 - e;
+    sh1 = sh / 2;
+    sh2 = sh - sh / 2;
+    const float p1 = pow2f_l2(sh1), p2 = pow2f_l2(sh2);
+#pragma unroll
+    for (int a = 0; a < 32; ++a) {
+      const float v = wt(a);
+      c[a] = v > 0.f ? __float2uint_rz((v * p1) * p2) : 0u;
+    }
+#pragma unroll
+    for (int a = 0; a < 32; ++a)
+      if (a % 16) c[a] += c[a - 1];
+    t0 = c[15];
+    t1 = c[31];
+  }
+  // chunk totals of the partner: offsets of chunks 0..3 and T as level2_fp32 forms them
+  const uint32_t u0 = __shfl_xor_sync(0xffffffffu, t0, 1);
+  const uint32_t u1 = __shfl_xor_sync(0xffffffffu, t1, 1);
+  if (pos) {
+    const uint32_t a0 = h == 0 ? t0 : u0, a1 = h == 0 ? t1 : u1;   // chunks 0, 1
+    const uint32_t a2 = h == 0 ? u0 : t0, a3 = h == 0 ? u1 : t1;   // chunks 2, 3
+    const uint32_t off1 = a0, off2 = off1 + a1, off3 = off2 + a2;
+    const uint32_t T = off3 + a3;
+    const uint32_t o0 = h == 0 ? 0u : off2, o1 = h == 0 ? off1 : off3;
+    tot = (__uint2float_rn(T) * pow2f_l2(-sh1)) * pow2f_l2(-sh2);
+    const uint64_t Rr = recip_2p62(T);
+#pragma unroll
+    for (int a = 0; a < 32; ++a) {
+      const uint32_t P = (a < 16 ? o0 : o1) + c[a];
+      const uint32_t q = (uint32_t)(((uint64_t)P * Rr) >> 31);
+      c[a] = P == T ? kCdfOne : min(q, kCdfOne - 1u);
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < 32; ++a) c[a] = kCdfOne;
   }
   *total = tot;
   return ok;
