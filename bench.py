@@ -73,18 +73,16 @@ def tensor_peak(kind):
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture, see profiles/)
 # per step of the named workload, keyed by kernel, workload and a hash of the kernel's sources:
-# a kernel changed since its counters were taken reports null.  The headline's chain and
-# level-2 figures are scaled from captures of the W = 64 x L = 100 wire (8 tasks) by the
-# units processed (both the weights and the g blocks grow as n^2 per task): x 100 per task,
-# x 256 / 8 tasks.
+# a kernel changed since its counters were taken reports null.  The headline's chain figure
+# (which writes the level-2 blocks itself) is scaled from a capture of the W = 64 x L = 100
+# wire (8 tasks) by the units processed (the blocks written and the g blocks read both grow as
+# n^2 per task): x 100 per task, x 256 / 8 tasks.
 MEASURED_TRAFFIC = {
     ("walk_kernel", "wire_W10_L50_eta0.05_64E", "2175f1dcd66360d9"): 133278464,
-    ("chain_cta_kernel", "wire_W64_L1000_eta0.005_256E", "7a863ab2ab935cf2"): 4565932748800,
-    ("two_level_kernel", "wire_W64_L1000_eta0.005_256E", "5d548d12518c95ef"): 9015689600000,
+    ("chain_cta_kernel", "wire_W64_L1000_eta0.005_256E", "a3bffe9ce92a6da4"): 5145210496000,
 }
 TRAFFIC_SOURCES = {"walk_kernel": ["k_walk.cu", "philox.cuh"],
-                   "chain_cta_kernel": ["k_chain_cta.cu", "level2.cuh"],
-                   "two_level_kernel": ["k_alias.cu"]}
+                   "chain_cta_kernel": ["k_chain_cta.cu", "level2.cuh"]}
 
 
 def measured_traffic(kernel, workload):
@@ -338,8 +336,13 @@ def rooflines(prof, wl, prec, counts, steps, probe_gbs=None, probe_src=None):
                     ent.update(bound="l2", peak=round(probe_gbs, 1),
                                frac=round(ach / probe_gbs, 4), peak_source=probe_src)
         if ent is not None:
-            ent.update(kernel=kname, launches_per_step=launches / steps,
-                       ms_per_step=round(ms / steps, 4), traffic=measured_traffic(kname, wl.name))
+            # traffic: the measured DRAM bytes per step over the launches of a step (the
+            # average launch, as achieved is the average launch's rate)
+            tps = measured_traffic(kname, wl.name)
+            lps = launches / steps
+            ent.update(kernel=kname, launches_per_step=lps, ms_per_step=round(ms / steps, 4),
+                       traffic=int(tps / lps) if tps is not None else None,
+                       traffic_per_step=tps)
             out[kname] = ent
     return out
 
