@@ -28,8 +28,10 @@
 //
 // Thread layout of the block products: 256 threads as 16 x 16; thread (ty, tx) owns rows
 // ty + 16 a and columns tx + 16 b (a, b < RT = ceil(W / 16)) of the W x W result, blocks row-major
-// with stride W in shared memory.  Every W x W block is in the precision of the tables
-// (complex64 or complex128); seeds and the accumulated gradient are FP64.
+// with stride W in shared memory.  Every W x W block, the seeds and the per-step arithmetic are
+// in the precision of the tables (complex64 or complex128; the FP64 pipe of this GPU is 1/64 of
+// the FP32 rate, so an FP32 build keeps FP64 out of the per-step work: the modes, broadenings
+// and dephasing rates are staged as FP32 in shared memory); the gradient is accumulated in FP64.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -43,8 +45,6 @@ constexpr int kAdjThreads = 256;
 
 __device__ __forceinline__ cd conj_(cd a) { return cd{a.x, -a.y}; }
 __device__ __forceinline__ cf conj_(cf a) { return cf{a.x, -a.y}; }
-__device__ __forceinline__ cd widen(cd a) { return a; }
-__device__ __forceinline__ cd widen(cf a) { return cd{(double)a.x, (double)a.y}; }
 
 // Lead self-energy Sigma_r = Phi diag(sigma) Phi^T, entry (a, b) (FP64; both leads alike)
 __device__ __forceinline__ cd lead_sigma(int a, int b, int W, const double* phi, const cd* sg) {
@@ -237,7 +237,7 @@ struct AdjArgs {
   const double* phi;
   const cd* sig;
   const double* gam;
-  const double* wbar;        // [rows x K] per task at wt_off
+  const void* wbar;          // [rows x K] per task at wt_off, in the precision of the tables
   const double* ubar;        // per task at mode_off
   uint64_t site_off0;        // dT of the group's first task (sites of earlier tasks before it)
   double* dV;
@@ -257,7 +257,7 @@ __host__ __device__ inline int adj_ncols(int W) {
 // then the other columns NC at a time in increasing order.  Scratch per CTA: X and Y
 // [L][W][NC W]; per task of the group: gl, gr, Psi [L][W][W], Tl [2][W][W].
 template <typename C, int RT, int RTN>
-__global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : 2) adj_column_kernel(AdjArgs g, const C* __restrict__ gl_all,
+__global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : (sizeof(C) == 8 ? 3 : 2)) adj_column_kernel(AdjArgs g, const C* __restrict__ gl_all,
                                                                  const C* __restrict__ gr_all,
                                                                  C* __restrict__ psi_all,
                                                                  C* __restrict__ tl_all,
@@ -276,6 +276,9 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : 2) adj_column_kerne
   C* fcol = rowk + W;
   int* perm = reinterpret_cast<int*>(fcol + W);
   int* flag = perm + W;
+  // FP32 builds: Phi, Gamma (per mode) and one slice's eta as R, after the integer words
+  R* aux = reinterpret_cast<R*>(
+      smem_raw + ((reinterpret_cast<unsigned char*>(flag + 2) - smem_raw + 15) & ~(size_t)15));
   const int p = g.p;
   const int sp = p == 0 ? 0 : L - 1;
   const R t = (R)d0.t;
@@ -298,8 +301,28 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : 2) adj_column_kerne
     const double* phi = g.phi + d.phi_off;
     const cd* sg = g.sig + d.lead_off;
     const double* gam = g.gam + d.lead_off;
-    const double* wb = g.wbar + d.wt_off;
+    const R* wb = static_cast<const R*>(g.wbar) + d.wt_off;
     const double* ub = g.ubar + d.mode_off + p * W;
+    const R* phiR;                                     // Phi [x][m'], Gamma_m', ubar_m' as R
+    const R* gamR;
+    const R* ubR;
+    R* etaS = nullptr;                                 // FP32: eta of the current slice
+    if constexpr (sizeof(R) == 4) {
+      __syncthreads();
+      for (int idx = tid; idx < WW; idx += blockDim.x) aux[idx] = (R)phi[idx];
+      for (int m = tid; m < W; m += blockDim.x) {
+        aux[WW + m] = (R)gam[m];
+        aux[WW + W + m] = (R)ub[m];
+      }
+      phiR = aux;
+      gamR = aux + WW;
+      ubR = aux + WW + W;
+      etaS = aux + WW + 2 * W;
+    } else {
+      phiR = phi;
+      gamR = gam;
+      ubR = ub;
+    }
     const C* gl = gl_all + (uint64_t)tl * L * WW;
     const C* gr = gr_all + (uint64_t)tl * L * WW;
     C* Psi = psi_all + (uint64_t)tl * L * WW;
@@ -379,8 +402,8 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : 2) adj_column_kerne
       __syncthreads();
       for (int idx = tid; idx < WW; idx += blockDim.x) {
         const int a = idx / W, b = idx - a * W;
-        sT[idx] = mkc(phi[idx], 0.0, C{});                         // Phi [x][m']
-        sB[idx] = mkc(phi[b * W + a], 0.0, C{});                   // Phi^T [m'][y]
+        sT[idx] = C{phiR[idx], R(0)};                              // Phi [x][m']
+        sB[idx] = C{phiR[b * W + a], R(0)};                        // Phi^T [m'][y]
       }
       for (int k = 0; k < L; ++k) {
         __syncthreads();
@@ -395,44 +418,53 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : 2) adj_column_kerne
         __syncthreads();
         for (int idx = tid; idx < WW; idx += blockDim.x) {
           const int nu = idx / W, mp = idx - nu * W;
-          cd z = mk(0.0, 0.0);
-          for (int x = 0; x < W; ++x)
-            z = z + phi[x * W + nu] * widen(Psi[(uint64_t)sr * WW + x * W + mp]);
-          sA[idx] = to_c(z, C{});
+          R zx = 0, zy = 0;
+          for (int x = 0; x < W; ++x) {
+            const R f = phiR[x * W + nu];
+            const C ps = Psi[(uint64_t)sr * WW + x * W + mp];
+            zx += f * ps.x;
+            zy += f * ps.y;
+          }
+          sA[idx] = C{zx, zy};
         }
         __syncthreads();
         for (int idx = tid; idx < WW; idx += blockDim.x) {
           const int x = idx / W, mp = idx - x * W;
-          double tx = 0.0, ty = 0.0;
+          R tx = 0, ty = 0;
           for (int nu = 0; nu < W; ++nu) {
-            const double f = gam[nu] * phi[x * W + nu];
-            const cd z = widen(sA[nu * W + mp]);
+            const R f = gamR[nu] * phiR[x * W + nu];
+            const C z = sA[nu * W + mp];
             tx += f * z.x;
             ty -= f * z.y;
           }
-          Tl[(uint64_t)r * WW + idx] = to_c(mk(tx, ty), C{});
+          Tl[(uint64_t)r * WW + idx] = C{tx, ty};
         }
       }
       __syncthreads();
       for (int k = 0; k < L; ++k) {
+        if constexpr (sizeof(R) == 4) {
+          if (tid < W) etaS[tid] = (R)eta[k * W + tid];       // readers of the last slice passed a barrier
+        }
         __syncthreads();
         for (int idx = tid; idx < WW; idx += blockDim.x) {
           const int mp = idx / W, i = idx - mp * W;              // psibar_k [i][m']
-          const double* wrow = wb + (uint64_t)(n + p * W + mp) * K;
+          const R* wrow = wb + (uint64_t)(n + p * W + mp) * K;
           const int b = k * W + i;
-          const cd ps = widen(Psi[(uint64_t)k * WW + i * W + mp]);
-          const double f = wrow[b] * eta[b];
-          double vx = f * ps.x, vy = -f * ps.y;
+          const C ps = Psi[(uint64_t)k * WW + i * W + mp];
+          R eb;
+          if constexpr (sizeof(R) == 4) eb = etaS[i]; else eb = eta[b];
+          const R f = wrow[b] * eb;
+          R vx = f * ps.x, vy = -f * ps.y;
           for (int r = 0; r < 2; ++r) {
             const int sr = r == 0 ? 0 : L - 1;
             if (k != sr) continue;
-            const double wl = wrow[n + r];
-            if (wl == 0.0) continue;
-            const cd tv = widen(Tl[(uint64_t)r * WW + i * W + mp]);
+            const R wl = wrow[n + r];
+            if (wl == R(0)) continue;
+            const C tv = Tl[(uint64_t)r * WW + i * W + mp];
             vx += wl * tv.x;
             vy += wl * tv.y;
           }
-          sA[i * W + mp] = to_c(mk(vx, vy), C{});
+          sA[i * W + mp] = C{vx, vy};
         }
         __syncthreads();
         cta_prod<C, RT, RTN>(sA, sB, W, W, acc);
@@ -443,9 +475,9 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : 2) adj_column_kerne
     __syncthreads();
     for (int idx = tid; idx < WW; idx += blockDim.x) {
       const int a = idx / W, b = idx - a * W;
-      double v = 0.0;
-      for (int nu = 0; nu < W; ++nu) v += gam[nu] * phi[a * W + nu] * phi[b * W + nu];
-      sT[idx] = mkc(v, 0.0, C{});
+      R v = 0;
+      for (int nu = 0; nu < W; ++nu) v += gamR[nu] * phiR[a * W + nu] * phiR[b * W + nu];
+      sT[idx] = C{v, R(0)};
     }
     // ---- forward elimination: y_k = g^L_k (U_k - t y_{k-1}), U_k = Gbar[k-block, columns]
     for (int k = 0; k < L; ++k) {
@@ -463,38 +495,44 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : 2) adj_column_kerne
       // in the products' thread layout (row i, panel column jj2 = c W + j): the panel's shared
       // and global accesses stay conflict-free and coalesced; the seeds wbar_{(m,j),(k,i)} are
       // read two rows of 16 per warp
-      for_tile<RT, RTN>(W, N, [&](int, int, int i, int jj2) {
+      R er[RT];                                        // eta of this thread's rows of slice k
+#pragma unroll
+      for (int a = 0; a < RT; ++a) {
+        const int i = (tid >> 4) + 16 * a;
+        er[a] = i < W ? (R)eta[k * W + i] : R(0);
+      }
+      for_tile<RT, RTN>(W, N, [&](int a, int, int i, int jj2) {
         const int c = jj2 / W, j = jj2 - c * W;
-        C u = mkc(0.0, 0.0, C{});
+        C u = C{R(0), R(0)};
         if (c < ncols) {
           const int m = col_m(c);
-          const double* wrow = wb + (uint64_t)(m * W + j) * K;
+          const R* wrow = wb + (uint64_t)(m * W + j) * K;
           const int b = k * W + i;
-          const cd xv = widen(X[(uint64_t)k * XS + i * N + jj2]);
-          const double f = wrow[b] * eta[b];
-          double ux = f * xv.x, uy = -f * xv.y;
+          const C xv = X[(uint64_t)k * XS + i * N + jj2];
+          const R f = wrow[b] * er[a];
+          R ux = f * xv.x, uy = -f * xv.y;
           if (edge) {
-            double wl = 0.0;
+            R wl = 0;
             if (k == 0) wl += wrow[n];
             if (k == L - 1) wl += wrow[n + 1];
-            if (wl != 0.0) {
-              const cd tb = widen(sA[i * N + jj2]);
+            if (wl != R(0)) {
+              const C tb = sA[i * N + jj2];
               ux += wl * tb.x;
               uy += wl * tb.y;
             }
           }
           if (inj) {
-            const cd cc = widen(Y[(uint64_t)k * WW + i * W + j]);
+            const C cc = Y[(uint64_t)k * WW + i * W + j];
             ux += cc.x;
             uy += cc.y;
             if (k == sp) {
               // mode weights u_m' = lambda_m' <phi_m'|A|phi_m'>: i sum ubar Gamma phi phi
-              double v = 0.0;
-              for (int mp = 0; mp < W; ++mp) v += ub[mp] * gam[mp] * phi[i * W + mp] * phi[j * W + mp];
+              R v = 0;
+              for (int mp = 0; mp < W; ++mp) v += ubR[mp] * gamR[mp] * phiR[i * W + mp] * phiR[j * W + mp];
               uy += v;
             }
           }
-          u = to_c(mk(ux, uy), C{});
+          u = C{ux, uy};
         }
         if (k > 0) u = u - t * sB[i * N + jj2];
         sB[i * N + jj2] = u;
@@ -526,18 +564,18 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : 2) adj_column_kerne
       // gamma terms
       for (int a = warp; a < W; a += kAdjThreads / 32) {
         const int site = k * W + a;
-        double zx = 0.0, zy = 0.0, ex = 0.0;
+        R zx = 0, zy = 0, ex = 0;
         for (int jj2 = lane; jj2 < ncols * W; jj2 += 32) {
           const int c = jj2 / W, j = jj2 - c * W;
-          const cd z = widen(sB[a * N + jj2]);
-          const cd x = widen(X[(uint64_t)k * XS + a * N + jj2]);
+          const C z = sB[a * N + jj2];
+          const C x = X[(uint64_t)k * XS + a * N + jj2];
           zx += z.x * x.x - z.y * x.y;
           zy += z.x * x.y + z.y * x.x;
           ex += wb[(uint64_t)(col_m(c) * W + j) * K + site] * (x.x * x.x + x.y * x.y);
         }
         if (inj) {
           for (int j = lane; j < W; j += 32) {
-            const cd ps = widen(Psi[(uint64_t)k * WW + a * W + j]);
+            const C ps = Psi[(uint64_t)k * WW + a * W + j];
             ex += wb[(uint64_t)(n + p * W + j) * K + site] * (ps.x * ps.x + ps.y * ps.y);
           }
         }
@@ -547,8 +585,8 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : 2) adj_column_kerne
           ex += __shfl_down_sync(0xffffffffu, ex, o);
         }
         if (lane == 0) {
-          atomicAdd(g.dV + so + site, 2.0 * zx);
-          atomicAdd(g.dE + so + site, zy + ex);
+          atomicAdd(g.dV + so + site, 2.0 * (double)zx);
+          atomicAdd(g.dE + so + site, (double)zy + (double)ex);
         }
       }
     }
@@ -563,7 +601,11 @@ template <typename C>
 size_t column_smem(int W) {
   const size_t NP = (size_t)adj_ncols(W) * W;
   const size_t PA = (size_t)W * W > W * NP ? (size_t)W * W : W * NP;
-  return sizeof(C) * (PA + W * NP + (size_t)W * W + 2 * W) + sizeof(int) * (size_t)(W + 2);
+  const size_t base =
+      sizeof(C) * (PA + W * NP + (size_t)W * W + 2 * W) + sizeof(int) * (size_t)(W + 2);
+  // FP32: Phi, Gamma, ubar and one slice's eta staged as FP32 behind the integer words
+  const size_t aux = sizeof(C) == 8 ? sizeof(float) * ((size_t)W * W + 3 * W) : 0;
+  return ((base + 15) & ~(size_t)15) + aux;
 }
 
 template <typename C, int RT, int RTN>
@@ -691,13 +733,13 @@ cudaError_t launch_adjoint_expand(const TaskDesc* d_tasks, int task0, int n_grou
 cudaError_t launch_adjoint_columns(const TaskDesc* d_tasks, int task0, int n_group, int W,
                                    int precision, int start_lead, const double* d_wire,
                                    const double* d_phi, const cd* d_sig, const double* d_gam,
-                                   const double* d_wbar, const double* d_ubar, uint64_t site_off0,
+                                   const void* d_wbar, const double* d_ubar, uint64_t site_off0,
                                    double* d_dV, double* d_dE, const void* d_gl, const void* d_gr,
                                    void* d_psi, void* d_tl, void* d_xs, void* d_ys, int slots,
                                    int32_t* d_err, cudaStream_t s) {
   if (n_group == 0 || slots == 0) return cudaSuccess;
   AdjArgs a{d_tasks, task0, n_group, start_lead, d_wire, d_phi, d_sig, d_gam, d_wbar, d_ubar,
-            site_off0, d_dV, d_dE, d_err};
+            site_off0, d_dV, d_dE, d_err};                  // d_wbar: FP64, or FP32 for FP32 tables
   if (precision == NEGF_FP64)
     return columns_impl<cd>(a, W, d_gl, d_gr, d_psi, d_tl, d_xs, d_ys, slots, s);
   return columns_impl<cf>(a, W, d_gl, d_gr, d_psi, d_tl, d_xs, d_ys, slots, s);

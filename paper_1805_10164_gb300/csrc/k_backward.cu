@@ -31,15 +31,16 @@ __device__ __forceinline__ cf conjc(cf a) { return cf{a.x, -a.y}; }
 
 // ---- seeds: wbar_ab = c_p (s_ab / w_ab - S_a / rowsum_a) for every row; one warp per row.
 // Injection-mode seeds ubar_m = P_hat + c_p s_m / u_m (rows = rows + 2 jobs per task: the last
-// two are the mode rows).
-template <typename R>
+// two are the mode rows).  The seeds are formed in FP64 and stored as Wo (FP64, or FP32 for the
+// block-column adjoint of FP32 tables, which forms its products in FP32).
+template <typename R, typename Wo>
 __global__ void seeds_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, uint32_t n_jobs,
                              const R* __restrict__ weights, const double* __restrict__ rowsum,
                              const double* __restrict__ mode_w, const double* __restrict__ cvals,
                              const unsigned long long* __restrict__ counts,
                              const unsigned long long* __restrict__ score, uint64_t stride,
                              const unsigned long long* __restrict__ mode_score,
-                             uint32_t mode_stride, int p, double* __restrict__ wbar,
+                             uint32_t mode_stride, int p, Wo* __restrict__ wbar,
                              double* __restrict__ ubar) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t job = blockIdx.x * (blockDim.x >> 5) + warp;
@@ -77,7 +78,7 @@ __global__ void seeds_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
       const double s = ((double)Cq[b] - Ph * ((double)C0[b] + (double)C1[b])) * invN;
       double v = 0.0;
       if (wv > 0.0) v = s / wv;
-      wbar[off + b] = c * (v - Srs);
+      wbar[off + b] = (Wo)(c * (v - Srs));
     }
   } else if (row == d.rows) {
     // injection modes of the start lead p (W up to 64: two per lane)
@@ -415,23 +416,25 @@ cudaError_t launch_backward_seeds(const TaskDesc* d_tasks, int n_tasks, uint32_t
                                   const double* d_mode_w, const double* d_c,
                                   const uint64_t* d_counts, const uint64_t* d_score,
                                   uint64_t stride, const uint64_t* d_mode_score,
-                                  uint32_t mode_stride, int start_lead, double* d_wbar,
-                                  double* d_ubar, cudaStream_t s) {
+                                  uint32_t mode_stride, int start_lead, void* d_wbar,
+                                  int wbar_fp32, double* d_ubar, cudaStream_t s) {
   if (n_jobs == 0) return cudaSuccess;
   const unsigned blocks = (n_jobs + 7) / 8;
   const auto* cnt = reinterpret_cast<const unsigned long long*>(d_counts);
   const auto* sc = reinterpret_cast<const unsigned long long*>(d_score);
   const auto* ms = reinterpret_cast<const unsigned long long*>(d_mode_score);
   if (precision == NEGF_FP64)
-    seeds_kernel<double><<<blocks, 256, 0, s>>>(d_tasks, n_tasks, n_jobs,
-                                                static_cast<const double*>(d_weights), d_rowsum,
-                                                d_mode_w, d_c, cnt, sc, stride, ms, mode_stride,
-                                                start_lead, d_wbar, d_ubar);
+    seeds_kernel<double, double><<<blocks, 256, 0, s>>>(
+        d_tasks, n_tasks, n_jobs, static_cast<const double*>(d_weights), d_rowsum, d_mode_w, d_c,
+        cnt, sc, stride, ms, mode_stride, start_lead, static_cast<double*>(d_wbar), d_ubar);
+  else if (wbar_fp32)
+    seeds_kernel<float, float><<<blocks, 256, 0, s>>>(
+        d_tasks, n_tasks, n_jobs, static_cast<const float*>(d_weights), d_rowsum, d_mode_w, d_c,
+        cnt, sc, stride, ms, mode_stride, start_lead, static_cast<float*>(d_wbar), d_ubar);
   else
-    seeds_kernel<float><<<blocks, 256, 0, s>>>(d_tasks, n_tasks, n_jobs,
-                                               static_cast<const float*>(d_weights), d_rowsum,
-                                               d_mode_w, d_c, cnt, sc, stride, ms, mode_stride,
-                                               start_lead, d_wbar, d_ubar);
+    seeds_kernel<float, double><<<blocks, 256, 0, s>>>(
+        d_tasks, n_tasks, n_jobs, static_cast<const float*>(d_weights), d_rowsum, d_mode_w, d_c,
+        cnt, sc, stride, ms, mode_stride, start_lead, static_cast<double*>(d_wbar), d_ubar);
   return cudaGetLastError();
 }
 

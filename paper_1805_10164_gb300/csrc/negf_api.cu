@@ -1608,7 +1608,7 @@ negf_status negf_current_backward(negf_ctx ctx, negf_tables t, negf_tally tl, do
     e = negf::launch_backward_seeds(t->d_tasks, nt, t->total_jobs, prec, t->d_weights, t->d_rowsum,
                                     t->d_mode_w, t->d_c, tl->d_counts, tl->d_score,
                                     tl->score_stride, tl->d_mode_score, tl->mode_stride,
-                                    tl->start_lead, d_wbar, d_ubar, s);
+                                    tl->start_lead, d_wbar, 0, d_ubar, s);
   }
   for (int k = 0; k < nt && e == cudaSuccess; ++k) {
     const TaskDesc& d = t->h_tasks[k];
@@ -1750,7 +1750,10 @@ negf_status negf_current_backward_rgf(negf_ctx ctx, negf_tables t, negf_tally tl
   unsigned char* d_ck = nullptr;
   unsigned char* d_tbuf = nullptr;
   unsigned char* d_sbuf = nullptr;
-  cudaError_t e = dalloc(&d_wbar, std::max<uint64_t>(t->score_stride, 1), s, nullptr);
+  // the weight seeds in the precision of the tables (FP32 tables: FP32 seeds, half the words)
+  const bool wbar32 = prec != NEGF_FP64;
+  const uint64_t wbar_words = std::max<uint64_t>(t->score_stride, 1);
+  cudaError_t e = dalloc(&d_wbar, wbar32 ? (wbar_words + 1) / 2 : wbar_words, s, nullptr);
   if (e == cudaSuccess) e = dalloc(&d_ubar, std::max<uint32_t>(t->mode_stride, 1), s, nullptr);
   if (e == cudaSuccess) e = dalloc(&d_dT, 2 * std::max<uint64_t>(n_sites_tasks, 1), s, nullptr);
   if (e == cudaSuccess) e = dalloc(&d_seed, std::max(nw, 1), s, nullptr);
@@ -1779,7 +1782,7 @@ negf_status negf_current_backward_rgf(negf_ctx ctx, negf_tables t, negf_tally tl
     e = negf::launch_backward_seeds(t->d_tasks, nt, t->total_jobs, prec, t->d_weights, t->d_rowsum,
                                     t->d_mode_w, t->d_c, tl->d_counts, tl->d_score,
                                     tl->score_stride, tl->d_mode_score, tl->mode_stride,
-                                    tl->start_lead, d_wbar, d_ubar, s);
+                                    tl->start_lead, d_wbar, wbar32 ? 1 : 0, d_ubar, s);
   }
   if (e == cudaSuccess) {
     ProfScope ps(ctx, "adjoint_sweep_kernel", 1);

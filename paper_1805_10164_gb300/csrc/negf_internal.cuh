@@ -227,8 +227,8 @@ cudaError_t launch_backward_seeds(const TaskDesc* d_tasks, int n_tasks, uint32_t
                                   const double* d_mode_w, const double* d_c,
                                   const uint64_t* d_counts, const uint64_t* d_score,
                                   uint64_t stride, const uint64_t* d_mode_score,
-                                  uint32_t mode_stride, int start_lead, double* d_wbar,
-                                  double* d_ubar, cudaStream_t s);
+                                  uint32_t mode_stride, int start_lead, void* d_wbar,
+                                  int wbar_fp32, double* d_ubar, cudaStream_t s);
 cudaError_t launch_backward_task(const TaskDesc& d, int precision, const void* G,
                                  const void* gphi, const double* wbar, const double* ubar,
                                  const double* eta, const double* phi, const double* gam,
@@ -255,7 +255,7 @@ cudaError_t launch_adjoint_expand(const TaskDesc* d_tasks, int task0, int n_grou
 cudaError_t launch_adjoint_columns(const TaskDesc* d_tasks, int task0, int n_group, int W,
                                    int precision, int start_lead, const double* d_wire,
                                    const double* d_phi, const cd* d_sig, const double* d_gam,
-                                   const double* d_wbar, const double* d_ubar, uint64_t site_off0,
+                                   const void* d_wbar, const double* d_ubar, uint64_t site_off0,
                                    double* d_dV, double* d_dE, const void* d_gl, const void* d_gr,
                                    void* d_psi, void* d_tl, void* d_xs, void* d_ys, int slots,
                                    int32_t* d_err, cudaStream_t s);
