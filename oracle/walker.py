@@ -21,18 +21,24 @@ from .philox import philox4x32_10
 MASK32 = np.uint64(0xFFFFFFFF)
 
 
-def walk(entries, mode_entries, n, W, c_open, task, start_lead, seed, wids, max_steps):
+def walk(entries, mode_entries, n, W, c_open, task, start_lead, seed, wids, max_steps,
+         path=None):
     """Run walkers ``wids`` (uint64 array) to absorption.  Returns (lead int32, steps uint32).
 
     entries [n + 2W, n + 2] uint64 alias rows, mode_entries [2, W] uint64 injection alias rows,
-    c_open [2] bool (lead p has an open channel).  Pinned by: the empirical absorption
-    probabilities and mean steps of many walkers against the exact chain expectation.
+    c_open [2] bool (lead p has an open channel).  ``path``, a dict, receives the walk itself:
+    "mode" (the injection mode of every walker) and "steps", one (walker positions, row, column)
+    triple per transition drawn.  Pinned by: the empirical absorption probabilities and mean
+    steps of many walkers against the exact chain expectation.
     """
     wids = np.asarray(wids, dtype=np.uint64)
     m = wids.size
     K = n + 2
     lead = np.full(m, -2, dtype=np.int32)
     steps = np.zeros(m, dtype=np.uint32)
+    if path is not None:
+        path["mode"] = np.zeros(m, dtype=np.int64)
+        path["steps"] = []
     if m == 0:
         return lead, steps
     if not c_open[start_lead]:
@@ -63,11 +69,15 @@ def walk(entries, mode_entries, n, W, c_open, task, start_lead, seed, wids, max_
             keep = y < (e & MASK32)
             mode = np.where(keep, c, (e >> np.uint64(32)).astype(np.int64))
             row[active] = n + start_lead * W + mode
+            if path is not None:
+                path["mode"][active] = mode
         else:
             c = ((x * np.uint64(K)) >> np.uint64(32)).astype(np.int64)
             e = entries[row[active], c]
             keep = y < (e & MASK32)
             j = np.where(keep, c, (e >> np.uint64(32)).astype(np.int64))
+            if path is not None:
+                path["steps"].append((active.copy(), row[active].copy(), j.copy()))
             steps[active] = s
             done = j >= n
             lead[active[done]] = (j[done] - n).astype(np.int32)
@@ -81,7 +91,7 @@ def walk(entries, mode_entries, n, W, c_open, task, start_lead, seed, wids, max_
 
 
 def walk_two_level(level1, level2, mode_entries, n, L, W, c_open, task, start_lead, seed, wids,
-                   max_steps):
+                   max_steps, path=None):
     """The same walk over two-level tables (level1 [n + 2W, L + 2] alias entries, level2
     [n + 2W, L, alias.level2_words(W)] inverse-CDF blocks).
 
@@ -89,7 +99,8 @@ def walk_two_level(level1, level2, mode_entries, n, L, W, c_open, task, start_le
     s >= 1 is transition s: words (x0, x1) draw the slice or lead from the row's level-1 entries
     (K1 = L + 2), and for a slice k the word x2 draws the site a from level-2 block (row, k)
     with v = x2 >> 1 (alias.draw_level2); the next row is k*W + a.  Outcomes and step counts as
-    in ``walk``.
+    in ``walk``; ``path`` as in ``walk``, the column of a transition being the site k W + a or
+    the lead n + r.
     Pinned by: absorption probabilities and mean steps against the exact chain expectation.
     """
     wids = np.asarray(wids, dtype=np.uint64)
@@ -97,6 +108,9 @@ def walk_two_level(level1, level2, mode_entries, n, L, W, c_open, task, start_le
     K1 = L + 2
     lead = np.full(m, -2, dtype=np.int32)
     steps = np.zeros(m, dtype=np.uint32)
+    if path is not None:
+        path["mode"] = np.zeros(m, dtype=np.int64)
+        path["steps"] = []
     if m == 0:
         return lead, steps
     if not c_open[start_lead]:
@@ -121,6 +135,8 @@ def walk_two_level(level1, level2, mode_entries, n, L, W, c_open, task, start_le
             e = mode_entries[start_lead][c]
             mode = np.where(x1 < (e & MASK32), c, (e >> np.uint64(32)).astype(np.int64))
             row[active] = n + start_lead * W + mode
+            if path is not None:
+                path["mode"][active] = mode
         else:
             r = row[active]
             c = ((x0 * np.uint64(K1)) >> np.uint64(32)).astype(np.int64)
@@ -132,6 +148,8 @@ def walk_two_level(level1, level2, mode_entries, n, L, W, c_open, task, start_le
             kk = np.where(done, 0, k)
             v = (x2 >> np.uint64(1)).astype(np.int64)
             a = draw_level2(level2[r, kk], W, v)
+            if path is not None:
+                path["steps"].append((active.copy(), r.copy(), np.where(done, n + k - L, kk * W + a)))
             row[active] = np.where(done, 0, kk * W + a)
             active = active[~done]
         s += 1

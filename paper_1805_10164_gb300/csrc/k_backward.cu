@@ -63,22 +63,49 @@ __global__ void seeds_kernel(const TaskDesc* __restrict__ tasks, int n_tasks, ui
     const uint64_t off = d.wt_off + (uint64_t)row * K;
     const unsigned long long* C0 = score + off;
     const unsigned long long* C1 = score + stride + off;
-    const unsigned long long* Cq = q == 0 ? C0 : C1;
-    // FP64 divisions are slow on this GPU: 1/N and S/rowsum once per row, s/w per entry
+    // The FP64 pipe of this GPU is narrow: 1/N and S/rowsum once per row; S from the row's
+    // integer count sums (exact): with s_ab = (Cq - Ph (C0 + C1)) / N,
+    // S = (sum Cq - Ph (sum C0 + sum C1)) / N
     const double invN = N > 0.0 ? 1.0 / N : 0.0;
-    double S = 0.0;
-    for (int b = lane; b < K; b += 32)
-      S += ((double)Cq[b] - Ph * ((double)C0[b] + (double)C1[b])) * invN;
-    for (int o = 16; o > 0; o >>= 1) S += __shfl_down_sync(0xffffffffu, S, o);
-    S = __shfl_sync(0xffffffffu, S, 0);
+    unsigned long long sq = 0, s01 = 0;
+    for (int b = lane; b < K; b += 32) {
+      const unsigned long long c0 = C0[b], c1 = C1[b];
+      sq += q == 0 ? c0 : c1;
+      s01 += c0 + c1;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      sq += __shfl_xor_sync(0xffffffffu, sq, o);
+      s01 += __shfl_xor_sync(0xffffffffu, s01, o);
+    }
+    const double S = ((double)sq - Ph * (double)s01) * invN;
     const double rs = rowsum[d.row_base + row];
     const double Srs = rs > 0.0 ? S / rs : 0.0;
+    // wbar = c (s / w - S / rs) = (c / N) (Cq - Ph (C0 + C1)) / w - c S / rs
+    const double cN = c * invN, cS = c * Srs;
     for (int b = lane; b < K; b += 32) {
-      const double wv = (double)weights[off + b];
-      const double s = ((double)Cq[b] - Ph * ((double)C0[b] + (double)C1[b])) * invN;
+      const unsigned long long c0 = C0[b], c1 = C1[b];
+      const double D = fma(-Ph, (double)(c0 + c1), (double)(q == 0 ? c0 : c1));
       double v = 0.0;
-      if (wv > 0.0) v = s / wv;
-      wbar[off + b] = (Wo)(c * (v - Srs));
+      if (sizeof(R) == 4) {
+        // FP32 weight w: 1/w from the FP32 reciprocal and one Newton step in FP64
+        // (r <- r + r (1 - w r): relative error ~2^-46, far below the FP32 table bar); weights
+        // whose reciprocal leaves the normal FP32 range are divided in FP64
+        const float wf = (float)weights[off + b];
+        if (wf > 0.f) {
+          const double wv = (double)wf;
+          if (wf >= 0x1p-125f && wf <= 0x1p125f) {
+            double r = (double)__frcp_rn(wf);
+            r = fma(r, fma(-wv, r, 1.0), r);
+            v = D * r;
+          } else {
+            v = D / wv;
+          }
+        }
+      } else {
+        const double wv = (double)weights[off + b];
+        if (wv > 0.0) v = D / wv;
+      }
+      wbar[off + b] = (Wo)fma(cN, v, -cS);
     }
   } else if (row == d.rows) {
     // injection modes of the start lead p (W up to 64: two per lane)

@@ -30,6 +30,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kFields = NEGF_TALLY_FIELDS;   // done, absorbed L, absorbed R, truncated, steps
 constexpr int kMaxWindow = 1024;             // tasks per launch (40 KB shared tally)
+constexpr int kPath = 16;                     // score walks: transitions recorded per walker
 constexpr unsigned kRun = 32;                // consecutive walkers handed to a lane at a time
 constexpr int kClaimMin = 8;                 // dry lanes that trigger a claim
 constexpr unsigned kFlushAt = 1u << 26;      // flush a lane's counters before they can overflow
@@ -49,10 +50,12 @@ __device__ __forceinline__ void flush_lane(unsigned* s_tally, int task_local, un
   }
 }
 
-// Score tallies (kScore): when a walk is absorbed at lead r it is replayed from its first draw
-// (same counters, same tables) and every transition a -> b adds 1 to score[r][a][b] of its task
-// (and the injection mode to mode_score[r][m]); these are the counts the score-function
-// gradient needs.
+// Score tallies (kScore): when a walk is absorbed at lead r every transition a -> b adds 1 to
+// score[r][a][b] of its task (and the injection mode to mode_score[r][m]); these are the counts
+// the score-function gradient needs.  The lead is known only at the end, so a walk records its
+// first kPath transitions (the column drawn at each, in shared memory: each row is the previous
+// column) and commits them when it is absorbed; a longer walk is replayed from its first draw
+// (same counters, same tables).
 struct ScoreOut {
   unsigned long long* cnt;        // [2][stride] at each task's wt_off (rows x K, either layout)
   unsigned long long* mode_cnt;   // [2][mode_stride] at each task's mode_off (2 x W)
@@ -96,7 +99,8 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
     unsigned long long* __restrict__ counter, unsigned long long* __restrict__ tally /*window*/,
     int32_t* __restrict__ trace_lead, uint32_t* __restrict__ trace_steps, ScoreOut score,
     const uint64_t* __restrict__ run) {
-  extern __shared__ unsigned s_tally[];   // [n_tasks][kFields][lo, hi]
+  extern __shared__ unsigned s_tally[];   // [n_tasks][kFields][lo, hi], then (kScore) the paths
+  uint32_t* s_path = s_tally + n_tasks * kFields * 2;   // [kPath][kThreads]
   if (run) {
     // seed and walker id offset supplied on the device (relaunched graphs)
     const uint64_t seed = run[0];
@@ -117,11 +121,16 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
   bool has[kSlots];
   unsigned long long g[kSlots];
   uint32_t row[kSlots], b[kSlots], steps[kSlots], wid_lo[kSlots], wid_hi[kSlots];
+  uint32_t inj[kSlots];                                  // kScore: the injection mode
+  // kScore: the column drawn at transition st (1-based) of the lane's walker
+  auto record = [&](uint32_t st, uint32_t j) {
+    if (kScore && st <= (uint32_t)kPath) s_path[(st - 1) * kThreads + threadIdx.x] = j;
+  };
 #pragma unroll
   for (int sl = 0; sl < kSlots; ++sl) {
     has[sl] = false;
     g[sl] = 0;
-    row[sl] = b[sl] = steps[sl] = wid_lo[sl] = wid_hi[sl] = 0;
+    row[sl] = b[sl] = steps[sl] = wid_lo[sl] = wid_hi[sl] = inj[sl] = 0;
   }
   // this lane's run of walker indices [r_next, r_end)
   unsigned long long r_next = 0, r_end = 0;
@@ -228,10 +237,12 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
         if (b[sl] == 0) {
           const uint32_t c = __umulhi(r.x, W);
           const uint64_t e = __ldg(mrow + c);
-          row[sl] = inj_row0 + (r.y < (uint32_t)e ? c : (uint32_t)(e >> 32));
+          inj[sl] = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+          row[sl] = inj_row0 + inj[sl];
         } else {
           const uint32_t j = two_level_draw(l1row, trow, row[sl], L, W, B2, r);
           ++steps[sl];
+          record(steps[sl], j);
           if (j >= n) outcome = (int)(j - n);
           else if (steps[sl] >= max_steps) outcome = -2;
           else row[sl] = j;
@@ -241,12 +252,14 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
         if (b[sl] == 0) {
           const uint32_t c = __umulhi(r.x, W);
           const uint64_t e = __ldg(mrow + c);
-          row[sl] = inj_row0 + (r.y < (uint32_t)e ? c : (uint32_t)(e >> 32));
+          inj[sl] = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
+          row[sl] = inj_row0 + inj[sl];
         } else {
           const uint32_t c = __umulhi(r.x, K);
           const uint64_t e = __ldg(trow + (uint64_t)row[sl] * K + c);
           const uint32_t j = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
           ++steps[sl];
+          record(steps[sl], j);
           if (j >= n) outcome = (int)(j - n);
           else if (steps[sl] >= max_steps) outcome = -2;
           else row[sl] = j;
@@ -256,14 +269,25 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
           const uint64_t e = __ldg(trow + (uint64_t)row[sl] * K + c);
           const uint32_t j = r.w < (uint32_t)e ? c : (uint32_t)(e >> 32);
           ++steps[sl];
+          record(steps[sl], j);
           if (j >= n) outcome = (int)(j - n);
           else if (steps[sl] >= max_steps) outcome = -2;
           else row[sl] = j;
         }
         ++b[sl];
       }
-      if (kScore && outcome >= 0) {
-        // replay the finished walk and count its transitions under its absorbing lead
+      if (kScore && outcome >= 0 && steps[sl] <= (uint32_t)kPath) {
+        // count the recorded transitions of the finished walk under its absorbing lead
+        unsigned long long* cnt = score.cnt + (size_t)outcome * score.stride + t_wt_off;
+        atomicAdd(score.mode_cnt + (size_t)outcome * score.mode_stride + t_mode_off + inj[sl], 1ull);
+        uint32_t rrow = inj_row0 + inj[sl];
+        for (uint32_t st = 0; st < steps[sl]; ++st) {
+          const uint32_t j = s_path[st * kThreads + threadIdx.x];
+          atomicAdd(cnt + (uint64_t)rrow * K + j, 1ull);
+          rrow = j;
+        }
+      } else if (kScore && outcome >= 0) {
+        // a walk longer than the record: replay it and count its transitions
         unsigned long long* cnt = score.cnt + (size_t)outcome * score.stride + t_wt_off;
         unsigned long long* mcnt =
             score.mode_cnt + (size_t)outcome * score.mode_stride + t_mode_off;
@@ -393,7 +417,8 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const unsigned long long total = (unsigned long long)nt * walkers_per_task;
-    const size_t smem = sizeof(unsigned) * 2 * (size_t)nt * kFields;
+    const size_t smem = sizeof(unsigned) * 2 * (size_t)nt * kFields +
+                        (d_score ? sizeof(uint32_t) * kPath * kThreads : 0);
     const ScoreOut so{reinterpret_cast<unsigned long long*>(d_score),
                       reinterpret_cast<unsigned long long*>(d_mode_score),
                       (unsigned long long)score_stride, mode_stride};

@@ -399,6 +399,42 @@ def test_walker_reproducible_and_truncation():
     assert np.array_equal(lead >= 0, (a[1] <= 2))
 
 
+@pytest.mark.parametrize("two_level", [False, True])
+def test_walker_path_is_the_walk(two_level):
+    """The recorded path is the walk itself: one transition per step, the first row the
+    injection row of the drawn mode, each later row the previous column, the last column of an
+    absorbed walk its lead, and the empirical transition frequencies out of a row those of the
+    row's weights."""
+    on, et = _wire(6, 2, 10, 0.5)
+    r = pipeline.task_reference(on, et, 1.0, -0.3)
+    n, W = r["n"], r["W"]
+    ids = np.arange(3000)
+    path = {}
+    if two_level:
+        l1, l2 = alias.build_two_level(r["tab"]["w"], 10, 2)
+        lead, steps = walker.walk_two_level(l1, l2, r["mode_entries"], n, 10, W, r["c_open"], 5,
+                                            1, 77, ids, 10**6, path=path)
+    else:
+        lead, steps = walker.walk(r["entries"], r["mode_entries"], n, W, r["c_open"], 5, 1, 77,
+                                  ids, 10**6, path=path)
+    assert np.all(lead >= 0)
+    seen = np.zeros(ids.size, dtype=np.int64)
+    cur = n + 1 * W + path["mode"]
+    counts = np.zeros_like(r["tab"]["w"])
+    for idx, row, col in path["steps"]:
+        assert np.array_equal(row, cur[idx])
+        seen[idx] += 1
+        cur[idx] = col
+        np.add.at(counts, (row, col), 1.0)
+    assert np.array_equal(seen, steps.astype(np.int64))
+    assert np.array_equal(cur - n, lead)
+    P = r["tab"]["w"] / r["tab"]["w"].sum(1, keepdims=True)
+    busy = counts.sum(1) > 2000
+    assert busy.any()
+    emp = counts[busy] / counts[busy].sum(1, keepdims=True)
+    assert np.max(np.abs(emp - P[busy])) < 6 * np.sqrt(0.25 / 2000)
+
+
 def test_walker_closed_lead():
     """Energy outside the lead band: no open channel, nothing is injected."""
     r = pipeline.task_reference(np.zeros((6, 1)), np.full((6, 1), 0.1), 1.0, 2.5)
