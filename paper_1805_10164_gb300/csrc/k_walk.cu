@@ -41,6 +41,15 @@ __device__ __forceinline__ void smem_add64(unsigned* lohi, unsigned v) {
   if (old + v < old) atomicAdd(lohi + 1, 1u);
 }
 
+// copy 0 of the injection-mode counts <- the sum of the kModeReplicas copies (m2 = 2 mode_stride)
+__global__ void mode_reduce_kernel(unsigned long long* __restrict__ mode, uint32_t m2) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= m2) return;
+  unsigned long long v = 0;
+  for (int r = 0; r < kModeReplicas; ++r) v += mode[(size_t)r * m2 + i];
+  mode[i] = v;
+}
+
 __device__ __forceinline__ void flush_lane(unsigned* s_tally, int task_local, unsigned (&a)[kFields]) {
   unsigned* t = s_tally + task_local * kFields * 2;
 #pragma unroll
@@ -91,7 +100,7 @@ __device__ __forceinline__ uint32_t two_level_draw(const uint64_t* __restrict__ 
 
 // kTwo: the launch may hold two-level tasks (one-level launches compile without that path).
 template <bool kTrace, bool kScore, int kSlotsReq, bool kTwo>
-__global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
+__global__ void __launch_bounds__(kThreads, kScore ? 3 : (kSlotsReq == 2 ? 4 : 5)) walk_kernel(
     const TaskDesc* __restrict__ tasks, int task0, int n_tasks, uint32_t id_base,
     const uint64_t* __restrict__ tab, const uint64_t* __restrict__ mode_tab,
     const double* __restrict__ cvals, int start_lead, PhiloxKey key, uint64_t walkers_per_task,
@@ -100,7 +109,7 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
     int32_t* __restrict__ trace_lead, uint32_t* __restrict__ trace_steps, ScoreOut score,
     const uint64_t* __restrict__ run) {
   extern __shared__ unsigned s_tally[];   // [n_tasks][kFields][lo, hi], then (kScore) the paths
-  uint32_t* s_path = s_tally + n_tasks * kFields * 2;   // [kPath][kThreads]
+  uint32_t* s_path = s_tally + n_tasks * kFields * 2;   // [kSlots][kPath][kThreads]
   if (run) {
     // seed and walker id offset supplied on the device (relaunched graphs)
     const uint64_t seed = run[0];
@@ -115,16 +124,17 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
   const unsigned lt_mask = (1u << lane) - 1u;
   const unsigned long long total = (unsigned long long)n_tasks * walkers_per_task;
 
-  // kSlots walkers per lane (registers), so that their dependent gathers overlap (one when the
-  // transitions are also replayed for the score tally); b = next Philox block (draws 2b, 2b + 1)
-  constexpr int kSlots = kScore ? 1 : kSlotsReq;
+  // kSlots walkers per lane (registers), so that their dependent gathers overlap; b = next
+  // Philox block (draws 2b, 2b + 1)
+  constexpr int kSlots = kSlotsReq;
   bool has[kSlots];
   unsigned long long g[kSlots];
   uint32_t row[kSlots], b[kSlots], steps[kSlots], wid_lo[kSlots], wid_hi[kSlots];
   uint32_t inj[kSlots];                                  // kScore: the injection mode
-  // kScore: the column drawn at transition st (1-based) of the lane's walker
-  auto record = [&](uint32_t st, uint32_t j) {
-    if (kScore && st <= (uint32_t)kPath) s_path[(st - 1) * kThreads + threadIdx.x] = j;
+  // kScore: the column drawn at transition st (1-based) of the lane's walker in slot sl
+  auto record = [&](int sl, uint32_t st, uint32_t j) {
+    if (kScore && st <= (uint32_t)kPath)
+      s_path[((uint32_t)sl * kPath + st - 1) * kThreads + threadIdx.x] = j;
   };
 #pragma unroll
   for (int sl = 0; sl < kSlots; ++sl) {
@@ -242,7 +252,7 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
         } else {
           const uint32_t j = two_level_draw(l1row, trow, row[sl], L, W, B2, r);
           ++steps[sl];
-          record(steps[sl], j);
+          record(sl, steps[sl], j);
           if (j >= n) outcome = (int)(j - n);
           else if (steps[sl] >= max_steps) outcome = -2;
           else row[sl] = j;
@@ -259,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
           const uint64_t e = __ldg(trow + (uint64_t)row[sl] * K + c);
           const uint32_t j = r.y < (uint32_t)e ? c : (uint32_t)(e >> 32);
           ++steps[sl];
-          record(steps[sl], j);
+          record(sl, steps[sl], j);
           if (j >= n) outcome = (int)(j - n);
           else if (steps[sl] >= max_steps) outcome = -2;
           else row[sl] = j;
@@ -269,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
           const uint64_t e = __ldg(trow + (uint64_t)row[sl] * K + c);
           const uint32_t j = r.w < (uint32_t)e ? c : (uint32_t)(e >> 32);
           ++steps[sl];
-          record(steps[sl], j);
+          record(sl, steps[sl], j);
           if (j >= n) outcome = (int)(j - n);
           else if (steps[sl] >= max_steps) outcome = -2;
           else row[sl] = j;
@@ -279,10 +289,13 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
       if (kScore && outcome >= 0 && steps[sl] <= (uint32_t)kPath) {
         // count the recorded transitions of the finished walk under its absorbing lead
         unsigned long long* cnt = score.cnt + (size_t)outcome * score.stride + t_wt_off;
-        atomicAdd(score.mode_cnt + (size_t)outcome * score.mode_stride + t_mode_off + inj[sl], 1ull);
+        atomicAdd(score.mode_cnt +
+                      ((size_t)(blockIdx.x % kModeReplicas) * 2 + outcome) * score.mode_stride +
+                      t_mode_off + inj[sl],
+                  1ull);
         uint32_t rrow = inj_row0 + inj[sl];
         for (uint32_t st = 0; st < steps[sl]; ++st) {
-          const uint32_t j = s_path[st * kThreads + threadIdx.x];
+          const uint32_t j = s_path[((uint32_t)sl * kPath + st) * kThreads + threadIdx.x];
           atomicAdd(cnt + (uint64_t)rrow * K + j, 1ull);
           rrow = j;
         }
@@ -290,7 +303,8 @@ __global__ void __launch_bounds__(kThreads, kSlotsReq == 2 ? 4 : 5) walk_kernel(
         // a walk longer than the record: replay it and count its transitions
         unsigned long long* cnt = score.cnt + (size_t)outcome * score.stride + t_wt_off;
         unsigned long long* mcnt =
-            score.mode_cnt + (size_t)outcome * score.mode_stride + t_mode_off;
+            score.mode_cnt + ((size_t)(blockIdx.x % kModeReplicas) * 2 + outcome) * score.mode_stride +
+            t_mode_off;
         uint32_t rrow = 0;
         bool live = true;
         for (uint32_t bb = 0; live; ++bb) {
@@ -417,6 +431,7 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
     cudaError_t e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
     const unsigned long long total = (unsigned long long)nt * walkers_per_task;
+    // score walks: one slot (a second measured slower), with its path record
     const size_t smem = sizeof(unsigned) * 2 * (size_t)nt * kFields +
                         (d_score ? sizeof(uint32_t) * kPath * kThreads : 0);
     const ScoreOut so{reinterpret_cast<unsigned long long*>(d_score),
@@ -450,6 +465,12 @@ cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_
         d_trace_lead, d_trace_steps, so, d_run);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+  }
+  if (d_mode_score) {
+    const uint32_t m2 = 2 * mode_stride;
+    mode_reduce_kernel<<<(m2 + 255) / 256, 256, 0, s>>>(
+        reinterpret_cast<unsigned long long*>(d_mode_score), m2);
+    return cudaGetLastError();
   }
   return cudaSuccess;
 }

@@ -1488,13 +1488,14 @@ negf_status negf_walk_score(negf_ctx ctx, negf_tables t, int32_t start_lead, uin
   const size_t nc = (size_t)std::max(1, t->n_tasks) * NEGF_TALLY_FIELDS;
   cudaError_t e = dalloc(&tl->d_counts, nc, s, nullptr);
   if (e == cudaSuccess) e = dalloc(&tl->d_score, 2 * std::max<uint64_t>(tl->score_stride, 1), s, nullptr);
-  if (e == cudaSuccess) e = dalloc(&tl->d_mode_score, 2 * (size_t)std::max<uint32_t>(tl->mode_stride, 1), s, nullptr);
+  // the injection-mode counts in negf::kModeReplicas copies, summed into the first by the walk
+  const size_t mode_words = 2 * (size_t)std::max<uint32_t>(tl->mode_stride, 1) * negf::kModeReplicas;
+  if (e == cudaSuccess) e = dalloc(&tl->d_mode_score, mode_words, s, nullptr);
   if (e == cudaSuccess) e = cudaMemsetAsync(tl->d_counts, 0, sizeof(uint64_t) * nc, s);
   if (e == cudaSuccess)
     e = cudaMemsetAsync(tl->d_score, 0, sizeof(uint64_t) * 2 * std::max<uint64_t>(tl->score_stride, 1), s);
   if (e == cudaSuccess)
-    e = cudaMemsetAsync(tl->d_mode_score, 0,
-                        sizeof(uint64_t) * 2 * std::max<uint32_t>(tl->mode_stride, 1), s);
+    e = cudaMemsetAsync(tl->d_mode_score, 0, sizeof(uint64_t) * mode_words, s);
   if (e == cudaSuccess) {
     ProfScope ps(ctx, "walk_score_kernel", (t->n_tasks + 1023) / 1024);
     e = negf::launch_walk(t->d_tasks, 0, t->n_tasks, 0, t->d_tab, t->d_mode_tab, t->d_c,

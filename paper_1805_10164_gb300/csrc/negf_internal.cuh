@@ -177,11 +177,15 @@ cudaError_t launch_two_level_split(const TaskDesc* d_tasks, int n_tasks, uint32_
 // the counters of those tasks (index 0 = task0).  The Philox task number of d_tasks[k] is
 // id_base + k.  max_blocks_per_sm > 0 caps the persistent grid (leaving room for concurrent
 // kernels).  With d_score non-null every absorbed walk also adds its transitions to
-// d_score[lead][tab_off + a K + b] and its injection mode to d_mode_score[lead][mode_off + m].
+// d_score[lead][tab_off + a K + b] and its injection mode to d_mode_score[lead][mode_off + m]:
+// d_mode_score holds kModeReplicas zeroed copies [replica][lead][mode_stride] (every walker of a
+// task adds to the same W counters; each block adds to copy blockIdx % kModeReplicas), summed
+// into copy 0 before the call returns.
 // With d_run non-null the seed and id_offset arguments are ignored and read on the device from
 // d_run[0] (seed) and d_run[1] (walker id offset), so a captured graph can be relaunched with
 // new values.  two_level: some task of the launch has two-level tables (false: every task is
 // one-level, and the launch takes a kernel compiled without the two-level draw).
+constexpr int kModeReplicas = 64;
 cudaError_t launch_walk(const TaskDesc* d_tasks, int task0, int n_tasks, uint32_t id_base,
                         const uint64_t* d_tab, const uint64_t* d_mode_tab, const double* d_c,
                         int start_lead, uint64_t seed, uint64_t walkers_per_task,
