@@ -230,6 +230,27 @@ __device__ __forceinline__ void load_block(C* dst, const C* __restrict__ src, in
   for (int idx = threadIdx.x; idx < count; idx += blockDim.x) dst[idx] = src[idx];
 }
 
+// A block of up to 256 RT^2 entries (a W x W block, W <= 16 RT) read into registers one step
+// ahead: fetch() issues the loads before a product, put() stores them after it.
+template <typename C, int RT>
+struct BlockAhead {
+  C v[RT * RT];
+  __device__ __forceinline__ void fetch(const C* __restrict__ src, int count) {
+#pragma unroll
+    for (int q = 0; q < RT * RT; ++q) {
+      const int idx = threadIdx.x + q * kAdjThreads;
+      if (idx < count) v[q] = src[idx];
+    }
+  }
+  __device__ __forceinline__ void put(C* dst, int count) const {
+#pragma unroll
+    for (int q = 0; q < RT * RT; ++q) {
+      const int idx = threadIdx.x + q * kAdjThreads;
+      if (idx < count) dst[idx] = v[q];
+    }
+  }
+};
+
 struct AdjArgs {
   const TaskDesc* tasks;
   int task0, n_group, p;
@@ -368,12 +389,19 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : (sizeof(C) == 8 ? 3
         sB[a * N + c * W + b] = X[(uint64_t)m * XS + a * N + c * W + b];
       }
     };
+    // narrow panels (RT = 1): each step's g block, panel entries and seeds are read one step
+    // ahead, while the previous product runs
+    constexpr bool kAhead = RT == 1;
+    BlockAhead<C, RT> ga;
+    if (kAhead && m_hi - 1 >= 0) ga.fetch(gl + (uint64_t)(m_hi - 1) * WW, WW);
     for (int k = m_hi - 1; k >= 0; --k) {
       __syncthreads();
       for (int c = 0; c < ncols; ++c)
         if (col_m(c) == k + 1) inject(c, col_m(c));
-      load_block(sA, gl + (uint64_t)k * WW, WW);
+      if (kAhead) ga.put(sA, WW);
+      else load_block(sA, gl + (uint64_t)k * WW, WW);
       __syncthreads();
+      if (kAhead && k > 0) ga.fetch(gl + (uint64_t)(k - 1) * WW, WW);
       cta_prod<C, RT, RTN>(sA, sB, W, N, acc);
       __syncthreads();
       for_tile<RT, RTN>(W, N, [&](int a, int b, int i, int j) {
@@ -382,12 +410,15 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : (sizeof(C) == 8 ? 3
         if (col_m(j / W) > k) X[(uint64_t)k * XS + i * N + j] = v;
       });
     }
+    if (kAhead && m_lo + 1 < L) ga.fetch(gr + (uint64_t)(m_lo + 1) * WW, WW);
     for (int k = m_lo + 1; k < L; ++k) {
       __syncthreads();
       for (int c = 0; c < ncols; ++c)
         if (col_m(c) == k - 1) inject(c, col_m(c));
-      load_block(sA, gr + (uint64_t)k * WW, WW);
+      if (kAhead) ga.put(sA, WW);
+      else load_block(sA, gr + (uint64_t)k * WW, WW);
       __syncthreads();
+      if (kAhead && k + 1 < L) ga.fetch(gr + (uint64_t)(k + 1) * WW, WW);
       cta_prod<C, RT, RTN>(sA, sB, W, N, acc);
       __syncthreads();
       for_tile<RT, RTN>(W, N, [&](int a, int b, int i, int j) {
@@ -480,6 +511,31 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : (sizeof(C) == 8 ? 3
       sT[idx] = C{v, R(0)};
     }
     // ---- forward elimination: y_k = g^L_k (U_k - t y_{k-1}), U_k = Gbar[k-block, columns]
+    // kAhead: this thread's panel entries X[k][i][jj2], seeds wbar_{(m,j),(k,i)} and eta of
+    // slice k, read one step ahead
+    C xa[RT][RTN];
+    R wa[RT][RTN], ea[RT];
+    auto fetch_eta = [&](int k) {
+#pragma unroll
+      for (int a = 0; a < RT; ++a) {
+        const int i = (tid >> 4) + 16 * a;
+        ea[a] = i < W ? (R)eta[k * W + i] : R(0);
+      }
+    };
+    auto fetch_seeds = [&](int k) {
+      fetch_eta(k);
+      for_tile<RT, RTN>(W, N, [&](int a, int bb, int i, int jj2) {
+        const int c = jj2 / W, j = jj2 - c * W;
+        if (c < ncols) {
+          xa[a][bb] = X[(uint64_t)k * XS + i * N + jj2];
+          wa[a][bb] = wb[(uint64_t)(col_m(c) * W + j) * K + k * W + i];
+        }
+      });
+    };
+    if (kAhead) {
+      ga.fetch(gl, WW);
+      fetch_seeds(0);
+    }
     for (int k = 0; k < L; ++k) {
       const bool edge = k == 0 || k == L - 1;
       __syncthreads();
@@ -495,21 +551,22 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : (sizeof(C) == 8 ? 3
       // in the products' thread layout (row i, panel column jj2 = c W + j): the panel's shared
       // and global accesses stay conflict-free and coalesced; the seeds wbar_{(m,j),(k,i)} are
       // read two rows of 16 per warp
-      R er[RT];                                        // eta of this thread's rows of slice k
-#pragma unroll
-      for (int a = 0; a < RT; ++a) {
-        const int i = (tid >> 4) + 16 * a;
-        er[a] = i < W ? (R)eta[k * W + i] : R(0);
-      }
-      for_tile<RT, RTN>(W, N, [&](int a, int, int i, int jj2) {
+      if (!kAhead) fetch_eta(k);
+      for_tile<RT, RTN>(W, N, [&](int a, int bb, int i, int jj2) {
         const int c = jj2 / W, j = jj2 - c * W;
         C u = C{R(0), R(0)};
         if (c < ncols) {
           const int m = col_m(c);
           const R* wrow = wb + (uint64_t)(m * W + j) * K;
-          const int b = k * W + i;
-          const C xv = X[(uint64_t)k * XS + i * N + jj2];
-          const R f = wrow[b] * er[a];
+          C xv;
+          R f;
+          if constexpr (RT == 1) {                     // read one step ahead
+            xv = xa[a][bb];
+            f = wa[a][bb] * ea[a];
+          } else {
+            xv = X[(uint64_t)k * XS + i * N + jj2];
+            f = wrow[k * W + i] * ea[a];
+          }
           R ux = f * xv.x, uy = -f * xv.y;
           if (edge) {
             R wl = 0;
@@ -538,8 +595,13 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : (sizeof(C) == 8 ? 3
         sB[i * N + jj2] = u;
       });
       __syncthreads();
-      load_block(sA, gl + (uint64_t)k * WW, WW);
+      if (kAhead) ga.put(sA, WW);
+      else load_block(sA, gl + (uint64_t)k * WW, WW);
       __syncthreads();
+      if (kAhead && k + 1 < L) {
+        ga.fetch(gl + (uint64_t)(k + 1) * WW, WW);
+        fetch_seeds(k + 1);
+      }
       cta_prod<C, RT, RTN>(sA, sB, W, N, acc);
       __syncthreads();
       for_tile<RT, RTN>(W, N, [&](int a, int b, int i, int j) {
@@ -548,45 +610,104 @@ __global__ void __launch_bounds__(kAdjThreads, RT >= 2 ? 1 : (sizeof(C) == 8 ? 3
       });
     }
     // ---- back substitution z_k = y_k - t g^L_k z_{k+1}, and the diagonal of G Gbar G
+    // kAhead: g^L_k, this thread's y_k entries (in xa) and its warp's diagonal inputs (rows
+    // a = warp + 8 q, panel columns lane + 32 e: X[k] and the seeds) read one step ahead
+    C xd[2][2];
+    R wd[2][2];
+    auto fetch_y = [&](int k) {
+      for_tile<RT, RTN>(W, N, [&](int a, int bb, int i, int j) {
+        xa[a][bb] = Y[(uint64_t)k * XS + i * N + j];
+      });
+    };
+    auto fetch_diag = [&](int k) {
+#pragma unroll
+      for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int a = warp + 8 * q, jj2 = lane + 32 * e;
+          if (a < W && jj2 < ncols * W) {
+            const int c = jj2 / W, j = jj2 - c * W;
+            xd[q][e] = X[(uint64_t)k * XS + a * N + jj2];
+            wd[q][e] = wb[(uint64_t)(col_m(c) * W + j) * K + k * W + a];
+          }
+        }
+    };
+    // the diagonal of row a of slice k from z (sB) and X[k]: sum_j z[a][j] X[a][j] and the
+    // explicit gamma terms, added to the gradient by lane 0
+    auto diag_row = [&](int k, int a, R zx, R zy, R ex) {
+      const int site = k * W + a;
+      if (inj) {
+        for (int j = lane; j < W; j += 32) {
+          const C ps = Psi[(uint64_t)k * WW + a * W + j];
+          ex += wb[(uint64_t)(n + p * W + j) * K + site] * (ps.x * ps.x + ps.y * ps.y);
+        }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        zx += __shfl_down_sync(0xffffffffu, zx, o);
+        zy += __shfl_down_sync(0xffffffffu, zy, o);
+        ex += __shfl_down_sync(0xffffffffu, ex, o);
+      }
+      if (lane == 0) {
+        atomicAdd(g.dV + so + site, 2.0 * (double)zx);
+        atomicAdd(g.dE + so + site, (double)zy + (double)ex);
+      }
+    };
+    if (kAhead) {
+      if (L >= 2) {
+        ga.fetch(gl + (uint64_t)(L - 2) * WW, WW);
+        fetch_y(L - 2);
+      }
+      fetch_diag(L - 1);
+    }
     for (int k = L - 1; k >= 0; --k) {
       if (k < L - 1) {
         __syncthreads();
-        load_block(sA, gl + (uint64_t)k * WW, WW);
+        if (kAhead) ga.put(sA, WW);
+        else load_block(sA, gl + (uint64_t)k * WW, WW);
         __syncthreads();
+        if (kAhead && k > 0) ga.fetch(gl + (uint64_t)(k - 1) * WW, WW);
         cta_prod<C, RT, RTN>(sA, sB, W, N, acc);
         __syncthreads();
         for_tile<RT, RTN>(W, N, [&](int a, int b, int i, int j) {
-          sB[i * N + j] = Y[(uint64_t)k * XS + i * N + j] - t * acc[a][b];
+          const C y = kAhead ? xa[a][b] : Y[(uint64_t)k * XS + i * N + j];
+          sB[i * N + j] = y - t * acc[a][b];
         });
+        if (kAhead && k > 0) fetch_y(k - 1);
       }
       __syncthreads();
-      // site (k, a): warp per row; sum over the columns of z[a][.] X[a][.] and the explicit
-      // gamma terms
-      for (int a = warp; a < W; a += kAdjThreads / 32) {
-        const int site = k * W + a;
-        R zx = 0, zy = 0, ex = 0;
-        for (int jj2 = lane; jj2 < ncols * W; jj2 += 32) {
-          const int c = jj2 / W, j = jj2 - c * W;
-          const C z = sB[a * N + jj2];
-          const C x = X[(uint64_t)k * XS + a * N + jj2];
-          zx += z.x * x.x - z.y * x.y;
-          zy += z.x * x.y + z.y * x.x;
-          ex += wb[(uint64_t)(col_m(c) * W + j) * K + site] * (x.x * x.x + x.y * x.y);
-        }
-        if (inj) {
-          for (int j = lane; j < W; j += 32) {
-            const C ps = Psi[(uint64_t)k * WW + a * W + j];
-            ex += wb[(uint64_t)(n + p * W + j) * K + site] * (ps.x * ps.x + ps.y * ps.y);
+      if constexpr (RT == 1) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int a = warp + 8 * q;
+          if (a >= W) continue;                          // warp-uniform
+          R zx = 0, zy = 0, ex = 0;
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int jj2 = lane + 32 * e;
+            if (jj2 < ncols * W) {
+              const C z = sB[a * N + jj2];
+              const C x = xd[q][e];
+              zx += z.x * x.x - z.y * x.y;
+              zy += z.x * x.y + z.y * x.x;
+              ex += wd[q][e] * (x.x * x.x + x.y * x.y);
+            }
           }
+          diag_row(k, a, zx, zy, ex);
         }
-        for (int o = 16; o > 0; o >>= 1) {
-          zx += __shfl_down_sync(0xffffffffu, zx, o);
-          zy += __shfl_down_sync(0xffffffffu, zy, o);
-          ex += __shfl_down_sync(0xffffffffu, ex, o);
-        }
-        if (lane == 0) {
-          atomicAdd(g.dV + so + site, 2.0 * (double)zx);
-          atomicAdd(g.dE + so + site, (double)zy + (double)ex);
+        if (k > 0) fetch_diag(k - 1);
+      } else {
+        for (int a = warp; a < W; a += kAdjThreads / 32) {
+          const int site = k * W + a;
+          R zx = 0, zy = 0, ex = 0;
+          for (int jj2 = lane; jj2 < ncols * W; jj2 += 32) {
+            const int c = jj2 / W, j = jj2 - c * W;
+            const C z = sB[a * N + jj2];
+            const C x = X[(uint64_t)k * XS + a * N + jj2];
+            zx += z.x * x.x - z.y * x.y;
+            zy += z.x * x.y + z.y * x.x;
+            ex += wb[(uint64_t)(col_m(c) * W + j) * K + site] * (x.x * x.x + x.y * x.y);
+          }
+          diag_row(k, a, zx, zy, ex);
         }
       }
     }
