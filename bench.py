@@ -78,7 +78,7 @@ def tensor_peak(kind):
 # wire (8 tasks) by the units processed (the blocks written and the g blocks read both grow as
 # n^2 per task): x 100 per task, x 256 / 8 tasks.
 MEASURED_TRAFFIC = {
-    ("walk_kernel", "wire_W10_L50_eta0.05_64E", "2175f1dcd66360d9"): 133278464,
+    ("walk_kernel", "wire_W10_L50_eta0.05_64E", "83e0ebef3d6f1969"): 133926400,
     ("chain_cta_kernel", "wire_W64_L1000_eta0.005_256E", "a3bffe9ce92a6da4"): 5145210496000,
 }
 TRAFFIC_SOURCES = {"walk_kernel": ["k_walk.cu", "philox.cuh"],
