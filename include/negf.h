@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define NEGF_ABI_VERSION 5
+#define NEGF_ABI_VERSION 6
 #define NEGF_MAX_W 64            /* widest supported slice (sites across the wire) */
 #define NEGF_MAX_SITES 6400      /* largest W*L per wire with one-level tables */
 #define NEGF_MAX_SITES_TWO_LEVEL 65536 /* largest W*L per wire with two-level tables */
@@ -317,13 +317,44 @@ int32_t negf_plan_num_waves(negf_plan plan);
 uint64_t negf_plan_device_bytes(negf_plan plan);
 void negf_plan_destroy(negf_plan plan);
 
+/* --- inelastic Buttiker probes (Sec. II.F, Step 7') ----------------------------------------- */
+
+/* Walks in which the walker's energy changes at every probe it visits (Step 7', Eq.
+ * draw_E_last): after Step 6' has drawn a site j at the walker's grid energy E_e, the next
+ * energy E_e' of the wire's grid is drawn with probability proportional to
+ * w_e' exp(-(E_e' - E_e)^2 / (2 sigma_E^2)) A_jj(E_e') (w_e' the energy's weight from
+ * negf_wire.energy_weight, A_jj the row sum of site row j at E_e'; sigma_E = 0: the same energy,
+ * the elastic walk's law).  This is Buttiker's inelastic probe with the redistribution rate
+ * lambda~_j(E', E) = eta_j K(E' - E) / sum_E'' w K(E'' - E) A_jj(E''), which satisfies the
+ * charge-conservation condition (Eq. condition4_buttiker) with gamma_j = eta_j, so the Step 6'
+ * tables of every energy are the elastic ones.  Walker ids, seeds, max_steps and the tally are
+ * as for negf_walk; counts go to the injection task, so that negf_current gives
+ * T_qp(E_0) = c_p(E_0) P(q | p, E_0) per injection energy.  Random numbers: Philox block 0 is
+ * the injection draw; block s >= 1 is transition s, words (x0, x1) for the next index from the
+ * row at the walker's energy, (x2, x3) for the next energy from the energy row of the site
+ * drawn.  Needs one-level tables (NEGF_E_INVALID for two-level ones) with every grid energy of
+ * a wire in the same handle; sigma_E finite and >= 0.  The energy rows ([sites][nE] alias rows
+ * per task, built on the device for the call) are freed before it returns. */
+negf_status negf_walk_inelastic(negf_ctx ctx, negf_tables tables, int32_t start_lead,
+                                uint64_t seed, uint64_t walkers_per_task,
+                                uint64_t walker_id_offset, uint32_t max_steps, double sigma_E,
+                                negf_tally* out);
+/* The Step 7' energy rows of task `task` (the wire's energy E_e of that task): host_buf gets
+ * n x nE alias entries (site-major; entry = threshold | alias << 32 over the wire's nE grid
+ * energies), built as negf_walk_inelastic builds them.  host_buf NULL: *bytes receives the size
+ * needed.  Synchronises. */
+negf_status negf_export_energy_tables(negf_ctx ctx, negf_tables tables, int32_t task,
+                                      double sigma_E, void* host_buf, size_t* bytes);
+
 /* --- gradient (paper silent) ---------------------------------------------------------------- */
 
-/* negf_walk that also records score tallies: every walk absorbed at lead r is replayed and
- * each transition a -> b adds 1 to counts[r][table_offset + a K + b] of its task (b a site, or
- * n + r' for lead r'; the same rows x K numbering for one- and two-level tables), its injection
- * mode m to mode_counts[r][mode_offset + p W + m] (offsets from negf_get_task_info).  Replaying
- * doubles the walk work.  The tables must still hold their alias rows (negf_build_tables). */
+/* negf_walk that also records score tallies: for every walk absorbed at lead r each transition
+ * a -> b adds 1 to counts[r][table_offset + a K + b] of its task (b a site, or n + r' for lead
+ * r'; the same rows x K numbering for one- and two-level tables), its injection mode m to
+ * mode_counts[r][mode_offset + p W + m] (offsets from negf_get_task_info).  A walk's transitions
+ * are recorded as it walks (up to 128; longer walks are replayed from their first draw), the
+ * same walks as negf_walk with the same arguments.  The tables must still hold their alias rows
+ * (negf_build_tables). */
 negf_status negf_walk_score(negf_ctx ctx, negf_tables tables, int32_t start_lead, uint64_t seed,
                             uint64_t walkers_per_task, uint64_t walker_id_offset,
                             uint32_t max_steps, negf_tally* out);

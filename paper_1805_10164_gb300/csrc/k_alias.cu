@@ -496,6 +496,50 @@ __global__ void __launch_bounds__(32 * kL2Warps) level2_cdf_kernel(
   if (__any_sync(0xffffffffu, !ok) && lane == 0) atomicOr(err, ERR_NONFINITE);
 }
 
+// Step 7' energy rows of inelastic Buttiker probes (Sec. II.F, Eq. draw_E_last): for task t (the
+// energy E_e of its wire) and site i, the alias row over the wire's grid energies e' of
+//   w_e' K(E_e' - E_e) A_ii(E_e'),   K(dE) = exp(-dE^2 / (2 sigma^2)) (the identity for
+// sigma = 0), A_ii(E_e') the row sum of site row i of the wire's task at e' (after the alias
+// build), w_e' the energy's quadrature weight.  One warp per (task, site) row, into
+// etab + eoff(t) + i nE.
+__global__ void energy_alias_kernel(const TaskDesc* __restrict__ tasks, int n_tasks,
+                                    const EnergyDesc* __restrict__ edesc,
+                                    const uint32_t* __restrict__ job_base, uint32_t total_jobs,
+                                    int cap, double sigma, const double* __restrict__ rowsum,
+                                    uint64_t* __restrict__ etab, int32_t* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nwarps = blockDim.x >> 5;
+  unsigned char* base = smem_raw + (size_t)warp * alias_warp_bytes(cap, (int)sizeof(double));
+  uint64_t* s_u = reinterpret_cast<uint64_t*>(base);
+  uint64_t* s_c = s_u + (size_t)32 * alias_pitch(cap);
+  uint32_t* s_x = reinterpret_cast<uint32_t*>(s_c + (size_t)32 * alias_pitch(cap));
+  double* s_w = reinterpret_cast<double*>(base + alias_stage_off(cap));
+  for (uint32_t job = blockIdx.x * nwarps + warp; job < total_jobs; job += gridDim.x * nwarps) {
+    int lo = 0, hi = n_tasks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (job_base[mid] <= job) lo = mid; else hi = mid - 1;
+    }
+    const TaskDesc& d = tasks[lo];
+    const EnergyDesc ed = edesc[lo];
+    const int i = (int)(job - job_base[lo]);
+    const int nE = ed.nE;
+    const double inv2s2 = sigma > 0.0 ? 0.5 / (sigma * sigma) : 0.0;
+    for (int ep = lane; ep < nE; ep += 32) {
+      const TaskDesc& dp = tasks[ed.t0 + ep];
+      const double dE = dp.E - d.E;
+      const double K = sigma > 0.0 ? exp(-dE * dE * inv2s2) : (ep == d.e_idx ? 1.0 : 0.0);
+      s_w[ep] = dp.w_E * K * rowsum[dp.row_base + i];
+    }
+    __syncwarp();
+    double total = 0.0;
+    alias_row<double>(s_w, nE, 0.0, false, 0.0, 0.0, etab + ed.eoff + (uint64_t)i * nE, &total,
+                      s_u, s_c, s_x, err, [] {});
+    __syncwarp();
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_two_level_split(const TaskDesc* d_tasks, int n_tasks, uint32_t n_jobs,
@@ -527,6 +571,31 @@ cudaError_t launch_two_level_split(const TaskDesc* d_tasks, int n_tasks, uint32_
   if (max_W <= 16) return run(level2_cdf_kernel<float, 16>, 0.f, 16);
   if (max_W <= 32) return run(level2_cdf_kernel<float, 32>, 0.f, 32);
   return run(level2_cdf_kernel<float, 64>, 0.f, 64);
+}
+
+cudaError_t launch_energy_tables(const TaskDesc* d_tasks, int n_tasks, const EnergyDesc* d_edesc,
+                                 const uint32_t* d_job_base, uint32_t total_jobs, int max_nE,
+                                 double sigma, const double* d_rowsum, uint64_t* d_etab,
+                                 int32_t* d_err, cudaStream_t s) {
+  if (total_jobs == 0) return cudaSuccess;
+  const int cap = max_nE < 64 ? 64 : max_nE;
+  const size_t per_warp = alias_warp_bytes(cap, (int)sizeof(double));
+  int warps = 4;
+  while (warps > 1 && per_warp * warps > 200 * 1024) --warps;
+  const size_t smem = per_warp * warps;
+  if (smem > 220 * 1024) return cudaErrorInvalidValue;     // energy grids beyond shared memory
+  cudaError_t e = cudaFuncSetAttribute(energy_alias_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  uint32_t blocks = (total_jobs + warps - 1) / warps;
+  if (blocks > (uint32_t)sms * 16) blocks = (uint32_t)sms * 16;
+  energy_alias_kernel<<<blocks, warps * 32, smem, s>>>(d_tasks, n_tasks, d_edesc, d_job_base,
+                                                      total_jobs, cap, sigma, d_rowsum, d_etab,
+                                                      d_err);
+  return cudaGetLastError();
 }
 
 int alias_warps_max(int max_K) {

@@ -1410,6 +1410,144 @@ negf_status negf_walk(negf_ctx ctx, negf_tables t, int32_t start_lead, uint64_t 
   return NEGF_OK;
 }
 
+// Step 7' energy rows of every (task, site) of one-level tables (inelastic Buttiker probes):
+// descriptors, job bases and the alias rows, on the ctx stream.  d_edesc and d_etab are the
+// caller's to free (stream-ordered).
+static negf_status energy_tables(negf_ctx ctx, negf_tables t, double sigma, const char* who,
+                                 negf::EnergyDesc** d_edesc, uint64_t** d_etab,
+                                 std::vector<negf::EnergyDesc>* h_out) {
+  *d_edesc = nullptr;
+  *d_etab = nullptr;
+  if (!(sigma >= 0.0) || !isfinite(sigma))
+    return fail(ctx, NEGF_E_INVALID, "%s: sigma_E must be finite and >= 0", who);
+  if (t->any_two)
+    return fail(ctx, NEGF_E_INVALID, "%s: inelastic walks need one-level tables", who);
+  const cudaStream_t s = ctx->stream;
+  std::vector<negf::EnergyDesc> ed(std::max(1, t->n_tasks));
+  std::vector<uint32_t> jb(std::max(1, t->n_tasks));
+  uint64_t eoff = 0, jobs = 0;
+  int max_nE = 1;
+  for (int w = 0; w < t->n_wires; ++w) {
+    const int k0 = t->h_wire_task0[w], k1 = t->h_wire_task0[w + 1];
+    for (int k = k0; k < k1; ++k) {
+      ed[k].eoff = eoff;
+      ed[k].nE = k1 - k0;
+      ed[k].t0 = k0;
+      jb[k] = (uint32_t)jobs;
+      eoff += (uint64_t)t->h_tasks[k].n * (k1 - k0);
+      jobs += (uint64_t)t->h_tasks[k].n;
+      max_nE = std::max(max_nE, k1 - k0);
+    }
+  }
+  if (jobs > 0xffffffffull || max_nE > 4096)
+    return fail(ctx, NEGF_E_INVALID, "%s: too many sites or energies for the energy rows", who);
+  cudaError_t e = dalloc(d_edesc, ed.size(), s, nullptr);
+  uint32_t* d_jb = nullptr;
+  if (e == cudaSuccess) e = dalloc(&d_jb, jb.size(), s, nullptr);
+  if (e == cudaSuccess) e = dalloc(d_etab, std::max<uint64_t>(eoff, 1), s, nullptr);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(*d_edesc, ed.data(), sizeof(negf::EnergyDesc) * ed.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(d_jb, jb.data(), sizeof(uint32_t) * jb.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    ProfScope ps(ctx, "energy_alias_kernel", 1);
+    e = negf::launch_energy_tables(t->d_tasks, t->n_tasks, *d_edesc, d_jb, (uint32_t)jobs,
+                                   max_nE, sigma, t->d_rowsum, *d_etab, t->d_err, s);
+  }
+  // the host copies of ed and jb must outlive the asynchronous copies
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  dfree(d_jb, s);
+  if (e != cudaSuccess) {
+    dfree(*d_edesc, s);
+    dfree(*d_etab, s);
+    return fail(ctx, NEGF_E_CUDA, "%s: %s", who, cudaGetErrorString(e));
+  }
+  if (h_out) *h_out = ed;
+  return NEGF_OK;
+}
+
+negf_status negf_walk_inelastic(negf_ctx ctx, negf_tables t, int32_t start_lead, uint64_t seed,
+                                uint64_t walkers_per_task, uint64_t walker_id_offset,
+                                uint32_t max_steps, double sigma_E, negf_tally* out) {
+  negf_status st = walk_common(ctx, t, start_lead, max_steps, "negf_walk_inelastic");
+  if (st != NEGF_OK) return st;
+  if (!out) return fail(ctx, NEGF_E_INVALID, "negf_walk_inelastic: out is NULL");
+  *out = nullptr;
+  if (walkers_per_task > (1ull << 40))
+    return fail(ctx, NEGF_E_INVALID, "negf_walk_inelastic: walkers_per_task above 2^40");
+  DeviceGuard g(ctx->device);
+  negf::EnergyDesc* d_edesc = nullptr;
+  uint64_t* d_etab = nullptr;
+  st = energy_tables(ctx, t, sigma_E, "negf_walk_inelastic", &d_edesc, &d_etab, nullptr);
+  if (st != NEGF_OK) return st;
+  negf_tally tl = new (std::nothrow) negf_tally_s;
+  if (!tl) {
+    dfree(d_edesc, ctx->stream);
+    dfree(d_etab, ctx->stream);
+    return fail(ctx, NEGF_E_NOMEM, "negf_walk_inelastic: host allocation");
+  }
+  tl->ctx = ctx;
+  tl->n_tasks = t->n_tasks;
+  tl->start_lead = start_lead;
+  const size_t nc = (size_t)std::max(1, t->n_tasks) * NEGF_TALLY_FIELDS;
+  cudaError_t e = dalloc(&tl->d_counts, nc, ctx->stream, nullptr);
+  if (e == cudaSuccess) e = cudaMemsetAsync(tl->d_counts, 0, sizeof(uint64_t) * nc, ctx->stream);
+  if (e == cudaSuccess) {
+    ProfScope ps(ctx, "inelastic_walk_kernel", (t->n_tasks + 1023) / 1024);
+    e = negf::launch_inelastic_walk(t->d_tasks, t->n_tasks, d_edesc, t->d_tab, t->d_mode_tab,
+                                    t->d_c, d_etab, start_lead, seed, walkers_per_task,
+                                    walker_id_offset, max_steps, tl->d_counts, ctx->sm_count,
+                                    ctx->stream);
+  }
+  dfree(d_edesc, ctx->stream);
+  dfree(d_etab, ctx->stream);
+  if (e != cudaSuccess) {
+    dfree(tl->d_counts, ctx->stream);
+    delete tl;
+    return fail(ctx, NEGF_E_CUDA, "negf_walk_inelastic: %s", cudaGetErrorString(e));
+  }
+  *out = tl;
+  return NEGF_OK;
+}
+
+negf_status negf_export_energy_tables(negf_ctx ctx, negf_tables t, int32_t task, double sigma_E,
+                                      void* host_buf, size_t* bytes) {
+  if (!ctx || !t || t->ctx != ctx || !bytes)
+    return fail(ctx, NEGF_E_INVALID, "negf_export_energy_tables: bad argument");
+  if (task < 0 || task >= t->n_tasks)
+    return fail(ctx, NEGF_E_INVALID, "negf_export_energy_tables: task %d out of range", task);
+  int nE = 0;
+  for (int w = 0; w < t->n_wires; ++w)
+    if (task >= t->h_wire_task0[w] && task < t->h_wire_task0[w + 1])
+      nE = t->h_wire_task0[w + 1] - t->h_wire_task0[w];
+  const size_t need = sizeof(uint64_t) * (size_t)t->h_tasks[task].n * nE;
+  if (!host_buf) {
+    *bytes = need;
+    return NEGF_OK;
+  }
+  if (*bytes < need)
+    return fail(ctx, NEGF_E_INVALID, "negf_export_energy_tables: buffer of %zu bytes, need %zu",
+                *bytes, need);
+  DeviceGuard g(ctx->device);
+  negf::EnergyDesc* d_edesc = nullptr;
+  uint64_t* d_etab = nullptr;
+  std::vector<negf::EnergyDesc> ed;
+  negf_status st = energy_tables(ctx, t, sigma_E, "negf_export_energy_tables", &d_edesc, &d_etab, &ed);
+  if (st != NEGF_OK) return st;
+  cudaError_t e = cudaMemcpyAsync(host_buf, d_etab + ed[task].eoff, need, cudaMemcpyDeviceToHost,
+                                  ctx->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  dfree(d_edesc, ctx->stream);
+  dfree(d_etab, ctx->stream);
+  if (e != cudaSuccess) return fail(ctx, NEGF_E_CUDA, "negf_export_energy_tables: %s", cudaGetErrorString(e));
+  int32_t err = 0;
+  if (cudaMemcpy(&err, t->d_err, sizeof(err), cudaMemcpyDeviceToHost) == cudaSuccess && err)
+    return fail(ctx, NEGF_E_NUMERIC, "negf_export_energy_tables: energy rows not finite");
+  *bytes = need;
+  return NEGF_OK;
+}
+
 negf_status negf_walk_trace(negf_ctx ctx, negf_tables t, int32_t task, int32_t start_lead,
                             uint64_t seed, uint64_t walker_id_offset, uint64_t n_walkers,
                             uint32_t max_steps, int32_t* d_lead, uint32_t* d_steps) {

@@ -138,6 +138,27 @@ cudaError_t launch_block_columns(const TaskDesc* d_tasks, int n_tasks, uint32_t 
                                  int chain_warps = 0, int cols_max_W = -1);
 // Warps per CTA the chain kernel can use for max_W (shared memory bound), and its default.
 int chain_warps_max(int max_W, int precision);
+// Inelastic Buttiker probes (Step 7'): per task, its wire's first task t0, number of grid
+// energies nE and the offset of its energy rows [n][nE] in the energy table.
+struct EnergyDesc {
+  uint64_t eoff;
+  int32_t nE, t0;
+};
+// Step 7' energy alias rows of every (task, site): job_base[k] = first job of task k (its n
+// sites follow); d_rowsum after the alias build (A_ii of every site row).
+cudaError_t launch_energy_tables(const TaskDesc* d_tasks, int n_tasks, const EnergyDesc* d_edesc,
+                                 const uint32_t* d_job_base, uint32_t total_jobs, int max_nE,
+                                 double sigma, const double* d_rowsum, uint64_t* d_etab,
+                                 int32_t* d_err, cudaStream_t s);
+// Inelastic walks of every task (injection at the task's energy; Step 6' rows of the walker's
+// current energy, Step 7' energy rows after every site), tallied per injection task as the
+// elastic walk's tally.
+cudaError_t launch_inelastic_walk(const TaskDesc* d_tasks, int n_tasks, const EnergyDesc* d_edesc,
+                                  const uint64_t* d_tab, const uint64_t* d_mode_tab,
+                                  const double* d_c, const uint64_t* d_etab, int start_lead,
+                                  uint64_t seed, uint64_t walkers_per_task, uint64_t id_offset,
+                                  uint32_t max_steps, uint64_t* d_tally, int sm_count,
+                                  cudaStream_t s);
 // Alias tables of every row (and mode row); replaces the A values in rowsum by the FP64 row
 // sums after checking them.
 cudaError_t launch_alias_build(const TaskDesc* d_tasks, int n_tasks, uint32_t total_jobs,

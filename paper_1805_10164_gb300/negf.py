@@ -118,6 +118,8 @@ def load():
         "negf_tables_num_waves": (I32, [P]),
         "negf_probe_gather": (I32, [P, U64, I32, I32, C.POINTER(D)]),
         "negf_walk_score": (I32, [P, P, I32, U64, U64, U64, U32, C.POINTER(P)]),
+        "negf_walk_inelastic": (I32, [P, P, I32, U64, U64, U64, U32, C.c_double, C.POINTER(P)]),
+        "negf_export_energy_tables": (I32, [P, P, I32, C.c_double, P, C.POINTER(C.c_size_t)]),
         "negf_tally_score_counts": (I32, [P, P, P, P]),
         "negf_tally_score_accumulate": (I32, [P, P, P, P]),
         "negf_tally_score_size": (U64, [P]),
@@ -428,6 +430,28 @@ def negf_probe_gather(ctx, table_bytes, ilp=8, chain=64):
     _check(ctx, load().negf_probe_gather(ctx, int(table_bytes), int(ilp), int(chain),
                                          C.byref(out)))
     return out.value
+
+
+def negf_walk_inelastic(ctx, tables, start_lead, seed, walkers_per_task, sigma_E,
+                        walker_id_offset=0, max_steps=1 << 20):
+    out = C.c_void_p()
+    _check(ctx, load().negf_walk_inelastic(ctx, tables, int(start_lead), int(seed),
+                                           int(walkers_per_task), int(walker_id_offset),
+                                           int(max_steps), float(sigma_E), C.byref(out)))
+    return out
+
+
+def negf_export_energy_tables(ctx, tables, task, sigma_E):
+    """The Step 7' energy rows of a task: uint64 [n, nE] alias entries."""
+    lib = load()
+    nbytes = C.c_size_t(0)
+    _check(ctx, lib.negf_export_energy_tables(ctx, tables, int(task), float(sigma_E), None,
+                                              C.byref(nbytes)))
+    buf = np.empty(nbytes.value // 8, dtype=np.uint64)
+    _check(ctx, lib.negf_export_energy_tables(ctx, tables, int(task), float(sigma_E),
+                                              buf.ctypes.data, C.byref(nbytes)))
+    info = negf_get_task_info(ctx, tables, task)
+    return buf.reshape(info["n"], -1)
 
 
 def negf_walk_score(ctx, tables, start_lead, seed, walkers_per_task, walker_id_offset=0,

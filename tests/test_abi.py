@@ -33,7 +33,7 @@ def test_library_exports_every_declared_symbol(lib_path):
     lib = ctypes.CDLL(lib_path)
     missing = [n for n in declared_functions() if not hasattr(lib, n)]
     assert not missing, missing
-    assert lib.negf_abi_version() == 5
+    assert lib.negf_abi_version() == 6
 
 
 def test_binding_signatures_cover_header(lib_path):
