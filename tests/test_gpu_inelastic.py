@@ -153,3 +153,47 @@ def test_refusals(ctx):
     finally:
         negf.negf_tables_free(two)
         negf.negf_tables_free(one)
+
+
+def test_several_wires_in_one_handle(ctx):
+    """Energy rows and walks of wires of different widths, lengths and grids in one table
+    handle: each wire's walkers hop over its own grid only (tallies count for count against
+    the oracle walker on each wire's exported tables)."""
+    wires = [inputs.small_wire(82, W=2, L=5, n_energy=4, eta=0.5, e_lo=-1.8, e_hi=1.8),
+             inputs.small_wire(83, W=4, L=3, n_energy=7, eta=0.3, e_lo=-3.2, e_hi=3.2)]
+    sigma = 0.6
+    tables = negf.negf_build_tables(ctx, wires, precision="fp64")
+    try:
+        N, seed = 1500, 0xBEE5
+        for p in (0, 1):
+            tally = negf.negf_walk_inelastic(ctx, tables, p, seed + p, N, sigma)
+            try:
+                got = negf.negf_tally_counts(ctx, tally, sum(len(w.energy) for w in wires))
+            finally:
+                negf.negf_tally_free(tally)
+            t0 = 0
+            for w in wires:
+                nE = len(w.energy)
+                ent, ment, c_open, erows = [], [], [], []
+                for k in range(nE):
+                    info = negf.negf_get_task_info(ctx, tables, t0 + k)
+                    ent.append(negf.negf_export_tables(ctx, tables, t0 + k, "alias").reshape(
+                        info["rows"], info["K"]))
+                    ment.append(negf.negf_export_tables(ctx, tables, t0 + k, "mode_alias").reshape(
+                        2, info["W"]))
+                    c_open.append(info["c"] > 0)
+                    erows.append(negf.negf_export_energy_tables(ctx, tables, t0 + k, sigma))
+                ent, ment, c_open = np.stack(ent), np.stack(ment), np.stack(c_open)
+                erows = np.stack(erows, axis=1)
+                assert erows.shape == (w.W * w.L, nE, nE)
+                for e0 in range(nE):
+                    lead, steps = inelastic.walk(ent, ment, erows, w.W * w.L, w.W, c_open, e0,
+                                                 t0 + e0, p, seed + p, np.arange(N, dtype=np.uint64),
+                                                 1 << 20)
+                    want = [N, np.sum(lead == 0), np.sum(lead == 1), np.sum(lead == -2),
+                            int(steps.astype(np.uint64).sum())]
+                    assert np.array_equal(got[t0 + e0].astype(np.int64),
+                                          np.array(want, dtype=np.int64)), (p, t0, e0)
+                t0 += nE
+    finally:
+        negf.negf_tables_free(tables)
