@@ -73,3 +73,16 @@ def test_rooflines_of_a_step():
     assert r["two_level_kernel"]["bound"] == "hbm" and 0.2 < r["two_level_kernel"]["frac"] < 1.0
     assert r["walk_kernel"]["bound"] == "hbm"
     assert "rgf_sweep_kernel" not in r
+
+
+def test_traffic_is_reported_per_launch():
+    """The measured DRAM traffic of the headline chain (keyed to the current sources) over the
+    launches of a step: the figure of the average launch, as achieved is its rate."""
+    wl = bench.workload("wire_64x1000")
+    tps = bench.measured_traffic("chain_cta_kernel", wl.name)
+    assert tps is not None and tps > 0
+    prof = {"chain_cta_kernel": (2 * 86, 2 * 7706.0)}
+    counts = np.zeros((256, 5), dtype=np.uint64)
+    r = bench.rooflines(prof, wl, "fp32", counts, 2)["chain_cta_kernel"]
+    assert r["traffic_per_step"] == tps
+    assert r["traffic"] == int(tps / 86)
